@@ -1,0 +1,177 @@
+/*
+ * msgfem.h -- C ABI of the GB300 (sm_103a) MS-GFEM local stage.
+ *
+ * Multiscale-spectral GFEM for 3-D anisotropic linear elasticity on a
+ * laminated beam (Benezech et al., arXiv 2211.13893).  The library computes,
+ * for every overlapping subdomain Omega_j with oversampling domain Omega*_j:
+ *   - the subdomain stiffness a_{Omega*_j} of trilinear hexahedra with
+ *     ply-rotated orthotropic tensors (Sec. 2, Eqs. eq-hooke, weak_form,
+ *     element_stiffness, restricted_bilinear_form);
+ *   - the n_loc smallest eigenpairs of the A-harmonic local eigenproblem
+ *     (Sec. 3.3, Eq. AHarmonicGeneralizeEigenProblem; matrix form
+ *     Eq. algebraicAharmonic) and the local particular function (Eq. up_r);
+ *   - the partition-of-unity weighted basis and its Galerkin contribution to
+ *     the coarse problem (Eq. AHarmonic_coarse_space, Sec. 4.3-4.4,
+ *     Eq. GFEM_coarse_approximation), and the coarse solution u^G.
+ *
+ * Geometry and numbering.  The mesh is a box of nx * ny * nz bricks of size
+ * hx * hy * hz; node (i, j, k) sits at (i hx, j hy, k hz) and has global id
+ * (i (ny+1) + j)(nz+1) + k; DoF 3 id + c holds displacement component c.
+ * Element (i, j, k) has index (i ny + j) nz + k; layer k is ply k.  The x = 0
+ * face is clamped (Gamma_D, zero displacement); the x = L face carries a
+ * uniform compressive traction (-traction, 0, 0); the other faces are free.
+ *
+ * Decomposition.  The non-overlapping subdomains are an sx * sy box partition
+ * in (x, y) over the full thickness (Sec. 3.1); subdomain (a, b) has index
+ * j = a sy + b.  Omega_j grows the box by `overlap` element layers,
+ * Omega*_j by `oversampling` layers, both counted from the non-overlapping
+ * box and clipped to the mesh (Secs. 3.3, 4.2).
+ *
+ * Memory and ownership.  All pointers passed in are owned by the caller and
+ * are read (and copied where needed) during the call only.  Output arrays are
+ * caller-allocated; an output pointer may be host or device memory (the
+ * library checks with cudaPointerGetAttributes).  Device memory used by the
+ * computation is owned by the handle: it is allocated by msgfem_setup with
+ * cudaMalloc and released by msgfem_destroy.  Work is issued on the stream
+ * given in msgfem_options (NULL = legacy default stream); every call returns
+ * only after its results are complete on that stream.
+ *
+ * Errors.  Every call returns a status; msgfem_last_error gives a message.
+ * Calls must come in the order setup -> local_spaces -> coarse_assemble ->
+ * solve (MSGFEM_ESTATE otherwise); local_spaces may be repeated after
+ * msgfem_update_angles.  A handle is not thread-safe.
+ */
+#ifndef MSGFEM_H
+#define MSGFEM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct msgfem* msgfem_h;
+
+typedef enum {
+  MSGFEM_OK = 0,
+  MSGFEM_EINVAL = 1,    /* invalid argument or descriptor */
+  MSGFEM_ENOMEM = 2,    /* device or host allocation failed */
+  MSGFEM_ECUDA = 3,     /* a CUDA call failed */
+  MSGFEM_ENOTSPD = 4,   /* a local matrix lost positive definiteness in a pivot */
+  MSGFEM_ENOCONV = 5,   /* eigensolver hit max_iter; results are the last iterate */
+  MSGFEM_ESTATE = 6     /* call out of order */
+} msgfem_status;
+
+/* Box mesh of nx * ny * nz bricks (Sec. 5.1: one element per ply). */
+typedef struct {
+  int nx, ny, nz;
+  double hx, hy, hz;
+  double traction;      /* magnitude of the compressive traction on x = L (MPa) */
+} msgfem_mesh;
+
+/* Orthotropic ply material and fibre angles (Sec. 5.1).
+ * E9 = {E11, E22, E33, G12, G13, G23, nu12, nu13, nu23} in the ply axes.
+ * elem_angle_deg[(i ny + j) nz + k] is the fibre angle of element (i, j, k),
+ * measured from x toward y about +z (host or device pointer). */
+typedef struct {
+  const double* E9;
+  const double* elem_angle_deg;
+} msgfem_plies;
+
+typedef struct {
+  int sx, sy;           /* subdomains along x and y */
+} msgfem_partition;
+
+typedef enum { MSGFEM_FP64 = 0, MSGFEM_MIXED = 1 } msgfem_precision;
+
+typedef struct {
+  int precision;        /* msgfem_precision */
+  int block;            /* subspace block size p; 0 = n_loc + max(8, n_loc / 2) */
+  int max_iter;         /* eigensolver iteration cap; 0 = 100 */
+  double tol;           /* stop when ||theta E S^-1 T x - x||_T <= tol per wanted pair (or the
+                           decrease stalls below 1e2 tol); 0 = 1e-7 */
+  unsigned long long seed;  /* seed of the counter-based start-block generator */
+  void* stream;         /* cudaStream_t to issue work on; NULL = default stream */
+  int profile;          /* 1: time the phases with CUDA events (msgfem_get_profile) */
+} msgfem_options;
+
+/* Phase timers (CUDA events on the handle's stream, milliseconds, summed over
+ * calls since msgfem_setup or the last msgfem_reset_profile) and algorithmic
+ * work of the last local stage.  Flop counts use the unpadded layer sizes:
+ * factorisation sum_l (n^3/3 + n^3/3 [inverse] + 2 n^3 [update, panel]) per
+ * matrix; one block solve (4 (nL - 1) + 2 nL) n^2 p. */
+typedef struct {
+  double assemble_ms;   /* element stiffness, stencils, layer blocks */
+  double factor_ms;     /* layer-block Cholesky + inverses of K and A11 */
+  double solve_ms;      /* all block triangular solves of the iteration */
+  double iterate_ms;    /* the whole eigen-iteration including solves */
+  double coarse_ms;     /* coarse_assemble + solve */
+  double factor_flops;  /* per local stage */
+  double solve_flops;   /* per local stage, all solve calls */
+  long long launches;   /* kernel launches issued by the library (all calls) */
+  int solve_calls;      /* block solves in the last local stage */
+} msgfem_profile;
+
+/* Per-subdomain diagnostics filled by msgfem_get_info. */
+typedef struct {
+  int n_star_dof;       /* DoFs of Omega*_j */
+  int n1, n2, n3;       /* sizes of the DoF classes B1, B2, B3 (Sec. 4.3) */
+  int floating;         /* 1 if Omega*_j does not touch the clamped face */
+  int iterations;       /* eigensolver iterations used */
+  int basis_size;       /* coarse basis functions contributed (n_loc [+1]) */
+  double residual;      /* max relative eigen-residual over the n_loc pairs */
+} msgfem_subinfo;
+
+/* Partition, DoF classes (Sec. 4.3) and partition of unity (Sec. 4.2) on the
+ * host; copies the angles and allocates all device memory.  The handle is
+ * written to *out.  Errors: EINVAL (sizes <= 0, overlap < 1, oversampling <
+ * overlap, a subdomain without interior), ENOMEM, ECUDA. */
+msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies,
+                           const msgfem_partition* part, int overlap, int oversampling,
+                           const msgfem_options* opt, msgfem_h* out);
+
+/* Replace the element angles (same layout as msgfem_plies.elem_angle_deg). */
+msgfem_status msgfem_update_angles(msgfem_h h, const double* elem_angle_deg);
+
+/* The local stage: element stiffness and subdomain matrices (Eqs.
+ * element_stiffness, restricted_bilinear_form), the n_loc smallest eigenpairs
+ * of Eq. AHarmonicGeneralizeEigenProblem per subdomain (subspace iteration
+ * with shift-invert at zero, Rayleigh-Ritz in FP64) and the particular
+ * functions (Eq. up_r).  lambda_out (N * n_loc doubles, subdomain-major,
+ * ascending; may be NULL) receives the eigenvalues.  Errors: EINVAL
+ * (n_loc < 1 or larger than the A-harmonic space of a subdomain), ENOTSPD,
+ * ENOCONV, ECUDA. */
+msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out);
+
+/* PoU-weighted basis with Gram-Schmidt and the appended particular function
+ * (Sec. 4.3-4.4), coarse matrix A^H_{ij} = V_i^T A V_j and load b^H
+ * (Eq. GFEM_coarse_approximation).  *coarse_dim_out receives dim V_H. */
+msgfem_status msgfem_coarse_assemble(msgfem_h h, int* coarse_dim_out);
+
+/* Coarse solve A^H c = b^H (FP64 Cholesky) and u^G = sum_j V_j c_j.
+ * u_out receives u^G on all 3 (nx+1)(ny+1)(nz+1) DoFs (may be NULL).  If
+ * u_ref is not NULL (fine solution u_h, same layout), *energy_err_out
+ * receives ||u_ref - u^G||_a / ||u_ref||_a (Theorem 1). */
+msgfem_status msgfem_solve(msgfem_h h, double* u_out, const double* u_ref, double* energy_err_out);
+
+/* Eigenvectors of subdomain j on the DoFs of Omega*_j, column-major
+ * n_star_dof * n_loc, normalised phi^T B phi = 1 (B as in Eq.
+ * algebraicAharmonic).  Node (i, j, k) of the Omega*_j node box
+ * [i0, i1] x [j0, j1] x [0, nz] has local id ((i - i0)(j1 - j0 + 1) + (j - j0))(nz + 1) + k
+ * and local DoFs 3 id + c; DoFs in B3 are zero.  *rows and *cols receive the
+ * shape; phi_out may be NULL to query it.  box_out (may be NULL) receives the
+ * Omega*_j node box {i0, i1, j0, j1}. */
+msgfem_status msgfem_get_basis(msgfem_h h, int j, double* phi_out, int* rows, int* cols, int* box_out);
+
+msgfem_status msgfem_get_info(msgfem_h h, int j, msgfem_subinfo* info);
+/* Copy the phase timers (requires msgfem_options.profile = 1 for times). */
+msgfem_status msgfem_get_profile(msgfem_h h, msgfem_profile* out);
+msgfem_status msgfem_reset_profile(msgfem_h h);
+int msgfem_num_subdomains(msgfem_h h);
+const char* msgfem_last_error(msgfem_h h);
+void msgfem_destroy(msgfem_h h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

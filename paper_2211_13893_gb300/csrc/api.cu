@@ -1,0 +1,664 @@
+// C ABI of libmsgfem and the driver of the local stage (see include/msgfem.h).
+//
+// Local stage per subdomain (batched over all subdomains in every launch):
+//  1. K_e per element type, node stencils of a_{Omega*}, layer blocks of
+//     K = A_{Omega*}[B1+B2, B1+B2] and A11 (Eqs. element_stiffness,
+//     restricted_bilinear_form, algebraicAharmonic);
+//  2. layer-block Cholesky with block inverses of K (pinned 3-2-1 on floating
+//     subdomains) and A11;
+//  3. subspace iteration for S x = lambda T x (S = E^T K E, T = E^T B E,
+//     E = [-A11^{-1} A12; I], the reduced form of Eq. algebraicAharmonic)
+//     with shift-invert at zero through S^{-1} E^T = [K^{-1}]_{2,:}: each
+//     step solves W = K^{-1} B Phi and re-extends X = W|B2 A-harmonically,
+//     Phi = E X (one A11 solve), followed by Rayleigh-Ritz in FP64.  On
+//     floating subdomains the six rigid modes are the exact lambda = 0
+//     eigenvectors; the iteration runs in their B-orthogonal complement;
+//  4. the particular function psi (Eq. up_r, one A11 solve);
+//  5. the relative eigen-residual ||S x - theta T x|| / (||S x|| + theta ||T x||).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "internal.h"
+
+msgfem_status cuda_fail(msgfem* h, cudaError_t e, const char* what, const char* file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "CUDA error %s (%s) in %s at %s:%d", cudaGetErrorName(e), cudaGetErrorString(e), what,
+           file, line);
+  if (h) h->err = buf;
+  return MSGFEM_ECUDA;
+}
+
+#define CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return cuda_fail(h, e_, #x, __FILE__, __LINE__); } while (0)
+#define CK_LAUNCH() CK(cudaGetLastError())
+
+namespace {
+
+template <typename T>
+msgfem_status dalloc(msgfem* h, T** p, size_t count) {
+  void* ptr = nullptr;
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(&ptr, bytes);
+  if (e != cudaSuccess) {
+    h->err = "cudaMalloc failed for " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e);
+    return MSGFEM_ENOMEM;
+  }
+  h->allocs.push_back(ptr);
+  *p = static_cast<T*>(ptr);
+  return MSGFEM_OK;
+}
+
+#define TRY(x) do { msgfem_status st_ = (x); if (st_ != MSGFEM_OK) return st_; } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+msgfem_status set_angles(msgfem* h, const double* ang) {
+  const size_t nel = (size_t)h->NX * h->NY * h->NZ;
+  h->h_angles.resize(nel);
+  if (is_device_ptr(ang)) {
+    CK(cudaMemcpy(h->h_angles.data(), ang, nel * sizeof(double), cudaMemcpyDeviceToHost));
+  } else {
+    memcpy(h->h_angles.data(), ang, nel * sizeof(double));
+  }
+  for (size_t e = 0; e < nel; ++e)
+    if (!std::isfinite(h->h_angles[e])) {
+      h->err = "non-finite element angle";
+      return MSGFEM_EINVAL;
+    }
+  // element types: one per ply when the angle depends on the layer only
+  bool layered = true;
+  for (size_t e = 0; e < nel && layered; ++e) layered = h->h_angles[e] == h->h_angles[e % h->NZ];
+  std::vector<double> types;
+  if (layered) {
+    types.assign(h->h_angles.begin(), h->h_angles.begin() + h->NZ);
+  } else {
+    types = h->h_angles;
+  }
+  if ((int)types.size() > h->type_cap) {
+    h->type_cap = (int)types.size();
+    TRY(dalloc(h, &h->d_angles_type, types.size()));
+    TRY(dalloc(h, &h->d_Ke, types.size() * 576));
+  }
+  h->layered = layered ? 1 : 0;
+  h->ntypes = (int)types.size();
+  CK(cudaMemcpyAsync(h->d_angles_type, types.data(), types.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return MSGFEM_OK;
+}
+
+msgfem_status allocate(msgfem* h) {
+  for (int j = 0; j < h->N; ++j) {
+    SubDev& s = h->sub[j];
+    HostSub& hs = h->hsub[j];
+    const size_t bK2 = (size_t)s.bK * s.bK, bA2 = (size_t)s.bA * s.bA;
+    TRY(dalloc(h, &s.stencil, (size_t)s.nnode * 243));
+    TRY(dalloc(h, &s.mu, s.nnode));
+    signed char* cls;
+    TRY(dalloc(h, &cls, s.npl));
+    s.cls = cls;
+    TRY(dalloc(h, &s.mapK, s.bK));
+    TRY(dalloc(h, &s.mapA, s.bA));
+    TRY(dalloc(h, &s.invK, 3 * s.npl));
+    TRY(dalloc(h, &s.invA, 3 * s.npl));
+    TRY(dalloc(h, &s.DK, bK2 * (2 * s.nzn - 1)));
+    s.EK = s.DK + bK2 * s.nzn;
+    TRY(dalloc(h, &s.LK, bK2 * s.nzn));
+    TRY(dalloc(h, &s.DA, bA2 * (2 * s.nzn - 1)));
+    s.EA = s.DA + bA2 * s.nzn;
+    TRY(dalloc(h, &s.LA, bA2 * s.nzn));
+    TRY(dalloc(h, &s.ycK, (size_t)s.nzn * s.bK * PST));
+    TRY(dalloc(h, &s.ycA, (size_t)s.nzn * s.bA * PST));
+    TRY(dalloc(h, &s.rcK, (size_t)s.bK * PST));
+    TRY(dalloc(h, &s.rcA, (size_t)s.bA * PST));
+    double** mvs[] = {&s.Phi, &s.Z, &s.KPhi, &s.W, &s.T1, &s.R, &s.BR, &s.EV, &s.CB, &s.CW};
+    for (double** m : mvs) {
+      TRY(dalloc(h, m, (size_t)s.nfull * PST));
+      CK(cudaMemset(*m, 0, (size_t)s.nfull * PST * sizeof(double)));
+    }
+    TRY(dalloc(h, &s.bload, s.nfull));
+    TRY(dalloc(h, &s.psi, s.nfull));
+    TRY(dalloc(h, &s.G1, PST * PST));
+    TRY(dalloc(h, &s.G2, PST * PST));
+    TRY(dalloc(h, &s.G3, PST * PST));
+    TRY(dalloc(h, &s.Y, PST * PST));
+    TRY(dalloc(h, &s.theta, PST));
+    TRY(dalloc(h, &s.resid, PST));
+    TRY(dalloc(h, &s.status, 4));
+    CK(cudaMemset(s.status, 0, 4 * sizeof(int)));
+    CK(cudaMemcpy(s.mu, hs.mu.data(), hs.mu.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(cls, hs.cls.data(), hs.cls.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s.mapK, hs.mapK.data(), hs.mapK.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s.mapA, hs.mapA.data(), hs.mapA.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s.invK, hs.invK.data(), hs.invK.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s.invA, hs.invA.data(), hs.invA.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s.bload, hs.bload.data(), hs.bload.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  TRY(dalloc(h, &h->d_sub, h->N));
+  CK(cudaMemcpy(h->d_sub, h->sub.data(), h->N * sizeof(SubDev), cudaMemcpyHostToDevice));
+  TRY(dalloc(h, &h->d_E9, 9));
+  CK(cudaMemcpy(h->d_E9, h->E9, 9 * sizeof(double), cudaMemcpyHostToDevice));
+  int maxnode = 0;
+  for (const auto& s : h->sub) maxnode = std::max(maxnode, s.nnode);
+  const size_t nchunk = (3 * (size_t)maxnode + 511) / 512;
+  TRY(dalloc(h, &h->d_gram_part, nchunk * h->N * PST * PST));
+  TRY(dalloc(h, &h->d_flags, h->N + 1));
+  TRY(dalloc(h, &h->d_notspd, h->N + 1));
+  TRY(dalloc(h, &h->d_ncols, h->N));
+  TRY(dalloc(h, &h->d_coff, h->N));
+  TRY(dalloc(h, &h->d_m, h->N));
+  TRY(dalloc(h, &h->d_pairs, h->pairs.size()));
+  CK(cudaMemcpy(h->d_pairs, h->pairs.data(), h->pairs.size() * sizeof(CoarsePair), cudaMemcpyHostToDevice));
+  int maxrows = 0;
+  for (const auto& p : h->pairs) maxrows = std::max(maxrows, (p.x1 - p.x0 + 1) * (p.y1 - p.y0 + 1) * (h->NZ + 1) * 3);
+  TRY(dalloc(h, &h->d_pair_part, ((size_t)maxrows + 511) / 512 * h->pairs.size() * PST * PST));
+  const size_t ndof = 3 * (size_t)(h->NX + 1) * (h->NY + 1) * (h->NZ + 1);
+  TRY(dalloc(h, &h->d_u, ndof));
+  TRY(dalloc(h, &h->d_ref, ndof));
+  TRY(dalloc(h, &h->d_energy, 2 * 1024));
+  // schedules
+  build_factor_schedule(h);
+  build_solve_schedules(h);
+  TRY(dalloc(h, &h->fact.d_gemm, h->fact.gemm.size()));
+  TRY(dalloc(h, &h->fact.d_potrf, h->fact.potrf.size()));
+  CK(cudaMemcpy(h->fact.d_gemm, h->fact.gemm.data(), h->fact.gemm.size() * sizeof(GemmTask), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->fact.d_potrf, h->fact.potrf.data(), h->fact.potrf.size() * sizeof(PotrfTask),
+                cudaMemcpyHostToDevice));
+  for (SolveSchedule* ss : {&h->solveK, &h->solveA}) {
+    TRY(dalloc(h, &ss->d_tasks, ss->tasks.size()));
+    CK(cudaMemcpy(ss->d_tasks, ss->tasks.data(), ss->tasks.size() * sizeof(SolveTask), cudaMemcpyHostToDevice));
+  }
+  return MSGFEM_OK;
+}
+
+msgfem_status set_active(msgfem* h, const std::vector<int>& act) {
+  std::vector<int> a(act);
+  a.push_back(1);
+  CK(cudaMemcpyAsync(h->d_flags, a.data(), a.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  return MSGFEM_OK;
+}
+
+template <typename T>
+msgfem_status read_sub_array(msgfem* h, int j, const T* dptr, T* out, size_t n) {
+  (void)j;
+  CK(cudaMemcpy(out, dptr, n * sizeof(T), cudaMemcpyDeviceToHost));
+  return MSGFEM_OK;
+}
+
+enum { TAG_ASSEMBLE = 0, TAG_FACTOR, TAG_SOLVE, TAG_ITERATE, TAG_COARSE };
+
+cudaEvent_t take_event(msgfem* h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+int span_begin(msgfem* h, int tag) {
+  if (!h->opt.profile) return -1;
+  msgfem::Span sp{tag, take_event(h), take_event(h)};
+  cudaEventRecord(sp.a, h->stream);
+  h->spans.push_back(sp);
+  return (int)h->spans.size() - 1;
+}
+
+void span_end(msgfem* h, int idx) {
+  if (idx >= 0) cudaEventRecord(h->spans[idx].b, h->stream);
+}
+
+void spans_collect(msgfem* h) {
+  if (h->spans.empty()) return;
+  cudaStreamSynchronize(h->stream);
+  for (auto& sp : h->spans) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, sp.a, sp.b);
+    double* dst = sp.tag == TAG_ASSEMBLE ? &h->prof.assemble_ms : sp.tag == TAG_FACTOR ? &h->prof.factor_ms
+                : sp.tag == TAG_SOLVE ? &h->prof.solve_ms : sp.tag == TAG_ITERATE ? &h->prof.iterate_ms
+                : &h->prof.coarse_ms;
+    *dst += ms;
+    h->ev_pool.push_back(sp.a);
+    h->ev_pool.push_back(sp.b);
+  }
+  h->spans.clear();
+}
+
+// algorithmic flops of the layer-block factorisation (unpadded sizes)
+double factor_flops(const msgfem* h) {
+  double f = 0.0;
+  for (const auto& s : h->sub)
+    for (int n : {s.nK, s.nA}) {
+      const double n3 = (double)n * n * n;
+      f += s.nzn * (2.0 * n3 / 3.0) + (s.nzn - 1) * 2.0 * n3;
+    }
+  return f;
+}
+
+double solve_flops(const msgfem* h, int mat, int p) {
+  double f = 0.0;
+  for (const auto& s : h->sub) {
+    const double n = mat == 0 ? s.nK : s.nA;
+    f += (4.0 * (s.nzn - 1) + 2.0 * s.nzn) * n * n * p;
+  }
+  return f;
+}
+
+void timed_solve(msgfem* h, int mat, int src, int dst, int neg) {
+  const int sp = span_begin(h, TAG_SOLVE);
+  run_solve_mv(mat == 0 ? h->solveK : h->solveA, h->stream, src, dst, neg);
+  span_end(h, sp);
+  h->prof.solve_flops += solve_flops(h, mat, h->p);
+  h->prof.solve_calls += 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, const msgfem_partition* part,
+                           int overlap, int oversampling, const msgfem_options* opt, msgfem_h* out) {
+  if (out == nullptr) return MSGFEM_EINVAL;
+  *out = nullptr;
+  if (!mesh || !plies || !part || !plies->E9 || !plies->elem_angle_deg) return MSGFEM_EINVAL;
+  if (mesh->nx <= 0 || mesh->ny <= 0 || mesh->nz <= 0 || !(mesh->hx > 0) || !(mesh->hy > 0) || !(mesh->hz > 0))
+    return MSGFEM_EINVAL;
+  if (part->sx <= 0 || part->sy <= 0 || part->sx > mesh->nx || part->sy > mesh->ny) return MSGFEM_EINVAL;
+  if (overlap < 1 || oversampling < overlap) return MSGFEM_EINVAL;
+  msgfem* h = new msgfem();
+  h->NX = mesh->nx; h->NY = mesh->ny; h->NZ = mesh->nz;
+  h->hx = mesh->hx; h->hy = mesh->hy; h->hz = mesh->hz; h->traction = mesh->traction;
+  memcpy(h->E9, plies->E9, sizeof(h->E9));
+  h->sx = part->sx; h->sy = part->sy; h->o = overlap; h->os = oversampling;
+  memset(&h->opt, 0, sizeof(h->opt));
+  if (opt) h->opt = *opt;
+  if (h->opt.max_iter <= 0) h->opt.max_iter = 100;
+  if (!(h->opt.tol > 0)) h->opt.tol = 1e-7;
+  h->stream = static_cast<cudaStream_t>(h->opt.stream);
+  *out = h;
+  msgfem_status st = build_problem(h);
+  if (st != MSGFEM_OK) return st;
+  st = allocate(h);
+  if (st != MSGFEM_OK) return st;
+  st = set_angles(h, plies->elem_angle_deg);
+  if (st != MSGFEM_OK) return st;
+  set_dense_context(h->d_flags, h->d_notspd, h->d_sub);
+  h->stage = 1;
+  return MSGFEM_OK;
+}
+
+msgfem_status msgfem_update_angles(msgfem_h h, const double* ang) {
+  if (!h || !ang) return MSGFEM_EINVAL;
+  if (h->stage < 1) return MSGFEM_ESTATE;
+  msgfem_status st = set_angles(h, ang);
+  if (st == MSGFEM_OK) h->stage = 1;
+  return st;
+}
+
+msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
+  if (!h) return MSGFEM_EINVAL;
+  if (h->stage < 1) return MSGFEM_ESTATE;
+  if (n_loc < 1) { h->err = "n_loc must be >= 1"; return MSGFEM_EINVAL; }
+  int p = h->opt.block > 0 ? h->opt.block : n_loc + std::max(8, n_loc / 2);
+  if (p > PST - 1) p = PST - 1;
+  for (int j = 0; j < h->N; ++j) {
+    const int nw = n_loc - (h->sub[j].floating ? 6 : 0);
+    if (n_loc > h->n2[j]) { h->err = "n_loc exceeds the B2 size of a subdomain"; return MSGFEM_EINVAL; }
+    if (nw > p) { h->err = "n_loc too large for the block size (at most 31 columns)"; return MSGFEM_EINVAL; }
+  }
+  h->n_loc = n_loc;
+  h->p = p;
+  cudaStream_t st = h->stream;
+  set_dense_context(h->d_flags, h->d_notspd, h->d_sub);
+  std::vector<int> act(h->N, 1);
+  TRY(set_active(h, act));
+  CK(cudaMemsetAsync(h->d_notspd, 0, (h->N + 1) * sizeof(int), st));
+  for (auto& s : h->sub) CK(cudaMemsetAsync(s.status, 0, 4 * sizeof(int), st));
+  h->prof.factor_flops = factor_flops(h);
+  h->prof.solve_flops = 0.0;
+  h->prof.solve_calls = 0;
+  // 1. assembly
+  int sp = span_begin(h, TAG_ASSEMBLE);
+  launch_element_stiffness(h);
+  launch_stencil(h);
+  launch_layer_blocks(h);
+  span_end(h, sp);
+  CK_LAUNCH();
+  // 2. factorisations of K and A11
+  sp = span_begin(h, TAG_FACTOR);
+  run_schedule(h->fact, st);
+  span_end(h, sp);
+  CK_LAUNCH();
+  const int sp_iter = span_begin(h, TAG_ITERATE);
+  // rigid modes, B-orthonormal (floating)
+  launch_rigid_modes(h);
+  launch_stencil_apply(h, MV_R, MV_BR, 3, 1.0);
+  launch_gram(h, MV_R, MV_BR, GM_G1);
+  launch_chol_inv_small(h, GM_G1, nullptr, 6, 0);
+  launch_rotate(h, MV_R, GM_Y, 6);
+  launch_rotate(h, MV_BR, GM_Y, 6);
+  // 3. start block X0 on B2, A-harmonic extension, and psi in the last column
+  launch_random_b2(h, MV_W, p, h->opt.seed);
+  launch_stencil_apply(h, MV_W, MV_T1, 0, 1.0);
+  launch_copy_col(h, SRC_BLOAD, 0, MV_T1, PST - 1, -1.0);
+  timed_solve(h, 1, MV_T1, MV_W, 1);
+  launch_copy_col(h, MV_W, PST - 1, SRC_PSI, 0, 1.0);
+  launch_copy_col(h, MV_W, PST - 1, MV_W, PST - 1, 0.0);
+  launch_gram(h, MV_BR, MV_W, GM_G3);
+  launch_sub_rc(h, MV_W, MV_R, GM_G3, 6);
+  launch_copy_mv(h, MV_W, MV_PHI);
+  CK_LAUNCH();
+  h->iters.assign(h->N, 0);
+  std::vector<double> theta((size_t)h->N * PST), gdiag((size_t)h->N * PST * PST);
+  int it = 0;
+  bool all_done = false;
+  std::vector<std::vector<double>> dhist(h->N);
+  for (it = 0; it < h->opt.max_iter; ++it) {
+    // Rayleigh-Ritz on span(Phi) (Phi is B-orthogonal to the rigid modes)
+    launch_stencil_apply(h, MV_PHI, MV_Z, 3, 1.0);
+    launch_stencil_apply(h, MV_PHI, MV_KPHI, 0, 1.0);
+    launch_gram(h, MV_PHI, MV_Z, GM_G1);
+    launch_gram(h, MV_PHI, MV_KPHI, GM_G2);
+    launch_small_eig(h, p);
+    launch_rotate(h, MV_PHI, GM_Y, p);
+    launch_rotate(h, MV_Z, GM_Y, p);
+    launch_rotate(h, MV_KPHI, GM_Y, p);
+    // shift-invert step: W = K^{-1} Z, X = W|B2, Phi_new = E X
+    timed_solve(h, 0, MV_Z, MV_W, 0);
+    launch_zero_pins(h, MV_W);
+    launch_mask_rows(h, MV_W, 1 << 2);
+    launch_stencil_apply(h, MV_W, MV_T1, 0, 1.0);
+    timed_solve(h, 1, MV_T1, MV_W, 1);
+    // B-orthogonal projection out of the rigid modes (floating subdomains)
+    launch_gram(h, MV_BR, MV_W, GM_G3);
+    launch_sub_rc(h, MV_W, MV_R, GM_G3, 6);
+    // convergence: d_i = theta_i Phi_new_i - Phi_i vanishes at an eigenpair;
+    // ||d_i||_T = ||D_mu d_i||_a is the energy of the error of the PoU-weighted
+    // basis function (Phi_i has ||Phi_i||_T = 1)
+    launch_theta_axpy(h, MV_W, MV_PHI, MV_T1, p);
+    launch_stencil_apply(h, MV_T1, MV_CW, 3, 1.0);
+    launch_gram(h, MV_T1, MV_CW, GM_G3);
+    CK_LAUNCH();
+    std::vector<int> act_now(act);
+    all_done = true;
+    for (int j = 0; j < h->N; ++j) {
+      if (!act[j]) continue;
+      h->iters[j] = it + 1;
+      CK(cudaMemcpyAsync(&theta[(size_t)j * PST], h->sub[j].theta, PST * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(&gdiag[(size_t)j * PST * PST], h->sub[j].G3, PST * PST * sizeof(double),
+                         cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    for (int j = 0; j < h->N; ++j) {
+      if (!act[j]) continue;
+      const int nw = n_loc - (h->sub[j].floating ? 6 : 0);
+      double dmax = 0.0;
+      for (int c = 0; c < nw; ++c)
+        dmax = std::max(dmax, std::sqrt(std::fabs(gdiag[(size_t)j * PST * PST + (size_t)c * PST + c])));
+      // converged, or stalled at the rounding floor of the solves (less than 10 %
+      // decrease over three iterations while already below 100 tol)
+      bool done = dmax <= h->opt.tol;
+      auto& hist = dhist[j];
+      hist.push_back(dmax);
+      if (!done && hist.size() >= 4 && dmax <= 1e2 * h->opt.tol && dmax > 0.9 * hist[hist.size() - 4]) done = true;
+      if (done) act_now[j] = 0;
+      else all_done = false;
+    }
+    if (all_done || it + 1 == h->opt.max_iter) break;
+    // continue with the new block on subdomains not yet converged
+    TRY(set_active(h, act_now));
+    launch_copy_mv(h, MV_W, MV_PHI);
+    act = act_now;
+  }
+  TRY(set_active(h, std::vector<int>(h->N, 1)));
+  // 4. final residuals: S x = (K Phi)|B2, T x = -(K y~)|B2 with y~ = A11^{-1} Z|B1
+  for (auto& s : h->sub) CK(cudaMemsetAsync(s.T1, 0, (size_t)s.nfull * PST * sizeof(double), st));
+  timed_solve(h, 1, MV_Z, MV_T1, 0);
+  launch_stencil_apply(h, MV_T1, MV_W, 0, 1.0);
+  launch_colnorms(h, MV_KPHI, MV_W, p);
+  span_end(h, sp_iter);
+  // eigenvectors: [rigid modes (floating), Ritz vectors]
+  for (int j = 0; j < h->N; ++j) {
+    const SubDev& s = h->sub[j];
+    const int nr = s.floating ? std::min(6, n_loc) : 0;
+    CK(cudaMemsetAsync(s.EV, 0, (size_t)s.nfull * PST * sizeof(double), st));
+    CK(cudaMemcpy2DAsync(s.EV, PST * sizeof(double), s.R, PST * sizeof(double), nr * sizeof(double), s.nfull,
+                         cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpy2DAsync(s.EV + nr, PST * sizeof(double), s.Phi, PST * sizeof(double),
+                         (n_loc - nr) * sizeof(double), s.nfull, cudaMemcpyDeviceToDevice, st));
+  }
+  CK_LAUNCH();
+  std::vector<int> notspd(h->N + 1);
+  CK(cudaMemcpyAsync(notspd.data(), h->d_notspd, (h->N + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
+  h->resid_max.assign(h->N, 0.0);
+  std::vector<double> res(PST);
+  for (int j = 0; j < h->N; ++j) {
+    CK(cudaMemcpyAsync(res.data(), h->sub[j].resid, PST * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&theta[(size_t)j * PST], h->sub[j].theta, PST * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int nw = n_loc - (h->sub[j].floating ? 6 : 0);
+    for (int c = 0; c < nw; ++c) h->resid_max[j] = std::max(h->resid_max[j], res[c]);
+  }
+  if (lambda_out) {
+    std::vector<double> lam((size_t)h->N * n_loc);
+    for (int j = 0; j < h->N; ++j) {
+      const int nr = h->sub[j].floating ? std::min(6, n_loc) : 0;
+      for (int c = 0; c < n_loc; ++c) lam[(size_t)j * n_loc + c] = c < nr ? 0.0 : theta[(size_t)j * PST + c - nr];
+    }
+    if (is_device_ptr(lambda_out)) {
+      CK(cudaMemcpy(lambda_out, lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice));
+    } else {
+      memcpy(lambda_out, lam.data(), lam.size() * sizeof(double));
+    }
+  }
+  h->stage = 2;
+  spans_collect(h);
+  for (int j = 0; j <= h->N; ++j)
+    if (notspd[j]) {
+      h->err = "non-positive pivot in a layer-block factorisation";
+      return MSGFEM_ENOTSPD;
+    }
+  if (!all_done) {
+    h->err = "eigensolver reached max_iter";
+    return MSGFEM_ENOCONV;
+  }
+  return MSGFEM_OK;
+}
+
+msgfem_status msgfem_coarse_assemble(msgfem_h h, int* coarse_dim_out) {
+  if (!h) return MSGFEM_EINVAL;
+  if (h->stage < 2) return MSGFEM_ESTATE;
+  cudaStream_t st = h->stream;
+  const int n_loc = h->n_loc;
+  set_dense_context(h->d_flags, h->d_notspd, h->d_sub);
+  TRY(set_active(h, std::vector<int>(h->N, 1)));
+  const int sp_c = span_begin(h, TAG_COARSE);
+  // basis [phi_1..phi_nloc, psi] in CB; psi only on loaded subdomains
+  std::vector<int> ncols(h->N);
+  for (int j = 0; j < h->N; ++j) {
+    const SubDev& s = h->sub[j];
+    ncols[j] = n_loc + (s.loaded ? 1 : 0);
+    CK(cudaMemcpyAsync(s.CB, s.EV, (size_t)s.nfull * PST * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  CK(cudaMemcpyAsync(h->d_ncols, ncols.data(), h->N * sizeof(int), cudaMemcpyHostToDevice, st));
+  for (int j = 0; j < h->N; ++j)
+    if (h->sub[j].loaded)
+      CK(cudaMemcpy2DAsync(h->sub[j].CB + n_loc, PST * sizeof(double), h->sub[j].psi, sizeof(double), sizeof(double),
+                           h->sub[j].nfull, cudaMemcpyDeviceToDevice, st));
+  // Gram-Schmidt in the B inner product (CholeskyQR, twice); psi dropped if dependent
+  for (int pass = 0; pass < 2; ++pass) {
+    launch_stencil_apply(h, MV_CB, MV_CW, 3, 1.0);
+    launch_gram(h, MV_CB, MV_CW, GM_G1);
+    launch_chol_inv_small(h, GM_G1, h->d_ncols, 0, pass == 0 ? 1 : 0);
+    launch_rotate(h, MV_CB, GM_Y, PST);
+    if (pass == 0) {
+      h->basis_m.assign(h->N, 0);
+      for (int j = 0; j < h->N; ++j) {
+        int stt[4];
+        CK(cudaMemcpyAsync(stt, h->sub[j].status, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        h->basis_m[j] = stt[2];
+      }
+      CK(cudaMemcpyAsync(h->d_ncols, h->basis_m.data(), h->N * sizeof(int), cudaMemcpyHostToDevice, st));
+    }
+  }
+  launch_scale_rows_mu(h, MV_CB);
+  launch_stencil_apply(h, MV_CB, MV_CW, 0, 1.0);
+  CK_LAUNCH();
+  // coarse layout
+  h->coff.assign(h->N, 0);
+  int Nc = 0;
+  for (int j = 0; j < h->N; ++j) { h->coff[j] = Nc; Nc += h->basis_m[j]; }
+  const int NcPad = (Nc + TILE - 1) / TILE * TILE;
+  if (NcPad != h->NcPad) {
+    h->NcPad = NcPad;
+    TRY(dalloc(h, &h->d_AH, (size_t)NcPad * NcPad));
+    TRY(dalloc(h, &h->d_AHinv, (size_t)NcPad * NcPad));
+    TRY(dalloc(h, &h->d_bH, (size_t)NcPad * PST));
+    TRY(dalloc(h, &h->d_cH, (size_t)NcPad * PST));
+    TRY(dalloc(h, &h->d_yH, (size_t)NcPad * PST));
+    TRY(dalloc(h, &h->d_rH, (size_t)NcPad * PST));
+    build_coarse_schedules(h);
+    TRY(dalloc(h, &h->cfact.d_gemm, h->cfact.gemm.size()));
+    TRY(dalloc(h, &h->cfact.d_potrf, h->cfact.potrf.size()));
+    CK(cudaMemcpy(h->cfact.d_gemm, h->cfact.gemm.data(), h->cfact.gemm.size() * sizeof(GemmTask),
+                  cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->cfact.d_potrf, h->cfact.potrf.data(), h->cfact.potrf.size() * sizeof(PotrfTask),
+                  cudaMemcpyHostToDevice));
+    TRY(dalloc(h, &h->csolve.d_tasks, h->csolve.tasks.size()));
+    CK(cudaMemcpy(h->csolve.d_tasks, h->csolve.tasks.data(), h->csolve.tasks.size() * sizeof(SolveTask),
+                  cudaMemcpyHostToDevice));
+  }
+  h->Nc = Nc;
+  CK(cudaMemcpyAsync(h->d_coff, h->coff.data(), h->N * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->d_m, h->basis_m.data(), h->N * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(h->d_AH, 0, (size_t)NcPad * NcPad * sizeof(double), st));
+  launch_coarse_blocks(h);
+  launch_coarse_rhs(h);
+  CK(cudaMemsetAsync(h->d_notspd + h->N, 0, sizeof(int), st));
+  run_schedule(h->cfact, st);
+  span_end(h, sp_c);
+  CK_LAUNCH();
+  spans_collect(h);
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, h->d_notspd + h->N, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (coarse_dim_out) *coarse_dim_out = Nc;
+  h->stage = 3;
+  if (bad) {
+    h->err = "coarse matrix is not numerically positive definite";
+    return MSGFEM_ENOTSPD;
+  }
+  return MSGFEM_OK;
+}
+
+msgfem_status msgfem_solve(msgfem_h h, double* u_out, const double* u_ref, double* energy_err_out) {
+  if (!h) return MSGFEM_EINVAL;
+  if (h->stage < 3) return MSGFEM_ESTATE;
+  cudaStream_t st = h->stream;
+  set_dense_context(h->d_flags, h->d_notspd, h->d_sub);
+  const int sp_c = span_begin(h, TAG_COARSE);
+  run_solve_mv(h->csolve, st, 0, 0, 0);
+  launch_prolong(h);
+  span_end(h, sp_c);
+  CK_LAUNCH();
+  const size_t ndof = 3 * (size_t)(h->NX + 1) * (h->NY + 1) * (h->NZ + 1);
+  if (u_out) {
+    CK(cudaMemcpyAsync(u_out, h->d_u, ndof * sizeof(double), cudaMemcpyDefault, st));
+  }
+  if (u_ref) {
+    CK(cudaMemcpyAsync(h->d_ref, u_ref, ndof * sizeof(double), cudaMemcpyDefault, st));
+    launch_energy(h, h->d_ref, h->d_u, h->d_energy);
+    const int nb = energy_blocks(h);
+    std::vector<double> e(2 * nb);
+    CK(cudaMemcpyAsync(e.data(), h->d_energy, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double num = 0.0, den = 0.0;
+    for (int b = 0; b < nb; ++b) { num += e[2 * b]; den += e[2 * b + 1]; }
+    if (energy_err_out) *energy_err_out = den > 0 ? std::sqrt(std::max(num, 0.0) / den) : 0.0;
+  }
+  CK(cudaStreamSynchronize(st));
+  spans_collect(h);
+  h->stage = 4;
+  return MSGFEM_OK;
+}
+
+msgfem_status msgfem_get_basis(msgfem_h h, int j, double* phi_out, int* rows, int* cols, int* box_out) {
+  if (!h || j < 0 || j >= h->N) return MSGFEM_EINVAL;
+  if (h->stage < 2) return MSGFEM_ESTATE;
+  const SubDev& s = h->sub[j];
+  if (rows) *rows = s.nfull;
+  if (cols) *cols = h->n_loc;
+  if (box_out) { box_out[0] = s.I0; box_out[1] = s.I1; box_out[2] = s.J0; box_out[3] = s.J1; }
+  if (phi_out) {
+    double* tmp = nullptr;
+    const size_t n = (size_t)s.nfull * h->n_loc;
+    CK(cudaMalloc(&tmp, n * sizeof(double)));
+    launch_basis_out(h, j, tmp, h->n_loc);
+    cudaError_t e = cudaMemcpyAsync(phi_out, tmp, n * sizeof(double), cudaMemcpyDefault, h->stream);
+    cudaError_t e2 = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    CK(e);
+    CK(e2);
+  }
+  return MSGFEM_OK;
+}
+
+msgfem_status msgfem_get_info(msgfem_h h, int j, msgfem_subinfo* info) {
+  if (!h || !info || j < 0 || j >= h->N) return MSGFEM_EINVAL;
+  const SubDev& s = h->sub[j];
+  info->n_star_dof = s.nfull;
+  info->n1 = h->n1[j];
+  info->n2 = h->n2[j];
+  info->n3 = h->n3[j];
+  info->floating = s.floating;
+  info->iterations = j < (int)h->iters.size() ? h->iters[j] : 0;
+  info->basis_size = j < (int)h->basis_m.size() ? h->basis_m[j] : 0;
+  info->residual = j < (int)h->resid_max.size() ? h->resid_max[j] : 0.0;
+  return MSGFEM_OK;
+}
+
+msgfem_status msgfem_get_profile(msgfem_h h, msgfem_profile* out) {
+  if (!h || !out) return MSGFEM_EINVAL;
+  spans_collect(h);
+  *out = h->prof;
+  out->launches = g_launch_count;
+  return MSGFEM_OK;
+}
+
+msgfem_status msgfem_reset_profile(msgfem_h h) {
+  if (!h) return MSGFEM_EINVAL;
+  spans_collect(h);
+  const double ff = h->prof.factor_flops, sf = h->prof.solve_flops;
+  const int sc = h->prof.solve_calls;
+  h->prof = msgfem_profile{};
+  h->prof.factor_flops = ff;
+  h->prof.solve_flops = sf;
+  h->prof.solve_calls = sc;
+  return MSGFEM_OK;
+}
+
+int msgfem_num_subdomains(msgfem_h h) { return h ? h->N : 0; }
+
+const char* msgfem_last_error(msgfem_h h) { return h ? h->err.c_str() : "null handle"; }
+
+void msgfem_destroy(msgfem_h h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  for (void* p : h->allocs) cudaFree(p);
+  for (auto& sp : h->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  delete h;
+}
+
+}  // extern "C"

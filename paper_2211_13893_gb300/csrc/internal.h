@@ -1,0 +1,228 @@
+// Internal declarations of libmsgfem (not part of the C ABI).
+//
+// Layouts (FP64):
+//  * Omega*_j is a node box [I0, I1] x [J0, J1] x [0, NZ]; in-layer node
+//    q = (i - I0) * nyn + (j - J0); local node n = k * npl + q; full-layout
+//    row 3 n + c.  A "multivector" is [nfull][PST] row-major (PST columns).
+//  * Layer blocks: for M in {K, A11} the DoFs of one node layer kept by M are
+//    numbered compactly (c = 0 .. nM - 1) and padded with identity rows to bM
+//    (a multiple of TILE).  Diagonal blocks D_l and sub-diagonal blocks E_l
+//    (rows layer l + 1, columns layer l) are stored contiguously, bM x bM
+//    row-major; after factorisation D_l holds L_l, E_l holds L_{l+1,l} and
+//    a separate array holds Linv_l = L_l^{-1}.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "msgfem.h"
+
+#define TILE 64
+#define PST 32
+
+// Tile GEMM task: C(64x64) = [C +] sign * [P *] A(64 x K) * op(B)
+enum { G_TRANSB = 1, G_ACC = 2, G_NEG = 4, G_POSTMUL = 8 };
+struct GemmTask {
+  const double* A;
+  const double* B;
+  double* C;
+  const double* P;   // G_POSTMUL: 64x64 tile with leading dimension ldc
+  int lda, ldb, ldc, K;
+  int flags, sub;
+};
+
+struct PotrfTask {
+  double* D;   // 64x64 diagonal tile, in place -> L
+  double* Li;  // 64x64 output tile -> L^{-1}
+  int ld, sub;
+};
+
+// Solve step: C(64 x PST) = init + sign * op(A) * B
+enum { S_TRANSA = 1, S_NEG = 2, S_INIT_GATHER = 4, S_INIT_TILE = 8, S_SCATTER = 16 };
+struct SolveTask {
+  const double* A;
+  const double* B;      // K x PST compact
+  double* C;            // 64 x PST compact tile
+  const double* init;   // S_INIT_TILE: 64 x PST compact tile
+  const int* gmap;      // S_INIT_GATHER: 64 in-layer full rows (or -1)
+  const int* smap;      // S_SCATTER: 64 in-layer full rows (or -1)
+  int lda, K, flags, sub, row_off;
+};
+
+// multivector selectors
+enum { MV_PHI = 0, MV_Z, MV_KPHI, MV_W, MV_T1, MV_R, MV_BR, MV_EV, MV_CB, MV_CW };
+enum { GM_G1 = 0, GM_G2, GM_G3, GM_Y };
+
+// Device-visible per-subdomain descriptor.
+struct SubDev {
+  int I0, I1, J0, J1;          // Omega* node box
+  int oI0, oI1, oJ0, oJ1;      // Omega node box
+  int nxn, nyn, nzn, npl, nnode, nfull;
+  int nK, nA, bK, bA;          // compact / padded layer sizes
+  int floating;
+  int pin[6];                  // pinned full-layout rows (floating), -1 unused
+  int loaded;                  // Omega* touches the loaded face x = L
+  double* stencil;             // [nnode][27][9]
+  double* mu;                  // [nnode]
+  const signed char* cls;      // [npl] 1, 2, 3
+  int* mapK; int* mapA;        // [bK], [bA]
+  int* invK; int* invA;        // [3 npl]
+  double* DK; double* EK; double* LK;   // [nzn][bK^2], [nzn-1][bK^2] (contiguous after DK), [nzn][bK^2]
+  double* DA; double* EA; double* LA;
+  double* ycK; double* ycA;    // [nzn][b][PST]
+  double* rcK; double* rcA;    // [b][PST]
+  double* Phi; double* Z; double* KPhi; double* W; double* T1;
+  double* R; double* BR; double* EV; double* CB; double* CW;   // [nfull][PST]
+  double* bload;               // [nfull]
+  double* psi;                 // [nfull]
+  double* G1; double* G2; double* G3; double* Y;   // [PST][PST]
+  double* theta;               // [PST]
+  double* resid;               // [PST]
+  int* status;                 // [4]: 1 RR pencil degenerate, 2 kept basis columns
+};
+
+struct Schedule {
+  struct Step { int kind, first, count; };   // kind 0 gemm, 1 potrf
+  std::vector<Step> steps;
+  std::vector<GemmTask> gemm;
+  std::vector<PotrfTask> potrf;
+  GemmTask* d_gemm = nullptr;
+  PotrfTask* d_potrf = nullptr;
+};
+
+struct SolveSchedule {
+  struct Step { int first, count; };
+  std::vector<Step> steps;
+  std::vector<SolveTask> tasks;
+  SolveTask* d_tasks = nullptr;
+};
+
+struct CoarsePair { int s, t, x0, x1, y0, y1; };   // (i, j) node box of Omega_s cap Omega*_t
+
+// Host copies of the per-subdomain set-up arrays (uploaded once).
+struct HostSub {
+  std::vector<signed char> cls;
+  std::vector<int> mapK, mapA, invK, invA;
+  std::vector<double> mu, bload;
+};
+
+struct msgfem {
+  int NX = 0, NY = 0, NZ = 0;
+  double hx = 0, hy = 0, hz = 0, traction = 0;
+  double E9[9];
+  int sx = 0, sy = 0, o = 0, os = 0;
+  msgfem_options opt;
+  cudaStream_t stream = nullptr;
+  int N = 0;
+  int layered = 0, ntypes = 0, type_cap = 0;
+  std::vector<double> h_angles;
+  std::vector<SubDev> sub;
+  std::vector<HostSub> hsub;
+  std::vector<int> n1, n2, n3, iters, basis_m;
+  std::vector<double> resid_max;
+  std::vector<void*> allocs;
+  SubDev* d_sub = nullptr;
+  double* d_E9 = nullptr;
+  double* d_angles_type = nullptr;   // [ntypes]
+  double* d_Ke = nullptr;            // [ntypes][576]
+  double* d_gram_part = nullptr;
+  int* d_flags = nullptr;            // [N + 1] active flags (entry N: coarse, always 1)
+  int* d_notspd = nullptr;           // [N + 1]
+  int* d_ncols = nullptr;            // [N]
+  Schedule fact;
+  SolveSchedule solveK, solveA;
+  std::vector<CoarsePair> pairs;
+  CoarsePair* d_pairs = nullptr;
+  double* d_pair_part = nullptr;
+  int Nc = 0, NcPad = 0;
+  std::vector<int> coff;
+  int* d_coff = nullptr;
+  int* d_m = nullptr;
+  double* d_AH = nullptr;
+  double* d_AHinv = nullptr;
+  double* d_bH = nullptr;
+  double* d_cH = nullptr;
+  double* d_yH = nullptr;
+  double* d_rH = nullptr;
+  double* d_u = nullptr;
+  double* d_ref = nullptr;
+  double* d_energy = nullptr;
+  Schedule cfact;
+  SolveSchedule csolve;
+  int n_loc = 0, p = 0;
+  // profiling (CUDA events on the handle's stream)
+  struct Span { int tag; cudaEvent_t a, b; };
+  std::vector<Span> spans;
+  std::vector<cudaEvent_t> ev_pool;
+  msgfem_profile prof{};
+  int stage = 0;   // 1 setup, 2 local spaces, 3 coarse assembled, 4 solved
+  std::string err;
+};
+
+extern long long g_launch_count;   // kernel launches issued by this library
+
+// host scheduling (setup.cpp)
+msgfem_status build_problem(msgfem* h);
+void build_factor_schedule(msgfem* h);
+void build_solve_schedules(msgfem* h);
+void build_coarse_schedules(msgfem* h);
+
+// launchers
+void set_dense_context(int* active, int* notspd, const SubDev* subs);
+void run_schedule(const Schedule& s, cudaStream_t st);
+void run_solve_mv(const SolveSchedule& s, cudaStream_t st, int src, int dst, int gather_neg);
+void launch_element_stiffness(msgfem* h);
+void launch_stencil(msgfem* h);
+void launch_layer_blocks(msgfem* h);
+void launch_stencil_apply(msgfem* h, int src, int dst, int mode, double alpha);
+void launch_gram(msgfem* h, int wx, int wy, int wg);
+void launch_small_eig(msgfem* h, int p);
+void launch_rotate(msgfem* h, int which, int wy, int ncols);
+void launch_sub_rc(msgfem* h, int wout, int wr, int wc, int nr);
+void launch_random_b2(msgfem* h, int which, int p, unsigned long long seed);
+void launch_mask_rows(msgfem* h, int which, int keep);
+void launch_zero_pins(msgfem* h, int which);
+void launch_copy_col(msgfem* h, int wsrc, int scol, int wdst, int dcol, double sign);
+void launch_copy_mv(msgfem* h, int wsrc, int wdst);
+void launch_rigid_modes(msgfem* h);
+void launch_chol_inv_small(msgfem* h, int wg, const int* d_ncols, int nfixed, int drop_last);
+void launch_colnorms(msgfem* h, int wa, int wb, int p);
+void launch_scale_rows_mu(msgfem* h, int which);
+void launch_theta_axpy(msgfem* h, int wx, int wy, int wd, int p);
+void launch_coarse_blocks(msgfem* h);
+void launch_coarse_rhs(msgfem* h);
+void launch_prolong(msgfem* h);
+int energy_blocks(msgfem* h);
+void launch_energy(msgfem* h, const double* d_ref, const double* d_u, double* d_out);
+void launch_basis_out(msgfem* h, int j, double* d_out, int ncols);
+
+// source selectors for k_copy_col
+enum { SRC_BLOAD = -1, SRC_PSI = -2 };
+
+#ifdef __CUDACC__
+__device__ __forceinline__ double* mv_ptr(const SubDev& s, int which) {
+  switch (which) {
+    case MV_PHI: return s.Phi;
+    case MV_Z: return s.Z;
+    case MV_KPHI: return s.KPhi;
+    case MV_W: return s.W;
+    case MV_T1: return s.T1;
+    case MV_R: return s.R;
+    case MV_BR: return s.BR;
+    case MV_EV: return s.EV;
+    case MV_CB: return s.CB;
+    default: return s.CW;
+  }
+}
+__device__ __forceinline__ double* gm_ptr(const SubDev& s, int which) {
+  switch (which) {
+    case GM_G1: return s.G1;
+    case GM_G2: return s.G2;
+    case GM_G3: return s.G3;
+    default: return s.Y;
+  }
+}
+#endif

@@ -1,0 +1,229 @@
+// Local assembly on the GPU: ply tensors, element stiffness, node stencils of
+// a_{Omega*_j} and the dense z-layer blocks of K and A11.
+//
+// Material (Sec. 2, Eq. eq-hooke; Sec. 5.1): the orthotropic ply stiffness
+// in its axes is the inverse of the engineering compliance; it is rotated to
+// the laminate frame with the Voigt strain transformation M(theta) of a
+// rotation about z, C = M^T C_ply M, so that eps:C:eps is invariant.
+// Element (Eq. element_stiffness): K_e = sum_g B_g^T C B_g det J w_g over
+// 2x2x2 Gauss points of the trilinear brick, with the 6x24 Voigt B matrix.
+// GPU node order inside an element: a = ax + 2 ay + 4 az, (ax, ay, az) in
+// {0,1}^3; element DoF 3 a + c.
+#include "internal.h"
+
+namespace {
+
+__device__ void ply_stiffness(const double* E9, double theta_deg, double C[6][6]) {
+  const double E1 = E9[0], E2 = E9[1], E3 = E9[2], G12 = E9[3], G13 = E9[4], G23 = E9[5];
+  const double n12 = E9[6], n13 = E9[7], n23 = E9[8];
+  // normal compliance block and its inverse (cofactors)
+  const double s11 = 1.0 / E1, s22 = 1.0 / E2, s33 = 1.0 / E3;
+  const double s12 = -n12 / E1, s13 = -n13 / E1, s23 = -n23 / E2;
+  const double c11 = s22 * s33 - s23 * s23, c12 = s13 * s23 - s12 * s33, c13 = s12 * s23 - s13 * s22;
+  const double c22 = s11 * s33 - s13 * s13, c23 = s12 * s13 - s11 * s23, c33 = s11 * s22 - s12 * s12;
+  const double det = s11 * c11 + s12 * c12 + s13 * c13;
+  double Cm[6][6];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) Cm[i][j] = 0.0;
+  Cm[0][0] = c11 / det; Cm[0][1] = Cm[1][0] = c12 / det; Cm[0][2] = Cm[2][0] = c13 / det;
+  Cm[1][1] = c22 / det; Cm[1][2] = Cm[2][1] = c23 / det; Cm[2][2] = c33 / det;
+  Cm[3][3] = G23; Cm[4][4] = G13; Cm[5][5] = G12;
+  // eps_ply = M eps_global (Voigt 11 22 33 23 13 12, engineering shear)
+  double th = theta_deg * (3.14159265358979323846 / 180.0);
+  const double c = cos(th), s = sin(th);
+  double M[6][6];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) M[i][j] = 0.0;
+  M[0][0] = c * c; M[0][1] = s * s; M[0][5] = c * s;
+  M[1][0] = s * s; M[1][1] = c * c; M[1][5] = -c * s;
+  M[2][2] = 1.0;
+  M[3][3] = c; M[3][4] = -s;
+  M[4][3] = s; M[4][4] = c;
+  M[5][0] = -2.0 * c * s; M[5][1] = 2.0 * c * s; M[5][5] = c * c - s * s;
+  double CM[6][6];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      double a = 0.0;
+      for (int k = 0; k < 6; ++k) a += Cm[i][k] * M[k][j];
+      CM[i][j] = a;
+    }
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      double a = 0.0;
+      for (int k = 0; k < 6; ++k) a += M[k][i] * CM[k][j];
+      C[i][j] = a;
+    }
+}
+
+// One block per element type; thread (r, c) computes K_e[r][c].
+__global__ void __launch_bounds__(576)
+k_element_stiffness(const double* __restrict__ angles, const double* __restrict__ E9, int layered,
+                    int NX, int NY, int NZ, double hx, double hy, double hz, double* __restrict__ Ke) {
+  const int type = blockIdx.x;
+  __shared__ double C[6][6];
+  __shared__ double dN[8][8][3];   // [gauss][node][d/dx, d/dy, d/dz]
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    // layered: type = ply k, angle of element (0, 0, k); otherwise type = element index
+    const double th = angles[type];   // per-type angle (per ply if layered, else per element)
+    double Cl[6][6];
+    ply_stiffness(E9, th, Cl);
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) C[i][j] = Cl[i][j];
+  }
+  if (tid < 64) {
+    const int g = tid >> 3, a = tid & 7;
+    const double gp = 0.57735026918962576451;   // 1/sqrt(3)
+    const double xi[3] = {(g & 1) ? gp : -gp, (g & 2) ? gp : -gp, (g & 4) ? gp : -gp};
+    const double sa[3] = {(a & 1) ? 1.0 : -1.0, (a & 2) ? 1.0 : -1.0, (a & 4) ? 1.0 : -1.0};
+    const double f0 = 1.0 + sa[0] * xi[0], f1 = 1.0 + sa[1] * xi[1], f2 = 1.0 + sa[2] * xi[2];
+    dN[g][a][0] = 0.125 * sa[0] * f1 * f2 * (2.0 / hx);
+    dN[g][a][1] = 0.125 * f0 * sa[1] * f2 * (2.0 / hy);
+    dN[g][a][2] = 0.125 * f0 * f1 * sa[2] * (2.0 / hz);
+  }
+  __syncthreads();
+  const int r = tid / 24, c = tid % 24;
+  const int ar = r / 3, cr = r % 3, ac = c / 3, cc = c % 3;
+  const double detw = hx * hy * hz / 8.0;
+  double acc = 0.0;
+  for (int g = 0; g < 8; ++g) {
+    double br[6], bc[6];
+    const double* dr = dN[g][ar];
+    const double* dc = dN[g][ac];
+    // column of B for DoF (a, comp): rows xx, yy, zz, yz, xz, xy
+    br[0] = cr == 0 ? dr[0] : 0.0; br[1] = cr == 1 ? dr[1] : 0.0; br[2] = cr == 2 ? dr[2] : 0.0;
+    br[3] = cr == 1 ? dr[2] : (cr == 2 ? dr[1] : 0.0);
+    br[4] = cr == 0 ? dr[2] : (cr == 2 ? dr[0] : 0.0);
+    br[5] = cr == 0 ? dr[1] : (cr == 1 ? dr[0] : 0.0);
+    bc[0] = cc == 0 ? dc[0] : 0.0; bc[1] = cc == 1 ? dc[1] : 0.0; bc[2] = cc == 2 ? dc[2] : 0.0;
+    bc[3] = cc == 1 ? dc[2] : (cc == 2 ? dc[1] : 0.0);
+    bc[4] = cc == 0 ? dc[2] : (cc == 2 ? dc[0] : 0.0);
+    bc[5] = cc == 0 ? dc[1] : (cc == 1 ? dc[0] : 0.0);
+    for (int i = 0; i < 6; ++i) {
+      double t = 0.0;
+      for (int j = 0; j < 6; ++j) t += C[i][j] * bc[j];
+      acc += br[i] * t;
+    }
+  }
+  Ke[(size_t)type * 576 + tid] = acc * detw;
+}
+
+// Node stencil of a_{Omega*}: thread per (node, neighbour slot); slot
+// (di, dj, dk) = ((s/9)-1, ((s/3)%3)-1, (s%3)-1).  Only elements inside the
+// Omega* box contribute (Eq. restricted_bilinear_form).
+__global__ void __launch_bounds__(216)
+k_stencil(const SubDev* __restrict__ subs, const double* __restrict__ Ke, int layered, int NY, int NZ) {
+  const SubDev s = subs[blockIdx.y];
+  const int tid = threadIdx.x;
+  const int node = blockIdx.x * 8 + tid / 27, slot = tid % 27;
+  if (node >= s.nnode) return;
+  const int k = node / s.npl, q = node % s.npl;
+  const int gi = s.I0 + q / s.nyn, gj = s.J0 + q % s.nyn;
+  const int di = slot / 9 - 1, dj = (slot / 3) % 3 - 1, dk = slot % 3 - 1;
+  double acc[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) acc[e] = 0.0;
+  for (int ez = 0; ez < 2; ++ez)
+    for (int ey = 0; ey < 2; ++ey)
+      for (int ex = 0; ex < 2; ++ex) {
+        const int ie = gi - 1 + ex, je = gj - 1 + ey, ke = k - 1 + ez;
+        if (ie < s.I0 || ie >= s.I1 || je < s.J0 || je >= s.J1 || ke < 0 || ke >= NZ) continue;
+        const int ax = gi - ie, ay = gj - je, az = k - ke;              // node position in element
+        const int bx = ax + di, by = ay + dj, bz = az + dk;            // neighbour position
+        if (bx < 0 || bx > 1 || by < 0 || by > 1 || bz < 0 || bz > 1) continue;
+        const int a = ax + 2 * ay + 4 * az, b = bx + 2 * by + 4 * bz;
+        const int type = layered ? ke : (ie * NY + je) * NZ + ke;
+        const double* K = Ke + (size_t)type * 576;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc) acc[c * 3 + cc] += K[(3 * a + c) * 24 + 3 * b + cc];
+      }
+  double* out = s.stencil + ((size_t)node * 27 + slot) * 9;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) out[e] = acc[e];
+}
+
+__device__ __forceinline__ bool is_pinned(const SubDev& s, int row) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    if (s.pin[i] == row) return true;
+  return false;
+}
+
+// Scatter the stencil into the layer blocks of K (mat 0) and A11 (mat 1).
+// Thread per (node, slot); slots with dk = 0 go to D_k, dk = -1 to E_{k-1}.
+__global__ void __launch_bounds__(216)
+k_layer_blocks(const SubDev* __restrict__ subs) {
+  const SubDev s = subs[blockIdx.y];
+  const int tid = threadIdx.x;
+  const int node = blockIdx.x * 8 + tid / 27, slot = tid % 27;
+  if (node >= s.nnode) return;
+  const int dk = slot % 3 - 1;
+  if (dk == 1) return;
+  const int k = node / s.npl, q = node % s.npl;
+  if (dk == -1 && k == 0) return;
+  const int di = slot / 9 - 1, dj = (slot / 3) % 3 - 1;
+  const int qi = q / s.nyn + di, qj = q % s.nyn + dj;
+  if (qi < 0 || qi >= s.nxn || qj < 0 || qj >= s.nyn) return;
+  const int q2 = qi * s.nyn + qj;
+  const double* st = s.stencil + ((size_t)node * 27 + slot) * 9;
+  for (int mat = 0; mat < 2; ++mat) {
+    const int* inv = mat == 0 ? s.invK : s.invA;
+    const int b = mat == 0 ? s.bK : s.bA;
+    double* blk = (dk == 0) ? ((mat == 0 ? s.DK : s.DA) + (size_t)k * b * b)
+                            : ((mat == 0 ? s.EK : s.EA) + (size_t)(k - 1) * b * b);
+    for (int c = 0; c < 3; ++c) {
+      const int rr = inv[3 * q + c];
+      if (rr < 0) continue;
+      if (mat == 0 && s.floating && is_pinned(s, (k * s.npl + q) * 3 + c)) continue;
+      for (int cc = 0; cc < 3; ++cc) {
+        const int col = inv[3 * q2 + cc];
+        if (col < 0) continue;
+        if (mat == 0 && s.floating && is_pinned(s, ((k + dk) * s.npl + q2) * 3 + cc)) continue;
+        blk[(size_t)rr * b + col] = st[c * 3 + cc];
+      }
+    }
+  }
+}
+
+// Identity on padding rows and pinned DoFs.
+__global__ void k_block_identity(const SubDev* __restrict__ subs) {
+  const SubDev s = subs[blockIdx.y];
+  const int k = blockIdx.x;
+  if (k >= s.nzn) return;
+  for (int c = s.nK + threadIdx.x; c < s.bK; c += blockDim.x) s.DK[(size_t)k * s.bK * s.bK + (size_t)c * s.bK + c] = 1.0;
+  for (int c = s.nA + threadIdx.x; c < s.bA; c += blockDim.x) s.DA[(size_t)k * s.bA * s.bA + (size_t)c * s.bA + c] = 1.0;
+  if (s.floating && threadIdx.x < 6 && s.pin[threadIdx.x] >= 0) {
+    const int row = s.pin[threadIdx.x];
+    const int layer = row / (3 * s.npl), r = s.invK[row % (3 * s.npl)];
+    if (layer == k && r >= 0) s.DK[(size_t)k * s.bK * s.bK + (size_t)r * s.bK + r] = 1.0;
+  }
+}
+
+}  // namespace
+
+void launch_element_stiffness(msgfem* h) {
+  k_element_stiffness<<<h->ntypes, 576, 0, h->stream>>>(h->d_angles_type, h->d_E9, h->layered, h->NX, h->NY,
+                                                        h->NZ, h->hx, h->hy, h->hz, h->d_Ke); ++g_launch_count;
+}
+
+void launch_stencil(msgfem* h) {
+  int maxn = 0;
+  for (const auto& s : h->sub) maxn = std::max(maxn, s.nnode);
+  dim3 grid((maxn + 7) / 8, h->N);
+  k_stencil<<<grid, 216, 0, h->stream>>>(h->d_sub, h->d_Ke, h->layered, h->NY, h->NZ); ++g_launch_count;
+}
+
+void launch_layer_blocks(msgfem* h) {
+  for (const auto& s : h->sub) {
+    cudaMemsetAsync(s.DK, 0, sizeof(double) * (size_t)s.bK * s.bK * (2 * s.nzn - 1), h->stream);
+    cudaMemsetAsync(s.DA, 0, sizeof(double) * (size_t)s.bA * s.bA * (2 * s.nzn - 1), h->stream);
+  }
+  int maxn = 0, maxz = 0;
+  for (const auto& s : h->sub) { maxn = std::max(maxn, s.nnode); maxz = std::max(maxz, s.nzn); }
+  dim3 grid((maxn + 7) / 8, h->N);
+  k_layer_blocks<<<grid, 216, 0, h->stream>>>(h->d_sub); ++g_launch_count;
+  dim3 g2(maxz, h->N);
+  k_block_identity<<<g2, 128, 0, h->stream>>>(h->d_sub); ++g_launch_count;
+}

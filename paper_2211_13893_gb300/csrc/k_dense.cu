@@ -1,0 +1,262 @@
+// Dense FP64 tile kernels behind the layer-block Cholesky factorisation and
+// the block triangular solves of the local shift-invert operator.
+//
+// The factorisation of a block-tridiagonal SPD matrix (z-layer blocks, see
+// internal.h) is expressed as a static list of 64x64 tile tasks grouped into
+// steps (built once by the host scheduler in setup.cpp):
+//   SYRK    D_l -= L_{l,l-1} L_{l,l-1}^T
+//   POTRF   L_kk = chol(D_kk), Li_kk = L_kk^{-1}          (one CTA per tile)
+//   TRMM    L_ik = D_ik Li_kk^T   (panel below, and the E_l panel)
+//   UPDATE  D_ij -= L_ik L_jk^T   (trailing tiles of the panel)
+//   TRTRI   Linv_ik = -Li_ii sum_m L_im Linv_mk             (block inverse)
+// FP64 arithmetic on this part runs at ~2 DFMA/clk/SM, so every kernel is
+// bound by the FP64 pipe; the tile kernels only need enough independent
+// tasks in flight to occupy all SMs.
+#include "internal.h"
+
+namespace {
+
+constexpr int KC = 16;   // K chunk of the tile GEMM
+
+__global__ void __launch_bounds__(256)
+k_tile_gemm(const GemmTask* __restrict__ tasks, const int* __restrict__ active) {
+  const GemmTask t = tasks[blockIdx.x];
+  if (t.sub >= 0 && active != nullptr && !active[t.sub]) return;
+  __shared__ double smem[64 * 65];
+  double (*As)[65] = reinterpret_cast<double (*)[65]>(smem);                 // [KC][65]: As[k][m]
+  double (*Bs)[65] = reinterpret_cast<double (*)[65]>(smem + KC * 65);      // [KC][65]: Bs[k][n]
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  const bool transB = (t.flags & G_TRANSB) != 0;
+  for (int k0 = 0; k0 < t.K; k0 += KC) {
+    {
+      const int r = tid >> 2, c = (tid & 3) * 4;
+      const double* a = t.A + (size_t)r * t.lda + k0 + c;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) As[c + i][r] = a[i];
+    }
+    if (transB) {
+      const int n = tid >> 2, c = (tid & 3) * 4;
+      const double* b = t.B + (size_t)n * t.ldb + k0 + c;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) Bs[c + i][n] = b[i];
+    } else {
+      const int k = tid >> 4, n = (tid & 15) * 4;
+      const double* b = t.B + (size_t)(k0 + k) * t.ldb + n;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) Bs[k][n + i] = b[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  if (t.flags & G_POSTMUL) {
+    // C = P * (A op(B)) with the 64x64 product staged in shared memory
+    double (*Cs)[65] = reinterpret_cast<double (*)[65]>(smem);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) Cs[ty + 16 * i][tx + 16 * j] = acc[i][j];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int m = 0; m < 64; ++m) {
+      double b[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Cs[m][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const double p = t.P[(size_t)(ty + 16 * i) * t.ldc + m];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(p, b[j], acc[i][j]);
+      }
+    }
+  }
+  const double sgn = (t.flags & G_NEG) ? -1.0 : 1.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      double* c = t.C + (size_t)(ty + 16 * i) * t.ldc + tx + 16 * j;
+      const double v = sgn * acc[i][j];
+      *c = (t.flags & G_ACC) ? *c + v : v;
+    }
+}
+
+// Cholesky and inverse of one 64x64 SPD tile in shared memory.  L occupies
+// the lower triangle of A; X = L^{-1} is kept transposed in the strict upper
+// triangle shifted by one column (X[i][c] at A[c][i + 1], using the pad column).
+__global__ void __launch_bounds__(256)
+k_tile_potrf_inv(const PotrfTask* __restrict__ tasks, const int* __restrict__ active,
+                 int* __restrict__ notspd) {
+  const PotrfTask t = tasks[blockIdx.x];
+  if (t.sub >= 0 && active != nullptr && !active[t.sub]) return;
+  __shared__ double A[64][65];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = 0;
+  for (int e = tid; e < 64 * 64; e += 256) {
+    const int r = e >> 6, c = e & 63;
+    A[r][c] = (c <= r) ? t.D[(size_t)r * t.ld + c] : 0.0;
+  }
+  if (tid < 64) A[tid][64] = 0.0;
+  __syncthreads();
+  for (int j = 0; j < 64; ++j) {
+    if (tid == 0) {
+      double d = A[j][j];
+      if (!(d > 0.0)) { bad = 1; d = 1e-300; }
+      A[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    const double djj = A[j][j];
+    for (int i = j + 1 + tid; i < 64; i += 256) A[i][j] /= djj;
+    __syncthreads();
+    const int n = 63 - j;
+    for (int e = tid; e < n * n; e += 256) {
+      const int ii = j + 1 + e / n, kk = j + 1 + e % n;
+      if (kk <= ii) A[ii][kk] = fma(-A[ii][j], A[kk][j], A[ii][kk]);
+    }
+    __syncthreads();
+  }
+  // X = L^{-1} row by row: X[i][c] = -(sum_{m=c}^{i-1} L[i][m] X[m][c]) / L[i][i]
+  for (int i = 0; i < 64; ++i) {
+    for (int c = tid; c <= i; c += 256) {
+      if (c == i) {
+        A[i][i + 1] = 1.0 / A[i][i];
+      } else {
+        double s = 0.0;
+        for (int m = c; m < i; ++m) s = fma(A[i][m], A[c][m + 1], s);
+        A[c][i + 1] = -s / A[i][i];
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < 64 * 64; e += 256) {
+    const int r = e >> 6, c = e & 63;
+    t.D[(size_t)r * t.ld + c] = (c <= r) ? A[r][c] : 0.0;
+    t.Li[(size_t)r * t.ld + c] = (c <= r) ? A[c][r + 1] : 0.0;
+  }
+  if (tid == 0 && bad && notspd != nullptr) atomicExch(&notspd[t.sub >= 0 ? t.sub : 0], 1);
+}
+
+// One step of a block triangular solve: C(64 x PST) = init + sign op(A) B.
+constexpr int SKC = 32;
+__global__ void __launch_bounds__(256)
+k_solve_step(const SolveTask* __restrict__ tasks, const SubDev* __restrict__ subs,
+             const int* __restrict__ active, int src, int dst, int gather_neg) {
+  const SolveTask t = tasks[blockIdx.x];
+  if (t.sub >= 0 && active != nullptr && !active[t.sub]) return;
+  __shared__ double As[SKC][65];
+  __shared__ double Bs[SKC][PST + 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc[4][2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = 0.0;
+  const bool transA = (t.flags & S_TRANSA) != 0;
+  for (int k0 = 0; k0 < t.K; k0 += SKC) {
+    if (!transA) {
+      const int r = tid >> 2, c = (tid & 3) * 8;
+      const double* a = t.A + (size_t)r * t.lda + k0 + c;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) As[c + i][r] = a[i];
+    } else {
+      const int k = tid >> 3, m = (tid & 7) * 8;
+      const double* a = t.A + (size_t)(k0 + k) * t.lda + m;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) As[k][m + i] = a[i];
+    }
+    {
+      const int k = tid >> 3, c = (tid & 7) * 4;
+      const double* b = t.B + (size_t)(k0 + k) * PST + c;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) Bs[k][c + i] = b[i];
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < SKC; ++kk) {
+      double a[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      const double b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        acc[i][0] = fma(a[i], b0, acc[i][0]);
+        acc[i][1] = fma(a[i], b1, acc[i][1]);
+      }
+    }
+    __syncthreads();
+  }
+  const double sgn = (t.flags & S_NEG) ? -1.0 : 1.0;
+  const double* gfull = nullptr;
+  double* sfull = nullptr;
+  if (t.flags & (S_INIT_GATHER | S_SCATTER)) {
+    const SubDev& s = subs[t.sub];
+    if (t.flags & S_INIT_GATHER) gfull = mv_ptr(s, src) + (size_t)t.row_off * PST;
+    if (t.flags & S_SCATTER) sfull = mv_ptr(s, dst) + (size_t)t.row_off * PST;
+  }
+  const double gs = gather_neg ? -1.0 : 1.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = ty + 16 * i;
+    const int gm = (t.flags & S_INIT_GATHER) ? t.gmap[r] : -1;
+    const int sm = (t.flags & S_SCATTER) ? t.smap[r] : -1;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int c = tx + 16 * j;
+      double v = sgn * acc[i][j];
+      if (t.flags & S_INIT_TILE) v += t.init[r * PST + c];
+      if (gm >= 0) v += gs * gfull[(size_t)gm * PST + c];
+      t.C[r * PST + c] = v;
+      if (sm >= 0) sfull[(size_t)sm * PST + c] = v;
+    }
+  }
+}
+
+}  // namespace
+
+long long g_launch_count = 0;
+
+static int* g_active = nullptr;   // set by the driver before schedule runs
+static int* g_notspd = nullptr;
+static const SubDev* g_subs = nullptr;
+
+void set_dense_context(int* active, int* notspd, const SubDev* subs) {
+  g_active = active;
+  g_notspd = notspd;
+  g_subs = subs;
+}
+
+void run_schedule(const Schedule& s, cudaStream_t st) {
+  for (const auto& step : s.steps) {
+    if (step.count == 0) continue;
+    if (step.kind == 0)
+      k_tile_gemm<<<step.count, 256, 0, st>>>(s.d_gemm + step.first, g_active);
+    else
+      k_tile_potrf_inv<<<step.count, 256, 0, st>>>(s.d_potrf + step.first, g_active, g_notspd);
+    ++g_launch_count;
+  }
+}
+
+void run_solve_mv(const SolveSchedule& s, cudaStream_t st, int src, int dst, int gather_neg) {
+  for (const auto& step : s.steps) {
+    if (step.count == 0) continue;
+    k_solve_step<<<step.count, 256, 0, st>>>(s.d_tasks + step.first, g_subs, g_active, src, dst, gather_neg); ++g_launch_count;
+  }
+}

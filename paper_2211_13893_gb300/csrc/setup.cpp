@@ -1,0 +1,400 @@
+// Host-side set-up: box decomposition, DoF classes, partition of unity, the
+// compact layer numberings and the static task schedules of the layer-block
+// factorisation and solves.
+//
+// Decomposition (Secs. 3.1, 3.3): subdomain (a, b) owns the element box
+// [a NX / sx, (a+1) NX / sx) x [b NY / sy, (b+1) NY / sy) x [0, NZ); Omega
+// and Omega* grow it by o and o* element layers, clipped to the mesh.
+// DoF classes on Omega* (Sec. 4.3): class 3 (B3) = nodes on the clamped face
+// x = 0; class 2 (B2) = other nodes on the closure of the part of dOmega*
+// inside Omega; class 1 (B1) = the rest.
+// Partition of unity (Sec. 4.2): weights start at 0 on the closure of the
+// part of dOmega inside Omega and 2o elsewhere in Omega, then 2o - 1 Jacobi
+// sweeps of w_p <- min(w_p, min_q w_q + 1, 2o) over nodes q sharing an
+// element with p; mu_{j,p} = w_{j,p} / sum_i w_{i,p}.
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <tuple>
+
+#include "internal.h"
+
+namespace {
+
+struct Box { int x0, x1, y0, y1; };   // element box [x0, x1) x [y0, y1)
+
+Box grow(const Box& b, int m, int NX, int NY) {
+  return {std::max(0, b.x0 - m), std::min(NX, b.x1 + m), std::max(0, b.y0 - m), std::min(NY, b.y1 + m)};
+}
+
+// relaxed PoU weights on the node box of Omega (3-D array, k fastest)
+std::vector<double> pou_weights(const Box& om, int NX, int NY, int NZ, int o) {
+  const int nx = om.x1 - om.x0 + 1, ny = om.y1 - om.y0 + 1, nz = NZ + 1;
+  std::vector<double> w((size_t)nx * ny * nz), nw;
+  auto idx = [&](int i, int j, int k) { return ((size_t)i * ny + j) * nz + k; };
+  for (int i = 0; i < nx; ++i)
+    for (int j = 0; j < ny; ++j) {
+      const int gi = om.x0 + i, gj = om.y0 + j;
+      const bool cut = (gi == om.x0 && om.x0 > 0) || (gi == om.x1 && om.x1 < NX) ||
+                       (gj == om.y0 && om.y0 > 0) || (gj == om.y1 && om.y1 < NY);
+      for (int k = 0; k < nz; ++k) w[idx(i, j, k)] = cut ? 0.0 : 2.0 * o;
+    }
+  for (int sweep = 0; sweep < 2 * o - 1; ++sweep) {
+    nw = w;
+    for (int i = 0; i < nx; ++i)
+      for (int j = 0; j < ny; ++j)
+        for (int k = 0; k < nz; ++k) {
+          double best = w[idx(i, j, k)];
+          for (int di = -1; di <= 1; ++di)
+            for (int dj = -1; dj <= 1; ++dj)
+              for (int dk = -1; dk <= 1; ++dk) {
+                const int a = i + di, b = j + dj, c = k + dk;
+                if (a < 0 || a >= nx || b < 0 || b >= ny || c < 0 || c >= nz) continue;
+                best = std::min(best, w[idx(a, b, c)] + 1.0);
+              }
+          nw[idx(i, j, k)] = std::min(best, 2.0 * o);
+        }
+    w.swap(nw);
+  }
+  return w;
+}
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+msgfem_status build_problem(msgfem* h) {
+  const int NX = h->NX, NY = h->NY, NZ = h->NZ;
+  h->N = h->sx * h->sy;
+  h->sub.assign(h->N, SubDev{});
+  h->hsub.assign(h->N, HostSub{});
+  h->n1.assign(h->N, 0);
+  h->n2.assign(h->N, 0);
+  h->n3.assign(h->N, 0);
+  std::vector<Box> omega(h->N), star(h->N);
+  for (int a = 0; a < h->sx; ++a)
+    for (int b = 0; b < h->sy; ++b) {
+      const int j = a * h->sy + b;
+      Box hat{(a * NX) / h->sx, ((a + 1) * NX) / h->sx, (b * NY) / h->sy, ((b + 1) * NY) / h->sy};
+      if (hat.x1 <= hat.x0 || hat.y1 <= hat.y0) {
+        h->err = "partition has an empty subdomain";
+        return MSGFEM_EINVAL;
+      }
+      omega[j] = grow(hat, h->o, NX, NY);
+      star[j] = grow(hat, h->os, NX, NY);
+    }
+  // partition of unity: global weight sums
+  const size_t nnodes = (size_t)(NX + 1) * (NY + 1) * (NZ + 1);
+  std::vector<double> total(nnodes, 0.0);
+  std::vector<std::vector<double>> wts(h->N);
+  for (int j = 0; j < h->N; ++j) {
+    const Box& om = omega[j];
+    wts[j] = pou_weights(om, NX, NY, NZ, h->o);
+    const int nx = om.x1 - om.x0 + 1, ny = om.y1 - om.y0 + 1;
+    for (int i = 0; i < nx; ++i)
+      for (int jj = 0; jj < ny; ++jj)
+        for (int k = 0; k <= NZ; ++k)
+          total[((size_t)(om.x0 + i) * (NY + 1) + om.y0 + jj) * (NZ + 1) + k] +=
+              wts[j][((size_t)i * ny + jj) * (NZ + 1) + k];
+  }
+  for (size_t n = 0; n < nnodes; ++n)
+    if (!(total[n] > 0.0)) {
+      h->err = "partition of unity: a node has zero total weight";
+      return MSGFEM_EINVAL;
+    }
+  for (int j = 0; j < h->N; ++j) {
+    SubDev& s = h->sub[j];
+    HostSub& hs = h->hsub[j];
+    const Box& st = star[j];
+    const Box& om = omega[j];
+    s.I0 = st.x0; s.I1 = st.x1; s.J0 = st.y0; s.J1 = st.y1;
+    s.oI0 = om.x0; s.oI1 = om.x1; s.oJ0 = om.y0; s.oJ1 = om.y1;
+    s.nxn = st.x1 - st.x0 + 1;
+    s.nyn = st.y1 - st.y0 + 1;
+    s.nzn = NZ + 1;
+    s.npl = s.nxn * s.nyn;
+    s.nnode = s.npl * s.nzn;
+    s.nfull = 3 * s.nnode;
+    s.floating = st.x0 > 0 ? 1 : 0;
+    s.loaded = st.x1 == NX ? 1 : 0;
+    hs.cls.assign(s.npl, 1);
+    int c1 = 0, c2 = 0, c3 = 0;
+    for (int q = 0; q < s.npl; ++q) {
+      const int gi = s.I0 + q / s.nyn, gj = s.J0 + q % s.nyn;
+      signed char c = 1;
+      if (gi == 0) c = 3;
+      else if ((gi == st.x0 && st.x0 > 0) || (gi == st.x1 && st.x1 < NX) || (gj == st.y0 && st.y0 > 0) ||
+               (gj == st.y1 && st.y1 < NY))
+        c = 2;
+      hs.cls[q] = c;
+      (c == 1 ? c1 : c == 2 ? c2 : c3)++;
+    }
+    h->n1[j] = 3 * c1 * s.nzn;
+    h->n2[j] = 3 * c2 * s.nzn;
+    h->n3[j] = 3 * c3 * s.nzn;
+    s.nK = 3 * (c1 + c2);
+    s.nA = 3 * c1;
+    s.bK = round_up(std::max(s.nK, 1), TILE);
+    s.bA = round_up(std::max(s.nA, 1), TILE);
+    hs.mapK.assign(s.bK, -1);
+    hs.mapA.assign(s.bA, -1);
+    hs.invK.assign(3 * s.npl, -1);
+    hs.invA.assign(3 * s.npl, -1);
+    int ck = 0, ca = 0;
+    for (int q = 0; q < s.npl; ++q)
+      for (int c = 0; c < 3; ++c) {
+        if (hs.cls[q] != 3) { hs.mapK[ck] = 3 * q + c; hs.invK[3 * q + c] = ck++; }
+        if (hs.cls[q] == 1) { hs.mapA[ca] = 3 * q + c; hs.invA[3 * q + c] = ca++; }
+      }
+    for (int i = 0; i < 6; ++i) s.pin[i] = -1;
+    if (s.floating) {
+      // 3-2-1 pins on three bottom corners of the Omega* box
+      const int qa = 0, qb = (s.nxn - 1) * s.nyn, qc = s.nyn - 1;
+      s.pin[0] = 3 * qa; s.pin[1] = 3 * qa + 1; s.pin[2] = 3 * qa + 2;
+      s.pin[3] = 3 * qb + 1; s.pin[4] = 3 * qb + 2;
+      s.pin[5] = 3 * qc + 2;
+    }
+    // mu on Omega* nodes (zero outside Omega)
+    hs.mu.assign(s.nnode, 0.0);
+    const int onx = om.x1 - om.x0 + 1, ony = om.y1 - om.y0 + 1;
+    for (int k = 0; k <= NZ; ++k)
+      for (int q = 0; q < s.npl; ++q) {
+        const int gi = s.I0 + q / s.nyn, gj = s.J0 + q % s.nyn;
+        if (gi < om.x0 || gi > om.x1 || gj < om.y0 || gj > om.y1) continue;
+        const double w = wts[j][((size_t)(gi - om.x0) * ony + (gj - om.y0)) * (NZ + 1) + k];
+        (void)onx;
+        hs.mu[(size_t)k * s.npl + q] = w / total[((size_t)gi * (NY + 1) + gj) * (NZ + 1) + k];
+      }
+    // consistent nodal load of the traction (-p, 0, 0) on x = L
+    hs.bload.assign(s.nfull, 0.0);
+    if (s.loaded)
+      for (int k = 0; k <= NZ; ++k)
+        for (int q = 0; q < s.npl; ++q) {
+          const int gi = s.I0 + q / s.nyn, gj = s.J0 + q % s.nyn;
+          if (gi != NX) continue;
+          const double wy = (gj == 0 || gj == NY) ? 0.5 : 1.0, wz = (k == 0 || k == NZ) ? 0.5 : 1.0;
+          hs.bload[((size_t)k * s.npl + q) * 3] = -h->traction * h->hy * h->hz * wy * wz;
+        }
+  }
+  // coarse pairs: Omega_s node box intersected with Omega*_t node box
+  h->pairs.clear();
+  for (int s = 0; s < h->N; ++s)
+    for (int t = 0; t < h->N; ++t) {
+      const SubDev& S = h->sub[s];
+      const SubDev& T = h->sub[t];
+      const int x0 = std::max(S.oI0, T.I0), x1 = std::min(S.oI1, T.I1);
+      const int y0 = std::max(S.oJ0, T.J0), y1 = std::min(S.oJ1, T.J1);
+      if (x0 <= x1 && y0 <= y1) h->pairs.push_back({s, t, x0, x1, y0, y1});
+    }
+  return MSGFEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Factorisation schedule: per layer, SYRK; per tile column k: POTRF, TRMM,
+// UPDATE; then TRTRI rows 1..T-1.  Tasks of all subdomains (and of K and A11)
+// with the same key are launched together.
+namespace {
+
+struct FactorKeys {
+  std::map<long long, std::vector<GemmTask>> gemm;
+  std::map<long long, std::vector<PotrfTask>> potrf;
+};
+
+void add_matrix_tasks(FactorKeys& fk, double* D, double* E, double* L, int b, int nL, int sub, int Tmax) {
+  const int T = b / TILE;
+  const long long per_layer = 4LL * Tmax;
+  auto tileD = [&](int l, int i, int j) { return D + (size_t)l * b * b + (size_t)i * TILE * b + (size_t)j * TILE; };
+  auto tileE = [&](int l, int i, int j) { return E + (size_t)l * b * b + (size_t)i * TILE * b + (size_t)j * TILE; };
+  auto tileL = [&](int l, int i, int j) { return L + (size_t)l * b * b + (size_t)i * TILE * b + (size_t)j * TILE; };
+  for (int l = 0; l < nL; ++l) {
+    const long long base = l * per_layer;
+    if (l > 0)
+      for (int i = 0; i < T; ++i)
+        for (int j = 0; j <= i; ++j)
+          fk.gemm[base].push_back({tileE(l - 1, i, 0), tileE(l - 1, j, 0), tileD(l, i, j), nullptr, b, b, b, b,
+                                   G_TRANSB | G_ACC | G_NEG, sub});
+    for (int k = 0; k < T; ++k) {
+      fk.potrf[base + 1 + 3 * k].push_back({tileD(l, k, k), tileL(l, k, k), b, sub});
+      auto& trmm = fk.gemm[base + 2 + 3 * k];
+      for (int i = k + 1; i < T; ++i)
+        trmm.push_back({tileD(l, i, k), tileL(l, k, k), tileD(l, i, k), nullptr, b, b, b, TILE, G_TRANSB, sub});
+      if (l + 1 < nL)
+        for (int i = 0; i < T; ++i)
+          trmm.push_back({tileE(l, i, k), tileL(l, k, k), tileE(l, i, k), nullptr, b, b, b, TILE, G_TRANSB, sub});
+      auto& upd = fk.gemm[base + 3 + 3 * k];
+      for (int j = k + 1; j < T; ++j) {
+        for (int i = j; i < T; ++i)
+          upd.push_back({tileD(l, i, k), tileD(l, j, k), tileD(l, i, j), nullptr, b, b, b, TILE,
+                         G_TRANSB | G_ACC | G_NEG, sub});
+        if (l + 1 < nL)
+          for (int i = 0; i < T; ++i)
+            upd.push_back({tileE(l, i, k), tileD(l, j, k), tileE(l, i, j), nullptr, b, b, b, TILE,
+                           G_TRANSB | G_ACC | G_NEG, sub});
+      }
+    }
+    for (int i = 1; i < T; ++i) {
+      auto& tr = fk.gemm[base + 1 + 3 * Tmax + (i - 1)];
+      for (int k = 0; k < i; ++k)
+        tr.push_back({tileD(l, i, k), tileL(l, k, k), tileL(l, i, k), tileL(l, i, i), b, b, b, (i - k) * TILE,
+                      G_POSTMUL | G_NEG, sub});
+    }
+  }
+}
+
+void flatten(FactorKeys& fk, Schedule& sch) {
+  sch.steps.clear();
+  sch.gemm.clear();
+  sch.potrf.clear();
+  std::map<long long, int> kinds;
+  for (auto& kv : fk.gemm) kinds[kv.first] = 0;
+  for (auto& kv : fk.potrf) kinds[kv.first] = 1;
+  for (auto& kv : kinds) {
+    if (kv.second == 0) {
+      auto& v = fk.gemm[kv.first];
+      if (v.empty()) continue;
+      sch.steps.push_back({0, (int)sch.gemm.size(), (int)v.size()});
+      sch.gemm.insert(sch.gemm.end(), v.begin(), v.end());
+    } else {
+      auto& v = fk.potrf[kv.first];
+      if (v.empty()) continue;
+      sch.steps.push_back({1, (int)sch.potrf.size(), (int)v.size()});
+      sch.potrf.insert(sch.potrf.end(), v.begin(), v.end());
+    }
+  }
+}
+
+// Solve schedule of one matrix kind over all subdomains.
+void add_solve_tasks(std::map<long long, std::vector<SolveTask>>& keys, double* E, double* L, double* yc, double* rc,
+                     const int* map, int b, int nL, int npl, int sub) {
+  const int T = b / TILE;
+  for (int l = 0; l < nL; ++l) {
+    const int row_off = l * 3 * npl;
+    for (int i = 0; i < T; ++i) {
+      SolveTask f1{};
+      f1.C = rc + (size_t)i * TILE * PST;
+      f1.gmap = map + i * TILE;
+      f1.row_off = row_off;
+      f1.sub = sub;
+      f1.flags = S_INIT_GATHER;
+      if (l > 0) {
+        f1.A = E + (size_t)(l - 1) * b * b + (size_t)i * TILE * b;
+        f1.B = yc + (size_t)(l - 1) * b * PST;
+        f1.lda = b;
+        f1.K = b;
+        f1.flags |= S_NEG;
+      }
+      keys[2LL * l].push_back(f1);
+      SolveTask f2{};
+      f2.C = yc + (size_t)l * b * PST + (size_t)i * TILE * PST;
+      f2.A = L + (size_t)l * b * b + (size_t)i * TILE * b;
+      f2.B = rc;
+      f2.lda = b;
+      f2.K = (i + 1) * TILE;
+      f2.sub = sub;
+      keys[2LL * l + 1].push_back(f2);
+    }
+  }
+  for (int l = nL - 1; l >= 0; --l) {
+    const long long kb = 2LL * nL + 2LL * (nL - 1 - l);
+    const int row_off = l * 3 * npl;
+    for (int i = 0; i < T; ++i) {
+      SolveTask b1{};
+      b1.C = rc + (size_t)i * TILE * PST;
+      b1.init = yc + (size_t)l * b * PST + (size_t)i * TILE * PST;
+      b1.flags = S_INIT_TILE;
+      b1.sub = sub;
+      if (l + 1 < nL) {
+        b1.A = E + (size_t)l * b * b + (size_t)i * TILE;
+        b1.B = yc + (size_t)(l + 1) * b * PST;
+        b1.lda = b;
+        b1.K = b;
+        b1.flags |= S_TRANSA | S_NEG;
+      }
+      keys[kb].push_back(b1);
+      SolveTask b2{};
+      b2.C = yc + (size_t)l * b * PST + (size_t)i * TILE * PST;
+      b2.A = L + (size_t)l * b * b + (size_t)i * TILE * b + (size_t)i * TILE;
+      b2.B = rc + (size_t)i * TILE * PST;
+      b2.lda = b;
+      b2.K = b - i * TILE;
+      b2.flags = S_TRANSA | S_SCATTER;
+      b2.smap = map + i * TILE;
+      b2.row_off = row_off;
+      b2.sub = sub;
+      keys[kb + 1].push_back(b2);
+    }
+  }
+}
+
+void flatten_solve(std::map<long long, std::vector<SolveTask>>& keys, SolveSchedule& sch) {
+  sch.steps.clear();
+  sch.tasks.clear();
+  for (auto& kv : keys) {
+    if (kv.second.empty()) continue;
+    sch.steps.push_back({(int)sch.tasks.size(), (int)kv.second.size()});
+    sch.tasks.insert(sch.tasks.end(), kv.second.begin(), kv.second.end());
+  }
+}
+
+}  // namespace
+
+void build_factor_schedule(msgfem* h) {
+  FactorKeys fk;
+  int Tmax = 1;
+  for (const auto& s : h->sub) Tmax = std::max(Tmax, std::max(s.bK, s.bA) / TILE);
+  for (int j = 0; j < h->N; ++j) {
+    SubDev& s = h->sub[j];
+    add_matrix_tasks(fk, s.DK, s.EK, s.LK, s.bK, s.nzn, j, Tmax);
+    add_matrix_tasks(fk, s.DA, s.EA, s.LA, s.bA, s.nzn, j, Tmax);
+  }
+  flatten(fk, h->fact);
+}
+
+void build_solve_schedules(msgfem* h) {
+  std::map<long long, std::vector<SolveTask>> kk, ka;
+  for (int j = 0; j < h->N; ++j) {
+    SubDev& s = h->sub[j];
+    add_solve_tasks(kk, s.EK, s.LK, s.ycK, s.rcK, s.mapK, s.bK, s.nzn, s.npl, j);
+    add_solve_tasks(ka, s.EA, s.LA, s.ycA, s.rcA, s.mapA, s.bA, s.nzn, s.npl, j);
+  }
+  flatten_solve(kk, h->solveK);
+  flatten_solve(ka, h->solveA);
+}
+
+// Coarse matrix: one dense block of size NcPad, factorised by the same tile
+// tasks (subdomain index N is the always-active coarse slot), and solved
+// with one forward and one backward sweep.
+void build_coarse_schedules(msgfem* h) {
+  FactorKeys fk;
+  const int b = h->NcPad;
+  add_matrix_tasks(fk, h->d_AH, nullptr, h->d_AHinv, b, 1, h->N, b / TILE);
+  flatten(fk, h->cfact);
+  const int T = b / TILE;
+  std::map<long long, std::vector<SolveTask>> keys;
+  for (int i = 0; i < T; ++i) {
+    SolveTask f1{};
+    f1.C = h->d_rH + (size_t)i * TILE * PST;
+    f1.init = h->d_bH + (size_t)i * TILE * PST;
+    f1.flags = S_INIT_TILE;
+    f1.sub = h->N;
+    keys[0].push_back(f1);
+    SolveTask f2{};
+    f2.C = h->d_yH + (size_t)i * TILE * PST;
+    f2.A = h->d_AHinv + (size_t)i * TILE * b;
+    f2.B = h->d_rH;
+    f2.lda = b;
+    f2.K = (i + 1) * TILE;
+    f2.sub = h->N;
+    keys[1].push_back(f2);
+    SolveTask b2{};
+    b2.C = h->d_cH + (size_t)i * TILE * PST;
+    b2.A = h->d_AHinv + (size_t)i * TILE * b + (size_t)i * TILE;
+    b2.B = h->d_yH + (size_t)i * TILE * PST;
+    b2.lda = b;
+    b2.K = b - i * TILE;
+    b2.flags = S_TRANSA;
+    b2.sub = h->N;
+    keys[2].push_back(b2);
+  }
+  flatten_solve(keys, h->csolve);
+}

@@ -1,0 +1,190 @@
+"""ctypes binding of libmsgfem (include/msgfem.h): argument marshalling only.
+
+Every step of the local stage runs in the library's CUDA kernels; this module
+only converts arrays and reports status codes.  It fails loudly when the
+library has not been built.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libmsgfem.so")
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTSPD", 5: "ENOCONV", 6: "ESTATE"}
+EXPORTS = ("msgfem_setup", "msgfem_update_angles", "msgfem_local_spaces", "msgfem_coarse_assemble",
+           "msgfem_solve", "msgfem_get_basis", "msgfem_get_info", "msgfem_num_subdomains",
+           "msgfem_get_profile", "msgfem_reset_profile", "msgfem_last_error", "msgfem_destroy")
+
+
+class MsgfemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Mesh(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("hx", C.c_double), ("hy", C.c_double),
+                ("hz", C.c_double), ("traction", C.c_double)]
+
+
+class Plies(C.Structure):
+    _fields_ = [("E9", C.c_void_p), ("elem_angle_deg", C.c_void_p)]
+
+
+class Partition(C.Structure):
+    _fields_ = [("sx", C.c_int), ("sy", C.c_int)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("block", C.c_int), ("max_iter", C.c_int), ("tol", C.c_double),
+                ("seed", C.c_ulonglong), ("stream", C.c_void_p), ("profile", C.c_int)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("assemble_ms", C.c_double), ("factor_ms", C.c_double), ("solve_ms", C.c_double),
+                ("iterate_ms", C.c_double), ("coarse_ms", C.c_double), ("factor_flops", C.c_double),
+                ("solve_flops", C.c_double), ("launches", C.c_longlong), ("solve_calls", C.c_int)]
+
+
+class SubInfo(C.Structure):
+    _fields_ = [("n_star_dof", C.c_int), ("n1", C.c_int), ("n2", C.c_int), ("n3", C.c_int), ("floating", C.c_int),
+                ("iterations", C.c_int), ("basis_size", C.c_int), ("residual", C.c_double)]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libmsgfem.so; raises if it is missing (there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2211_13893_gb300.build.build()")
+    lib = C.CDLL(path)
+    h = C.c_void_p
+    sig = {
+        "msgfem_setup": (C.c_int, [C.POINTER(Mesh), C.POINTER(Plies), C.POINTER(Partition), C.c_int, C.c_int,
+                                   C.POINTER(Options), C.POINTER(h)]),
+        "msgfem_update_angles": (C.c_int, [h, C.c_void_p]),
+        "msgfem_local_spaces": (C.c_int, [h, C.c_int, C.c_void_p]),
+        "msgfem_coarse_assemble": (C.c_int, [h, C.POINTER(C.c_int)]),
+        "msgfem_solve": (C.c_int, [h, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
+        "msgfem_get_basis": (C.c_int, [h, C.c_int, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                       C.POINTER(C.c_int)]),
+        "msgfem_get_info": (C.c_int, [h, C.c_int, C.POINTER(SubInfo)]),
+        "msgfem_get_profile": (C.c_int, [h, C.POINTER(Profile)]),
+        "msgfem_reset_profile": (C.c_int, [h]),
+        "msgfem_num_subdomains": (C.c_int, [h]),
+        "msgfem_last_error": (C.c_char_p, [h]),
+        "msgfem_destroy": (None, [h]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Host numpy array (C-contiguous float64) or a torch CUDA tensor -> address."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+class MSGFEM:
+    """One MS-GFEM problem: a laminated box mesh, its decomposition and the handle."""
+
+    def __init__(self, nx, ny, nz, hx, hy, hz, traction, E9, elem_angles, sx, sy, overlap, oversampling,
+                 block=0, max_iter=0, tol=0.0, seed=0, stream=None, precision=0, profile=0):
+        self.lib = load_library()
+        self.h = C.c_void_p()
+        self._E9 = np.ascontiguousarray(E9, dtype=np.float64)
+        ang = elem_angles
+        if not hasattr(ang, "data_ptr"):
+            ang = np.ascontiguousarray(ang, dtype=np.float64).reshape(-1)
+        self._ang = ang
+        self.mesh = Mesh(nx, ny, nz, hx, hy, hz, traction)
+        self.n_dof = 3 * (nx + 1) * (ny + 1) * (nz + 1)
+        plies = Plies(self._E9.ctypes.data, _ptr(ang))
+        part = Partition(sx, sy)
+        opt = Options(precision, block, max_iter, tol, seed, stream, profile)
+        st = self.lib.msgfem_setup(C.byref(self.mesh), C.byref(plies), C.byref(part), overlap, oversampling,
+                                   C.byref(opt), C.byref(self.h))
+        self._check(st)
+        self.N = self.lib.msgfem_num_subdomains(self.h)
+        self.n_loc = None
+
+    @classmethod
+    def from_config(cls, cfg, angles, **kw):
+        return cls(cfg.NX, cfg.NY, cfg.NZ, cfg.hx, cfg.hy, cfg.t, cfg.traction, cfg.material, angles,
+                   cfg.sx, cfg.sy, cfg.overlap, cfg.oversampling, **kw)
+
+    def _check(self, st, allow=()):
+        if st != 0 and st not in allow:
+            msg = self.lib.msgfem_last_error(self.h) if self.h else b""
+            raise MsgfemError(st, (msg or b"").decode())
+        return st
+
+    def update_angles(self, angles):
+        if not hasattr(angles, "data_ptr"):
+            angles = np.ascontiguousarray(angles, dtype=np.float64).reshape(-1)
+        self._ang = angles
+        self._check(self.lib.msgfem_update_angles(self.h, _ptr(angles)))
+
+    def local_spaces(self, n_loc, lam_out=None, allow_noconv=False):
+        """Returns eigenvalues (N, n_loc) (numpy) or fills lam_out (device tensor)."""
+        self.n_loc = n_loc
+        out = lam_out if lam_out is not None else np.zeros((self.N, n_loc))
+        self._check(self.lib.msgfem_local_spaces(self.h, n_loc, _ptr(out)), allow=(5,) if allow_noconv else ())
+        return out
+
+    def coarse_assemble(self):
+        nc = C.c_int()
+        self._check(self.lib.msgfem_coarse_assemble(self.h, C.byref(nc)))
+        return nc.value
+
+    def solve(self, u_ref=None, u_out=None):
+        """Returns (u^G, energy error or None); u_out may be a device tensor."""
+        u = u_out if u_out is not None else np.zeros(self.n_dof)
+        err = C.c_double(-1.0)
+        if u_ref is not None and not hasattr(u_ref, "data_ptr"):
+            u_ref = np.ascontiguousarray(u_ref, dtype=np.float64)
+        self._check(self.lib.msgfem_solve(self.h, _ptr(u), _ptr(u_ref), C.byref(err)))
+        return u, (err.value if u_ref is not None else None)
+
+    def basis(self, j):
+        rows, cols, box = C.c_int(), C.c_int(), (C.c_int * 4)()
+        self._check(self.lib.msgfem_get_basis(self.h, j, None, C.byref(rows), C.byref(cols), box))
+        out = np.zeros(rows.value * cols.value)
+        self._check(self.lib.msgfem_get_basis(self.h, j, out.ctypes.data, C.byref(rows), C.byref(cols), box))
+        return out.reshape(cols.value, rows.value).T, tuple(box)
+
+    def info(self, j):
+        inf = SubInfo()
+        self._check(self.lib.msgfem_get_info(self.h, j, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in SubInfo._fields_}
+
+    def profile(self, reset=False):
+        pr = Profile()
+        self._check(self.lib.msgfem_get_profile(self.h, C.byref(pr)))
+        if reset:
+            self._check(self.lib.msgfem_reset_profile(self.h))
+        return {k: getattr(pr, k) for k, _ in Profile._fields_}
+
+    def close(self):
+        if self.h:
+            self.lib.msgfem_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
