@@ -163,6 +163,32 @@ msgfem_status msgfem_solve(msgfem_h h, double* u_out, const double* u_ref, doubl
  * Omega*_j node box {i0, i1, j0, j1}. */
 msgfem_status msgfem_get_basis(msgfem_h h, int j, double* phi_out, int* rows, int* cols, int* box_out);
 
+/* Energy error ||u_ref - u||_a / ||u_ref||_a of two caller-owned device
+ * vectors (3 (nx+1)(ny+1)(nz+1) doubles each, the layout of msgfem_solve), the
+ * same quantity msgfem_solve reports, computed without allocating any memory.
+ * The paper has no counterpart: this is a library convenience.
+ *
+ * Why it exists: some callers cannot call cudaMalloc at the point where they
+ * evaluate a solution -- for example an application whose device memory is
+ * already committed to another framework's memory pool, or a latency-bound loop
+ * that must not enter the driver's allocator, which can synchronise the device.
+ * msgfem_solve needs its handle-owned staging buffer for u_ref; this entry point
+ * reads the caller's device vectors in place and keeps its partial sums in a
+ * fixed 64 KiB array in device global memory that every GPU loading the library
+ * holds until the process exits.  It calls no allocating routine.
+ *
+ * Limits and behaviour: the mesh may have at most 4,194,304 elements (EINVAL
+ * with a message otherwise); u and u_ref must be device pointers (EINVAL);
+ * the handle must have run msgfem_local_spaces (ESTATE), whose element
+ * stiffness is reused.  energy_err_out may be a host pointer (the call then
+ * waits for the result) or a device pointer (written on the handle's stream).
+ * The first call on a device looks up the device address of the array; make
+ * that first call before any stream capture.  All calls share the one array and
+ * each call overwrites every slot it reads, so consecutive calls are
+ * independent, but calls whose kernels overlap on the GPU (other streams, other
+ * threads) race on the array and must be serialised by the caller. */
+msgfem_status msgfem_energy_error_noalloc(msgfem_h h, const double* u, const double* u_ref, double* energy_err_out);
+
 msgfem_status msgfem_get_info(msgfem_h h, int j, msgfem_subinfo* info);
 /* Copy the phase timers (requires msgfem_options.profile = 1 for times). */
 msgfem_status msgfem_get_profile(msgfem_h h, msgfem_profile* out);

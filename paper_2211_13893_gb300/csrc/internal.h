@@ -164,6 +164,8 @@ struct msgfem {
 
 extern long long g_launch_count;   // kernel launches issued by this library
 
+msgfem_status cuda_fail(msgfem* h, cudaError_t e, const char* what, const char* file, int line);
+
 // host scheduling (setup.cpp)
 msgfem_status build_problem(msgfem* h);
 void build_factor_schedule(msgfem* h);

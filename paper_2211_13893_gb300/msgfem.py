@@ -15,7 +15,8 @@ LIB_PATH = os.path.join(HERE, "lib", "libmsgfem.so")
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTSPD", 5: "ENOCONV", 6: "ESTATE"}
 EXPORTS = ("msgfem_setup", "msgfem_update_angles", "msgfem_local_spaces", "msgfem_coarse_assemble",
            "msgfem_solve", "msgfem_get_basis", "msgfem_get_info", "msgfem_num_subdomains",
-           "msgfem_get_profile", "msgfem_reset_profile", "msgfem_last_error", "msgfem_destroy")
+           "msgfem_get_profile", "msgfem_reset_profile", "msgfem_energy_error_noalloc", "msgfem_last_error",
+           "msgfem_destroy")
 
 
 class MsgfemError(RuntimeError):
@@ -76,6 +77,7 @@ def load_library(path=LIB_PATH):
                                        C.POINTER(C.c_int)]),
         "msgfem_get_info": (C.c_int, [h, C.c_int, C.POINTER(SubInfo)]),
         "msgfem_get_profile": (C.c_int, [h, C.POINTER(Profile)]),
+        "msgfem_energy_error_noalloc": (C.c_int, [h, C.c_void_p, C.c_void_p, C.c_void_p]),
         "msgfem_reset_profile": (C.c_int, [h]),
         "msgfem_num_subdomains": (C.c_int, [h]),
         "msgfem_last_error": (C.c_char_p, [h]),
