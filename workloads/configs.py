@@ -16,6 +16,7 @@ Sizes are the ones of the five benchmark workloads:
 * ``c5``  the c1 beam with a per-sample wrinkle field of ply-angle
   perturbation (learned warm-start workload).
 
+``p2`` has c2-sized subdomains but only six of them (profiling).
 Smaller ``t*`` workloads are test cases that span several layers, ragged
 partitions and both clamped and floating subdomains.
 """
@@ -74,6 +75,9 @@ CONFIGS = {
                      noise_sd_deg=1.0, noise_seed=1),
     "c3": BeamConfig("c3", 384, 24, 48, sx=32, sy=2, overlap=2, oversampling=4, n_loc=24),
     "c5": BeamConfig("c5", 24, 4, 12, sx=2, sy=1, overlap=1, oversampling=2, n_loc=8),
+    # profiling case: c2-sized subdomains (one interior), six subdomains in all
+    "p2": BeamConfig("p2", 36, 12, 39, sx=3, sy=2, overlap=2, oversampling=4, n_loc=20,
+                     noise_sd_deg=1.0, noise_seed=1),
     # test cases: a few layers, ragged partitions, clamped / floating / interior subdomains
     "t1": BeamConfig("t1", 8, 2, 3, sx=2, sy=1, overlap=1, oversampling=1, n_loc=6),
     "t2": BeamConfig("t2", 12, 4, 4, sx=3, sy=2, overlap=1, oversampling=2, n_loc=10),
