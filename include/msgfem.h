@@ -86,13 +86,14 @@ typedef enum { MSGFEM_FP64 = 0, MSGFEM_MIXED = 1 } msgfem_precision;
 
 typedef struct {
   int precision;        /* msgfem_precision */
-  int block;            /* subspace block size p; 0 = n_loc + max(8, n_loc / 2) */
-  int max_iter;         /* eigensolver iteration cap; 0 = 100 */
+  int block;            /* subspace iteration block size p; 0 = n_loc + max(8, n_loc / 2) */
+  int max_iter;         /* subspace iteration cap; 0 = 100 (block Krylov stops at a basis of 96) */
   double tol;           /* stop when ||theta E S^-1 T x - x||_T <= tol per wanted pair (or the
                            decrease stalls below 1e2 tol); 0 = 1e-7 */
   unsigned long long seed;  /* seed of the counter-based start-block generator */
   void* stream;         /* cudaStream_t to issue work on; NULL = default stream */
   int profile;          /* 1: time the phases with CUDA events (msgfem_get_profile) */
+  int solver;           /* 0: block Krylov (block width 8, basis <= 96), 1: subspace iteration */
 } msgfem_options;
 
 /* Phase timers (CUDA events on the handle's stream, milliseconds, summed over

@@ -21,6 +21,24 @@
 
 #include "internal.h"
 
+void launch_stencil_kb(msgfem* h, int src, int dst, int mode, double alpha);
+void launch_gram_kb(msgfem* h, int wx, int xs, int nx, int wy, int only_floating);
+void launch_update_kb(msgfem* h, int wx, int xs, int nx, int wy, int only_floating);
+void launch_h_accum(msgfem* h, int m, int j, int add);
+void launch_cholqr_kb(msgfem* h, int j, int pass);
+void launch_rotate_kb(msgfem* h, int which);
+void launch_store_block(msgfem* h, int src, int j);
+void launch_random_kb(msgfem* h, int which, unsigned long long seed);
+void launch_mask_kb(msgfem* h, int which, int keep);
+void launch_zero_pins_kb(msgfem* h, int which);
+void launch_load_col_kb(msgfem* h, int which, double sign);
+void launch_take_col_kb(msgfem* h, int which);
+void launch_zero_kb(msgfem* h, int which);
+void launch_rr_krylov(msgfem* h, const int* d_m, const int* d_nw);
+void launch_ritz(msgfem* h, const int* d_m, const int* d_nw, int scale, bool masked);
+void launch_restart(msgfem* h, int m, int k);
+constexpr double KRYLOV_SIGMA = 1e-2;   // N = S + sigma T (matches KSIGMA in k_krylov.cu)
+
 msgfem_status cuda_fail(msgfem* h, cudaError_t e, const char* what, const char* file, int line) {
   char buf[512];
   snprintf(buf, sizeof(buf), "CUDA error %s (%s) in %s at %s:%d", cudaGetErrorName(e), cudaGetErrorString(e), what,
@@ -132,6 +150,21 @@ msgfem_status allocate(msgfem* h) {
     TRY(dalloc(h, &s.theta, PST));
     TRY(dalloc(h, &s.resid, PST));
     TRY(dalloc(h, &s.status, 4));
+    TRY(dalloc(h, &s.QB, (size_t)s.nfull * MQ));
+    CK(cudaMemset(s.QB, 0, (size_t)s.nfull * MQ * sizeof(double)));
+    double** kbs[] = {&s.Zb, &s.Wb, &s.Tb};
+    for (double** m : kbs) {
+      TRY(dalloc(h, m, (size_t)s.nfull * KB));
+      CK(cudaMemset(*m, 0, (size_t)s.nfull * KB * sizeof(double)));
+    }
+    TRY(dalloc(h, &s.ycK8, (size_t)s.nzn * s.bK * KB));
+    TRY(dalloc(h, &s.ycA8, (size_t)s.nzn * s.bA * KB));
+    TRY(dalloc(h, &s.rcK8, (size_t)s.bK * KB));
+    TRY(dalloc(h, &s.rcA8, (size_t)s.bA * KB));
+    TRY(dalloc(h, &s.H, (size_t)(MQ + KB) * MQ));
+    CK(cudaMemset(s.H, 0, (size_t)(MQ + KB) * MQ * sizeof(double)));
+    TRY(dalloc(h, &s.Hc, (size_t)MQ * KB));
+    TRY(dalloc(h, &s.Yk, (size_t)MQ * PST));
     CK(cudaMemset(s.status, 0, 4 * sizeof(int)));
     CK(cudaMemcpy(s.mu, hs.mu.data(), hs.mu.size() * sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(cls, hs.cls.data(), hs.cls.size(), cudaMemcpyHostToDevice));
@@ -171,7 +204,9 @@ msgfem_status allocate(msgfem* h) {
   CK(cudaMemcpy(h->fact.d_gemm, h->fact.gemm.data(), h->fact.gemm.size() * sizeof(GemmTask), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(h->fact.d_potrf, h->fact.potrf.data(), h->fact.potrf.size() * sizeof(PotrfTask),
                 cudaMemcpyHostToDevice));
-  for (SolveSchedule* ss : {&h->solveK, &h->solveA}) {
+  TRY(dalloc(h, &h->d_mk, h->N));
+  TRY(dalloc(h, &h->d_nwk, h->N));
+  for (SolveSchedule* ss : {&h->solveK, &h->solveA, &h->solveK8, &h->solveA8}) {
     TRY(dalloc(h, &ss->d_tasks, ss->tasks.size()));
     CK(cudaMemcpy(ss->d_tasks, ss->tasks.data(), ss->tasks.size() * sizeof(SolveTask), cudaMemcpyHostToDevice));
   }
@@ -261,7 +296,225 @@ void timed_solve(msgfem* h, int mat, int src, int dst, int neg) {
   h->prof.solve_calls += 1;
 }
 
+void timed_solve8(msgfem* h, int mat, int src, int dst, int neg) {
+  const int sp = span_begin(h, TAG_SOLVE);
+  run_solve_mv(mat == 0 ? h->solveK8 : h->solveA8, h->stream, src, dst, neg, KB);
+  span_end(h, sp);
+  h->prof.solve_flops += solve_flops(h, mat, KB);
+  h->prof.solve_calls += 1;
+}
+
+// B-orthogonal projection of a KB-wide block out of the rigid modes (floating only)
+void project_rigid_kb(msgfem* h, int which) {
+  launch_gram_kb(h, MV_BR, PST, 6, which, 1);
+  launch_update_kb(h, MV_R, PST, 6, which, 1);
+}
+
+// CholeskyQR2 of the working block in the N inner product (R_{j+1} into H)
+void cholqr2_kb(msgfem* h, int j) {
+  for (int pass = 1; pass <= 2; ++pass) {
+    launch_stencil_kb(h, MV_WB, MV_ZB, 4, KRYLOV_SIGMA);
+    launch_gram_kb(h, MV_WB, KB, KB, MV_ZB, 0);
+    launch_cholqr_kb(h, j, pass);
+    launch_rotate_kb(h, MV_WB);
+  }
+}
+
+// W <- M W for A-harmonic W: Z = B W, K solve, restrict to B2, A11 re-extension
+void apply_M_kb(msgfem* h) {
+  launch_stencil_kb(h, MV_WB, MV_ZB, 3, 1.0);
+  timed_solve8(h, 0, MV_ZB, MV_WB, 0);
+  launch_zero_pins_kb(h, MV_WB);
+  launch_mask_kb(h, MV_WB, 1 << 2);
+  launch_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
+  timed_solve8(h, 1, MV_TB, MV_WB, 1);
+  project_rigid_kb(h, MV_WB);
+}
+
 }  // namespace
+
+// Subspace iteration with Rayleigh-Ritz every step (solver = 1).
+msgfem_status run_subspace(msgfem* h, int n_loc, int p, bool& all_done) {
+  cudaStream_t st = h->stream;
+  std::vector<int> act(h->N, 1);
+  // 3. start block X0 on B2, A-harmonic extension, and psi in the last column
+  launch_random_b2(h, MV_W, p, h->opt.seed);
+  launch_stencil_apply(h, MV_W, MV_T1, 0, 1.0);
+  launch_copy_col(h, SRC_BLOAD, 0, MV_T1, PST - 1, -1.0);
+  timed_solve(h, 1, MV_T1, MV_W, 1);
+  launch_copy_col(h, MV_W, PST - 1, SRC_PSI, 0, 1.0);
+  launch_copy_col(h, MV_W, PST - 1, MV_W, PST - 1, 0.0);
+  launch_gram(h, MV_BR, MV_W, GM_G3);
+  launch_sub_rc(h, MV_W, MV_R, GM_G3, 6);
+  launch_copy_mv(h, MV_W, MV_PHI);
+  CK_LAUNCH();
+  h->iters.assign(h->N, 0);
+  std::vector<double> theta((size_t)h->N * PST), gdiag((size_t)h->N * PST * PST);
+  int it = 0;
+  all_done = false;
+  std::vector<std::vector<double>> dhist(h->N);
+  for (it = 0; it < h->opt.max_iter; ++it) {
+    // Rayleigh-Ritz on span(Phi) (Phi is B-orthogonal to the rigid modes)
+    launch_stencil_apply(h, MV_PHI, MV_Z, 3, 1.0);
+    launch_stencil_apply(h, MV_PHI, MV_KPHI, 0, 1.0);
+    launch_gram(h, MV_PHI, MV_Z, GM_G1);
+    launch_gram(h, MV_PHI, MV_KPHI, GM_G2);
+    launch_small_eig(h, p);
+    launch_rotate(h, MV_PHI, GM_Y, p);
+    launch_rotate(h, MV_Z, GM_Y, p);
+    launch_rotate(h, MV_KPHI, GM_Y, p);
+    // shift-invert step: W = K^{-1} Z, X = W|B2, Phi_new = E X
+    timed_solve(h, 0, MV_Z, MV_W, 0);
+    launch_zero_pins(h, MV_W);
+    launch_mask_rows(h, MV_W, 1 << 2);
+    launch_stencil_apply(h, MV_W, MV_T1, 0, 1.0);
+    timed_solve(h, 1, MV_T1, MV_W, 1);
+    // B-orthogonal projection out of the rigid modes (floating subdomains)
+    launch_gram(h, MV_BR, MV_W, GM_G3);
+    launch_sub_rc(h, MV_W, MV_R, GM_G3, 6);
+    // convergence: d_i = theta_i Phi_new_i - Phi_i vanishes at an eigenpair;
+    // ||d_i||_T = ||D_mu d_i||_a is the energy of the error of the PoU-weighted
+    // basis function (Phi_i has ||Phi_i||_T = 1)
+    launch_theta_axpy(h, MV_W, MV_PHI, MV_T1, p);
+    launch_stencil_apply(h, MV_T1, MV_CW, 3, 1.0);
+    launch_gram(h, MV_T1, MV_CW, GM_G3);
+    CK_LAUNCH();
+    std::vector<int> act_now(act);
+    all_done = true;
+    for (int j = 0; j < h->N; ++j) {
+      if (!act[j]) continue;
+      h->iters[j] = it + 1;
+      CK(cudaMemcpyAsync(&theta[(size_t)j * PST], h->sub[j].theta, PST * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(&gdiag[(size_t)j * PST * PST], h->sub[j].G3, PST * PST * sizeof(double),
+                         cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    for (int j = 0; j < h->N; ++j) {
+      if (!act[j]) continue;
+      const int nw = n_loc - (h->sub[j].floating ? 6 : 0);
+      double dmax = 0.0;
+      for (int c = 0; c < nw; ++c)
+        dmax = std::max(dmax, std::sqrt(std::fabs(gdiag[(size_t)j * PST * PST + (size_t)c * PST + c])));
+      // converged, or stalled at the rounding floor of the solves (less than 10 %
+      // decrease over three iterations while already below 100 tol)
+      bool done = dmax <= h->opt.tol;
+      auto& hist = dhist[j];
+      hist.push_back(dmax);
+      if (!done && hist.size() >= 4 && dmax <= 1e2 * h->opt.tol && dmax > 0.9 * hist[hist.size() - 4]) done = true;
+      if (done) act_now[j] = 0;
+      else all_done = false;
+    }
+    if (all_done || it + 1 == h->opt.max_iter) break;
+    // continue with the new block on subdomains not yet converged
+    TRY(set_active(h, act_now));
+    launch_copy_mv(h, MV_W, MV_PHI);
+    act = act_now;
+  }
+  return MSGFEM_OK;
+}
+
+// Block Krylov (block Lanczos, full re-orthogonalisation) on M = S^{-1} T in
+// the N = S + sigma T inner product, block width KB, basis up to MQ
+// (solver = 0, default).
+msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
+  cudaStream_t st = h->stream;
+  std::vector<int> nw(h->N), act(h->N, 1), mk(h->N, 0);
+  int nwmax = 0;
+  for (int j = 0; j < h->N; ++j) {
+    nw[j] = n_loc - (h->sub[j].floating ? std::min(6, n_loc) : 0);
+    nwmax = std::max(nwmax, nw[j]);
+  }
+  CK(cudaMemcpyAsync(h->d_nwk, nw.data(), h->N * sizeof(int), cudaMemcpyHostToDevice, st));
+  // particular function psi: A11 psi_1 = b_1 (one column of a KB-wide solve)
+  launch_load_col_kb(h, MV_TB, -1.0);
+  launch_zero_kb(h, MV_WB);
+  timed_solve8(h, 1, MV_TB, MV_WB, 1);
+  launch_take_col_kb(h, MV_WB);
+  for (int j = 0; j < h->N; ++j)
+    if (nw[j] <= 0) act[j] = 0;
+  TRY(set_active(h, act));
+  // start block on B2, A-harmonic extension, first application of M
+  launch_random_kb(h, MV_WB, h->opt.seed);
+  launch_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
+  timed_solve8(h, 1, MV_TB, MV_WB, 1);
+  project_rigid_kb(h, MV_WB);
+  apply_M_kb(h);
+  // Q_0 = W R^{-1} with W^T N W = R^T R (CholeskyQR2)
+  cholqr2_kb(h, -1);
+  launch_store_block(h, MV_WB, 0);
+  CK_LAUNCH();
+  h->iters.assign(h->N, 0);
+  std::vector<double> res((size_t)h->N * PST);
+  all_done = true;
+  for (int j = 0; j < h->N; ++j) all_done = all_done && !act[j];
+  const int jmax = MQ / KB;
+  const int kkeep = std::min(PST, MQ - 2 * KB);   // Ritz vectors kept at a thick restart
+  int restarts = 0;
+  std::vector<int> kvec(h->N, kkeep);
+  for (int j = 0; j < jmax && !all_done; ++j) {
+    const int m = (j + 1) * KB;
+    apply_M_kb(h);   // W = M Q_j (W held Q_j)
+    // two passes of block Gram-Schmidt against Q_0..Q_j in the N inner product
+    for (int pass = 0; pass < 2; ++pass) {
+      launch_stencil_kb(h, MV_WB, MV_ZB, 4, KRYLOV_SIGMA);
+      launch_gram_kb(h, MV_QB, MQ, m, MV_ZB, 0);
+      launch_h_accum(h, m, j, pass);
+      launch_update_kb(h, MV_QB, MQ, m, MV_WB, 0);
+    }
+    cholqr2_kb(h, j);
+    if (m < MQ) launch_store_block(h, MV_WB, j + 1);
+    CK_LAUNCH();
+    // Rayleigh-Ritz where the basis can hold the wanted pairs plus one block
+    bool any = false;
+    for (int s = 0; s < h->N; ++s) {
+      mk[s] = (act[s] && m >= nw[s] + KB) ? m : 0;
+      any = any || mk[s] > 0;
+      if (act[s]) h->iters[s] = j + 1;
+    }
+    if (!any && m < MQ) continue;
+    const bool full = m >= MQ;
+    if (full)
+      for (int s = 0; s < h->N; ++s) if (act[s]) mk[s] = m;
+    CK(cudaMemcpyAsync(h->d_mk, mk.data(), h->N * sizeof(int), cudaMemcpyHostToDevice, st));
+    // a full basis computes kkeep Ritz pairs (the wanted ones come first) for the restart
+    if (full) CK(cudaMemcpyAsync(h->d_ncols, kvec.data(), h->N * sizeof(int), cudaMemcpyHostToDevice, st));
+    launch_rr_krylov(h, h->d_mk, full ? h->d_ncols : h->d_nwk);
+    CK_LAUNCH();
+    for (int s = 0; s < h->N; ++s)
+      if (mk[s] > 0) CK(cudaMemcpyAsync(&res[(size_t)s * PST], h->sub[s].resid, PST * sizeof(double),
+                                        cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    all_done = true;
+    for (int s = 0; s < h->N; ++s) {
+      if (!act[s]) continue;
+      if (mk[s] > 0) {
+        double rmax = 0.0;
+        for (int c = 0; c < nw[s]; ++c) rmax = std::max(rmax, res[(size_t)s * PST + c]);
+        h->m_final[s] = mk[s];
+        if (rmax <= h->opt.tol) act[s] = 0;
+      }
+      if (act[s]) all_done = false;
+    }
+    TRY(set_active(h, act));
+    if (full && !all_done && restarts < 8) {
+      // thick restart of the unconverged subdomains: keep kkeep Ritz vectors and
+      // the residual block, continue from block kkeep / KB
+      ++restarts;
+      launch_ritz(h, h->d_mk, h->d_ncols, 0, true);
+      launch_restart(h, m, kkeep);
+      CK_LAUNCH();
+      j = kkeep / KB - 1;
+    }
+  }
+  // Ritz vectors of the wanted pairs (theta ascending in s.theta)
+  TRY(set_active(h, std::vector<int>(h->N, 1)));
+  CK(cudaMemcpyAsync(h->d_mk, h->m_final.data(), h->N * sizeof(int), cudaMemcpyHostToDevice, st));
+  launch_ritz(h, h->d_mk, h->d_nwk, 1, false);
+  launch_stencil_apply(h, MV_PHI, MV_Z, 3, 1.0);
+  launch_stencil_apply(h, MV_PHI, MV_KPHI, 0, 1.0);
+  CK_LAUNCH();
+  return MSGFEM_OK;
+}
 
 extern "C" {
 
@@ -346,79 +599,14 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   launch_chol_inv_small(h, GM_G1, nullptr, 6, 0);
   launch_rotate(h, MV_R, GM_Y, 6);
   launch_rotate(h, MV_BR, GM_Y, 6);
-  // 3. start block X0 on B2, A-harmonic extension, and psi in the last column
-  launch_random_b2(h, MV_W, p, h->opt.seed);
-  launch_stencil_apply(h, MV_W, MV_T1, 0, 1.0);
-  launch_copy_col(h, SRC_BLOAD, 0, MV_T1, PST - 1, -1.0);
-  timed_solve(h, 1, MV_T1, MV_W, 1);
-  launch_copy_col(h, MV_W, PST - 1, SRC_PSI, 0, 1.0);
-  launch_copy_col(h, MV_W, PST - 1, MV_W, PST - 1, 0.0);
-  launch_gram(h, MV_BR, MV_W, GM_G3);
-  launch_sub_rc(h, MV_W, MV_R, GM_G3, 6);
-  launch_copy_mv(h, MV_W, MV_PHI);
-  CK_LAUNCH();
-  h->iters.assign(h->N, 0);
-  std::vector<double> theta((size_t)h->N * PST), gdiag((size_t)h->N * PST * PST);
-  int it = 0;
   bool all_done = false;
-  std::vector<std::vector<double>> dhist(h->N);
-  for (it = 0; it < h->opt.max_iter; ++it) {
-    // Rayleigh-Ritz on span(Phi) (Phi is B-orthogonal to the rigid modes)
-    launch_stencil_apply(h, MV_PHI, MV_Z, 3, 1.0);
-    launch_stencil_apply(h, MV_PHI, MV_KPHI, 0, 1.0);
-    launch_gram(h, MV_PHI, MV_Z, GM_G1);
-    launch_gram(h, MV_PHI, MV_KPHI, GM_G2);
-    launch_small_eig(h, p);
-    launch_rotate(h, MV_PHI, GM_Y, p);
-    launch_rotate(h, MV_Z, GM_Y, p);
-    launch_rotate(h, MV_KPHI, GM_Y, p);
-    // shift-invert step: W = K^{-1} Z, X = W|B2, Phi_new = E X
-    timed_solve(h, 0, MV_Z, MV_W, 0);
-    launch_zero_pins(h, MV_W);
-    launch_mask_rows(h, MV_W, 1 << 2);
-    launch_stencil_apply(h, MV_W, MV_T1, 0, 1.0);
-    timed_solve(h, 1, MV_T1, MV_W, 1);
-    // B-orthogonal projection out of the rigid modes (floating subdomains)
-    launch_gram(h, MV_BR, MV_W, GM_G3);
-    launch_sub_rc(h, MV_W, MV_R, GM_G3, 6);
-    // convergence: d_i = theta_i Phi_new_i - Phi_i vanishes at an eigenpair;
-    // ||d_i||_T = ||D_mu d_i||_a is the energy of the error of the PoU-weighted
-    // basis function (Phi_i has ||Phi_i||_T = 1)
-    launch_theta_axpy(h, MV_W, MV_PHI, MV_T1, p);
-    launch_stencil_apply(h, MV_T1, MV_CW, 3, 1.0);
-    launch_gram(h, MV_T1, MV_CW, GM_G3);
-    CK_LAUNCH();
-    std::vector<int> act_now(act);
-    all_done = true;
-    for (int j = 0; j < h->N; ++j) {
-      if (!act[j]) continue;
-      h->iters[j] = it + 1;
-      CK(cudaMemcpyAsync(&theta[(size_t)j * PST], h->sub[j].theta, PST * sizeof(double), cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(&gdiag[(size_t)j * PST * PST], h->sub[j].G3, PST * PST * sizeof(double),
-                         cudaMemcpyDeviceToHost, st));
-    }
-    CK(cudaStreamSynchronize(st));
-    for (int j = 0; j < h->N; ++j) {
-      if (!act[j]) continue;
-      const int nw = n_loc - (h->sub[j].floating ? 6 : 0);
-      double dmax = 0.0;
-      for (int c = 0; c < nw; ++c)
-        dmax = std::max(dmax, std::sqrt(std::fabs(gdiag[(size_t)j * PST * PST + (size_t)c * PST + c])));
-      // converged, or stalled at the rounding floor of the solves (less than 10 %
-      // decrease over three iterations while already below 100 tol)
-      bool done = dmax <= h->opt.tol;
-      auto& hist = dhist[j];
-      hist.push_back(dmax);
-      if (!done && hist.size() >= 4 && dmax <= 1e2 * h->opt.tol && dmax > 0.9 * hist[hist.size() - 4]) done = true;
-      if (done) act_now[j] = 0;
-      else all_done = false;
-    }
-    if (all_done || it + 1 == h->opt.max_iter) break;
-    // continue with the new block on subdomains not yet converged
-    TRY(set_active(h, act_now));
-    launch_copy_mv(h, MV_W, MV_PHI);
-    act = act_now;
+  if (h->opt.solver == 1) {
+    TRY(run_subspace(h, n_loc, p, all_done));
+  } else {
+    h->m_final.assign(h->N, 0);
+    TRY(run_krylov(h, n_loc, all_done));
   }
+  std::vector<double> theta((size_t)h->N * PST);
   TRY(set_active(h, std::vector<int>(h->N, 1)));
   // 4. final residuals: S x = (K Phi)|B2, T x = -(K y~)|B2 with y~ = A11^{-1} Z|B1
   for (auto& s : h->sub) CK(cudaMemsetAsync(s.T1, 0, (size_t)s.nfull * PST * sizeof(double), st));

@@ -22,6 +22,8 @@
 
 #define TILE 64
 #define PST 32
+#define KB 8      // block width of the block Krylov eigensolver
+#define MQ 96     // largest Krylov basis (12 blocks)
 
 // Tile GEMM task: C(64x64) = [C +] sign * [P *] A(64 x K) * op(B)
 enum { G_TRANSB = 1, G_ACC = 2, G_NEG = 4, G_POSTMUL = 8 };
@@ -53,7 +55,8 @@ struct SolveTask {
 };
 
 // multivector selectors
-enum { MV_PHI = 0, MV_Z, MV_KPHI, MV_W, MV_T1, MV_R, MV_BR, MV_EV, MV_CB, MV_CW };
+enum { MV_PHI = 0, MV_Z, MV_KPHI, MV_W, MV_T1, MV_R, MV_BR, MV_EV, MV_CB, MV_CW,
+       MV_QB, MV_ZB, MV_WB, MV_TB };   // QB: [nfull][MQ]; ZB, WB, TB: [nfull][KB]
 enum { GM_G1 = 0, GM_G2, GM_G3, GM_Y };
 
 // Device-visible per-subdomain descriptor.
@@ -82,6 +85,14 @@ struct SubDev {
   double* theta;               // [PST]
   double* resid;               // [PST]
   int* status;                 // [4]: 1 RR pencil degenerate, 2 kept basis columns
+  // block Krylov eigensolver
+  double* QB;                  // [nfull][MQ] T-orthonormal basis (A-harmonic vectors)
+  double* Zb; double* Wb; double* Tb;   // [nfull][KB] working blocks
+  double* ycK8; double* ycA8;  // [nzn][b][KB] compact solve buffers
+  double* rcK8; double* rcA8;  // [b][KB]
+  double* H;                   // [MQ + KB][MQ] projected operator Q^T T M Q and R_{m+1}
+  double* Hc;                  // [MQ][KB] block inner products
+  double* Yk;                  // [MQ][PST] Ritz coefficients of the wanted pairs
 };
 
 struct Schedule {
@@ -121,7 +132,7 @@ struct msgfem {
   std::vector<double> h_angles;
   std::vector<SubDev> sub;
   std::vector<HostSub> hsub;
-  std::vector<int> n1, n2, n3, iters, basis_m;
+  std::vector<int> n1, n2, n3, iters, basis_m, m_final;
   std::vector<double> resid_max;
   std::vector<void*> allocs;
   SubDev* d_sub = nullptr;
@@ -132,8 +143,11 @@ struct msgfem {
   int* d_flags = nullptr;            // [N + 1] active flags (entry N: coarse, always 1)
   int* d_notspd = nullptr;           // [N + 1]
   int* d_ncols = nullptr;            // [N]
+  int* d_mk = nullptr;               // [N] Krylov basis size at the last Rayleigh-Ritz
+  int* d_nwk = nullptr;              // [N] wanted Ritz pairs
   Schedule fact;
-  SolveSchedule solveK, solveA;
+  SolveSchedule solveK, solveA;     // PST columns
+  SolveSchedule solveK8, solveA8;   // KB columns
   std::vector<CoarsePair> pairs;
   CoarsePair* d_pairs = nullptr;
   double* d_pair_part = nullptr;
@@ -175,7 +189,7 @@ void build_coarse_schedules(msgfem* h);
 // launchers
 void set_dense_context(int* active, int* notspd, const SubDev* subs);
 void run_schedule(const Schedule& s, cudaStream_t st);
-void run_solve_mv(const SolveSchedule& s, cudaStream_t st, int src, int dst, int gather_neg);
+void run_solve_mv(const SolveSchedule& s, cudaStream_t st, int src, int dst, int gather_neg, int width = PST);
 void launch_element_stiffness(msgfem* h);
 void launch_stencil(msgfem* h);
 void launch_layer_blocks(msgfem* h);
@@ -216,8 +230,15 @@ __device__ __forceinline__ double* mv_ptr(const SubDev& s, int which) {
     case MV_BR: return s.BR;
     case MV_EV: return s.EV;
     case MV_CB: return s.CB;
-    default: return s.CW;
+    case MV_CW: return s.CW;
+    case MV_QB: return s.QB;
+    case MV_ZB: return s.Zb;
+    case MV_WB: return s.Wb;
+    default: return s.Tb;
   }
+}
+__device__ __forceinline__ int mv_stride(int which) {
+  return which == MV_QB ? MQ : (which >= MV_ZB ? KB : PST);
 }
 __device__ __forceinline__ double* gm_ptr(const SubDev& s, int which) {
   switch (which) {

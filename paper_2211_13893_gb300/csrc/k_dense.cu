@@ -156,19 +156,28 @@ k_tile_potrf_inv(const PotrfTask* __restrict__ tasks, const int* __restrict__ ac
   if (tid == 0 && bad && notspd != nullptr) atomicExch(&notspd[t.sub >= 0 ? t.sub : 0], 1);
 }
 
-// One step of a block triangular solve: C(64 x PST) = init + sign op(A) B.
+// One step of a block triangular solve: C(64 x PC) = init + sign op(A) B,
+// with PC right-hand sides (compact buffers and full-layout multivectors both
+// have row stride PC).
 constexpr int SKC = 32;
+template <int PC>
 __global__ void __launch_bounds__(256)
 k_solve_step(const SolveTask* __restrict__ tasks, const SubDev* __restrict__ subs,
              const int* __restrict__ active, int src, int dst, int gather_neg) {
+  constexpr int TXN = PC < 16 ? PC : 16;   // threads along columns
+  constexpr int CPT = PC / TXN;            // columns per thread
+  constexpr int TYN = 256 / TXN;           // threads along rows
+  constexpr int RPT = 64 / TYN;            // rows per thread
   const SolveTask t = tasks[blockIdx.x];
   if (t.sub >= 0 && active != nullptr && !active[t.sub]) return;
   __shared__ double As[SKC][65];
-  __shared__ double Bs[SKC][PST + 1];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[4][2];
+  __shared__ double Bs[SKC][PC + 1];
+  const int tid = threadIdx.x, tx = tid % TXN, ty = tid / TXN;
+  double acc[RPT][CPT];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = 0.0;
+  for (int i = 0; i < RPT; ++i)
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) acc[i][j] = 0.0;
   const bool transA = (t.flags & S_TRANSA) != 0;
   for (int k0 = 0; k0 < t.K; k0 += SKC) {
     if (!transA) {
@@ -182,24 +191,19 @@ k_solve_step(const SolveTask* __restrict__ tasks, const SubDev* __restrict__ sub
 #pragma unroll
       for (int i = 0; i < 8; ++i) As[k][m + i] = a[i];
     }
-    {
-      const int k = tid >> 3, c = (tid & 7) * 4;
-      const double* b = t.B + (size_t)(k0 + k) * PST + c;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) Bs[k][c + i] = b[i];
-    }
+    for (int e = tid; e < SKC * PC; e += 256) Bs[e / PC][e % PC] = t.B[(size_t)(k0 + e / PC) * PC + e % PC];
     __syncthreads();
 #pragma unroll 8
     for (int kk = 0; kk < SKC; ++kk) {
-      double a[4];
+      double a[RPT], b[CPT];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
-      const double b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+      for (int i = 0; i < RPT; ++i) a[i] = As[kk][ty + TYN * i];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        acc[i][0] = fma(a[i], b0, acc[i][0]);
-        acc[i][1] = fma(a[i], b1, acc[i][1]);
-      }
+      for (int j = 0; j < CPT; ++j) b[j] = Bs[kk][tx + TXN * j];
+#pragma unroll
+      for (int i = 0; i < RPT; ++i)
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
@@ -208,23 +212,23 @@ k_solve_step(const SolveTask* __restrict__ tasks, const SubDev* __restrict__ sub
   double* sfull = nullptr;
   if (t.flags & (S_INIT_GATHER | S_SCATTER)) {
     const SubDev& s = subs[t.sub];
-    if (t.flags & S_INIT_GATHER) gfull = mv_ptr(s, src) + (size_t)t.row_off * PST;
-    if (t.flags & S_SCATTER) sfull = mv_ptr(s, dst) + (size_t)t.row_off * PST;
+    if (t.flags & S_INIT_GATHER) gfull = mv_ptr(s, src) + (size_t)t.row_off * PC;
+    if (t.flags & S_SCATTER) sfull = mv_ptr(s, dst) + (size_t)t.row_off * PC;
   }
   const double gs = gather_neg ? -1.0 : 1.0;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = ty + 16 * i;
-    const int gm = (t.flags & S_INIT_GATHER) ? t.gmap[r] : -1;
-    const int sm = (t.flags & S_SCATTER) ? t.smap[r] : -1;
+  for (int i = 0; i < RPT; ++i) {
+    const int r = ty + TYN * i;
+    const int gmr = (t.flags & S_INIT_GATHER) ? t.gmap[r] : -1;
+    const int smr = (t.flags & S_SCATTER) ? t.smap[r] : -1;
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int c = tx + 16 * j;
+    for (int j = 0; j < CPT; ++j) {
+      const int c = tx + TXN * j;
       double v = sgn * acc[i][j];
-      if (t.flags & S_INIT_TILE) v += t.init[r * PST + c];
-      if (gm >= 0) v += gs * gfull[(size_t)gm * PST + c];
-      t.C[r * PST + c] = v;
-      if (sm >= 0) sfull[(size_t)sm * PST + c] = v;
+      if (t.flags & S_INIT_TILE) v += t.init[r * PC + c];
+      if (gmr >= 0) v += gs * gfull[(size_t)gmr * PC + c];
+      t.C[r * PC + c] = v;
+      if (smr >= 0) sfull[(size_t)smr * PC + c] = v;
     }
   }
 }
@@ -254,9 +258,13 @@ void run_schedule(const Schedule& s, cudaStream_t st) {
   }
 }
 
-void run_solve_mv(const SolveSchedule& s, cudaStream_t st, int src, int dst, int gather_neg) {
+void run_solve_mv(const SolveSchedule& s, cudaStream_t st, int src, int dst, int gather_neg, int width) {
   for (const auto& step : s.steps) {
     if (step.count == 0) continue;
-    k_solve_step<<<step.count, 256, 0, st>>>(s.d_tasks + step.first, g_subs, g_active, src, dst, gather_neg); ++g_launch_count;
+    if (width == KB)
+      k_solve_step<KB><<<step.count, 256, 0, st>>>(s.d_tasks + step.first, g_subs, g_active, src, dst, gather_neg);
+    else
+      k_solve_step<PST><<<step.count, 256, 0, st>>>(s.d_tasks + step.first, g_subs, g_active, src, dst, gather_neg);
+    ++g_launch_count;
   }
 }

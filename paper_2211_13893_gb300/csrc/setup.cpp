@@ -252,6 +252,7 @@ void flatten(FactorKeys& fk, Schedule& sch) {
     if (kv.second == 0) {
       auto& v = fk.gemm[kv.first];
       if (v.empty()) continue;
+      std::stable_sort(v.begin(), v.end(), [](const GemmTask& x, const GemmTask& y) { return x.K > y.K; });
       sch.steps.push_back({0, (int)sch.gemm.size(), (int)v.size()});
       sch.gemm.insert(sch.gemm.end(), v.begin(), v.end());
     } else {
@@ -265,27 +266,27 @@ void flatten(FactorKeys& fk, Schedule& sch) {
 
 // Solve schedule of one matrix kind over all subdomains.
 void add_solve_tasks(std::map<long long, std::vector<SolveTask>>& keys, double* E, double* L, double* yc, double* rc,
-                     const int* map, int b, int nL, int npl, int sub) {
+                     const int* map, int b, int nL, int npl, int sub, int PW) {
   const int T = b / TILE;
   for (int l = 0; l < nL; ++l) {
     const int row_off = l * 3 * npl;
     for (int i = 0; i < T; ++i) {
       SolveTask f1{};
-      f1.C = rc + (size_t)i * TILE * PST;
+      f1.C = rc + (size_t)i * TILE * PW;
       f1.gmap = map + i * TILE;
       f1.row_off = row_off;
       f1.sub = sub;
       f1.flags = S_INIT_GATHER;
       if (l > 0) {
         f1.A = E + (size_t)(l - 1) * b * b + (size_t)i * TILE * b;
-        f1.B = yc + (size_t)(l - 1) * b * PST;
+        f1.B = yc + (size_t)(l - 1) * b * PW;
         f1.lda = b;
         f1.K = b;
         f1.flags |= S_NEG;
       }
       keys[2LL * l].push_back(f1);
       SolveTask f2{};
-      f2.C = yc + (size_t)l * b * PST + (size_t)i * TILE * PST;
+      f2.C = yc + (size_t)l * b * PW + (size_t)i * TILE * PW;
       f2.A = L + (size_t)l * b * b + (size_t)i * TILE * b;
       f2.B = rc;
       f2.lda = b;
@@ -299,22 +300,22 @@ void add_solve_tasks(std::map<long long, std::vector<SolveTask>>& keys, double* 
     const int row_off = l * 3 * npl;
     for (int i = 0; i < T; ++i) {
       SolveTask b1{};
-      b1.C = rc + (size_t)i * TILE * PST;
-      b1.init = yc + (size_t)l * b * PST + (size_t)i * TILE * PST;
+      b1.C = rc + (size_t)i * TILE * PW;
+      b1.init = yc + (size_t)l * b * PW + (size_t)i * TILE * PW;
       b1.flags = S_INIT_TILE;
       b1.sub = sub;
       if (l + 1 < nL) {
         b1.A = E + (size_t)l * b * b + (size_t)i * TILE;
-        b1.B = yc + (size_t)(l + 1) * b * PST;
+        b1.B = yc + (size_t)(l + 1) * b * PW;
         b1.lda = b;
         b1.K = b;
         b1.flags |= S_TRANSA | S_NEG;
       }
       keys[kb].push_back(b1);
       SolveTask b2{};
-      b2.C = yc + (size_t)l * b * PST + (size_t)i * TILE * PST;
+      b2.C = yc + (size_t)l * b * PW + (size_t)i * TILE * PW;
       b2.A = L + (size_t)l * b * b + (size_t)i * TILE * b + (size_t)i * TILE;
-      b2.B = rc + (size_t)i * TILE * PST;
+      b2.B = rc + (size_t)i * TILE * PW;
       b2.lda = b;
       b2.K = b - i * TILE;
       b2.flags = S_TRANSA | S_SCATTER;
@@ -331,6 +332,9 @@ void flatten_solve(std::map<long long, std::vector<SolveTask>>& keys, SolveSched
   sch.tasks.clear();
   for (auto& kv : keys) {
     if (kv.second.empty()) continue;
+    // longest tasks first: CTAs are dispatched in launch order (LPT balance)
+    std::stable_sort(kv.second.begin(), kv.second.end(),
+                     [](const SolveTask& x, const SolveTask& y) { return x.K > y.K; });
     sch.steps.push_back({(int)sch.tasks.size(), (int)kv.second.size()});
     sch.tasks.insert(sch.tasks.end(), kv.second.begin(), kv.second.end());
   }
@@ -351,14 +355,18 @@ void build_factor_schedule(msgfem* h) {
 }
 
 void build_solve_schedules(msgfem* h) {
-  std::map<long long, std::vector<SolveTask>> kk, ka;
+  std::map<long long, std::vector<SolveTask>> kk, ka, kk8, ka8;
   for (int j = 0; j < h->N; ++j) {
     SubDev& s = h->sub[j];
-    add_solve_tasks(kk, s.EK, s.LK, s.ycK, s.rcK, s.mapK, s.bK, s.nzn, s.npl, j);
-    add_solve_tasks(ka, s.EA, s.LA, s.ycA, s.rcA, s.mapA, s.bA, s.nzn, s.npl, j);
+    add_solve_tasks(kk, s.EK, s.LK, s.ycK, s.rcK, s.mapK, s.bK, s.nzn, s.npl, j, PST);
+    add_solve_tasks(ka, s.EA, s.LA, s.ycA, s.rcA, s.mapA, s.bA, s.nzn, s.npl, j, PST);
+    add_solve_tasks(kk8, s.EK, s.LK, s.ycK8, s.rcK8, s.mapK, s.bK, s.nzn, s.npl, j, KB);
+    add_solve_tasks(ka8, s.EA, s.LA, s.ycA8, s.rcA8, s.mapA, s.bA, s.nzn, s.npl, j, KB);
   }
   flatten_solve(kk, h->solveK);
   flatten_solve(ka, h->solveA);
+  flatten_solve(kk8, h->solveK8);
+  flatten_solve(ka8, h->solveA8);
 }
 
 // Coarse matrix: one dense block of size NcPad, factorised by the same tile
