@@ -177,7 +177,8 @@ def run_ours(args):
     ang = element_angles(cfg).reshape(-1)
     ang_dev = torch.tensor(ang, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    m = MSGFEM.from_config(cfg, ang_dev, seed=1234 + rank, stream=stream.cuda_stream, profile=1)
+    m = MSGFEM.from_config(cfg, ang_dev, seed=1234 + rank, stream=stream.cuda_stream, profile=1,
+                           streams=args.streams)
     lam_dev = torch.empty((m.N, cfg.n_loc), dtype=torch.float64, device=dev)
     u_dev = torch.empty(m.n_dof, dtype=torch.float64, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
@@ -294,6 +295,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=16, help="oracle subdomains per timed sample")
     ap.add_argument("--ref-warmup", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--streams", type=int, default=0, help="stream groups of the library (0 = its default)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -94,6 +94,7 @@ typedef struct {
   void* stream;         /* cudaStream_t to issue work on; NULL = default stream */
   int profile;          /* 1: time the phases with CUDA events (msgfem_get_profile) */
   int solver;           /* 0: block Krylov (block width 8, basis <= 96), 1: subspace iteration */
+  int streams;          /* independent task groups run on their own streams (1..16); 0 = 16 */
 } msgfem_options;
 
 /* Phase timers (CUDA events on the handle's stream, milliseconds, summed over

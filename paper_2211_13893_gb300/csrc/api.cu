@@ -200,10 +200,7 @@ msgfem_status allocate(msgfem* h) {
   build_factor_schedule(h);
   build_solve_schedules(h);
   TRY(dalloc(h, &h->fact.d_gemm, h->fact.gemm.size()));
-  TRY(dalloc(h, &h->fact.d_potrf, h->fact.potrf.size()));
   CK(cudaMemcpy(h->fact.d_gemm, h->fact.gemm.data(), h->fact.gemm.size() * sizeof(GemmTask), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(h->fact.d_potrf, h->fact.potrf.data(), h->fact.potrf.size() * sizeof(PotrfTask),
-                cudaMemcpyHostToDevice));
   TRY(dalloc(h, &h->d_mk, h->N));
   TRY(dalloc(h, &h->d_nwk, h->N));
   for (SolveSchedule* ss : {&h->solveK, &h->solveA, &h->solveK8, &h->solveA8}) {
@@ -290,7 +287,7 @@ double solve_flops(const msgfem* h, int mat, int p) {
 
 void timed_solve(msgfem* h, int mat, int src, int dst, int neg) {
   const int sp = span_begin(h, TAG_SOLVE);
-  run_solve_mv(mat == 0 ? h->solveK : h->solveA, h->stream, src, dst, neg);
+  run_solve_mv(mat == 0 ? h->solveK : h->solveA, h->stream, src, dst, neg, PST, &h->gs);
   span_end(h, sp);
   h->prof.solve_flops += solve_flops(h, mat, h->p);
   h->prof.solve_calls += 1;
@@ -298,7 +295,7 @@ void timed_solve(msgfem* h, int mat, int src, int dst, int neg) {
 
 void timed_solve8(msgfem* h, int mat, int src, int dst, int neg) {
   const int sp = span_begin(h, TAG_SOLVE);
-  run_solve_mv(mat == 0 ? h->solveK8 : h->solveA8, h->stream, src, dst, neg, KB);
+  run_solve_mv(mat == 0 ? h->solveK8 : h->solveA8, h->stream, src, dst, neg, KB, &h->gs);
   span_end(h, sp);
   h->prof.solve_flops += solve_flops(h, mat, KB);
   h->prof.solve_calls += 1;
@@ -537,6 +534,7 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
   if (h->opt.max_iter <= 0) h->opt.max_iter = 100;
   if (!(h->opt.tol > 0)) h->opt.tol = 1e-7;
   h->stream = static_cast<cudaStream_t>(h->opt.stream);
+  h->ngroup = h->opt.streams > 0 ? std::min(h->opt.streams, NGROUP) : NGROUP;
   *out = h;
   msgfem_status st = build_problem(h);
   if (st != MSGFEM_OK) return st;
@@ -544,6 +542,11 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
   if (st != MSGFEM_OK) return st;
   st = set_angles(h, plies->elem_angle_deg);
   if (st != MSGFEM_OK) return st;
+  for (int g = 0; g < h->ngroup; ++g) {
+    CK(cudaStreamCreateWithFlags(&h->gs.s[g], cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->gs.join[g], cudaEventDisableTiming));
+  }
+  CK(cudaEventCreateWithFlags(&h->gs.fork, cudaEventDisableTiming));
   set_dense_context(h->d_flags, h->d_notspd, h->d_sub);
   h->stage = 1;
   return MSGFEM_OK;
@@ -588,7 +591,7 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   CK_LAUNCH();
   // 2. factorisations of K and A11
   sp = span_begin(h, TAG_FACTOR);
-  run_schedule(h->fact, st);
+  run_schedule(h->fact, st, &h->gs);
   span_end(h, sp);
   CK_LAUNCH();
   const int sp_iter = span_begin(h, TAG_ITERATE);
@@ -717,10 +720,7 @@ msgfem_status msgfem_coarse_assemble(msgfem_h h, int* coarse_dim_out) {
     TRY(dalloc(h, &h->d_rH, (size_t)NcPad * PST));
     build_coarse_schedules(h);
     TRY(dalloc(h, &h->cfact.d_gemm, h->cfact.gemm.size()));
-    TRY(dalloc(h, &h->cfact.d_potrf, h->cfact.potrf.size()));
     CK(cudaMemcpy(h->cfact.d_gemm, h->cfact.gemm.data(), h->cfact.gemm.size() * sizeof(GemmTask),
-                  cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(h->cfact.d_potrf, h->cfact.potrf.data(), h->cfact.potrf.size() * sizeof(PotrfTask),
                   cudaMemcpyHostToDevice));
     TRY(dalloc(h, &h->csolve.d_tasks, h->csolve.tasks.size()));
     CK(cudaMemcpy(h->csolve.d_tasks, h->csolve.tasks.data(), h->csolve.tasks.size() * sizeof(SolveTask),
@@ -845,6 +845,11 @@ void msgfem_destroy(msgfem_h h) {
   else cudaDeviceSynchronize();
   for (void* p : h->allocs) cudaFree(p);
   for (auto& sp : h->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
+  for (int g = 0; g < NGROUP; ++g) {
+    if (h->gs.s[g]) cudaStreamDestroy(h->gs.s[g]);
+    if (h->gs.join[g]) cudaEventDestroy(h->gs.join[g]);
+  }
+  if (h->gs.fork) cudaEventDestroy(h->gs.fork);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
 }

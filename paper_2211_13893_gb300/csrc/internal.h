@@ -25,8 +25,10 @@
 #define KB 8      // block width of the block Krylov eigensolver
 #define MQ 96     // largest Krylov basis (12 blocks)
 
-// Tile GEMM task: C(64x64) = [C +] sign * [P *] A(64 x K) * op(B)
-enum { G_TRANSB = 1, G_ACC = 2, G_NEG = 4, G_POSTMUL = 8 };
+// Tile task: C(64x64) = [C +] sign * [P *] A(64 x K) * op(B), or with
+// G_POTRF the Cholesky factor and inverse of the SPD tile C (in place) with the
+// inverse written to P.
+enum { G_TRANSB = 1, G_ACC = 2, G_NEG = 4, G_POSTMUL = 8, G_POTRF = 16 };
 struct GemmTask {
   const double* A;
   const double* B;
@@ -36,11 +38,6 @@ struct GemmTask {
   int flags, sub;
 };
 
-struct PotrfTask {
-  double* D;   // 64x64 diagonal tile, in place -> L
-  double* Li;  // 64x64 output tile -> L^{-1}
-  int ld, sub;
-};
 
 // Solve step: C(64 x PST) = init + sign * op(A) * B
 enum { S_TRANSA = 1, S_NEG = 2, S_INIT_GATHER = 4, S_INIT_TILE = 8, S_SCATTER = 16 };
@@ -95,20 +92,27 @@ struct SubDev {
   double* Yk;                  // [MQ][PST] Ritz coefficients of the wanted pairs
 };
 
+// A schedule is a set of independent groups (each a sequence of steps, run on
+// its own stream); steps[g] lists the launches of group g in order.
+#define NGROUP 16   // most stream groups a schedule may use
 struct Schedule {
-  struct Step { int kind, first, count; };   // kind 0 gemm, 1 potrf
-  std::vector<Step> steps;
+  struct Step { int first, count; };
+  std::vector<std::vector<Step>> steps;
   std::vector<GemmTask> gemm;
-  std::vector<PotrfTask> potrf;
   GemmTask* d_gemm = nullptr;
-  PotrfTask* d_potrf = nullptr;
 };
 
 struct SolveSchedule {
   struct Step { int first, count; };
-  std::vector<Step> steps;
+  std::vector<std::vector<Step>> steps;
   std::vector<SolveTask> tasks;
   SolveTask* d_tasks = nullptr;
+};
+
+// Fork/join of the group streams around a schedule run.
+struct StreamSet {
+  cudaStream_t s[NGROUP] = {};
+  cudaEvent_t fork = nullptr, join[NGROUP] = {};
 };
 
 struct CoarsePair { int s, t, x0, x1, y0, y1; };   // (i, j) node box of Omega_s cap Omega*_t
@@ -127,6 +131,8 @@ struct msgfem {
   int sx = 0, sy = 0, o = 0, os = 0;
   msgfem_options opt;
   cudaStream_t stream = nullptr;
+  StreamSet gs;                      // streams of independent schedule groups
+  int ngroup = NGROUP;               // groups in use (msgfem_options.streams)
   int N = 0;
   int layered = 0, ntypes = 0, type_cap = 0;
   std::vector<double> h_angles;
@@ -188,8 +194,9 @@ void build_coarse_schedules(msgfem* h);
 
 // launchers
 void set_dense_context(int* active, int* notspd, const SubDev* subs);
-void run_schedule(const Schedule& s, cudaStream_t st);
-void run_solve_mv(const SolveSchedule& s, cudaStream_t st, int src, int dst, int gather_neg, int width = PST);
+void run_schedule(const Schedule& s, cudaStream_t st, const StreamSet* gs = nullptr);
+void run_solve_mv(const SolveSchedule& s, cudaStream_t st, int src, int dst, int gather_neg, int width = PST,
+                  const StreamSet* gs = nullptr);
 void launch_element_stiffness(msgfem* h);
 void launch_stencil(msgfem* h);
 void launch_layer_blocks(msgfem* h);

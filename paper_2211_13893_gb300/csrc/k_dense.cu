@@ -9,7 +9,9 @@
 //   TRMM    L_ik = D_ik Li_kk^T   (panel below, and the E_l panel)
 //   UPDATE  D_ij -= L_ik L_jk^T   (trailing tiles of the panel)
 //   TRTRI   Linv_ik = -Li_ii sum_m L_im Linv_mk             (block inverse)
-// FP64 arithmetic on this part runs at ~2 DFMA/clk/SM, so every kernel is
+// POTRF and GEMM tasks share one kernel, so independent work of different
+// phases (the block inverse of layer l and the factorisation of layer l + 1)
+// can fill the same launch.  FP64 arithmetic on this part runs at ~2 DFMA/clk/SM, so every kernel is
 // bound by the FP64 pipe; the tile kernels only need enough independent
 // tasks in flight to occupy all SMs.
 #include "internal.h"
@@ -17,12 +19,71 @@
 namespace {
 
 constexpr int KC = 16;   // K chunk of the tile GEMM
+constexpr int TILE_SMEM = 2 * 64 * 65 * (int)sizeof(double);   // dynamic shared memory per CTA
 
+// Cholesky and inverse of one 64x64 SPD tile in shared memory.  L occupies
+// the lower triangle of A; X = L^{-1} is kept transposed in the strict upper
+// triangle shifted by one column (X[i][c] at A[c][i + 1], using the pad column).
+__device__ void tile_potrf_inv(const GemmTask& t, double (*A)[65], int* notspd) {
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = 0;
+  for (int e = tid; e < 64 * 64; e += 256) {
+    const int r = e >> 6, c = e & 63;
+    A[r][c] = (c <= r) ? t.C[(size_t)r * t.ldc + c] : 0.0;
+  }
+  if (tid < 64) A[tid][64] = 0.0;
+  __syncthreads();
+  for (int j = 0; j < 64; ++j) {
+    if (tid == 0) {
+      double d = A[j][j];
+      if (!(d > 0.0)) { bad = 1; d = 1e-300; }
+      A[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    const double djj = A[j][j];
+    for (int i = j + 1 + tid; i < 64; i += 256) A[i][j] /= djj;
+    __syncthreads();
+    const int n = 63 - j;
+    for (int e = tid; e < n * n; e += 256) {
+      const int ii = j + 1 + e / n, kk = j + 1 + e % n;
+      if (kk <= ii) A[ii][kk] = fma(-A[ii][j], A[kk][j], A[ii][kk]);
+    }
+    __syncthreads();
+  }
+  // X = L^{-1} row by row: X[i][c] = -(sum_{m=c}^{i-1} L[i][m] X[m][c]) / L[i][i]
+  for (int i = 0; i < 64; ++i) {
+    for (int c = tid; c <= i; c += 256) {
+      if (c == i) {
+        A[i][i + 1] = 1.0 / A[i][i];
+      } else {
+        double s = 0.0;
+        for (int m = c; m < i; ++m) s = fma(A[i][m], A[c][m + 1], s);
+        A[c][i + 1] = -s / A[i][i];
+      }
+    }
+    __syncthreads();
+  }
+  double* Li = const_cast<double*>(t.P);
+  for (int e = tid; e < 64 * 64; e += 256) {
+    const int r = e >> 6, c = e & 63;
+    t.C[(size_t)r * t.ldc + c] = (c <= r) ? A[r][c] : 0.0;
+    Li[(size_t)r * t.ldc + c] = (c <= r) ? A[c][r + 1] : 0.0;
+  }
+  if (tid == 0 && bad && notspd != nullptr) atomicExch(&notspd[t.sub >= 0 ? t.sub : 0], 1);
+}
+
+// One tile task per CTA: a 64x64 GEMM tile (4x4 outputs per thread, operands
+// staged through shared memory in K chunks of 16) or a tile POTRF.
 __global__ void __launch_bounds__(256)
-k_tile_gemm(const GemmTask* __restrict__ tasks, const int* __restrict__ active) {
+k_tile_task(const GemmTask* __restrict__ tasks, const int* __restrict__ active, int* __restrict__ notspd) {
   const GemmTask t = tasks[blockIdx.x];
   if (t.sub >= 0 && active != nullptr && !active[t.sub]) return;
-  __shared__ double smem[64 * 65];
+  extern __shared__ double smem[];
+  if (t.flags & G_POTRF) {
+    tile_potrf_inv(t, reinterpret_cast<double (*)[65]>(smem), notspd);
+    return;
+  }
   double (*As)[65] = reinterpret_cast<double (*)[65]>(smem);                 // [KC][65]: As[k][m]
   double (*Bs)[65] = reinterpret_cast<double (*)[65]>(smem + KC * 65);      // [KC][65]: Bs[k][n]
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -66,12 +127,14 @@ k_tile_gemm(const GemmTask* __restrict__ tasks, const int* __restrict__ active) 
     __syncthreads();
   }
   if (t.flags & G_POSTMUL) {
-    // C = P * (A op(B)) with the 64x64 product staged in shared memory
+    // C = P * (A op(B)): product and P both staged in shared memory
     double (*Cs)[65] = reinterpret_cast<double (*)[65]>(smem);
+    double (*Ps)[65] = reinterpret_cast<double (*)[65]>(smem + 64 * 65);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) Cs[ty + 16 * i][tx + 16 * j] = acc[i][j];
+    for (int e = tid; e < 64 * 64; e += 256) Ps[e >> 6][e & 63] = t.P[(size_t)(e >> 6) * t.ldc + (e & 63)];
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -83,9 +146,9 @@ k_tile_gemm(const GemmTask* __restrict__ tasks, const int* __restrict__ active) 
       for (int j = 0; j < 4; ++j) b[j] = Cs[m][tx + 16 * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const double p = t.P[(size_t)(ty + 16 * i) * t.ldc + m];
+        const double pv = Ps[ty + 16 * i][m];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(p, b[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(pv, b[j], acc[i][j]);
       }
     }
   }
@@ -98,62 +161,6 @@ k_tile_gemm(const GemmTask* __restrict__ tasks, const int* __restrict__ active) 
       const double v = sgn * acc[i][j];
       *c = (t.flags & G_ACC) ? *c + v : v;
     }
-}
-
-// Cholesky and inverse of one 64x64 SPD tile in shared memory.  L occupies
-// the lower triangle of A; X = L^{-1} is kept transposed in the strict upper
-// triangle shifted by one column (X[i][c] at A[c][i + 1], using the pad column).
-__global__ void __launch_bounds__(256)
-k_tile_potrf_inv(const PotrfTask* __restrict__ tasks, const int* __restrict__ active,
-                 int* __restrict__ notspd) {
-  const PotrfTask t = tasks[blockIdx.x];
-  if (t.sub >= 0 && active != nullptr && !active[t.sub]) return;
-  __shared__ double A[64][65];
-  __shared__ int bad;
-  const int tid = threadIdx.x;
-  if (tid == 0) bad = 0;
-  for (int e = tid; e < 64 * 64; e += 256) {
-    const int r = e >> 6, c = e & 63;
-    A[r][c] = (c <= r) ? t.D[(size_t)r * t.ld + c] : 0.0;
-  }
-  if (tid < 64) A[tid][64] = 0.0;
-  __syncthreads();
-  for (int j = 0; j < 64; ++j) {
-    if (tid == 0) {
-      double d = A[j][j];
-      if (!(d > 0.0)) { bad = 1; d = 1e-300; }
-      A[j][j] = sqrt(d);
-    }
-    __syncthreads();
-    const double djj = A[j][j];
-    for (int i = j + 1 + tid; i < 64; i += 256) A[i][j] /= djj;
-    __syncthreads();
-    const int n = 63 - j;
-    for (int e = tid; e < n * n; e += 256) {
-      const int ii = j + 1 + e / n, kk = j + 1 + e % n;
-      if (kk <= ii) A[ii][kk] = fma(-A[ii][j], A[kk][j], A[ii][kk]);
-    }
-    __syncthreads();
-  }
-  // X = L^{-1} row by row: X[i][c] = -(sum_{m=c}^{i-1} L[i][m] X[m][c]) / L[i][i]
-  for (int i = 0; i < 64; ++i) {
-    for (int c = tid; c <= i; c += 256) {
-      if (c == i) {
-        A[i][i + 1] = 1.0 / A[i][i];
-      } else {
-        double s = 0.0;
-        for (int m = c; m < i; ++m) s = fma(A[i][m], A[c][m + 1], s);
-        A[c][i + 1] = -s / A[i][i];
-      }
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < 64 * 64; e += 256) {
-    const int r = e >> 6, c = e & 63;
-    t.D[(size_t)r * t.ld + c] = (c <= r) ? A[r][c] : 0.0;
-    t.Li[(size_t)r * t.ld + c] = (c <= r) ? A[c][r + 1] : 0.0;
-  }
-  if (tid == 0 && bad && notspd != nullptr) atomicExch(&notspd[t.sub >= 0 ? t.sub : 0], 1);
 }
 
 // One step of a block triangular solve: C(64 x PC) = init + sign op(A) B,
@@ -247,24 +254,51 @@ void set_dense_context(int* active, int* notspd, const SubDev* subs) {
   g_subs = subs;
 }
 
-void run_schedule(const Schedule& s, cudaStream_t st) {
-  for (const auto& step : s.steps) {
-    if (step.count == 0) continue;
-    if (step.kind == 0)
-      k_tile_gemm<<<step.count, 256, 0, st>>>(s.d_gemm + step.first, g_active);
-    else
-      k_tile_potrf_inv<<<step.count, 256, 0, st>>>(s.d_potrf + step.first, g_active, g_notspd);
-    ++g_launch_count;
+// Launch the steps of all groups: group g on stream gs->s[g] (forked from and
+// joined back to st); without a stream set everything goes to st in order.
+template <typename Sched, typename Launch>
+static void run_groups(const Sched& s, cudaStream_t st, const StreamSet* gs, Launch launch) {
+  const int ng = (int)s.steps.size();
+  const bool multi = gs != nullptr && ng > 1;
+  if (multi) {
+    cudaEventRecord(gs->fork, st);
+    for (int g = 0; g < ng; ++g) cudaStreamWaitEvent(gs->s[g], gs->fork, 0);
+  }
+  size_t maxlen = 0;
+  for (const auto& v : s.steps) maxlen = std::max(maxlen, v.size());
+  for (size_t k = 0; k < maxlen; ++k)
+    for (int g = 0; g < ng; ++g) {
+      if (k >= s.steps[g].size() || s.steps[g][k].count == 0) continue;
+      launch(s.steps[g][k], multi ? gs->s[g] : st);
+      ++g_launch_count;
+    }
+  if (multi) {
+    for (int g = 0; g < ng; ++g) {
+      cudaEventRecord(gs->join[g], gs->s[g]);
+      cudaStreamWaitEvent(st, gs->join[g], 0);
+    }
   }
 }
 
-void run_solve_mv(const SolveSchedule& s, cudaStream_t st, int src, int dst, int gather_neg, int width) {
-  for (const auto& step : s.steps) {
-    if (step.count == 0) continue;
-    if (width == KB)
-      k_solve_step<KB><<<step.count, 256, 0, st>>>(s.d_tasks + step.first, g_subs, g_active, src, dst, gather_neg);
-    else
-      k_solve_step<PST><<<step.count, 256, 0, st>>>(s.d_tasks + step.first, g_subs, g_active, src, dst, gather_neg);
-    ++g_launch_count;
+void run_schedule(const Schedule& s, cudaStream_t st, const StreamSet* gs) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_tile_task, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
+    attr = true;
   }
+  run_groups(s, st, gs, [&](const Schedule::Step& step, cudaStream_t stream) {
+    k_tile_task<<<step.count, 256, TILE_SMEM, stream>>>(s.d_gemm + step.first, g_active, g_notspd);
+  });
+}
+
+void run_solve_mv(const SolveSchedule& s, cudaStream_t st, int src, int dst, int gather_neg, int width,
+                  const StreamSet* gs) {
+  run_groups(s, st, gs, [&](const SolveSchedule::Step& step, cudaStream_t stream) {
+    if (width == KB)
+      k_solve_step<KB><<<step.count, 256, 0, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
+                                                       gather_neg);
+    else
+      k_solve_step<PST><<<step.count, 256, 0, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
+                                                        gather_neg);
+  });
 }

@@ -191,37 +191,38 @@ msgfem_status build_problem(msgfem* h) {
 
 // ---------------------------------------------------------------------------
 // Factorisation schedule: per layer, SYRK; per tile column k: POTRF, TRMM,
-// UPDATE; then TRTRI rows 1..T-1.  Tasks of all subdomains (and of K and A11)
-// with the same key are launched together.
+// UPDATE.  The block inverse of layer l (TRTRI rows 1..T-1, each row depending
+// on the previous one) needs only L_l, so row i is issued together with the
+// (i-1)-th step of layer l + 1: it fills the SMs that the narrow POTRF and
+// TRMM steps leave idle.  Tasks of all subdomains (and of K and A11) with the
+// same key are launched together; within a step the longest tasks go first.
 namespace {
 
-struct FactorKeys {
-  std::map<long long, std::vector<GemmTask>> gemm;
-  std::map<long long, std::vector<PotrfTask>> potrf;
-};
+using FactorKeys = std::map<long long, std::vector<GemmTask>>;
 
-void add_matrix_tasks(FactorKeys& fk, double* D, double* E, double* L, int b, int nL, int sub, int Tmax) {
+void add_matrix_tasks(FactorKeys& fk, double* D, double* E, double* L, int b, int nL, int sub, int Tmax,
+                      long long skew = 0) {
   const int T = b / TILE;
-  const long long per_layer = 4LL * Tmax;
+  const long long per_layer = 3LL * Tmax + 1;
   auto tileD = [&](int l, int i, int j) { return D + (size_t)l * b * b + (size_t)i * TILE * b + (size_t)j * TILE; };
   auto tileE = [&](int l, int i, int j) { return E + (size_t)l * b * b + (size_t)i * TILE * b + (size_t)j * TILE; };
   auto tileL = [&](int l, int i, int j) { return L + (size_t)l * b * b + (size_t)i * TILE * b + (size_t)j * TILE; };
   for (int l = 0; l < nL; ++l) {
-    const long long base = l * per_layer;
+    const long long base = l * per_layer + skew;
     if (l > 0)
       for (int i = 0; i < T; ++i)
         for (int j = 0; j <= i; ++j)
-          fk.gemm[base].push_back({tileE(l - 1, i, 0), tileE(l - 1, j, 0), tileD(l, i, j), nullptr, b, b, b, b,
-                                   G_TRANSB | G_ACC | G_NEG, sub});
+          fk[base].push_back({tileE(l - 1, i, 0), tileE(l - 1, j, 0), tileD(l, i, j), nullptr, b, b, b, b,
+                              G_TRANSB | G_ACC | G_NEG, sub});
     for (int k = 0; k < T; ++k) {
-      fk.potrf[base + 1 + 3 * k].push_back({tileD(l, k, k), tileL(l, k, k), b, sub});
-      auto& trmm = fk.gemm[base + 2 + 3 * k];
+      fk[base + 1 + 3 * k].push_back({nullptr, nullptr, tileD(l, k, k), tileL(l, k, k), 0, 0, b, 0, G_POTRF, sub});
+      auto& trmm = fk[base + 2 + 3 * k];
       for (int i = k + 1; i < T; ++i)
         trmm.push_back({tileD(l, i, k), tileL(l, k, k), tileD(l, i, k), nullptr, b, b, b, TILE, G_TRANSB, sub});
       if (l + 1 < nL)
         for (int i = 0; i < T; ++i)
           trmm.push_back({tileE(l, i, k), tileL(l, k, k), tileE(l, i, k), nullptr, b, b, b, TILE, G_TRANSB, sub});
-      auto& upd = fk.gemm[base + 3 + 3 * k];
+      auto& upd = fk[base + 3 + 3 * k];
       for (int j = k + 1; j < T; ++j) {
         for (int i = j; i < T; ++i)
           upd.push_back({tileD(l, i, k), tileD(l, j, k), tileD(l, i, j), nullptr, b, b, b, TILE,
@@ -232,8 +233,10 @@ void add_matrix_tasks(FactorKeys& fk, double* D, double* E, double* L, int b, in
                            G_TRANSB | G_ACC | G_NEG, sub});
       }
     }
+    // block inverse rows, deferred into the steps of the next layer
+    const long long next = (l + 1) * per_layer + skew;
     for (int i = 1; i < T; ++i) {
-      auto& tr = fk.gemm[base + 1 + 3 * Tmax + (i - 1)];
+      auto& tr = fk[next + (i - 1)];
       for (int k = 0; k < i; ++k)
         tr.push_back({tileD(l, i, k), tileL(l, k, k), tileL(l, i, k), tileL(l, i, i), b, b, b, (i - k) * TILE,
                       G_POSTMUL | G_NEG, sub});
@@ -241,32 +244,29 @@ void add_matrix_tasks(FactorKeys& fk, double* D, double* E, double* L, int b, in
   }
 }
 
-void flatten(FactorKeys& fk, Schedule& sch) {
-  sch.steps.clear();
-  sch.gemm.clear();
-  sch.potrf.clear();
-  std::map<long long, int> kinds;
-  for (auto& kv : fk.gemm) kinds[kv.first] = 0;
-  for (auto& kv : fk.potrf) kinds[kv.first] = 1;
-  for (auto& kv : kinds) {
-    if (kv.second == 0) {
-      auto& v = fk.gemm[kv.first];
-      if (v.empty()) continue;
-      std::stable_sort(v.begin(), v.end(), [](const GemmTask& x, const GemmTask& y) { return x.K > y.K; });
-      sch.steps.push_back({0, (int)sch.gemm.size(), (int)v.size()});
-      sch.gemm.insert(sch.gemm.end(), v.begin(), v.end());
-    } else {
-      auto& v = fk.potrf[kv.first];
-      if (v.empty()) continue;
-      sch.steps.push_back({1, (int)sch.potrf.size(), (int)v.size()});
-      sch.potrf.insert(sch.potrf.end(), v.begin(), v.end());
-    }
+void flatten(FactorKeys& fk, Schedule& sch, bool append = false) {
+  if (!append) {
+    sch.steps.clear();
+    sch.gemm.clear();
+  }
+  sch.steps.emplace_back();
+  for (auto& kv : fk) {
+    auto& v = kv.second;
+    if (v.empty()) continue;
+    // POTRF tasks (short critical path) and then the longest GEMM tasks first
+    std::stable_sort(v.begin(), v.end(), [](const GemmTask& x, const GemmTask& y) {
+      const int px = (x.flags & G_POTRF) ? 1 : 0, py = (y.flags & G_POTRF) ? 1 : 0;
+      if (px != py) return px > py;
+      return x.K > y.K;
+    });
+    sch.steps.back().push_back({(int)sch.gemm.size(), (int)v.size()});
+    sch.gemm.insert(sch.gemm.end(), v.begin(), v.end());
   }
 }
 
 // Solve schedule of one matrix kind over all subdomains.
 void add_solve_tasks(std::map<long long, std::vector<SolveTask>>& keys, double* E, double* L, double* yc, double* rc,
-                     const int* map, int b, int nL, int npl, int sub, int PW) {
+                     const int* map, int b, int nL, int npl, int sub, int PW, long long skew = 0) {
   const int T = b / TILE;
   for (int l = 0; l < nL; ++l) {
     const int row_off = l * 3 * npl;
@@ -284,7 +284,7 @@ void add_solve_tasks(std::map<long long, std::vector<SolveTask>>& keys, double* 
         f1.K = b;
         f1.flags |= S_NEG;
       }
-      keys[2LL * l].push_back(f1);
+      keys[2LL * l + skew].push_back(f1);
       SolveTask f2{};
       f2.C = yc + (size_t)l * b * PW + (size_t)i * TILE * PW;
       f2.A = L + (size_t)l * b * b + (size_t)i * TILE * b;
@@ -292,11 +292,11 @@ void add_solve_tasks(std::map<long long, std::vector<SolveTask>>& keys, double* 
       f2.lda = b;
       f2.K = (i + 1) * TILE;
       f2.sub = sub;
-      keys[2LL * l + 1].push_back(f2);
+      keys[2LL * l + 1 + skew].push_back(f2);
     }
   }
   for (int l = nL - 1; l >= 0; --l) {
-    const long long kb = 2LL * nL + 2LL * (nL - 1 - l);
+    const long long kb = 2LL * nL + 1 + 2LL * (nL - 1 - l) + skew;
     const int row_off = l * 3 * npl;
     for (int i = 0; i < T; ++i) {
       SolveTask b1{};
@@ -327,46 +327,66 @@ void add_solve_tasks(std::map<long long, std::vector<SolveTask>>& keys, double* 
   }
 }
 
-void flatten_solve(std::map<long long, std::vector<SolveTask>>& keys, SolveSchedule& sch) {
-  sch.steps.clear();
-  sch.tasks.clear();
+void flatten_solve(std::map<long long, std::vector<SolveTask>>& keys, SolveSchedule& sch, bool append = false) {
+  if (!append) {
+    sch.steps.clear();
+    sch.tasks.clear();
+  }
+  sch.steps.emplace_back();
   for (auto& kv : keys) {
     if (kv.second.empty()) continue;
     // longest tasks first: CTAs are dispatched in launch order (LPT balance)
     std::stable_sort(kv.second.begin(), kv.second.end(),
                      [](const SolveTask& x, const SolveTask& y) { return x.K > y.K; });
-    sch.steps.push_back({(int)sch.tasks.size(), (int)kv.second.size()});
+    sch.steps.back().push_back({(int)sch.tasks.size(), (int)kv.second.size()});
     sch.tasks.insert(sch.tasks.end(), kv.second.begin(), kv.second.end());
   }
 }
 
 }  // namespace
 
+// The 2N factorisations are independent chains; they are dealt into NGROUP
+// groups, each launched on its own stream, so that a group's narrow steps
+// (POTRF, TRMM, late UPDATEs) overlap the wide steps of the others instead of
+// waiting at a common launch boundary.
 void build_factor_schedule(msgfem* h) {
-  FactorKeys fk;
   int Tmax = 1;
   for (const auto& s : h->sub) Tmax = std::max(Tmax, std::max(s.bK, s.bA) / TILE);
+  const int ng = h->ngroup;
+  std::vector<FactorKeys> fk(ng);
+  int chain = 0;
   for (int j = 0; j < h->N; ++j) {
     SubDev& s = h->sub[j];
-    add_matrix_tasks(fk, s.DK, s.EK, s.LK, s.bK, s.nzn, j, Tmax);
-    add_matrix_tasks(fk, s.DA, s.EA, s.LA, s.bA, s.nzn, j, Tmax);
+    add_matrix_tasks(fk[chain++ % ng], s.DK, s.EK, s.LK, s.bK, s.nzn, j, Tmax);
+    add_matrix_tasks(fk[chain++ % ng], s.DA, s.EA, s.LA, s.bA, s.nzn, j, Tmax);
   }
-  flatten(fk, h->fact);
+  h->fact.steps.clear();
+  h->fact.gemm.clear();
+  for (int g = 0; g < ng; ++g) flatten(fk[g], h->fact, true);
 }
 
 void build_solve_schedules(msgfem* h) {
-  std::map<long long, std::vector<SolveTask>> kk, ka, kk8, ka8;
+  // subdomains dealt into NGROUP groups (streams) as well
+  const int ng = h->ngroup;
+  std::vector<std::map<long long, std::vector<SolveTask>>> kk(ng), ka(ng), kk8(ng), ka8(ng);
   for (int j = 0; j < h->N; ++j) {
     SubDev& s = h->sub[j];
-    add_solve_tasks(kk, s.EK, s.LK, s.ycK, s.rcK, s.mapK, s.bK, s.nzn, s.npl, j, PST);
-    add_solve_tasks(ka, s.EA, s.LA, s.ycA, s.rcA, s.mapA, s.bA, s.nzn, s.npl, j, PST);
-    add_solve_tasks(kk8, s.EK, s.LK, s.ycK8, s.rcK8, s.mapK, s.bK, s.nzn, s.npl, j, KB);
-    add_solve_tasks(ka8, s.EA, s.LA, s.ycA8, s.rcA8, s.mapA, s.bA, s.nzn, s.npl, j, KB);
+    const int g = j % ng;
+    add_solve_tasks(kk[g], s.EK, s.LK, s.ycK, s.rcK, s.mapK, s.bK, s.nzn, s.npl, j, PST);
+    add_solve_tasks(ka[g], s.EA, s.LA, s.ycA, s.rcA, s.mapA, s.bA, s.nzn, s.npl, j, PST);
+    add_solve_tasks(kk8[g], s.EK, s.LK, s.ycK8, s.rcK8, s.mapK, s.bK, s.nzn, s.npl, j, KB);
+    add_solve_tasks(ka8[g], s.EA, s.LA, s.ycA8, s.rcA8, s.mapA, s.bA, s.nzn, s.npl, j, KB);
   }
-  flatten_solve(kk, h->solveK);
-  flatten_solve(ka, h->solveA);
-  flatten_solve(kk8, h->solveK8);
-  flatten_solve(ka8, h->solveA8);
+  for (SolveSchedule* ss : {&h->solveK, &h->solveA, &h->solveK8, &h->solveA8}) {
+    ss->steps.clear();
+    ss->tasks.clear();
+  }
+  for (int g = 0; g < ng; ++g) {
+    flatten_solve(kk[g], h->solveK, true);
+    flatten_solve(ka[g], h->solveA, true);
+    flatten_solve(kk8[g], h->solveK8, true);
+    flatten_solve(ka8[g], h->solveA8, true);
+  }
 }
 
 // Coarse matrix: one dense block of size NcPad, factorised by the same tile
