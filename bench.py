@@ -262,7 +262,12 @@ def run_ours(args):
     extra = {"iterations_max": max(i["iterations"] for i in infos),
              "residual_max": max(i["residual"] for i in infos),
              "lambda_sub5_head": [float(x) for x in lam_dev[5 % m.N, :8].cpu().numpy()]}
+    lam_fp64 = lam_dev.clone()
+    u_fp64 = u_dev.clone()
     m.close()
+    mixed = None
+    if not args.no_mixed:
+        mixed = run_mixed(args, cfg, ang_dev, stream, dev, rank, lam_fp64, u_fp64, flush, world)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
@@ -279,10 +284,58 @@ def run_ours(args):
                            "l2": "flushed between timed steps (256 MiB write); working set ~25 GB >> L2",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "solver": extra}
+                "clocks": clocks, "solver": extra, "mixed": mixed}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_mixed(args, cfg, ang_dev, stream, dev, rank, lam_fp64, u_fp64, flush, world):
+    """The same workload in mixed precision (FP32 factors and solves with FP64
+    refinement); its solution is compared with the FP64 one in the energy norm."""
+    import ctypes as C
+    import torch
+    from paper_2211_13893_gb300 import MSGFEM
+    m = MSGFEM.from_config(cfg, ang_dev, seed=1234 + rank, stream=stream.cuda_stream, profile=1,
+                           streams=args.streams, precision=1)
+    lam = torch.empty_like(lam_fp64)
+    u = torch.empty_like(u_fp64)
+
+    def step():
+        m.local_spaces(cfg.n_loc, lam_out=lam)
+        m.coarse_assemble()
+        m.solve(u_out=u)
+
+    for _ in range(max(2, args.warmup - 1)):
+        step()
+    torch.cuda.synchronize()
+    m.profile(reset=True)
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    prof = m.profile()
+    total = sum(ms)
+    if world > 1:
+        t = torch.tensor([total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+    e = C.c_double(-1.0)
+    m.lib.msgfem_energy_error_noalloc(m.h, u.data_ptr(), u_fp64.data_ptr(), C.addressof(e))
+    rel = ((lam - lam_fp64).abs() / lam_fp64.abs().amax(dim=1, keepdim=True).clamp_min(1e-2)).max().item()
+    out = {"value": world * m.N * args.steps / (total / 1000.0), "unit": "subdomains/s",
+           "ms_per_step": total / args.steps, "dtype": "f32 factors/solves + f64 refinement/RR/coarse",
+           "factor_ms_per_step": prof["factor_ms"] / args.steps, "solve_ms_per_step": prof["solve_ms"] / args.steps,
+           "factor_tflops": prof["factor_flops"] * args.steps / (prof["factor_ms"] / 1000.0) / 1e12
+           if prof["factor_ms"] else None,
+           "eig_rel_diff_vs_fp64": rel, "energy_norm_diff_vs_fp64": e.value}
+    m.close()
+    return out
 
 
 def main():
@@ -295,6 +348,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=16, help="oracle subdomains per timed sample")
     ap.add_argument("--ref-warmup", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison run")
     ap.add_argument("--streams", type=int, default=0, help="stream groups of the library (0 = its default)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

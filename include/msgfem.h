@@ -82,6 +82,10 @@ typedef struct {
   int sx, sy;           /* subdomains along x and y */
 } msgfem_partition;
 
+/* MSGFEM_FP64: all arithmetic in FP64.  MSGFEM_MIXED: layer blocks, their
+ * factorisation and the block solves in FP32, every solve refined to FP64
+ * accuracy with FP64 stencil residuals; Gram products, Rayleigh-Ritz,
+ * CholeskyQR2, residual checks and the coarse problem stay FP64. */
 typedef enum { MSGFEM_FP64 = 0, MSGFEM_MIXED = 1 } msgfem_precision;
 
 typedef struct {
@@ -95,6 +99,7 @@ typedef struct {
   int profile;          /* 1: time the phases with CUDA events (msgfem_get_profile) */
   int solver;           /* 0: block Krylov (block width 8, basis <= 96), 1: subspace iteration */
   int streams;          /* independent task groups run on their own streams (1..16); 0 = 16 */
+  int refine;           /* MSGFEM_MIXED: FP64 refinement steps after each FP32 solve; 0 = 5 */
 } msgfem_options;
 
 /* Phase timers (CUDA events on the handle's stream, milliseconds, summed over

@@ -126,16 +126,38 @@ msgfem_status allocate(msgfem* h) {
     TRY(dalloc(h, &s.mapA, s.bA));
     TRY(dalloc(h, &s.invK, 3 * s.npl));
     TRY(dalloc(h, &s.invA, 3 * s.npl));
-    TRY(dalloc(h, &s.DK, bK2 * (2 * s.nzn - 1)));
-    s.EK = s.DK + bK2 * s.nzn;
-    TRY(dalloc(h, &s.LK, bK2 * s.nzn));
-    TRY(dalloc(h, &s.DA, bA2 * (2 * s.nzn - 1)));
-    s.EA = s.DA + bA2 * s.nzn;
-    TRY(dalloc(h, &s.LA, bA2 * s.nzn));
-    TRY(dalloc(h, &s.ycK, (size_t)s.nzn * s.bK * PST));
-    TRY(dalloc(h, &s.ycA, (size_t)s.nzn * s.bA * PST));
-    TRY(dalloc(h, &s.rcK, (size_t)s.bK * PST));
-    TRY(dalloc(h, &s.rcA, (size_t)s.bA * PST));
+    if (h->mixed) {
+      // FP32 layer blocks, factors and solve buffers
+      TRY(dalloc(h, &s.DKf, bK2 * (2 * s.nzn - 1)));
+      s.EKf = s.DKf + bK2 * s.nzn;
+      TRY(dalloc(h, &s.LKf, bK2 * s.nzn));
+      TRY(dalloc(h, &s.DAf, bA2 * (2 * s.nzn - 1)));
+      s.EAf = s.DAf + bA2 * s.nzn;
+      TRY(dalloc(h, &s.LAf, bA2 * s.nzn));
+      TRY(dalloc(h, &s.ycKf, (size_t)s.nzn * s.bK * PST));
+      TRY(dalloc(h, &s.ycAf, (size_t)s.nzn * s.bA * PST));
+      TRY(dalloc(h, &s.rcKf, (size_t)s.bK * PST));
+      TRY(dalloc(h, &s.rcAf, (size_t)s.bA * PST));
+      TRY(dalloc(h, &s.ycK8f, (size_t)s.nzn * s.bK * KB));
+      TRY(dalloc(h, &s.ycA8f, (size_t)s.nzn * s.bA * KB));
+      TRY(dalloc(h, &s.rcK8f, (size_t)s.bK * KB));
+      TRY(dalloc(h, &s.rcA8f, (size_t)s.bA * KB));
+    } else {
+      TRY(dalloc(h, &s.DK, bK2 * (2 * s.nzn - 1)));
+      s.EK = s.DK + bK2 * s.nzn;
+      TRY(dalloc(h, &s.LK, bK2 * s.nzn));
+      TRY(dalloc(h, &s.DA, bA2 * (2 * s.nzn - 1)));
+      s.EA = s.DA + bA2 * s.nzn;
+      TRY(dalloc(h, &s.LA, bA2 * s.nzn));
+      TRY(dalloc(h, &s.ycK, (size_t)s.nzn * s.bK * PST));
+      TRY(dalloc(h, &s.ycA, (size_t)s.nzn * s.bA * PST));
+      TRY(dalloc(h, &s.rcK, (size_t)s.bK * PST));
+      TRY(dalloc(h, &s.rcA, (size_t)s.bA * PST));
+      TRY(dalloc(h, &s.ycK8, (size_t)s.nzn * s.bK * KB));
+      TRY(dalloc(h, &s.ycA8, (size_t)s.nzn * s.bA * KB));
+      TRY(dalloc(h, &s.rcK8, (size_t)s.bK * KB));
+      TRY(dalloc(h, &s.rcA8, (size_t)s.bA * KB));
+    }
     double** mvs[] = {&s.Phi, &s.Z, &s.KPhi, &s.W, &s.T1, &s.R, &s.BR, &s.EV, &s.CB, &s.CW};
     for (double** m : mvs) {
       TRY(dalloc(h, m, (size_t)s.nfull * PST));
@@ -157,10 +179,6 @@ msgfem_status allocate(msgfem* h) {
       TRY(dalloc(h, m, (size_t)s.nfull * KB));
       CK(cudaMemset(*m, 0, (size_t)s.nfull * KB * sizeof(double)));
     }
-    TRY(dalloc(h, &s.ycK8, (size_t)s.nzn * s.bK * KB));
-    TRY(dalloc(h, &s.ycA8, (size_t)s.nzn * s.bA * KB));
-    TRY(dalloc(h, &s.rcK8, (size_t)s.bK * KB));
-    TRY(dalloc(h, &s.rcA8, (size_t)s.bA * KB));
     TRY(dalloc(h, &s.H, (size_t)(MQ + KB) * MQ));
     CK(cudaMemset(s.H, 0, (size_t)(MQ + KB) * MQ * sizeof(double)));
     TRY(dalloc(h, &s.Hc, (size_t)MQ * KB));
@@ -199,11 +217,24 @@ msgfem_status allocate(msgfem* h) {
   // schedules
   build_factor_schedule(h);
   build_solve_schedules(h);
-  TRY(dalloc(h, &h->fact.d_gemm, h->fact.gemm.size()));
-  CK(cudaMemcpy(h->fact.d_gemm, h->fact.gemm.data(), h->fact.gemm.size() * sizeof(GemmTask), cudaMemcpyHostToDevice));
+  if (h->mixed) {
+    TRY(dalloc(h, &h->factf.d_gemm, h->factf.gemm.size()));
+    CK(cudaMemcpy(h->factf.d_gemm, h->factf.gemm.data(), h->factf.gemm.size() * sizeof(TileTaskT<float>),
+                  cudaMemcpyHostToDevice));
+    for (SolveScheduleT<float>* ss : {&h->solveKf, &h->solveAf, &h->solveK8f, &h->solveA8f}) {
+      TRY(dalloc(h, &ss->d_tasks, ss->tasks.size()));
+      CK(cudaMemcpy(ss->d_tasks, ss->tasks.data(), ss->tasks.size() * sizeof(SolveTaskT<float>),
+                    cudaMemcpyHostToDevice));
+    }
+  } else {
+    TRY(dalloc(h, &h->fact.d_gemm, h->fact.gemm.size()));
+    CK(cudaMemcpy(h->fact.d_gemm, h->fact.gemm.data(), h->fact.gemm.size() * sizeof(GemmTask),
+                  cudaMemcpyHostToDevice));
+  }
   TRY(dalloc(h, &h->d_mk, h->N));
   TRY(dalloc(h, &h->d_nwk, h->N));
   for (SolveSchedule* ss : {&h->solveK, &h->solveA, &h->solveK8, &h->solveA8}) {
+    if (ss->tasks.empty()) continue;
     TRY(dalloc(h, &ss->d_tasks, ss->tasks.size()));
     CK(cudaMemcpy(ss->d_tasks, ss->tasks.data(), ss->tasks.size() * sizeof(SolveTask), cudaMemcpyHostToDevice));
   }
@@ -285,20 +316,54 @@ double solve_flops(const msgfem* h, int mat, int p) {
   return f;
 }
 
-void timed_solve(msgfem* h, int mat, int src, int dst, int neg) {
+// One block solve (K: mat 0, A11: mat 1) of PST or KB right-hand sides in the
+// handle's precision; add = 1 accumulates into the destination.
+void timed_solve_w(msgfem* h, int mat, int src, int dst, int neg, int width, int add) {
   const int sp = span_begin(h, TAG_SOLVE);
-  run_solve_mv(mat == 0 ? h->solveK : h->solveA, h->stream, src, dst, neg, PST, &h->gs);
+  if (h->mixed) {
+    const SolveScheduleT<float>& sc = width == KB ? (mat == 0 ? h->solveK8f : h->solveA8f)
+                                                  : (mat == 0 ? h->solveKf : h->solveAf);
+    run_solve_mv(sc, h->stream, src, dst, neg, width, &h->gs, add);
+  } else {
+    const SolveScheduleT<double>& sc = width == KB ? (mat == 0 ? h->solveK8 : h->solveA8)
+                                                   : (mat == 0 ? h->solveK : h->solveA);
+    run_solve_mv(sc, h->stream, src, dst, neg, width, &h->gs, add);
+  }
   span_end(h, sp);
-  h->prof.solve_flops += solve_flops(h, mat, h->p);
+  h->prof.solve_flops += solve_flops(h, mat, width == KB ? KB : h->p);
   h->prof.solve_calls += 1;
 }
 
-void timed_solve8(msgfem* h, int mat, int src, int dst, int neg) {
-  const int sp = span_begin(h, TAG_SOLVE);
-  run_solve_mv(mat == 0 ? h->solveK8 : h->solveA8, h->stream, src, dst, neg, KB, &h->gs);
-  span_end(h, sp);
-  h->prof.solve_flops += solve_flops(h, mat, KB);
-  h->prof.solve_calls += 1;
+void timed_solve(msgfem* h, int mat, int src, int dst, int neg) { timed_solve_w(h, mat, src, dst, neg, PST, 0); }
+void timed_solve8(msgfem* h, int mat, int src, int dst, int neg) { timed_solve_w(h, mat, src, dst, neg, KB, 0); }
+
+// W = K^{-1} Z on KB-wide blocks (pinned rows zero).  In mixed precision the
+// FP32 solve is followed by h->refine steps of iterative refinement with the
+// FP64 stencil residual Z - K W.
+void solve_K_kb(msgfem* h) {
+  timed_solve8(h, 0, MV_ZB, MV_WB, 0);
+  launch_zero_pins_kb(h, MV_WB);
+  if (!h->mixed) return;
+  for (int r = 0; r < h->refine; ++r) {
+    launch_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
+    launch_x_minus_y(h, MV_ZB, MV_TB, MV_TB, KB);
+    launch_zero_pins_kb(h, MV_TB);
+    timed_solve_w(h, 0, MV_TB, MV_WB, 0, KB, 1);
+    launch_zero_pins_kb(h, MV_WB);
+  }
+}
+
+// A-harmonic re-extension of a KB-wide block whose B1 rows are zero:
+// W_B1 = -A11^{-1} (K W)_B1, refined in mixed precision with the FP64
+// residual of the harmonic condition (K W)_B1.
+void extend_kb(msgfem* h) {
+  launch_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
+  timed_solve8(h, 1, MV_TB, MV_WB, 1);
+  if (!h->mixed) return;
+  for (int r = 0; r < h->refine; ++r) {
+    launch_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
+    timed_solve_w(h, 1, MV_TB, MV_WB, 1, KB, 1);
+  }
 }
 
 // B-orthogonal projection of a KB-wide block out of the rigid modes (floating only)
@@ -320,11 +385,9 @@ void cholqr2_kb(msgfem* h, int j) {
 // W <- M W for A-harmonic W: Z = B W, K solve, restrict to B2, A11 re-extension
 void apply_M_kb(msgfem* h) {
   launch_stencil_kb(h, MV_WB, MV_ZB, 3, 1.0);
-  timed_solve8(h, 0, MV_ZB, MV_WB, 0);
-  launch_zero_pins_kb(h, MV_WB);
+  solve_K_kb(h);
   launch_mask_kb(h, MV_WB, 1 << 2);
-  launch_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
-  timed_solve8(h, 1, MV_TB, MV_WB, 1);
+  extend_kb(h);
   project_rigid_kb(h, MV_WB);
 }
 
@@ -422,18 +485,23 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
     nwmax = std::max(nwmax, nw[j]);
   }
   CK(cudaMemcpyAsync(h->d_nwk, nw.data(), h->N * sizeof(int), cudaMemcpyHostToDevice, st));
-  // particular function psi: A11 psi_1 = b_1 (one column of a KB-wide solve)
+  // particular function psi: A11 psi_1 = b_1 (one column of a KB-wide solve),
+  // refined in mixed precision with the FP64 residual (K psi - b)_B1
   launch_load_col_kb(h, MV_TB, -1.0);
   launch_zero_kb(h, MV_WB);
   timed_solve8(h, 1, MV_TB, MV_WB, 1);
+  for (int r = 0; h->mixed && r < h->refine; ++r) {
+    launch_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
+    launch_sub_load_kb(h, MV_TB);
+    timed_solve_w(h, 1, MV_TB, MV_WB, 1, KB, 1);
+  }
   launch_take_col_kb(h, MV_WB);
   for (int j = 0; j < h->N; ++j)
     if (nw[j] <= 0) act[j] = 0;
   TRY(set_active(h, act));
   // start block on B2, A-harmonic extension, first application of M
   launch_random_kb(h, MV_WB, h->opt.seed);
-  launch_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
-  timed_solve8(h, 1, MV_TB, MV_WB, 1);
+  extend_kb(h);
   project_rigid_kb(h, MV_WB);
   apply_M_kb(h);
   // Q_0 = W R^{-1} with W^T N W = R^T R (CholeskyQR2)
@@ -535,6 +603,12 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
   if (!(h->opt.tol > 0)) h->opt.tol = 1e-7;
   h->stream = static_cast<cudaStream_t>(h->opt.stream);
   h->ngroup = h->opt.streams > 0 ? std::min(h->opt.streams, NGROUP) : NGROUP;
+  if (h->opt.precision != MSGFEM_FP64 && h->opt.precision != MSGFEM_MIXED) {
+    h->err = "unknown precision";
+    return MSGFEM_EINVAL;
+  }
+  h->mixed = h->opt.precision == MSGFEM_MIXED;
+  h->refine = h->opt.refine > 0 ? h->opt.refine : 5;
   *out = h;
   msgfem_status st = build_problem(h);
   if (st != MSGFEM_OK) return st;
@@ -586,12 +660,14 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   int sp = span_begin(h, TAG_ASSEMBLE);
   launch_element_stiffness(h);
   launch_stencil(h);
-  launch_layer_blocks(h);
+  if (h->mixed) launch_layer_blocks_f32(h);
+  else launch_layer_blocks(h);
   span_end(h, sp);
   CK_LAUNCH();
   // 2. factorisations of K and A11
   sp = span_begin(h, TAG_FACTOR);
-  run_schedule(h->fact, st, &h->gs);
+  if (h->mixed) run_schedule(h->factf, st, &h->gs);
+  else run_schedule(h->fact, st, &h->gs);
   span_end(h, sp);
   CK_LAUNCH();
   const int sp_iter = span_begin(h, TAG_ITERATE);
@@ -603,6 +679,10 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   launch_rotate(h, MV_R, GM_Y, 6);
   launch_rotate(h, MV_BR, GM_Y, 6);
   bool all_done = false;
+  if (h->opt.solver == 1 && h->mixed) {
+    h->err = "subspace iteration (solver = 1) runs in FP64 only";
+    return MSGFEM_EINVAL;
+  }
   if (h->opt.solver == 1) {
     TRY(run_subspace(h, n_loc, p, all_done));
   } else {
@@ -614,6 +694,11 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   // 4. final residuals: S x = (K Phi)|B2, T x = -(K y~)|B2 with y~ = A11^{-1} Z|B1
   for (auto& s : h->sub) CK(cudaMemsetAsync(s.T1, 0, (size_t)s.nfull * PST * sizeof(double), st));
   timed_solve(h, 1, MV_Z, MV_T1, 0);
+  for (int r = 0; h->mixed && r < h->refine; ++r) {   // refine y~: residual Z - K y~ on B1
+    launch_stencil_apply(h, MV_T1, MV_W, 0, 1.0);
+    launch_x_minus_y(h, MV_Z, MV_W, MV_W, PST);
+    timed_solve_w(h, 1, MV_W, MV_T1, 0, PST, 1);
+  }
   launch_stencil_apply(h, MV_T1, MV_W, 0, 1.0);
   launch_colnorms(h, MV_KPHI, MV_W, p);
   span_end(h, sp_iter);

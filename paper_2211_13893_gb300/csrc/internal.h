@@ -29,27 +29,31 @@
 // G_POTRF the Cholesky factor and inverse of the SPD tile C (in place) with the
 // inverse written to P.
 enum { G_TRANSB = 1, G_ACC = 2, G_NEG = 4, G_POSTMUL = 8, G_POTRF = 16 };
-struct GemmTask {
-  const double* A;
-  const double* B;
-  double* C;
-  const double* P;   // G_POSTMUL: 64x64 tile with leading dimension ldc
+template <typename T>
+struct TileTaskT {
+  const T* A;
+  const T* B;
+  T* C;
+  const T* P;   // G_POSTMUL: 64x64 tile with leading dimension ldc; G_POTRF: inverse output
   int lda, ldb, ldc, K;
   int flags, sub;
 };
+using GemmTask = TileTaskT<double>;
 
 
 // Solve step: C(64 x PST) = init + sign * op(A) * B
 enum { S_TRANSA = 1, S_NEG = 2, S_INIT_GATHER = 4, S_INIT_TILE = 8, S_SCATTER = 16 };
-struct SolveTask {
-  const double* A;
-  const double* B;      // K x PST compact
-  double* C;            // 64 x PST compact tile
-  const double* init;   // S_INIT_TILE: 64 x PST compact tile
+template <typename T>
+struct SolveTaskT {
+  const T* A;
+  const T* B;           // K x PC compact
+  T* C;                 // 64 x PC compact tile
+  const T* init;        // S_INIT_TILE: 64 x PC compact tile
   const int* gmap;      // S_INIT_GATHER: 64 in-layer full rows (or -1)
   const int* smap;      // S_SCATTER: 64 in-layer full rows (or -1)
   int lda, K, flags, sub, row_off;
 };
+using SolveTask = SolveTaskT<double>;
 
 // multivector selectors
 enum { MV_PHI = 0, MV_Z, MV_KPHI, MV_W, MV_T1, MV_R, MV_BR, MV_EV, MV_CB, MV_CW,
@@ -87,6 +91,11 @@ struct SubDev {
   double* Zb; double* Wb; double* Tb;   // [nfull][KB] working blocks
   double* ycK8; double* ycA8;  // [nzn][b][KB] compact solve buffers
   double* rcK8; double* rcA8;  // [b][KB]
+  // FP32 copies for the mixed-precision path (layer blocks, factors, solve buffers)
+  float* DKf; float* EKf; float* LKf;
+  float* DAf; float* EAf; float* LAf;
+  float* ycK8f; float* ycA8f; float* rcK8f; float* rcA8f;   // KB columns
+  float* ycKf; float* ycAf; float* rcKf; float* rcAf;       // PST columns
   double* H;                   // [MQ + KB][MQ] projected operator Q^T T M Q and R_{m+1}
   double* Hc;                  // [MQ][KB] block inner products
   double* Yk;                  // [MQ][PST] Ritz coefficients of the wanted pairs
@@ -95,19 +104,24 @@ struct SubDev {
 // A schedule is a set of independent groups (each a sequence of steps, run on
 // its own stream); steps[g] lists the launches of group g in order.
 #define NGROUP 16   // most stream groups a schedule may use
-struct Schedule {
-  struct Step { int first, count; };
+struct SchedStep { int first, count; };
+template <typename T>
+struct ScheduleT {
+  using Step = SchedStep;
   std::vector<std::vector<Step>> steps;
-  std::vector<GemmTask> gemm;
-  GemmTask* d_gemm = nullptr;
+  std::vector<TileTaskT<T>> gemm;
+  TileTaskT<T>* d_gemm = nullptr;
 };
+using Schedule = ScheduleT<double>;
 
-struct SolveSchedule {
-  struct Step { int first, count; };
+template <typename T>
+struct SolveScheduleT {
+  using Step = SchedStep;
   std::vector<std::vector<Step>> steps;
-  std::vector<SolveTask> tasks;
-  SolveTask* d_tasks = nullptr;
+  std::vector<SolveTaskT<T>> tasks;
+  SolveTaskT<T>* d_tasks = nullptr;
 };
+using SolveSchedule = SolveScheduleT<double>;
 
 // Fork/join of the group streams around a schedule run.
 struct StreamSet {
@@ -154,6 +168,10 @@ struct msgfem {
   Schedule fact;
   SolveSchedule solveK, solveA;     // PST columns
   SolveSchedule solveK8, solveA8;   // KB columns
+  ScheduleT<float> factf;            // mixed precision: FP32 factorisation
+  SolveScheduleT<float> solveKf, solveAf, solveK8f, solveA8f;
+  int mixed = 0;                     // precision == MSGFEM_MIXED
+  int refine = 2;                    // FP64 refinement steps per FP32 solve
   std::vector<CoarsePair> pairs;
   CoarsePair* d_pairs = nullptr;
   double* d_pair_part = nullptr;
@@ -194,12 +212,16 @@ void build_coarse_schedules(msgfem* h);
 
 // launchers
 void set_dense_context(int* active, int* notspd, const SubDev* subs);
-void run_schedule(const Schedule& s, cudaStream_t st, const StreamSet* gs = nullptr);
-void run_solve_mv(const SolveSchedule& s, cudaStream_t st, int src, int dst, int gather_neg, int width = PST,
-                  const StreamSet* gs = nullptr);
+template <typename T>
+void run_schedule(const ScheduleT<T>& s, cudaStream_t st, const StreamSet* gs = nullptr);
+// solve steps; scatter_add adds the result into the destination multivector
+template <typename T>
+void run_solve_mv(const SolveScheduleT<T>& s, cudaStream_t st, int src, int dst, int gather_neg, int width = PST,
+                  const StreamSet* gs = nullptr, int scatter_add = 0);
 void launch_element_stiffness(msgfem* h);
 void launch_stencil(msgfem* h);
 void launch_layer_blocks(msgfem* h);
+void launch_layer_blocks_f32(msgfem* h);
 void launch_stencil_apply(msgfem* h, int src, int dst, int mode, double alpha);
 void launch_gram(msgfem* h, int wx, int wy, int wg);
 void launch_small_eig(msgfem* h, int p);
@@ -215,6 +237,8 @@ void launch_chol_inv_small(msgfem* h, int wg, const int* d_ncols, int nfixed, in
 void launch_colnorms(msgfem* h, int wa, int wb, int p);
 void launch_scale_rows_mu(msgfem* h, int which);
 void launch_theta_axpy(msgfem* h, int wx, int wy, int wd, int p);
+void launch_x_minus_y(msgfem* h, int wx, int wy, int wd, int stride);
+void launch_sub_load_kb(msgfem* h, int which);
 void launch_coarse_blocks(msgfem* h);
 void launch_coarse_rhs(msgfem* h);
 void launch_prolong(msgfem* h);

@@ -9,6 +9,8 @@
 // 2x2x2 Gauss points of the trilinear brick, with the 6x24 Voigt B matrix.
 // GPU node order inside an element: a = ax + 2 ay + 4 az, (ax, ay, az) in
 // {0,1}^3; element DoF 3 a + c.
+#include <type_traits>
+
 #include "internal.h"
 
 namespace {
@@ -151,8 +153,19 @@ __device__ __forceinline__ bool is_pinned(const SubDev& s, int row) {
   return false;
 }
 
+template <typename T> struct Blocks;
+template <> struct Blocks<double> {
+  __device__ static double* D(const SubDev& s, int mat) { return mat == 0 ? s.DK : s.DA; }
+  __device__ static double* E(const SubDev& s, int mat) { return mat == 0 ? s.EK : s.EA; }
+};
+template <> struct Blocks<float> {
+  __device__ static float* D(const SubDev& s, int mat) { return mat == 0 ? s.DKf : s.DAf; }
+  __device__ static float* E(const SubDev& s, int mat) { return mat == 0 ? s.EKf : s.EAf; }
+};
+
 // Scatter the stencil into the layer blocks of K (mat 0) and A11 (mat 1).
 // Thread per (node, slot); slots with dk = 0 go to D_k, dk = -1 to E_{k-1}.
+template <typename T>
 __global__ void __launch_bounds__(216)
 k_layer_blocks(const SubDev* __restrict__ subs) {
   const SubDev s = subs[blockIdx.y];
@@ -171,8 +184,7 @@ k_layer_blocks(const SubDev* __restrict__ subs) {
   for (int mat = 0; mat < 2; ++mat) {
     const int* inv = mat == 0 ? s.invK : s.invA;
     const int b = mat == 0 ? s.bK : s.bA;
-    double* blk = (dk == 0) ? ((mat == 0 ? s.DK : s.DA) + (size_t)k * b * b)
-                            : ((mat == 0 ? s.EK : s.EA) + (size_t)(k - 1) * b * b);
+    T* blk = (dk == 0) ? (Blocks<T>::D(s, mat) + (size_t)k * b * b) : (Blocks<T>::E(s, mat) + (size_t)(k - 1) * b * b);
     for (int c = 0; c < 3; ++c) {
       const int rr = inv[3 * q + c];
       if (rr < 0) continue;
@@ -181,23 +193,26 @@ k_layer_blocks(const SubDev* __restrict__ subs) {
         const int col = inv[3 * q2 + cc];
         if (col < 0) continue;
         if (mat == 0 && s.floating && is_pinned(s, ((k + dk) * s.npl + q2) * 3 + cc)) continue;
-        blk[(size_t)rr * b + col] = st[c * 3 + cc];
+        blk[(size_t)rr * b + col] = (T)st[c * 3 + cc];
       }
     }
   }
 }
 
 // Identity on padding rows and pinned DoFs.
+template <typename T>
 __global__ void k_block_identity(const SubDev* __restrict__ subs) {
   const SubDev s = subs[blockIdx.y];
   const int k = blockIdx.x;
   if (k >= s.nzn) return;
-  for (int c = s.nK + threadIdx.x; c < s.bK; c += blockDim.x) s.DK[(size_t)k * s.bK * s.bK + (size_t)c * s.bK + c] = 1.0;
-  for (int c = s.nA + threadIdx.x; c < s.bA; c += blockDim.x) s.DA[(size_t)k * s.bA * s.bA + (size_t)c * s.bA + c] = 1.0;
+  T* DK = Blocks<T>::D(s, 0);
+  T* DA = Blocks<T>::D(s, 1);
+  for (int c = s.nK + threadIdx.x; c < s.bK; c += blockDim.x) DK[(size_t)k * s.bK * s.bK + (size_t)c * s.bK + c] = (T)1;
+  for (int c = s.nA + threadIdx.x; c < s.bA; c += blockDim.x) DA[(size_t)k * s.bA * s.bA + (size_t)c * s.bA + c] = (T)1;
   if (s.floating && threadIdx.x < 6 && s.pin[threadIdx.x] >= 0) {
     const int row = s.pin[threadIdx.x];
     const int layer = row / (3 * s.npl), r = s.invK[row % (3 * s.npl)];
-    if (layer == k && r >= 0) s.DK[(size_t)k * s.bK * s.bK + (size_t)r * s.bK + r] = 1.0;
+    if (layer == k && r >= 0) DK[(size_t)k * s.bK * s.bK + (size_t)r * s.bK + r] = (T)1;
   }
 }
 
@@ -215,15 +230,21 @@ void launch_stencil(msgfem* h) {
   k_stencil<<<grid, 216, 0, h->stream>>>(h->d_sub, h->d_Ke, h->layered, h->NY, h->NZ); ++g_launch_count;
 }
 
-void launch_layer_blocks(msgfem* h) {
+template <typename T>
+static void layer_blocks_t(msgfem* h) {
   for (const auto& s : h->sub) {
-    cudaMemsetAsync(s.DK, 0, sizeof(double) * (size_t)s.bK * s.bK * (2 * s.nzn - 1), h->stream);
-    cudaMemsetAsync(s.DA, 0, sizeof(double) * (size_t)s.bA * s.bA * (2 * s.nzn - 1), h->stream);
+    T* DK = std::is_same<T, float>::value ? (T*)s.DKf : (T*)s.DK;
+    T* DA = std::is_same<T, float>::value ? (T*)s.DAf : (T*)s.DA;
+    cudaMemsetAsync(DK, 0, sizeof(T) * (size_t)s.bK * s.bK * (2 * s.nzn - 1), h->stream);
+    cudaMemsetAsync(DA, 0, sizeof(T) * (size_t)s.bA * s.bA * (2 * s.nzn - 1), h->stream);
   }
   int maxn = 0, maxz = 0;
   for (const auto& s : h->sub) { maxn = std::max(maxn, s.nnode); maxz = std::max(maxz, s.nzn); }
   dim3 grid((maxn + 7) / 8, h->N);
-  k_layer_blocks<<<grid, 216, 0, h->stream>>>(h->d_sub); ++g_launch_count;
+  k_layer_blocks<T><<<grid, 216, 0, h->stream>>>(h->d_sub); ++g_launch_count;
   dim3 g2(maxz, h->N);
-  k_block_identity<<<g2, 128, 0, h->stream>>>(h->d_sub); ++g_launch_count;
+  k_block_identity<T><<<g2, 128, 0, h->stream>>>(h->d_sub); ++g_launch_count;
 }
+
+void launch_layer_blocks(msgfem* h) { layer_blocks_t<double>(h); }
+void launch_layer_blocks_f32(msgfem* h) { layer_blocks_t<float>(h); }

@@ -1,5 +1,6 @@
-// Dense FP64 tile kernels behind the layer-block Cholesky factorisation and
-// the block triangular solves of the local shift-invert operator.
+// Dense tile kernels behind the layer-block Cholesky factorisation and the
+// block triangular solves of the local shift-invert operator, for FP64 (plain
+// path) and FP32 (mixed path) block storage.
 //
 // The factorisation of a block-tridiagonal SPD matrix (z-layer blocks, see
 // internal.h) is expressed as a static list of 64x64 tile tasks grouped into
@@ -11,9 +12,10 @@
 //   TRTRI   Linv_ik = -Li_ii sum_m L_im Linv_mk             (block inverse)
 // POTRF and GEMM tasks share one kernel, so independent work of different
 // phases (the block inverse of layer l and the factorisation of layer l + 1)
-// can fill the same launch.  FP64 arithmetic on this part runs at ~2 DFMA/clk/SM, so every kernel is
-// bound by the FP64 pipe; the tile kernels only need enough independent
-// tasks in flight to occupy all SMs.
+// can fill the same launch.  FP64 arithmetic runs at ~2 DFMA/clk/SM on this
+// part, so the FP64 kernels are bound by the FP64 pipe and only need enough
+// independent tasks in flight.  The tile Cholesky is computed in FP64 in both
+// precisions (it is 1/40 of the work).
 #include "internal.h"
 
 namespace {
@@ -21,16 +23,17 @@ namespace {
 constexpr int KC = 16;   // K chunk of the tile GEMM
 constexpr int TILE_SMEM = 2 * 64 * 65 * (int)sizeof(double);   // dynamic shared memory per CTA
 
-// Cholesky and inverse of one 64x64 SPD tile in shared memory.  L occupies
-// the lower triangle of A; X = L^{-1} is kept transposed in the strict upper
-// triangle shifted by one column (X[i][c] at A[c][i + 1], using the pad column).
-__device__ void tile_potrf_inv(const GemmTask& t, double (*A)[65], int* notspd) {
+// Cholesky and inverse of one 64x64 SPD tile in shared memory (FP64).  L
+// occupies the lower triangle of A; X = L^{-1} is kept transposed in the strict
+// upper triangle shifted by one column (X[i][c] at A[c][i + 1], the pad column).
+template <typename T>
+__device__ void tile_potrf_inv(const TileTaskT<T>& t, double (*A)[65], int* notspd) {
   __shared__ int bad;
   const int tid = threadIdx.x;
   if (tid == 0) bad = 0;
   for (int e = tid; e < 64 * 64; e += 256) {
     const int r = e >> 6, c = e & 63;
-    A[r][c] = (c <= r) ? t.C[(size_t)r * t.ldc + c] : 0.0;
+    A[r][c] = (c <= r) ? (double)t.C[(size_t)r * t.ldc + c] : 0.0;
   }
   if (tid < 64) A[tid][64] = 0.0;
   __syncthreads();
@@ -64,57 +67,59 @@ __device__ void tile_potrf_inv(const GemmTask& t, double (*A)[65], int* notspd) 
     }
     __syncthreads();
   }
-  double* Li = const_cast<double*>(t.P);
+  T* Li = const_cast<T*>(t.P);
   for (int e = tid; e < 64 * 64; e += 256) {
     const int r = e >> 6, c = e & 63;
-    t.C[(size_t)r * t.ldc + c] = (c <= r) ? A[r][c] : 0.0;
-    Li[(size_t)r * t.ldc + c] = (c <= r) ? A[c][r + 1] : 0.0;
+    t.C[(size_t)r * t.ldc + c] = (T)((c <= r) ? A[r][c] : 0.0);
+    Li[(size_t)r * t.ldc + c] = (T)((c <= r) ? A[c][r + 1] : 0.0);
   }
   if (tid == 0 && bad && notspd != nullptr) atomicExch(&notspd[t.sub >= 0 ? t.sub : 0], 1);
 }
 
 // One tile task per CTA: a 64x64 GEMM tile (4x4 outputs per thread, operands
 // staged through shared memory in K chunks of 16) or a tile POTRF.
+template <typename T>
 __global__ void __launch_bounds__(256)
-k_tile_task(const GemmTask* __restrict__ tasks, const int* __restrict__ active, int* __restrict__ notspd) {
-  const GemmTask t = tasks[blockIdx.x];
+k_tile_task(const TileTaskT<T>* __restrict__ tasks, const int* __restrict__ active, int* __restrict__ notspd) {
+  const TileTaskT<T> t = tasks[blockIdx.x];
   if (t.sub >= 0 && active != nullptr && !active[t.sub]) return;
-  extern __shared__ double smem[];
+  extern __shared__ double smem_d[];
   if (t.flags & G_POTRF) {
-    tile_potrf_inv(t, reinterpret_cast<double (*)[65]>(smem), notspd);
+    tile_potrf_inv(t, reinterpret_cast<double (*)[65]>(smem_d), notspd);
     return;
   }
-  double (*As)[65] = reinterpret_cast<double (*)[65]>(smem);                 // [KC][65]: As[k][m]
-  double (*Bs)[65] = reinterpret_cast<double (*)[65]>(smem + KC * 65);      // [KC][65]: Bs[k][n]
+  T* smem = reinterpret_cast<T*>(smem_d);
+  T (*As)[65] = reinterpret_cast<T (*)[65]>(smem);                 // [KC][65]: As[k][m]
+  T (*Bs)[65] = reinterpret_cast<T (*)[65]>(smem + KC * 65);      // [KC][65]: Bs[k][n]
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
   const bool transB = (t.flags & G_TRANSB) != 0;
   for (int k0 = 0; k0 < t.K; k0 += KC) {
     {
       const int r = tid >> 2, c = (tid & 3) * 4;
-      const double* a = t.A + (size_t)r * t.lda + k0 + c;
+      const T* a = t.A + (size_t)r * t.lda + k0 + c;
 #pragma unroll
       for (int i = 0; i < 4; ++i) As[c + i][r] = a[i];
     }
     if (transB) {
       const int n = tid >> 2, c = (tid & 3) * 4;
-      const double* b = t.B + (size_t)n * t.ldb + k0 + c;
+      const T* b = t.B + (size_t)n * t.ldb + k0 + c;
 #pragma unroll
       for (int i = 0; i < 4; ++i) Bs[c + i][n] = b[i];
     } else {
       const int k = tid >> 4, n = (tid & 15) * 4;
-      const double* b = t.B + (size_t)(k0 + k) * t.ldb + n;
+      const T* b = t.B + (size_t)(k0 + k) * t.ldb + n;
 #pragma unroll
       for (int i = 0; i < 4; ++i) Bs[k][n + i] = b[i];
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < KC; ++kk) {
-      double a[4], b[4];
+      T a[4], b[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -128,8 +133,8 @@ k_tile_task(const GemmTask* __restrict__ tasks, const int* __restrict__ active, 
   }
   if (t.flags & G_POSTMUL) {
     // C = P * (A op(B)): product and P both staged in shared memory
-    double (*Cs)[65] = reinterpret_cast<double (*)[65]>(smem);
-    double (*Ps)[65] = reinterpret_cast<double (*)[65]>(smem + 64 * 65);
+    T (*Cs)[65] = reinterpret_cast<T (*)[65]>(smem);
+    T (*Ps)[65] = reinterpret_cast<T (*)[65]>(smem + 64 * 65);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -139,62 +144,63 @@ k_tile_task(const GemmTask* __restrict__ tasks, const int* __restrict__ active, 
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+      for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
     for (int m = 0; m < 64; ++m) {
-      double b[4];
+      T b[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) b[j] = Cs[m][tx + 16 * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const double pv = Ps[ty + 16 * i][m];
+        const T pv = Ps[ty + 16 * i][m];
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = fma(pv, b[j], acc[i][j]);
       }
     }
   }
-  const double sgn = (t.flags & G_NEG) ? -1.0 : 1.0;
+  const T sgn = (t.flags & G_NEG) ? (T)-1 : (T)1;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      double* c = t.C + (size_t)(ty + 16 * i) * t.ldc + tx + 16 * j;
-      const double v = sgn * acc[i][j];
+      T* c = t.C + (size_t)(ty + 16 * i) * t.ldc + tx + 16 * j;
+      const T v = sgn * acc[i][j];
       *c = (t.flags & G_ACC) ? *c + v : v;
     }
 }
 
 // One step of a block triangular solve: C(64 x PC) = init + sign op(A) B,
-// with PC right-hand sides (compact buffers and full-layout multivectors both
-// have row stride PC).
+// with PC right-hand sides.  Compact buffers have scalar type T; the
+// full-layout multivectors gathered from / scattered to are FP64 with row
+// stride PC (scatter_add accumulates instead of overwriting).
 constexpr int SKC = 32;
-template <int PC>
+template <typename T, int PC>
 __global__ void __launch_bounds__(256)
-k_solve_step(const SolveTask* __restrict__ tasks, const SubDev* __restrict__ subs,
-             const int* __restrict__ active, int src, int dst, int gather_neg) {
+k_solve_step(const SolveTaskT<T>* __restrict__ tasks, const SubDev* __restrict__ subs,
+             const int* __restrict__ active, int src, int dst, int gather_neg, int scatter_add) {
   constexpr int TXN = PC < 16 ? PC : 16;   // threads along columns
   constexpr int CPT = PC / TXN;            // columns per thread
   constexpr int TYN = 256 / TXN;           // threads along rows
   constexpr int RPT = 64 / TYN;            // rows per thread
-  const SolveTask t = tasks[blockIdx.x];
+  const SolveTaskT<T> t = tasks[blockIdx.x];
   if (t.sub >= 0 && active != nullptr && !active[t.sub]) return;
-  __shared__ double As[SKC][65];
-  __shared__ double Bs[SKC][PC + 1];
+  __shared__ T As[SKC][65];
+  __shared__ T Bs[SKC][PC + 1];
   const int tid = threadIdx.x, tx = tid % TXN, ty = tid / TXN;
-  double acc[RPT][CPT];
+  T acc[RPT][CPT];
 #pragma unroll
   for (int i = 0; i < RPT; ++i)
 #pragma unroll
-    for (int j = 0; j < CPT; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < CPT; ++j) acc[i][j] = (T)0;
   const bool transA = (t.flags & S_TRANSA) != 0;
   for (int k0 = 0; k0 < t.K; k0 += SKC) {
     if (!transA) {
       const int r = tid >> 2, c = (tid & 3) * 8;
-      const double* a = t.A + (size_t)r * t.lda + k0 + c;
+      const T* a = t.A + (size_t)r * t.lda + k0 + c;
 #pragma unroll
       for (int i = 0; i < 8; ++i) As[c + i][r] = a[i];
     } else {
       const int k = tid >> 3, m = (tid & 7) * 8;
-      const double* a = t.A + (size_t)(k0 + k) * t.lda + m;
+      const T* a = t.A + (size_t)(k0 + k) * t.lda + m;
 #pragma unroll
       for (int i = 0; i < 8; ++i) As[k][m + i] = a[i];
     }
@@ -202,7 +208,7 @@ k_solve_step(const SolveTask* __restrict__ tasks, const SubDev* __restrict__ sub
     __syncthreads();
 #pragma unroll 8
     for (int kk = 0; kk < SKC; ++kk) {
-      double a[RPT], b[CPT];
+      T a[RPT], b[CPT];
 #pragma unroll
       for (int i = 0; i < RPT; ++i) a[i] = As[kk][ty + TYN * i];
 #pragma unroll
@@ -214,7 +220,7 @@ k_solve_step(const SolveTask* __restrict__ tasks, const SubDev* __restrict__ sub
     }
     __syncthreads();
   }
-  const double sgn = (t.flags & S_NEG) ? -1.0 : 1.0;
+  const T sgn = (t.flags & S_NEG) ? (T)-1 : (T)1;
   const double* gfull = nullptr;
   double* sfull = nullptr;
   if (t.flags & (S_INIT_GATHER | S_SCATTER)) {
@@ -231,11 +237,14 @@ k_solve_step(const SolveTask* __restrict__ tasks, const SubDev* __restrict__ sub
 #pragma unroll
     for (int j = 0; j < CPT; ++j) {
       const int c = tx + TXN * j;
-      double v = sgn * acc[i][j];
+      T v = sgn * acc[i][j];
       if (t.flags & S_INIT_TILE) v += t.init[r * PC + c];
-      if (gmr >= 0) v += gs * gfull[(size_t)gmr * PC + c];
+      if (gmr >= 0) v += (T)(gs * gfull[(size_t)gmr * PC + c]);
       t.C[r * PC + c] = v;
-      if (smr >= 0) sfull[(size_t)smr * PC + c] = v;
+      if (smr >= 0) {
+        double* o = sfull + (size_t)smr * PC + c;
+        *o = scatter_add ? *o + (double)v : (double)v;
+      }
     }
   }
 }
@@ -280,25 +289,34 @@ static void run_groups(const Sched& s, cudaStream_t st, const StreamSet* gs, Lau
   }
 }
 
-void run_schedule(const Schedule& s, cudaStream_t st, const StreamSet* gs) {
+template <typename T>
+void run_schedule(const ScheduleT<T>& s, cudaStream_t st, const StreamSet* gs) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_tile_task, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
+    cudaFuncSetAttribute(k_tile_task<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
     attr = true;
   }
-  run_groups(s, st, gs, [&](const Schedule::Step& step, cudaStream_t stream) {
-    k_tile_task<<<step.count, 256, TILE_SMEM, stream>>>(s.d_gemm + step.first, g_active, g_notspd);
+  run_groups(s, st, gs, [&](const SchedStep& step, cudaStream_t stream) {
+    k_tile_task<T><<<step.count, 256, TILE_SMEM, stream>>>(s.d_gemm + step.first, g_active, g_notspd);
   });
 }
 
-void run_solve_mv(const SolveSchedule& s, cudaStream_t st, int src, int dst, int gather_neg, int width,
-                  const StreamSet* gs) {
-  run_groups(s, st, gs, [&](const SolveSchedule::Step& step, cudaStream_t stream) {
+template <typename T>
+void run_solve_mv(const SolveScheduleT<T>& s, cudaStream_t st, int src, int dst, int gather_neg, int width,
+                  const StreamSet* gs, int scatter_add) {
+  run_groups(s, st, gs, [&](const SchedStep& step, cudaStream_t stream) {
     if (width == KB)
-      k_solve_step<KB><<<step.count, 256, 0, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
-                                                       gather_neg);
+      k_solve_step<T, KB><<<step.count, 256, 0, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
+                                                          gather_neg, scatter_add);
     else
-      k_solve_step<PST><<<step.count, 256, 0, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
-                                                        gather_neg);
+      k_solve_step<T, PST><<<step.count, 256, 0, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
+                                                           gather_neg, scatter_add);
   });
 }
+
+template void run_schedule<double>(const ScheduleT<double>&, cudaStream_t, const StreamSet*);
+template void run_schedule<float>(const ScheduleT<float>&, cudaStream_t, const StreamSet*);
+template void run_solve_mv<double>(const SolveScheduleT<double>&, cudaStream_t, int, int, int, int,
+                                   const StreamSet*, int);
+template void run_solve_mv<float>(const SolveScheduleT<float>&, cudaStream_t, int, int, int, int,
+                                  const StreamSet*, int);

@@ -613,3 +613,37 @@ void launch_theta_axpy(msgfem* h, int wx, int wy, int wd, int p) {
   dim3 grid(256, h->N);
   k_theta_axpy<<<grid, 256, 0, h->stream>>>(h->d_sub, act(h), wx, wy, wd, p); ++g_launch_count;
 }
+
+namespace {
+// D = X - Y on multivectors of the same stride (rows of all subdomains)
+__global__ void k_x_minus_y(const SubDev* __restrict__ subs, const int* __restrict__ active, int wx, int wy,
+                            int wd, int stride) {
+  const int sidx = blockIdx.y;
+  if (active != nullptr && !active[sidx]) return;
+  const SubDev& s = subs[sidx];
+  const double* X = mv_ptr(s, wx);
+  const double* Yv = mv_ptr(s, wy);
+  double* D = mv_ptr(s, wd);
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)s.nfull * stride;
+       e += (size_t)gridDim.x * blockDim.x)
+    D[e] = X[e] - Yv[e];
+}
+
+// X[:, 0] -= bload (KB-wide block)
+__global__ void k_sub_load_kb(const SubDev* __restrict__ subs, int which) {
+  const SubDev& s = subs[blockIdx.y];
+  double* X = mv_ptr(s, which);
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < s.nfull; r += gridDim.x * blockDim.x)
+    X[(size_t)r * KB] -= s.bload[r];
+}
+}  // namespace
+
+void launch_x_minus_y(msgfem* h, int wx, int wy, int wd, int stride) {
+  dim3 grid(256, h->N);
+  k_x_minus_y<<<grid, 256, 0, h->stream>>>(h->d_sub, act(h), wx, wy, wd, stride); ++g_launch_count;
+}
+
+void launch_sub_load_kb(msgfem* h, int which) {
+  dim3 grid(64, h->N);
+  k_sub_load_kb<<<grid, 256, 0, h->stream>>>(h->d_sub, which); ++g_launch_count;
+}

@@ -198,10 +198,12 @@ msgfem_status build_problem(msgfem* h) {
 // same key are launched together; within a step the longest tasks go first.
 namespace {
 
-using FactorKeys = std::map<long long, std::vector<GemmTask>>;
+template <typename T>
+using FactorKeysT = std::map<long long, std::vector<TileTaskT<T>>>;
+using FactorKeys = FactorKeysT<double>;
 
-void add_matrix_tasks(FactorKeys& fk, double* D, double* E, double* L, int b, int nL, int sub, int Tmax,
-                      long long skew = 0) {
+template <typename Sc>
+void add_matrix_tasks(FactorKeysT<Sc>& fk, Sc* D, Sc* E, Sc* L, int b, int nL, int sub, int Tmax, long long skew = 0) {
   const int T = b / TILE;
   const long long per_layer = 3LL * Tmax + 1;
   auto tileD = [&](int l, int i, int j) { return D + (size_t)l * b * b + (size_t)i * TILE * b + (size_t)j * TILE; };
@@ -244,7 +246,8 @@ void add_matrix_tasks(FactorKeys& fk, double* D, double* E, double* L, int b, in
   }
 }
 
-void flatten(FactorKeys& fk, Schedule& sch, bool append = false) {
+template <typename T>
+void flatten(FactorKeysT<T>& fk, ScheduleT<T>& sch, bool append = false) {
   if (!append) {
     sch.steps.clear();
     sch.gemm.clear();
@@ -254,7 +257,7 @@ void flatten(FactorKeys& fk, Schedule& sch, bool append = false) {
     auto& v = kv.second;
     if (v.empty()) continue;
     // POTRF tasks (short critical path) and then the longest GEMM tasks first
-    std::stable_sort(v.begin(), v.end(), [](const GemmTask& x, const GemmTask& y) {
+    std::stable_sort(v.begin(), v.end(), [](const TileTaskT<T>& x, const TileTaskT<T>& y) {
       const int px = (x.flags & G_POTRF) ? 1 : 0, py = (y.flags & G_POTRF) ? 1 : 0;
       if (px != py) return px > py;
       return x.K > y.K;
@@ -265,13 +268,14 @@ void flatten(FactorKeys& fk, Schedule& sch, bool append = false) {
 }
 
 // Solve schedule of one matrix kind over all subdomains.
-void add_solve_tasks(std::map<long long, std::vector<SolveTask>>& keys, double* E, double* L, double* yc, double* rc,
+template <typename Sc>
+void add_solve_tasks(std::map<long long, std::vector<SolveTaskT<Sc>>>& keys, Sc* E, Sc* L, Sc* yc, Sc* rc,
                      const int* map, int b, int nL, int npl, int sub, int PW, long long skew = 0) {
   const int T = b / TILE;
   for (int l = 0; l < nL; ++l) {
     const int row_off = l * 3 * npl;
     for (int i = 0; i < T; ++i) {
-      SolveTask f1{};
+      SolveTaskT<Sc> f1{};
       f1.C = rc + (size_t)i * TILE * PW;
       f1.gmap = map + i * TILE;
       f1.row_off = row_off;
@@ -285,7 +289,7 @@ void add_solve_tasks(std::map<long long, std::vector<SolveTask>>& keys, double* 
         f1.flags |= S_NEG;
       }
       keys[2LL * l + skew].push_back(f1);
-      SolveTask f2{};
+      SolveTaskT<Sc> f2{};
       f2.C = yc + (size_t)l * b * PW + (size_t)i * TILE * PW;
       f2.A = L + (size_t)l * b * b + (size_t)i * TILE * b;
       f2.B = rc;
@@ -299,7 +303,7 @@ void add_solve_tasks(std::map<long long, std::vector<SolveTask>>& keys, double* 
     const long long kb = 2LL * nL + 1 + 2LL * (nL - 1 - l) + skew;
     const int row_off = l * 3 * npl;
     for (int i = 0; i < T; ++i) {
-      SolveTask b1{};
+      SolveTaskT<Sc> b1{};
       b1.C = rc + (size_t)i * TILE * PW;
       b1.init = yc + (size_t)l * b * PW + (size_t)i * TILE * PW;
       b1.flags = S_INIT_TILE;
@@ -312,7 +316,7 @@ void add_solve_tasks(std::map<long long, std::vector<SolveTask>>& keys, double* 
         b1.flags |= S_TRANSA | S_NEG;
       }
       keys[kb].push_back(b1);
-      SolveTask b2{};
+      SolveTaskT<Sc> b2{};
       b2.C = yc + (size_t)l * b * PW + (size_t)i * TILE * PW;
       b2.A = L + (size_t)l * b * b + (size_t)i * TILE * b + (size_t)i * TILE;
       b2.B = rc + (size_t)i * TILE * PW;
@@ -327,7 +331,9 @@ void add_solve_tasks(std::map<long long, std::vector<SolveTask>>& keys, double* 
   }
 }
 
-void flatten_solve(std::map<long long, std::vector<SolveTask>>& keys, SolveSchedule& sch, bool append = false) {
+template <typename T>
+void flatten_solve(std::map<long long, std::vector<SolveTaskT<T>>>& keys, SolveScheduleT<T>& sch,
+                   bool append = false) {
   if (!append) {
     sch.steps.clear();
     sch.tasks.clear();
@@ -337,7 +343,7 @@ void flatten_solve(std::map<long long, std::vector<SolveTask>>& keys, SolveSched
     if (kv.second.empty()) continue;
     // longest tasks first: CTAs are dispatched in launch order (LPT balance)
     std::stable_sort(kv.second.begin(), kv.second.end(),
-                     [](const SolveTask& x, const SolveTask& y) { return x.K > y.K; });
+                     [](const SolveTaskT<T>& x, const SolveTaskT<T>& y) { return x.K > y.K; });
     sch.steps.back().push_back({(int)sch.tasks.size(), (int)kv.second.size()});
     sch.tasks.insert(sch.tasks.end(), kv.second.begin(), kv.second.end());
   }
@@ -353,6 +359,19 @@ void build_factor_schedule(msgfem* h) {
   int Tmax = 1;
   for (const auto& s : h->sub) Tmax = std::max(Tmax, std::max(s.bK, s.bA) / TILE);
   const int ng = h->ngroup;
+  if (h->mixed) {
+    std::vector<FactorKeysT<float>> fk(ng);
+    int chain = 0;
+    for (int j = 0; j < h->N; ++j) {
+      SubDev& s = h->sub[j];
+      add_matrix_tasks(fk[chain++ % ng], s.DKf, s.EKf, s.LKf, s.bK, s.nzn, j, Tmax);
+      add_matrix_tasks(fk[chain++ % ng], s.DAf, s.EAf, s.LAf, s.bA, s.nzn, j, Tmax);
+    }
+    h->factf.steps.clear();
+    h->factf.gemm.clear();
+    for (int g = 0; g < ng; ++g) flatten(fk[g], h->factf, true);
+    return;
+  }
   std::vector<FactorKeys> fk(ng);
   int chain = 0;
   for (int j = 0; j < h->N; ++j) {
@@ -365,28 +384,46 @@ void build_factor_schedule(msgfem* h) {
   for (int g = 0; g < ng; ++g) flatten(fk[g], h->fact, true);
 }
 
-void build_solve_schedules(msgfem* h) {
-  // subdomains dealt into NGROUP groups (streams) as well
+template <typename T>
+void build_solves_t(msgfem* h, SolveScheduleT<T>& sK, SolveScheduleT<T>& sA, SolveScheduleT<T>& sK8,
+                    SolveScheduleT<T>& sA8, bool f32) {
   const int ng = h->ngroup;
-  std::vector<std::map<long long, std::vector<SolveTask>>> kk(ng), ka(ng), kk8(ng), ka8(ng);
+  using Keys = std::map<long long, std::vector<SolveTaskT<T>>>;
+  std::vector<Keys> kk(ng), ka(ng), kk8(ng), ka8(ng);
   for (int j = 0; j < h->N; ++j) {
     SubDev& s = h->sub[j];
     const int g = j % ng;
-    add_solve_tasks(kk[g], s.EK, s.LK, s.ycK, s.rcK, s.mapK, s.bK, s.nzn, s.npl, j, PST);
-    add_solve_tasks(ka[g], s.EA, s.LA, s.ycA, s.rcA, s.mapA, s.bA, s.nzn, s.npl, j, PST);
-    add_solve_tasks(kk8[g], s.EK, s.LK, s.ycK8, s.rcK8, s.mapK, s.bK, s.nzn, s.npl, j, KB);
-    add_solve_tasks(ka8[g], s.EA, s.LA, s.ycA8, s.rcA8, s.mapA, s.bA, s.nzn, s.npl, j, KB);
+    T* EK = f32 ? (T*)s.EKf : (T*)s.EK;
+    T* LK = f32 ? (T*)s.LKf : (T*)s.LK;
+    T* EA = f32 ? (T*)s.EAf : (T*)s.EA;
+    T* LA = f32 ? (T*)s.LAf : (T*)s.LA;
+    add_solve_tasks(kk[g], EK, LK, f32 ? (T*)s.ycKf : (T*)s.ycK, f32 ? (T*)s.rcKf : (T*)s.rcK, s.mapK, s.bK, s.nzn,
+                    s.npl, j, PST);
+    add_solve_tasks(ka[g], EA, LA, f32 ? (T*)s.ycAf : (T*)s.ycA, f32 ? (T*)s.rcAf : (T*)s.rcA, s.mapA, s.bA, s.nzn,
+                    s.npl, j, PST);
+    add_solve_tasks(kk8[g], EK, LK, f32 ? (T*)s.ycK8f : (T*)s.ycK8, f32 ? (T*)s.rcK8f : (T*)s.rcK8, s.mapK, s.bK,
+                    s.nzn, s.npl, j, KB);
+    add_solve_tasks(ka8[g], EA, LA, f32 ? (T*)s.ycA8f : (T*)s.ycA8, f32 ? (T*)s.rcA8f : (T*)s.rcA8, s.mapA, s.bA,
+                    s.nzn, s.npl, j, KB);
   }
-  for (SolveSchedule* ss : {&h->solveK, &h->solveA, &h->solveK8, &h->solveA8}) {
+  for (SolveScheduleT<T>* ss : {&sK, &sA, &sK8, &sA8}) {
     ss->steps.clear();
     ss->tasks.clear();
   }
   for (int g = 0; g < ng; ++g) {
-    flatten_solve(kk[g], h->solveK, true);
-    flatten_solve(ka[g], h->solveA, true);
-    flatten_solve(kk8[g], h->solveK8, true);
-    flatten_solve(ka8[g], h->solveA8, true);
+    flatten_solve(kk[g], sK, true);
+    flatten_solve(ka[g], sA, true);
+    flatten_solve(kk8[g], sK8, true);
+    flatten_solve(ka8[g], sA8, true);
   }
+}
+
+// Subdomains are dealt into the stream groups as well.
+void build_solve_schedules(msgfem* h) {
+  if (h->mixed)
+    build_solves_t<float>(h, h->solveKf, h->solveAf, h->solveK8f, h->solveA8f, true);
+  else
+    build_solves_t<double>(h, h->solveK, h->solveA, h->solveK8, h->solveA8, false);
 }
 
 // Coarse matrix: one dense block of size NcPad, factorised by the same tile
@@ -395,7 +432,7 @@ void build_solve_schedules(msgfem* h) {
 void build_coarse_schedules(msgfem* h) {
   FactorKeys fk;
   const int b = h->NcPad;
-  add_matrix_tasks(fk, h->d_AH, nullptr, h->d_AHinv, b, 1, h->N, b / TILE);
+  add_matrix_tasks<double>(fk, h->d_AH, nullptr, h->d_AHinv, b, 1, h->N, b / TILE);
   flatten(fk, h->cfact);
   const int T = b / TILE;
   std::map<long long, std::vector<SolveTask>> keys;

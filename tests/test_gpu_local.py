@@ -37,12 +37,12 @@ def gap_sizes(lam_ext, n):
     return out
 
 
-def run_case(name, seed=7, tol_lam=1e-8, tol_angle=1e-5, solver=0):
+def run_case(name, seed=7, tol_lam=1e-8, tol_angle=1e-5, solver=0, precision=0):
     cfg = get_config(name)
     ang = element_angles(cfg)
     ref = run_msgfem(cfg, angles=ang, n_loc=cfg.n_loc + 1)        # one more to locate the gap at n_loc
     ref_n = run_msgfem(cfg, angles=ang, uh=None)
-    m = _msgfem().from_config(cfg, ang, seed=seed, solver=solver)
+    m = _msgfem().from_config(cfg, ang, seed=seed, solver=solver, precision=precision)
     lam = m.local_spaces(cfg.n_loc)
     nc = m.coarse_assemble()
     _, err = m.solve(u_ref=ref_n.uh)
@@ -68,6 +68,13 @@ def run_case(name, seed=7, tol_lam=1e-8, tol_angle=1e-5, solver=0):
 def test_local_stage_parity(name):
     """Block Krylov eigensolver (the default)."""
     run_case(name)
+
+
+@pytest.mark.parametrize("name", ["t1", "t2", "t3", "t4", "c1"])
+def test_local_stage_parity_mixed(name):
+    """Mixed precision: FP32 factors and solves with FP64 refinement; the
+    eigenvalue target for this path is 1e-5 relative."""
+    run_case(name, precision=1, tol_lam=1e-5, tol_angle=1e-4)
 
 
 @pytest.mark.parametrize("name", ["t2", "c1"])
