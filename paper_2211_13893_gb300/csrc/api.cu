@@ -316,19 +316,48 @@ double solve_flops(const msgfem* h, int mat, int p) {
   return f;
 }
 
+// Replay the graph stored under `key`, capturing it on the private stream the
+// first time: a schedule of thousands of small launches becomes one launch.
+// The kernel-node count is added to the launch counter on every replay.
+template <typename Issue>
+void run_graph(msgfem* h, uint64_t key, Issue issue) {
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    const long long before = g_launch_count;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+    issue(h->cap);
+    cudaStreamEndCapture(h->cap, &g);
+    if (g) {
+      cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+    }
+    const long long nodes = g_launch_count - before;
+    g_launch_count = before;
+    it = h->graphs.emplace(key, std::make_pair(ex, nodes)).first;
+  }
+  if (it->second.first) cudaGraphLaunch(it->second.first, h->stream);
+  g_launch_count += it->second.second;
+}
+
 // One block solve (K: mat 0, A11: mat 1) of PST or KB right-hand sides in the
 // handle's precision; add = 1 accumulates into the destination.
 void timed_solve_w(msgfem* h, int mat, int src, int dst, int neg, int width, int add) {
   const int sp = span_begin(h, TAG_SOLVE);
-  if (h->mixed) {
-    const SolveScheduleT<float>& sc = width == KB ? (mat == 0 ? h->solveK8f : h->solveA8f)
-                                                  : (mat == 0 ? h->solveKf : h->solveAf);
-    run_solve_mv(sc, h->stream, src, dst, neg, width, &h->gs, add);
-  } else {
-    const SolveScheduleT<double>& sc = width == KB ? (mat == 0 ? h->solveK8 : h->solveA8)
-                                                   : (mat == 0 ? h->solveK : h->solveA);
-    run_solve_mv(sc, h->stream, src, dst, neg, width, &h->gs, add);
-  }
+  const uint64_t key = ((uint64_t)1 << 60) | ((uint64_t)mat << 40) | ((uint64_t)width << 32) |
+                       ((uint64_t)src << 16) | ((uint64_t)dst << 4) | ((uint64_t)neg << 1) | (uint64_t)add;
+  run_graph(h, key, [&](cudaStream_t cs) {
+    if (h->mixed) {
+      const SolveScheduleT<float>& sc = width == KB ? (mat == 0 ? h->solveK8f : h->solveA8f)
+                                                    : (mat == 0 ? h->solveKf : h->solveAf);
+      run_solve_mv(sc, cs, src, dst, neg, width, &h->gs, add);
+    } else {
+      const SolveScheduleT<double>& sc = width == KB ? (mat == 0 ? h->solveK8 : h->solveA8)
+                                                     : (mat == 0 ? h->solveK : h->solveA);
+      run_solve_mv(sc, cs, src, dst, neg, width, &h->gs, add);
+    }
+  });
   span_end(h, sp);
   h->prof.solve_flops += solve_flops(h, mat, width == KB ? KB : h->p);
   h->prof.solve_calls += 1;
@@ -621,6 +650,8 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
     CK(cudaEventCreateWithFlags(&h->gs.join[g], cudaEventDisableTiming));
   }
   CK(cudaEventCreateWithFlags(&h->gs.fork, cudaEventDisableTiming));
+  CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  prepare_tile_kernels();
   set_dense_context(h->d_flags, h->d_notspd, h->d_sub);
   h->stage = 1;
   return MSGFEM_OK;
@@ -666,8 +697,10 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   CK_LAUNCH();
   // 2. factorisations of K and A11
   sp = span_begin(h, TAG_FACTOR);
-  if (h->mixed) run_schedule(h->factf, st, &h->gs);
-  else run_schedule(h->fact, st, &h->gs);
+  run_graph(h, (uint64_t)2 << 60, [&](cudaStream_t cs) {
+    if (h->mixed) run_schedule(h->factf, cs, &h->gs);
+    else run_schedule(h->fact, cs, &h->gs);
+  });
   span_end(h, sp);
   CK_LAUNCH();
   const int sp_iter = span_begin(h, TAG_ITERATE);
@@ -935,6 +968,9 @@ void msgfem_destroy(msgfem_h h) {
     if (h->gs.join[g]) cudaEventDestroy(h->gs.join[g]);
   }
   if (h->gs.fork) cudaEventDestroy(h->gs.fork);
+  for (auto& kv : h->graphs)
+    if (kv.second.first) cudaGraphExecDestroy(kv.second.first);
+  if (h->cap) cudaStreamDestroy(h->cap);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
 }

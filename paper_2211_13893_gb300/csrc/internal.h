@@ -15,7 +15,9 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "msgfem.h"
@@ -120,6 +122,7 @@ struct SolveScheduleT {
   std::vector<std::vector<Step>> steps;
   std::vector<SolveTaskT<T>> tasks;
   SolveTaskT<T>* d_tasks = nullptr;
+  int kmax = 0;   // largest inner dimension of a task (shared-memory sizing)
 };
 using SolveSchedule = SolveScheduleT<double>;
 
@@ -146,6 +149,8 @@ struct msgfem {
   msgfem_options opt;
   cudaStream_t stream = nullptr;
   StreamSet gs;                      // streams of independent schedule groups
+  cudaStream_t cap = nullptr;        // private stream on which schedules are captured as graphs
+  std::map<uint64_t, std::pair<cudaGraphExec_t, long long>> graphs;   // key -> (graph, kernel nodes)
   int ngroup = NGROUP;               // groups in use (msgfem_options.streams)
   int N = 0;
   int layered = 0, ntypes = 0, type_cap = 0;
@@ -212,6 +217,7 @@ void build_coarse_schedules(msgfem* h);
 
 // launchers
 void set_dense_context(int* active, int* notspd, const SubDev* subs);
+void prepare_tile_kernels();
 template <typename T>
 void run_schedule(const ScheduleT<T>& s, cudaStream_t st, const StreamSet* gs = nullptr);
 // solve steps; scatter_add adds the result into the destination multivector

@@ -249,6 +249,179 @@ k_solve_step(const SolveTaskT<T>* __restrict__ tasks, const SubDev* __restrict__
   }
 }
 
+// Streaming variant of the solve step for KB right-hand sides: the small
+// B block (K x KB) is staged once in shared memory (rows padded by one 16-byte
+// vector so that the vector reads of neighbouring rows fall in distinct bank
+// groups) and every thread streams its part of the factor block A with
+// independent coalesced loads, so that many loads are in flight (the solves
+// are bound by memory, not arithmetic).
+//   plain A:      lane <-> k, each warp owns 8 rows (R at a time), the partial
+//                 sums are reduced with warp shuffles;
+//   transposed A: thread <-> (16-byte vector of output rows, k group), the k
+//                 groups are summed through shared memory.
+// The staging area is reused for the reduction after a barrier.
+template <typename T> struct SolveVec;
+template <> struct SolveVec<float> { using V = float4; static constexpr int N = 4; };
+template <> struct SolveVec<double> { using V = double2; static constexpr int N = 2; };
+
+template <typename T>
+__device__ __forceinline__ void load_row_kb(const T* p, T (&b)[KB]) {
+  using V = typename SolveVec<T>::V;
+  constexpr int N = SolveVec<T>::N;
+#pragma unroll
+  for (int j = 0; j < KB / N; ++j) {
+    const V v = reinterpret_cast<const V*>(p)[j];
+    if constexpr (N == 4) {
+      b[4 * j] = v.x; b[4 * j + 1] = v.y; b[4 * j + 2] = v.z; b[4 * j + 3] = v.w;
+    } else {
+      b[2 * j] = v.x; b[2 * j + 1] = v.y;
+    }
+  }
+}
+
+template <typename T>
+__host__ __device__ constexpr int solve_bst() { return KB + SolveVec<T>::N; }
+template <typename T>
+__host__ __device__ constexpr int solve_kg() { return 256 / (64 / SolveVec<T>::N); }
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_solve_stream(const SolveTaskT<T>* __restrict__ tasks, const SubDev* __restrict__ subs,
+               const int* __restrict__ active, int src, int dst, int gather_neg, int scatter_add) {
+  constexpr int BST = solve_bst<T>();
+  constexpr int VN = SolveVec<T>::N;
+  constexpr int TPR = 64 / VN;          // threads across the 64 output rows (transposed A)
+  constexpr int KG = 256 / TPR;         // k groups (transposed A)
+  constexpr int R = sizeof(T) == 4 ? 8 : 4;   // rows per pass (plain A)
+  constexpr int NP = 8 / R;
+  using V = typename SolveVec<T>::V;
+  const SolveTaskT<T> t = tasks[blockIdx.x];
+  if (t.sub >= 0 && active != nullptr && !active[t.sub]) return;
+  extern __shared__ double smem_s[];
+  T* Bs = reinterpret_cast<T*>(smem_s);     // [K][BST], later [64][KB] or [KG][64][KB]
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int e = tid; e < t.K * KB; e += 256) Bs[(e / KB) * BST + e % KB] = t.B[e];
+  __syncthreads();
+  const bool transA = (t.flags & S_TRANSA) != 0;
+  static_assert(8 * KB == 64, "the plain-A reduction assumes KB == 8");
+  T res[2] = {(T)0, (T)0};
+  if (!transA) {
+#pragma unroll
+    for (int g = 0; g < NP; ++g) {
+      const int r0 = w * 8 + g * R;
+      T acc[R][KB];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < KB; ++c) acc[r][c] = (T)0;
+      const T* a0 = t.A + (size_t)r0 * t.lda;
+      for (int k = lane; k < t.K; k += 64) {
+        const bool two = k + 32 < t.K;
+        T a[2][R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          a[0][r] = a0[(size_t)r * t.lda + k];
+          a[1][r] = two ? a0[(size_t)r * t.lda + k + 32] : (T)0;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          T b[KB];
+          load_row_kb<T>(Bs + (size_t)(two || h == 0 ? k + 32 * h : k) * BST, b);
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < KB; ++c) acc[r][c] = fma(a[h][r], b[c], acc[r][c]);
+        }
+      }
+      // every lane holds all R x KB sums after the butterfly; lane L keeps
+      // entries L and L + 32 of the 8 x KB block of its warp (rows 4j + L / KB)
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < KB; ++c) {
+          T v = acc[r][c];
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+          const int idx = g * R * KB + r * KB + c;
+          if (lane == idx % 32) res[idx / 32] = v;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 2; ++j) Bs[(w * 8 + 4 * j + lane / KB) * KB + lane % KB] = res[j];
+  } else {
+    const int mv = tid % TPR, kg = tid / TPR;
+    T acc[VN][KB];
+#pragma unroll
+    for (int v = 0; v < VN; ++v)
+#pragma unroll
+      for (int c = 0; c < KB; ++c) acc[v][c] = (T)0;
+    const T* a0 = t.A + mv * VN;
+#pragma unroll 4
+    for (int k = kg; k < t.K; k += KG) {
+      const V av = *reinterpret_cast<const V*>(a0 + (size_t)k * t.lda);
+      T a[VN];
+      if constexpr (VN == 4) {
+        a[0] = av.x; a[1] = av.y; a[2] = av.z; a[3] = av.w;
+      } else {
+        a[0] = av.x; a[1] = av.y;
+      }
+      T b[KB];
+      load_row_kb<T>(Bs + (size_t)k * BST, b);
+#pragma unroll
+      for (int v = 0; v < VN; ++v)
+#pragma unroll
+        for (int c = 0; c < KB; ++c) acc[v][c] = fma(a[v], b[c], acc[v][c]);
+    }
+    __syncthreads();
+    T* red = Bs;
+#pragma unroll
+    for (int v = 0; v < VN; ++v)
+#pragma unroll
+      for (int c = 0; c < KB; ++c) red[((size_t)kg * 64 + mv * VN + v) * KB + c] = acc[v][c];
+  }
+  __syncthreads();
+  const T sgn = (t.flags & S_NEG) ? (T)-1 : (T)1;
+  const double* gfull = nullptr;
+  double* sfull = nullptr;
+  if (t.flags & (S_INIT_GATHER | S_SCATTER)) {
+    const SubDev& s = subs[t.sub];
+    if (t.flags & S_INIT_GATHER) gfull = mv_ptr(s, src) + (size_t)t.row_off * KB;
+    if (t.flags & S_SCATTER) sfull = mv_ptr(s, dst) + (size_t)t.row_off * KB;
+  }
+  const double gs = gather_neg ? -1.0 : 1.0;
+  for (int e = tid; e < 64 * KB; e += 256) {
+    const int r = e / KB, c = e % KB;
+    T v;
+    if (transA) {
+      v = (T)0;
+#pragma unroll
+      for (int q = 0; q < KG; ++q) v += Bs[(size_t)q * 64 * KB + e];
+    } else {
+      v = Bs[e];
+    }
+    v = sgn * v;
+    if (t.flags & S_INIT_TILE) v += t.init[r * KB + c];
+    const int gmr = (t.flags & S_INIT_GATHER) ? t.gmap[r] : -1;
+    if (gmr >= 0) v += (T)(gs * gfull[(size_t)gmr * KB + c]);
+    t.C[r * KB + c] = v;
+    const int smr = (t.flags & S_SCATTER) ? t.smap[r] : -1;
+    if (smr >= 0) {
+      double* o = sfull + (size_t)smr * KB + c;
+      *o = scatter_add ? *o + (double)v : (double)v;
+    }
+  }
+}
+
+constexpr size_t SOLVE_SMEM_MAX = 200 * 1024;
+
+template <typename T>
+size_t solve_stream_smem(int kmax) {
+  const size_t stage = (size_t)kmax * solve_bst<T>();
+  const size_t red = (size_t)solve_kg<T>() * 64 * KB;
+  return (stage > red ? stage : red) * sizeof(T);
+}
+
 }  // namespace
 
 long long g_launch_count = 0;
@@ -289,13 +462,21 @@ static void run_groups(const Sched& s, cudaStream_t st, const StreamSet* gs, Lau
   }
 }
 
+// Dynamic shared memory above 48 KiB must be enabled before the first launch
+// (and before any stream capture of one).
+void prepare_tile_kernels() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(k_tile_task<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
+  cudaFuncSetAttribute(k_tile_task<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
+  cudaFuncSetAttribute(k_solve_stream<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
+  cudaFuncSetAttribute(k_solve_stream<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
+  done = true;
+}
+
 template <typename T>
 void run_schedule(const ScheduleT<T>& s, cudaStream_t st, const StreamSet* gs) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_tile_task<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
-    attr = true;
-  }
+  prepare_tile_kernels();
   run_groups(s, st, gs, [&](const SchedStep& step, cudaStream_t stream) {
     k_tile_task<T><<<step.count, 256, TILE_SMEM, stream>>>(s.d_gemm + step.first, g_active, g_notspd);
   });
@@ -304,8 +485,14 @@ void run_schedule(const ScheduleT<T>& s, cudaStream_t st, const StreamSet* gs) {
 template <typename T>
 void run_solve_mv(const SolveScheduleT<T>& s, cudaStream_t st, int src, int dst, int gather_neg, int width,
                   const StreamSet* gs, int scatter_add) {
+  prepare_tile_kernels();
+  const size_t smem = solve_stream_smem<T>(s.kmax);
+  const bool stream_ok = smem <= SOLVE_SMEM_MAX;
   run_groups(s, st, gs, [&](const SchedStep& step, cudaStream_t stream) {
-    if (width == KB)
+    if (width == KB && stream_ok)
+      k_solve_stream<T><<<step.count, 256, smem, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
+                                                           gather_neg, scatter_add);
+    else if (width == KB)
       k_solve_step<T, KB><<<step.count, 256, 0, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
                                                           gather_neg, scatter_add);
     else

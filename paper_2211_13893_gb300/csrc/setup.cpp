@@ -337,6 +337,7 @@ void flatten_solve(std::map<long long, std::vector<SolveTaskT<T>>>& keys, SolveS
   if (!append) {
     sch.steps.clear();
     sch.tasks.clear();
+    sch.kmax = 0;
   }
   sch.steps.emplace_back();
   for (auto& kv : keys) {
@@ -345,6 +346,7 @@ void flatten_solve(std::map<long long, std::vector<SolveTaskT<T>>>& keys, SolveS
     std::stable_sort(kv.second.begin(), kv.second.end(),
                      [](const SolveTaskT<T>& x, const SolveTaskT<T>& y) { return x.K > y.K; });
     sch.steps.back().push_back({(int)sch.tasks.size(), (int)kv.second.size()});
+    for (const auto& t : kv.second) sch.kmax = std::max(sch.kmax, t.K);
     sch.tasks.insert(sch.tasks.end(), kv.second.begin(), kv.second.end());
   }
 }
@@ -409,6 +411,7 @@ void build_solves_t(msgfem* h, SolveScheduleT<T>& sK, SolveScheduleT<T>& sA, Sol
   for (SolveScheduleT<T>* ss : {&sK, &sA, &sK8, &sA8}) {
     ss->steps.clear();
     ss->tasks.clear();
+    ss->kmax = 0;
   }
   for (int g = 0; g < ng; ++g) {
     flatten_solve(kk[g], sK, true);
