@@ -26,6 +26,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk x 2 flop x max SM clock (derived, 1.26)
+
+
+def _hbm_peak():
+    """Measured copy bandwidth of the GB300s (GB/s), else the fallback."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "of fallback (6.8 TB/s)"
 METRIC = "local eigensolves/s on 1 GB300 at fixed energy-norm error: plain FP64 vs mixed+warm"
 L2_BYTES = 129 * 2 ** 20
 
@@ -232,7 +241,9 @@ def run_ours(args):
             "time_share": share,
             "factor": {"tflops": fact_tf, "ms_per_step": prof["factor_ms"] / args.steps},
             "solve": {"tflops": solve_tf, "ms_per_step": prof["solve_ms"] / args.steps,
-                      "calls_per_step": prof["solve_calls"]},
+                      "calls_per_step": prof["solve_calls"],
+                      "gbs": prof["solve_bytes"] * args.steps / (prof["solve_ms"] / 1000.0) / 1e9
+                      if prof["solve_ms"] else None},
             "iterate_ms_per_step": prof["iterate_ms"] / args.steps,
             "assemble_ms_per_step": prof["assemble_ms"] / args.steps,
             "coarse_ms_per_step": prof["coarse_ms"] / args.steps}
@@ -327,13 +338,20 @@ def run_mixed(args, cfg, ang_dev, stream, dev, rank, lam_fp64, u_fp64, flush, wo
         total = float(t.item())
     e = C.c_double(-1.0)
     m.lib.msgfem_energy_error_noalloc(m.h, u.data_ptr(), u_fp64.data_ptr(), C.addressof(e))
+    hbm, hbm_note = _hbm_peak()
+    solve_gbs = prof["solve_bytes"] * args.steps / (prof["solve_ms"] / 1000.0) / 1e9 if prof["solve_ms"] else 0.0
     rel = ((lam - lam_fp64).abs() / lam_fp64.abs().amax(dim=1, keepdim=True).clamp_min(1e-2)).max().item()
     out = {"value": world * m.N * args.steps / (total / 1000.0), "unit": "subdomains/s",
            "ms_per_step": total / args.steps, "dtype": "f32 factors/solves + f64 refinement/RR/coarse",
            "factor_ms_per_step": prof["factor_ms"] / args.steps, "solve_ms_per_step": prof["solve_ms"] / args.steps,
            "factor_tflops": prof["factor_flops"] * args.steps / (prof["factor_ms"] / 1000.0) / 1e12
            if prof["factor_ms"] else None,
-           "eig_rel_diff_vs_fp64": rel, "energy_norm_diff_vs_fp64": e.value}
+           "eig_rel_diff_vs_fp64": rel, "energy_norm_diff_vs_fp64": e.value,
+           "roofline": {"bound": "hbm", "achieved": solve_gbs, "peak": hbm, "unit": "GB/s",
+                        "frac": solve_gbs / hbm, "peak_note": hbm_note,
+                        "kernel": "k_solve_stream (FP32 block solves, 8 right-hand sides)",
+                        "time_share": prof["solve_ms"] / total if total else None,
+                        "calls_per_step": prof["solve_calls"]}}
     m.close()
     return out
 

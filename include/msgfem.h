@@ -117,6 +117,13 @@ typedef struct {
   double solve_flops;   /* per local stage, all solve calls */
   long long launches;   /* kernel launches issued by the library (all calls) */
   int solve_calls;      /* block solves in the last local stage */
+  double solve_bytes;   /* per local stage, all solve calls: factor blocks read (the
+                           inverse diagonal blocks as triangles, the coupling blocks whole,
+                           forward and backward) in the factor's precision, plus the FP64
+                           right-hand side read and solution written */
+  double stencil_ms;    /* stencil products (K, B, K + sigma B) inside the iteration */
+  double ortho_ms;      /* Gram, block updates, CholeskyQR, basis rotations */
+  double stencil_flops; /* per local stage: 2 x 27 x 9 flop per node and column (x2 for K + sigma B) */
 } msgfem_profile;
 
 /* Per-subdomain diagnostics filled by msgfem_get_info. */

@@ -47,8 +47,6 @@ msgfem_status cuda_fail(msgfem* h, cudaError_t e, const char* what, const char* 
   return MSGFEM_ECUDA;
 }
 
-#define CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return cuda_fail(h, e_, #x, __FILE__, __LINE__); } while (0)
-#define CK_LAUNCH() CK(cudaGetLastError())
 
 namespace {
 
@@ -66,7 +64,6 @@ msgfem_status dalloc(msgfem* h, T** p, size_t count) {
   return MSGFEM_OK;
 }
 
-#define TRY(x) do { msgfem_status st_ = (x); if (st_ != MSGFEM_OK) return st_; } while (0)
 
 bool is_device_ptr(const void* p) {
   if (p == nullptr) return false;
@@ -255,7 +252,7 @@ msgfem_status read_sub_array(msgfem* h, int j, const T* dptr, T* out, size_t n) 
   return MSGFEM_OK;
 }
 
-enum { TAG_ASSEMBLE = 0, TAG_FACTOR, TAG_SOLVE, TAG_ITERATE, TAG_COARSE };
+enum { TAG_ASSEMBLE = 0, TAG_FACTOR, TAG_SOLVE, TAG_ITERATE, TAG_COARSE, TAG_STENCIL, TAG_ORTHO };
 
 cudaEvent_t take_event(msgfem* h) {
   if (!h->ev_pool.empty()) {
@@ -288,6 +285,7 @@ void spans_collect(msgfem* h) {
     cudaEventElapsedTime(&ms, sp.a, sp.b);
     double* dst = sp.tag == TAG_ASSEMBLE ? &h->prof.assemble_ms : sp.tag == TAG_FACTOR ? &h->prof.factor_ms
                 : sp.tag == TAG_SOLVE ? &h->prof.solve_ms : sp.tag == TAG_ITERATE ? &h->prof.iterate_ms
+                : sp.tag == TAG_STENCIL ? &h->prof.stencil_ms : sp.tag == TAG_ORTHO ? &h->prof.ortho_ms
                 : &h->prof.coarse_ms;
     *dst += ms;
     h->ev_pool.push_back(sp.a);
@@ -295,6 +293,38 @@ void spans_collect(msgfem* h) {
   }
   h->spans.clear();
 }
+
+// Stencil products (K, B = D_mu K D_mu and the N = S + sigma T products of the
+// Krylov solver) and the orthogonalisation kernels are timed as phases of
+// their own; the stencil flops count 2 x 27 x 9 per node and column (twice
+// that for the combined K + sigma B pass, mode 4).
+double stencil_flops(const msgfem* h, int width, int mode) {
+  double n = 0.0;
+  for (const auto& s : h->sub) n += s.nnode;
+  return n * 2.0 * 27.0 * 9.0 * width * (mode == 4 ? 2.0 : 1.0);
+}
+void timed_stencil_kb(msgfem* h, int src, int dst, int mode, double alpha) {
+  const int sp = span_begin(h, TAG_STENCIL);
+  launch_stencil_kb(h, src, dst, mode, alpha);
+  span_end(h, sp);
+  h->prof.stencil_flops += stencil_flops(h, KB, mode);
+}
+void timed_stencil_apply(msgfem* h, int src, int dst, int mode, double alpha) {
+  const int sp = span_begin(h, TAG_STENCIL);
+  launch_stencil_apply(h, src, dst, mode, alpha);
+  span_end(h, sp);
+  h->prof.stencil_flops += stencil_flops(h, PST, mode);
+}
+#define MSGFEM_TIMED_ORTHO(name, params, args) \
+  void timed_##name params { const int sp = span_begin(h, TAG_ORTHO); launch_##name args; span_end(h, sp); }
+MSGFEM_TIMED_ORTHO(gram_kb, (msgfem* h, int wx, int xs, int nx, int wy, int of), (h, wx, xs, nx, wy, of))
+MSGFEM_TIMED_ORTHO(update_kb, (msgfem* h, int wx, int xs, int nx, int wy, int of), (h, wx, xs, nx, wy, of))
+MSGFEM_TIMED_ORTHO(h_accum, (msgfem* h, int m, int j, int add), (h, m, j, add))
+MSGFEM_TIMED_ORTHO(cholqr_kb, (msgfem* h, int j, int pass), (h, j, pass))
+MSGFEM_TIMED_ORTHO(rotate_kb, (msgfem* h, int which), (h, which))
+MSGFEM_TIMED_ORTHO(gram, (msgfem* h, int wx, int wy, int wg), (h, wx, wy, wg))
+MSGFEM_TIMED_ORTHO(rotate, (msgfem* h, int which, int wy, int ncols), (h, which, wy, ncols))
+#undef MSGFEM_TIMED_ORTHO
 
 // algorithmic flops of the layer-block factorisation (unpadded sizes)
 double factor_flops(const msgfem* h) {
@@ -314,6 +344,19 @@ double solve_flops(const msgfem* h, int mat, int p) {
     f += (4.0 * (s.nzn - 1) + 2.0 * s.nzn) * n * n * p;
   }
   return f;
+}
+
+// algorithmic bytes of one block solve: the inverse diagonal blocks (lower
+// triangles) and coupling blocks read forward and backward, plus the FP64
+// right-hand side read and the solution written
+double solve_bytes(const msgfem* h, int mat, int p) {
+  double b = 0.0;
+  const double es = h->mixed ? 4.0 : 8.0;
+  for (const auto& s : h->sub) {
+    const double n = mat == 0 ? s.nK : s.nA;
+    b += 2.0 * (s.nzn * n * (n + 1) / 2.0 + (s.nzn - 1) * n * n) * es + 2.0 * s.nzn * n * p * 8.0;
+  }
+  return b;
 }
 
 // Replay the graph stored under `key`, capturing it on the private stream the
@@ -360,6 +403,7 @@ void timed_solve_w(msgfem* h, int mat, int src, int dst, int neg, int width, int
   });
   span_end(h, sp);
   h->prof.solve_flops += solve_flops(h, mat, width == KB ? KB : h->p);
+  h->prof.solve_bytes += solve_bytes(h, mat, width == KB ? KB : h->p);
   h->prof.solve_calls += 1;
 }
 
@@ -374,7 +418,7 @@ void solve_K_kb(msgfem* h) {
   launch_zero_pins_kb(h, MV_WB);
   if (!h->mixed) return;
   for (int r = 0; r < h->refine; ++r) {
-    launch_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
+    timed_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
     launch_x_minus_y(h, MV_ZB, MV_TB, MV_TB, KB);
     launch_zero_pins_kb(h, MV_TB);
     timed_solve_w(h, 0, MV_TB, MV_WB, 0, KB, 1);
@@ -386,34 +430,34 @@ void solve_K_kb(msgfem* h) {
 // W_B1 = -A11^{-1} (K W)_B1, refined in mixed precision with the FP64
 // residual of the harmonic condition (K W)_B1.
 void extend_kb(msgfem* h) {
-  launch_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
+  timed_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
   timed_solve8(h, 1, MV_TB, MV_WB, 1);
   if (!h->mixed) return;
   for (int r = 0; r < h->refine; ++r) {
-    launch_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
+    timed_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
     timed_solve_w(h, 1, MV_TB, MV_WB, 1, KB, 1);
   }
 }
 
 // B-orthogonal projection of a KB-wide block out of the rigid modes (floating only)
 void project_rigid_kb(msgfem* h, int which) {
-  launch_gram_kb(h, MV_BR, PST, 6, which, 1);
-  launch_update_kb(h, MV_R, PST, 6, which, 1);
+  timed_gram_kb(h, MV_BR, PST, 6, which, 1);
+  timed_update_kb(h, MV_R, PST, 6, which, 1);
 }
 
 // CholeskyQR2 of the working block in the N inner product (R_{j+1} into H)
 void cholqr2_kb(msgfem* h, int j) {
   for (int pass = 1; pass <= 2; ++pass) {
-    launch_stencil_kb(h, MV_WB, MV_ZB, 4, KRYLOV_SIGMA);
-    launch_gram_kb(h, MV_WB, KB, KB, MV_ZB, 0);
-    launch_cholqr_kb(h, j, pass);
-    launch_rotate_kb(h, MV_WB);
+    timed_stencil_kb(h, MV_WB, MV_ZB, 4, KRYLOV_SIGMA);
+    timed_gram_kb(h, MV_WB, KB, KB, MV_ZB, 0);
+    timed_cholqr_kb(h, j, pass);
+    timed_rotate_kb(h, MV_WB);
   }
 }
 
 // W <- M W for A-harmonic W: Z = B W, K solve, restrict to B2, A11 re-extension
 void apply_M_kb(msgfem* h) {
-  launch_stencil_kb(h, MV_WB, MV_ZB, 3, 1.0);
+  timed_stencil_kb(h, MV_WB, MV_ZB, 3, 1.0);
   solve_K_kb(h);
   launch_mask_kb(h, MV_WB, 1 << 2);
   extend_kb(h);
@@ -428,12 +472,12 @@ msgfem_status run_subspace(msgfem* h, int n_loc, int p, bool& all_done) {
   std::vector<int> act(h->N, 1);
   // 3. start block X0 on B2, A-harmonic extension, and psi in the last column
   launch_random_b2(h, MV_W, p, h->opt.seed);
-  launch_stencil_apply(h, MV_W, MV_T1, 0, 1.0);
+  timed_stencil_apply(h, MV_W, MV_T1, 0, 1.0);
   launch_copy_col(h, SRC_BLOAD, 0, MV_T1, PST - 1, -1.0);
   timed_solve(h, 1, MV_T1, MV_W, 1);
   launch_copy_col(h, MV_W, PST - 1, SRC_PSI, 0, 1.0);
   launch_copy_col(h, MV_W, PST - 1, MV_W, PST - 1, 0.0);
-  launch_gram(h, MV_BR, MV_W, GM_G3);
+  timed_gram(h, MV_BR, MV_W, GM_G3);
   launch_sub_rc(h, MV_W, MV_R, GM_G3, 6);
   launch_copy_mv(h, MV_W, MV_PHI);
   CK_LAUNCH();
@@ -444,29 +488,29 @@ msgfem_status run_subspace(msgfem* h, int n_loc, int p, bool& all_done) {
   std::vector<std::vector<double>> dhist(h->N);
   for (it = 0; it < h->opt.max_iter; ++it) {
     // Rayleigh-Ritz on span(Phi) (Phi is B-orthogonal to the rigid modes)
-    launch_stencil_apply(h, MV_PHI, MV_Z, 3, 1.0);
-    launch_stencil_apply(h, MV_PHI, MV_KPHI, 0, 1.0);
-    launch_gram(h, MV_PHI, MV_Z, GM_G1);
-    launch_gram(h, MV_PHI, MV_KPHI, GM_G2);
+    timed_stencil_apply(h, MV_PHI, MV_Z, 3, 1.0);
+    timed_stencil_apply(h, MV_PHI, MV_KPHI, 0, 1.0);
+    timed_gram(h, MV_PHI, MV_Z, GM_G1);
+    timed_gram(h, MV_PHI, MV_KPHI, GM_G2);
     launch_small_eig(h, p);
-    launch_rotate(h, MV_PHI, GM_Y, p);
-    launch_rotate(h, MV_Z, GM_Y, p);
-    launch_rotate(h, MV_KPHI, GM_Y, p);
+    timed_rotate(h, MV_PHI, GM_Y, p);
+    timed_rotate(h, MV_Z, GM_Y, p);
+    timed_rotate(h, MV_KPHI, GM_Y, p);
     // shift-invert step: W = K^{-1} Z, X = W|B2, Phi_new = E X
     timed_solve(h, 0, MV_Z, MV_W, 0);
     launch_zero_pins(h, MV_W);
     launch_mask_rows(h, MV_W, 1 << 2);
-    launch_stencil_apply(h, MV_W, MV_T1, 0, 1.0);
+    timed_stencil_apply(h, MV_W, MV_T1, 0, 1.0);
     timed_solve(h, 1, MV_T1, MV_W, 1);
     // B-orthogonal projection out of the rigid modes (floating subdomains)
-    launch_gram(h, MV_BR, MV_W, GM_G3);
+    timed_gram(h, MV_BR, MV_W, GM_G3);
     launch_sub_rc(h, MV_W, MV_R, GM_G3, 6);
     // convergence: d_i = theta_i Phi_new_i - Phi_i vanishes at an eigenpair;
     // ||d_i||_T = ||D_mu d_i||_a is the energy of the error of the PoU-weighted
     // basis function (Phi_i has ||Phi_i||_T = 1)
     launch_theta_axpy(h, MV_W, MV_PHI, MV_T1, p);
-    launch_stencil_apply(h, MV_T1, MV_CW, 3, 1.0);
-    launch_gram(h, MV_T1, MV_CW, GM_G3);
+    timed_stencil_apply(h, MV_T1, MV_CW, 3, 1.0);
+    timed_gram(h, MV_T1, MV_CW, GM_G3);
     CK_LAUNCH();
     std::vector<int> act_now(act);
     all_done = true;
@@ -520,7 +564,7 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
   launch_zero_kb(h, MV_WB);
   timed_solve8(h, 1, MV_TB, MV_WB, 1);
   for (int r = 0; h->mixed && r < h->refine; ++r) {
-    launch_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
+    timed_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
     launch_sub_load_kb(h, MV_TB);
     timed_solve_w(h, 1, MV_TB, MV_WB, 1, KB, 1);
   }
@@ -528,8 +572,14 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
   for (int j = 0; j < h->N; ++j)
     if (nw[j] <= 0) act[j] = 0;
   TRY(set_active(h, act));
-  // start block on B2, A-harmonic extension, first application of M
+  // start block on B2 (random, or a registered warm start on its first
+  // columns), A-harmonic extension, first application of M
   launch_random_kb(h, MV_WB, h->opt.seed);
+  std::vector<int> warm(h->N, 0);
+  if ((int)h->warm.size() == h->N && warm_upload(h)) {
+    launch_load_start(h, MV_WB);
+    for (int j = 0; j < h->N; ++j) warm[j] = h->warm[j].X0 != nullptr;
+  }
   extend_kb(h);
   project_rigid_kb(h, MV_WB);
   apply_M_kb(h);
@@ -550,10 +600,10 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
     apply_M_kb(h);   // W = M Q_j (W held Q_j)
     // two passes of block Gram-Schmidt against Q_0..Q_j in the N inner product
     for (int pass = 0; pass < 2; ++pass) {
-      launch_stencil_kb(h, MV_WB, MV_ZB, 4, KRYLOV_SIGMA);
-      launch_gram_kb(h, MV_QB, MQ, m, MV_ZB, 0);
-      launch_h_accum(h, m, j, pass);
-      launch_update_kb(h, MV_QB, MQ, m, MV_WB, 0);
+      timed_stencil_kb(h, MV_WB, MV_ZB, 4, KRYLOV_SIGMA);
+      timed_gram_kb(h, MV_QB, MQ, m, MV_ZB, 0);
+      timed_h_accum(h, m, j, pass);
+      timed_update_kb(h, MV_QB, MQ, m, MV_WB, 0);
     }
     cholqr2_kb(h, j);
     if (m < MQ) launch_store_block(h, MV_WB, j + 1);
@@ -561,7 +611,9 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
     // Rayleigh-Ritz where the basis can hold the wanted pairs plus one block
     bool any = false;
     for (int s = 0; s < h->N; ++s) {
-      mk[s] = (act[s] && m >= nw[s] + KB) ? m : 0;
+      // Rayleigh-Ritz once the basis can hold the wanted pairs plus one block
+      // (a warm-started subdomain: once it can hold the wanted pairs)
+      mk[s] = (act[s] && m >= nw[s] + (warm[s] ? 0 : KB)) ? m : 0;
       any = any || mk[s] > 0;
       if (act[s]) h->iters[s] = j + 1;
     }
@@ -604,8 +656,8 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
   TRY(set_active(h, std::vector<int>(h->N, 1)));
   CK(cudaMemcpyAsync(h->d_mk, h->m_final.data(), h->N * sizeof(int), cudaMemcpyHostToDevice, st));
   launch_ritz(h, h->d_mk, h->d_nwk, 1, false);
-  launch_stencil_apply(h, MV_PHI, MV_Z, 3, 1.0);
-  launch_stencil_apply(h, MV_PHI, MV_KPHI, 0, 1.0);
+  timed_stencil_apply(h, MV_PHI, MV_Z, 3, 1.0);
+  timed_stencil_apply(h, MV_PHI, MV_KPHI, 0, 1.0);
   CK_LAUNCH();
   return MSGFEM_OK;
 }
@@ -686,6 +738,8 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   for (auto& s : h->sub) CK(cudaMemsetAsync(s.status, 0, 4 * sizeof(int), st));
   h->prof.factor_flops = factor_flops(h);
   h->prof.solve_flops = 0.0;
+  h->prof.solve_bytes = 0.0;
+  h->prof.stencil_flops = 0.0;
   h->prof.solve_calls = 0;
   // 1. assembly
   int sp = span_begin(h, TAG_ASSEMBLE);
@@ -706,11 +760,11 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   const int sp_iter = span_begin(h, TAG_ITERATE);
   // rigid modes, B-orthonormal (floating)
   launch_rigid_modes(h);
-  launch_stencil_apply(h, MV_R, MV_BR, 3, 1.0);
-  launch_gram(h, MV_R, MV_BR, GM_G1);
+  timed_stencil_apply(h, MV_R, MV_BR, 3, 1.0);
+  timed_gram(h, MV_R, MV_BR, GM_G1);
   launch_chol_inv_small(h, GM_G1, nullptr, 6, 0);
-  launch_rotate(h, MV_R, GM_Y, 6);
-  launch_rotate(h, MV_BR, GM_Y, 6);
+  timed_rotate(h, MV_R, GM_Y, 6);
+  timed_rotate(h, MV_BR, GM_Y, 6);
   bool all_done = false;
   if (h->opt.solver == 1 && h->mixed) {
     h->err = "subspace iteration (solver = 1) runs in FP64 only";
@@ -728,11 +782,11 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   for (auto& s : h->sub) CK(cudaMemsetAsync(s.T1, 0, (size_t)s.nfull * PST * sizeof(double), st));
   timed_solve(h, 1, MV_Z, MV_T1, 0);
   for (int r = 0; h->mixed && r < h->refine; ++r) {   // refine y~: residual Z - K y~ on B1
-    launch_stencil_apply(h, MV_T1, MV_W, 0, 1.0);
+    timed_stencil_apply(h, MV_T1, MV_W, 0, 1.0);
     launch_x_minus_y(h, MV_Z, MV_W, MV_W, PST);
     timed_solve_w(h, 1, MV_W, MV_T1, 0, PST, 1);
   }
-  launch_stencil_apply(h, MV_T1, MV_W, 0, 1.0);
+  timed_stencil_apply(h, MV_T1, MV_W, 0, 1.0);
   launch_colnorms(h, MV_KPHI, MV_W, p);
   span_end(h, sp_iter);
   // eigenvectors: [rigid modes (floating), Ritz vectors]
@@ -805,10 +859,10 @@ msgfem_status msgfem_coarse_assemble(msgfem_h h, int* coarse_dim_out) {
                            h->sub[j].nfull, cudaMemcpyDeviceToDevice, st));
   // Gram-Schmidt in the B inner product (CholeskyQR, twice); psi dropped if dependent
   for (int pass = 0; pass < 2; ++pass) {
-    launch_stencil_apply(h, MV_CB, MV_CW, 3, 1.0);
-    launch_gram(h, MV_CB, MV_CW, GM_G1);
+    timed_stencil_apply(h, MV_CB, MV_CW, 3, 1.0);
+    timed_gram(h, MV_CB, MV_CW, GM_G1);
     launch_chol_inv_small(h, GM_G1, h->d_ncols, 0, pass == 0 ? 1 : 0);
-    launch_rotate(h, MV_CB, GM_Y, PST);
+    timed_rotate(h, MV_CB, GM_Y, PST);
     if (pass == 0) {
       h->basis_m.assign(h->N, 0);
       for (int j = 0; j < h->N; ++j) {
@@ -821,7 +875,7 @@ msgfem_status msgfem_coarse_assemble(msgfem_h h, int* coarse_dim_out) {
     }
   }
   launch_scale_rows_mu(h, MV_CB);
-  launch_stencil_apply(h, MV_CB, MV_CW, 0, 1.0);
+  timed_stencil_apply(h, MV_CB, MV_CW, 0, 1.0);
   CK_LAUNCH();
   // coarse layout
   h->coff.assign(h->N, 0);
@@ -944,11 +998,14 @@ msgfem_status msgfem_get_profile(msgfem_h h, msgfem_profile* out) {
 msgfem_status msgfem_reset_profile(msgfem_h h) {
   if (!h) return MSGFEM_EINVAL;
   spans_collect(h);
-  const double ff = h->prof.factor_flops, sf = h->prof.solve_flops;
+  const double ff = h->prof.factor_flops, sf = h->prof.solve_flops, sb = h->prof.solve_bytes;
+  const double stf = h->prof.stencil_flops;
   const int sc = h->prof.solve_calls;
   h->prof = msgfem_profile{};
   h->prof.factor_flops = ff;
   h->prof.solve_flops = sf;
+  h->prof.solve_bytes = sb;
+  h->prof.stencil_flops = stf;
   h->prof.solve_calls = sc;
   return MSGFEM_OK;
 }

@@ -141,6 +141,12 @@ struct HostSub {
   std::vector<double> mu, bload;
 };
 
+// A start block registered for the block Krylov eigensolver (learned warm start).
+struct WarmStart {
+  const float* X0 = nullptr;   // device [n2][ld], first ncols columns used
+  int ld = 0, ncols = 0;
+};
+
 struct msgfem {
   int NX = 0, NY = 0, NZ = 0;
   double hx = 0, hy = 0, hz = 0, traction = 0;
@@ -203,6 +209,10 @@ struct msgfem {
   msgfem_profile prof{};
   int stage = 0;   // 1 setup, 2 local spaces, 3 coarse assembled, 4 solved
   std::string err;
+  // learned warm start
+  std::vector<WarmStart> warm;       // [N] registered start blocks
+  void* d_warm = nullptr;            // device descriptors of the start blocks
+  std::vector<int*> d_b2rows;        // [N] ascending full-layout rows of B2
 };
 
 extern long long g_launch_count;   // kernel launches issued by this library
@@ -251,6 +261,16 @@ void launch_prolong(msgfem* h);
 int energy_blocks(msgfem* h);
 void launch_energy(msgfem* h, const double* d_ref, const double* d_u, double* d_out);
 void launch_basis_out(msgfem* h, int j, double* d_out, int ncols);
+
+// learned warm start (k_warm.cu)
+msgfem_status warm_rows(msgfem* h);
+bool warm_upload(msgfem* h);
+void launch_load_start(msgfem* h, int which);
+
+// error helpers shared by the translation units that return msgfem_status
+#define CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return cuda_fail(h, e_, #x, __FILE__, __LINE__); } while (0)
+#define CK_LAUNCH() CK(cudaGetLastError())
+#define TRY(x) do { msgfem_status st_ = (x); if (st_ != MSGFEM_OK) return st_; } while (0)
 
 // source selectors for k_copy_col
 enum { SRC_BLOAD = -1, SRC_PSI = -2 };

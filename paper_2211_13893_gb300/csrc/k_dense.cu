@@ -18,6 +18,21 @@
 // precisions (it is 1/40 of the work).
 #include "internal.h"
 
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
+
+// compile-time tunables of the streaming solve
+#ifndef SOLVE_CLUSTER
+#define SOLVE_CLUSTER 1   // CTAs (one cluster) per 64-row task, splitting its inner dimension
+#endif
+#ifndef SOLVE_MIN_BLOCKS
+#define SOLVE_MIN_BLOCKS 2   // resident CTAs per SM the register budget is sized for
+#endif
+#ifndef SOLVE_ROWS_F32
+#define SOLVE_ROWS_F32 4  // rows per warp pass of the FP32 plain-A variant (4 or 8)
+#endif
+
 namespace {
 
 constexpr int KC = 16;   // K chunk of the tile GEMM
@@ -249,20 +264,29 @@ k_solve_step(const SolveTaskT<T>* __restrict__ tasks, const SubDev* __restrict__
   }
 }
 
-// Streaming variant of the solve step for KB right-hand sides: the small
-// B block (K x KB) is staged once in shared memory (rows padded by one 16-byte
-// vector so that the vector reads of neighbouring rows fall in distinct bank
-// groups) and every thread streams its part of the factor block A with
-// independent coalesced loads, so that many loads are in flight (the solves
-// are bound by memory, not arithmetic).
-//   plain A:      lane <-> k, each warp owns 8 rows (R at a time), the partial
-//                 sums are reduced with warp shuffles;
-//   transposed A: thread <-> (16-byte vector of output rows, k group), the k
-//                 groups are summed through shared memory.
-// The staging area is reused for the reduction after a barrier.
+// Streaming variant of the solve step for KB right-hand sides.  The solves
+// are bound by memory, not arithmetic: every task reads a 64-row slab of a
+// factor block once.  The small B block (K x KB) is staged once in shared
+// memory and every thread keeps several 16-byte loads of A in flight.
+//   plain A:      lane <-> a 16-byte vector of consecutive k, each warp owns
+//                 8 rows (R at a time), partial sums reduced with shuffles;
+//   transposed A: thread <-> (16-byte vector of output rows, k group), the
+//                 k groups are summed through shared memory.
+// Staging layout: rows of B in chunks of VN rows (one A vector), each chunk
+// padded by one 16-byte vector so that the chunks read by the 8 lanes of a
+// 128-bit shared-memory phase fall in distinct bank groups.  The staging area
+// is reused for the reduction after a barrier.
 template <typename T> struct SolveVec;
-template <> struct SolveVec<float> { using V = float4; static constexpr int N = 4; };
-template <> struct SolveVec<double> { using V = double2; static constexpr int N = 2; };
+template <> struct SolveVec<float> {
+  using V = float4;
+  static constexpr int N = 4;
+  __device__ static void split(const V& v, float (&a)[4]) { a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w; }
+};
+template <> struct SolveVec<double> {
+  using V = double2;
+  static constexpr int N = 2;
+  __device__ static void split(const V& v, double (&a)[2]) { a[0] = v.x; a[1] = v.y; }
+};
 
 template <typename T>
 __device__ __forceinline__ void load_row_kb(const T* p, T (&b)[KB]) {
@@ -270,42 +294,58 @@ __device__ __forceinline__ void load_row_kb(const T* p, T (&b)[KB]) {
   constexpr int N = SolveVec<T>::N;
 #pragma unroll
   for (int j = 0; j < KB / N; ++j) {
-    const V v = reinterpret_cast<const V*>(p)[j];
-    if constexpr (N == 4) {
-      b[4 * j] = v.x; b[4 * j + 1] = v.y; b[4 * j + 2] = v.z; b[4 * j + 3] = v.w;
-    } else {
-      b[2 * j] = v.x; b[2 * j + 1] = v.y;
-    }
+    T e[N];
+    SolveVec<T>::split(reinterpret_cast<const V*>(p)[j], e);
+#pragma unroll
+    for (int i = 0; i < N; ++i) b[N * j + i] = e[i];
   }
 }
 
+// elements per staged chunk of VN rows (padded), and the number of k groups
+// of the transposed variant
 template <typename T>
-__host__ __device__ constexpr int solve_bst() { return KB + SolveVec<T>::N; }
+__host__ __device__ constexpr int solve_cs() { return SolveVec<T>::N * (KB + 1); }
 template <typename T>
 __host__ __device__ constexpr int solve_kg() { return 256 / (64 / SolveVec<T>::N); }
 
-template <typename T>
-__global__ void __launch_bounds__(256)
+template <typename T, int CL>
+__global__ void __launch_bounds__(256, SOLVE_MIN_BLOCKS)
 k_solve_stream(const SolveTaskT<T>* __restrict__ tasks, const SubDev* __restrict__ subs,
                const int* __restrict__ active, int src, int dst, int gather_neg, int scatter_add) {
-  constexpr int BST = solve_bst<T>();
   constexpr int VN = SolveVec<T>::N;
+  constexpr int CS = solve_cs<T>();
   constexpr int TPR = 64 / VN;          // threads across the 64 output rows (transposed A)
-  constexpr int KG = 256 / TPR;         // k groups (transposed A)
-  constexpr int R = sizeof(T) == 4 ? 8 : 4;   // rows per pass (plain A)
+  constexpr int KG = solve_kg<T>();     // k groups (transposed A)
+  constexpr int R = sizeof(T) == 4 ? SOLVE_ROWS_F32 : 4;   // rows per pass (plain A)
   constexpr int NP = 8 / R;
+  static_assert(8 * KB == 64, "the plain-A reduction assumes KB == 8");
+  static_assert(64 % CL == 0, "cluster size must divide the tile rows");
   using V = typename SolveVec<T>::V;
-  const SolveTaskT<T> t = tasks[blockIdx.x];
-  if (t.sub >= 0 && active != nullptr && !active[t.sub]) return;
+  // CL consecutive CTAs (one thread-block cluster) share a task and split its
+  // inner dimension; rank q takes chunks [c0, c1) of VN columns
+  const int rank = blockIdx.x % CL;
+  const SolveTaskT<T> t = tasks[blockIdx.x / CL];
+  if (t.sub >= 0 && active != nullptr && !active[t.sub]) return;   // uniform over the cluster
   extern __shared__ double smem_s[];
-  T* Bs = reinterpret_cast<T*>(smem_s);     // [K][BST], later [64][KB] or [KG][64][KB]
+  T* Out = reinterpret_cast<T*>(smem_s);   // [64][KB] partial result of this CTA
+  T* Bs = Out + 64 * KB;                   // staging of B rows [k0, k1), later the reduction area
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  for (int e = tid; e < t.K * KB; e += 256) Bs[(e / KB) * BST + e % KB] = t.B[e];
+  const int nch = t.K / VN, per = (nch + CL - 1) / CL;
+  const int c0 = min(rank * per, nch), c1 = min(c0 + per, nch);
+  const int k0 = c0 * VN, kl = (c1 - c0) * VN;
+  {
+    // vector loads of B (rows of KB elements are 16-byte aligned); VN-element
+    // vector e covers row e / (KB / VN), columns (e % (KB / VN)) * VN ...
+    const V* Bv = reinterpret_cast<const V*>(t.B + (size_t)k0 * KB);
+    for (int e = tid; e < kl * (KB / VN); e += 256) {
+      const int k = e / (KB / VN), c = (e % (KB / VN)) * VN;
+      *reinterpret_cast<V*>(Bs + (k / VN) * CS + (k % VN) * KB + c) = Bv[e];
+    }
+  }
   __syncthreads();
   const bool transA = (t.flags & S_TRANSA) != 0;
-  static_assert(8 * KB == 64, "the plain-A reduction assumes KB == 8");
-  T res[2] = {(T)0, (T)0};
   if (!transA) {
+    T res[2] = {(T)0, (T)0};
 #pragma unroll
     for (int g = 0; g < NP; ++g) {
       const int r0 = w * 8 + g * R;
@@ -315,22 +355,33 @@ k_solve_stream(const SolveTaskT<T>* __restrict__ tasks, const SubDev* __restrict
 #pragma unroll
         for (int c = 0; c < KB; ++c) acc[r][c] = (T)0;
       const T* a0 = t.A + (size_t)r0 * t.lda;
-      for (int k = lane; k < t.K; k += 64) {
-        const bool two = k + 32 < t.K;
-        T a[2][R];
+      // the loads of the next chunk are issued before the arithmetic of the
+      // current one (register double buffer)
+      V nxt[R];
+      if (c0 + lane < c1) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          a[0][r] = a0[(size_t)r * t.lda + k];
-          a[1][r] = two ? a0[(size_t)r * t.lda + k + 32] : (T)0;
+        for (int r = 0; r < R; ++r)
+          nxt[r] = *reinterpret_cast<const V*>(a0 + (size_t)r * t.lda + (size_t)(c0 + lane) * VN);
+      }
+#pragma unroll 1
+      for (int kc = c0 + lane; kc < c1; kc += 32) {
+        T a[R][VN];
+#pragma unroll
+        for (int r = 0; r < R; ++r) SolveVec<T>::split(nxt[r], a[r]);
+        if (kc + 32 < c1) {
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+            nxt[r] = *reinterpret_cast<const V*>(a0 + (size_t)r * t.lda + (size_t)(kc + 32) * VN);
         }
+        const T* bp = Bs + (size_t)(kc - c0) * CS;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int v = 0; v < VN; ++v) {
           T b[KB];
-          load_row_kb<T>(Bs + (size_t)(two || h == 0 ? k + 32 * h : k) * BST, b);
+          load_row_kb<T>(bp + v * KB, b);
 #pragma unroll
           for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int c = 0; c < KB; ++c) acc[r][c] = fma(a[h][r], b[c], acc[r][c]);
+            for (int c = 0; c < KB; ++c) acc[r][c] = fma(a[r][v], b[c], acc[r][c]);
         }
       }
       // every lane holds all R x KB sums after the butterfly; lane L keeps
@@ -346,9 +397,8 @@ k_solve_stream(const SolveTaskT<T>* __restrict__ tasks, const SubDev* __restrict
           if (lane == idx % 32) res[idx / 32] = v;
         }
     }
-    __syncthreads();
 #pragma unroll
-    for (int j = 0; j < 2; ++j) Bs[(w * 8 + 4 * j + lane / KB) * KB + lane % KB] = res[j];
+    for (int j = 0; j < 2; ++j) Out[(w * 8 + 4 * j + lane / KB) * KB + lane % KB] = res[j];
   } else {
     const int mv = tid % TPR, kg = tid / TPR;
     T acc[VN][KB];
@@ -357,30 +407,35 @@ k_solve_stream(const SolveTaskT<T>* __restrict__ tasks, const SubDev* __restrict
 #pragma unroll
       for (int c = 0; c < KB; ++c) acc[v][c] = (T)0;
     const T* a0 = t.A + mv * VN;
-#pragma unroll 4
-    for (int k = kg; k < t.K; k += KG) {
-      const V av = *reinterpret_cast<const V*>(a0 + (size_t)k * t.lda);
+#pragma unroll 8
+    for (int k = kg; k < kl; k += KG) {
       T a[VN];
-      if constexpr (VN == 4) {
-        a[0] = av.x; a[1] = av.y; a[2] = av.z; a[3] = av.w;
-      } else {
-        a[0] = av.x; a[1] = av.y;
-      }
+      SolveVec<T>::split(*reinterpret_cast<const V*>(a0 + (size_t)(k0 + k) * t.lda), a);
       T b[KB];
-      load_row_kb<T>(Bs + (size_t)k * BST, b);
+      load_row_kb<T>(Bs + (size_t)(k / VN) * CS + (k % VN) * KB, b);
 #pragma unroll
       for (int v = 0; v < VN; ++v)
 #pragma unroll
         for (int c = 0; c < KB; ++c) acc[v][c] = fma(a[v], b[c], acc[v][c]);
     }
     __syncthreads();
-    T* red = Bs;
 #pragma unroll
     for (int v = 0; v < VN; ++v)
 #pragma unroll
-      for (int c = 0; c < KB; ++c) red[((size_t)kg * 64 + mv * VN + v) * KB + c] = acc[v][c];
+      for (int c = 0; c < KB; ++c) Bs[((size_t)kg * 64 + mv * VN + v) * KB + c] = acc[v][c];
+    __syncthreads();
+    for (int e = tid; e < 64 * KB; e += 256) {
+      T v = (T)0;
+#pragma unroll
+      for (int q = 0; q < KG; ++q) v += Bs[(size_t)q * 64 * KB + e];
+      Out[e] = v;
+    }
   }
-  __syncthreads();
+  // sum the partial results of the cluster (distributed shared memory); rank q
+  // finishes rows [q 64 / CL, (q + 1) 64 / CL)
+  constexpr int RPR = 64 / CL;
+  if constexpr (CL > 1) cg::this_cluster().sync();
+  else __syncthreads();
   const T sgn = (t.flags & S_NEG) ? (T)-1 : (T)1;
   const double* gfull = nullptr;
   double* sfull = nullptr;
@@ -390,15 +445,16 @@ k_solve_stream(const SolveTaskT<T>* __restrict__ tasks, const SubDev* __restrict
     if (t.flags & S_SCATTER) sfull = mv_ptr(s, dst) + (size_t)t.row_off * KB;
   }
   const double gs = gather_neg ? -1.0 : 1.0;
-  for (int e = tid; e < 64 * KB; e += 256) {
-    const int r = e / KB, c = e % KB;
-    T v;
-    if (transA) {
-      v = (T)0;
+  for (int e = tid; e < RPR * KB; e += 256) {
+    const int ee = rank * RPR * KB + e;
+    const int r = ee / KB, c = ee % KB;
+    T v = (T)0;
+    if constexpr (CL > 1) {
+      cg::cluster_group cl = cg::this_cluster();
 #pragma unroll
-      for (int q = 0; q < KG; ++q) v += Bs[(size_t)q * 64 * KB + e];
+      for (int q = 0; q < CL; ++q) v += cl.map_shared_rank(Out, q)[ee];
     } else {
-      v = Bs[e];
+      v = Out[ee];
     }
     v = sgn * v;
     if (t.flags & S_INIT_TILE) v += t.init[r * KB + c];
@@ -411,15 +467,21 @@ k_solve_stream(const SolveTaskT<T>* __restrict__ tasks, const SubDev* __restrict
       *o = scatter_add ? *o + (double)v : (double)v;
     }
   }
+  // keep this CTA's partial result alive until every peer has read it
+  if constexpr (CL > 1) cg::this_cluster().sync();
 }
 
-constexpr size_t SOLVE_SMEM_MAX = 200 * 1024;
+constexpr size_t SOLVE_SMEM_MAX = 110 * 1024;
 
+constexpr int SOLVE_CL = SOLVE_CLUSTER;   // CTAs per task (cluster size) of the streaming solve
+
+// shared memory of k_solve_stream<T, cl> for tasks with inner dimension <= kmax
 template <typename T>
-size_t solve_stream_smem(int kmax) {
-  const size_t stage = (size_t)kmax * solve_bst<T>();
+size_t solve_stream_smem(int kmax, int cl) {
+  const int nch = (kmax + SolveVec<T>::N - 1) / SolveVec<T>::N;
+  const size_t stage = (size_t)((nch + cl - 1) / cl) * solve_cs<T>();
   const size_t red = (size_t)solve_kg<T>() * 64 * KB;
-  return (stage > red ? stage : red) * sizeof(T);
+  return (64 * KB + (stage > red ? stage : red)) * sizeof(T);
 }
 
 }  // namespace
@@ -469,8 +531,8 @@ void prepare_tile_kernels() {
   if (done) return;
   cudaFuncSetAttribute(k_tile_task<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
   cudaFuncSetAttribute(k_tile_task<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
-  cudaFuncSetAttribute(k_solve_stream<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
-  cudaFuncSetAttribute(k_solve_stream<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
+  cudaFuncSetAttribute(k_solve_stream<double, SOLVE_CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
+  cudaFuncSetAttribute(k_solve_stream<float, SOLVE_CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
   done = true;
 }
 
@@ -486,13 +548,28 @@ template <typename T>
 void run_solve_mv(const SolveScheduleT<T>& s, cudaStream_t st, int src, int dst, int gather_neg, int width,
                   const StreamSet* gs, int scatter_add) {
   prepare_tile_kernels();
-  const size_t smem = solve_stream_smem<T>(s.kmax);
+  const size_t smem = solve_stream_smem<T>(s.kmax, SOLVE_CL);
   const bool stream_ok = smem <= SOLVE_SMEM_MAX;
   run_groups(s, st, gs, [&](const SchedStep& step, cudaStream_t stream) {
-    if (width == KB && stream_ok)
-      k_solve_stream<T><<<step.count, 256, smem, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
-                                                           gather_neg, scatter_add);
-    else if (width == KB)
+    if (width == KB && stream_ok && SOLVE_CL == 1) {
+      k_solve_stream<T, 1><<<step.count, 256, smem, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
+                                                              gather_neg, scatter_add);
+    } else if (width == KB && stream_ok) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(step.count * SOLVE_CL);
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = stream;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = SOLVE_CL;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      cudaLaunchKernelEx(&cfg, k_solve_stream<T, SOLVE_CL>, (const SolveTaskT<T>*)(s.d_tasks + step.first),
+                         (const SubDev*)g_subs, (const int*)g_active, src, dst, gather_neg, scatter_add);
+    } else if (width == KB)
       k_solve_step<T, KB><<<step.count, 256, 0, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
                                                           gather_neg, scatter_add);
     else

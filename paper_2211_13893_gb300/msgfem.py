@@ -16,7 +16,11 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTSPD", 5: "ENOCO
 EXPORTS = ("msgfem_setup", "msgfem_update_angles", "msgfem_local_spaces", "msgfem_coarse_assemble",
            "msgfem_solve", "msgfem_get_basis", "msgfem_get_info", "msgfem_num_subdomains",
            "msgfem_get_profile", "msgfem_reset_profile", "msgfem_energy_error_noalloc", "msgfem_last_error",
-           "msgfem_destroy")
+           "msgfem_destroy",
+           # include/msgfem_warm.h
+           "msgfem_net_create", "msgfem_net_param_count", "msgfem_net_get_params", "msgfem_net_set_params",
+           "msgfem_net_forward", "msgfem_net_gradient", "msgfem_net_adam_step", "msgfem_net_destroy",
+           "msgfem_warm_features", "msgfem_warm_sizes", "msgfem_warm_targets", "msgfem_set_start_block")
 
 
 class MsgfemError(RuntimeError):
@@ -47,7 +51,9 @@ class Options(C.Structure):
 class Profile(C.Structure):
     _fields_ = [("assemble_ms", C.c_double), ("factor_ms", C.c_double), ("solve_ms", C.c_double),
                 ("iterate_ms", C.c_double), ("coarse_ms", C.c_double), ("factor_flops", C.c_double),
-                ("solve_flops", C.c_double), ("launches", C.c_longlong), ("solve_calls", C.c_int)]
+                ("solve_flops", C.c_double), ("launches", C.c_longlong), ("solve_calls", C.c_int),
+                ("solve_bytes", C.c_double), ("stencil_ms", C.c_double), ("ortho_ms", C.c_double),
+                ("stencil_flops", C.c_double)]
 
 
 class SubInfo(C.Structure):
@@ -83,6 +89,19 @@ def load_library(path=LIB_PATH):
         "msgfem_num_subdomains": (C.c_int, [h]),
         "msgfem_last_error": (C.c_char_p, [h]),
         "msgfem_destroy": (None, [h]),
+        "msgfem_net_create": (C.c_int, [C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(h)]),
+        "msgfem_net_param_count": (C.c_longlong, [h]),
+        "msgfem_net_get_params": (C.c_int, [h, C.c_void_p]),
+        "msgfem_net_set_params": (C.c_int, [h, C.c_void_p]),
+        "msgfem_net_forward": (C.c_int, [h, C.c_void_p, C.c_int, C.c_void_p]),
+        "msgfem_net_gradient": (C.c_int, [h, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+        "msgfem_net_adam_step": (C.c_int, [h, C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.c_float, C.c_float,
+                                           C.c_float, C.c_void_p]),
+        "msgfem_net_destroy": (None, [h]),
+        "msgfem_warm_features": (C.c_int, [h, C.c_void_p, C.c_float, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+        "msgfem_warm_sizes": (C.c_int, [h, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "msgfem_warm_targets": (C.c_int, [h, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
+        "msgfem_set_start_block": (C.c_int, [h, C.c_int, C.c_void_p, C.c_int, C.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -181,9 +200,87 @@ class MSGFEM:
             self._check(self.lib.msgfem_reset_profile(self.h))
         return {k: getattr(pr, k) for k, _ in Profile._fields_}
 
+    # learned warm start (include/msgfem_warm.h)
+    def warm_features(self, dtheta, scale, feat, ld):
+        """Fill feat (device float32 [N][ld]) from dtheta (device float64, one per element)."""
+        nf = C.c_int()
+        self._check(self.lib.msgfem_warm_features(self.h, _ptr(dtheta), scale, _ptr(feat), ld, C.byref(nf)))
+        return nf.value
+
+    def warm_sizes(self, j, n_loc=0):
+        """(n2, nw): interface rows and wanted non-rigid pairs of subdomain j."""
+        n2, nw = C.c_int(), C.c_int()
+        self._check(self.lib.msgfem_warm_sizes(self.h, j, n_loc, C.byref(n2), C.byref(nw)))
+        return n2.value, nw.value
+
+    def warm_targets(self, j, out, ld, ref=None):
+        """B2 rows of subdomain j's wanted eigenvectors into out (device float32 [n2][ld])."""
+        self._check(self.lib.msgfem_warm_targets(self.h, j, _ptr(ref), _ptr(out), ld))
+
+    def set_start_block(self, j, X0, ld=0, ncols=0):
+        """Register X0 (device float32 [n2][ld]) as subdomain j's start block; None clears it."""
+        self._check(self.lib.msgfem_set_start_block(self.h, j, _ptr(X0), ld, ncols))
+
     def close(self):
         if self.h:
             self.lib.msgfem_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Net:
+    """Warm-start network (include/msgfem_warm.h): MLP with tanh hidden layers, FP32."""
+
+    def __init__(self, sizes, max_batch, params=None, stream=None):
+        self.lib = load_library()
+        self.h = C.c_void_p()
+        self.sizes = [int(x) for x in sizes]
+        sz = (C.c_int * len(self.sizes))(*self.sizes)
+        init = None
+        if params is not None:
+            init = np.ascontiguousarray(params, dtype=np.float32)
+        st = self.lib.msgfem_net_create(len(self.sizes), sz, int(max_batch), _ptr(init), stream, C.byref(self.h))
+        if st != 0:
+            raise MsgfemError(st, "msgfem_net_create")
+        self.n_params = int(self.lib.msgfem_net_param_count(self.h))
+
+    def _check(self, st, what):
+        if st != 0:
+            raise MsgfemError(st, what)
+
+    def params(self):
+        out = np.zeros(self.n_params, dtype=np.float32)
+        self._check(self.lib.msgfem_net_get_params(self.h, out.ctypes.data), "get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(self.lib.msgfem_net_set_params(self.h, p.ctypes.data), "set_params")
+
+    def forward(self, X, Y, batch):
+        self._check(self.lib.msgfem_net_forward(self.h, _ptr(X), int(batch), _ptr(Y)), "forward")
+
+    def gradient(self, X, T, batch):
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = C.c_double()
+        self._check(self.lib.msgfem_net_gradient(self.h, _ptr(X), _ptr(T), int(batch), g.ctypes.data,
+                                                 C.addressof(loss)), "gradient")
+        return loss.value, g
+
+    def adam_step(self, X, T, batch, lr, beta1=0.9, beta2=0.999, eps=1e-8, want_loss=False):
+        loss = C.c_double()
+        self._check(self.lib.msgfem_net_adam_step(self.h, _ptr(X), _ptr(T), int(batch), lr, beta1, beta2, eps,
+                                                  C.addressof(loss) if want_loss else None), "adam_step")
+        return loss.value if want_loss else None
+
+    def close(self):
+        if self.h:
+            self.lib.msgfem_net_destroy(self.h)
             self.h = C.c_void_p()
 
     def __del__(self):

@@ -1,5 +1,5 @@
 """The C-ABI library builds for sm_103a, loads, and exports every entry point
-declared in include/msgfem.h (no GPU needed: no compute call is made)."""
+declared in include/*.h (no GPU needed: no compute call is made)."""
 import os
 import re
 import subprocess
@@ -10,7 +10,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_symbols():
-    txt = open(os.path.join(ROOT, "include", "msgfem.h")).read()
+    inc = os.path.join(ROOT, "include")
+    txt = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(msgfem_[a-z_]+)\s*\(", txt)))
 

@@ -3,6 +3,8 @@
 All angles are in degrees, measured from the beam axis x toward y about +z.
 Nothing here depends on the MS-GFEM method itself.
 """
+import functools
+
 import numpy as np
 
 _CYCLE = (0.0, 90.0, 45.0, -45.0)
@@ -33,25 +35,32 @@ def ply_angles(cfg) -> np.ndarray:
     return ang
 
 
-def wrinkle_field(cfg, sample: int, sd_deg: float = 3.0, corr_len: float = 10.0) -> np.ndarray:
-    """Gaussian random field of ply-angle perturbation at element centroids.
-
-    Squared-exponential covariance sd^2 exp(-|x - x'|^2 / (2 l^2)) in 3-D,
-    sampled through a Cholesky factor of the covariance with a jitter of
-    1e-10 sd^2 on the diagonal; the sample index is the seed.
-    Returns an array of shape (NX, NY, NZ) in degrees.
-    """
-    xs = (np.arange(cfg.NX) + 0.5) * cfg.hx
-    ys = (np.arange(cfg.NY) + 0.5) * cfg.hy
-    zs = (np.arange(cfg.NZ) + 0.5) * cfg.t
+@functools.lru_cache(maxsize=8)
+def _wrinkle_factor(NX, NY, NZ, hx, hy, t, sd_deg, corr_len):
+    xs = (np.arange(NX) + 0.5) * hx
+    ys = (np.arange(NY) + 0.5) * hy
+    zs = (np.arange(NZ) + 0.5) * t
     X, Y, Z = np.meshgrid(xs, ys, zs, indexing="ij")
     P = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
     d2 = ((P[:, None, :] - P[None, :, :]) ** 2).sum(-1)
     cov = sd_deg ** 2 * np.exp(-d2 / (2.0 * corr_len ** 2))
     cov[np.diag_indices_from(cov)] += 1e-10 * sd_deg ** 2
     L = np.linalg.cholesky(cov)
+    L.setflags(write=False)
+    return L
+
+
+def wrinkle_field(cfg, sample: int, sd_deg: float = 3.0, corr_len: float = 10.0) -> np.ndarray:
+    """Gaussian random field of ply-angle perturbation at element centroids.
+
+    Squared-exponential covariance sd^2 exp(-|x - x'|^2 / (2 l^2)) in 3-D,
+    sampled through a Cholesky factor of the covariance with a jitter of
+    1e-10 sd^2 on the diagonal (computed once per mesh); the sample index is
+    the seed.  Returns an array of shape (NX, NY, NZ) in degrees.
+    """
+    L = _wrinkle_factor(cfg.NX, cfg.NY, cfg.NZ, cfg.hx, cfg.hy, cfg.t, float(sd_deg), float(corr_len))
     rng = np.random.default_rng(sample)
-    return (L @ rng.standard_normal(P.shape[0])).reshape(cfg.NX, cfg.NY, cfg.NZ)
+    return (L @ rng.standard_normal(L.shape[0])).reshape(cfg.NX, cfg.NY, cfg.NZ)
 
 
 def element_angles(cfg, sample=None) -> np.ndarray:
