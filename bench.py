@@ -244,6 +244,10 @@ def run_ours(args):
                       "calls_per_step": prof["solve_calls"],
                       "gbs": prof["solve_bytes"] * args.steps / (prof["solve_ms"] / 1000.0) / 1e9
                       if prof["solve_ms"] else None},
+            "stencil": {"ms_per_step": prof["stencil_ms"] / args.steps,
+                        "tflops": prof["stencil_flops"] * args.steps / (prof["stencil_ms"] / 1000.0) / 1e12
+                        if prof["stencil_ms"] else None},
+            "ortho_ms_per_step": prof["ortho_ms"] / args.steps,
             "iterate_ms_per_step": prof["iterate_ms"] / args.steps,
             "assemble_ms_per_step": prof["assemble_ms"] / args.steps,
             "coarse_ms_per_step": prof["coarse_ms"] / args.steps}
@@ -279,6 +283,9 @@ def run_ours(args):
     mixed = None
     if not args.no_mixed:
         mixed = run_mixed(args, cfg, ang_dev, stream, dev, rank, lam_fp64, u_fp64, flush, world)
+    warm = None
+    if not args.no_warm and rank == 0:
+        warm = run_warm_c5(args, dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
@@ -295,7 +302,7 @@ def run_ours(args):
                            "l2": "flushed between timed steps (256 MiB write); working set ~25 GB >> L2",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "solver": extra, "mixed": mixed}
+                "clocks": clocks, "solver": extra, "mixed": mixed, "warm_c5": warm}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -347,12 +354,105 @@ def run_mixed(args, cfg, ang_dev, stream, dev, rank, lam_fp64, u_fp64, flush, wo
            "factor_tflops": prof["factor_flops"] * args.steps / (prof["factor_ms"] / 1000.0) / 1e12
            if prof["factor_ms"] else None,
            "eig_rel_diff_vs_fp64": rel, "energy_norm_diff_vs_fp64": e.value,
+           "iterate_ms_per_step": prof["iterate_ms"] / args.steps,
+           "stencil": {"ms_per_step": prof["stencil_ms"] / args.steps,
+                       "tflops": prof["stencil_flops"] * args.steps / (prof["stencil_ms"] / 1000.0) / 1e12
+                       if prof["stencil_ms"] else None},
+           "ortho_ms_per_step": prof["ortho_ms"] / args.steps,
            "roofline": {"bound": "hbm", "achieved": solve_gbs, "peak": hbm, "unit": "GB/s",
                         "frac": solve_gbs / hbm, "peak_note": hbm_note,
                         "kernel": "k_solve_stream (FP32 block solves, 8 right-hand sides)",
                         "time_share": prof["solve_ms"] / total if total else None,
                         "calls_per_step": prof["solve_calls"]}}
     m.close()
+    return out
+
+
+def run_warm_c5(args, dev, n_train=384, n_test=128):
+    """Learned warm start on the wrinkled c1 beam (c5): 512 seeded wrinkle
+    fields, the network trained on the eigenbases of samples 0..383 (computed
+    by the eigensolver itself, cold), tested on 384..511.  Reports iterations to
+    the 1e-6 energy-norm tolerance, the largest principal angle between the
+    start block and the converged wanted space, and local-stage solves/s for
+    the cold start, nominal-basis reuse and the trained network (inference
+    included in the warm timing)."""
+    import numpy as np
+    import torch
+    from paper_2211_13893_gb300 import MSGFEM
+    from paper_2211_13893_gb300.warm import WarmStart
+    from workloads import element_angles, get_config, wrinkle_field
+    cfg = get_config("c5")
+    base = element_angles(cfg)
+    stream = torch.cuda.current_stream(dev)
+    m = MSGFEM.from_config(cfg, torch.tensor(base.reshape(-1), dtype=torch.float64, device=dev), seed=5,
+                           tol=1e-6, stream=stream.cuda_stream)
+    ws = WarmStart(m, cfg.n_loc, hidden=(256, 256), seed=3, stream=stream.cuda_stream)
+    m.local_spaces(cfg.n_loc)
+    ws.set_nominal()
+    t0 = time.perf_counter()
+    fields = [wrinkle_field(cfg, s) for s in range(n_train + n_test)]
+    ang = [torch.tensor((base + f).reshape(-1), dtype=torch.float64, device=dev) for f in fields]
+    dth = [torch.tensor(f.reshape(-1), dtype=torch.float64, device=dev) for f in fields]
+    X, T = [], [[] for _ in range(m.N)]
+    for s in range(n_train):
+        m.update_angles(ang[s])
+        m.local_spaces(cfg.n_loc)
+        X.append(ws.features(dth[s]))
+        for j, t in enumerate(ws.targets()):
+            T[j].append(t.reshape(-1))
+    X = torch.stack(X)
+    T = [torch.stack(t) for t in T]
+    t_data = time.perf_counter() - t0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    losses = ws.fit(X, T, steps=1500, lr=1e-3, batch=64)
+    e1.record(stream)
+    e1.synchronize()
+    train_ms = e0.elapsed_time(e1)
+
+    def angle(A, B):
+        qa, _ = np.linalg.qr(A)
+        qb, _ = np.linalg.qr(B)
+        sv = np.linalg.svd(qa.T @ qb, compute_uv=False)
+        return float(np.arccos(np.clip(sv.min(), -1.0, 1.0)))
+
+    res = {k: {"iters": [], "ms": [], "angle": []} for k in ("cold", "nominal", "learned")}
+    for s in range(n_train, n_train + n_test):
+        m.update_angles(ang[s])
+        conv = None
+        for kind in ("cold", "nominal", "learned"):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if kind == "cold":
+                ws.apply(None)
+                blocks = None
+            elif kind == "nominal":
+                blocks = ws.nominal
+                ws.apply(blocks)
+            else:
+                blocks = ws.predict(ws.features(dth[s]))
+                ws.apply(blocks)
+            m.local_spaces(cfg.n_loc)
+            b.record(stream)
+            b.synchronize()
+            res[kind]["ms"].append(a.elapsed_time(b))
+            res[kind]["iters"].append(sum(m.info(j)["iterations"] for j in range(m.N)) / m.N)
+            if conv is None:
+                conv = [t.cpu().numpy() for t in ws.targets(ref=False)]
+            for j, (n2, nw) in enumerate(ws.sizes):
+                start = (blocks[j].cpu().numpy()[:, :nw] if blocks is not None
+                         else np.random.default_rng(s).standard_normal((n2, nw)))
+                res[kind]["angle"].append(angle(start, conv[j][:, :nw]))
+    ws.apply(None)
+    m.close()
+    out = {"workload": "c1 beam 24x4x12 + seeded 3-D wrinkle field (sd 3 deg, l = 10 mm), 2x1 subdomains, "
+                       "n_loc=8, FP64, tol 1e-6", "train_samples": n_train, "test_samples": n_test,
+           "data_gen_s": t_data, "train_ms": train_ms, "final_losses": losses}
+    for k, r in res.items():
+        out[k] = {"iterations_mean": float(np.mean(r["iters"])), "start_angle_rad_mean": float(np.mean(r["angle"])),
+                  "solves_per_s": 2.0 * len(r["ms"]) / (sum(r["ms"]) / 1000.0),
+                  "ms_per_sample": float(np.mean(r["ms"]))}
     return out
 
 
@@ -367,6 +467,7 @@ def main():
     ap.add_argument("--ref-warmup", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison run")
+    ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start (c5) run")
     ap.add_argument("--streams", type=int, default=0, help="stream groups of the library (0 = its default)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
