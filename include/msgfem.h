@@ -123,7 +123,8 @@ typedef struct {
                            right-hand side read and solution written */
   double stencil_ms;    /* stencil products (K, B, K + sigma B) inside the iteration */
   double ortho_ms;      /* Gram, block updates, CholeskyQR, basis rotations */
-  double stencil_flops; /* per local stage: 2 x 27 x 9 flop per node and column (x2 for K + sigma B) */
+  double stencil_flops; /* per local stage: 18 flop per (node, neighbour) pair and column, 24 for the
+                           fused K + sigma B pass */
 } msgfem_profile;
 
 /* Per-subdomain diagnostics filled by msgfem_get_info. */

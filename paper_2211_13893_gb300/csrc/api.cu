@@ -296,12 +296,13 @@ void spans_collect(msgfem* h) {
 
 // Stencil products (K, B = D_mu K D_mu and the N = S + sigma T products of the
 // Krylov solver) and the orthogonalisation kernels are timed as phases of
-// their own; the stencil flops count 2 x 27 x 9 per node and column (twice
-// that for the combined K + sigma B pass, mode 4).
+// their own.  Stencil flops: 18 per (node, neighbour) pair and column, 24 for
+// the fused K + sigma D_mu K D_mu pass (mode 4); a box of n nodes per axis has
+// (3 n - 2) (node, neighbour) pairs along that axis.
 double stencil_flops(const msgfem* h, int width, int mode) {
-  double n = 0.0;
-  for (const auto& s : h->sub) n += s.nnode;
-  return n * 2.0 * 27.0 * 9.0 * width * (mode == 4 ? 2.0 : 1.0);
+  double pairs = 0.0;
+  for (const auto& s : h->sub) pairs += (3.0 * s.nxn - 2.0) * (3.0 * s.nyn - 2.0) * (3.0 * s.nzn - 2.0);
+  return pairs * (mode == 4 ? 24.0 : 18.0) * width;
 }
 void timed_stencil_kb(msgfem* h, int src, int dst, int mode, double alpha) {
   const int sp = span_begin(h, TAG_STENCIL);
@@ -825,6 +826,11 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   }
   h->stage = 2;
   spans_collect(h);
+  if (h->mixed && solve_pipeline_failed()) {
+    h->stage = 1;
+    h->err = "a bulk-copy pipeline wait of the FP32 block solves expired";
+    return MSGFEM_ECUDA;
+  }
   for (int j = 0; j <= h->N; ++j)
     if (notspd[j]) {
       h->err = "non-positive pivot in a layer-block factorisation";

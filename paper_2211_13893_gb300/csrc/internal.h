@@ -123,6 +123,7 @@ struct SolveScheduleT {
   std::vector<SolveTaskT<T>> tasks;
   SolveTaskT<T>* d_tasks = nullptr;
   int kmax = 0;   // largest inner dimension of a task (shared-memory sizing)
+  bool k64 = true;   // every inner dimension is a multiple of 64
 };
 using SolveSchedule = SolveScheduleT<double>;
 
@@ -228,6 +229,7 @@ void build_coarse_schedules(msgfem* h);
 // launchers
 void set_dense_context(int* active, int* notspd, const SubDev* subs);
 void prepare_tile_kernels();
+int solve_pipeline_failed();
 template <typename T>
 void run_schedule(const ScheduleT<T>& s, cudaStream_t st, const StreamSet* gs = nullptr);
 // solve steps; scatter_add adds the result into the destination multivector

@@ -19,12 +19,16 @@
 #include "internal.h"
 
 #include <cooperative_groups.h>
+#include <type_traits>
 
 namespace cg = cooperative_groups;
 
 // compile-time tunables of the streaming solve
 #ifndef SOLVE_CLUSTER
 #define SOLVE_CLUSTER 1   // CTAs (one cluster) per 64-row task, splitting its inner dimension
+#endif
+#ifndef SOLVE_BULK
+#define SOLVE_BULK 0      // FP32 solves through the bulk-copy pipeline (k_solve_bulk); measured slower
 #endif
 #ifndef SOLVE_MIN_BLOCKS
 #define SOLVE_MIN_BLOCKS 2   // resident CTAs per SM the register budget is sized for
@@ -471,6 +475,203 @@ k_solve_stream(const SolveTaskT<T>* __restrict__ tasks, const SubDev* __restrict
   if constexpr (CL > 1) cg::this_cluster().sync();
 }
 
+// ---------------------------------------------------------------------------
+// FP32 solve step with asynchronous bulk copies (the mixed-precision path).
+// The factor slab of a task (64 rows x K, or K x 64 read transposed) is
+// streamed through a ring of BULK_DEPTH shared-memory stages of 64 x 64 floats
+// (16 KiB): one warp issues, per stage, 64 row copies of 256 bytes with
+// cp.async.bulk, completing on the stage's mbarrier; all warps consume the
+// stage once its barrier flips.  With BULK_DEPTH stages in flight per CTA the
+// copy engine keeps ~48 KiB per CTA in flight without spending registers.
+// Thread (g, h) of the 16 x 16 thread grid owns 4 output rows (g) and a
+// 4-wide k slice (h) of every stage and keeps a 4 x KB accumulator; the 16 k
+// slices are summed through shared memory at the end.
+// Every mbarrier wait is bounded: on expiry the CTA records the failure in
+// g_bulk_timeout, drains its outstanding copies (bounded again) and returns.
+constexpr int BULK_DEPTH = 4;
+constexpr int BULK_STAGE = 64 * 64;             // floats per stage
+constexpr int BULK_CS = 4 * (KB + 1);           // floats per staged chunk of 4 B rows (padded)
+constexpr unsigned BULK_SPIN = 1u << 22;        // polls before a wait is declared failed
+
+__device__ int g_bulk_timeout = 0;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool bulk_wait(unsigned bar, unsigned parity) {
+  for (unsigned it = 0; it < BULK_SPIN; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// warp 0: copy stage i of the slab into ring slot i % BULK_DEPTH
+__device__ __forceinline__ void bulk_issue(const SolveTaskT<float>& t, bool transA, int i, float* ring,
+                                           unsigned bar0, int lane) {
+  const int slot = i % BULK_DEPTH;
+  const unsigned bar = bar0 + 8u * slot;
+  if (lane == 0) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(64u * 256u) : "memory");
+  }
+  __syncwarp();
+  float* dst0 = ring + (size_t)slot * BULK_STAGE;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int r = lane + 32 * h;
+    // plain: row r, columns [64 i, 64 i + 64); transposed: row 64 i + r, columns [0, 64)
+    const float* src = transA ? t.A + (size_t)(64 * i + r) * t.lda : t.A + (size_t)r * t.lda + 64 * i;
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst0 + r * 64)), "l"(src), "r"(256u), "r"(bar)
+        : "memory");
+  }
+}
+
+__global__ void __launch_bounds__(256, 2)
+k_solve_bulk(const SolveTaskT<float>* __restrict__ tasks, const SubDev* __restrict__ subs,
+             const int* __restrict__ active, int src, int dst, int gather_neg, int scatter_add) {
+  const SolveTaskT<float> t = tasks[blockIdx.x];
+  if (t.sub >= 0 && active != nullptr && !active[t.sub]) return;
+  extern __shared__ __align__(128) unsigned char smem_b[];
+  float* ring = reinterpret_cast<float*>(smem_b);                     // [BULK_DEPTH][64][64]
+  float* Bs = ring + BULK_DEPTH * BULK_STAGE;                         // [K / 4][BULK_CS]
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(Bs + (size_t)(t.K / 4) * BULK_CS);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const bool transA = (t.flags & S_TRANSA) != 0;
+  const int nst = t.K / 64;
+  const unsigned bar0 = smem_u32(bars);
+  if (tid == 0) {
+    for (int q = 0; q < BULK_DEPTH; ++q)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8u * q) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (w == 0)
+    for (int i = 0; i < min(BULK_DEPTH, nst); ++i) bulk_issue(t, transA, i, ring, bar0, lane);
+  {
+    const float4* Bv = reinterpret_cast<const float4*>(t.B);
+    for (int e = tid; e < t.K * (KB / 4); e += 256) {
+      const int k = e / (KB / 4), c = (e % (KB / 4)) * 4;
+      *reinterpret_cast<float4*>(Bs + (k / 4) * BULK_CS + (k % 4) * KB + c) = Bv[e];
+    }
+  }
+  __syncthreads();
+  // thread grid: plain A: h = tid % 16 (k slice), g = tid / 16 (rows);
+  //              transposed: g = tid % 16 (rows), h = tid / 16 (k slice)
+  const int h = transA ? tid / 16 : tid % 16;
+  const int g = transA ? tid % 16 : tid / 16;
+  float acc[4][KB];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < KB; ++c) acc[r][c] = 0.f;
+  int done = 0;          // stages consumed (their copies have landed)
+  bool failed = false;
+  for (int i = 0; i < nst; ++i) {
+    const int slot = i % BULK_DEPTH;
+    const bool ok = bulk_wait(bar0 + 8u * slot, (unsigned)((i / BULK_DEPTH) & 1));
+    const float* stg = ring + (size_t)slot * BULK_STAGE;
+    if (ok) {
+      const float* bp = Bs + (size_t)(16 * i + h) * BULK_CS;   // B rows 64 i + 4 h .. + 3
+      float b[4][KB];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const float4 b0 = *reinterpret_cast<const float4*>(bp + v * KB);
+        const float4 b1 = *reinterpret_cast<const float4*>(bp + v * KB + 4);
+        b[v][0] = b0.x; b[v][1] = b0.y; b[v][2] = b0.z; b[v][3] = b0.w;
+        b[v][4] = b1.x; b[v][5] = b1.y; b[v][6] = b1.z; b[v][7] = b1.w;
+      }
+      if (!transA) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const float4 a = *reinterpret_cast<const float4*>(stg + (4 * g + r) * 64 + 4 * h);
+          const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+#pragma unroll
+            for (int c = 0; c < KB; ++c) acc[r][c] = fmaf(av[v], b[v][c], acc[r][c]);
+        }
+      } else {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const float4 a = *reinterpret_cast<const float4*>(stg + (4 * h + v) * 64 + 4 * g);
+          const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < KB; ++c) acc[r][c] = fmaf(av[r], b[v][c], acc[r][c]);
+        }
+      }
+    }
+    // every warp is done with the slot; a failed wait anywhere stops the CTA
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    ++done;
+    if (w == 0 && i + BULK_DEPTH < nst) bulk_issue(t, transA, i + BULK_DEPTH, ring, bar0, lane);
+  }
+  const int issued = min(nst, done + BULK_DEPTH);
+  if (failed) {
+    if (tid == 0) {
+      atomicExch(&g_bulk_timeout, 1);
+      // let the copies in flight land before the shared memory is released
+      for (int i = done; i < issued; ++i) bulk_wait(bar0 + 8u * (i % BULK_DEPTH), (unsigned)((i / BULK_DEPTH) & 1));
+    }
+    __syncthreads();
+    return;
+  }
+  // sum the 16 k slices: red[h][row][c] in the (now idle) ring
+  float* red = ring;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    float* o = red + ((size_t)h * 64 + 4 * g + r) * KB;
+    *reinterpret_cast<float4*>(o) = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+    *reinterpret_cast<float4*>(o + 4) = make_float4(acc[r][4], acc[r][5], acc[r][6], acc[r][7]);
+  }
+  __syncthreads();
+  const float sgn = (t.flags & S_NEG) ? -1.f : 1.f;
+  const double* gfull = nullptr;
+  double* sfull = nullptr;
+  if (t.flags & (S_INIT_GATHER | S_SCATTER)) {
+    const SubDev& s = subs[t.sub];
+    if (t.flags & S_INIT_GATHER) gfull = mv_ptr(s, src) + (size_t)t.row_off * KB;
+    if (t.flags & S_SCATTER) sfull = mv_ptr(s, dst) + (size_t)t.row_off * KB;
+  }
+  const double gsg = gather_neg ? -1.0 : 1.0;
+  for (int e = tid; e < 64 * KB; e += 256) {
+    const int r = e / KB, c = e % KB;
+    float v = 0.f;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v += red[(size_t)q * 64 * KB + e];
+    v = sgn * v;
+    if (t.flags & S_INIT_TILE) v += t.init[r * KB + c];
+    const int gmr = (t.flags & S_INIT_GATHER) ? t.gmap[r] : -1;
+    if (gmr >= 0) v += (float)(gsg * gfull[(size_t)gmr * KB + c]);
+    t.C[r * KB + c] = v;
+    const int smr = (t.flags & S_SCATTER) ? t.smap[r] : -1;
+    if (smr >= 0) {
+      double* o = sfull + (size_t)smr * KB + c;
+      *o = scatter_add ? *o + (double)v : (double)v;
+    }
+  }
+}
+
+size_t solve_bulk_smem(int kmax) {
+  return (size_t)BULK_DEPTH * BULK_STAGE * sizeof(float) + (size_t)((kmax + 3) / 4) * BULK_CS * sizeof(float) +
+         BULK_DEPTH * sizeof(unsigned long long);
+}
+
 constexpr size_t SOLVE_SMEM_MAX = 110 * 1024;
 
 constexpr int SOLVE_CL = SOLVE_CLUSTER;   // CTAs per task (cluster size) of the streaming solve
@@ -533,6 +734,7 @@ void prepare_tile_kernels() {
   cudaFuncSetAttribute(k_tile_task<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
   cudaFuncSetAttribute(k_solve_stream<double, SOLVE_CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
   cudaFuncSetAttribute(k_solve_stream<float, SOLVE_CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
+  cudaFuncSetAttribute(k_solve_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
   done = true;
 }
 
@@ -550,7 +752,17 @@ void run_solve_mv(const SolveScheduleT<T>& s, cudaStream_t st, int src, int dst,
   prepare_tile_kernels();
   const size_t smem = solve_stream_smem<T>(s.kmax, SOLVE_CL);
   const bool stream_ok = smem <= SOLVE_SMEM_MAX;
+  // FP32: bulk-copy pipeline when every task's inner dimension is a multiple of 64
+  const size_t bsmem = solve_bulk_smem(s.kmax);
+  const bool bulk_ok = std::is_same<T, float>::value && s.k64 && bsmem <= SOLVE_SMEM_MAX && SOLVE_BULK;
   run_groups(s, st, gs, [&](const SchedStep& step, cudaStream_t stream) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (width == KB && bulk_ok) {
+        k_solve_bulk<<<step.count, 256, bsmem, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
+                                                         gather_neg, scatter_add);
+        return;
+      }
+    }
     if (width == KB && stream_ok && SOLVE_CL == 1) {
       k_solve_stream<T, 1><<<step.count, 256, smem, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
                                                               gather_neg, scatter_add);
@@ -576,6 +788,17 @@ void run_solve_mv(const SolveScheduleT<T>& s, cudaStream_t st, int src, int dst,
       k_solve_step<T, PST><<<step.count, 256, 0, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
                                                            gather_neg, scatter_add);
   });
+}
+
+// 1 if a bulk-copy pipeline wait expired since the last call (and clear it)
+int solve_pipeline_failed() {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_bulk_timeout, sizeof(int)) != cudaSuccess) return 1;
+  if (v) {
+    const int z = 0;
+    cudaMemcpyToSymbol(g_bulk_timeout, &z, sizeof(int));
+  }
+  return v;
 }
 
 template void run_schedule<double>(const ScheduleT<double>&, cudaStream_t, const StreamSet*);

@@ -338,6 +338,7 @@ void flatten_solve(std::map<long long, std::vector<SolveTaskT<T>>>& keys, SolveS
     sch.steps.clear();
     sch.tasks.clear();
     sch.kmax = 0;
+    sch.k64 = true;
   }
   sch.steps.emplace_back();
   for (auto& kv : keys) {
@@ -346,7 +347,10 @@ void flatten_solve(std::map<long long, std::vector<SolveTaskT<T>>>& keys, SolveS
     std::stable_sort(kv.second.begin(), kv.second.end(),
                      [](const SolveTaskT<T>& x, const SolveTaskT<T>& y) { return x.K > y.K; });
     sch.steps.back().push_back({(int)sch.tasks.size(), (int)kv.second.size()});
-    for (const auto& t : kv.second) sch.kmax = std::max(sch.kmax, t.K);
+    for (const auto& t : kv.second) {
+      sch.kmax = std::max(sch.kmax, t.K);
+      if (t.K % 64 != 0) sch.k64 = false;
+    }
     sch.tasks.insert(sch.tasks.end(), kv.second.begin(), kv.second.end());
   }
 }
@@ -412,6 +416,7 @@ void build_solves_t(msgfem* h, SolveScheduleT<T>& sK, SolveScheduleT<T>& sA, Sol
     ss->steps.clear();
     ss->tasks.clear();
     ss->kmax = 0;
+    ss->k64 = true;
   }
   for (int g = 0; g < ng; ++g) {
     flatten_solve(kk[g], sK, true);

@@ -21,7 +21,7 @@ KB = 8   # width of the eigensolver's start block
 
 
 class WarmStart:
-    def __init__(self, m, n_loc, hidden=(256, 256), scale=1.0 / 3.0, seed=0, max_batch=512, stream=None):
+    def __init__(self, m, n_loc, hidden=(32,), scale=1.0 / 3.0, seed=0, max_batch=512, stream=None):
         import torch
         self.torch = torch
         self.m = m
@@ -85,7 +85,7 @@ class WarmStart:
             sizes, p = self._init_params(j)
             self.nets.append(Net(sizes, self.max_batch, p, self.stream))
 
-    def fit(self, X, T, steps=600, lr=1e-3, batch=64, seed=0):
+    def fit(self, X, T, steps=4000, lr=3e-4, batch=64, seed=0):
         """X: device [S][N][nfeat]; T: list over j of device [S][n2 * KB].  Returns final losses."""
         torch = self.torch
         if not self.nets:

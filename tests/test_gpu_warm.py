@@ -97,7 +97,7 @@ def test_warm_start_on_wrinkled_beam():
     from paper_2211_13893_gb300.warm import WarmStart
     cfg, m = _c5_handle()
     n_loc = cfg.n_loc
-    ws = WarmStart(m, n_loc, hidden=(128, 128), seed=3)
+    ws = WarmStart(m, n_loc, hidden=(32,), seed=3)
     m.local_spaces(n_loc)
     ws.set_nominal()
     n_train, n_test = 96, 12
@@ -112,7 +112,7 @@ def test_warm_start_on_wrinkled_beam():
             T[j].append(t.reshape(-1))
     X = torch.stack(X)
     T = [torch.stack(t) for t in T]
-    losses = ws.fit(X, T, steps=400, lr=1e-3, batch=32)
+    losses = ws.fit(X, T, steps=1500, lr=3e-4, batch=32)
     assert all(np.isfinite(losses))
     ang_w, ang_c, it_w, it_c = [], [], [], []
     for s in range(384, 384 + n_test):
