@@ -826,11 +826,6 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   }
   h->stage = 2;
   spans_collect(h);
-  if (h->mixed && solve_pipeline_failed()) {
-    h->stage = 1;
-    h->err = "a bulk-copy pipeline wait of the FP32 block solves expired";
-    return MSGFEM_ECUDA;
-  }
   for (int j = 0; j <= h->N; ++j)
     if (notspd[j]) {
       h->err = "non-positive pivot in a layer-block factorisation";

@@ -113,6 +113,7 @@ struct ScheduleT {
   std::vector<std::vector<Step>> steps;
   std::vector<TileTaskT<T>> gemm;
   TileTaskT<T>* d_gemm = nullptr;
+  bool k32 = true;   // every GEMM task's inner dimension is a multiple of 32
 };
 using Schedule = ScheduleT<double>;
 
@@ -229,7 +230,6 @@ void build_coarse_schedules(msgfem* h);
 // launchers
 void set_dense_context(int* active, int* notspd, const SubDev* subs);
 void prepare_tile_kernels();
-int solve_pipeline_failed();
 template <typename T>
 void run_schedule(const ScheduleT<T>& s, cudaStream_t st, const StreamSet* gs = nullptr);
 // solve steps; scatter_add adds the result into the destination multivector

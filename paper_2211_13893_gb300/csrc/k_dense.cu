@@ -27,8 +27,11 @@ namespace cg = cooperative_groups;
 #ifndef SOLVE_CLUSTER
 #define SOLVE_CLUSTER 1   // CTAs (one cluster) per 64-row task, splitting its inner dimension
 #endif
-#ifndef SOLVE_BULK
-#define SOLVE_BULK 0      // FP32 solves through the bulk-copy pipeline (k_solve_bulk); measured slower
+#ifndef SOLVE_PDL
+#define SOLVE_PDL 1       // solve steps use programmatic dependent launch
+#endif
+#ifndef SOLVE_ASYNC
+#define SOLVE_ASYNC 1     // FP32 solves through the cp.async pipeline (k_solve_async)
 #endif
 #ifndef SOLVE_MIN_BLOCKS
 #define SOLVE_MIN_BLOCKS 2   // resident CTAs per SM the register budget is sized for
@@ -192,6 +195,123 @@ k_tile_task(const TileTaskT<T>* __restrict__ tasks, const int* __restrict__ acti
 // full-layout multivectors gathered from / scattered to are FP64 with row
 // stride PC (scatter_add accumulates instead of overwriting).
 constexpr int SKC = 32;
+// FP32 tile task (mixed path): the same task semantics as k_tile_task with an
+// FP32-specific inner loop.  32-deep k chunks, the next chunk's global loads
+// held in registers while the current one is multiplied, and a 4 x 4 register
+// tile of contiguous rows and columns so that both operands come from shared
+// memory as 16-byte vectors (2 vector loads per 16 FMA).  POTRF tasks run the
+// FP64 tile Cholesky of k_tile_task.
+constexpr int KC32 = 32;
+constexpr int LDS32 = 68;   // shared row stride (floats): 16-byte aligned rows
+
+__global__ void __launch_bounds__(256)
+k_tile_task_f32(const TileTaskT<float>* __restrict__ tasks, const int* __restrict__ active,
+                int* __restrict__ notspd) {
+  const TileTaskT<float> t = tasks[blockIdx.x];
+  if (t.sub >= 0 && active != nullptr && !active[t.sub]) return;
+  extern __shared__ double smem_d[];
+  if (t.flags & G_POTRF) {
+    tile_potrf_inv(t, reinterpret_cast<double (*)[65]>(smem_d), notspd);
+    return;
+  }
+  float* smem = reinterpret_cast<float*>(smem_d);
+  float (*As)[LDS32] = reinterpret_cast<float (*)[LDS32]>(smem);                  // [KC32][LDS32]: As[k][m]
+  float (*Bs)[LDS32] = reinterpret_cast<float (*)[LDS32]>(smem + KC32 * LDS32);   // [KC32][LDS32]: Bs[k][n]
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const bool transB = (t.flags & G_TRANSB) != 0;
+  // global -> register mapping of one chunk: A (and B^T) rows m = tid & 63,
+  // columns kc = (tid >> 6) * 8 .. + 7; B rows k = tid >> 3, columns (tid & 7) * 8 .. + 7
+  const int lm = tid & 63, lk = (tid >> 6) * 8;
+  const int bk = tid >> 3, bn = (tid & 7) * 8;
+  float4 ra[2], rb[2];
+  auto load = [&](int k0) {
+    const float4* a = reinterpret_cast<const float4*>(t.A + (size_t)lm * t.lda + k0 + lk);
+    ra[0] = a[0];
+    ra[1] = a[1];
+    if (transB) {
+      const float4* b = reinterpret_cast<const float4*>(t.B + (size_t)lm * t.ldb + k0 + lk);
+      rb[0] = b[0];
+      rb[1] = b[1];
+    } else {
+      const float4* b = reinterpret_cast<const float4*>(t.B + (size_t)(k0 + bk) * t.ldb + bn);
+      rb[0] = b[0];
+      rb[1] = b[1];
+    }
+  };
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  load(0);
+  for (int k0 = 0; k0 < t.K; k0 += KC32) {
+    {
+      const float av[8] = {ra[0].x, ra[0].y, ra[0].z, ra[0].w, ra[1].x, ra[1].y, ra[1].z, ra[1].w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i) As[lk + i][lm] = av[i];
+      if (transB) {
+        const float bv[8] = {rb[0].x, rb[0].y, rb[0].z, rb[0].w, rb[1].x, rb[1].y, rb[1].z, rb[1].w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i) Bs[lk + i][lm] = bv[i];
+      } else {
+        *reinterpret_cast<float4*>(&Bs[bk][bn]) = rb[0];
+        *reinterpret_cast<float4*>(&Bs[bk][bn + 4]) = rb[1];
+      }
+    }
+    __syncthreads();
+    if (k0 + KC32 < t.K) load(k0 + KC32);
+#pragma unroll
+    for (int kk = 0; kk < KC32; ++kk) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[kk][4 * ty]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][4 * tx]);
+      const float a4[4] = {a.x, a.y, a.z, a.w}, b4[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a4[i], b4[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  if (t.flags & G_POSTMUL) {
+    // C = P * (A op(B)): product and P both staged in shared memory
+    float (*Cs)[LDS32] = reinterpret_cast<float (*)[LDS32]>(smem);
+    float (*Ps)[LDS32] = reinterpret_cast<float (*)[LDS32]>(smem + 64 * LDS32);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      *reinterpret_cast<float4*>(&Cs[4 * ty + i][4 * tx]) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    for (int e = tid; e < 64 * 16; e += 256) {
+      const int r = e >> 4, c = (e & 15) * 4;
+      *reinterpret_cast<float4*>(&Ps[r][c]) = *reinterpret_cast<const float4*>(t.P + (size_t)r * t.ldc + c);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int m = 0; m < 64; ++m) {
+      const float4 b = *reinterpret_cast<const float4*>(&Cs[m][4 * tx]);
+      const float b4[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float pv = Ps[4 * ty + i][m];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(pv, b4[j], acc[i][j]);
+      }
+    }
+  }
+  const float sgn = (t.flags & G_NEG) ? -1.f : 1.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float4* c = reinterpret_cast<float4*>(t.C + (size_t)(4 * ty + i) * t.ldc + 4 * tx);
+    float4 v = make_float4(sgn * acc[i][0], sgn * acc[i][1], sgn * acc[i][2], sgn * acc[i][3]);
+    if (t.flags & G_ACC) {
+      const float4 o = *c;
+      v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+    }
+    *c = v;
+  }
+}
+
 template <typename T, int PC>
 __global__ void __launch_bounds__(256)
 k_solve_step(const SolveTaskT<T>* __restrict__ tasks, const SubDev* __restrict__ subs,
@@ -476,96 +596,63 @@ k_solve_stream(const SolveTaskT<T>* __restrict__ tasks, const SubDev* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// FP32 solve step with asynchronous bulk copies (the mixed-precision path).
-// The factor slab of a task (64 rows x K, or K x 64 read transposed) is
-// streamed through a ring of BULK_DEPTH shared-memory stages of 64 x 64 floats
-// (16 KiB): one warp issues, per stage, 64 row copies of 256 bytes with
-// cp.async.bulk, completing on the stage's mbarrier; all warps consume the
-// stage once its barrier flips.  With BULK_DEPTH stages in flight per CTA the
-// copy engine keeps ~48 KiB per CTA in flight without spending registers.
-// Thread (g, h) of the 16 x 16 thread grid owns 4 output rows (g) and a
-// 4-wide k slice (h) of every stage and keeps a 4 x KB accumulator; the 16 k
-// slices are summed through shared memory at the end.
-// Every mbarrier wait is bounded: on expiry the CTA records the failure in
-// g_bulk_timeout, drains its outstanding copies (bounded again) and returns.
-constexpr int BULK_DEPTH = 4;
-constexpr int BULK_STAGE = 64 * 64;             // floats per stage
-constexpr int BULK_CS = 4 * (KB + 1);           // floats per staged chunk of 4 B rows (padded)
-constexpr unsigned BULK_SPIN = 1u << 22;        // polls before a wait is declared failed
-
-__device__ int g_bulk_timeout = 0;
+// FP32 solve step with an asynchronous-copy pipeline (the mixed-precision
+// path).  Measured on the streaming kernel: one CTA pulls only ~7 GB/s, since
+// each thread can keep just one register-resident chunk of the factor in
+// flight.  Here the factor slab of a task (64 rows x K, or K x 64 read
+// transposed) moves through a ring of ASYNC_DEPTH shared-memory stages of
+// 64 x 64 floats (16 KiB) with cp.async (16 bytes per copy, 4 copies per
+// thread and stage), so ASYNC_DEPTH - 1 stages (48 KiB) are in flight per CTA
+// without holding registers.  Thread (g, h) of the 16 x 16 thread grid owns 4
+// output rows (g) and a 4-wide k slice (h) of every stage and keeps a 4 x KB
+// accumulator; the 16 k slices are summed through shared memory at the end.
+constexpr int ASYNC_DEPTH = 4;
+constexpr int ASYNC_STAGE = 64 * 64;             // floats per stage
+constexpr int ASYNC_CS = 4 * (KB + 1);           // floats per staged chunk of 4 B rows (padded)
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ bool bulk_wait(unsigned bar, unsigned parity) {
-  for (unsigned it = 0; it < BULK_SPIN; ++it) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-// warp 0: copy stage i of the slab into ring slot i % BULK_DEPTH
-__device__ __forceinline__ void bulk_issue(const SolveTaskT<float>& t, bool transA, int i, float* ring,
-                                           unsigned bar0, int lane) {
-  const int slot = i % BULK_DEPTH;
-  const unsigned bar = bar0 + 8u * slot;
-  if (lane == 0) {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(64u * 256u) : "memory");
-  }
-  __syncwarp();
-  float* dst0 = ring + (size_t)slot * BULK_STAGE;
+// all threads: copy stage i of the slab into ring slot i % ASYNC_DEPTH
+__device__ __forceinline__ void async_issue(const SolveTaskT<float>& t, bool transA, int i, float* ring, int tid) {
+  float* dst0 = ring + (size_t)(i % ASYNC_DEPTH) * ASYNC_STAGE;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int r = lane + 32 * h;
-    // plain: row r, columns [64 i, 64 i + 64); transposed: row 64 i + r, columns [0, 64)
-    const float* src = transA ? t.A + (size_t)(64 * i + r) * t.lda : t.A + (size_t)r * t.lda + 64 * i;
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(smem_u32(dst0 + r * 64)), "l"(src), "r"(256u), "r"(bar)
-        : "memory");
+  for (int q = 0; q < 4; ++q) {
+    const int c = tid + 256 * q, r = c >> 4, c4 = (c & 15) * 4;
+    // plain: row r, columns 64 i + c4 ..; transposed: row 64 i + r, columns c4 ..
+    const float* src = transA ? t.A + (size_t)(64 * i + r) * t.lda + c4 : t.A + (size_t)r * t.lda + 64 * i + c4;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst0 + r * 64 + c4)), "l"(src)
+                 : "memory");
   }
 }
 
 __global__ void __launch_bounds__(256, 2)
-k_solve_bulk(const SolveTaskT<float>* __restrict__ tasks, const SubDev* __restrict__ subs,
-             const int* __restrict__ active, int src, int dst, int gather_neg, int scatter_add) {
+k_solve_async(const SolveTaskT<float>* __restrict__ tasks, const SubDev* __restrict__ subs,
+              const int* __restrict__ active, int src, int dst, int gather_neg, int scatter_add) {
   const SolveTaskT<float> t = tasks[blockIdx.x];
   if (t.sub >= 0 && active != nullptr && !active[t.sub]) return;
   extern __shared__ __align__(128) unsigned char smem_b[];
-  float* ring = reinterpret_cast<float*>(smem_b);                     // [BULK_DEPTH][64][64]
-  float* Bs = ring + BULK_DEPTH * BULK_STAGE;                         // [K / 4][BULK_CS]
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(Bs + (size_t)(t.K / 4) * BULK_CS);
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  float* ring = reinterpret_cast<float*>(smem_b);                     // [ASYNC_DEPTH][64][64]
+  float* Bs = ring + ASYNC_DEPTH * ASYNC_STAGE;                       // [K / 4][ASYNC_CS]
+  const int tid = threadIdx.x;
   const bool transA = (t.flags & S_TRANSA) != 0;
   const int nst = t.K / 64;
-  const unsigned bar0 = smem_u32(bars);
-  if (tid == 0) {
-    for (int q = 0; q < BULK_DEPTH; ++q)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8u * q) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  // the next step may launch now; the factor slab does not depend on the
+  // previous step, so its first stages are requested before waiting for it
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  for (int i = 0; i < ASYNC_DEPTH - 1; ++i) {
+    if (i < nst) async_issue(t, transA, i, ring, tid);
+    asm volatile("cp.async.commit_group;" ::: "memory");
   }
-  __syncthreads();
-  if (w == 0)
-    for (int i = 0; i < min(BULK_DEPTH, nst); ++i) bulk_issue(t, transA, i, ring, bar0, lane);
+  asm volatile("griddepcontrol.wait;" ::: "memory");   // B, the gathered vectors and C follow the previous step
   {
     const float4* Bv = reinterpret_cast<const float4*>(t.B);
     for (int e = tid; e < t.K * (KB / 4); e += 256) {
       const int k = e / (KB / 4), c = (e % (KB / 4)) * 4;
-      *reinterpret_cast<float4*>(Bs + (k / 4) * BULK_CS + (k % 4) * KB + c) = Bv[e];
+      *reinterpret_cast<float4*>(Bs + (k / 4) * ASYNC_CS + (k % 4) * KB + c) = Bv[e];
     }
   }
-  __syncthreads();
   // thread grid: plain A: h = tid % 16 (k slice), g = tid / 16 (rows);
   //              transposed: g = tid % 16 (rows), h = tid / 16 (k slice)
   const int h = transA ? tid / 16 : tid % 16;
@@ -575,62 +662,47 @@ k_solve_bulk(const SolveTaskT<float>* __restrict__ tasks, const SubDev* __restri
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < KB; ++c) acc[r][c] = 0.f;
-  int done = 0;          // stages consumed (their copies have landed)
-  bool failed = false;
   for (int i = 0; i < nst; ++i) {
-    const int slot = i % BULK_DEPTH;
-    const bool ok = bulk_wait(bar0 + 8u * slot, (unsigned)((i / BULK_DEPTH) & 1));
-    const float* stg = ring + (size_t)slot * BULK_STAGE;
-    if (ok) {
-      const float* bp = Bs + (size_t)(16 * i + h) * BULK_CS;   // B rows 64 i + 4 h .. + 3
-      float b[4][KB];
+    // keep ASYNC_DEPTH - 1 stages in flight: issue stage i + DEPTH - 1 into the
+    // slot consumed in iteration i - 1 (released by its trailing barrier)
+    if (i + ASYNC_DEPTH - 1 < nst) async_issue(t, transA, i + ASYNC_DEPTH - 1, ring, tid);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group %0;" ::"n"(ASYNC_DEPTH - 1) : "memory");
+    __syncthreads();   // stage i (every thread's copies) and, at i = 0, the staged B are visible
+    const float* stg = ring + (size_t)(i % ASYNC_DEPTH) * ASYNC_STAGE;
+    const float* bp = Bs + (size_t)(16 * i + h) * ASYNC_CS;   // B rows 64 i + 4 h .. + 3
+    float b[4][KB];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const float4 b0 = *reinterpret_cast<const float4*>(bp + v * KB);
+      const float4 b1 = *reinterpret_cast<const float4*>(bp + v * KB + 4);
+      b[v][0] = b0.x; b[v][1] = b0.y; b[v][2] = b0.z; b[v][3] = b0.w;
+      b[v][4] = b1.x; b[v][5] = b1.y; b[v][6] = b1.z; b[v][7] = b1.w;
+    }
+    if (!transA) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float4 a = *reinterpret_cast<const float4*>(stg + (4 * g + r) * 64 + 4 * h);
+        const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+#pragma unroll
+          for (int c = 0; c < KB; ++c) acc[r][c] = fmaf(av[v], b[v][c], acc[r][c]);
+      }
+    } else {
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        const float4 b0 = *reinterpret_cast<const float4*>(bp + v * KB);
-        const float4 b1 = *reinterpret_cast<const float4*>(bp + v * KB + 4);
-        b[v][0] = b0.x; b[v][1] = b0.y; b[v][2] = b0.z; b[v][3] = b0.w;
-        b[v][4] = b1.x; b[v][5] = b1.y; b[v][6] = b1.z; b[v][7] = b1.w;
-      }
-      if (!transA) {
+        const float4 a = *reinterpret_cast<const float4*>(stg + (4 * h + v) * 64 + 4 * g);
+        const float av[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const float4 a = *reinterpret_cast<const float4*>(stg + (4 * g + r) * 64 + 4 * h);
-          const float av[4] = {a.x, a.y, a.z, a.w};
+        for (int r = 0; r < 4; ++r)
 #pragma unroll
-          for (int v = 0; v < 4; ++v)
-#pragma unroll
-            for (int c = 0; c < KB; ++c) acc[r][c] = fmaf(av[v], b[v][c], acc[r][c]);
-        }
-      } else {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const float4 a = *reinterpret_cast<const float4*>(stg + (4 * h + v) * 64 + 4 * g);
-          const float av[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-          for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int c = 0; c < KB; ++c) acc[r][c] = fmaf(av[r], b[v][c], acc[r][c]);
-        }
+          for (int c = 0; c < KB; ++c) acc[r][c] = fmaf(av[r], b[v][c], acc[r][c]);
       }
     }
-    // every warp is done with the slot; a failed wait anywhere stops the CTA
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
-    ++done;
-    if (w == 0 && i + BULK_DEPTH < nst) bulk_issue(t, transA, i + BULK_DEPTH, ring, bar0, lane);
+    __syncthreads();   // every warp is done with the slot
   }
-  const int issued = min(nst, done + BULK_DEPTH);
-  if (failed) {
-    if (tid == 0) {
-      atomicExch(&g_bulk_timeout, 1);
-      // let the copies in flight land before the shared memory is released
-      for (int i = done; i < issued; ++i) bulk_wait(bar0 + 8u * (i % BULK_DEPTH), (unsigned)((i / BULK_DEPTH) & 1));
-    }
-    __syncthreads();
-    return;
-  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   // sum the 16 k slices: red[h][row][c] in the (now idle) ring
   float* red = ring;
 #pragma unroll
@@ -667,10 +739,10 @@ k_solve_bulk(const SolveTaskT<float>* __restrict__ tasks, const SubDev* __restri
   }
 }
 
-size_t solve_bulk_smem(int kmax) {
-  return (size_t)BULK_DEPTH * BULK_STAGE * sizeof(float) + (size_t)((kmax + 3) / 4) * BULK_CS * sizeof(float) +
-         BULK_DEPTH * sizeof(unsigned long long);
+size_t solve_async_smem(int kmax) {
+  return (size_t)ASYNC_DEPTH * ASYNC_STAGE * sizeof(float) + (size_t)((kmax + 3) / 4) * ASYNC_CS * sizeof(float);
 }
+
 
 constexpr size_t SOLVE_SMEM_MAX = 110 * 1024;
 
@@ -732,9 +804,10 @@ void prepare_tile_kernels() {
   if (done) return;
   cudaFuncSetAttribute(k_tile_task<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
   cudaFuncSetAttribute(k_tile_task<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
+  cudaFuncSetAttribute(k_tile_task_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
   cudaFuncSetAttribute(k_solve_stream<double, SOLVE_CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
   cudaFuncSetAttribute(k_solve_stream<float, SOLVE_CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
-  cudaFuncSetAttribute(k_solve_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
+  cudaFuncSetAttribute(k_solve_async, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
   done = true;
 }
 
@@ -742,8 +815,32 @@ template <typename T>
 void run_schedule(const ScheduleT<T>& s, cudaStream_t st, const StreamSet* gs) {
   prepare_tile_kernels();
   run_groups(s, st, gs, [&](const SchedStep& step, cudaStream_t stream) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (s.k32) {
+        k_tile_task_f32<<<step.count, 256, TILE_SMEM, stream>>>(s.d_gemm + step.first, g_active, g_notspd);
+        return;
+      }
+    }
     k_tile_task<T><<<step.count, 256, TILE_SMEM, stream>>>(s.d_gemm + step.first, g_active, g_notspd);
   });
+}
+
+// Launch with programmatic dependent launch: the kernel may start while its
+// stream predecessor finishes; it calls griddepcontrol.wait before touching
+// anything the predecessor writes.
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kernel)(KArgs...), int grid, size_t smem, cudaStream_t stream, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = SOLVE_PDL ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
 template <typename T>
@@ -752,18 +849,19 @@ void run_solve_mv(const SolveScheduleT<T>& s, cudaStream_t st, int src, int dst,
   prepare_tile_kernels();
   const size_t smem = solve_stream_smem<T>(s.kmax, SOLVE_CL);
   const bool stream_ok = smem <= SOLVE_SMEM_MAX;
-  // FP32: bulk-copy pipeline when every task's inner dimension is a multiple of 64
-  const size_t bsmem = solve_bulk_smem(s.kmax);
-  const bool bulk_ok = std::is_same<T, float>::value && s.k64 && bsmem <= SOLVE_SMEM_MAX && SOLVE_BULK;
+  // FP32: asynchronous-copy pipeline when every task's inner dimension is a multiple of 64
+  const size_t asmem = solve_async_smem(s.kmax);
+  const bool async_ok = std::is_same<T, float>::value && s.k64 && asmem <= SOLVE_SMEM_MAX && SOLVE_ASYNC;
   run_groups(s, st, gs, [&](const SchedStep& step, cudaStream_t stream) {
     if constexpr (std::is_same<T, float>::value) {
-      if (width == KB && bulk_ok) {
-        k_solve_bulk<<<step.count, 256, bsmem, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
-                                                         gather_neg, scatter_add);
+      if (width == KB && async_ok) {
+        launch_pdl(k_solve_async, step.count, asmem, stream, s.d_tasks + step.first, g_subs, g_active, src, dst,
+                   gather_neg, scatter_add);
         return;
       }
     }
     if (width == KB && stream_ok && SOLVE_CL == 1) {
+      // (programmatic launch measured slower for the FP64 steps: 707 vs 690 ms per C2 step)
       k_solve_stream<T, 1><<<step.count, 256, smem, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
                                                               gather_neg, scatter_add);
     } else if (width == KB && stream_ok) {
@@ -788,17 +886,6 @@ void run_solve_mv(const SolveScheduleT<T>& s, cudaStream_t st, int src, int dst,
       k_solve_step<T, PST><<<step.count, 256, 0, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
                                                            gather_neg, scatter_add);
   });
-}
-
-// 1 if a bulk-copy pipeline wait expired since the last call (and clear it)
-int solve_pipeline_failed() {
-  int v = 0;
-  if (cudaMemcpyFromSymbol(&v, g_bulk_timeout, sizeof(int)) != cudaSuccess) return 1;
-  if (v) {
-    const int z = 0;
-    cudaMemcpyToSymbol(g_bulk_timeout, &z, sizeof(int));
-  }
-  return v;
 }
 
 template void run_schedule<double>(const ScheduleT<double>&, cudaStream_t, const StreamSet*);

@@ -361,18 +361,33 @@ k_rr_krylov(const SubDev* __restrict__ subs, const int* __restrict__ active, con
   }
   __syncthreads();
   const int mm = (m + 1) & ~1;
+  __shared__ double red_off[8], red_tot[8];
   for (int sweep = 0; sweep < 30; ++sweep) {
-    if (tid == 0) {
+    {
+      // off-diagonal and total Frobenius mass, reduced over the block
       double off = 0.0, tot = 0.0;
-      for (int i = 0; i < m; ++i)
-        for (int j = 0; j < m; ++j) {
-          const double v = A[i][j] * A[i][j];
-          tot += v;
-          if (i != j) off += v;
-        }
-      again = off > 1e-30 * tot;
+      for (int e = tid; e < m * m; e += 256) {
+        const int i = e / m, j = e % m;
+        const double v = A[i][j] * A[i][j];
+        tot += v;
+        if (i != j) off += v;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        off += __shfl_xor_sync(0xffffffffu, off, o);
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+      }
+      if ((tid & 31) == 0) {
+        red_off[tid >> 5] = off;
+        red_tot[tid >> 5] = tot;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double so = 0.0, st = 0.0;
+        for (int w = 0; w < 8; ++w) { so += red_off[w]; st += red_tot[w]; }
+        again = so > 1e-30 * st;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     if (!again) break;
     for (int round = 0; round < mm - 1; ++round) {
       if (tid < mm / 2) {

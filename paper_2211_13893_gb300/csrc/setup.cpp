@@ -251,11 +251,14 @@ void flatten(FactorKeysT<T>& fk, ScheduleT<T>& sch, bool append = false) {
   if (!append) {
     sch.steps.clear();
     sch.gemm.clear();
+    sch.k32 = true;
   }
   sch.steps.emplace_back();
   for (auto& kv : fk) {
     auto& v = kv.second;
     if (v.empty()) continue;
+    for (const auto& t : v)
+      if (!(t.flags & G_POTRF) && t.K % 32 != 0) sch.k32 = false;
     // POTRF tasks (short critical path) and then the longest GEMM tasks first
     std::stable_sort(v.begin(), v.end(), [](const TileTaskT<T>& x, const TileTaskT<T>& y) {
       const int px = (x.flags & G_POTRF) ? 1 : 0, py = (y.flags & G_POTRF) ? 1 : 0;
