@@ -99,7 +99,14 @@ typedef struct {
   int profile;          /* 1: time the phases with CUDA events (msgfem_get_profile) */
   int solver;           /* 0: block Krylov (block width 8, basis <= 96), 1: subspace iteration */
   int streams;          /* independent task groups run on their own streams (1..16); 0 = 16 */
-  int refine;           /* MSGFEM_MIXED: FP64 refinement steps after each FP32 solve; 0 = 5 */
+  int refine;           /* MSGFEM_MIXED: most FP64 refinement steps after each FP32 solve (a
+                           subdomain stops once its relative residual is below 1e-13 or stops
+                           falling); 0 = 8 */
+  int instances;        /* batch of S >= 1 copies of the mesh and partition, each with its own
+                           element angles (elem_angle_deg holds S consecutive fields);
+                           subdomain j of copy i is subdomain i N0 + j of the handle.  With
+                           S > 1 the handle runs the local stage only (msgfem_coarse_assemble
+                           returns EINVAL).  0 = 1 */
 } msgfem_options;
 
 /* Phase timers (CUDA events on the handle's stream, milliseconds, summed over

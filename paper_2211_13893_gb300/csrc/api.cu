@@ -27,7 +27,7 @@ void launch_update_kb(msgfem* h, int wx, int xs, int nx, int wy, int only_floati
 void launch_h_accum(msgfem* h, int m, int j, int add);
 void launch_cholqr_kb(msgfem* h, int j, int pass);
 void launch_rotate_kb(msgfem* h, int which);
-void launch_store_block(msgfem* h, int src, int j);
+void launch_store_block(msgfem* h, int src, int j, int dst);
 void launch_random_kb(msgfem* h, int which, unsigned long long seed);
 void launch_mask_kb(msgfem* h, int which, int keep);
 void launch_zero_pins_kb(msgfem* h, int which);
@@ -35,7 +35,7 @@ void launch_load_col_kb(msgfem* h, int which, double sign);
 void launch_take_col_kb(msgfem* h, int which);
 void launch_zero_kb(msgfem* h, int which);
 void launch_rr_krylov(msgfem* h, const int* d_m, const int* d_nw);
-void launch_ritz(msgfem* h, const int* d_m, const int* d_nw, int scale, bool masked);
+void launch_ritz(msgfem* h, const int* d_m, const int* d_nw, int scale, bool masked, int src, int dst);
 void launch_restart(msgfem* h, int m, int k);
 constexpr double KRYLOV_SIGMA = 1e-2;   // N = S + sigma T (matches KSIGMA in k_krylov.cu)
 
@@ -77,23 +77,27 @@ bool is_device_ptr(const void* p) {
 
 msgfem_status set_angles(msgfem* h, const double* ang) {
   const size_t nel = (size_t)h->NX * h->NY * h->NZ;
-  h->h_angles.resize(nel);
+  const size_t ntot = nel * h->S;   // one field per instance
+  h->h_angles.resize(ntot);
   if (is_device_ptr(ang)) {
-    CK(cudaMemcpy(h->h_angles.data(), ang, nel * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(h->h_angles.data(), ang, ntot * sizeof(double), cudaMemcpyDeviceToHost));
   } else {
-    memcpy(h->h_angles.data(), ang, nel * sizeof(double));
+    memcpy(h->h_angles.data(), ang, ntot * sizeof(double));
   }
-  for (size_t e = 0; e < nel; ++e)
+  for (size_t e = 0; e < ntot; ++e)
     if (!std::isfinite(h->h_angles[e])) {
       h->err = "non-finite element angle";
       return MSGFEM_EINVAL;
     }
-  // element types: one per ply when the angle depends on the layer only
+  // element types: one per ply (and instance) when the angle depends on the
+  // layer only, else one per element (and instance)
   bool layered = true;
-  for (size_t e = 0; e < nel && layered; ++e) layered = h->h_angles[e] == h->h_angles[e % h->NZ];
+  for (size_t e = 0; e < ntot && layered; ++e)
+    layered = h->h_angles[e] == h->h_angles[(e / nel) * nel + e % h->NZ];
   std::vector<double> types;
   if (layered) {
-    types.assign(h->h_angles.begin(), h->h_angles.begin() + h->NZ);
+    for (int i = 0; i < h->S; ++i)
+      types.insert(types.end(), h->h_angles.begin() + (size_t)i * nel, h->h_angles.begin() + (size_t)i * nel + h->NZ);
   } else {
     types = h->h_angles;
   }
@@ -171,6 +175,8 @@ msgfem_status allocate(msgfem* h) {
     TRY(dalloc(h, &s.status, 4));
     TRY(dalloc(h, &s.QB, (size_t)s.nfull * MQ));
     CK(cudaMemset(s.QB, 0, (size_t)s.nfull * MQ * sizeof(double)));
+    TRY(dalloc(h, &s.NQ, (size_t)s.nfull * MQ));
+    CK(cudaMemset(s.NQ, 0, (size_t)s.nfull * MQ * sizeof(double)));
     double** kbs[] = {&s.Zb, &s.Wb, &s.Tb};
     for (double** m : kbs) {
       TRY(dalloc(h, m, (size_t)s.nfull * KB));
@@ -198,6 +204,9 @@ msgfem_status allocate(msgfem* h) {
   const size_t nchunk = (3 * (size_t)maxnode + 511) / 512;
   TRY(dalloc(h, &h->d_gram_part, nchunk * h->N * PST * PST));
   TRY(dalloc(h, &h->d_flags, h->N + 1));
+  TRY(dalloc(h, &h->d_flags_saved, h->N + 1));
+  TRY(dalloc(h, &h->d_rprev, (size_t)h->N * KB));
+  TRY(dalloc(h, &h->d_rref, (size_t)h->N * KB));
   TRY(dalloc(h, &h->d_notspd, h->N + 1));
   TRY(dalloc(h, &h->d_ncols, h->N));
   TRY(dalloc(h, &h->d_coff, h->N));
@@ -239,6 +248,7 @@ msgfem_status allocate(msgfem* h) {
 }
 
 msgfem_status set_active(msgfem* h, const std::vector<int>& act) {
+  h->act_host = act;
   std::vector<int> a(act);
   a.push_back(1);
   CK(cudaMemcpyAsync(h->d_flags, a.data(), a.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
@@ -299,9 +309,16 @@ void spans_collect(msgfem* h) {
 // their own.  Stencil flops: 18 per (node, neighbour) pair and column, 24 for
 // the fused K + sigma D_mu K D_mu pass (mode 4); a box of n nodes per axis has
 // (3 n - 2) (node, neighbour) pairs along that axis.
+// active(h, j): subdomain j takes part in the launches (inactive ones exit at once)
+bool active(const msgfem* h, int j) { return j >= (int)h->act_host.size() || h->act_host[j] != 0; }
+
 double stencil_flops(const msgfem* h, int width, int mode) {
   double pairs = 0.0;
-  for (const auto& s : h->sub) pairs += (3.0 * s.nxn - 2.0) * (3.0 * s.nyn - 2.0) * (3.0 * s.nzn - 2.0);
+  for (int j = 0; j < h->N; ++j) {
+    if (!active(h, j)) continue;
+    const SubDev& s = h->sub[j];
+    pairs += (3.0 * s.nxn - 2.0) * (3.0 * s.nyn - 2.0) * (3.0 * s.nzn - 2.0);
+  }
   return pairs * (mode == 4 ? 24.0 : 18.0) * width;
 }
 void timed_stencil_kb(msgfem* h, int src, int dst, int mode, double alpha) {
@@ -340,7 +357,9 @@ double factor_flops(const msgfem* h) {
 
 double solve_flops(const msgfem* h, int mat, int p) {
   double f = 0.0;
-  for (const auto& s : h->sub) {
+  for (int j = 0; j < h->N; ++j) {
+    if (!active(h, j)) continue;
+    const SubDev& s = h->sub[j];
     const double n = mat == 0 ? s.nK : s.nA;
     f += (4.0 * (s.nzn - 1) + 2.0 * s.nzn) * n * n * p;
   }
@@ -353,7 +372,9 @@ double solve_flops(const msgfem* h, int mat, int p) {
 double solve_bytes(const msgfem* h, int mat, int p) {
   double b = 0.0;
   const double es = h->mixed ? 4.0 : 8.0;
-  for (const auto& s : h->sub) {
+  for (int j = 0; j < h->N; ++j) {
+    if (!active(h, j)) continue;
+    const SubDev& s = h->sub[j];
     const double n = mat == 0 ? s.nK : s.nA;
     b += 2.0 * (s.nzn * n * (n + 1) / 2.0 + (s.nzn - 1) * n * n) * es + 2.0 * s.nzn * n * p * 8.0;
   }
@@ -411,33 +432,53 @@ void timed_solve_w(msgfem* h, int mat, int src, int dst, int neg, int width, int
 void timed_solve(msgfem* h, int mat, int src, int dst, int neg) { timed_solve_w(h, mat, src, dst, neg, PST, 0); }
 void timed_solve8(msgfem* h, int mat, int src, int dst, int neg) { timed_solve_w(h, mat, src, dst, neg, KB, 0); }
 
+// The active flags are saved around an adaptive refinement (subdomains drop
+// out of it one by one) and restored afterwards.
+void flags_save(msgfem* h) {
+  cudaMemcpyAsync(h->d_flags_saved, h->d_flags, (h->N + 1) * sizeof(int), cudaMemcpyDeviceToDevice, h->stream);
+}
+void flags_restore(msgfem* h) {
+  cudaMemcpyAsync(h->d_flags, h->d_flags_saved, (h->N + 1) * sizeof(int), cudaMemcpyDeviceToDevice, h->stream);
+}
+
 // W = K^{-1} Z on KB-wide blocks (pinned rows zero).  In mixed precision the
-// FP32 solve is followed by h->refine steps of iterative refinement with the
-// FP64 stencil residual Z - K W.
+// FP32 solve is followed by up to h->refine steps of iterative refinement with
+// the FP64 stencil residual Z - K W; a subdomain stops refining once its
+// relative residual is below REFINE_TOL or no longer falls (adaptive).
 void solve_K_kb(msgfem* h) {
   timed_solve8(h, 0, MV_ZB, MV_WB, 0);
   launch_zero_pins_kb(h, MV_WB);
   if (!h->mixed) return;
+  flags_save(h);
   for (int r = 0; r < h->refine; ++r) {
     timed_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
     launch_x_minus_y(h, MV_ZB, MV_TB, MV_TB, KB);
     launch_zero_pins_kb(h, MV_TB);
+    launch_refine_check(h, MV_TB, MV_ZB, KEEP_K, r);
     timed_solve_w(h, 0, MV_TB, MV_WB, 0, KB, 1);
     launch_zero_pins_kb(h, MV_WB);
   }
+  flags_restore(h);
 }
 
 // A-harmonic re-extension of a KB-wide block whose B1 rows are zero:
 // W_B1 = -A11^{-1} (K W)_B1, refined in mixed precision with the FP64
-// residual of the harmonic condition (K W)_B1.
+// residual of the harmonic condition (K W)_B1 (adaptive as above, relative to
+// the initial harmonic residual).
 void extend_kb(msgfem* h) {
   timed_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
+  if (h->mixed) {
+    flags_save(h);
+    launch_refine_check(h, MV_TB, -1, KEEP_A11, -1);
+  }
   timed_solve8(h, 1, MV_TB, MV_WB, 1);
   if (!h->mixed) return;
   for (int r = 0; r < h->refine; ++r) {
     timed_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
+    launch_refine_check(h, MV_TB, -1, KEEP_A11, r);
     timed_solve_w(h, 1, MV_TB, MV_WB, 1, KB, 1);
   }
+  flags_restore(h);
 }
 
 // B-orthogonal projection of a KB-wide block out of the rigid modes (floating only)
@@ -446,13 +487,16 @@ void project_rigid_kb(msgfem* h, int which) {
   timed_update_kb(h, MV_R, PST, 6, which, 1);
 }
 
-// CholeskyQR2 of the working block in the N inner product (R_{j+1} into H)
-void cholqr2_kb(msgfem* h, int j) {
+// CholeskyQR2 of the working block in the N inner product (R_{j+1} into H).
+// ZB holds N W on entry when have_nw (else it is formed here) and is rotated
+// along with W, so it holds N W on exit.
+void cholqr2_kb(msgfem* h, int j, bool have_nw) {
+  if (!have_nw) timed_stencil_kb(h, MV_WB, MV_ZB, 4, KRYLOV_SIGMA);
   for (int pass = 1; pass <= 2; ++pass) {
-    timed_stencil_kb(h, MV_WB, MV_ZB, 4, KRYLOV_SIGMA);
     timed_gram_kb(h, MV_WB, KB, KB, MV_ZB, 0);
     timed_cholqr_kb(h, j, pass);
     timed_rotate_kb(h, MV_WB);
+    timed_rotate_kb(h, MV_ZB);
   }
 }
 
@@ -563,12 +607,18 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
   // refined in mixed precision with the FP64 residual (K psi - b)_B1
   launch_load_col_kb(h, MV_TB, -1.0);
   launch_zero_kb(h, MV_WB);
+  if (h->mixed) {
+    flags_save(h);
+    launch_refine_check(h, MV_TB, -1, KEEP_A11, -1);   // reference ||b_B1||
+  }
   timed_solve8(h, 1, MV_TB, MV_WB, 1);
   for (int r = 0; h->mixed && r < h->refine; ++r) {
     timed_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
     launch_sub_load_kb(h, MV_TB);
+    launch_refine_check(h, MV_TB, -1, KEEP_A11, r);
     timed_solve_w(h, 1, MV_TB, MV_WB, 1, KB, 1);
   }
+  if (h->mixed) flags_restore(h);
   launch_take_col_kb(h, MV_WB);
   for (int j = 0; j < h->N; ++j)
     if (nw[j] <= 0) act[j] = 0;
@@ -585,8 +635,9 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
   project_rigid_kb(h, MV_WB);
   apply_M_kb(h);
   // Q_0 = W R^{-1} with W^T N W = R^T R (CholeskyQR2)
-  cholqr2_kb(h, -1);
-  launch_store_block(h, MV_WB, 0);
+  cholqr2_kb(h, -1, false);
+  launch_store_block(h, MV_WB, 0, MV_QB);
+  launch_store_block(h, MV_ZB, 0, MV_NQ);
   CK_LAUNCH();
   h->iters.assign(h->N, 0);
   std::vector<double> res((size_t)h->N * PST);
@@ -599,15 +650,23 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
   for (int j = 0; j < jmax && !all_done; ++j) {
     const int m = (j + 1) * KB;
     apply_M_kb(h);   // W = M Q_j (W held Q_j)
-    // two passes of block Gram-Schmidt against Q_0..Q_j in the N inner product
+    // two passes of block Gram-Schmidt against Q_0..Q_j in the N inner
+    // product.  Each pass forms N W with a stencil pass (the first pass removes
+    // most of W, so N W cannot be carried through it); the small correction of
+    // the second pass is applied to N W with the stored N Q, and CholeskyQR2
+    // rotates it along with W.
     for (int pass = 0; pass < 2; ++pass) {
       timed_stencil_kb(h, MV_WB, MV_ZB, 4, KRYLOV_SIGMA);
       timed_gram_kb(h, MV_QB, MQ, m, MV_ZB, 0);
       timed_h_accum(h, m, j, pass);
       timed_update_kb(h, MV_QB, MQ, m, MV_WB, 0);
     }
-    cholqr2_kb(h, j);
-    if (m < MQ) launch_store_block(h, MV_WB, j + 1);
+    timed_update_kb(h, MV_NQ, MQ, m, MV_ZB, 0);
+    cholqr2_kb(h, j, true);
+    if (m < MQ) {
+      launch_store_block(h, MV_WB, j + 1, MV_QB);
+      launch_store_block(h, MV_ZB, j + 1, MV_NQ);
+    }
     CK_LAUNCH();
     // Rayleigh-Ritz where the basis can hold the wanted pairs plus one block
     bool any = false;
@@ -647,7 +706,8 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
       // thick restart of the unconverged subdomains: keep kkeep Ritz vectors and
       // the residual block, continue from block kkeep / KB
       ++restarts;
-      launch_ritz(h, h->d_mk, h->d_ncols, 0, true);
+      launch_ritz(h, h->d_mk, h->d_ncols, 0, true, MV_QB, MV_PHI);
+      launch_ritz(h, h->d_mk, h->d_ncols, 0, true, MV_NQ, MV_CW);
       launch_restart(h, m, kkeep);
       CK_LAUNCH();
       j = kkeep / KB - 1;
@@ -656,7 +716,7 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
   // Ritz vectors of the wanted pairs (theta ascending in s.theta)
   TRY(set_active(h, std::vector<int>(h->N, 1)));
   CK(cudaMemcpyAsync(h->d_mk, h->m_final.data(), h->N * sizeof(int), cudaMemcpyHostToDevice, st));
-  launch_ritz(h, h->d_mk, h->d_nwk, 1, false);
+  launch_ritz(h, h->d_mk, h->d_nwk, 1, false, MV_QB, MV_PHI);
   timed_stencil_apply(h, MV_PHI, MV_Z, 3, 1.0);
   timed_stencil_apply(h, MV_PHI, MV_KPHI, 0, 1.0);
   CK_LAUNCH();
@@ -690,7 +750,8 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
     return MSGFEM_EINVAL;
   }
   h->mixed = h->opt.precision == MSGFEM_MIXED;
-  h->refine = h->opt.refine > 0 ? h->opt.refine : 5;
+  h->S = h->opt.instances > 1 ? h->opt.instances : 1;
+  h->refine = h->opt.refine > 0 ? h->opt.refine : 8;
   *out = h;
   msgfem_status st = build_problem(h);
   if (st != MSGFEM_OK) return st;
@@ -782,7 +843,7 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   // 4. final residuals: S x = (K Phi)|B2, T x = -(K y~)|B2 with y~ = A11^{-1} Z|B1
   for (auto& s : h->sub) CK(cudaMemsetAsync(s.T1, 0, (size_t)s.nfull * PST * sizeof(double), st));
   timed_solve(h, 1, MV_Z, MV_T1, 0);
-  for (int r = 0; h->mixed && r < h->refine; ++r) {   // refine y~: residual Z - K y~ on B1
+  for (int r = 0; h->mixed && r < std::min(h->refine, 5); ++r) {   // refine y~: residual Z - K y~ on B1
     timed_stencil_apply(h, MV_T1, MV_W, 0, 1.0);
     launch_x_minus_y(h, MV_Z, MV_W, MV_W, PST);
     timed_solve_w(h, 1, MV_W, MV_T1, 0, PST, 1);
@@ -841,6 +902,10 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
 msgfem_status msgfem_coarse_assemble(msgfem_h h, int* coarse_dim_out) {
   if (!h) return MSGFEM_EINVAL;
   if (h->stage < 2) return MSGFEM_ESTATE;
+  if (h->S > 1) {
+    h->err = "a handle with batched instances runs the local stage only";
+    return MSGFEM_EINVAL;
+  }
   cudaStream_t st = h->stream;
   const int n_loc = h->n_loc;
   set_dense_context(h->d_flags, h->d_notspd, h->d_sub);

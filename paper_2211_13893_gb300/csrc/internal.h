@@ -59,11 +59,12 @@ using SolveTask = SolveTaskT<double>;
 
 // multivector selectors
 enum { MV_PHI = 0, MV_Z, MV_KPHI, MV_W, MV_T1, MV_R, MV_BR, MV_EV, MV_CB, MV_CW,
-       MV_QB, MV_ZB, MV_WB, MV_TB };   // QB: [nfull][MQ]; ZB, WB, TB: [nfull][KB]
+       MV_QB, MV_ZB, MV_WB, MV_TB, MV_NQ };   // QB, NQ: [nfull][MQ]; ZB, WB, TB: [nfull][KB]
 enum { GM_G1 = 0, GM_G2, GM_G3, GM_Y };
 
 // Device-visible per-subdomain descriptor.
 struct SubDev {
+  int inst;                    // instance of the batch this subdomain belongs to
   int I0, I1, J0, J1;          // Omega* node box
   int oI0, oI1, oJ0, oJ1;      // Omega node box
   int nxn, nyn, nzn, npl, nnode, nfull;
@@ -89,7 +90,8 @@ struct SubDev {
   double* resid;               // [PST]
   int* status;                 // [4]: 1 RR pencil degenerate, 2 kept basis columns
   // block Krylov eigensolver
-  double* QB;                  // [nfull][MQ] T-orthonormal basis (A-harmonic vectors)
+  double* QB;                  // [nfull][MQ] N-orthonormal basis (A-harmonic vectors)
+  double* NQ;                  // [nfull][MQ] N QB, kept with the basis (no stencil to re-form it)
   double* Zb; double* Wb; double* Tb;   // [nfull][KB] working blocks
   double* ycK8; double* ycA8;  // [nzn][b][KB] compact solve buffers
   double* rcK8; double* rcA8;  // [b][KB]
@@ -161,11 +163,14 @@ struct msgfem {
   std::map<uint64_t, std::pair<cudaGraphExec_t, long long>> graphs;   // key -> (graph, kernel nodes)
   int ngroup = NGROUP;               // groups in use (msgfem_options.streams)
   int N = 0;
+  int S = 1;                         // instances of the mesh batched in this handle
+  int N0 = 0;                        // subdomains per instance (N = S N0)
   int layered = 0, ntypes = 0, type_cap = 0;
   std::vector<double> h_angles;
   std::vector<SubDev> sub;
   std::vector<HostSub> hsub;
   std::vector<int> n1, n2, n3, iters, basis_m, m_final;
+  std::vector<int> act_host;         // host copy of the active flags last uploaded
   std::vector<double> resid_max;
   std::vector<void*> allocs;
   SubDev* d_sub = nullptr;
@@ -174,6 +179,9 @@ struct msgfem {
   double* d_Ke = nullptr;            // [ntypes][576]
   double* d_gram_part = nullptr;
   int* d_flags = nullptr;            // [N + 1] active flags (entry N: coarse, always 1)
+  int* d_flags_saved = nullptr;      // [N + 1] flags saved around an adaptive refinement
+  double* d_rprev = nullptr;         // [N][KB] residual norms of the previous refinement step
+  double* d_rref = nullptr;          // [N][KB] reference residual norms of the refinement
   int* d_notspd = nullptr;           // [N + 1]
   int* d_ncols = nullptr;            // [N]
   int* d_mk = nullptr;               // [N] Krylov basis size at the last Rayleigh-Ritz
@@ -257,6 +265,16 @@ void launch_scale_rows_mu(msgfem* h, int which);
 void launch_theta_axpy(msgfem* h, int wx, int wy, int wd, int p);
 void launch_x_minus_y(msgfem* h, int wx, int wy, int wd, int stride);
 void launch_sub_load_kb(msgfem* h, int which);
+// adaptive refinement: clear the active flag of subdomains whose residual
+// block wr (rows of the DoF classes in the bit mask keep) is converged or
+// stagnant (step -1 records the reference norm)
+void launch_refine_check(msgfem* h, int wr, int wref, int keep, int step);
+constexpr int KEEP_K = (1 << 1) | (1 << 2);   // rows of K: B1 and B2
+constexpr int KEEP_A11 = 1 << 1;               // rows of A11: B1
+#ifndef MSGFEM_REFINE_TOL
+#define MSGFEM_REFINE_TOL 1e-13
+#endif
+constexpr double REFINE_TOL = MSGFEM_REFINE_TOL;   // relative residual at which refinement stops
 void launch_coarse_blocks(msgfem* h);
 void launch_coarse_rhs(msgfem* h);
 void launch_prolong(msgfem* h);
@@ -291,13 +309,14 @@ __device__ __forceinline__ double* mv_ptr(const SubDev& s, int which) {
     case MV_CB: return s.CB;
     case MV_CW: return s.CW;
     case MV_QB: return s.QB;
+    case MV_NQ: return s.NQ;
     case MV_ZB: return s.Zb;
     case MV_WB: return s.Wb;
     default: return s.Tb;
   }
 }
 __device__ __forceinline__ int mv_stride(int which) {
-  return which == MV_QB ? MQ : (which >= MV_ZB ? KB : PST);
+  return (which == MV_QB || which == MV_NQ) ? MQ : (which >= MV_ZB ? KB : PST);
 }
 __device__ __forceinline__ double* gm_ptr(const SubDev& s, int which) {
   switch (which) {

@@ -114,7 +114,7 @@ k_element_stiffness(const double* __restrict__ angles, const double* __restrict_
 // (di, dj, dk) = ((s/9)-1, ((s/3)%3)-1, (s%3)-1).  Only elements inside the
 // Omega* box contribute (Eq. restricted_bilinear_form).
 __global__ void __launch_bounds__(216)
-k_stencil(const SubDev* __restrict__ subs, const double* __restrict__ Ke, int layered, int NY, int NZ) {
+k_stencil(const SubDev* __restrict__ subs, const double* __restrict__ Ke, int layered, int NY, int NZ, int nel) {
   const SubDev s = subs[blockIdx.y];
   const int tid = threadIdx.x;
   const int node = blockIdx.x * 8 + tid / 27, slot = tid % 27;
@@ -134,7 +134,7 @@ k_stencil(const SubDev* __restrict__ subs, const double* __restrict__ Ke, int la
         const int bx = ax + di, by = ay + dj, bz = az + dk;            // neighbour position
         if (bx < 0 || bx > 1 || by < 0 || by > 1 || bz < 0 || bz > 1) continue;
         const int a = ax + 2 * ay + 4 * az, b = bx + 2 * by + 4 * bz;
-        const int type = layered ? ke : (ie * NY + je) * NZ + ke;
+        const int type = layered ? s.inst * NZ + ke : s.inst * nel + (ie * NY + je) * NZ + ke;
         const double* K = Ke + (size_t)type * 576;
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -227,7 +227,8 @@ void launch_stencil(msgfem* h) {
   int maxn = 0;
   for (const auto& s : h->sub) maxn = std::max(maxn, s.nnode);
   dim3 grid((maxn + 7) / 8, h->N);
-  k_stencil<<<grid, 216, 0, h->stream>>>(h->d_sub, h->d_Ke, h->layered, h->NY, h->NZ); ++g_launch_count;
+  k_stencil<<<grid, 216, 0, h->stream>>>(h->d_sub, h->d_Ke, h->layered, h->NY, h->NZ, h->NX * h->NY * h->NZ);
+  ++g_launch_count;
 }
 
 template <typename T>

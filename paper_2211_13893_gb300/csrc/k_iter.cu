@@ -629,6 +629,68 @@ __global__ void k_x_minus_y(const SubDev* __restrict__ subs, const int* __restri
     D[e] = X[e] - Yv[e];
 }
 
+// Adaptive iterative refinement of the FP32 solves.  Per active subdomain and
+// column, the residual norm of the KB-wide block R over the rows of the DoF
+// classes in keep (bit c for class c: B1 and B2 for K, B1 for A11; the rows
+// the solve acts on) is compared with a reference norm: the column of the right-hand side
+// block Ref, or, when Ref is absent, the residual recorded at step -1.  A
+// column is done when its relative residual is below tol or fell by less than
+// 10 % since the previous step (the FP64 rounding floor of the residual); a
+// subdomain whose columns are all done leaves the remaining refinement steps:
+// its active flag is cleared and the caller restores the flags afterwards.
+// Columns with a zero reference (unused columns) count as done.
+__global__ void __launch_bounds__(256)
+k_refine_check(const SubDev* __restrict__ subs, int* __restrict__ flags, int wr, int wref, int keep, int step,
+               double tol, double* __restrict__ prev, double* __restrict__ refn) {
+  const int sidx = blockIdx.x;
+  if (!flags[sidx]) return;
+  const SubDev& s = subs[sidx];
+  const double* R = mv_ptr(s, wr);
+  const double* F = wref >= 0 ? mv_ptr(s, wref) : nullptr;
+  // thread t handles column t % KB of rows t / KB, t / KB + 32, ...
+  const int c = threadIdx.x % KB;
+  double r2 = 0.0, f2 = 0.0;
+  for (int row = threadIdx.x / KB; row < s.nfull; row += blockDim.x / KB) {
+    if (!((keep >> s.cls[(row / 3) % s.npl]) & 1)) continue;
+    const double rv = R[(size_t)row * KB + c];
+    r2 += rv * rv;
+    if (F) {
+      const double fv = F[(size_t)row * KB + c];
+      f2 += fv * fv;
+    }
+  }
+  // lanes with equal column are KB apart within a warp
+  for (int o = 16; o >= KB; o >>= 1) {
+    r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    f2 += __shfl_xor_sync(0xffffffffu, f2, o);
+  }
+  __shared__ double sr[8][KB], sf[8][KB];
+  if ((threadIdx.x & 31) < KB) {
+    sr[threadIdx.x >> 5][c] = r2;
+    sf[threadIdx.x >> 5][c] = f2;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double* pv = prev + (size_t)sidx * KB;
+  double* rf = refn + (size_t)sidx * KB;
+  bool all_done = true;
+  for (int cc = 0; cc < KB; ++cc) {
+    double rt = 0.0, ft = 0.0;
+    for (int w = 0; w < 8; ++w) { rt += sr[w][cc]; ft += sf[w][cc]; }
+    const double rn = sqrt(rt);
+    if (step < 0) {   // record the reference only
+      rf[cc] = rn;
+      pv[cc] = rn;
+      continue;
+    }
+    const double ref = F ? sqrt(ft) : rf[cc];
+    const bool done = ref == 0.0 || rn <= tol * ref || (step > 0 && rn > 0.9 * pv[cc]);
+    pv[cc] = rn;
+    all_done = all_done && done;
+  }
+  if (step >= 0 && all_done) flags[sidx] = 0;
+}
+
 // X[:, 0] -= bload (KB-wide block)
 __global__ void k_sub_load_kb(const SubDev* __restrict__ subs, int which) {
   const SubDev& s = subs[blockIdx.y];
@@ -641,6 +703,12 @@ __global__ void k_sub_load_kb(const SubDev* __restrict__ subs, int which) {
 void launch_x_minus_y(msgfem* h, int wx, int wy, int wd, int stride) {
   dim3 grid(256, h->N);
   k_x_minus_y<<<grid, 256, 0, h->stream>>>(h->d_sub, act(h), wx, wy, wd, stride); ++g_launch_count;
+}
+
+void launch_refine_check(msgfem* h, int wr, int wref, int keep, int step) {
+  k_refine_check<<<h->N, 256, 0, h->stream>>>(h->d_sub, h->d_flags, wr, wref, keep, step, REFINE_TOL,
+                                               h->d_rprev, h->d_rref);
+  ++g_launch_count;
 }
 
 void launch_sub_load_kb(msgfem* h, int which) {

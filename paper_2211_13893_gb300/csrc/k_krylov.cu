@@ -254,15 +254,17 @@ k_rotate_kb(const SubDev* __restrict__ subs, const int* __restrict__ active, int
   }
 }
 
-// QB[:, j KB + c] = src[:, c]
-__global__ void k_store_block(const SubDev* __restrict__ subs, const int* __restrict__ active, int src, int j) {
+// dst[:, j KB + c] = src[:, c] (dst = QB or NQ)
+__global__ void k_store_block(const SubDev* __restrict__ subs, const int* __restrict__ active, int src, int j,
+                              int dst) {
   const int sidx = blockIdx.y;
   if (active != nullptr && !active[sidx]) return;
   const SubDev& s = subs[sidx];
   const double* X = mv_ptr(s, src);
+  double* D = mv_ptr(s, dst);
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)s.nfull * KB;
        e += (size_t)gridDim.x * blockDim.x)
-    s.QB[(e / KB) * MQ + j * KB + e % KB] = X[e];
+    D[(e / KB) * MQ + j * KB + e % KB] = X[e];
 }
 
 __global__ void k_zero_kb(const SubDev* __restrict__ subs, int which, int col0_only) {
@@ -459,11 +461,12 @@ k_rr_krylov(const SubDev* __restrict__ subs, const int* __restrict__ active, con
   }
 }
 
-// Phi[:, i] = QB[:, 0:m] Yk[:, i] for i < nw, zero for i >= nw; with
-// scale = 1 the columns are B-normalised (factor sqrt(theta_i + sigma)).
+// dst[:, i] = src[:, 0:m] Yk[:, i] for i < nw, zero for i >= nw (src = QB:
+// Ritz vectors; src = NQ: their N products); with scale = 1 the columns are
+// B-normalised (factor sqrt(theta_i + sigma)).
 __global__ void __launch_bounds__(256)
 k_ritz(const SubDev* __restrict__ subs, const int* __restrict__ active, const int* __restrict__ mvec,
-       const int* __restrict__ nwvec, int scale) {
+       const int* __restrict__ nwvec, int scale, int src, int dst) {
   const int sidx = blockIdx.y;
   if (active != nullptr && !active[sidx]) return;
   const SubDev& s = subs[sidx];
@@ -473,28 +476,32 @@ k_ritz(const SubDev* __restrict__ subs, const int* __restrict__ active, const in
   __syncthreads();
   const int lane = threadIdx.x & 31;
   for (int r = blockIdx.x * 8 + (threadIdx.x >> 5); r < s.nfull; r += gridDim.x * 8) {
-    const double* q = s.QB + (size_t)r * MQ;
+    const double* q = mv_ptr(s, src) + (size_t)r * MQ;
     double acc = 0.0;
     for (int a0 = 0; a0 < m; a0 += 32) {
       const double qv = (a0 + lane < m) ? q[a0 + lane] : 0.0;
       const int na = min(32, m - a0);
       for (int a = 0; a < na; ++a) acc = fma(__shfl_sync(0xffffffffu, qv, a), Ys[a0 + a][lane], acc);
     }
-    s.Phi[(size_t)r * PST + lane] = (lane < nw) ? (scale ? acc * sqrt(s.theta[lane] + KSIGMA) : acc) : 0.0;
+    mv_ptr(s, dst)[(size_t)r * PST + lane] = (lane < nw) ? (scale ? acc * sqrt(s.theta[lane] + KSIGMA) : acc) : 0.0;
   }
 }
 
-// Thick restart, basis part: QB[:, 0:k] = Phi[:, 0:k] (Ritz vectors),
-// QB[:, k:k+KB] = W (the residual block Q_{m+1}).
-__global__ void k_restart_basis(const SubDev* __restrict__ subs, const int* __restrict__ active, int k) {
+// Thick restart, basis part: dst[:, 0:k] = ritz[:, 0:k] (Ritz vectors),
+// dst[:, k:k+KB] = block (the residual block Q_{m+1}); run for QB and for NQ.
+__global__ void k_restart_basis(const SubDev* __restrict__ subs, const int* __restrict__ active, int k, int ritz,
+                                int block, int dst) {
   const int sidx = blockIdx.y;
   if (active != nullptr && !active[sidx]) return;
   const SubDev& s = subs[sidx];
+  const double* R = mv_ptr(s, ritz);
+  const double* B = mv_ptr(s, block);
+  double* D = mv_ptr(s, dst);
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)s.nfull * (k + KB);
        e += (size_t)gridDim.x * blockDim.x) {
     const size_t r = e / (k + KB);
     const int c = (int)(e % (k + KB));
-    s.QB[r * MQ + c] = c < k ? s.Phi[r * PST + c] : s.Wb[r * KB + (c - k)];
+    D[r * MQ + c] = c < k ? R[r * PST + c] : B[r * KB + (c - k)];
   }
 }
 
@@ -564,9 +571,9 @@ void launch_rotate_kb(msgfem* h, int which) {
   k_rotate_kb<<<grid, 256, 0, h->stream>>>(h->d_sub, h->d_flags, which); ++g_launch_count;
 }
 
-void launch_store_block(msgfem* h, int src, int j) {
+void launch_store_block(msgfem* h, int src, int j, int dst) {
   dim3 grid(256, h->N);
-  k_store_block<<<grid, 256, 0, h->stream>>>(h->d_sub, h->d_flags, src, j); ++g_launch_count;
+  k_store_block<<<grid, 256, 0, h->stream>>>(h->d_sub, h->d_flags, src, j, dst); ++g_launch_count;
 }
 
 void launch_random_kb(msgfem* h, int which, unsigned long long seed) {
@@ -606,13 +613,16 @@ void launch_rr_krylov(msgfem* h, const int* d_m, const int* d_nw) {
   k_rr_krylov<<<h->N, 256, smem, h->stream>>>(h->d_sub, h->d_flags, d_m, d_nw); ++g_launch_count;
 }
 
-void launch_ritz(msgfem* h, const int* d_m, const int* d_nw, int scale, bool masked) {
+void launch_ritz(msgfem* h, const int* d_m, const int* d_nw, int scale, bool masked, int src, int dst) {
   dim3 grid(std::max(1, (3 * max_nnode_k(h) + 8 * 16 - 1) / (8 * 16)), h->N);
-  k_ritz<<<grid, 256, 0, h->stream>>>(h->d_sub, masked ? h->d_flags : nullptr, d_m, d_nw, scale); ++g_launch_count;
+  k_ritz<<<grid, 256, 0, h->stream>>>(h->d_sub, masked ? h->d_flags : nullptr, d_m, d_nw, scale, src, dst);
+  ++g_launch_count;
 }
 
+// Thick restart: QB = [Ritz vectors (PHI) | W], NQ = [their N products (CW) | N W (ZB)]
 void launch_restart(msgfem* h, int m, int k) {
   dim3 grid(256, h->N);
-  k_restart_basis<<<grid, 256, 0, h->stream>>>(h->d_sub, h->d_flags, k); ++g_launch_count;
+  k_restart_basis<<<grid, 256, 0, h->stream>>>(h->d_sub, h->d_flags, k, MV_PHI, MV_WB, MV_QB); ++g_launch_count;
+  k_restart_basis<<<grid, 256, 0, h->stream>>>(h->d_sub, h->d_flags, k, MV_CW, MV_ZB, MV_NQ); ++g_launch_count;
   k_restart_h<<<h->N, 256, 0, h->stream>>>(h->d_sub, h->d_flags, m, k); ++g_launch_count;
 }

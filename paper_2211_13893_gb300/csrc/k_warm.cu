@@ -9,8 +9,9 @@ namespace {
 
 // features of subdomain j: dtheta on the elements of the Omega* box, (i, j, k) order, k fastest
 __global__ void k_warm_features(const SubDev* __restrict__ subs, const double* __restrict__ dtheta, int NY, int NZ,
-                                float scale, float* __restrict__ feat, int ld) {
+                                long long nel, float scale, float* __restrict__ feat, int ld) {
   const SubDev& s = subs[blockIdx.y];
+  dtheta += (size_t)s.inst * nel;   // the instance's field
   const int ex = s.I1 - s.I0, ey = s.J1 - s.J0;
   const int ne = ex * ey * NZ;
   float* f = feat + (size_t)blockIdx.y * ld;
@@ -202,7 +203,8 @@ msgfem_status msgfem_warm_features(msgfem_h h, const double* dtheta, float scale
     return MSGFEM_EINVAL;
   }
   dim3 grid((ld + 255) / 256, h->N);
-  k_warm_features<<<grid, 256, 0, h->stream>>>(h->d_sub, dtheta, h->NY, h->NZ, scale, feat, ld);
+  k_warm_features<<<grid, 256, 0, h->stream>>>(h->d_sub, dtheta, h->NY, h->NZ, (long long)h->NX * h->NY * h->NZ, scale,
+                                               feat, ld);
   ++g_launch_count;
   CK(cudaGetLastError());
   return MSGFEM_OK;

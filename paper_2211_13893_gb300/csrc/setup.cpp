@@ -107,6 +107,7 @@ msgfem_status build_problem(msgfem* h) {
     HostSub& hs = h->hsub[j];
     const Box& st = star[j];
     const Box& om = omega[j];
+    s.inst = 0;
     s.I0 = st.x0; s.I1 = st.x1; s.J0 = st.y0; s.J1 = st.y1;
     s.oI0 = om.x0; s.oI1 = om.x1; s.oJ0 = om.y0; s.oJ1 = om.y1;
     s.nxn = st.x1 - st.x0 + 1;
@@ -176,10 +177,26 @@ msgfem_status build_problem(msgfem* h) {
           hs.bload[((size_t)k * s.npl + q) * 3] = -h->traction * h->hy * h->hz * wy * wz;
         }
   }
+  // batched instances: subdomain j of instance i is subdomain i N0 + j
+  h->N0 = h->N;
+  if (h->S > 1) {
+    for (int i = 1; i < h->S; ++i)
+      for (int j = 0; j < h->N0; ++j) {
+        SubDev c = h->sub[j];
+        c.inst = i;
+        h->sub.push_back(c);
+        h->hsub.push_back(h->hsub[j]);
+        h->n1.push_back(h->n1[j]);
+        h->n2.push_back(h->n2[j]);
+        h->n3.push_back(h->n3[j]);
+      }
+    h->N = h->S * h->N0;
+  }
   // coarse pairs: Omega_s node box intersected with Omega*_t node box
+  // (within one instance; the coarse problem exists for unbatched handles)
   h->pairs.clear();
-  for (int s = 0; s < h->N; ++s)
-    for (int t = 0; t < h->N; ++t) {
+  for (int s = 0; s < h->N0; ++s)
+    for (int t = 0; t < h->N0; ++t) {
       const SubDev& S = h->sub[s];
       const SubDev& T = h->sub[t];
       const int x0 = std::max(S.oI0, T.I0), x1 = std::min(S.oI1, T.I1);

@@ -45,7 +45,7 @@ class Partition(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("block", C.c_int), ("max_iter", C.c_int), ("tol", C.c_double),
                 ("seed", C.c_ulonglong), ("stream", C.c_void_p), ("profile", C.c_int), ("solver", C.c_int),
-                ("streams", C.c_int), ("refine", C.c_int)]
+                ("streams", C.c_int), ("refine", C.c_int), ("instances", C.c_int)]
 
 
 class Profile(C.Structure):
@@ -124,7 +124,8 @@ class MSGFEM:
     """One MS-GFEM problem: a laminated box mesh, its decomposition and the handle."""
 
     def __init__(self, nx, ny, nz, hx, hy, hz, traction, E9, elem_angles, sx, sy, overlap, oversampling,
-                 block=0, max_iter=0, tol=0.0, seed=0, stream=None, precision=0, profile=0, solver=0, streams=0, refine=0):
+                 block=0, max_iter=0, tol=0.0, seed=0, stream=None, precision=0, profile=0, solver=0, streams=0, refine=0,
+                 instances=0):
         self.lib = load_library()
         self.h = C.c_void_p()
         self._E9 = np.ascontiguousarray(E9, dtype=np.float64)
@@ -136,7 +137,8 @@ class MSGFEM:
         self.n_dof = 3 * (nx + 1) * (ny + 1) * (nz + 1)
         plies = Plies(self._E9.ctypes.data, _ptr(ang))
         part = Partition(sx, sy)
-        opt = Options(precision, block, max_iter, tol, seed, stream, profile, solver, streams, refine)
+        opt = Options(precision, block, max_iter, tol, seed, stream, profile, solver, streams, refine, instances)
+        self.instances = max(1, instances)
         st = self.lib.msgfem_setup(C.byref(self.mesh), C.byref(plies), C.byref(part), overlap, oversampling,
                                    C.byref(opt), C.byref(self.h))
         self._check(st)
