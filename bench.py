@@ -145,19 +145,19 @@ def _oracle_sub(args):
     os.environ["OMP_NUM_THREADS"] = "1"
     import numpy as np  # noqa: F401
     from oracle.arpack import local_eigs_arpack
-    from oracle.assemble import ElementCache
+    from oracle.assemble import make_cache
     from oracle.local import local_eigs_dense, local_problem, particular
-    from oracle.mesh import BeamMesh
+    from oracle.mesh import make_mesh
     from oracle.partition import partition_of_unity, subdomains
     from workloads import element_angles, get_config
     cfg = get_config(name)
-    m = BeamMesh.from_config(cfg)
+    m = make_mesh(cfg)
     ang = element_angles(cfg)
     subs = subdomains(cfg)
     mus = partition_of_unity(m, subs, cfg.overlap)
     t0 = time.perf_counter()
     lp = local_problem(m, ang, cfg.material, subs[j], mus[j], m.compression_load(cfg.traction),
-                       ElementCache(m, cfg.material))
+                       make_cache(m, cfg.material))
     (local_eigs_arpack if solver == "arpack" else local_eigs_dense)(lp, cfg.n_loc)
     particular(lp)
     return time.perf_counter() - t0

@@ -25,10 +25,10 @@ import scipy.sparse as sp
 from workloads import element_angles
 
 from .arpack import local_eigs_arpack
-from .assemble import ElementCache, assemble_global
+from .assemble import assemble_global, make_cache
 from .fine import energy_norm, solve_fine
 from .local import local_eigs_dense, local_problem, particular
-from .mesh import BeamMesh
+from .mesh import make_mesh
 from .partition import partition_of_unity, subdomains
 
 
@@ -84,12 +84,12 @@ class MSGFEMResult:
 
 def run_msgfem(cfg, angles=None, n_loc=None, variant="ii", solver="dense", uh=None,
                keep_problems=False):
-    mesh = BeamMesh.from_config(cfg)
+    mesh = make_mesh(cfg)
     E = cfg.material
     if angles is None:
         angles = element_angles(cfg)
     n_loc = cfg.n_loc if n_loc is None else n_loc
-    cache = ElementCache(mesh, E)
+    cache = make_cache(mesh, E)
     A = assemble_global(mesh, angles, E, cache=cache)
     b = mesh.compression_load(cfg.traction)
     subs = subdomains(cfg)

@@ -7,7 +7,10 @@ normal z (Sec. 5.1, "standard tensor rotations").
 
 Conventions (the paper does not fix them): Voigt order 11, 22, 33, 23, 13, 12
 with engineering shear strains; the fibre axis of a ply at angle theta is
-(cos theta, sin theta, 0), theta measured from x toward y about +z.
+(cos theta, sin theta, 0), theta measured from x toward y about +z.  On a
+curved laminate (the C-section spar) each element carries its own reference
+frame (a0, a1, a2); the fibre is then cos theta a0 + sin theta a1 and the
+normal a2, the same rotation applied in the element's frame.
 """
 import numpy as np
 
@@ -60,9 +63,24 @@ def rotation_z(theta_deg):
     return np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
 
 
-def rotated_tensor(E, theta_deg):
-    """Global-frame C_ijkl = R_ip R_jq R_kr R_ls C0_pqrs of a ply at angle theta."""
-    R = rotation_z(theta_deg)
+def material_axes(theta_deg, frame=None):
+    """Columns: fibre, in-plane transverse and normal axes in global coordinates.
+
+    ``frame`` (rows a0, a1, a2, orthonormal and right-handed) is the ply's
+    reference frame: the fibre lies at angle theta from a0 toward a1 in the
+    a0-a1 plane and a2 is the laminate normal.  ``None`` is the box beam's
+    frame (x, y, z), where this is ``rotation_z``.
+    """
+    Rz = rotation_z(theta_deg)
+    if frame is None:
+        return Rz
+    return np.asarray(frame, dtype=np.float64).T @ Rz
+
+
+def rotated_tensor(E, theta_deg, frame=None):
+    """Global-frame C_ijkl = R_ip R_jq R_kr R_ls C0_pqrs of a ply at angle theta
+    (R = ``material_axes(theta, frame)``)."""
+    R = material_axes(theta_deg, frame)
     return np.einsum("ip,jq,kr,ls,pqrs->ijkl", R, R, R, R, ply_tensor(E))
 
 

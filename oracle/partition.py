@@ -3,8 +3,9 @@
 Sec. 3.1: non-overlapping subdomains hat-Omega_j are extended by o element
 layers to Omega_j; Sec. 3.3: Omega_j is extended further to the oversampling
 domain Omega*_j (o* layers counted from hat-Omega_j, Sec. 4.2).  The
-non-overlapping subdomains here are a regular sx x sy box partition in (x, y)
-spanning the full thickness; subdomain (a, b) has index j = a sy + b.
+non-overlapping subdomains here are element boxes in (x, y) spanning the full
+thickness: a regular sx x sy partition (subdomain (a, b) has index
+j = a sy + b) or a list of boxes given by the workload.
 
 DoF classes on Omega*_j (Sec. 4.3): B3 = nodes on the clamped face, B2 =
 nodes on the closure of the cut boundary dOmega*_j inside Omega (minus B3),
@@ -35,6 +36,16 @@ def _split(n, parts, a):
 
 
 def subdomains(cfg):
+    """Subdomains of a workload: the regular sx x sy box partition, or the
+    explicit non-overlapping element boxes of ``cfg.boxes`` (C-section)."""
+    boxes = getattr(cfg, "boxes", None)
+    if boxes is not None:
+        out = []
+        for idx, (x0, x1, y0, y1) in enumerate(boxes):
+            def grow(m, x0=x0, x1=x1, y0=y0, y1=y1):
+                return (max(0, x0 - m), min(cfg.NX, x1 + m), max(0, y0 - m), min(cfg.NY, y1 + m))
+            out.append(Subdomain(idx, (x0, x1, y0, y1), grow(cfg.overlap), grow(cfg.oversampling)))
+        return out
     out = []
     for a in range(cfg.sx):
         for b in range(cfg.sy):

@@ -6,22 +6,22 @@ import scipy.linalg as sla
 import scipy.sparse.linalg as spla
 
 from oracle.arpack import local_eigs_arpack, saddle_pencil
-from oracle.assemble import ElementCache
+from oracle.assemble import make_cache
 from oracle.coarse import run_msgfem
 from oracle.local import local_eigs_dense, local_problem, particular
-from oracle.mesh import BeamMesh
+from oracle.mesh import make_mesh
 from oracle.partition import partition_of_unity, subdomains
 from workloads import element_angles, get_config
 
 
 def problems(name, **kw):
     cfg = get_config(name).with_(**kw) if kw else get_config(name)
-    m = BeamMesh.from_config(cfg)
+    m = make_mesh(cfg)
     ang = element_angles(cfg)
     subs = subdomains(cfg)
     mus = partition_of_unity(m, subs, cfg.overlap)
     b = m.compression_load(cfg.traction)
-    cache = ElementCache(m, cfg.material)
+    cache = make_cache(m, cfg.material)
     return cfg, m, [local_problem(m, ang, cfg.material, s, mus[s.index], b, cache) for s in subs]
 
 
@@ -93,7 +93,7 @@ def test_rigid_modes_on_floating_subdomains():
     assert np.abs(phi1[:, :6] @ coef - R).max() < 1e-8 * np.abs(R).max()
 
 
-@pytest.mark.parametrize("name", ["t2", "c1"])
+@pytest.mark.parametrize("name", ["t2", "c1", "s1"])
 def test_arpack_baseline_agrees(name):
     cfg, m, lps = problems(name)
     for lp in lps:
@@ -127,7 +127,7 @@ def test_oversampling_accelerates_decay():
     assert (inv[1] < inv[0]).all()
 
 
-@pytest.mark.parametrize("name", ["t1", "t2"])
+@pytest.mark.parametrize("name", ["t1", "t2", "s1"])
 def test_full_local_space_reproduces_fine_solution(name):
     """With n_loc = n2 the local spaces contain u_h|Omega* - psi_j, so the coarse
     Galerkin solution equals u_h up to roundoff (Eqs. global_particular_function,

@@ -88,5 +88,9 @@ CONFIGS = {
 }
 
 
-def get_config(name: str) -> BeamConfig:
-    return CONFIGS[name]
+def get_config(name: str):
+    """A box-beam workload (``BeamConfig``) or a C-section one (``SectionConfig``)."""
+    if name in CONFIGS:
+        return CONFIGS[name]
+    from .section import SECTIONS
+    return SECTIONS[name]
