@@ -15,17 +15,19 @@
  *     Eq. GFEM_coarse_approximation), and the coarse solution u^G.
  *
  * Geometry and numbering.  The mesh is a box of nx * ny * nz bricks of size
- * hx * hy * hz; node (i, j, k) sits at (i hx, j hy, k hz) and has global id
+ * hx * hy * hz, or a structured mesh with given node coordinates (see
+ * msgfem_mesh); node (i, j, k) sits at (i hx, j hy, k hz) and has global id
  * (i (ny+1) + j)(nz+1) + k; DoF 3 id + c holds displacement component c.
  * Element (i, j, k) has index (i ny + j) nz + k; layer k is ply k.  The x = 0
  * face is clamped (Gamma_D, zero displacement); the x = L face carries a
  * uniform compressive traction (-traction, 0, 0); the other faces are free.
  *
  * Decomposition.  The non-overlapping subdomains are an sx * sy box partition
- * in (x, y) over the full thickness (Sec. 3.1); subdomain (a, b) has index
- * j = a sy + b.  Omega_j grows the box by `overlap` element layers,
- * Omega*_j by `oversampling` layers, both counted from the non-overlapping
- * box and clipped to the mesh (Secs. 3.3, 4.2).
+ * in (x, y) over the full thickness (Sec. 3.1), subdomain (a, b) having index
+ * j = a sy + b, or a list of element boxes (msgfem_partition.boxes).
+ * Omega_j grows the box by `overlap` element layers, Omega*_j by
+ * `oversampling` layers, both counted from the non-overlapping box and
+ * clipped to the mesh (Secs. 3.3, 4.2).
  *
  * Memory and ownership.  All pointers passed in are owned by the caller and
  * are read (and copied where needed) during the call only.  Output arrays are
@@ -62,24 +64,46 @@ typedef enum {
   MSGFEM_ESTATE = 6     /* call out of order */
 } msgfem_status;
 
-/* Box mesh of nx * ny * nz bricks (Sec. 5.1: one element per ply). */
+/* Structured hexahedral mesh of nx * ny * nz elements (Sec. 5.1: one element
+ * per ply).  With xyz == NULL it is the box of bricks hx * hy * hz described
+ * above.  Otherwise xyz holds the coordinates of every node, 3 doubles per
+ * node in the global node order (host or device pointer, copied during
+ * msgfem_setup), hx, hy, hz are ignored, and each element is the trilinear
+ * map of its 8 nodes (curved laminates such as a C-section spar: index j then
+ * runs along the arc of the cross-section and k through the thickness).  The
+ * boundary faces stay the index faces: i = 0 clamped, i = nx loaded. */
 typedef struct {
   int nx, ny, nz;
   double hx, hy, hz;
-  double traction;      /* magnitude of the compressive traction on x = L (MPa) */
+  double traction;      /* magnitude of the compressive traction on x = L (MPa): the load is
+                           the consistent nodal force of (-traction, 0, 0) over the i = nx face */
+  const double* xyz;    /* NULL (box) or [(nx+1)(ny+1)(nz+1)][3] node coordinates */
 } msgfem_mesh;
 
 /* Orthotropic ply material and fibre angles (Sec. 5.1).
  * E9 = {E11, E22, E33, G12, G13, G23, nu12, nu13, nu23} in the ply axes.
- * elem_angle_deg[(i ny + j) nz + k] is the fibre angle of element (i, j, k),
- * measured from x toward y about +z (host or device pointer). */
+ * elem_angle_deg[(i ny + j) nz + k] is the fibre angle of element (i, j, k)
+ * (host or device pointer).  The angle is measured in the element's ply
+ * frame: elem_frame[9 e .. 9 e + 8] holds three orthonormal, right-handed
+ * unit vectors a0, a1, a2 (row-major 3 x 3, global coordinates); the fibre is
+ * cos(theta) a0 + sin(theta) a1 and a2 is the laminate normal.  NULL means
+ * a0, a1, a2 = x, y, z for every element (theta from x toward y about +z).
+ * The frames are copied during msgfem_setup (host or device pointer). */
 typedef struct {
   const double* E9;
   const double* elem_angle_deg;
+  const double* elem_frame;   /* NULL or [nx ny nz][9] */
 } msgfem_plies;
 
+/* Non-overlapping subdomains (Sec. 3.1): with n_boxes == 0 the regular
+ * sx * sy box partition described above; otherwise n_boxes element boxes
+ * boxes[4 j .. 4 j + 3] = {x0, x1, y0, y1} (elements [x0, x1) x [y0, y1) x
+ * all k) that must tile the nx * ny element grid exactly (EINVAL otherwise);
+ * subdomain j is box j and sx, sy are ignored.  Host pointer, copied. */
 typedef struct {
   int sx, sy;           /* subdomains along x and y */
+  int n_boxes;          /* 0 or the number of explicit boxes */
+  const int* boxes;     /* NULL or [n_boxes][4] */
 } msgfem_partition;
 
 /* MSGFEM_FP64: all arithmetic in FP64.  MSGFEM_MIXED: layer blocks, their
@@ -107,6 +131,13 @@ typedef struct {
                            subdomain j of copy i is subdomain i N0 + j of the handle.  With
                            S > 1 the handle runs the local stage only (msgfem_coarse_assemble
                            returns EINVAL).  0 = 1 */
+  double wave_mb;       /* device memory (MiB) for the layer blocks, factors and block-solve
+                           buffers.  Subdomains whose storage does not fit at once are processed
+                           in waves that share one pool of this size (largest first, a wave
+                           closed when the next subdomain no longer fits); results do not
+                           depend on the grouping.  0 = 80 % of the device memory free at
+                           set-up less room for the element matrices (one wave when everything
+                           fits).  ENOMEM if one subdomain alone exceeds it */
 } msgfem_options;
 
 /* Phase timers (CUDA events on the handle's stream, milliseconds, summed over
@@ -132,6 +163,8 @@ typedef struct {
   double ortho_ms;      /* Gram, block updates, CholeskyQR, basis rotations */
   double stencil_flops; /* per local stage: 18 flop per (node, neighbour) pair and column, 24 for the
                            fused K + sigma B pass */
+  int waves;            /* waves of subdomains per local stage (msgfem_options.wave_mb) */
+  double pool_mb;       /* size of the shared layer-block / factor / solve-buffer pool (MiB) */
 } msgfem_profile;
 
 /* Per-subdomain diagnostics filled by msgfem_get_info. */
@@ -147,7 +180,8 @@ typedef struct {
 /* Partition, DoF classes (Sec. 4.3) and partition of unity (Sec. 4.2) on the
  * host; copies the angles and allocates all device memory.  The handle is
  * written to *out.  Errors: EINVAL (sizes <= 0, overlap < 1, oversampling <
- * overlap, a subdomain without interior), ENOMEM, ECUDA. */
+ * overlap, a subdomain without interior, boxes that do not tile the mesh,
+ * non-finite coordinates or frames), ENOMEM, ECUDA. */
 msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies,
                            const msgfem_partition* part, int overlap, int oversampling,
                            const msgfem_options* opt, msgfem_h* out);

@@ -19,6 +19,8 @@
 #include <cstdio>
 #include <cstring>
 
+#include <type_traits>
+
 #include "internal.h"
 
 void launch_stencil_kb(msgfem* h, int src, int dst, int mode, double alpha);
@@ -91,7 +93,8 @@ msgfem_status set_angles(msgfem* h, const double* ang) {
     }
   // element types: one per ply (and instance) when the angle depends on the
   // layer only, else one per element (and instance)
-  bool layered = true;
+  // (node coordinates or ply frames make every element its own type)
+  bool layered = h->h_xyz.empty() && h->h_frame.empty();
   for (size_t e = 0; e < ntot && layered; ++e)
     layered = h->h_angles[e] == h->h_angles[(e / nel) * nel + e % h->NZ];
   std::vector<double> types;
@@ -113,6 +116,111 @@ msgfem_status set_angles(msgfem* h, const double* ang) {
   return MSGFEM_OK;
 }
 
+// Layer blocks (D, E, Linv of K and A11), their factors and the compact solve
+// buffers of one subdomain, in the factor's precision; the parts are laid out
+// in this order, each aligned to 256 bytes.  Returns the bytes used.
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+template <typename T>
+size_t place_blocks(SubDev& s, char* base, bool assign) {
+  const size_t bK2 = (size_t)s.bK * s.bK, bA2 = (size_t)s.bA * s.bA;
+  const size_t parts[12] = {bK2 * (2 * s.nzn - 1), bK2 * s.nzn, bA2 * (2 * s.nzn - 1), bA2 * s.nzn,
+                            (size_t)s.nzn * s.bK * PST, (size_t)s.nzn * s.bA * PST, (size_t)s.bK * PST,
+                            (size_t)s.bA * PST, (size_t)s.nzn * s.bK * KB, (size_t)s.nzn * s.bA * KB,
+                            (size_t)s.bK * KB, (size_t)s.bA * KB};
+  size_t off = 0;
+  T* p[12];
+  for (int i = 0; i < 12; ++i) {
+    p[i] = reinterpret_cast<T*>(base + off);
+    off = align_up(off + parts[i] * sizeof(T), 256);
+  }
+  if (assign) {
+    if constexpr (std::is_same<T, float>::value) {
+      s.DKf = p[0]; s.EKf = p[0] + bK2 * s.nzn; s.LKf = p[1];
+      s.DAf = p[2]; s.EAf = p[2] + bA2 * s.nzn; s.LAf = p[3];
+      s.ycKf = p[4]; s.ycAf = p[5]; s.rcKf = p[6]; s.rcAf = p[7];
+      s.ycK8f = p[8]; s.ycA8f = p[9]; s.rcK8f = p[10]; s.rcA8f = p[11];
+    } else {
+      s.DK = p[0]; s.EK = p[0] + bK2 * s.nzn; s.LK = p[1];
+      s.DA = p[2]; s.EA = p[2] + bA2 * s.nzn; s.LA = p[3];
+      s.ycK = p[4]; s.ycA = p[5]; s.rcK = p[6]; s.rcA = p[7];
+      s.ycK8 = p[8]; s.ycA8 = p[9]; s.rcK8 = p[10]; s.rcA8 = p[11];
+    }
+  }
+  return off;
+}
+
+size_t block_bytes(msgfem* h, SubDev& s) {
+  return h->mixed ? place_blocks<float>(s, nullptr, false) : place_blocks<double>(s, nullptr, false);
+}
+
+// Group the subdomains into waves whose factor storage fits the budget
+// (msgfem_options.wave_mb, or by default 80 % of the free device memory less
+// room for the element matrices), allocate one pool for the largest wave and
+// point every subdomain at its slot.  Subdomains are taken largest first and a
+// wave is closed when the next one no longer fits (waves of similar sizes).
+// When everything fits: one wave of all subdomains in index order.
+msgfem_status alloc_waves(msgfem* h) {
+  std::vector<size_t> bytes(h->N);
+  size_t total = 0;
+  for (int j = 0; j < h->N; ++j) total += (bytes[j] = block_bytes(h, h->sub[j]));
+  size_t budget;
+  if (h->opt.wave_mb > 0) {
+    budget = (size_t)(h->opt.wave_mb * 1048576.0);
+  } else {
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    const size_t ke = (size_t)h->NX * h->NY * h->NZ * (size_t)h->S * 576 * sizeof(double);
+    const size_t reserve = ke + ((size_t)2 << 30);
+    budget = fr > reserve ? (size_t)(0.8 * (double)(fr - reserve)) : 0;
+  }
+  h->waves.clear();
+  h->wave_of.assign(h->N, 0);
+  if (total <= budget) {
+    h->waves.emplace_back();
+    for (int j = 0; j < h->N; ++j) h->waves[0].members.push_back(j);
+  } else {
+    std::vector<int> order(h->N);
+    for (int j = 0; j < h->N; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bytes[a] > bytes[b]; });
+    size_t used = 0;
+    for (int j : order) {
+      if (bytes[j] > budget) {
+        h->err = "a subdomain's factor storage exceeds the wave budget (msgfem_options.wave_mb)";
+        return MSGFEM_ENOMEM;
+      }
+      if (h->waves.empty() || used + bytes[j] > budget) {
+        h->waves.emplace_back();
+        used = 0;
+      }
+      h->waves.back().members.push_back(j);
+      used += bytes[j];
+    }
+    for (auto& w : h->waves) std::sort(w.members.begin(), w.members.end());
+  }
+  size_t pool = 0;
+  for (size_t w = 0; w < h->waves.size(); ++w) {
+    size_t sum = 0;
+    for (int j : h->waves[w].members) {
+      sum += bytes[j];
+      h->wave_of[j] = (int)w;
+    }
+    pool = std::max(pool, sum);
+  }
+  char* base = nullptr;
+  TRY(dalloc(h, &base, pool));
+  h->d_pool = base;
+  h->pool_bytes = pool;
+  for (auto& w : h->waves) {
+    size_t off = 0;
+    for (int j : w.members) {
+      SubDev& s = h->sub[j];
+      off += h->mixed ? place_blocks<float>(s, base + off, true) : place_blocks<double>(s, base + off, true);
+    }
+  }
+  return MSGFEM_OK;
+}
+
 msgfem_status allocate(msgfem* h) {
   for (int j = 0; j < h->N; ++j) {
     SubDev& s = h->sub[j];
@@ -127,38 +235,8 @@ msgfem_status allocate(msgfem* h) {
     TRY(dalloc(h, &s.mapA, s.bA));
     TRY(dalloc(h, &s.invK, 3 * s.npl));
     TRY(dalloc(h, &s.invA, 3 * s.npl));
-    if (h->mixed) {
-      // FP32 layer blocks, factors and solve buffers
-      TRY(dalloc(h, &s.DKf, bK2 * (2 * s.nzn - 1)));
-      s.EKf = s.DKf + bK2 * s.nzn;
-      TRY(dalloc(h, &s.LKf, bK2 * s.nzn));
-      TRY(dalloc(h, &s.DAf, bA2 * (2 * s.nzn - 1)));
-      s.EAf = s.DAf + bA2 * s.nzn;
-      TRY(dalloc(h, &s.LAf, bA2 * s.nzn));
-      TRY(dalloc(h, &s.ycKf, (size_t)s.nzn * s.bK * PST));
-      TRY(dalloc(h, &s.ycAf, (size_t)s.nzn * s.bA * PST));
-      TRY(dalloc(h, &s.rcKf, (size_t)s.bK * PST));
-      TRY(dalloc(h, &s.rcAf, (size_t)s.bA * PST));
-      TRY(dalloc(h, &s.ycK8f, (size_t)s.nzn * s.bK * KB));
-      TRY(dalloc(h, &s.ycA8f, (size_t)s.nzn * s.bA * KB));
-      TRY(dalloc(h, &s.rcK8f, (size_t)s.bK * KB));
-      TRY(dalloc(h, &s.rcA8f, (size_t)s.bA * KB));
-    } else {
-      TRY(dalloc(h, &s.DK, bK2 * (2 * s.nzn - 1)));
-      s.EK = s.DK + bK2 * s.nzn;
-      TRY(dalloc(h, &s.LK, bK2 * s.nzn));
-      TRY(dalloc(h, &s.DA, bA2 * (2 * s.nzn - 1)));
-      s.EA = s.DA + bA2 * s.nzn;
-      TRY(dalloc(h, &s.LA, bA2 * s.nzn));
-      TRY(dalloc(h, &s.ycK, (size_t)s.nzn * s.bK * PST));
-      TRY(dalloc(h, &s.ycA, (size_t)s.nzn * s.bA * PST));
-      TRY(dalloc(h, &s.rcK, (size_t)s.bK * PST));
-      TRY(dalloc(h, &s.rcA, (size_t)s.bA * PST));
-      TRY(dalloc(h, &s.ycK8, (size_t)s.nzn * s.bK * KB));
-      TRY(dalloc(h, &s.ycA8, (size_t)s.nzn * s.bA * KB));
-      TRY(dalloc(h, &s.rcK8, (size_t)s.bK * KB));
-      TRY(dalloc(h, &s.rcA8, (size_t)s.bA * KB));
-    }
+    (void)bK2;
+    (void)bA2;
     double** mvs[] = {&s.Phi, &s.Z, &s.KPhi, &s.W, &s.T1, &s.R, &s.BR, &s.EV, &s.CB, &s.CW};
     for (double** m : mvs) {
       TRY(dalloc(h, m, (size_t)s.nfull * PST));
@@ -195,6 +273,7 @@ msgfem_status allocate(msgfem* h) {
     CK(cudaMemcpy(s.invA, hs.invA.data(), hs.invA.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(s.bload, hs.bload.data(), hs.bload.size() * sizeof(double), cudaMemcpyHostToDevice));
   }
+  TRY(alloc_waves(h));
   TRY(dalloc(h, &h->d_sub, h->N));
   CK(cudaMemcpy(h->d_sub, h->sub.data(), h->N * sizeof(SubDev), cudaMemcpyHostToDevice));
   TRY(dalloc(h, &h->d_E9, 9));
@@ -223,27 +302,29 @@ msgfem_status allocate(msgfem* h) {
   // schedules
   build_factor_schedule(h);
   build_solve_schedules(h);
-  if (h->mixed) {
-    TRY(dalloc(h, &h->factf.d_gemm, h->factf.gemm.size()));
-    CK(cudaMemcpy(h->factf.d_gemm, h->factf.gemm.data(), h->factf.gemm.size() * sizeof(TileTaskT<float>),
-                  cudaMemcpyHostToDevice));
-    for (SolveScheduleT<float>* ss : {&h->solveKf, &h->solveAf, &h->solveK8f, &h->solveA8f}) {
-      TRY(dalloc(h, &ss->d_tasks, ss->tasks.size()));
-      CK(cudaMemcpy(ss->d_tasks, ss->tasks.data(), ss->tasks.size() * sizeof(SolveTaskT<float>),
+  for (WaveSched& w : h->waves) {
+    if (h->mixed) {
+      TRY(dalloc(h, &w.factf.d_gemm, w.factf.gemm.size()));
+      CK(cudaMemcpy(w.factf.d_gemm, w.factf.gemm.data(), w.factf.gemm.size() * sizeof(TileTaskT<float>),
                     cudaMemcpyHostToDevice));
+      for (SolveScheduleT<float>* ss : {&w.solveKf, &w.solveAf, &w.solveK8f, &w.solveA8f}) {
+        TRY(dalloc(h, &ss->d_tasks, ss->tasks.size()));
+        CK(cudaMemcpy(ss->d_tasks, ss->tasks.data(), ss->tasks.size() * sizeof(SolveTaskT<float>),
+                      cudaMemcpyHostToDevice));
+      }
+    } else {
+      TRY(dalloc(h, &w.fact.d_gemm, w.fact.gemm.size()));
+      CK(cudaMemcpy(w.fact.d_gemm, w.fact.gemm.data(), w.fact.gemm.size() * sizeof(GemmTask),
+                    cudaMemcpyHostToDevice));
+      for (SolveSchedule* ss : {&w.solveK, &w.solveA, &w.solveK8, &w.solveA8}) {
+        if (ss->tasks.empty()) continue;
+        TRY(dalloc(h, &ss->d_tasks, ss->tasks.size()));
+        CK(cudaMemcpy(ss->d_tasks, ss->tasks.data(), ss->tasks.size() * sizeof(SolveTask), cudaMemcpyHostToDevice));
+      }
     }
-  } else {
-    TRY(dalloc(h, &h->fact.d_gemm, h->fact.gemm.size()));
-    CK(cudaMemcpy(h->fact.d_gemm, h->fact.gemm.data(), h->fact.gemm.size() * sizeof(GemmTask),
-                  cudaMemcpyHostToDevice));
   }
   TRY(dalloc(h, &h->d_mk, h->N));
   TRY(dalloc(h, &h->d_nwk, h->N));
-  for (SolveSchedule* ss : {&h->solveK, &h->solveA, &h->solveK8, &h->solveA8}) {
-    if (ss->tasks.empty()) continue;
-    TRY(dalloc(h, &ss->d_tasks, ss->tasks.size()));
-    CK(cudaMemcpy(ss->d_tasks, ss->tasks.data(), ss->tasks.size() * sizeof(SolveTask), cudaMemcpyHostToDevice));
-  }
   return MSGFEM_OK;
 }
 
@@ -410,16 +491,18 @@ void run_graph(msgfem* h, uint64_t key, Issue issue) {
 // handle's precision; add = 1 accumulates into the destination.
 void timed_solve_w(msgfem* h, int mat, int src, int dst, int neg, int width, int add) {
   const int sp = span_begin(h, TAG_SOLVE);
-  const uint64_t key = ((uint64_t)1 << 60) | ((uint64_t)mat << 40) | ((uint64_t)width << 32) |
-                       ((uint64_t)src << 16) | ((uint64_t)dst << 4) | ((uint64_t)neg << 1) | (uint64_t)add;
+  const uint64_t key = ((uint64_t)1 << 60) | ((uint64_t)h->cur << 48) | ((uint64_t)mat << 40) |
+                       ((uint64_t)width << 32) | ((uint64_t)src << 16) | ((uint64_t)dst << 4) | ((uint64_t)neg << 1) |
+                       (uint64_t)add;
+  const WaveSched& w = h->waves[h->cur];
   run_graph(h, key, [&](cudaStream_t cs) {
     if (h->mixed) {
-      const SolveScheduleT<float>& sc = width == KB ? (mat == 0 ? h->solveK8f : h->solveA8f)
-                                                    : (mat == 0 ? h->solveKf : h->solveAf);
+      const SolveScheduleT<float>& sc = width == KB ? (mat == 0 ? w.solveK8f : w.solveA8f)
+                                                    : (mat == 0 ? w.solveKf : w.solveAf);
       run_solve_mv(sc, cs, src, dst, neg, width, &h->gs, add);
     } else {
-      const SolveScheduleT<double>& sc = width == KB ? (mat == 0 ? h->solveK8 : h->solveA8)
-                                                     : (mat == 0 ? h->solveK : h->solveA);
+      const SolveScheduleT<double>& sc = width == KB ? (mat == 0 ? w.solveK8 : w.solveA8)
+                                                     : (mat == 0 ? w.solveK : w.solveA);
       run_solve_mv(sc, cs, src, dst, neg, width, &h->gs, add);
     }
   });
@@ -514,7 +597,7 @@ void apply_M_kb(msgfem* h) {
 // Subspace iteration with Rayleigh-Ritz every step (solver = 1).
 msgfem_status run_subspace(msgfem* h, int n_loc, int p, bool& all_done) {
   cudaStream_t st = h->stream;
-  std::vector<int> act(h->N, 1);
+  std::vector<int> act(h->base_act);
   // 3. start block X0 on B2, A-harmonic extension, and psi in the last column
   launch_random_b2(h, MV_W, p, h->opt.seed);
   timed_stencil_apply(h, MV_W, MV_T1, 0, 1.0);
@@ -526,7 +609,6 @@ msgfem_status run_subspace(msgfem* h, int n_loc, int p, bool& all_done) {
   launch_sub_rc(h, MV_W, MV_R, GM_G3, 6);
   launch_copy_mv(h, MV_W, MV_PHI);
   CK_LAUNCH();
-  h->iters.assign(h->N, 0);
   std::vector<double> theta((size_t)h->N * PST), gdiag((size_t)h->N * PST * PST);
   int it = 0;
   all_done = false;
@@ -596,7 +678,7 @@ msgfem_status run_subspace(msgfem* h, int n_loc, int p, bool& all_done) {
 // (solver = 0, default).
 msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
   cudaStream_t st = h->stream;
-  std::vector<int> nw(h->N), act(h->N, 1), mk(h->N, 0);
+  std::vector<int> nw(h->N), act(h->base_act), mk(h->N, 0);
   int nwmax = 0;
   for (int j = 0; j < h->N; ++j) {
     nw[j] = n_loc - (h->sub[j].floating ? std::min(6, n_loc) : 0);
@@ -639,7 +721,6 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
   launch_store_block(h, MV_WB, 0, MV_QB);
   launch_store_block(h, MV_ZB, 0, MV_NQ);
   CK_LAUNCH();
-  h->iters.assign(h->N, 0);
   std::vector<double> res((size_t)h->N * PST);
   all_done = true;
   for (int j = 0; j < h->N; ++j) all_done = all_done && !act[j];
@@ -714,7 +795,7 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
     }
   }
   // Ritz vectors of the wanted pairs (theta ascending in s.theta)
-  TRY(set_active(h, std::vector<int>(h->N, 1)));
+  TRY(set_active(h, h->base_act));
   CK(cudaMemcpyAsync(h->d_mk, h->m_final.data(), h->N * sizeof(int), cudaMemcpyHostToDevice, st));
   launch_ritz(h, h->d_mk, h->d_nwk, 1, false, MV_QB, MV_PHI);
   timed_stencil_apply(h, MV_PHI, MV_Z, 3, 1.0);
@@ -730,15 +811,46 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
   if (out == nullptr) return MSGFEM_EINVAL;
   *out = nullptr;
   if (!mesh || !plies || !part || !plies->E9 || !plies->elem_angle_deg) return MSGFEM_EINVAL;
-  if (mesh->nx <= 0 || mesh->ny <= 0 || mesh->nz <= 0 || !(mesh->hx > 0) || !(mesh->hy > 0) || !(mesh->hz > 0))
+  if (mesh->nx <= 0 || mesh->ny <= 0 || mesh->nz <= 0) return MSGFEM_EINVAL;
+  if (mesh->xyz == nullptr && (!(mesh->hx > 0) || !(mesh->hy > 0) || !(mesh->hz > 0))) return MSGFEM_EINVAL;
+  if (part->n_boxes < 0 || (part->n_boxes > 0 && part->boxes == nullptr)) return MSGFEM_EINVAL;
+  if (part->n_boxes == 0 && (part->sx <= 0 || part->sy <= 0 || part->sx > mesh->nx || part->sy > mesh->ny))
     return MSGFEM_EINVAL;
-  if (part->sx <= 0 || part->sy <= 0 || part->sx > mesh->nx || part->sy > mesh->ny) return MSGFEM_EINVAL;
   if (overlap < 1 || oversampling < overlap) return MSGFEM_EINVAL;
   msgfem* h = new msgfem();
   h->NX = mesh->nx; h->NY = mesh->ny; h->NZ = mesh->nz;
   h->hx = mesh->hx; h->hy = mesh->hy; h->hz = mesh->hz; h->traction = mesh->traction;
   memcpy(h->E9, plies->E9, sizeof(h->E9));
   h->sx = part->sx; h->sy = part->sy; h->o = overlap; h->os = oversampling;
+  if (part->n_boxes > 0) {
+    h->boxes.assign(part->boxes, part->boxes + 4 * (size_t)part->n_boxes);
+    h->sx = part->n_boxes;
+    h->sy = 1;
+  }
+  // node coordinates and ply frames (host or device), copied
+  const size_t nnodes = (size_t)(h->NX + 1) * (h->NY + 1) * (h->NZ + 1);
+  const size_t nel = (size_t)h->NX * h->NY * h->NZ;
+  auto copy_in = [&](const double* src, size_t n, std::vector<double>& dst) -> bool {
+    dst.resize(n);
+    if (is_device_ptr(src)) {
+      if (cudaMemcpy(dst.data(), src, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+    } else {
+      memcpy(dst.data(), src, n * sizeof(double));
+    }
+    for (double v : dst)
+      if (!std::isfinite(v)) return false;
+    return true;
+  };
+  if (mesh->xyz != nullptr && !copy_in(mesh->xyz, 3 * nnodes, h->h_xyz)) {
+    *out = h;
+    h->err = "node coordinates: copy failed or non-finite value";
+    return MSGFEM_EINVAL;
+  }
+  if (plies->elem_frame != nullptr && !copy_in(plies->elem_frame, 9 * nel, h->h_frame)) {
+    *out = h;
+    h->err = "ply frames: copy failed or non-finite value";
+    return MSGFEM_EINVAL;
+  }
   memset(&h->opt, 0, sizeof(h->opt));
   if (opt) h->opt = *opt;
   if (h->opt.max_iter <= 0) h->opt.max_iter = 100;
@@ -757,6 +869,14 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
   if (st != MSGFEM_OK) return st;
   st = allocate(h);
   if (st != MSGFEM_OK) return st;
+  if (!h->h_xyz.empty()) {
+    TRY(dalloc(h, &h->d_xyz, h->h_xyz.size()));
+    CK(cudaMemcpy(h->d_xyz, h->h_xyz.data(), h->h_xyz.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  if (!h->h_frame.empty()) {
+    TRY(dalloc(h, &h->d_frame, h->h_frame.size()));
+    CK(cudaMemcpy(h->d_frame, h->h_frame.data(), h->h_frame.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
   st = set_angles(h, plies->elem_angle_deg);
   if (st != MSGFEM_OK) return st;
   for (int g = 0; g < h->ngroup; ++g) {
@@ -803,54 +923,81 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   h->prof.solve_bytes = 0.0;
   h->prof.stencil_flops = 0.0;
   h->prof.solve_calls = 0;
-  // 1. assembly
+  if (h->opt.solver == 1 && h->mixed) {
+    h->err = "subspace iteration (solver = 1) runs in FP64 only";
+    return MSGFEM_EINVAL;
+  }
+  if (h->opt.solver == 1 && h->waves.size() > 1) {
+    h->err = "subspace iteration (solver = 1) needs every subdomain resident (one wave)";
+    return MSGFEM_EINVAL;
+  }
+  // 1. assembly: element stiffness and the node stencils of every subdomain
   int sp = span_begin(h, TAG_ASSEMBLE);
   launch_element_stiffness(h);
   launch_stencil(h);
-  if (h->mixed) launch_layer_blocks_f32(h);
-  else launch_layer_blocks(h);
   span_end(h, sp);
   CK_LAUNCH();
-  // 2. factorisations of K and A11
-  sp = span_begin(h, TAG_FACTOR);
-  run_graph(h, (uint64_t)2 << 60, [&](cudaStream_t cs) {
-    if (h->mixed) run_schedule(h->factf, cs, &h->gs);
-    else run_schedule(h->fact, cs, &h->gs);
-  });
-  span_end(h, sp);
-  CK_LAUNCH();
-  const int sp_iter = span_begin(h, TAG_ITERATE);
   // rigid modes, B-orthonormal (floating)
+  int sp_iter = span_begin(h, TAG_ITERATE);
   launch_rigid_modes(h);
   timed_stencil_apply(h, MV_R, MV_BR, 3, 1.0);
   timed_gram(h, MV_R, MV_BR, GM_G1);
   launch_chol_inv_small(h, GM_G1, nullptr, 6, 0);
   timed_rotate(h, MV_R, GM_Y, 6);
   timed_rotate(h, MV_BR, GM_Y, 6);
-  bool all_done = false;
-  if (h->opt.solver == 1 && h->mixed) {
-    h->err = "subspace iteration (solver = 1) runs in FP64 only";
-    return MSGFEM_EINVAL;
-  }
-  if (h->opt.solver == 1) {
-    TRY(run_subspace(h, n_loc, p, all_done));
-  } else {
-    h->m_final.assign(h->N, 0);
-    TRY(run_krylov(h, n_loc, all_done));
-  }
-  std::vector<double> theta((size_t)h->N * PST);
-  TRY(set_active(h, std::vector<int>(h->N, 1)));
-  // 4. final residuals: S x = (K Phi)|B2, T x = -(K y~)|B2 with y~ = A11^{-1} Z|B1
-  for (auto& s : h->sub) CK(cudaMemsetAsync(s.T1, 0, (size_t)s.nfull * PST * sizeof(double), st));
-  timed_solve(h, 1, MV_Z, MV_T1, 0);
-  for (int r = 0; h->mixed && r < std::min(h->refine, 5); ++r) {   // refine y~: residual Z - K y~ on B1
-    timed_stencil_apply(h, MV_T1, MV_W, 0, 1.0);
-    launch_x_minus_y(h, MV_Z, MV_W, MV_W, PST);
-    timed_solve_w(h, 1, MV_W, MV_T1, 0, PST, 1);
-  }
-  timed_stencil_apply(h, MV_T1, MV_W, 0, 1.0);
-  launch_colnorms(h, MV_KPHI, MV_W, p);
   span_end(h, sp_iter);
+  bool all_done = true;
+  h->iters.assign(h->N, 0);
+  h->m_final.assign(h->N, 0);
+  // waves: layer blocks, factorisations, eigensolver and final residuals of
+  // the subdomains that share the factor pool (one wave when all fit)
+  for (size_t w = 0; w < h->waves.size(); ++w) {
+    h->cur = (int)w;
+    const WaveSched& ws = h->waves[w];
+    h->base_act.assign(h->N, 0);
+    for (int j : ws.members) h->base_act[j] = 1;
+    TRY(set_active(h, h->base_act));
+    sp = span_begin(h, TAG_ASSEMBLE);
+    if (h->mixed) launch_layer_blocks_f32(h);
+    else launch_layer_blocks(h);
+    span_end(h, sp);
+    CK_LAUNCH();
+    // 2. factorisations of K and A11
+    sp = span_begin(h, TAG_FACTOR);
+    run_graph(h, ((uint64_t)2 << 60) | ((uint64_t)w << 48), [&](cudaStream_t cs) {
+      if (h->mixed) run_schedule(ws.factf, cs, &h->gs);
+      else run_schedule(ws.fact, cs, &h->gs);
+    });
+    span_end(h, sp);
+    CK_LAUNCH();
+    sp_iter = span_begin(h, TAG_ITERATE);
+    bool done = false;
+    if (h->opt.solver == 1) {
+      TRY(run_subspace(h, n_loc, p, done));
+    } else {
+      TRY(run_krylov(h, n_loc, done));
+    }
+    all_done = all_done && done;
+    TRY(set_active(h, h->base_act));
+    // 4. final residuals: S x = (K Phi)|B2, T x = -(K y~)|B2 with y~ = A11^{-1} Z|B1
+    for (int j : ws.members) {
+      const SubDev& s = h->sub[j];
+      CK(cudaMemsetAsync(s.T1, 0, (size_t)s.nfull * PST * sizeof(double), st));
+    }
+    timed_solve(h, 1, MV_Z, MV_T1, 0);
+    for (int r = 0; h->mixed && r < std::min(h->refine, 5); ++r) {   // refine y~: residual Z - K y~ on B1
+      timed_stencil_apply(h, MV_T1, MV_W, 0, 1.0);
+      launch_x_minus_y(h, MV_Z, MV_W, MV_W, PST);
+      timed_solve_w(h, 1, MV_W, MV_T1, 0, PST, 1);
+    }
+    timed_stencil_apply(h, MV_T1, MV_W, 0, 1.0);
+    launch_colnorms(h, MV_KPHI, MV_W, p);
+    span_end(h, sp_iter);
+  }
+  h->cur = 0;
+  h->base_act.assign(h->N, 1);
+  std::vector<double> theta((size_t)h->N * PST);
+  TRY(set_active(h, h->base_act));
   // eigenvectors: [rigid modes (floating), Ritz vectors]
   for (int j = 0; j < h->N; ++j) {
     const SubDev& s = h->sub[j];
@@ -1058,6 +1205,8 @@ msgfem_status msgfem_get_profile(msgfem_h h, msgfem_profile* out) {
   spans_collect(h);
   *out = h->prof;
   out->launches = g_launch_count;
+  out->waves = (int)h->waves.size();
+  out->pool_mb = (double)h->pool_bytes / 1048576.0;
   return MSGFEM_OK;
 }
 

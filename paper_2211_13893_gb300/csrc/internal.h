@@ -136,6 +136,16 @@ struct StreamSet {
   cudaEvent_t fork = nullptr, join[NGROUP] = {};
 };
 
+// Static schedules of one wave of subdomains (FP64, or FP32 in mixed precision).
+struct WaveSched {
+  std::vector<int> members;          // subdomains of the wave
+  ScheduleT<double> fact;
+  SolveScheduleT<double> solveK, solveA;     // PST columns
+  SolveScheduleT<double> solveK8, solveA8;   // KB columns
+  ScheduleT<float> factf;                    // mixed precision: FP32 factorisation
+  SolveScheduleT<float> solveKf, solveAf, solveK8f, solveA8f;
+};
+
 struct CoarsePair { int s, t, x0, x1, y0, y1; };   // (i, j) node box of Omega_s cap Omega*_t
 
 // Host copies of the per-subdomain set-up arrays (uploaded once).
@@ -154,6 +164,11 @@ struct WarmStart {
 struct msgfem {
   int NX = 0, NY = 0, NZ = 0;
   double hx = 0, hy = 0, hz = 0, traction = 0;
+  std::vector<double> h_xyz;         // node coordinates (general mesh), empty for the box
+  std::vector<double> h_frame;       // per-element ply frames, empty = x, y, z
+  std::vector<int> boxes;            // explicit non-overlapping element boxes, 4 per subdomain
+  double* d_xyz = nullptr;           // device copies (nullptr for the box / default frames)
+  double* d_frame = nullptr;
   double E9[9];
   int sx = 0, sy = 0, o = 0, os = 0;
   msgfem_options opt;
@@ -171,6 +186,7 @@ struct msgfem {
   std::vector<HostSub> hsub;
   std::vector<int> n1, n2, n3, iters, basis_m, m_final;
   std::vector<int> act_host;         // host copy of the active flags last uploaded
+  std::vector<int> base_act;         // members of the wave being processed (all ones: one wave)
   std::vector<double> resid_max;
   std::vector<void*> allocs;
   SubDev* d_sub = nullptr;
@@ -186,11 +202,14 @@ struct msgfem {
   int* d_ncols = nullptr;            // [N]
   int* d_mk = nullptr;               // [N] Krylov basis size at the last Rayleigh-Ritz
   int* d_nwk = nullptr;              // [N] wanted Ritz pairs
-  Schedule fact;
-  SolveSchedule solveK, solveA;     // PST columns
-  SolveSchedule solveK8, solveA8;   // KB columns
-  ScheduleT<float> factf;            // mixed precision: FP32 factorisation
-  SolveScheduleT<float> solveKf, solveAf, solveK8f, solveA8f;
+  // Waves: subdomains whose layer blocks, factors and solve buffers share one
+  // pool of device memory, processed one wave after another by the local
+  // stage (one wave holding every subdomain when everything fits).
+  std::vector<WaveSched> waves;
+  int cur = 0;                       // wave being processed
+  std::vector<int> wave_of;          // [N] wave of each subdomain
+  void* d_pool = nullptr;            // layer-block / solve-buffer pool
+  size_t pool_bytes = 0;
   int mixed = 0;                     // precision == MSGFEM_MIXED
   int refine = 2;                    // FP64 refinement steps per FP32 solve
   std::vector<CoarsePair> pairs;
@@ -245,6 +264,8 @@ template <typename T>
 void run_solve_mv(const SolveScheduleT<T>& s, cudaStream_t st, int src, int dst, int gather_neg, int width = PST,
                   const StreamSet* gs = nullptr, int scatter_add = 0);
 void launch_element_stiffness(msgfem* h);
+// node coordinates of node (i, j, k): given, or those of the box (setup.cpp)
+void node_xyz(const msgfem* h, int i, int j, int k, double X[3]);
 void launch_stencil(msgfem* h);
 void launch_layer_blocks(msgfem* h);
 void launch_layer_blocks_f32(msgfem* h);

@@ -3,10 +3,14 @@
 //
 // Material (Sec. 2, Eq. eq-hooke; Sec. 5.1): the orthotropic ply stiffness
 // in its axes is the inverse of the engineering compliance; it is rotated to
-// the laminate frame with the Voigt strain transformation M(theta) of a
-// rotation about z, C = M^T C_ply M, so that eps:C:eps is invariant.
-// Element (Eq. element_stiffness): K_e = sum_g B_g^T C B_g det J w_g over
-// 2x2x2 Gauss points of the trilinear brick, with the 6x24 Voigt B matrix.
+// the global frame with the Voigt strain transformation M of the ply axes
+// (rows of Q: fibre cos t a0 + sin t a1, transverse -sin t a0 + cos t a1,
+// normal a2 of the element's frame; a0, a1, a2 = x, y, z on the box beam),
+// C = M^T C_ply M, so that eps:C:eps is invariant.
+// Element (Eq. element_stiffness): K_e = sum_g B_g^T C B_g det J_g over the
+// 2x2x2 Gauss points (weights 1) of the trilinear map of the element's eight
+// nodes (a brick on the box beam), with the 6x24 Voigt B matrix, three
+// non-zeros per column.
 // GPU node order inside an element: a = ax + 2 ay + 4 az, (ax, ay, az) in
 // {0,1}^3; element DoF 3 a + c.
 #include <type_traits>
@@ -15,7 +19,7 @@
 
 namespace {
 
-__device__ void ply_stiffness(const double* E9, double theta_deg, double C[6][6]) {
+__device__ void ply_stiffness(const double* E9, double theta_deg, const double* frame, double C[6][6]) {
   const double E1 = E9[0], E2 = E9[1], E3 = E9[2], G12 = E9[3], G13 = E9[4], G23 = E9[5];
   const double n12 = E9[6], n13 = E9[7], n23 = E9[8];
   // normal compliance block and its inverse (cofactors)
@@ -30,84 +34,139 @@ __device__ void ply_stiffness(const double* E9, double theta_deg, double C[6][6]
   Cm[0][0] = c11 / det; Cm[0][1] = Cm[1][0] = c12 / det; Cm[0][2] = Cm[2][0] = c13 / det;
   Cm[1][1] = c22 / det; Cm[1][2] = Cm[2][1] = c23 / det; Cm[2][2] = c33 / det;
   Cm[3][3] = G23; Cm[4][4] = G13; Cm[5][5] = G12;
-  // eps_ply = M eps_global (Voigt 11 22 33 23 13 12, engineering shear)
+  // ply axes (rows of Q) in global coordinates
   double th = theta_deg * (3.14159265358979323846 / 180.0);
   const double c = cos(th), s = sin(th);
+  double a[3][3] = {{1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}, {0.0, 0.0, 1.0}};
+  if (frame != nullptr)
+    for (int r = 0; r < 3; ++r)
+      for (int d = 0; d < 3; ++d) a[r][d] = frame[3 * r + d];
+  double Q[3][3];
+  for (int d = 0; d < 3; ++d) {
+    Q[0][d] = c * a[0][d] + s * a[1][d];
+    Q[1][d] = -s * a[0][d] + c * a[1][d];
+    Q[2][d] = a[2][d];
+  }
+  // eps_ply = M eps_global (Voigt 11 22 33 23 13 12, engineering shear):
+  // M[(i,j)][(p,q)] = (i == j ? 1 : 2) * (p == q ? Q_ip Q_jp : (Q_ip Q_jq + Q_iq Q_jp) / 2)
+  const int vi[6] = {0, 1, 2, 1, 0, 0}, vj[6] = {0, 1, 2, 2, 2, 1};
   double M[6][6];
-  for (int i = 0; i < 6; ++i)
-    for (int j = 0; j < 6; ++j) M[i][j] = 0.0;
-  M[0][0] = c * c; M[0][1] = s * s; M[0][5] = c * s;
-  M[1][0] = s * s; M[1][1] = c * c; M[1][5] = -c * s;
-  M[2][2] = 1.0;
-  M[3][3] = c; M[3][4] = -s;
-  M[4][3] = s; M[4][4] = c;
-  M[5][0] = -2.0 * c * s; M[5][1] = 2.0 * c * s; M[5][5] = c * c - s * s;
+  for (int I = 0; I < 6; ++I)
+    for (int J = 0; J < 6; ++J) {
+      const int i = vi[I], j = vj[I], p = vi[J], q = vj[J];
+      const double f = (i == j) ? 1.0 : 2.0;
+      M[I][J] = (p == q) ? f * Q[i][p] * Q[j][p] : 0.5 * f * (Q[i][p] * Q[j][q] + Q[i][q] * Q[j][p]);
+    }
   double CM[6][6];
   for (int i = 0; i < 6; ++i)
     for (int j = 0; j < 6; ++j) {
-      double a = 0.0;
-      for (int k = 0; k < 6; ++k) a += Cm[i][k] * M[k][j];
-      CM[i][j] = a;
+      double acc = 0.0;
+      for (int k = 0; k < 6; ++k) acc += Cm[i][k] * M[k][j];
+      CM[i][j] = acc;
     }
   for (int i = 0; i < 6; ++i)
     for (int j = 0; j < 6; ++j) {
-      double a = 0.0;
-      for (int k = 0; k < 6; ++k) a += M[k][i] * CM[k][j];
-      C[i][j] = a;
+      double acc = 0.0;
+      for (int k = 0; k < 6; ++k) acc += M[k][i] * CM[k][j];
+      C[i][j] = acc;
     }
 }
 
 // One block per element type; thread (r, c) computes K_e[r][c].
+//   layered: type = instance * NZ + ply k (box beam, angle per ply);
+//   otherwise type = instance * nel + element.  With node coordinates (xyz)
+//   or ply frames the types are always per element.
 __global__ void __launch_bounds__(576)
 k_element_stiffness(const double* __restrict__ angles, const double* __restrict__ E9, int layered,
-                    int NX, int NY, int NZ, double hx, double hy, double hz, double* __restrict__ Ke) {
+                    int NX, int NY, int NZ, double hx, double hy, double hz, const double* __restrict__ xyz,
+                    const double* __restrict__ frame, double* __restrict__ Ke) {
   const int type = blockIdx.x;
+  const int nel = NX * NY * NZ;
+  const int e = layered ? type % NZ : type % nel;   // element of the first instance
+  const int ie = layered ? 0 : e / (NY * NZ), je = layered ? 0 : (e / NZ) % NY, ke = e % NZ;
   __shared__ double C[6][6];
-  __shared__ double dN[8][8][3];   // [gauss][node][d/dx, d/dy, d/dz]
+  __shared__ double X[8][3];        // corner coordinates
+  __shared__ double Jinv[8][3][3];  // [gauss][r][d] = d xi_r / d x_d
+  __shared__ double detJ[8];
+  __shared__ double dN[8][8][3];    // [gauss][node][d/dx, d/dy, d/dz]
   const int tid = threadIdx.x;
   if (tid == 0) {
-    // layered: type = ply k, angle of element (0, 0, k); otherwise type = element index
-    const double th = angles[type];   // per-type angle (per ply if layered, else per element)
     double Cl[6][6];
-    ply_stiffness(E9, th, Cl);
+    ply_stiffness(E9, angles[type], frame != nullptr ? frame + (size_t)e * 9 : nullptr, Cl);
     for (int i = 0; i < 6; ++i)
       for (int j = 0; j < 6; ++j) C[i][j] = Cl[i][j];
   }
+  if (tid < 24) {
+    const int a = tid / 3, d = tid % 3;
+    const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
+    if (xyz != nullptr) {
+      const size_t node = ((size_t)(ie + ax) * (NY + 1) + (je + ay)) * (NZ + 1) + (ke + az);
+      X[a][d] = xyz[3 * node + d];
+    } else {
+      X[a][d] = d == 0 ? ax * hx : (d == 1 ? ay * hy : az * hz);
+    }
+  }
+  __syncthreads();
+  const double gp = 0.57735026918962576451;   // 1/sqrt(3)
+  if (tid < 8) {
+    // Jacobian J[d][r] = dx_d / dxi_r at Gauss point g, its determinant and inverse
+    const int g = tid;
+    const double xi[3] = {(g & 1) ? gp : -gp, (g & 2) ? gp : -gp, (g & 4) ? gp : -gp};
+    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int a = 0; a < 8; ++a) {
+      const double sa[3] = {(a & 1) ? 1.0 : -1.0, (a & 2) ? 1.0 : -1.0, (a & 4) ? 1.0 : -1.0};
+      const double f0 = 1.0 + sa[0] * xi[0], f1 = 1.0 + sa[1] * xi[1], f2 = 1.0 + sa[2] * xi[2];
+      const double dr[3] = {0.125 * sa[0] * f1 * f2, 0.125 * f0 * sa[1] * f2, 0.125 * f0 * f1 * sa[2]};
+      for (int d = 0; d < 3; ++d)
+        for (int r = 0; r < 3; ++r) J[d][r] += X[a][d] * dr[r];
+    }
+    const double m00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const double m01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const double m02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const double dt = J[0][0] * m00 + J[0][1] * m01 + J[0][2] * m02;
+    const double inv = 1.0 / dt;
+    // (J^{-1})[r][d] = cofactor(J)[d][r] / det
+    Jinv[g][0][0] = m00 * inv;
+    Jinv[g][1][0] = m01 * inv;
+    Jinv[g][2][0] = m02 * inv;
+    Jinv[g][0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * inv;
+    Jinv[g][1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * inv;
+    Jinv[g][2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * inv;
+    Jinv[g][0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * inv;
+    Jinv[g][1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * inv;
+    Jinv[g][2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * inv;
+    detJ[g] = dt;
+  }
+  __syncthreads();
   if (tid < 64) {
     const int g = tid >> 3, a = tid & 7;
-    const double gp = 0.57735026918962576451;   // 1/sqrt(3)
     const double xi[3] = {(g & 1) ? gp : -gp, (g & 2) ? gp : -gp, (g & 4) ? gp : -gp};
     const double sa[3] = {(a & 1) ? 1.0 : -1.0, (a & 2) ? 1.0 : -1.0, (a & 4) ? 1.0 : -1.0};
     const double f0 = 1.0 + sa[0] * xi[0], f1 = 1.0 + sa[1] * xi[1], f2 = 1.0 + sa[2] * xi[2];
-    dN[g][a][0] = 0.125 * sa[0] * f1 * f2 * (2.0 / hx);
-    dN[g][a][1] = 0.125 * f0 * sa[1] * f2 * (2.0 / hy);
-    dN[g][a][2] = 0.125 * f0 * f1 * sa[2] * (2.0 / hz);
+    const double dr[3] = {0.125 * sa[0] * f1 * f2, 0.125 * f0 * sa[1] * f2, 0.125 * f0 * f1 * sa[2]};
+    for (int d = 0; d < 3; ++d) dN[g][a][d] = dr[0] * Jinv[g][0][d] + dr[1] * Jinv[g][1][d] + dr[2] * Jinv[g][2][d];
   }
   __syncthreads();
+  // B column of DoF (a, c): row c holds dN/dx_c, two shear rows the other derivatives
+  const int ROW[3][3] = {{0, 4, 5}, {1, 3, 5}, {2, 3, 4}};
+  const int DER[3][3] = {{0, 2, 1}, {1, 2, 0}, {2, 1, 0}};
   const int r = tid / 24, c = tid % 24;
   const int ar = r / 3, cr = r % 3, ac = c / 3, cc = c % 3;
-  const double detw = hx * hy * hz / 8.0;
   double acc = 0.0;
   for (int g = 0; g < 8; ++g) {
-    double br[6], bc[6];
     const double* dr = dN[g][ar];
     const double* dc = dN[g][ac];
-    // column of B for DoF (a, comp): rows xx, yy, zz, yz, xz, xy
-    br[0] = cr == 0 ? dr[0] : 0.0; br[1] = cr == 1 ? dr[1] : 0.0; br[2] = cr == 2 ? dr[2] : 0.0;
-    br[3] = cr == 1 ? dr[2] : (cr == 2 ? dr[1] : 0.0);
-    br[4] = cr == 0 ? dr[2] : (cr == 2 ? dr[0] : 0.0);
-    br[5] = cr == 0 ? dr[1] : (cr == 1 ? dr[0] : 0.0);
-    bc[0] = cc == 0 ? dc[0] : 0.0; bc[1] = cc == 1 ? dc[1] : 0.0; bc[2] = cc == 2 ? dc[2] : 0.0;
-    bc[3] = cc == 1 ? dc[2] : (cc == 2 ? dc[1] : 0.0);
-    bc[4] = cc == 0 ? dc[2] : (cc == 2 ? dc[0] : 0.0);
-    bc[5] = cc == 0 ? dc[1] : (cc == 1 ? dc[0] : 0.0);
-    for (int i = 0; i < 6; ++i) {
-      double t = 0.0;
-      for (int j = 0; j < 6; ++j) t += C[i][j] * bc[j];
-      acc += br[i] * t;
+    double t = 0.0;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      double u = 0.0;
+#pragma unroll
+      for (int n = 0; n < 3; ++n) u += C[ROW[cr][m]][ROW[cc][n]] * dc[DER[cc][n]];
+      t += dr[DER[cr][m]] * u;
     }
+    acc += t * detJ[g];
   }
-  Ke[(size_t)type * 576 + tid] = acc * detw;
+  Ke[(size_t)type * 576 + tid] = acc;
 }
 
 // Node stencil of a_{Omega*}: thread per (node, neighbour slot); slot
@@ -167,7 +226,8 @@ template <> struct Blocks<float> {
 // Thread per (node, slot); slots with dk = 0 go to D_k, dk = -1 to E_{k-1}.
 template <typename T>
 __global__ void __launch_bounds__(216)
-k_layer_blocks(const SubDev* __restrict__ subs) {
+k_layer_blocks(const SubDev* __restrict__ subs, const int* __restrict__ active) {
+  if (!active[blockIdx.y]) return;
   const SubDev s = subs[blockIdx.y];
   const int tid = threadIdx.x;
   const int node = blockIdx.x * 8 + tid / 27, slot = tid % 27;
@@ -201,7 +261,8 @@ k_layer_blocks(const SubDev* __restrict__ subs) {
 
 // Identity on padding rows and pinned DoFs.
 template <typename T>
-__global__ void k_block_identity(const SubDev* __restrict__ subs) {
+__global__ void k_block_identity(const SubDev* __restrict__ subs, const int* __restrict__ active) {
+  if (!active[blockIdx.y]) return;
   const SubDev s = subs[blockIdx.y];
   const int k = blockIdx.x;
   if (k >= s.nzn) return;
@@ -220,7 +281,8 @@ __global__ void k_block_identity(const SubDev* __restrict__ subs) {
 
 void launch_element_stiffness(msgfem* h) {
   k_element_stiffness<<<h->ntypes, 576, 0, h->stream>>>(h->d_angles_type, h->d_E9, h->layered, h->NX, h->NY,
-                                                        h->NZ, h->hx, h->hy, h->hz, h->d_Ke); ++g_launch_count;
+                                                        h->NZ, h->hx, h->hy, h->hz, h->d_xyz, h->d_frame,
+                                                        h->d_Ke); ++g_launch_count;
 }
 
 void launch_stencil(msgfem* h) {
@@ -231,9 +293,12 @@ void launch_stencil(msgfem* h) {
   ++g_launch_count;
 }
 
+// Layer blocks of the subdomains of the current wave (the active ones).
 template <typename T>
 static void layer_blocks_t(msgfem* h) {
-  for (const auto& s : h->sub) {
+  for (int j = 0; j < h->N; ++j) {
+    if (j < (int)h->act_host.size() && !h->act_host[j]) continue;
+    const SubDev& s = h->sub[j];
     T* DK = std::is_same<T, float>::value ? (T*)s.DKf : (T*)s.DK;
     T* DA = std::is_same<T, float>::value ? (T*)s.DAf : (T*)s.DA;
     cudaMemsetAsync(DK, 0, sizeof(T) * (size_t)s.bK * s.bK * (2 * s.nzn - 1), h->stream);
@@ -242,9 +307,9 @@ static void layer_blocks_t(msgfem* h) {
   int maxn = 0, maxz = 0;
   for (const auto& s : h->sub) { maxn = std::max(maxn, s.nnode); maxz = std::max(maxz, s.nzn); }
   dim3 grid((maxn + 7) / 8, h->N);
-  k_layer_blocks<T><<<grid, 216, 0, h->stream>>>(h->d_sub); ++g_launch_count;
+  k_layer_blocks<T><<<grid, 216, 0, h->stream>>>(h->d_sub, h->d_flags); ++g_launch_count;
   dim3 g2(maxz, h->N);
-  k_block_identity<T><<<g2, 128, 0, h->stream>>>(h->d_sub); ++g_launch_count;
+  k_block_identity<T><<<g2, 128, 0, h->stream>>>(h->d_sub, h->d_flags); ++g_launch_count;
 }
 
 void launch_layer_blocks(msgfem* h) { layer_blocks_t<double>(h); }

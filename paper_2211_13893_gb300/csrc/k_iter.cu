@@ -215,17 +215,34 @@ __global__ void k_copy_mv(const SubDev* __restrict__ subs, const int* __restrict
 }
 
 // Rigid-body modes of Omega* (floating subdomains): translations and
-// rotations about the node-box centre, in columns 0..5.
-__global__ void k_rigid(const SubDev* __restrict__ subs, double hx, double hy, double hz) {
+// rotations about the middle of two opposite corners of the node box, in
+// columns 0..5.  Node coordinates come from xyz (general mesh) or the box.
+__device__ __forceinline__ void node_pos(const double* xyz, int NY, int NZ, double hx, double hy, double hz, int i,
+                                         int j, int k, double P[3]) {
+  if (xyz != nullptr) {
+    const size_t n = ((size_t)i * (NY + 1) + j) * (NZ + 1) + k;
+    P[0] = xyz[3 * n]; P[1] = xyz[3 * n + 1]; P[2] = xyz[3 * n + 2];
+  } else {
+    P[0] = i * hx; P[1] = j * hy; P[2] = k * hz;
+  }
+}
+
+__global__ void k_rigid(const SubDev* __restrict__ subs, double hx, double hy, double hz,
+                        const double* __restrict__ xyz, int NY, int NZ) {
   const SubDev& s = subs[blockIdx.y];
   if (!s.floating) return;
-  const double cx = 0.5 * (s.I0 + s.I1) * hx, cy = 0.5 * (s.J0 + s.J1) * hy, cz = 0.5 * (s.nzn - 1) * hz;
+  double P0[3], P1[3];
+  node_pos(xyz, NY, NZ, hx, hy, hz, s.I0, s.J0, 0, P0);
+  node_pos(xyz, NY, NZ, hx, hy, hz, s.I1, s.J1, s.nzn - 1, P1);
+  const double cx = 0.5 * (P0[0] + P1[0]), cy = 0.5 * (P0[1] + P1[1]), cz = 0.5 * (P0[2] + P1[2]);
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)s.nfull * PST;
        e += (size_t)gridDim.x * blockDim.x) {
     const int row = (int)(e / PST), col = (int)(e % PST);
     const int node = row / 3, comp = row % 3;
     const int k = node / s.npl, q = node % s.npl;
-    const double x = (s.I0 + q / s.nyn) * hx - cx, y = (s.J0 + q % s.nyn) * hy - cy, z = k * hz - cz;
+    double P[3];
+    node_pos(xyz, NY, NZ, hx, hy, hz, s.I0 + q / s.nyn, s.J0 + q % s.nyn, k, P);
+    const double x = P[0] - cx, y = P[1] - cy, z = P[2] - cz;
     double v = 0.0;
     if (col < 3) v = (comp == col) ? 1.0 : 0.0;
     else if (col == 3) v = comp == 1 ? -z : (comp == 2 ? y : 0.0);    // e_x x r
@@ -464,8 +481,10 @@ k_small_eig(const SubDev* __restrict__ subs, const int* __restrict__ active, int
 // out[0][c] = ||A_c + alpha_c B_c||^2, out[1][c] = ||A_c||^2, out[2][c] = ||B_c||^2,
 // alpha_c = theta[c].  Partial per chunk; reduced by k_colnorm_reduce.
 __global__ void __launch_bounds__(256)
-k_colnorm_partial(const SubDev* __restrict__ subs, int wa, int wb, double* __restrict__ part, int nchunk) {
+k_colnorm_partial(const SubDev* __restrict__ subs, const int* __restrict__ active, int wa, int wb,
+                  double* __restrict__ part, int nchunk) {
   const int sidx = blockIdx.y;
+  if (active != nullptr && !active[sidx]) return;
   const SubDev& s = subs[sidx];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   __shared__ double red[8][3][32];
@@ -494,8 +513,10 @@ k_colnorm_partial(const SubDev* __restrict__ subs, int wa, int wb, double* __res
   }
 }
 
-__global__ void k_colnorm_reduce(const SubDev* __restrict__ subs, const double* __restrict__ part, int nchunk, int p) {
+__global__ void k_colnorm_reduce(const SubDev* __restrict__ subs, const int* __restrict__ active,
+                                 const double* __restrict__ part, int nchunk, int p) {
   const int sidx = blockIdx.x;
+  if (active != nullptr && !active[sidx]) return;
   const SubDev& s = subs[sidx];
   const int nc = (s.nfull + GRAM_ROWS - 1) / GRAM_ROWS;
   const int lane = threadIdx.x;
@@ -590,7 +611,7 @@ void launch_copy_mv(msgfem* h, int wsrc, int wdst) {
 
 void launch_rigid_modes(msgfem* h) {
   dim3 grid(256, h->N);
-  k_rigid<<<grid, 256, 0, h->stream>>>(h->d_sub, h->hx, h->hy, h->hz); ++g_launch_count;
+  k_rigid<<<grid, 256, 0, h->stream>>>(h->d_sub, h->hx, h->hy, h->hz, h->d_xyz, h->NY, h->NZ); ++g_launch_count;
 }
 
 void launch_chol_inv_small(msgfem* h, int wg, const int* d_ncols, int nfixed, int drop_last) {
@@ -600,8 +621,8 @@ void launch_chol_inv_small(msgfem* h, int wg, const int* d_ncols, int nfixed, in
 void launch_colnorms(msgfem* h, int wa, int wb, int p) {
   const int nchunk = (3 * max_nnode(h) + GRAM_ROWS - 1) / GRAM_ROWS;
   dim3 grid(nchunk, h->N);
-  k_colnorm_partial<<<grid, 256, 0, h->stream>>>(h->d_sub, wa, wb, h->d_gram_part, nchunk); ++g_launch_count;
-  k_colnorm_reduce<<<h->N, 32, 0, h->stream>>>(h->d_sub, h->d_gram_part, nchunk, p); ++g_launch_count;
+  k_colnorm_partial<<<grid, 256, 0, h->stream>>>(h->d_sub, act(h), wa, wb, h->d_gram_part, nchunk); ++g_launch_count;
+  k_colnorm_reduce<<<h->N, 32, 0, h->stream>>>(h->d_sub, act(h), h->d_gram_part, nchunk, p); ++g_launch_count;
 }
 
 void launch_scale_rows_mu(msgfem* h, int which) {
@@ -692,7 +713,8 @@ k_refine_check(const SubDev* __restrict__ subs, int* __restrict__ flags, int wr,
 }
 
 // X[:, 0] -= bload (KB-wide block)
-__global__ void k_sub_load_kb(const SubDev* __restrict__ subs, int which) {
+__global__ void k_sub_load_kb(const SubDev* __restrict__ subs, const int* __restrict__ active, int which) {
+  if (active != nullptr && !active[blockIdx.y]) return;
   const SubDev& s = subs[blockIdx.y];
   double* X = mv_ptr(s, which);
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < s.nfull; r += gridDim.x * blockDim.x)
@@ -713,5 +735,5 @@ void launch_refine_check(msgfem* h, int wr, int wref, int keep, int step) {
 
 void launch_sub_load_kb(msgfem* h, int which) {
   dim3 grid(64, h->N);
-  k_sub_load_kb<<<grid, 256, 0, h->stream>>>(h->d_sub, which); ++g_launch_count;
+  k_sub_load_kb<<<grid, 256, 0, h->stream>>>(h->d_sub, h->d_flags, which); ++g_launch_count;
 }

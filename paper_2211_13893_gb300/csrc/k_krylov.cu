@@ -267,7 +267,8 @@ __global__ void k_store_block(const SubDev* __restrict__ subs, const int* __rest
     D[(e / KB) * MQ + j * KB + e % KB] = X[e];
 }
 
-__global__ void k_zero_kb(const SubDev* __restrict__ subs, int which, int col0_only) {
+__global__ void k_zero_kb(const SubDev* __restrict__ subs, const int* __restrict__ active, int which, int col0_only) {
+  if (active != nullptr && !active[blockIdx.y]) return;
   const SubDev& s = subs[blockIdx.y];
   double* X = mv_ptr(s, which);
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)s.nfull * KB;
@@ -284,8 +285,10 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
   return x ^ (x >> 31);
 }
 
-__global__ void k_random_kb(const SubDev* __restrict__ subs, int which, unsigned long long seed) {
+__global__ void k_random_kb(const SubDev* __restrict__ subs, const int* __restrict__ active, int which,
+                            unsigned long long seed) {
   const int sidx = blockIdx.y;
+  if (active != nullptr && !active[sidx]) return;
   const SubDev& s = subs[sidx];
   double* X = mv_ptr(s, which);
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)s.nfull * KB;
@@ -313,7 +316,8 @@ __global__ void k_mask_kb(const SubDev* __restrict__ subs, const int* __restrict
   }
 }
 
-__global__ void k_zero_pins_kb(const SubDev* __restrict__ subs, int which) {
+__global__ void k_zero_pins_kb(const SubDev* __restrict__ subs, const int* __restrict__ active, int which) {
+  if (active != nullptr && !active[blockIdx.x]) return;
   const SubDev& s = subs[blockIdx.x];
   if (!s.floating) return;
   double* X = mv_ptr(s, which);
@@ -322,7 +326,8 @@ __global__ void k_zero_pins_kb(const SubDev* __restrict__ subs, int which) {
 }
 
 // dst[:, 0] = sign * bload, other columns zero (KB-wide block)
-__global__ void k_load_col_kb(const SubDev* __restrict__ subs, int which, double sign) {
+__global__ void k_load_col_kb(const SubDev* __restrict__ subs, const int* __restrict__ active, int which, double sign) {
+  if (active != nullptr && !active[blockIdx.y]) return;
   const SubDev& s = subs[blockIdx.y];
   double* X = mv_ptr(s, which);
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)s.nfull * KB;
@@ -330,7 +335,8 @@ __global__ void k_load_col_kb(const SubDev* __restrict__ subs, int which, double
     X[e] = (e % KB == 0) ? sign * s.bload[e / KB] : 0.0;
 }
 
-__global__ void k_take_col_kb(const SubDev* __restrict__ subs, int which) {
+__global__ void k_take_col_kb(const SubDev* __restrict__ subs, const int* __restrict__ active, int which) {
+  if (active != nullptr && !active[blockIdx.y]) return;
   const SubDev& s = subs[blockIdx.y];
   const double* X = mv_ptr(s, which);
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < s.nfull; r += gridDim.x * blockDim.x)
@@ -578,7 +584,7 @@ void launch_store_block(msgfem* h, int src, int j, int dst) {
 
 void launch_random_kb(msgfem* h, int which, unsigned long long seed) {
   dim3 grid(256, h->N);
-  k_random_kb<<<grid, 256, 0, h->stream>>>(h->d_sub, which, seed); ++g_launch_count;
+  k_random_kb<<<grid, 256, 0, h->stream>>>(h->d_sub, h->d_flags, which, seed); ++g_launch_count;
 }
 
 void launch_mask_kb(msgfem* h, int which, int keep) {
@@ -586,21 +592,21 @@ void launch_mask_kb(msgfem* h, int which, int keep) {
   k_mask_kb<<<grid, 256, 0, h->stream>>>(h->d_sub, h->d_flags, which, keep); ++g_launch_count;
 }
 
-void launch_zero_pins_kb(msgfem* h, int which) { k_zero_pins_kb<<<h->N, 6 * KB, 0, h->stream>>>(h->d_sub, which); ++g_launch_count; }
+void launch_zero_pins_kb(msgfem* h, int which) { k_zero_pins_kb<<<h->N, 6 * KB, 0, h->stream>>>(h->d_sub, h->d_flags, which); ++g_launch_count; }
 
 void launch_load_col_kb(msgfem* h, int which, double sign) {
   dim3 grid(256, h->N);
-  k_load_col_kb<<<grid, 256, 0, h->stream>>>(h->d_sub, which, sign); ++g_launch_count;
+  k_load_col_kb<<<grid, 256, 0, h->stream>>>(h->d_sub, h->d_flags, which, sign); ++g_launch_count;
 }
 
 void launch_take_col_kb(msgfem* h, int which) {
   dim3 grid(64, h->N);
-  k_take_col_kb<<<grid, 256, 0, h->stream>>>(h->d_sub, which); ++g_launch_count;
+  k_take_col_kb<<<grid, 256, 0, h->stream>>>(h->d_sub, h->d_flags, which); ++g_launch_count;
 }
 
 void launch_zero_kb(msgfem* h, int which) {
   dim3 grid(256, h->N);
-  k_zero_kb<<<grid, 256, 0, h->stream>>>(h->d_sub, which, 0); ++g_launch_count;
+  k_zero_kb<<<grid, 256, 0, h->stream>>>(h->d_sub, h->d_flags, which, 0); ++g_launch_count;
 }
 
 void launch_rr_krylov(msgfem* h, const int* d_m, const int* d_nw) {

@@ -130,7 +130,9 @@ k_warm_targets(const double* __restrict__ EV, const int* __restrict__ b2rows, in
 struct WarmDev { const float* X0; int ld, ncols, n2; const int* b2rows; };
 
 // start block rows on B2 from the registered X0 (first ncols columns)
-__global__ void k_load_start(const SubDev* __restrict__ subs, const WarmDev* __restrict__ warm, int which) {
+__global__ void k_load_start(const SubDev* __restrict__ subs, const int* __restrict__ active,
+                             const WarmDev* __restrict__ warm, int which) {
+  if (active != nullptr && !active[blockIdx.y]) return;
   const WarmDev wd = warm[blockIdx.y];
   if (wd.X0 == nullptr) return;
   double* X = mv_ptr(subs[blockIdx.y], which);
@@ -184,7 +186,7 @@ bool warm_upload(msgfem* h) {
 
 void launch_load_start(msgfem* h, int which) {
   dim3 grid(16, h->N);
-  k_load_start<<<grid, 256, 0, h->stream>>>(h->d_sub, static_cast<const WarmDev*>(h->d_warm), which);
+  k_load_start<<<grid, 256, 0, h->stream>>>(h->d_sub, h->d_flags, static_cast<const WarmDev*>(h->d_warm), which);
   ++g_launch_count;
 }
 

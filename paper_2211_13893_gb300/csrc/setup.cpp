@@ -3,8 +3,9 @@
 // factorisation and solves.
 //
 // Decomposition (Secs. 3.1, 3.3): subdomain (a, b) owns the element box
-// [a NX / sx, (a+1) NX / sx) x [b NY / sy, (b+1) NY / sy) x [0, NZ); Omega
-// and Omega* grow it by o and o* element layers, clipped to the mesh.
+// [a NX / sx, (a+1) NX / sx) x [b NY / sy, (b+1) NY / sy) x [0, NZ), or
+// subdomain j owns the j-th given box; Omega and Omega* grow it by o and o*
+// element layers, clipped to the mesh.
 // DoF classes on Omega* (Sec. 4.3): class 3 (B3) = nodes on the clamped face
 // x = 0; class 2 (B2) = other nodes on the closure of the part of dOmega*
 // inside Omega; class 1 (B1) = the rest.
@@ -61,28 +62,94 @@ std::vector<double> pou_weights(const Box& om, int NX, int NY, int NZ, int o) {
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
+// Consistent nodal load of the traction (-p, 0, 0) on the i = NX face: for
+// every face quad, int N_a dA over its bilinear map X(s, r), with 2x2 Gauss
+// points (exact on a planar quad, whose area element is linear in s and r).
+// Returns the x component per face node (j, k), index j (NZ + 1) + k.
+std::vector<double> end_face_load(const msgfem* h) {
+  const int NY = h->NY, NZ = h->NZ;
+  std::vector<double> f((size_t)(NY + 1) * (NZ + 1), 0.0);
+  const double gp = 0.57735026918962576451;
+  const int cj[4] = {0, 1, 1, 0}, ck[4] = {0, 0, 1, 1};
+  for (int j = 0; j < NY; ++j)
+    for (int k = 0; k < NZ; ++k) {
+      double X[4][3];
+      for (int a = 0; a < 4; ++a) node_xyz(h, h->NX, j + cj[a], k + ck[a], X[a]);
+      for (int g = 0; g < 4; ++g) {
+        const double s = (g & 1) ? gp : -gp, r = (g & 2) ? gp : -gp;
+        double Xs[3] = {0, 0, 0}, Xr[3] = {0, 0, 0}, N[4];
+        for (int a = 0; a < 4; ++a) {
+          const double sa = cj[a] ? 1.0 : -1.0, ra = ck[a] ? 1.0 : -1.0;
+          N[a] = 0.25 * (1.0 + sa * s) * (1.0 + ra * r);
+          for (int d = 0; d < 3; ++d) {
+            Xs[d] += 0.25 * sa * (1.0 + ra * r) * X[a][d];
+            Xr[d] += 0.25 * (1.0 + sa * s) * ra * X[a][d];
+          }
+        }
+        const double cx = Xs[1] * Xr[2] - Xs[2] * Xr[1], cy = Xs[2] * Xr[0] - Xs[0] * Xr[2],
+                     cz = Xs[0] * Xr[1] - Xs[1] * Xr[0];
+        const double dA = std::sqrt(cx * cx + cy * cy + cz * cz);
+        for (int a = 0; a < 4; ++a) f[(size_t)(j + cj[a]) * (NZ + 1) + k + ck[a]] += N[a] * dA;
+      }
+    }
+  for (double& v : f) v *= -h->traction;
+  return f;
+}
+
 }  // namespace
+
+void node_xyz(const msgfem* h, int i, int j, int k, double X[3]) {
+  if (!h->h_xyz.empty()) {
+    const size_t n = ((size_t)i * (h->NY + 1) + j) * (h->NZ + 1) + k;
+    X[0] = h->h_xyz[3 * n]; X[1] = h->h_xyz[3 * n + 1]; X[2] = h->h_xyz[3 * n + 2];
+  } else {
+    X[0] = i * h->hx; X[1] = j * h->hy; X[2] = k * h->hz;
+  }
+}
 
 msgfem_status build_problem(msgfem* h) {
   const int NX = h->NX, NY = h->NY, NZ = h->NZ;
-  h->N = h->sx * h->sy;
+  std::vector<Box> hats;
+  if (!h->boxes.empty()) {
+    // explicit boxes: each element of the NX x NY grid in exactly one box
+    std::vector<int> cover((size_t)NX * NY, 0);
+    for (size_t b = 0; b + 3 < h->boxes.size(); b += 4) {
+      Box hat{h->boxes[b], h->boxes[b + 1], h->boxes[b + 2], h->boxes[b + 3]};
+      if (hat.x0 < 0 || hat.x1 > NX || hat.y0 < 0 || hat.y1 > NY || hat.x1 <= hat.x0 || hat.y1 <= hat.y0) {
+        h->err = "partition box empty or outside the mesh";
+        return MSGFEM_EINVAL;
+      }
+      for (int x = hat.x0; x < hat.x1; ++x)
+        for (int y = hat.y0; y < hat.y1; ++y) cover[(size_t)x * NY + y]++;
+      hats.push_back(hat);
+    }
+    for (int c : cover)
+      if (c != 1) {
+        h->err = "partition boxes do not tile the mesh";
+        return MSGFEM_EINVAL;
+      }
+  } else {
+    for (int a = 0; a < h->sx; ++a)
+      for (int b = 0; b < h->sy; ++b)
+        hats.push_back({(a * NX) / h->sx, ((a + 1) * NX) / h->sx, (b * NY) / h->sy, ((b + 1) * NY) / h->sy});
+  }
+  h->N = (int)hats.size();
   h->sub.assign(h->N, SubDev{});
   h->hsub.assign(h->N, HostSub{});
   h->n1.assign(h->N, 0);
   h->n2.assign(h->N, 0);
   h->n3.assign(h->N, 0);
   std::vector<Box> omega(h->N), star(h->N);
-  for (int a = 0; a < h->sx; ++a)
-    for (int b = 0; b < h->sy; ++b) {
-      const int j = a * h->sy + b;
-      Box hat{(a * NX) / h->sx, ((a + 1) * NX) / h->sx, (b * NY) / h->sy, ((b + 1) * NY) / h->sy};
-      if (hat.x1 <= hat.x0 || hat.y1 <= hat.y0) {
-        h->err = "partition has an empty subdomain";
-        return MSGFEM_EINVAL;
-      }
-      omega[j] = grow(hat, h->o, NX, NY);
-      star[j] = grow(hat, h->os, NX, NY);
+  for (int j = 0; j < h->N; ++j) {
+    const Box& hat = hats[j];
+    if (hat.x1 <= hat.x0 || hat.y1 <= hat.y0) {
+      h->err = "partition has an empty subdomain";
+      return MSGFEM_EINVAL;
     }
+    omega[j] = grow(hat, h->o, NX, NY);
+    star[j] = grow(hat, h->os, NX, NY);
+  }
+  const std::vector<double> face = end_face_load(h);
   // partition of unity: global weight sums
   const size_t nnodes = (size_t)(NX + 1) * (NY + 1) * (NZ + 1);
   std::vector<double> total(nnodes, 0.0);
@@ -149,11 +216,31 @@ msgfem_status build_problem(msgfem* h) {
       }
     for (int i = 0; i < 6; ++i) s.pin[i] = -1;
     if (s.floating) {
-      // 3-2-1 pins on three bottom corners of the Omega* box
+      // 3-2-1 pins on three bottom corners A, B, C of the Omega* node box: all
+      // components at A; at B the two components least aligned with AB (they
+      // stop the rotations about the axes normal to AB); at C the component
+      // that the remaining rotation about AB moves most, max |(AB x AC)_c|
+      // (on the box beam: y, z at B and z at C)
       const int qa = 0, qb = (s.nxn - 1) * s.nyn, qc = s.nyn - 1;
+      double A[3], B[3], Cc[3];
+      node_xyz(h, s.I0, s.J0, 0, A);
+      node_xyz(h, s.I1, s.J0, 0, B);
+      node_xyz(h, s.I0, s.J1, 0, Cc);
+      const double ab[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+      const double ac[3] = {Cc[0] - A[0], Cc[1] - A[1], Cc[2] - A[2]};
+      int skip = 0;
+      for (int d = 1; d < 3; ++d)
+        if (std::fabs(ab[d]) > std::fabs(ab[skip])) skip = d;
+      const double nrm[3] = {ab[1] * ac[2] - ab[2] * ac[1], ab[2] * ac[0] - ab[0] * ac[2],
+                             ab[0] * ac[1] - ab[1] * ac[0]};
+      int cpin = 0;
+      for (int d = 1; d < 3; ++d)
+        if (std::fabs(nrm[d]) > std::fabs(nrm[cpin])) cpin = d;
       s.pin[0] = 3 * qa; s.pin[1] = 3 * qa + 1; s.pin[2] = 3 * qa + 2;
-      s.pin[3] = 3 * qb + 1; s.pin[4] = 3 * qb + 2;
-      s.pin[5] = 3 * qc + 2;
+      int np = 3;
+      for (int d = 0; d < 3; ++d)
+        if (d != skip) s.pin[np++] = 3 * qb + d;
+      s.pin[5] = 3 * qc + cpin;
     }
     // mu on Omega* nodes (zero outside Omega)
     hs.mu.assign(s.nnode, 0.0);
@@ -166,15 +253,14 @@ msgfem_status build_problem(msgfem* h) {
         (void)onx;
         hs.mu[(size_t)k * s.npl + q] = w / total[((size_t)gi * (NY + 1) + gj) * (NZ + 1) + k];
       }
-    // consistent nodal load of the traction (-p, 0, 0) on x = L
+    // consistent nodal load of the traction (-p, 0, 0) on the x = L face
     hs.bload.assign(s.nfull, 0.0);
     if (s.loaded)
       for (int k = 0; k <= NZ; ++k)
         for (int q = 0; q < s.npl; ++q) {
           const int gi = s.I0 + q / s.nyn, gj = s.J0 + q % s.nyn;
           if (gi != NX) continue;
-          const double wy = (gj == 0 || gj == NY) ? 0.5 : 1.0, wz = (k == 0 || k == NZ) ? 0.5 : 1.0;
-          hs.bload[((size_t)k * s.npl + q) * 3] = -h->traction * h->hy * h->hz * wy * wz;
+          hs.bload[((size_t)k * s.npl + q) * 3] = face[(size_t)gj * (NZ + 1) + k];
         }
   }
   // batched instances: subdomain j of instance i is subdomain i N0 + j
@@ -377,48 +463,52 @@ void flatten_solve(std::map<long long, std::vector<SolveTaskT<T>>>& keys, SolveS
 
 }  // namespace
 
-// The 2N factorisations are independent chains; they are dealt into NGROUP
-// groups, each launched on its own stream, so that a group's narrow steps
-// (POTRF, TRMM, late UPDATEs) overlap the wide steps of the others instead of
-// waiting at a common launch boundary.
+// The 2N factorisations of a wave are independent chains; they are dealt into
+// NGROUP groups, each launched on its own stream, so that a group's narrow
+// steps (POTRF, TRMM, late UPDATEs) overlap the wide steps of the others
+// instead of waiting at a common launch boundary.
 void build_factor_schedule(msgfem* h) {
   int Tmax = 1;
   for (const auto& s : h->sub) Tmax = std::max(Tmax, std::max(s.bK, s.bA) / TILE);
   const int ng = h->ngroup;
-  if (h->mixed) {
-    std::vector<FactorKeysT<float>> fk(ng);
-    int chain = 0;
-    for (int j = 0; j < h->N; ++j) {
-      SubDev& s = h->sub[j];
-      add_matrix_tasks(fk[chain++ % ng], s.DKf, s.EKf, s.LKf, s.bK, s.nzn, j, Tmax);
-      add_matrix_tasks(fk[chain++ % ng], s.DAf, s.EAf, s.LAf, s.bA, s.nzn, j, Tmax);
+  for (WaveSched& w : h->waves) {
+    if (h->mixed) {
+      std::vector<FactorKeysT<float>> fk(ng);
+      int chain = 0;
+      for (int j : w.members) {
+        SubDev& s = h->sub[j];
+        add_matrix_tasks(fk[chain++ % ng], s.DKf, s.EKf, s.LKf, s.bK, s.nzn, j, Tmax);
+        add_matrix_tasks(fk[chain++ % ng], s.DAf, s.EAf, s.LAf, s.bA, s.nzn, j, Tmax);
+      }
+      w.factf.steps.clear();
+      w.factf.gemm.clear();
+      for (int g = 0; g < ng; ++g) flatten(fk[g], w.factf, true);
+      continue;
     }
-    h->factf.steps.clear();
-    h->factf.gemm.clear();
-    for (int g = 0; g < ng; ++g) flatten(fk[g], h->factf, true);
-    return;
+    std::vector<FactorKeys> fk(ng);
+    int chain = 0;
+    for (int j : w.members) {
+      SubDev& s = h->sub[j];
+      add_matrix_tasks(fk[chain++ % ng], s.DK, s.EK, s.LK, s.bK, s.nzn, j, Tmax);
+      add_matrix_tasks(fk[chain++ % ng], s.DA, s.EA, s.LA, s.bA, s.nzn, j, Tmax);
+    }
+    w.fact.steps.clear();
+    w.fact.gemm.clear();
+    for (int g = 0; g < ng; ++g) flatten(fk[g], w.fact, true);
   }
-  std::vector<FactorKeys> fk(ng);
-  int chain = 0;
-  for (int j = 0; j < h->N; ++j) {
-    SubDev& s = h->sub[j];
-    add_matrix_tasks(fk[chain++ % ng], s.DK, s.EK, s.LK, s.bK, s.nzn, j, Tmax);
-    add_matrix_tasks(fk[chain++ % ng], s.DA, s.EA, s.LA, s.bA, s.nzn, j, Tmax);
-  }
-  h->fact.steps.clear();
-  h->fact.gemm.clear();
-  for (int g = 0; g < ng; ++g) flatten(fk[g], h->fact, true);
 }
 
+namespace {
 template <typename T>
-void build_solves_t(msgfem* h, SolveScheduleT<T>& sK, SolveScheduleT<T>& sA, SolveScheduleT<T>& sK8,
-                    SolveScheduleT<T>& sA8, bool f32) {
+void build_solves_t(msgfem* h, const std::vector<int>& members, SolveScheduleT<T>& sK, SolveScheduleT<T>& sA,
+                    SolveScheduleT<T>& sK8, SolveScheduleT<T>& sA8, bool f32) {
   const int ng = h->ngroup;
   using Keys = std::map<long long, std::vector<SolveTaskT<T>>>;
   std::vector<Keys> kk(ng), ka(ng), kk8(ng), ka8(ng);
-  for (int j = 0; j < h->N; ++j) {
+  for (size_t m = 0; m < members.size(); ++m) {
+    const int j = members[m];
     SubDev& s = h->sub[j];
-    const int g = j % ng;
+    const int g = (int)(m % ng);
     T* EK = f32 ? (T*)s.EKf : (T*)s.EK;
     T* LK = f32 ? (T*)s.LKf : (T*)s.LK;
     T* EA = f32 ? (T*)s.EAf : (T*)s.EA;
@@ -445,13 +535,16 @@ void build_solves_t(msgfem* h, SolveScheduleT<T>& sK, SolveScheduleT<T>& sA, Sol
     flatten_solve(ka8[g], sA8, true);
   }
 }
+}  // namespace
 
-// Subdomains are dealt into the stream groups as well.
+// Subdomains are dealt into the stream groups as well (per wave).
 void build_solve_schedules(msgfem* h) {
-  if (h->mixed)
-    build_solves_t<float>(h, h->solveKf, h->solveAf, h->solveK8f, h->solveA8f, true);
-  else
-    build_solves_t<double>(h, h->solveK, h->solveA, h->solveK8, h->solveA8, false);
+  for (WaveSched& w : h->waves) {
+    if (h->mixed)
+      build_solves_t<float>(h, w.members, w.solveKf, w.solveAf, w.solveK8f, w.solveA8f, true);
+    else
+      build_solves_t<double>(h, w.members, w.solveK, w.solveA, w.solveK8, w.solveA8, false);
+  }
 }
 
 // Coarse matrix: one dense block of size NcPad, factorised by the same tile

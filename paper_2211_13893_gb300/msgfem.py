@@ -31,21 +31,21 @@ class MsgfemError(RuntimeError):
 
 class Mesh(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("hx", C.c_double), ("hy", C.c_double),
-                ("hz", C.c_double), ("traction", C.c_double)]
+                ("hz", C.c_double), ("traction", C.c_double), ("xyz", C.c_void_p)]
 
 
 class Plies(C.Structure):
-    _fields_ = [("E9", C.c_void_p), ("elem_angle_deg", C.c_void_p)]
+    _fields_ = [("E9", C.c_void_p), ("elem_angle_deg", C.c_void_p), ("elem_frame", C.c_void_p)]
 
 
 class Partition(C.Structure):
-    _fields_ = [("sx", C.c_int), ("sy", C.c_int)]
+    _fields_ = [("sx", C.c_int), ("sy", C.c_int), ("n_boxes", C.c_int), ("boxes", C.c_void_p)]
 
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("block", C.c_int), ("max_iter", C.c_int), ("tol", C.c_double),
                 ("seed", C.c_ulonglong), ("stream", C.c_void_p), ("profile", C.c_int), ("solver", C.c_int),
-                ("streams", C.c_int), ("refine", C.c_int), ("instances", C.c_int)]
+                ("streams", C.c_int), ("refine", C.c_int), ("instances", C.c_int), ("wave_mb", C.c_double)]
 
 
 class Profile(C.Structure):
@@ -53,7 +53,7 @@ class Profile(C.Structure):
                 ("iterate_ms", C.c_double), ("coarse_ms", C.c_double), ("factor_flops", C.c_double),
                 ("solve_flops", C.c_double), ("launches", C.c_longlong), ("solve_calls", C.c_int),
                 ("solve_bytes", C.c_double), ("stencil_ms", C.c_double), ("ortho_ms", C.c_double),
-                ("stencil_flops", C.c_double)]
+                ("stencil_flops", C.c_double), ("waves", C.c_int), ("pool_mb", C.c_double)]
 
 
 class SubInfo(C.Structure):
@@ -121,11 +121,15 @@ def _ptr(a):
 
 
 class MSGFEM:
-    """One MS-GFEM problem: a laminated box mesh, its decomposition and the handle."""
+    """One MS-GFEM problem: a laminated hexahedral mesh, its decomposition and the handle.
+
+    ``xyz`` (node coordinates), ``frames`` (per-element ply frames) and
+    ``boxes`` (explicit subdomain boxes) are optional; without them the mesh
+    is the box beam of bricks hx * hy * hz with the sx * sy partition."""
 
     def __init__(self, nx, ny, nz, hx, hy, hz, traction, E9, elem_angles, sx, sy, overlap, oversampling,
                  block=0, max_iter=0, tol=0.0, seed=0, stream=None, precision=0, profile=0, solver=0, streams=0, refine=0,
-                 instances=0):
+                 instances=0, xyz=None, frames=None, boxes=None, wave_mb=0.0):
         self.lib = load_library()
         self.h = C.c_void_p()
         self._E9 = np.ascontiguousarray(E9, dtype=np.float64)
@@ -133,11 +137,16 @@ class MSGFEM:
         if not hasattr(ang, "data_ptr"):
             ang = np.ascontiguousarray(ang, dtype=np.float64).reshape(-1)
         self._ang = ang
-        self.mesh = Mesh(nx, ny, nz, hx, hy, hz, traction)
+        self._xyz = None if xyz is None else np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1)
+        self._frames = None if frames is None else np.ascontiguousarray(frames, dtype=np.float64).reshape(-1)
+        self._boxes = None if boxes is None else np.ascontiguousarray(boxes, dtype=np.int32).reshape(-1)
+        self.mesh = Mesh(nx, ny, nz, hx, hy, hz, traction, _ptr(self._xyz))
         self.n_dof = 3 * (nx + 1) * (ny + 1) * (nz + 1)
-        plies = Plies(self._E9.ctypes.data, _ptr(ang))
-        part = Partition(sx, sy)
-        opt = Options(precision, block, max_iter, tol, seed, stream, profile, solver, streams, refine, instances)
+        plies = Plies(self._E9.ctypes.data, _ptr(ang), _ptr(self._frames))
+        nb = 0 if self._boxes is None else len(self._boxes) // 4
+        part = Partition(sx, sy, nb, _ptr(self._boxes))
+        opt = Options(precision, block, max_iter, tol, seed, stream, profile, solver, streams, refine, instances,
+                      wave_mb)
         self.instances = max(1, instances)
         st = self.lib.msgfem_setup(C.byref(self.mesh), C.byref(plies), C.byref(part), overlap, oversampling,
                                    C.byref(opt), C.byref(self.h))
@@ -147,6 +156,15 @@ class MSGFEM:
 
     @classmethod
     def from_config(cls, cfg, angles, **kw):
+        """A workload description: a box beam, or a curved section with node
+        coordinates, ply frames and subdomain boxes (``workloads.section``)."""
+        if getattr(cfg, "kind", "beam") == "section":
+            from workloads.section import section_frames, section_nodes
+            kw.setdefault("xyz", section_nodes(cfg))
+            kw.setdefault("frames", section_frames(cfg))
+            kw.setdefault("boxes", np.array(cfg.boxes))
+            return cls(cfg.NX, cfg.NY, cfg.NZ, 0.0, 0.0, 0.0, cfg.traction, cfg.material, angles,
+                       cfg.sx, cfg.sy, cfg.overlap, cfg.oversampling, **kw)
         return cls(cfg.NX, cfg.NY, cfg.NZ, cfg.hx, cfg.hy, cfg.t, cfg.traction, cfg.material, angles,
                    cfg.sx, cfg.sy, cfg.overlap, cfg.oversampling, **kw)
 

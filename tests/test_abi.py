@@ -63,3 +63,11 @@ def test_setup_rejects_bad_descriptors(lib_path):
         p = msgfem.Partition(*part)
         st = lib.msgfem_setup(C.byref(m), C.byref(plies), C.byref(p), o, os_, C.byref(opt), C.byref(h))
         assert st == 1 and not h.value
+    # explicit boxes announced without an array; a box mesh without a brick size
+    p = msgfem.Partition(1, 1, 2, None)
+    m = msgfem.Mesh(2, 2, 2, 1.0, 1.0, 1.0, 1.0)
+    assert lib.msgfem_setup(C.byref(m), C.byref(plies), C.byref(p), 1, 1, C.byref(opt), C.byref(h)) == 1
+    m = msgfem.Mesh(2, 2, 2, 0.0, 1.0, 1.0, 1.0, None)
+    p = msgfem.Partition(1, 1)
+    assert lib.msgfem_setup(C.byref(m), C.byref(plies), C.byref(p), 1, 1, C.byref(opt), C.byref(h)) == 1
+    assert not h.value
