@@ -18,6 +18,12 @@ default); it also carries
                FP64 refinement: subdomains/s, the eigenvalue and energy-norm
                differences to the FP64 run, and an HBM roofline entry for the
                FP32 solves;
+  c4           the batched uneven C-section spar (250 x 110 x 32 curved hexes,
+               256 subdomains of 4k-42k DoF) in mixed precision, all in one
+               handle (memory-bounded waves when the factors do not fit):
+               subdomains/s, phase times, the FP32-solve HBM roofline entry and
+               the eigenvalues of sampled subdomains against stored oracle
+               values;
   warm_c5      the learned warm start on the wrinkled c1 beam (512 samples,
                384 for training), 128 beams batched per local stage: cold
                start vs nominal-basis reuse vs trained network;
@@ -320,6 +326,9 @@ def run_ours(args):
     mixed = None
     if not args.no_mixed:
         mixed = run_mixed(args, cfg, ang_dev, stream, dev, rank, lam_fp64, u_fp64, flush, world)
+    c4 = None
+    if not args.no_c4:
+        c4 = run_c4(args, dev, stream, flush, rank, world)
     warm = None
     if not args.no_warm and rank == 0:
         warm = run_warm_c5(args, dev)
@@ -339,10 +348,90 @@ def run_ours(args):
                            "l2": "flushed between timed steps (256 MiB write); working set ~25 GB >> L2",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "solver": extra, "mixed": mixed, "warm_c5": warm}
+                "clocks": clocks, "solver": extra, "mixed": mixed, "c4": c4, "warm_c5": warm}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_c4(args, dev, stream, flush, rank, world):
+    """The batched uneven C-section spar in mixed precision: one handle holding
+    all 256 subdomains (oversampling domains of 4k-42k DoF), one step = local
+    stage + coarse assembly + coarse solve, as for the main workload."""
+    import numpy as np
+    import torch
+    from paper_2211_13893_gb300 import MSGFEM
+    from workloads import element_angles, get_config
+    from workloads.section import omega_star_sizes
+    cfg = get_config("c4")
+    t0 = time.perf_counter()
+    ang = torch.tensor(element_angles(cfg).reshape(-1), dtype=torch.float64, device=dev)
+    m = MSGFEM.from_config(cfg, ang, seed=11, stream=stream.cuda_stream, profile=1, precision=1,
+                           streams=args.streams)
+    setup_s = time.perf_counter() - t0
+    lam = torch.empty((m.N, cfg.n_loc), dtype=torch.float64, device=dev)
+    u = torch.empty(m.n_dof, dtype=torch.float64, device=dev)
+
+    def step():
+        m.local_spaces(cfg.n_loc, lam_out=lam)
+        m.coarse_assemble()
+        m.solve(u_out=u)
+
+    step()                                   # warm-up: graph capture, first launches
+    torch.cuda.synchronize()
+    m.profile(reset=True)
+    ms = []
+    for _ in range(args.c4_steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with _Range("msgfem_timed_c4"):
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    prof = m.profile()
+    total = sum(ms)
+    if world > 1:
+        t = torch.tensor([total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+    k = args.c4_steps
+    infos = [m.info(j) for j in range(m.N)]
+    sizes = omega_star_sizes(cfg)
+    hbm, hbm_note = _hbm_peak()
+    solve_gbs = prof["solve_bytes"] * k / (prof["solve_ms"] / 1000.0) / 1e9 if prof["solve_ms"] else 0.0
+    sample = None
+    gold_path = os.path.join(ROOT, "tests", "golden", "c4_sample_eigs.json")
+    if os.path.exists(gold_path):
+        gold = json.load(open(gold_path))
+        lh = lam.cpu().numpy()
+        d = 0.0
+        for key, rec in gold["samples"].items():
+            ref = np.array(rec["lambda"])
+            d = max(d, float(np.abs(lh[int(key)] - ref).max() / max(abs(ref[-1]), 1e-2)))
+        sample = {"subdomains": [int(x) for x in gold["samples"]], "eig_rel_diff_vs_oracle_max": d}
+    out = {"workload": (f"C-section spar 250x110x32 curved hex ({cfg.n_dof} DoF, 32 plies), 256 subdomains "
+                        f"(16 x 16 graded boxes), overlap 1, oversampling 3, n_loc={cfg.n_loc}, "
+                        f"oversampling domains {int(sizes.min())}-{int(sizes.max())} DoF "
+                        f"(mean {int(sizes.mean())}); mixed precision"),
+           "value": world * m.N * k / (total / 1000.0), "unit": "subdomains/s", "ms_per_step": total / k,
+           "setup_s": setup_s, "waves": prof["waves"], "pool_gb": prof["pool_mb"] / 1024.0,
+           "assemble_ms_per_step": prof["assemble_ms"] / k, "factor_ms_per_step": prof["factor_ms"] / k,
+           "factor_tflops": prof["factor_flops"] * k / (prof["factor_ms"] / 1000.0) / 1e12
+           if prof["factor_ms"] else None,
+           "solve_ms_per_step": prof["solve_ms"] / k, "iterate_ms_per_step": prof["iterate_ms"] / k,
+           "stencil_ms_per_step": prof["stencil_ms"] / k, "ortho_ms_per_step": prof["ortho_ms"] / k,
+           "coarse_ms_per_step": prof["coarse_ms"] / k,
+           "iterations_max": max(i["iterations"] for i in infos),
+           "residual_max": max(i["residual"] for i in infos),
+           "roofline": {"bound": "hbm", "achieved": solve_gbs, "peak": hbm, "unit": "GB/s",
+                        "frac": solve_gbs / hbm, "peak_note": hbm_note,
+                        "kernel": "k_solve_async (FP32 block solves, 8 right-hand sides)",
+                        "time_share": prof["solve_ms"] / total if total else None},
+           "sampled_parity": sample}
+    m.close()
+    return out
 
 
 def run_mixed(args, cfg, ang_dev, stream, dev, rank, lam_fp64, u_fp64, flush, world):
@@ -517,6 +606,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison run")
     ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start (c5) run")
+    ap.add_argument("--no-c4", action="store_true", help="skip the batched C-section (c4) run")
+    ap.add_argument("--c4-steps", type=int, default=1, help="timed steps of the c4 run")
     ap.add_argument("--streams", type=int, default=0, help="stream groups of the library (0 = its default)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -131,6 +131,10 @@ typedef struct {
                            subdomain j of copy i is subdomain i N0 + j of the handle.  With
                            S > 1 the handle runs the local stage only (msgfem_coarse_assemble
                            returns EINVAL).  0 = 1 */
+  int solve_kernel;     /* kernel of the 8-column block solves: 0 = build default (FP32: cp.async
+                           ring, FP64: register streaming), 1 = cp.async ring (FP32 only),
+                           2 = register streaming, one CTA per 64-row task, 3 = two-CTA
+                           cluster per task (inner dimension split); msgfem_autotune sets it */
   double wave_mb;       /* device memory (MiB) for the layer blocks, factors and block-solve
                            buffers.  Subdomains whose storage does not fit at once are processed
                            in waves that share one pool of this size (largest first, a wave
@@ -166,6 +170,14 @@ typedef struct {
   int waves;            /* waves of subdomains per local stage (msgfem_options.wave_mb) */
   double pool_mb;       /* size of the shared layer-block / factor / solve-buffer pool (MiB) */
 } msgfem_profile;
+
+/* Launch shapes chosen by msgfem_autotune and what it measured. */
+typedef struct {
+  int streams;          /* stream groups of the block-solve schedules (4, 8 or 16) */
+  int solve_kernel;     /* msgfem_options.solve_kernel value chosen (1, 2 or 3) */
+  double best_ms;       /* time of one 8-column K solve plus one A11 solve of the measured wave */
+  double solve_ms[3][3];   /* [streams 4, 8, 16][kernel 1, 2, 3]; -1 = not applicable or not run */
+} msgfem_tuning;
 
 /* Per-subdomain diagnostics filled by msgfem_get_info. */
 typedef struct {
@@ -244,6 +256,20 @@ msgfem_status msgfem_get_basis(msgfem_h h, int j, double* phi_out, int* rows, in
  * independent, but calls whose kernels overlap on the GPU (other streams, other
  * threads) race on the array and must be serialised by the caller. */
 msgfem_status msgfem_energy_error_noalloc(msgfem_h h, const double* u, const double* u_ref, double* energy_err_out);
+
+/* Autotuner of the block-solve launches (not in the paper: a library
+ * convenience for batches of uneven subdomains).  On the subdomains of the
+ * last wave of the previous msgfem_local_spaces call (their factors are the
+ * resident ones) it times `reps` replays (0 = 3) of one 8-column K solve and
+ * one A11 solve, captured as a CUDA graph, for every combination of stream
+ * groups {4, 8, 16} (at most msgfem_options.streams) and solve kernel (the
+ * cp.async ring in mixed precision only, register streaming, two-CTA
+ * cluster), then regroups the solve schedules of every wave and sets the
+ * kernel to the fastest combination; later calls use it.  The working blocks
+ * the timing reads and writes are scratch of the eigensolver; results of the
+ * previous local stage are kept.  tuning (may be NULL) receives the choice
+ * and the measured times.  Errors: ESTATE before msgfem_local_spaces, ECUDA. */
+msgfem_status msgfem_autotune(msgfem_h h, int reps, msgfem_tuning* tuning);
 
 msgfem_status msgfem_get_info(msgfem_h h, int j, msgfem_subinfo* info);
 /* Copy the phase timers (requires msgfem_options.profile = 1 for times). */

@@ -221,6 +221,25 @@ msgfem_status alloc_waves(msgfem* h) {
   return MSGFEM_OK;
 }
 
+// Device copies of a wave's solve task lists (the handle keeps every copy it
+// made until msgfem_destroy; the autotuner re-uploads after regrouping).
+msgfem_status upload_wave_solves(msgfem* h, WaveSched& w) {
+  if (h->mixed) {
+    for (SolveScheduleT<float>* ss : {&w.solveKf, &w.solveAf, &w.solveK8f, &w.solveA8f}) {
+      TRY(dalloc(h, &ss->d_tasks, std::max<size_t>(ss->tasks.size(), 1)));
+      CK(cudaMemcpy(ss->d_tasks, ss->tasks.data(), ss->tasks.size() * sizeof(SolveTaskT<float>),
+                    cudaMemcpyHostToDevice));
+    }
+  } else {
+    for (SolveSchedule* ss : {&w.solveK, &w.solveA, &w.solveK8, &w.solveA8}) {
+      if (ss->tasks.empty()) continue;
+      TRY(dalloc(h, &ss->d_tasks, ss->tasks.size()));
+      CK(cudaMemcpy(ss->d_tasks, ss->tasks.data(), ss->tasks.size() * sizeof(SolveTask), cudaMemcpyHostToDevice));
+    }
+  }
+  return MSGFEM_OK;
+}
+
 msgfem_status allocate(msgfem* h) {
   for (int j = 0; j < h->N; ++j) {
     SubDev& s = h->sub[j];
@@ -307,21 +326,12 @@ msgfem_status allocate(msgfem* h) {
       TRY(dalloc(h, &w.factf.d_gemm, w.factf.gemm.size()));
       CK(cudaMemcpy(w.factf.d_gemm, w.factf.gemm.data(), w.factf.gemm.size() * sizeof(TileTaskT<float>),
                     cudaMemcpyHostToDevice));
-      for (SolveScheduleT<float>* ss : {&w.solveKf, &w.solveAf, &w.solveK8f, &w.solveA8f}) {
-        TRY(dalloc(h, &ss->d_tasks, ss->tasks.size()));
-        CK(cudaMemcpy(ss->d_tasks, ss->tasks.data(), ss->tasks.size() * sizeof(SolveTaskT<float>),
-                      cudaMemcpyHostToDevice));
-      }
     } else {
       TRY(dalloc(h, &w.fact.d_gemm, w.fact.gemm.size()));
       CK(cudaMemcpy(w.fact.d_gemm, w.fact.gemm.data(), w.fact.gemm.size() * sizeof(GemmTask),
                     cudaMemcpyHostToDevice));
-      for (SolveSchedule* ss : {&w.solveK, &w.solveA, &w.solveK8, &w.solveA8}) {
-        if (ss->tasks.empty()) continue;
-        TRY(dalloc(h, &ss->d_tasks, ss->tasks.size()));
-        CK(cudaMemcpy(ss->d_tasks, ss->tasks.data(), ss->tasks.size() * sizeof(SolveTask), cudaMemcpyHostToDevice));
-      }
     }
+    TRY(upload_wave_solves(h, w));
   }
   TRY(dalloc(h, &h->d_mk, h->N));
   TRY(dalloc(h, &h->d_nwk, h->N));
@@ -499,11 +509,11 @@ void timed_solve_w(msgfem* h, int mat, int src, int dst, int neg, int width, int
     if (h->mixed) {
       const SolveScheduleT<float>& sc = width == KB ? (mat == 0 ? w.solveK8f : w.solveA8f)
                                                     : (mat == 0 ? w.solveKf : w.solveAf);
-      run_solve_mv(sc, cs, src, dst, neg, width, &h->gs, add);
+      run_solve_mv(sc, cs, src, dst, neg, width, &h->gs, add, h->solve_variant);
     } else {
       const SolveScheduleT<double>& sc = width == KB ? (mat == 0 ? w.solveK8 : w.solveA8)
                                                      : (mat == 0 ? w.solveK : w.solveA);
-      run_solve_mv(sc, cs, src, dst, neg, width, &h->gs, add);
+      run_solve_mv(sc, cs, src, dst, neg, width, &h->gs, add, h->solve_variant);
     }
   });
   span_end(h, sp);
@@ -857,6 +867,13 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
   if (!(h->opt.tol > 0)) h->opt.tol = 1e-7;
   h->stream = static_cast<cudaStream_t>(h->opt.stream);
   h->ngroup = h->opt.streams > 0 ? std::min(h->opt.streams, NGROUP) : NGROUP;
+  h->ngroup_created = h->ngroup;
+  if (h->opt.solve_kernel < 0 || h->opt.solve_kernel > SOLVE_STREAM_CL2) {
+    *out = h;
+    h->err = "unknown solve_kernel";
+    return MSGFEM_EINVAL;
+  }
+  h->solve_variant = h->opt.solve_kernel;
   if (h->opt.precision != MSGFEM_FP64 && h->opt.precision != MSGFEM_MIXED) {
     h->err = "unknown precision";
     return MSGFEM_EINVAL;
@@ -1197,6 +1214,97 @@ msgfem_status msgfem_get_info(msgfem_h h, int j, msgfem_subinfo* info) {
   info->iterations = j < (int)h->iters.size() ? h->iters[j] : 0;
   info->basis_size = j < (int)h->basis_m.size() ? h->basis_m[j] : 0;
   info->residual = j < (int)h->resid_max.size() ? h->resid_max[j] : 0.0;
+  return MSGFEM_OK;
+}
+
+msgfem_status msgfem_autotune(msgfem_h h, int reps, msgfem_tuning* out) {
+  if (!h) return MSGFEM_EINVAL;
+  if (h->stage < 2) return MSGFEM_ESTATE;
+  if (reps <= 0) reps = 3;
+  cudaStream_t st = h->stream;
+  // the last wave's factors are the ones resident in the pool
+  const int last = (int)h->waves.size() - 1;
+  WaveSched& wl = h->waves[last];
+  h->cur = last;
+  h->base_act.assign(h->N, 0);
+  for (int j : wl.members) h->base_act[j] = 1;
+  TRY(set_active(h, h->base_act));
+  set_dense_context(h->d_flags, h->d_notspd, h->d_sub);
+  msgfem_tuning t;
+  memset(&t, 0, sizeof(t));
+  const int groups[3] = {4, 8, 16};
+  const int variants[3] = {SOLVE_ASYNC_RING, SOLVE_STREAM, SOLVE_STREAM_CL2};
+  double best = 1e300;
+  int best_g = h->ngroup, best_v = h->solve_variant;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int gi = 0; gi < 3; ++gi) {
+    for (int vi = 0; vi < 3; ++vi) t.solve_ms[gi][vi] = -1.0;
+    if (groups[gi] > h->ngroup_created) continue;
+    h->ngroup = groups[gi];
+    build_wave_solve_schedules(h, wl);
+    TRY(upload_wave_solves(h, wl));
+    for (int vi = 0; vi < 3; ++vi) {
+      const int v = variants[vi];
+      if (v == SOLVE_ASYNC_RING && !h->mixed) continue;
+      // one KB-wide K solve and one A11 solve of the wave's working blocks (scratch), as one graph
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ex = nullptr;
+      const long long before = g_launch_count;
+      CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+      if (h->mixed) {
+        run_solve_mv(wl.solveK8f, h->cap, MV_ZB, MV_WB, 0, KB, &h->gs, 0, v);
+        run_solve_mv(wl.solveA8f, h->cap, MV_TB, MV_WB, 1, KB, &h->gs, 0, v);
+      } else {
+        run_solve_mv(wl.solveK8, h->cap, MV_ZB, MV_WB, 0, KB, &h->gs, 0, v);
+        run_solve_mv(wl.solveA8, h->cap, MV_TB, MV_WB, 1, KB, &h->gs, 0, v);
+      }
+      CK(cudaStreamEndCapture(h->cap, &g));
+      g_launch_count = before;
+      CK(cudaGraphInstantiate(&ex, g, 0));
+      CK(cudaGraphDestroy(g));
+      CK(cudaGraphLaunch(ex, st));
+      CK(cudaEventRecord(e0, st));
+      for (int r = 0; r < reps; ++r) CK(cudaGraphLaunch(ex, st));
+      CK(cudaEventRecord(e1, st));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      CK(cudaGraphExecDestroy(ex));
+      t.solve_ms[gi][vi] = ms / reps;
+      if (ms / reps < best) {
+        best = ms / reps;
+        best_g = groups[gi];
+        best_v = v;
+      }
+    }
+  }
+  CK(cudaEventDestroy(e0));
+  CK(cudaEventDestroy(e1));
+  // adopt the choice: regroup every wave's solves, drop the captured solve graphs
+  h->ngroup = best_g;
+  h->solve_variant = best_v;
+  for (WaveSched& w : h->waves) {
+    build_wave_solve_schedules(h, w);
+    TRY(upload_wave_solves(h, w));
+  }
+  for (auto it = h->graphs.begin(); it != h->graphs.end();) {
+    if ((it->first >> 60) == 1) {
+      if (it->second.first) cudaGraphExecDestroy(it->second.first);
+      it = h->graphs.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  h->cur = 0;
+  h->base_act.assign(h->N, 1);
+  TRY(set_active(h, h->base_act));
+  CK(cudaStreamSynchronize(st));
+  t.streams = best_g;
+  t.solve_kernel = best_v;
+  t.best_ms = best;
+  if (out) *out = t;
   return MSGFEM_OK;
 }
 

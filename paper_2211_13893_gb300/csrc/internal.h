@@ -176,7 +176,9 @@ struct msgfem {
   StreamSet gs;                      // streams of independent schedule groups
   cudaStream_t cap = nullptr;        // private stream on which schedules are captured as graphs
   std::map<uint64_t, std::pair<cudaGraphExec_t, long long>> graphs;   // key -> (graph, kernel nodes)
-  int ngroup = NGROUP;               // groups in use (msgfem_options.streams)
+  int ngroup = NGROUP;               // groups in use (msgfem_options.streams, or the autotuner's choice)
+  int ngroup_created = NGROUP;       // streams created at set-up
+  int solve_variant = 0;             // kernel of the KB-wide block solves (SOLVE_*)
   int N = 0;
   int S = 1;                         // instances of the mesh batched in this handle
   int N0 = 0;                        // subdomains per instance (N = S N0)
@@ -252,6 +254,7 @@ msgfem_status cuda_fail(msgfem* h, cudaError_t e, const char* what, const char* 
 msgfem_status build_problem(msgfem* h);
 void build_factor_schedule(msgfem* h);
 void build_solve_schedules(msgfem* h);
+void build_wave_solve_schedules(msgfem* h, WaveSched& w);
 void build_coarse_schedules(msgfem* h);
 
 // launchers
@@ -260,9 +263,10 @@ void prepare_tile_kernels();
 template <typename T>
 void run_schedule(const ScheduleT<T>& s, cudaStream_t st, const StreamSet* gs = nullptr);
 // solve steps; scatter_add adds the result into the destination multivector
+enum { SOLVE_DEFAULT = 0, SOLVE_ASYNC_RING = 1, SOLVE_STREAM = 2, SOLVE_STREAM_CL2 = 3 };
 template <typename T>
 void run_solve_mv(const SolveScheduleT<T>& s, cudaStream_t st, int src, int dst, int gather_neg, int width = PST,
-                  const StreamSet* gs = nullptr, int scatter_add = 0);
+                  const StreamSet* gs = nullptr, int scatter_add = 0, int variant = SOLVE_DEFAULT);
 void launch_element_stiffness(msgfem* h);
 // node coordinates of node (i, j, k): given, or those of the box (setup.cpp)
 void node_xyz(const msgfem* h, int i, int j, int k, double X[3]);

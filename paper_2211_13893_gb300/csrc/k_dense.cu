@@ -807,6 +807,10 @@ void prepare_tile_kernels() {
   cudaFuncSetAttribute(k_tile_task_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
   cudaFuncSetAttribute(k_solve_stream<double, SOLVE_CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
   cudaFuncSetAttribute(k_solve_stream<float, SOLVE_CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
+  cudaFuncSetAttribute(k_solve_stream<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
+  cudaFuncSetAttribute(k_solve_stream<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
+  cudaFuncSetAttribute(k_solve_stream<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
+  cudaFuncSetAttribute(k_solve_stream<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
   cudaFuncSetAttribute(k_solve_async, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
   done = true;
 }
@@ -843,54 +847,77 @@ void launch_pdl(void (*kernel)(KArgs...), int grid, size_t smem, cudaStream_t st
   cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+// Cluster launch of the streaming solve: CL CTAs (one thread-block cluster) per
+// 64-row task, splitting its inner dimension.
+template <typename T, int CL>
+static void launch_stream_cluster(const SolveScheduleT<T>& s, const SchedStep& step, size_t smem, cudaStream_t stream,
+                                  int src, int dst, int gather_neg, int scatter_add) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(step.count * CL);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_solve_stream<T, CL>, (const SolveTaskT<T>*)(s.d_tasks + step.first),
+                     (const SubDev*)g_subs, (const int*)g_active, src, dst, gather_neg, scatter_add);
+}
+
+// variant (KB-wide solves): SOLVE_DEFAULT = the build's choice (FP32: the
+// cp.async ring when every inner dimension is a multiple of 64; FP64: register
+// streaming), SOLVE_ASYNC_RING, SOLVE_STREAM (register streaming, one CTA per
+// 64-row task), SOLVE_STREAM_CL2 (two-CTA cluster per task).  A variant that
+// does not apply (ring for FP64 or ragged inner dimensions, shared memory over
+// the limit) falls back to the default.
 template <typename T>
 void run_solve_mv(const SolveScheduleT<T>& s, cudaStream_t st, int src, int dst, int gather_neg, int width,
-                  const StreamSet* gs, int scatter_add) {
+                  const StreamSet* gs, int scatter_add, int variant) {
   prepare_tile_kernels();
   const size_t smem = solve_stream_smem<T>(s.kmax, SOLVE_CL);
   const bool stream_ok = smem <= SOLVE_SMEM_MAX;
+  const size_t smem2 = solve_stream_smem<T>(s.kmax, 2);
   // FP32: asynchronous-copy pipeline when every task's inner dimension is a multiple of 64
   const size_t asmem = solve_async_smem(s.kmax);
-  const bool async_ok = std::is_same<T, float>::value && s.k64 && asmem <= SOLVE_SMEM_MAX && SOLVE_ASYNC;
+  const bool async_ok = std::is_same<T, float>::value && s.k64 && asmem <= SOLVE_SMEM_MAX;
+  int v = variant;
+  if (v == SOLVE_ASYNC_RING && !async_ok) v = SOLVE_DEFAULT;
+  if (v == SOLVE_STREAM && !stream_ok) v = SOLVE_DEFAULT;
+  if (v == SOLVE_STREAM_CL2 && smem2 > SOLVE_SMEM_MAX) v = SOLVE_DEFAULT;
+  if (v == SOLVE_DEFAULT) v = (async_ok && SOLVE_ASYNC) ? SOLVE_ASYNC_RING : (SOLVE_CL == 2 ? SOLVE_STREAM_CL2 : SOLVE_STREAM);
   run_groups(s, st, gs, [&](const SchedStep& step, cudaStream_t stream) {
+    if (width != KB) {
+      k_solve_step<T, PST><<<step.count, 256, 0, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
+                                                           gather_neg, scatter_add);
+      return;
+    }
     if constexpr (std::is_same<T, float>::value) {
-      if (width == KB && async_ok) {
+      if (v == SOLVE_ASYNC_RING) {
         launch_pdl(k_solve_async, step.count, asmem, stream, s.d_tasks + step.first, g_subs, g_active, src, dst,
                    gather_neg, scatter_add);
         return;
       }
     }
-    if (width == KB && stream_ok && SOLVE_CL == 1) {
+    if (v == SOLVE_STREAM && stream_ok) {
       // (programmatic launch measured slower for the FP64 steps: 707 vs 690 ms per C2 step)
       k_solve_stream<T, 1><<<step.count, 256, smem, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
                                                               gather_neg, scatter_add);
-    } else if (width == KB && stream_ok) {
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(step.count * SOLVE_CL);
-      cfg.blockDim = dim3(256);
-      cfg.dynamicSmemBytes = smem;
-      cfg.stream = stream;
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = SOLVE_CL;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      cudaLaunchKernelEx(&cfg, k_solve_stream<T, SOLVE_CL>, (const SolveTaskT<T>*)(s.d_tasks + step.first),
-                         (const SubDev*)g_subs, (const int*)g_active, src, dst, gather_neg, scatter_add);
-    } else if (width == KB)
+    } else if (v == SOLVE_STREAM_CL2 && smem2 <= SOLVE_SMEM_MAX) {
+      launch_stream_cluster<T, 2>(s, step, smem2, stream, src, dst, gather_neg, scatter_add);
+    } else {
       k_solve_step<T, KB><<<step.count, 256, 0, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
                                                           gather_neg, scatter_add);
-    else
-      k_solve_step<T, PST><<<step.count, 256, 0, stream>>>(s.d_tasks + step.first, g_subs, g_active, src, dst,
-                                                           gather_neg, scatter_add);
+    }
   });
 }
 
 template void run_schedule<double>(const ScheduleT<double>&, cudaStream_t, const StreamSet*);
 template void run_schedule<float>(const ScheduleT<float>&, cudaStream_t, const StreamSet*);
 template void run_solve_mv<double>(const SolveScheduleT<double>&, cudaStream_t, int, int, int, int,
-                                   const StreamSet*, int);
+                                   const StreamSet*, int, int);
 template void run_solve_mv<float>(const SolveScheduleT<float>&, cudaStream_t, int, int, int, int,
-                                  const StreamSet*, int);
+                                  const StreamSet*, int, int);

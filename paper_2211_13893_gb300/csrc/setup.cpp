@@ -538,13 +538,15 @@ void build_solves_t(msgfem* h, const std::vector<int>& members, SolveScheduleT<T
 }  // namespace
 
 // Subdomains are dealt into the stream groups as well (per wave).
+void build_wave_solve_schedules(msgfem* h, WaveSched& w) {
+  if (h->mixed)
+    build_solves_t<float>(h, w.members, w.solveKf, w.solveAf, w.solveK8f, w.solveA8f, true);
+  else
+    build_solves_t<double>(h, w.members, w.solveK, w.solveA, w.solveK8, w.solveA8, false);
+}
+
 void build_solve_schedules(msgfem* h) {
-  for (WaveSched& w : h->waves) {
-    if (h->mixed)
-      build_solves_t<float>(h, w.members, w.solveKf, w.solveAf, w.solveK8f, w.solveA8f, true);
-    else
-      build_solves_t<double>(h, w.members, w.solveK, w.solveA, w.solveK8, w.solveA8, false);
-  }
+  for (WaveSched& w : h->waves) build_wave_solve_schedules(h, w);
 }
 
 // Coarse matrix: one dense block of size NcPad, factorised by the same tile

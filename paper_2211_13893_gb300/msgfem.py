@@ -16,6 +16,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTSPD", 5: "ENOCO
 EXPORTS = ("msgfem_setup", "msgfem_update_angles", "msgfem_local_spaces", "msgfem_coarse_assemble",
            "msgfem_solve", "msgfem_get_basis", "msgfem_get_info", "msgfem_num_subdomains",
            "msgfem_get_profile", "msgfem_reset_profile", "msgfem_energy_error_noalloc", "msgfem_last_error",
+           "msgfem_autotune",
            "msgfem_destroy",
            # include/msgfem_warm.h
            "msgfem_net_create", "msgfem_net_param_count", "msgfem_net_get_params", "msgfem_net_set_params",
@@ -45,7 +46,13 @@ class Partition(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("block", C.c_int), ("max_iter", C.c_int), ("tol", C.c_double),
                 ("seed", C.c_ulonglong), ("stream", C.c_void_p), ("profile", C.c_int), ("solver", C.c_int),
-                ("streams", C.c_int), ("refine", C.c_int), ("instances", C.c_int), ("wave_mb", C.c_double)]
+                ("streams", C.c_int), ("refine", C.c_int), ("instances", C.c_int), ("solve_kernel", C.c_int),
+                ("wave_mb", C.c_double)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("streams", C.c_int), ("solve_kernel", C.c_int), ("best_ms", C.c_double),
+                ("solve_ms", (C.c_double * 3) * 3)]
 
 
 class Profile(C.Structure):
@@ -84,6 +91,7 @@ def load_library(path=LIB_PATH):
                                        C.POINTER(C.c_int)]),
         "msgfem_get_info": (C.c_int, [h, C.c_int, C.POINTER(SubInfo)]),
         "msgfem_get_profile": (C.c_int, [h, C.POINTER(Profile)]),
+        "msgfem_autotune": (C.c_int, [h, C.c_int, C.POINTER(Tuning)]),
         "msgfem_energy_error_noalloc": (C.c_int, [h, C.c_void_p, C.c_void_p, C.c_void_p]),
         "msgfem_reset_profile": (C.c_int, [h]),
         "msgfem_num_subdomains": (C.c_int, [h]),
@@ -129,7 +137,7 @@ class MSGFEM:
 
     def __init__(self, nx, ny, nz, hx, hy, hz, traction, E9, elem_angles, sx, sy, overlap, oversampling,
                  block=0, max_iter=0, tol=0.0, seed=0, stream=None, precision=0, profile=0, solver=0, streams=0, refine=0,
-                 instances=0, xyz=None, frames=None, boxes=None, wave_mb=0.0):
+                 instances=0, xyz=None, frames=None, boxes=None, wave_mb=0.0, solve_kernel=0):
         self.lib = load_library()
         self.h = C.c_void_p()
         self._E9 = np.ascontiguousarray(E9, dtype=np.float64)
@@ -146,7 +154,7 @@ class MSGFEM:
         nb = 0 if self._boxes is None else len(self._boxes) // 4
         part = Partition(sx, sy, nb, _ptr(self._boxes))
         opt = Options(precision, block, max_iter, tol, seed, stream, profile, solver, streams, refine, instances,
-                      wave_mb)
+                      solve_kernel, wave_mb)
         self.instances = max(1, instances)
         st = self.lib.msgfem_setup(C.byref(self.mesh), C.byref(plies), C.byref(part), overlap, oversampling,
                                    C.byref(opt), C.byref(self.h))
@@ -207,6 +215,14 @@ class MSGFEM:
         out = np.zeros(rows.value * cols.value)
         self._check(self.lib.msgfem_get_basis(self.h, j, out.ctypes.data, C.byref(rows), C.byref(cols), box))
         return out.reshape(cols.value, rows.value).T, tuple(box)
+
+    def autotune(self, reps=0):
+        """Time the block-solve launch shapes on this handle and adopt the fastest
+        (include/msgfem.h msgfem_autotune); returns the choice and the timings."""
+        t = Tuning()
+        self._check(self.lib.msgfem_autotune(self.h, reps, C.byref(t)))
+        return {"streams": t.streams, "solve_kernel": t.solve_kernel, "best_ms": t.best_ms,
+                "solve_ms": [[t.solve_ms[g][v] for v in range(3)] for g in range(3)]}
 
     def info(self, j):
         inf = SubInfo()

@@ -1,0 +1,65 @@
+"""Write tests/golden/c4_sample_eigs.json: oracle eigenvalues of sampled
+subdomains of the full c4 C-section spar (250 x 110 x 32 curved hexahedra,
+2,758,239 DoF, 256 subdomains).
+
+Calls only oracle/ (and the seeded generators of workloads/): the curved mesh
+and ply frames, the partition of unity of all 256 subdomains (Sec. 4.2), and
+for each sampled subdomain the A-harmonic local eigenproblem (Eq.
+AHarmonicGeneralizeEigenProblem): dense-reduced for the small oversampling
+domains, the paper's own design (ARPACK shift-invert on the saddle pencil of
+Eq. algebraicAharmonic) for the large ones (the two agree to 1e-9, pinned in
+tests/test_oracle_gevp.py).  The samples cover the smallest domain (clamped
+end, flange tip), a clamped corner domain, a floating domain over a curved
+corner and a floating domain on the loaded end.
+
+    python tests/golden/make_c4_golden.py
+
+Takes a few minutes on 8 cores.
+"""
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "c4_sample_eigs.json")
+SAMPLES = {0: "dense", 18: "dense", 83: "arpack", 248: "arpack"}
+
+
+def main():
+    from oracle.arpack import local_eigs_arpack
+    from oracle.assemble import make_cache
+    from oracle.local import local_eigs_dense, local_problem
+    from oracle.mesh import make_mesh
+    from oracle.partition import partition_of_unity, subdomains
+    from workloads import element_angles, get_config
+    cfg = get_config("c4")
+    t0 = time.time()
+    m = make_mesh(cfg)
+    ang = element_angles(cfg)
+    subs = subdomains(cfg)
+    mus = partition_of_unity(m, subs, cfg.overlap)
+    b = m.compression_load(cfg.traction)
+    cache = make_cache(m, cfg.material)
+    print(f"mesh, partition of unity and load: {time.time() - t0:.1f} s", flush=True)
+    out = {"config": "c4", "n_loc": cfg.n_loc, "samples": {}}
+    for j, how in SAMPLES.items():
+        t1 = time.time()
+        lp = local_problem(m, ang, cfg.material, subs[j], mus[j], b, cache)
+        lam, _ = (local_eigs_dense if how == "dense" else local_eigs_arpack)(lp, cfg.n_loc)
+        out["samples"][str(j)] = {"solver": how, "n_star_dof": int(lp.n_star), "n1": int(len(lp.I1)),
+                                  "n2": int(len(lp.I2)), "n3": int(len(lp.I3)), "star": list(subs[j].star),
+                                  "lambda": [float(x) for x in lam]}
+        print(f"subdomain {j}: {lp.n_star} DoF, n2 {len(lp.I2)}, {how}, {time.time() - t1:.1f} s, "
+              f"lambda[:4] {np.array(lam[:4])}", flush=True)
+    with open(OUT, "w") as f:
+        json.dump(out, f, indent=1)
+    print(f"wrote {OUT} in {time.time() - t0:.1f} s")
+
+
+if __name__ == "__main__":
+    main()

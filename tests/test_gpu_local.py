@@ -37,12 +37,12 @@ def gap_sizes(lam_ext, n):
     return out
 
 
-def run_case(name, seed=7, tol_lam=1e-8, tol_angle=1e-5, solver=0, precision=0):
+def run_case(name, seed=7, tol_lam=1e-8, tol_angle=1e-5, solver=0, precision=0, **kw):
     cfg = get_config(name)
     ang = element_angles(cfg)
     ref = run_msgfem(cfg, angles=ang, n_loc=cfg.n_loc + 1)        # one more to locate the gap at n_loc
     ref_n = run_msgfem(cfg, angles=ang, uh=None)
-    m = _msgfem().from_config(cfg, ang, seed=seed, solver=solver, precision=precision)
+    m = _msgfem().from_config(cfg, ang, seed=seed, solver=solver, precision=precision, **kw)
     lam = m.local_spaces(cfg.n_loc)
     nc = m.coarse_assemble()
     _, err = m.solve(u_ref=ref_n.uh)

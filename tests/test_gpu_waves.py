@@ -1,4 +1,5 @@
-"""Memory-bounded waves and explicit subdomain boxes.
+"""Memory-bounded waves, explicit subdomain boxes, the block-solve kernels and
+the autotuner.
 
 A handle whose layer-block storage is capped (msgfem_options.wave_mb) runs the
 local stage in waves of subdomains that share one factor pool; every
@@ -65,3 +66,27 @@ def test_boxes_that_do_not_tile_are_rejected():
     with pytest.raises(MsgfemError) as e:
         MSGFEM.from_config(cfg, element_angles(cfg), boxes=boxes)
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("name,precision,kernel", [("t4", 0, 2), ("t4", 0, 3), ("s2", 1, 1), ("s2", 1, 2),
+                                                   ("s2", 1, 3)])
+def test_solve_kernels_parity(name, precision, kernel):
+    """Every block-solve kernel the autotuner may choose gives oracle parity."""
+    from test_gpu_local import run_case
+    tol = (1e-8, 1e-5) if precision == 0 else (1e-5, 1e-4)
+    run_case(name, precision=precision, tol_lam=tol[0], tol_angle=tol[1], solve_kernel=kernel)
+
+
+def test_autotune_keeps_results_and_adopts_choice():
+    from paper_2211_13893_gb300 import MSGFEM
+    cfg = get_config("s2")
+    ang = element_angles(cfg)
+    m = MSGFEM.from_config(cfg, ang, seed=7, precision=1)
+    la = m.local_spaces(cfg.n_loc)
+    t = m.autotune()
+    assert t["streams"] in (4, 8, 16) and t["solve_kernel"] in (1, 2, 3) and t["best_ms"] > 0
+    assert min(x for row in t["solve_ms"] for x in row if x > 0) == pytest.approx(t["best_ms"])
+    lb = m.local_spaces(cfg.n_loc)
+    m.close()
+    scale = np.abs(la).max(axis=1, keepdims=True)
+    assert (np.abs(la - lb) / scale).max() <= 1e-6

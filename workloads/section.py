@@ -194,10 +194,13 @@ def omega_star_sizes(cfg):
 SECTIONS = {
     # C-section spar of 1 m: web 200 mm, flanges 60 mm, inner radius 8 mm, 32 plies
     # of 0.25 mm; 4 mm elements along x and the straight segments, ~1 mm on the
-    # corner arcs (19 per corner); 16 x 16 boxes, graded along x (narrow at the
-    # clamped end) and narrower on the corners; overlap 1, oversampling 3.
-    "c4": SectionConfig("c4", xparts=(2, 3, 4, 6, 8, 10, 12, 14, 16, 18, 20, 22, 24, 26, 30, 35),
-                        sparts=(7, 6, 7, 6, 6, 8, 7, 8, 8, 7, 8, 6, 6, 7, 6, 7), n_loc=16),
+    # corner arcs (19 per corner): 250 x 110 x 32 elements, 2,758,239 DoF.
+    # 16 x 16 boxes, graded along x (1 element at the clamped end, ~21 in the
+    # span) and along the arc (short boxes at the flange tips, three per corner,
+    # six on the web); overlap 1, oversampling 3: oversampling domains of
+    # 4,455 to 41,580 DoF (mean 29,570).
+    "c4": SectionConfig("c4", xparts=(1, 2, 4, 8, 12, 20, 20, 20, 20, 21, 21, 21, 21, 21, 21, 17),
+                        sparts=(5, 8, 7, 6, 6, 8, 7, 8, 8, 7, 8, 6, 6, 7, 8, 5), n_loc=16),
     # test sections: curved corners, clamped / floating / interior subdomains
     "s1": SectionConfig("s1", length=24.0, web=12.0, flange=8.0, radius=2.0, n_plies=4, t=0.5,
                         h_len=3.0, h_arc=2.0, h_corner=1.0, xparts=(3, 5), sparts=(5, 5, 5, 5),
