@@ -378,6 +378,12 @@ def run_c4(args, dev, stream, flush, rank, world):
         m.solve(u_out=u)
 
     step()                                   # warm-up: graph capture, first launches
+    tuning = None
+    if not args.no_autotune:
+        t1 = time.perf_counter()
+        tuning = m.autotune()                # launch shapes of the block solves on this batch
+        tuning["seconds"] = time.perf_counter() - t1
+        step()                               # re-capture the solve graphs with the chosen shapes
     torch.cuda.synchronize()
     m.profile(reset=True)
     ms = []
@@ -429,7 +435,7 @@ def run_c4(args, dev, stream, flush, rank, world):
                         "frac": solve_gbs / hbm, "peak_note": hbm_note,
                         "kernel": "k_solve_async (FP32 block solves, 8 right-hand sides)",
                         "time_share": prof["solve_ms"] / total if total else None},
-           "sampled_parity": sample}
+           "sampled_parity": sample, "autotune": tuning}
     m.close()
     return out
 
@@ -608,6 +614,7 @@ def main():
     ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start (c5) run")
     ap.add_argument("--no-c4", action="store_true", help="skip the batched C-section (c4) run")
     ap.add_argument("--c4-steps", type=int, default=1, help="timed steps of the c4 run")
+    ap.add_argument("--no-autotune", action="store_true", help="c4 run with the default block-solve launches")
     ap.add_argument("--streams", type=int, default=0, help="stream groups of the library (0 = its default)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
