@@ -591,12 +591,42 @@ def run_warm_c5(args, dev, n_train=384, n_test=128, batch=128):
         res[kind] = {"iterations_mean": float(np.mean(iters)), "start_angle_rad_mean": float(np.mean(angs)),
                      "solves_per_s": m.N / (ms[-1] / 1000.0), "ms_per_batch": ms[-1]}
     ws.apply(None)
+    # the same test batch in mixed precision (FP32 factors and solves, FP64
+    # refinement): cold start vs the trained network's start blocks, and the
+    # eigenvalue difference to the FP64 run
+    lam64 = m.local_spaces(cfg.n_loc)
+    dth_dev = torch.tensor((base[None] + fields[n_train:n_train + S]).reshape(-1), dtype=torch.float64, device=dev)
+    mm = MSGFEM.from_config(cfg, dth_dev, seed=5, tol=1e-6, stream=stream.cuda_stream, instances=S, precision=1)
+    learned = ws.predict(ws.features(dth))
+    mixed = {}
+    lam32 = None
+    for kind in ("cold", "learned"):
+        ms = []
+        for rep in range(2):
+            for j in range(mm.N):
+                _, nw = ws.size(j)
+                mm.set_start_block(j, learned[j] if kind == "learned" else None, 8, nw)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lam32 = mm.local_spaces(cfg.n_loc)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        iters = [mm.info(j)["iterations"] for j in range(mm.N)]
+        mixed[kind] = {"iterations_mean": float(np.mean(iters)), "solves_per_s": mm.N / (ms[-1] / 1000.0),
+                       "ms_per_batch": ms[-1]}
+    mm.close()
     m.close()
+    top = np.abs(lam64).max(axis=1, keepdims=True)
+    mixed["eig_rel_diff_vs_fp64"] = float((np.abs(lam32 - lam64) / top).max())
+    mixed["speedup_learned_mixed_vs_cold_fp64"] = mixed["learned"]["solves_per_s"] / res["cold"]["solves_per_s"]
     out = {"workload": f"c1 beam 24x4x12 + seeded 3-D wrinkle field (sd 3 deg, l = 10 mm), 2x1 subdomains, "
                        f"n_loc=8, FP64, tol 1e-6; {S} beams batched per local stage",
            "train_samples": n_train, "test_samples": n_test, "data_gen_s": t_data, "train_ms": train_ms,
            "final_losses": losses}
     out.update(res)
+    out["mixed"] = mixed
     return out
 
 
