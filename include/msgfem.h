@@ -187,6 +187,8 @@ typedef struct {
   int iterations;       /* eigensolver iterations used */
   int basis_size;       /* coarse basis functions contributed (n_loc [+1]) */
   double residual;      /* max relative eigen-residual over the n_loc pairs */
+  int threshold_reached;   /* msgfem_coarse_assemble_threshold: 0 if every one of the n_loc
+                              eigenvalues was below 1 / t (the basis may need a larger n_loc) */
 } msgfem_subinfo;
 
 /* Partition, DoF classes (Sec. 4.3) and partition of unity (Sec. 4.2) on the
@@ -215,6 +217,15 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out);
  * (Sec. 4.3-4.4), coarse matrix A^H_{ij} = V_i^T A V_j and load b^H
  * (Eq. GFEM_coarse_approximation).  *coarse_dim_out receives dim V_H. */
 msgfem_status msgfem_coarse_assemble(msgfem_h h, int* coarse_dim_out);
+
+/* msgfem_coarse_assemble with local basis sizes chosen by an eigenvalue
+ * threshold (Sec. 5.5, Sec. 5.6; the error bound of Thm. error_bound is driven
+ * by 1 / lambda_{j, m_j + 1}): subdomain j keeps its eigenvectors with
+ * 1 / lambda > t (rigid modes always), m_j <= n_loc of the last local stage;
+ * t = 0 keeps all n_loc (msgfem_coarse_assemble).  When all n_loc eigenvalues
+ * of a subdomain are below 1 / t its msgfem_subinfo.threshold_reached is 0.
+ * Errors: EINVAL (t < 0), ESTATE, ENOTSPD. */
+msgfem_status msgfem_coarse_assemble_threshold(msgfem_h h, double t, int* coarse_dim_out);
 
 /* Coarse solve A^H c = b^H (FP64 Cholesky) and u^G = sum_j V_j c_j.
  * u_out receives u^G on all 3 (nx+1)(ny+1)(nz+1) DoFs (may be NULL).  If

@@ -83,7 +83,11 @@ class MSGFEMResult:
 
 
 def run_msgfem(cfg, angles=None, n_loc=None, variant="ii", solver="dense", uh=None,
-               keep_problems=False):
+               keep_problems=False, threshold=None):
+    """MS-GFEM with n_loc eigenvectors per subdomain, or, with ``threshold`` t,
+    the eigenvectors with 1 / lambda > t among the n_loc computed (Sec. 5.5,
+    Sec. 5.6: the local basis sizes m_j follow from a threshold on the
+    reciprocal eigenvalues)."""
     mesh = make_mesh(cfg)
     E = cfg.material
     if angles is None:
@@ -105,7 +109,10 @@ def run_msgfem(cfg, angles=None, n_loc=None, variant="ii", solver="dense", uh=No
         res.phi.append(phi)
         if keep_problems:
             res.problems.append(lp)
-        weighted = [lp.mu * phi[:, k] for k in range(phi.shape[1])]
+        m_j = phi.shape[1]
+        if threshold is not None:
+            m_j = int(np.sum(lam * threshold < 1.0))
+        weighted = [lp.mu * phi[:, k] for k in range(m_j)]
         psi_w = lp.mu * psi
         if variant == "ii":
             vecs = weighted + ([psi_w] if np.any(psi_w != 0.0) else [])

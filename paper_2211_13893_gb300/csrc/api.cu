@@ -1037,12 +1037,13 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
     const int nw = n_loc - (h->sub[j].floating ? 6 : 0);
     for (int c = 0; c < nw; ++c) h->resid_max[j] = std::max(h->resid_max[j], res[c]);
   }
+  std::vector<double>& lam = h->lam_host;
+  lam.assign((size_t)h->N * n_loc, 0.0);
+  for (int j = 0; j < h->N; ++j) {
+    const int nr = h->sub[j].floating ? std::min(6, n_loc) : 0;
+    for (int c = 0; c < n_loc; ++c) lam[(size_t)j * n_loc + c] = c < nr ? 0.0 : theta[(size_t)j * PST + c - nr];
+  }
   if (lambda_out) {
-    std::vector<double> lam((size_t)h->N * n_loc);
-    for (int j = 0; j < h->N; ++j) {
-      const int nr = h->sub[j].floating ? std::min(6, n_loc) : 0;
-      for (int c = 0; c < n_loc; ++c) lam[(size_t)j * n_loc + c] = c < nr ? 0.0 : theta[(size_t)j * PST + c - nr];
-    }
     if (is_device_ptr(lambda_out)) {
       CK(cudaMemcpy(lambda_out, lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice));
     } else {
@@ -1064,8 +1065,16 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
 }
 
 msgfem_status msgfem_coarse_assemble(msgfem_h h, int* coarse_dim_out) {
+  return msgfem_coarse_assemble_threshold(h, 0.0, coarse_dim_out);
+}
+
+msgfem_status msgfem_coarse_assemble_threshold(msgfem_h h, double t, int* coarse_dim_out) {
   if (!h) return MSGFEM_EINVAL;
   if (h->stage < 2) return MSGFEM_ESTATE;
+  if (!(t >= 0.0)) {
+    h->err = "threshold must be >= 0";
+    return MSGFEM_EINVAL;
+  }
   if (h->S > 1) {
     h->err = "a handle with batched instances runs the local stage only";
     return MSGFEM_EINVAL;
@@ -1075,18 +1084,30 @@ msgfem_status msgfem_coarse_assemble(msgfem_h h, int* coarse_dim_out) {
   set_dense_context(h->d_flags, h->d_notspd, h->d_sub);
   TRY(set_active(h, std::vector<int>(h->N, 1)));
   const int sp_c = span_begin(h, TAG_COARSE);
-  // basis [phi_1..phi_nloc, psi] in CB; psi only on loaded subdomains
+  // local basis sizes m_j (Sec. 5.5): with a threshold t > 0 the eigenvectors
+  // with 1 / lambda > t, i.e. lambda < 1 / t, of the n_loc computed (rigid
+  // modes always); t = 0 keeps all n_loc
+  h->m_sel.assign(h->N, n_loc);
+  h->thr_reached.assign(h->N, 1);
+  if (t > 0.0)
+    for (int j = 0; j < h->N; ++j) {
+      int m = 0;
+      while (m < n_loc && h->lam_host[(size_t)j * n_loc + m] * t < 1.0) ++m;
+      h->m_sel[j] = m;
+      h->thr_reached[j] = m < n_loc ? 1 : 0;
+    }
+  // basis [phi_1..phi_mj, psi] in CB; psi only on loaded subdomains
   std::vector<int> ncols(h->N);
   for (int j = 0; j < h->N; ++j) {
     const SubDev& s = h->sub[j];
-    ncols[j] = n_loc + (s.loaded ? 1 : 0);
+    ncols[j] = h->m_sel[j] + (s.loaded ? 1 : 0);
     CK(cudaMemcpyAsync(s.CB, s.EV, (size_t)s.nfull * PST * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
   CK(cudaMemcpyAsync(h->d_ncols, ncols.data(), h->N * sizeof(int), cudaMemcpyHostToDevice, st));
   for (int j = 0; j < h->N; ++j)
     if (h->sub[j].loaded)
-      CK(cudaMemcpy2DAsync(h->sub[j].CB + n_loc, PST * sizeof(double), h->sub[j].psi, sizeof(double), sizeof(double),
-                           h->sub[j].nfull, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpy2DAsync(h->sub[j].CB + h->m_sel[j], PST * sizeof(double), h->sub[j].psi, sizeof(double),
+                           sizeof(double), h->sub[j].nfull, cudaMemcpyDeviceToDevice, st));
   // Gram-Schmidt in the B inner product (CholeskyQR, twice); psi dropped if dependent
   for (int pass = 0; pass < 2; ++pass) {
     timed_stencil_apply(h, MV_CB, MV_CW, 3, 1.0);
@@ -1214,6 +1235,7 @@ msgfem_status msgfem_get_info(msgfem_h h, int j, msgfem_subinfo* info) {
   info->iterations = j < (int)h->iters.size() ? h->iters[j] : 0;
   info->basis_size = j < (int)h->basis_m.size() ? h->basis_m[j] : 0;
   info->residual = j < (int)h->resid_max.size() ? h->resid_max[j] : 0.0;
+  info->threshold_reached = j < (int)h->thr_reached.size() ? h->thr_reached[j] : 1;
   return MSGFEM_OK;
 }
 

@@ -187,6 +187,9 @@ struct msgfem {
   std::vector<SubDev> sub;
   std::vector<HostSub> hsub;
   std::vector<int> n1, n2, n3, iters, basis_m, m_final;
+  std::vector<double> lam_host;      // [N][n_loc] eigenvalues of the last local stage (rigid zeros first)
+  std::vector<int> m_sel;            // [N] eigenvectors in the coarse basis (threshold selection)
+  std::vector<int> thr_reached;      // [N] 0 if all n_loc eigenvalues were below the threshold
   std::vector<int> act_host;         // host copy of the active flags last uploaded
   std::vector<int> base_act;         // members of the wave being processed (all ones: one wave)
   std::vector<double> resid_max;

@@ -16,7 +16,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTSPD", 5: "ENOCO
 EXPORTS = ("msgfem_setup", "msgfem_update_angles", "msgfem_local_spaces", "msgfem_coarse_assemble",
            "msgfem_solve", "msgfem_get_basis", "msgfem_get_info", "msgfem_num_subdomains",
            "msgfem_get_profile", "msgfem_reset_profile", "msgfem_energy_error_noalloc", "msgfem_last_error",
-           "msgfem_autotune",
+           "msgfem_autotune", "msgfem_coarse_assemble_threshold",
            "msgfem_destroy",
            # include/msgfem_warm.h
            "msgfem_net_create", "msgfem_net_param_count", "msgfem_net_get_params", "msgfem_net_set_params",
@@ -65,7 +65,8 @@ class Profile(C.Structure):
 
 class SubInfo(C.Structure):
     _fields_ = [("n_star_dof", C.c_int), ("n1", C.c_int), ("n2", C.c_int), ("n3", C.c_int), ("floating", C.c_int),
-                ("iterations", C.c_int), ("basis_size", C.c_int), ("residual", C.c_double)]
+                ("iterations", C.c_int), ("basis_size", C.c_int), ("residual", C.c_double),
+                ("threshold_reached", C.c_int)]
 
 
 _lib = None
@@ -86,6 +87,7 @@ def load_library(path=LIB_PATH):
         "msgfem_update_angles": (C.c_int, [h, C.c_void_p]),
         "msgfem_local_spaces": (C.c_int, [h, C.c_int, C.c_void_p]),
         "msgfem_coarse_assemble": (C.c_int, [h, C.POINTER(C.c_int)]),
+        "msgfem_coarse_assemble_threshold": (C.c_int, [h, C.c_double, C.POINTER(C.c_int)]),
         "msgfem_solve": (C.c_int, [h, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
         "msgfem_get_basis": (C.c_int, [h, C.c_int, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                        C.POINTER(C.c_int)]),
@@ -195,9 +197,14 @@ class MSGFEM:
         self._check(self.lib.msgfem_local_spaces(self.h, n_loc, _ptr(out)), allow=(5,) if allow_noconv else ())
         return out
 
-    def coarse_assemble(self):
+    def coarse_assemble(self, threshold=None):
+        """Coarse Galerkin assembly; with a threshold t, subdomain j keeps the
+        eigenvectors with 1 / lambda > t (msgfem_coarse_assemble_threshold)."""
         nc = C.c_int()
-        self._check(self.lib.msgfem_coarse_assemble(self.h, C.byref(nc)))
+        if threshold is None:
+            self._check(self.lib.msgfem_coarse_assemble(self.h, C.byref(nc)))
+        else:
+            self._check(self.lib.msgfem_coarse_assemble_threshold(self.h, float(threshold), C.byref(nc)))
         return nc.value
 
     def solve(self, u_ref=None, u_out=None):

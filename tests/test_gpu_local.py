@@ -103,3 +103,21 @@ def test_deterministic_across_runs():
     ub, _ = b.solve()
     b.close()
     assert np.array_equal(la, lb) and np.array_equal(ua, ub)
+
+
+def test_threshold_selection_matches_oracle():
+    """Local basis sizes from the eigenvalue threshold t = 0.05 (keep lambda < 20):
+    6, 10 and 8 eigenvectors on the three subdomain pairs of t2; the coarse
+    dimension and the energy error match the oracle's threshold run."""
+    cfg = get_config("t2")
+    ang = element_angles(cfg)
+    ref = run_msgfem(cfg, angles=ang, threshold=0.05)
+    m = _msgfem().from_config(cfg, ang, seed=7)
+    m.local_spaces(cfg.n_loc)
+    nc = m.coarse_assemble(threshold=0.05)
+    _, err = m.solve(u_ref=ref.uh)
+    reached = [m.info(j)["threshold_reached"] for j in range(m.N)]
+    m.close()
+    assert nc == sum(ref.basis_counts)
+    assert reached == [1, 1, 0, 0, 1, 1]
+    assert abs(err - ref.energy_error) <= 0.01 * ref.energy_error, (err, ref.energy_error)

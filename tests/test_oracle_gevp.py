@@ -160,3 +160,23 @@ def test_pou_weighted_basis_is_a_orthonormal():
         _, phi = local_eigs_dense(lp, cfg.n_loc)
         W = lp.mu[:, None] * phi
         assert np.allclose(W.T @ (lp.A @ W), np.eye(phi.shape[1]), atol=1e-10)
+
+
+def test_threshold_selection_nested_and_exhaustive():
+    """Threshold t on 1 / lambda (Sec. 5.5): a t below every 1 / lambda keeps all
+    n_loc vectors (same result as n_loc); lowering t can only enlarge the local
+    spaces, so the energy error cannot increase; per-subdomain sizes follow the
+    eigenvalues."""
+    cfg = get_config("t2")
+    full = run_msgfem(cfg)
+    lam_all = np.concatenate(full.lam)
+    t_small = 0.5 / lam_all.max()
+    same = run_msgfem(cfg, threshold=t_small, uh=full.uh)
+    assert same.basis_counts == full.basis_counts and same.energy_error == full.energy_error
+    prev = np.inf
+    for t in (1e-1, 3e-2, 1e-2, 3e-3):
+        r = run_msgfem(cfg, threshold=t, uh=full.uh)
+        for lam, cnt, sub_full in zip(r.lam, r.basis_counts, full.basis_counts):
+            assert cnt <= sub_full
+        assert r.energy_error <= prev * (1 + 1e-12)
+        prev = r.energy_error
