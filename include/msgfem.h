@@ -135,6 +135,10 @@ typedef struct {
                            ring, FP64: register streaming), 1 = cp.async ring (FP32 only),
                            2 = register streaming, one CTA per 64-row task, 3 = two-CTA
                            cluster per task (inner dimension split); msgfem_autotune sets it */
+  int factor_schedule;  /* layer-block factorisation: 0 = right-looking (per tile column: POTRF,
+                           TRMM, update of the trailing matrix), 1 = left-looking (update of the
+                           column by all finished columns, then POTRF, TRMM); same work, fewer
+                           and longer tasks; msgfem_autotune sets it */
   double wave_mb;       /* device memory (MiB) for the layer blocks, factors and block-solve
                            buffers.  Subdomains whose storage does not fit at once are processed
                            in waves that share one pool of this size (largest first, a wave
@@ -173,6 +177,8 @@ typedef struct {
 
 /* Launch shapes chosen by msgfem_autotune and what it measured. */
 typedef struct {
+  int factor_schedule;  /* msgfem_options.factor_schedule chosen */
+  double factor_ms[2];  /* factorisation of the measured wave: right-, left-looking */
   int streams;          /* stream groups of the block-solve schedules (4, 8 or 16) */
   int solve_kernel;     /* msgfem_options.solve_kernel value chosen (1, 2 or 3) */
   double best_ms;       /* time of one 8-column K solve plus one A11 solve of the measured wave */
@@ -270,8 +276,10 @@ msgfem_status msgfem_energy_error_noalloc(msgfem_h h, const double* u, const dou
 
 /* Autotuner of the block-solve launches (not in the paper: a library
  * convenience for batches of uneven subdomains).  On the subdomains of the
- * last wave of the previous msgfem_local_spaces call (their factors are the
- * resident ones) it times `reps` replays (0 = 3) of one 8-column K solve and
+ * last wave of the previous msgfem_local_spaces call it first times the
+ * layer-block factorisation with the right- and the left-looking schedule
+ * (re-assembling the layer blocks before each run) and keeps the faster one,
+ * then times `reps` replays (0 = 3) of one 8-column K solve and
  * one A11 solve, captured as a CUDA graph, for every combination of stream
  * groups {4, 8, 16} (at most msgfem_options.streams) and solve kernel (the
  * cp.async ring in mixed precision only, register streaming, two-CTA

@@ -223,6 +223,18 @@ msgfem_status alloc_waves(msgfem* h) {
 
 // Device copies of a wave's solve task lists (the handle keeps every copy it
 // made until msgfem_destroy; the autotuner re-uploads after regrouping).
+msgfem_status upload_wave_factor(msgfem* h, WaveSched& w) {
+  if (h->mixed) {
+    TRY(dalloc(h, &w.factf.d_gemm, std::max<size_t>(w.factf.gemm.size(), 1)));
+    CK(cudaMemcpy(w.factf.d_gemm, w.factf.gemm.data(), w.factf.gemm.size() * sizeof(TileTaskT<float>),
+                  cudaMemcpyHostToDevice));
+  } else {
+    TRY(dalloc(h, &w.fact.d_gemm, std::max<size_t>(w.fact.gemm.size(), 1)));
+    CK(cudaMemcpy(w.fact.d_gemm, w.fact.gemm.data(), w.fact.gemm.size() * sizeof(GemmTask), cudaMemcpyHostToDevice));
+  }
+  return MSGFEM_OK;
+}
+
 msgfem_status upload_wave_solves(msgfem* h, WaveSched& w) {
   if (h->mixed) {
     for (SolveScheduleT<float>* ss : {&w.solveKf, &w.solveAf, &w.solveK8f, &w.solveA8f}) {
@@ -322,15 +334,7 @@ msgfem_status allocate(msgfem* h) {
   build_factor_schedule(h);
   build_solve_schedules(h);
   for (WaveSched& w : h->waves) {
-    if (h->mixed) {
-      TRY(dalloc(h, &w.factf.d_gemm, w.factf.gemm.size()));
-      CK(cudaMemcpy(w.factf.d_gemm, w.factf.gemm.data(), w.factf.gemm.size() * sizeof(TileTaskT<float>),
-                    cudaMemcpyHostToDevice));
-    } else {
-      TRY(dalloc(h, &w.fact.d_gemm, w.fact.gemm.size()));
-      CK(cudaMemcpy(w.fact.d_gemm, w.fact.gemm.data(), w.fact.gemm.size() * sizeof(GemmTask),
-                    cudaMemcpyHostToDevice));
-    }
+    TRY(upload_wave_factor(h, w));
     TRY(upload_wave_solves(h, w));
   }
   TRY(dalloc(h, &h->d_mk, h->N));
@@ -868,12 +872,19 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
   h->stream = static_cast<cudaStream_t>(h->opt.stream);
   h->ngroup = h->opt.streams > 0 ? std::min(h->opt.streams, NGROUP) : NGROUP;
   h->ngroup_created = h->ngroup;
+  h->ngroup_factor = h->ngroup;
   if (h->opt.solve_kernel < 0 || h->opt.solve_kernel > SOLVE_STREAM_CL2) {
     *out = h;
     h->err = "unknown solve_kernel";
     return MSGFEM_EINVAL;
   }
   h->solve_variant = h->opt.solve_kernel;
+  if (h->opt.factor_schedule < 0 || h->opt.factor_schedule > 1) {
+    *out = h;
+    h->err = "unknown factor_schedule";
+    return MSGFEM_EINVAL;
+  }
+  h->factor_left = h->opt.factor_schedule;
   if (h->opt.precision != MSGFEM_FP64 && h->opt.precision != MSGFEM_MIXED) {
     h->err = "unknown precision";
     return MSGFEM_EINVAL;
@@ -1254,6 +1265,38 @@ msgfem_status msgfem_autotune(msgfem_h h, int reps, msgfem_tuning* out) {
   set_dense_context(h->d_flags, h->d_notspd, h->d_sub);
   msgfem_tuning t;
   memset(&t, 0, sizeof(t));
+  cudaEvent_t f0, f1;
+  CK(cudaEventCreate(&f0));
+  CK(cudaEventCreate(&f1));
+  // factorisation schedule of the last wave: right- vs left-looking, each
+  // timed on freshly assembled layer blocks (the second of two runs)
+  int best_f = h->factor_left;
+  double best_fms = 1e300;
+  for (int fv = 0; fv < 2; ++fv) {
+    h->factor_left = fv;
+    build_wave_factor_schedule(h, wl);
+    TRY(upload_wave_factor(h, wl));
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {
+      if (h->mixed) launch_layer_blocks_f32(h);
+      else launch_layer_blocks(h);
+      CK(cudaEventRecord(f0, st));
+      if (h->mixed) run_schedule(wl.factf, st, &h->gs);
+      else run_schedule(wl.fact, st, &h->gs);
+      CK(cudaEventRecord(f1, st));
+      CK(cudaEventSynchronize(f1));
+      CK(cudaEventElapsedTime(&ms, f0, f1));
+    }
+    t.factor_ms[fv] = ms;
+    if (ms < best_fms) {
+      best_fms = ms;
+      best_f = fv;
+    }
+  }
+  CK(cudaEventDestroy(f0));
+  CK(cudaEventDestroy(f1));
+  h->factor_left = best_f;
+  t.factor_schedule = best_f;
   const int groups[3] = {4, 8, 16};
   const int variants[3] = {SOLVE_ASYNC_RING, SOLVE_STREAM, SOLVE_STREAM_CL2};
   double best = 1e300;
@@ -1304,7 +1347,12 @@ msgfem_status msgfem_autotune(msgfem_h h, int reps, msgfem_tuning* out) {
   }
   CK(cudaEventDestroy(e0));
   CK(cudaEventDestroy(e1));
-  // adopt the choice: regroup every wave's solves, drop the captured solve graphs
+  // adopt the choice: rebuild every wave's factorisation (its stream groups
+  // as chosen before) and regroup its solves, drop the captured graphs
+  for (WaveSched& w : h->waves) {
+    build_wave_factor_schedule(h, w);
+    TRY(upload_wave_factor(h, w));
+  }
   h->ngroup = best_g;
   h->solve_variant = best_v;
   for (WaveSched& w : h->waves) {
@@ -1312,7 +1360,7 @@ msgfem_status msgfem_autotune(msgfem_h h, int reps, msgfem_tuning* out) {
     TRY(upload_wave_solves(h, w));
   }
   for (auto it = h->graphs.begin(); it != h->graphs.end();) {
-    if ((it->first >> 60) == 1) {
+    if ((it->first >> 60) == 1 || (it->first >> 60) == 2) {
       if (it->second.first) cudaGraphExecDestroy(it->second.first);
       it = h->graphs.erase(it);
     } else {

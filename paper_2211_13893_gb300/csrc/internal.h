@@ -179,6 +179,8 @@ struct msgfem {
   int ngroup = NGROUP;               // groups in use (msgfem_options.streams, or the autotuner's choice)
   int ngroup_created = NGROUP;       // streams created at set-up
   int solve_variant = 0;             // kernel of the KB-wide block solves (SOLVE_*)
+  int factor_left = 0;               // factorisation schedule: 0 right-looking, 1 left-looking
+  int ngroup_factor = NGROUP;        // stream groups of the factorisation schedules
   int N = 0;
   int S = 1;                         // instances of the mesh batched in this handle
   int N0 = 0;                        // subdomains per instance (N = S N0)
@@ -256,6 +258,7 @@ msgfem_status cuda_fail(msgfem* h, cudaError_t e, const char* what, const char* 
 // host scheduling (setup.cpp)
 msgfem_status build_problem(msgfem* h);
 void build_factor_schedule(msgfem* h);
+void build_wave_factor_schedule(msgfem* h, WaveSched& w);
 void build_solve_schedules(msgfem* h);
 void build_wave_solve_schedules(msgfem* h, WaveSched& w);
 void build_coarse_schedules(msgfem* h);

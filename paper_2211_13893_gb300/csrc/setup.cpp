@@ -293,8 +293,11 @@ msgfem_status build_problem(msgfem* h) {
 }
 
 // ---------------------------------------------------------------------------
-// Factorisation schedule: per layer, SYRK; per tile column k: POTRF, TRMM,
-// UPDATE.  The block inverse of layer l (TRTRI rows 1..T-1, each row depending
+// Factorisation schedule: per layer, SYRK; per tile column k either
+// right-looking (POTRF, TRMM, UPDATE of the whole trailing matrix by column k,
+// inner dimension 64) or left-looking (UPDATE of column k by the finished
+// columns 0..k-1, inner dimension 64 k, then POTRF, TRMM): the same work in
+// fewer, longer tasks.  The block inverse of layer l (TRTRI rows 1..T-1, each row depending
 // on the previous one) needs only L_l, so row i is issued together with the
 // (i-1)-th step of layer l + 1: it fills the SMs that the narrow POTRF and
 // TRMM steps leave idle.  Tasks of all subdomains (and of K and A11) with the
@@ -306,7 +309,8 @@ using FactorKeysT = std::map<long long, std::vector<TileTaskT<T>>>;
 using FactorKeys = FactorKeysT<double>;
 
 template <typename Sc>
-void add_matrix_tasks(FactorKeysT<Sc>& fk, Sc* D, Sc* E, Sc* L, int b, int nL, int sub, int Tmax, long long skew = 0) {
+void add_matrix_tasks(FactorKeysT<Sc>& fk, Sc* D, Sc* E, Sc* L, int b, int nL, int sub, int Tmax, bool left = false,
+                      long long skew = 0) {
   const int T = b / TILE;
   const long long per_layer = 3LL * Tmax + 1;
   auto tileD = [&](int l, int i, int j) { return D + (size_t)l * b * b + (size_t)i * TILE * b + (size_t)j * TILE; };
@@ -319,7 +323,29 @@ void add_matrix_tasks(FactorKeysT<Sc>& fk, Sc* D, Sc* E, Sc* L, int b, int nL, i
         for (int j = 0; j <= i; ++j)
           fk[base].push_back({tileE(l - 1, i, 0), tileE(l - 1, j, 0), tileD(l, i, j), nullptr, b, b, b, b,
                               G_TRANSB | G_ACC | G_NEG, sub});
-    for (int k = 0; k < T; ++k) {
+    for (int k = 0; k < T && left; ++k) {
+      // left-looking: update of tile column k with all finished columns 0..k-1
+      // (one GEMM of inner dimension 64 k per tile instead of k GEMMs of 64)
+      auto& upd = fk[base + 1 + 3 * k];
+      if (k > 0) {
+        for (int i = k; i < T; ++i)
+          upd.push_back({tileD(l, i, 0), tileD(l, k, 0), tileD(l, i, k), nullptr, b, b, b, k * TILE,
+                         G_TRANSB | G_ACC | G_NEG, sub});
+        if (l + 1 < nL)
+          for (int i = 0; i < T; ++i)
+            upd.push_back({tileE(l, i, 0), tileD(l, k, 0), tileE(l, i, k), nullptr, b, b, b, k * TILE,
+                           G_TRANSB | G_ACC | G_NEG, sub});
+      }
+      fk[base + 2 + 3 * k].push_back({nullptr, nullptr, tileD(l, k, k), tileL(l, k, k), 0, 0, b, 0, G_POTRF, sub});
+      auto& trmm = fk[base + 3 + 3 * k];
+      for (int i = k + 1; i < T; ++i)
+        trmm.push_back({tileD(l, i, k), tileL(l, k, k), tileD(l, i, k), nullptr, b, b, b, TILE, G_TRANSB, sub});
+      if (l + 1 < nL)
+        for (int i = 0; i < T; ++i)
+          trmm.push_back({tileE(l, i, k), tileL(l, k, k), tileE(l, i, k), nullptr, b, b, b, TILE, G_TRANSB, sub});
+    }
+    for (int k = 0; k < T && !left; ++k) {
+      // right-looking: POTRF, TRMM, then the update of the whole trailing matrix
       fk[base + 1 + 3 * k].push_back({nullptr, nullptr, tileD(l, k, k), tileL(l, k, k), 0, 0, b, 0, G_POTRF, sub});
       auto& trmm = fk[base + 2 + 3 * k];
       for (int i = k + 1; i < T; ++i)
@@ -467,35 +493,38 @@ void flatten_solve(std::map<long long, std::vector<SolveTaskT<T>>>& keys, SolveS
 // NGROUP groups, each launched on its own stream, so that a group's narrow
 // steps (POTRF, TRMM, late UPDATEs) overlap the wide steps of the others
 // instead of waiting at a common launch boundary.
-void build_factor_schedule(msgfem* h) {
+void build_wave_factor_schedule(msgfem* h, WaveSched& w) {
   int Tmax = 1;
   for (const auto& s : h->sub) Tmax = std::max(Tmax, std::max(s.bK, s.bA) / TILE);
-  const int ng = h->ngroup;
-  for (WaveSched& w : h->waves) {
-    if (h->mixed) {
-      std::vector<FactorKeysT<float>> fk(ng);
-      int chain = 0;
-      for (int j : w.members) {
-        SubDev& s = h->sub[j];
-        add_matrix_tasks(fk[chain++ % ng], s.DKf, s.EKf, s.LKf, s.bK, s.nzn, j, Tmax);
-        add_matrix_tasks(fk[chain++ % ng], s.DAf, s.EAf, s.LAf, s.bA, s.nzn, j, Tmax);
-      }
-      w.factf.steps.clear();
-      w.factf.gemm.clear();
-      for (int g = 0; g < ng; ++g) flatten(fk[g], w.factf, true);
-      continue;
-    }
-    std::vector<FactorKeys> fk(ng);
+  const int ng = h->ngroup_factor;
+  const bool left = h->factor_left != 0;
+  if (h->mixed) {
+    std::vector<FactorKeysT<float>> fk(ng);
     int chain = 0;
     for (int j : w.members) {
       SubDev& s = h->sub[j];
-      add_matrix_tasks(fk[chain++ % ng], s.DK, s.EK, s.LK, s.bK, s.nzn, j, Tmax);
-      add_matrix_tasks(fk[chain++ % ng], s.DA, s.EA, s.LA, s.bA, s.nzn, j, Tmax);
+      add_matrix_tasks(fk[chain++ % ng], s.DKf, s.EKf, s.LKf, s.bK, s.nzn, j, Tmax, left);
+      add_matrix_tasks(fk[chain++ % ng], s.DAf, s.EAf, s.LAf, s.bA, s.nzn, j, Tmax, left);
     }
-    w.fact.steps.clear();
-    w.fact.gemm.clear();
-    for (int g = 0; g < ng; ++g) flatten(fk[g], w.fact, true);
+    w.factf.steps.clear();
+    w.factf.gemm.clear();
+    for (int g = 0; g < ng; ++g) flatten(fk[g], w.factf, true);
+    return;
   }
+  std::vector<FactorKeys> fk(ng);
+  int chain = 0;
+  for (int j : w.members) {
+    SubDev& s = h->sub[j];
+    add_matrix_tasks(fk[chain++ % ng], s.DK, s.EK, s.LK, s.bK, s.nzn, j, Tmax, left);
+    add_matrix_tasks(fk[chain++ % ng], s.DA, s.EA, s.LA, s.bA, s.nzn, j, Tmax, left);
+  }
+  w.fact.steps.clear();
+  w.fact.gemm.clear();
+  for (int g = 0; g < ng; ++g) flatten(fk[g], w.fact, true);
+}
+
+void build_factor_schedule(msgfem* h) {
+  for (WaveSched& w : h->waves) build_wave_factor_schedule(h, w);
 }
 
 namespace {

@@ -47,11 +47,12 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("block", C.c_int), ("max_iter", C.c_int), ("tol", C.c_double),
                 ("seed", C.c_ulonglong), ("stream", C.c_void_p), ("profile", C.c_int), ("solver", C.c_int),
                 ("streams", C.c_int), ("refine", C.c_int), ("instances", C.c_int), ("solve_kernel", C.c_int),
-                ("wave_mb", C.c_double)]
+                ("factor_schedule", C.c_int), ("wave_mb", C.c_double)]
 
 
 class Tuning(C.Structure):
-    _fields_ = [("streams", C.c_int), ("solve_kernel", C.c_int), ("best_ms", C.c_double),
+    _fields_ = [("factor_schedule", C.c_int), ("factor_ms", C.c_double * 2),
+                ("streams", C.c_int), ("solve_kernel", C.c_int), ("best_ms", C.c_double),
                 ("solve_ms", (C.c_double * 3) * 3)]
 
 
@@ -139,7 +140,8 @@ class MSGFEM:
 
     def __init__(self, nx, ny, nz, hx, hy, hz, traction, E9, elem_angles, sx, sy, overlap, oversampling,
                  block=0, max_iter=0, tol=0.0, seed=0, stream=None, precision=0, profile=0, solver=0, streams=0, refine=0,
-                 instances=0, xyz=None, frames=None, boxes=None, wave_mb=0.0, solve_kernel=0):
+                 instances=0, xyz=None, frames=None, boxes=None, wave_mb=0.0, solve_kernel=0,
+                 factor_schedule=0):
         self.lib = load_library()
         self.h = C.c_void_p()
         self._E9 = np.ascontiguousarray(E9, dtype=np.float64)
@@ -156,7 +158,7 @@ class MSGFEM:
         nb = 0 if self._boxes is None else len(self._boxes) // 4
         part = Partition(sx, sy, nb, _ptr(self._boxes))
         opt = Options(precision, block, max_iter, tol, seed, stream, profile, solver, streams, refine, instances,
-                      solve_kernel, wave_mb)
+                      solve_kernel, factor_schedule, wave_mb)
         self.instances = max(1, instances)
         st = self.lib.msgfem_setup(C.byref(self.mesh), C.byref(plies), C.byref(part), overlap, oversampling,
                                    C.byref(opt), C.byref(self.h))
@@ -228,7 +230,8 @@ class MSGFEM:
         (include/msgfem.h msgfem_autotune); returns the choice and the timings."""
         t = Tuning()
         self._check(self.lib.msgfem_autotune(self.h, reps, C.byref(t)))
-        return {"streams": t.streams, "solve_kernel": t.solve_kernel, "best_ms": t.best_ms,
+        return {"factor_schedule": t.factor_schedule, "factor_ms": [t.factor_ms[0], t.factor_ms[1]],
+                "streams": t.streams, "solve_kernel": t.solve_kernel, "best_ms": t.best_ms,
                 "solve_ms": [[t.solve_ms[g][v] for v in range(3)] for g in range(3)]}
 
     def info(self, j):

@@ -85,8 +85,17 @@ def test_autotune_keeps_results_and_adopts_choice():
     la = m.local_spaces(cfg.n_loc)
     t = m.autotune()
     assert t["streams"] in (4, 8, 16) and t["solve_kernel"] in (1, 2, 3) and t["best_ms"] > 0
+    assert t["factor_schedule"] in (0, 1) and min(t["factor_ms"]) > 0
     assert min(x for row in t["solve_ms"] for x in row if x > 0) == pytest.approx(t["best_ms"])
     lb = m.local_spaces(cfg.n_loc)
     m.close()
     scale = np.abs(la).max(axis=1, keepdims=True)
     assert (np.abs(la - lb) / scale).max() <= 1e-6
+
+
+@pytest.mark.parametrize("name,precision", [("t4", 0), ("s2", 1), ("c1", 1)])
+def test_left_looking_factorisation_parity(name, precision):
+    """The left-looking factorisation schedule gives oracle parity."""
+    from test_gpu_local import run_case
+    tol = (1e-8, 1e-5) if precision == 0 else (1e-5, 1e-4)
+    run_case(name, precision=precision, tol_lam=tol[0], tol_angle=tol[1], factor_schedule=1)
