@@ -244,7 +244,13 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
+    step()
+    tuning = None
+    if not args.no_autotune:
+        t1 = time.perf_counter()
+        tuning = m.autotune()                # factor schedule and block-solve launch shapes
+        tuning["seconds"] = time.perf_counter() - t1
+    for _ in range(max(1, args.warmup - 1)):
         step()
     barrier()
     m.profile(reset=True)
@@ -320,6 +326,7 @@ def run_ours(args):
     extra = {"iterations_max": max(i["iterations"] for i in infos),
              "residual_max": max(i["residual"] for i in infos),
              "lambda_sub5_head": [float(x) for x in lam_dev[5 % m.N, :8].cpu().numpy()]}
+    tuning_fp64 = tuning
     lam_fp64 = lam_dev.clone()
     u_fp64 = u_dev.clone()
     m.close()
@@ -348,7 +355,8 @@ def run_ours(args):
                            "l2": "flushed between timed steps (256 MiB write); working set ~25 GB >> L2",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "solver": extra, "mixed": mixed, "c4": c4, "warm_c5": warm}
+                "clocks": clocks, "solver": extra, "autotune": tuning_fp64, "mixed": mixed, "c4": c4,
+                "warm_c5": warm}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -456,6 +464,12 @@ def run_mixed(args, cfg, ang_dev, stream, dev, rank, lam_fp64, u_fp64, flush, wo
         m.coarse_assemble()
         m.solve(u_out=u)
 
+    step()
+    tuning = None
+    if not args.no_autotune:
+        t1 = time.perf_counter()
+        tuning = m.autotune()
+        tuning["seconds"] = time.perf_counter() - t1
     for _ in range(max(2, args.warmup - 1)):
         step()
     torch.cuda.synchronize()
@@ -491,7 +505,7 @@ def run_mixed(args, cfg, ang_dev, stream, dev, rank, lam_fp64, u_fp64, flush, wo
            "stencil": {"ms_per_step": prof["stencil_ms"] / args.steps,
                        "tflops": prof["stencil_flops"] * args.steps / (prof["stencil_ms"] / 1000.0) / 1e12
                        if prof["stencil_ms"] else None},
-           "ortho_ms_per_step": prof["ortho_ms"] / args.steps,
+           "ortho_ms_per_step": prof["ortho_ms"] / args.steps, "autotune": tuning,
            "roofline": {"bound": "hbm", "achieved": solve_gbs, "peak": hbm, "unit": "GB/s",
                         "frac": solve_gbs / hbm, "peak_note": hbm_note,
                         "kernel": "k_solve_stream (FP32 block solves, 8 right-hand sides)",
@@ -644,7 +658,7 @@ def main():
     ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start (c5) run")
     ap.add_argument("--no-c4", action="store_true", help="skip the batched C-section (c4) run")
     ap.add_argument("--c4-steps", type=int, default=1, help="timed steps of the c4 run")
-    ap.add_argument("--no-autotune", action="store_true", help="c4 run with the default block-solve launches")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default factor schedule and solve launches")
     ap.add_argument("--streams", type=int, default=0, help="stream groups of the library (0 = its default)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
