@@ -84,6 +84,21 @@ class _Range:
         return False
 
 
+def max_over_ranks(x, world, device):
+    """The largest value of x over all ranks (every rank gets it); x itself on one rank."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, steps, total_ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank * steps / (total_ms / 1000.0)
+
+
 def dist_env():
     return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
 
@@ -272,11 +287,8 @@ def run_ours(args):
     prof = m.profile()
     launches = prof["launches"] - launches0
     total_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * m.N * args.steps / (total_ms / 1000.0)
+    total_ms = max_over_ranks(total_ms, world, dev)
+    value = job_rate(world, m.N, args.steps, total_ms)
     # roofline of the dominant kernel class (FP64 ALU bound)
     fact_tf = prof["factor_flops"] * args.steps / (prof["factor_ms"] / 1000.0) / 1e12 if prof["factor_ms"] else 0.0
     solve_tf = prof["solve_flops"] * args.steps / (prof["solve_ms"] / 1000.0) / 1e12 if prof["solve_ms"] else 0.0
@@ -316,10 +328,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_ms.append(1000.0 * (time.perf_counter() - t0))
     e2e_total = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(e2e_total, world, dev)
     e2e = {"value": world * m.N * args.steps / (e2e_total / 1000.0), "unit": "subdomains/s",
            "h2d_bytes_per_step": int(ang.nbytes), "d2h_bytes_per_step": int(lam_host.numel() * 8 + u_host.numel() * 8)}
     infos = [m.info(j) for j in range(m.N)]
@@ -406,10 +415,7 @@ def run_c4(args, dev, stream, flush, rank, world):
         ms.append(e0.elapsed_time(e1))
     prof = m.profile()
     total = sum(ms)
-    if world > 1:
-        t = torch.tensor([total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
+    total = max_over_ranks(total, world, dev)
     k = args.c4_steps
     infos = [m.info(j) for j in range(m.N)]
     sizes = omega_star_sizes(cfg)
@@ -486,10 +492,7 @@ def run_mixed(args, cfg, ang_dev, stream, dev, rank, lam_fp64, u_fp64, flush, wo
         ms.append(e0.elapsed_time(e1))
     prof = m.profile()
     total = sum(ms)
-    if world > 1:
-        t = torch.tensor([total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
+    total = max_over_ranks(total, world, dev)
     e = C.c_double(-1.0)
     m.lib.msgfem_energy_error_noalloc(m.h, u.data_ptr(), u_fp64.data_ptr(), C.addressof(e))
     hbm, hbm_note = _hbm_peak()
