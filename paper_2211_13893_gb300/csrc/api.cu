@@ -66,6 +66,15 @@ msgfem_status dalloc(msgfem* h, T** p, size_t count) {
   return MSGFEM_OK;
 }
 
+// Release one allocation made by dalloc (task lists replaced by the autotuner).
+void dfree(msgfem* h, void* p) {
+  if (p == nullptr) return;
+  auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
+  if (it == h->allocs.end()) return;
+  cudaFree(p);
+  h->allocs.erase(it);
+}
+
 
 bool is_device_ptr(const void* p) {
   if (p == nullptr) return false;
@@ -221,9 +230,14 @@ msgfem_status alloc_waves(msgfem* h) {
   return MSGFEM_OK;
 }
 
-// Device copies of a wave's solve task lists (the handle keeps every copy it
-// made until msgfem_destroy; the autotuner re-uploads after regrouping).
+// Device copies of a wave's task lists (replacing earlier copies: the
+// autotuner re-uploads after regrouping).  Captured graphs that used the old
+// copies must be dropped by the caller.
 msgfem_status upload_wave_factor(msgfem* h, WaveSched& w) {
+  dfree(h, w.factf.d_gemm);
+  dfree(h, w.fact.d_gemm);
+  w.factf.d_gemm = nullptr;
+  w.fact.d_gemm = nullptr;
   if (h->mixed) {
     TRY(dalloc(h, &w.factf.d_gemm, std::max<size_t>(w.factf.gemm.size(), 1)));
     CK(cudaMemcpy(w.factf.d_gemm, w.factf.gemm.data(), w.factf.gemm.size() * sizeof(TileTaskT<float>),
@@ -236,6 +250,14 @@ msgfem_status upload_wave_factor(msgfem* h, WaveSched& w) {
 }
 
 msgfem_status upload_wave_solves(msgfem* h, WaveSched& w) {
+  for (SolveScheduleT<float>* ss : {&w.solveKf, &w.solveAf, &w.solveK8f, &w.solveA8f}) {
+    dfree(h, ss->d_tasks);
+    ss->d_tasks = nullptr;
+  }
+  for (SolveSchedule* ss : {&w.solveK, &w.solveA, &w.solveK8, &w.solveA8}) {
+    dfree(h, ss->d_tasks);
+    ss->d_tasks = nullptr;
+  }
   if (h->mixed) {
     for (SolveScheduleT<float>* ss : {&w.solveKf, &w.solveAf, &w.solveK8f, &w.solveA8f}) {
       TRY(dalloc(h, &ss->d_tasks, std::max<size_t>(ss->tasks.size(), 1)));
@@ -1255,6 +1277,17 @@ msgfem_status msgfem_autotune(msgfem_h h, int reps, msgfem_tuning* out) {
   if (h->stage < 2) return MSGFEM_ESTATE;
   if (reps <= 0) reps = 3;
   cudaStream_t st = h->stream;
+  CK(cudaStreamSynchronize(st));
+  // the task lists are re-uploaded below: drop every captured factorisation and
+  // solve graph first, so that none can replay a freed task list
+  for (auto it = h->graphs.begin(); it != h->graphs.end();) {
+    if ((it->first >> 60) == 1 || (it->first >> 60) == 2) {
+      if (it->second.first) cudaGraphExecDestroy(it->second.first);
+      it = h->graphs.erase(it);
+    } else {
+      ++it;
+    }
+  }
   // the last wave's factors are the ones resident in the pool
   const int last = (int)h->waves.size() - 1;
   WaveSched& wl = h->waves[last];
@@ -1358,14 +1391,6 @@ msgfem_status msgfem_autotune(msgfem_h h, int reps, msgfem_tuning* out) {
   for (WaveSched& w : h->waves) {
     build_wave_solve_schedules(h, w);
     TRY(upload_wave_solves(h, w));
-  }
-  for (auto it = h->graphs.begin(); it != h->graphs.end();) {
-    if ((it->first >> 60) == 1 || (it->first >> 60) == 2) {
-      if (it->second.first) cudaGraphExecDestroy(it->second.first);
-      it = h->graphs.erase(it);
-    } else {
-      ++it;
-    }
   }
   h->cur = 0;
   h->base_act.assign(h->N, 1);
