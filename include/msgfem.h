@@ -123,9 +123,11 @@ typedef struct {
   int profile;          /* 1: time the phases with CUDA events (msgfem_get_profile) */
   int solver;           /* 0: block Krylov (block width 8, basis <= 96), 1: subspace iteration */
   int streams;          /* independent task groups run on their own streams (1..16); 0 = 16 */
-  int refine;           /* MSGFEM_MIXED: most FP64 refinement steps after each FP32 solve (a
-                           subdomain stops once its relative residual is below 1e-13 or stops
-                           falling); 0 = 8 */
+  int refine;           /* MSGFEM_MIXED: most FP64 correction steps after each FP32 solve: for
+                           K, preconditioned CG steps with the FP32 factor as preconditioner;
+                           for A11, refinement steps.  A subdomain stops once its relative
+                           residual is below 1e-13 (refinement also when it stops falling);
+                           0 = 10 */
   int instances;        /* batch of S >= 1 copies of the mesh and partition, each with its own
                            element angles (elem_angle_deg holds S consecutive fields);
                            subdomain j of copy i is subdomain i N0 + j of the handle.  With

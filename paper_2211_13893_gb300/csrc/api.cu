@@ -308,7 +308,7 @@ msgfem_status allocate(msgfem* h) {
     CK(cudaMemset(s.QB, 0, (size_t)s.nfull * MQ * sizeof(double)));
     TRY(dalloc(h, &s.NQ, (size_t)s.nfull * MQ));
     CK(cudaMemset(s.NQ, 0, (size_t)s.nfull * MQ * sizeof(double)));
-    double** kbs[] = {&s.Zb, &s.Wb, &s.Tb};
+    double** kbs[] = {&s.Zb, &s.Wb, &s.Tb, &s.P1, &s.P2, &s.P3};
     for (double** m : kbs) {
       TRY(dalloc(h, m, (size_t)s.nfull * KB));
       CK(cudaMemset(*m, 0, (size_t)s.nfull * KB * sizeof(double)));
@@ -339,6 +339,8 @@ msgfem_status allocate(msgfem* h) {
   TRY(dalloc(h, &h->d_flags_saved, h->N + 1));
   TRY(dalloc(h, &h->d_rprev, (size_t)h->N * KB));
   TRY(dalloc(h, &h->d_rref, (size_t)h->N * KB));
+  TRY(dalloc(h, &h->d_pcg, (size_t)h->N * 4 * KB));
+  CK(cudaMemset(h->d_pcg, 0, (size_t)h->N * 4 * KB * sizeof(double)));
   TRY(dalloc(h, &h->d_notspd, h->N + 1));
   TRY(dalloc(h, &h->d_ncols, h->N));
   TRY(dalloc(h, &h->d_coff, h->N));
@@ -561,21 +563,38 @@ void flags_restore(msgfem* h) {
 }
 
 // W = K^{-1} Z on KB-wide blocks (pinned rows zero).  In mixed precision the
-// FP32 solve is followed by up to h->refine steps of iterative refinement with
-// the FP64 stencil residual Z - K W; a subdomain stops refining once its
-// relative residual is below REFINE_TOL or no longer falls (adaptive).
+// FP32 factor is only a preconditioner: the FP32 solve gives the start, then
+// preconditioned conjugate gradients on the FP64 system (residuals and
+// products by the FP64 stencil, one FP32 solve per step, scalars per column)
+// run until every column's relative residual is below REFINE_TOL or h->refine
+// steps are done.  Stationary refinement (W += M^-1 (Z - K W)) needs
+// kappa(K) u_32 well below 1 and stalls on the long floating subdomains of
+// curved laminates (pinned kappa ~ 2e7); CG converges in a few steps there.
 void solve_K_kb(msgfem* h) {
   timed_solve8(h, 0, MV_ZB, MV_WB, 0);
   launch_zero_pins_kb(h, MV_WB);
   if (!h->mixed) return;
   flags_save(h);
-  for (int r = 0; r < h->refine; ++r) {
-    timed_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
-    launch_x_minus_y(h, MV_ZB, MV_TB, MV_TB, KB);
-    launch_zero_pins_kb(h, MV_TB);
-    launch_refine_check(h, MV_TB, MV_ZB, KEEP_K, r);
-    timed_solve_w(h, 0, MV_TB, MV_WB, 0, KB, 1);
-    launch_zero_pins_kb(h, MV_WB);
+  // x = WB, b = ZB, r = TB, z = P1, p = P2, q = P3
+  timed_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
+  launch_x_minus_y(h, MV_ZB, MV_TB, MV_TB, KB);
+  launch_zero_pins_kb(h, MV_TB);
+  launch_refine_check(h, MV_TB, MV_ZB, KEEP_K, 0);
+  timed_solve_w(h, 0, MV_TB, MV_P1, 0, KB, 0);
+  launch_zero_pins_kb(h, MV_P1);
+  launch_coldot_kb(h, MV_TB, MV_P1, KEEP_K, 0);
+  launch_pcg_update(h, PCG_DIR0, MV_WB, MV_TB, MV_P1, MV_P2, MV_P3);
+  for (int it = 0; it < h->refine; ++it) {
+    timed_stencil_kb(h, MV_P2, MV_P3, 0, 1.0);
+    launch_zero_pins_kb(h, MV_P3);
+    launch_coldot_kb(h, MV_P2, MV_P3, KEEP_K, 1);
+    launch_pcg_update(h, PCG_STEP, MV_WB, MV_TB, MV_P1, MV_P2, MV_P3);
+    launch_refine_check(h, MV_TB, MV_ZB, KEEP_K, 0);
+    if (it + 1 == h->refine) break;
+    timed_solve_w(h, 0, MV_TB, MV_P1, 0, KB, 0);
+    launch_zero_pins_kb(h, MV_P1);
+    launch_coldot_kb(h, MV_TB, MV_P1, KEEP_K, 2);
+    launch_pcg_update(h, PCG_DIR, MV_WB, MV_TB, MV_P1, MV_P2, MV_P3);
   }
   flags_restore(h);
 }
@@ -913,7 +932,7 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
   }
   h->mixed = h->opt.precision == MSGFEM_MIXED;
   h->S = h->opt.instances > 1 ? h->opt.instances : 1;
-  h->refine = h->opt.refine > 0 ? h->opt.refine : 8;
+  h->refine = h->opt.refine > 0 ? h->opt.refine : 10;
   *out = h;
   msgfem_status st = build_problem(h);
   if (st != MSGFEM_OK) return st;

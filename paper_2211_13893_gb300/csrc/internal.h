@@ -59,7 +59,8 @@ using SolveTask = SolveTaskT<double>;
 
 // multivector selectors
 enum { MV_PHI = 0, MV_Z, MV_KPHI, MV_W, MV_T1, MV_R, MV_BR, MV_EV, MV_CB, MV_CW,
-       MV_QB, MV_ZB, MV_WB, MV_TB, MV_NQ };   // QB, NQ: [nfull][MQ]; ZB, WB, TB: [nfull][KB]
+       MV_QB, MV_ZB, MV_WB, MV_TB, MV_NQ,
+       MV_P1, MV_P2, MV_P3 };   // QB, NQ: [nfull][MQ]; ZB, WB, TB, P1-P3: [nfull][KB]
 enum { GM_G1 = 0, GM_G2, GM_G3, GM_Y };
 
 // Device-visible per-subdomain descriptor.
@@ -93,6 +94,7 @@ struct SubDev {
   double* QB;                  // [nfull][MQ] N-orthonormal basis (A-harmonic vectors)
   double* NQ;                  // [nfull][MQ] N QB, kept with the basis (no stencil to re-form it)
   double* Zb; double* Wb; double* Tb;   // [nfull][KB] working blocks
+  double* P1; double* P2; double* P3;   // [nfull][KB] preconditioned CG of the mixed K solves: z, p, q
   double* ycK8; double* ycA8;  // [nzn][b][KB] compact solve buffers
   double* rcK8; double* rcA8;  // [b][KB]
   // FP32 copies for the mixed-precision path (layer blocks, factors, solve buffers)
@@ -205,6 +207,7 @@ struct msgfem {
   int* d_flags_saved = nullptr;      // [N + 1] flags saved around an adaptive refinement
   double* d_rprev = nullptr;         // [N][KB] residual norms of the previous refinement step
   double* d_rref = nullptr;          // [N][KB] reference residual norms of the refinement
+  double* d_pcg = nullptr;           // [N][4][KB] CG scalars per column: r.z, p.q, new r.z
   int* d_notspd = nullptr;           // [N + 1]
   int* d_ncols = nullptr;            // [N]
   int* d_mk = nullptr;               // [N] Krylov basis size at the last Rayleigh-Ritz
@@ -296,6 +299,11 @@ void launch_scale_rows_mu(msgfem* h, int which);
 void launch_theta_axpy(msgfem* h, int wx, int wy, int wd, int p);
 void launch_x_minus_y(msgfem* h, int wx, int wy, int wd, int stride);
 void launch_sub_load_kb(msgfem* h, int which);
+// preconditioned CG of the mixed-precision K solves (KB-wide blocks): masked
+// column dots into slot `slot` of d_pcg, and the vector updates
+void launch_coldot_kb(msgfem* h, int wx, int wy, int keep, int slot);
+enum { PCG_STEP = 0, PCG_DIR = 1, PCG_DIR0 = 2 };
+void launch_pcg_update(msgfem* h, int mode, int wx, int wr, int wz, int wp, int wq);
 // adaptive refinement: clear the active flag of subdomains whose residual
 // block wr (rows of the DoF classes in the bit mask keep) is converged or
 // stagnant (step -1 records the reference norm)
@@ -343,6 +351,9 @@ __device__ __forceinline__ double* mv_ptr(const SubDev& s, int which) {
     case MV_NQ: return s.NQ;
     case MV_ZB: return s.Zb;
     case MV_WB: return s.Wb;
+    case MV_P1: return s.P1;
+    case MV_P2: return s.P2;
+    case MV_P3: return s.P3;
     default: return s.Tb;
   }
 }

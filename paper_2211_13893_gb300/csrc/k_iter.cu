@@ -733,6 +733,96 @@ void launch_refine_check(msgfem* h, int wr, int wref, int keep, int step) {
   ++g_launch_count;
 }
 
+namespace {
+// d[slot][c] = sum over rows of the DoF classes in `keep` of X[r][c] Y[r][c]
+// (one block per active subdomain; KB-wide blocks).
+__global__ void __launch_bounds__(256)
+k_coldot_kb(const SubDev* __restrict__ subs, const int* __restrict__ flags, int wx, int wy, int keep,
+            double* __restrict__ pcg, int slot) {
+  const int sidx = blockIdx.x;
+  if (!flags[sidx]) return;
+  const SubDev& s = subs[sidx];
+  const double* X = mv_ptr(s, wx);
+  const double* Y = mv_ptr(s, wy);
+  const int c = threadIdx.x % KB;
+  double acc = 0.0;
+  for (int row = threadIdx.x / KB; row < s.nfull; row += blockDim.x / KB) {
+    if (!((keep >> s.cls[(row / 3) % s.npl]) & 1)) continue;
+    acc += X[(size_t)row * KB + c] * Y[(size_t)row * KB + c];
+  }
+  for (int o = 16; o >= KB; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double sa[8][KB];
+  if ((threadIdx.x & 31) < KB) sa[threadIdx.x >> 5][c] = acc;
+  __syncthreads();
+  if (threadIdx.x < KB) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += sa[w][threadIdx.x];
+    pcg[((size_t)sidx * 4 + slot) * KB + threadIdx.x] = t;
+  }
+}
+
+// CG updates per column (scalars from d_pcg slots 0: r.z, 1: p.q, 2: new r.z):
+//   PCG_STEP: alpha = rz / pq; x += alpha p; r -= alpha q
+//   PCG_DIR:  beta = rz_new / rz; p = z + beta p
+//   PCG_DIR0: p = z
+// A non-positive or non-finite ratio gives a zero step (the column then stalls
+// and its refinement check stops it).
+__global__ void __launch_bounds__(256)
+k_pcg_update(const SubDev* __restrict__ subs, const int* __restrict__ flags, const double* __restrict__ pcg,
+             int mode, int wx, int wr, int wz, int wp, int wq) {
+  const int sidx = blockIdx.y;
+  if (!flags[sidx]) return;
+  const SubDev& s = subs[sidx];
+  const double* d = pcg + (size_t)sidx * 4 * KB;
+  double* X = mv_ptr(s, wx);
+  double* R = mv_ptr(s, wr);
+  const double* Z = mv_ptr(s, wz);
+  double* P = mv_ptr(s, wp);
+  const double* Q = mv_ptr(s, wq);
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)s.nfull * KB;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % KB);
+    if (mode == PCG_STEP) {
+      const double rz = d[c], pq = d[KB + c];
+      double a = rz / pq;
+      if (!(pq > 0.0) || !(rz > 0.0) || !isfinite(a)) a = 0.0;
+      X[e] += a * P[e];
+      R[e] -= a * Q[e];
+    } else if (mode == PCG_DIR) {
+      const double rz = d[c], rzn = d[2 * KB + c];
+      double b = rzn / rz;
+      if (!(rz > 0.0) || !isfinite(b)) b = 0.0;
+      P[e] = Z[e] + b * P[e];
+    } else {
+      P[e] = Z[e];
+    }
+  }
+}
+
+// slot 0 <- slot 2 (r.z of the new residual becomes the current one)
+__global__ void k_pcg_shift(const int* __restrict__ flags, double* __restrict__ pcg, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * KB) return;
+  const int sidx = i / KB, c = i % KB;
+  if (!flags[sidx]) return;
+  pcg[(size_t)sidx * 4 * KB + c] = pcg[((size_t)sidx * 4 + 2) * KB + c];
+}
+}  // namespace
+
+void launch_coldot_kb(msgfem* h, int wx, int wy, int keep, int slot) {
+  k_coldot_kb<<<h->N, 256, 0, h->stream>>>(h->d_sub, h->d_flags, wx, wy, keep, h->d_pcg, slot); ++g_launch_count;
+}
+
+void launch_pcg_update(msgfem* h, int mode, int wx, int wr, int wz, int wp, int wq) {
+  dim3 grid(64, h->N);
+  k_pcg_update<<<grid, 256, 0, h->stream>>>(h->d_sub, h->d_flags, h->d_pcg, mode, wx, wr, wz, wp, wq);
+  ++g_launch_count;
+  if (mode == PCG_DIR) {
+    k_pcg_shift<<<(h->N * KB + 255) / 256, 256, 0, h->stream>>>(h->d_flags, h->d_pcg, h->N);
+    ++g_launch_count;
+  }
+}
+
 void launch_sub_load_kb(msgfem* h, int which) {
   dim3 grid(64, h->N);
   k_sub_load_kb<<<grid, 256, 0, h->stream>>>(h->d_sub, h->d_flags, which); ++g_launch_count;
