@@ -58,8 +58,10 @@ def _hbm_peak():
 METRIC = "local eigensolves/s on 1 GB300 at fixed energy-norm error: plain FP64 vs mixed+warm"
 L2_BYTES = 129 * 2 ** 20
 
-# DRAM traffic of the dominant kernel from ncu (bytes per launch); None until measured for this code.
-NCU_TRAFFIC = None
+# DRAM traffic (bytes) of one FP64 layer-block factorisation (one replay of its graph) on
+# the c2 workload: ncu dram__bytes_read.sum + dram__bytes_write.sum of the factorisation
+# graph on p2 (six c2-sized subdomains, 6.21 GB), scaled by 32 / 6 subdomains.
+NCU_TRAFFIC = {"c2": 6.214e9 * 32 / 6}
 
 
 class _Range:
@@ -297,7 +299,9 @@ def run_ours(args):
     else:
         dom, achieved, share = "k_tile_gemm + k_tile_potrf_inv (layer-block Cholesky)", fact_tf, prof["factor_ms"] / total_ms
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC, "kernel": dom,
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get(args.config), "kernel": dom,
+            "traffic_note": "bytes per factorisation graph replay (one per step), from an ncu capture on p2 scaled "
+                            "to the workload's subdomains",
             "peak_note": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived; a DFMA probe measured 1.206 at ~1980 MHz)",
             "time_share": share,
             "factor": {"tflops": fact_tf, "ms_per_step": prof["factor_ms"] / args.steps},
