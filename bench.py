@@ -101,6 +101,14 @@ def job_rate(world, units_per_rank, steps, total_ms):
     return world * units_per_rank * steps / (total_ms / 1000.0)
 
 
+def _solve_kernel_name(tuning):
+    """Kernel of the FP32 8-column block solves for the autotuner's choice (default: the cp.async ring)."""
+    k = (tuning or {}).get("solve_kernel", 1)
+    return {1: "k_solve_async (FP32 block solves, 8 right-hand sides, cp.async ring)",
+            2: "k_solve_stream<float, 1> (FP32 block solves, 8 right-hand sides, register streaming)",
+            3: "k_solve_stream<float, 2> (FP32 block solves, 8 right-hand sides, two-CTA cluster)"}.get(k, str(k))
+
+
 def dist_env():
     return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
 
@@ -295,9 +303,9 @@ def run_ours(args):
     fact_tf = prof["factor_flops"] * args.steps / (prof["factor_ms"] / 1000.0) / 1e12 if prof["factor_ms"] else 0.0
     solve_tf = prof["solve_flops"] * args.steps / (prof["solve_ms"] / 1000.0) / 1e12 if prof["solve_ms"] else 0.0
     if prof["solve_ms"] >= prof["factor_ms"]:
-        dom, achieved, share = "k_solve_step (block triangular solves)", solve_tf, prof["solve_ms"] / total_ms
+        dom, achieved, share = "k_solve_stream<double> (block triangular solves)", solve_tf, prof["solve_ms"] / total_ms
     else:
-        dom, achieved, share = "k_tile_gemm + k_tile_potrf_inv (layer-block Cholesky)", fact_tf, prof["factor_ms"] / total_ms
+        dom, achieved, share = "k_tile_task<double> (layer-block Cholesky tile tasks)", fact_tf, prof["factor_ms"] / total_ms
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get(args.config), "kernel": dom,
             "traffic_note": "bytes per factorisation graph replay (one per step), from an ncu capture on p2 scaled "
@@ -452,7 +460,7 @@ def run_c4(args, dev, stream, flush, rank, world):
            "unconverged_subdomains": [j for j, i in enumerate(infos) if i["residual"] > 1e-5],
            "roofline": {"bound": "hbm", "achieved": solve_gbs, "peak": hbm, "unit": "GB/s",
                         "frac": solve_gbs / hbm, "peak_note": hbm_note,
-                        "kernel": "k_solve_async (FP32 block solves, 8 right-hand sides)",
+                        "kernel": _solve_kernel_name(tuning),
                         "time_share": prof["solve_ms"] / total if total else None},
            "sampled_parity": sample, "autotune": tuning}
     m.close()
@@ -516,7 +524,7 @@ def run_mixed(args, cfg, ang_dev, stream, dev, rank, lam_fp64, u_fp64, flush, wo
            "ortho_ms_per_step": prof["ortho_ms"] / args.steps, "autotune": tuning,
            "roofline": {"bound": "hbm", "achieved": solve_gbs, "peak": hbm, "unit": "GB/s",
                         "frac": solve_gbs / hbm, "peak_note": hbm_note,
-                        "kernel": "k_solve_stream (FP32 block solves, 8 right-hand sides)",
+                        "kernel": _solve_kernel_name(tuning),
                         "time_share": prof["solve_ms"] / total if total else None,
                         "calls_per_step": prof["solve_calls"]}}
     m.close()
