@@ -126,8 +126,8 @@ typedef struct {
   int refine;           /* MSGFEM_MIXED: most FP64 correction steps after each FP32 solve: for
                            K, preconditioned CG steps with the FP32 factor as preconditioner;
                            for A11, refinement steps.  A subdomain stops once its relative
-                           residual is below 1e-13 (refinement also when it stops falling);
-                           0 = 10 */
+                           residual is below 1e-11 (CG) or 1e-13 (refinement, also when it
+                           stops falling); 0 = 10 */
   int instances;        /* batch of S >= 1 copies of the mesh and partition, each with its own
                            element angles (elem_angle_deg holds S consecutive fields);
                            subdomain j of copy i is subdomain i N0 + j of the handle.  With

@@ -566,7 +566,7 @@ void flags_restore(msgfem* h) {
 // FP32 factor is only a preconditioner: the FP32 solve gives the start, then
 // preconditioned conjugate gradients on the FP64 system (residuals and
 // products by the FP64 stencil, one FP32 solve per step, scalars per column)
-// run until every column's relative residual is below REFINE_TOL or h->refine
+// run until every column's relative residual is below PCG_TOL or h->refine
 // steps are done.  Stationary refinement (W += M^-1 (Z - K W)) needs
 // kappa(K) u_32 well below 1 and stalls on the long floating subdomains of
 // curved laminates (pinned kappa ~ 2e7); CG converges in a few steps there.
@@ -579,7 +579,7 @@ void solve_K_kb(msgfem* h) {
   timed_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
   launch_x_minus_y(h, MV_ZB, MV_TB, MV_TB, KB);
   launch_zero_pins_kb(h, MV_TB);
-  launch_refine_check(h, MV_TB, MV_ZB, KEEP_K, 0);
+  launch_refine_check_tol(h, MV_TB, MV_ZB, KEEP_K, 0, PCG_TOL);
   timed_solve_w(h, 0, MV_TB, MV_P1, 0, KB, 0);
   launch_zero_pins_kb(h, MV_P1);
   launch_coldot_kb(h, MV_TB, MV_P1, KEEP_K, 0);
@@ -589,7 +589,7 @@ void solve_K_kb(msgfem* h) {
     launch_zero_pins_kb(h, MV_P3);
     launch_coldot_kb(h, MV_P2, MV_P3, KEEP_K, 1);
     launch_pcg_update(h, PCG_STEP, MV_WB, MV_TB, MV_P1, MV_P2, MV_P3);
-    launch_refine_check(h, MV_TB, MV_ZB, KEEP_K, 0);
+    launch_refine_check_tol(h, MV_TB, MV_ZB, KEEP_K, 0, PCG_TOL);
     if (it + 1 == h->refine) break;
     timed_solve_w(h, 0, MV_TB, MV_P1, 0, KB, 0);
     launch_zero_pins_kb(h, MV_P1);

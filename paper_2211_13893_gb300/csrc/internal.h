@@ -314,6 +314,10 @@ constexpr int KEEP_A11 = 1 << 1;               // rows of A11: B1
 #define MSGFEM_REFINE_TOL 1e-13
 #endif
 constexpr double REFINE_TOL = MSGFEM_REFINE_TOL;   // relative residual at which refinement stops
+// relative residual at which the conjugate-gradient K solves of the mixed path stop
+// (the eigensolver's own tolerance is 1e-7 in the energy norm)
+constexpr double PCG_TOL = 1e-11;
+void launch_refine_check_tol(msgfem* h, int wr, int wref, int keep, int step, double tol);
 void launch_coarse_blocks(msgfem* h);
 void launch_coarse_rhs(msgfem* h);
 void launch_prolong(msgfem* h);

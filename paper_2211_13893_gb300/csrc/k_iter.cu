@@ -728,25 +728,34 @@ void launch_x_minus_y(msgfem* h, int wx, int wy, int wd, int stride) {
 }
 
 void launch_refine_check(msgfem* h, int wr, int wref, int keep, int step) {
-  k_refine_check<<<h->N, 256, 0, h->stream>>>(h->d_sub, h->d_flags, wr, wref, keep, step, REFINE_TOL,
-                                               h->d_rprev, h->d_rref);
+  launch_refine_check_tol(h, wr, wref, keep, step, REFINE_TOL);
+}
+
+void launch_refine_check_tol(msgfem* h, int wr, int wref, int keep, int step, double tol) {
+  k_refine_check<<<h->N, 256, 0, h->stream>>>(h->d_sub, h->d_flags, wr, wref, keep, step, tol, h->d_rprev,
+                                               h->d_rref);
   ++g_launch_count;
 }
 
 namespace {
 // d[slot][c] = sum over rows of the DoF classes in `keep` of X[r][c] Y[r][c]
-// (one block per active subdomain; KB-wide blocks).
+// (KB-wide blocks): COLDOT_CH blocks per active subdomain write partial sums,
+// then one thread per (subdomain, column) adds them in a fixed order.
+constexpr int COLDOT_CH = 16;
+
 __global__ void __launch_bounds__(256)
-k_coldot_kb(const SubDev* __restrict__ subs, const int* __restrict__ flags, int wx, int wy, int keep,
-            double* __restrict__ pcg, int slot) {
-  const int sidx = blockIdx.x;
+k_coldot_kb_partial(const SubDev* __restrict__ subs, const int* __restrict__ flags, int wx, int wy, int keep,
+                    double* __restrict__ part) {
+  const int sidx = blockIdx.y;
   if (!flags[sidx]) return;
   const SubDev& s = subs[sidx];
   const double* X = mv_ptr(s, wx);
   const double* Y = mv_ptr(s, wy);
+  const int per = (s.nfull + COLDOT_CH - 1) / COLDOT_CH;
+  const int r0 = blockIdx.x * per, r1 = min(r0 + per, s.nfull);
   const int c = threadIdx.x % KB;
   double acc = 0.0;
-  for (int row = threadIdx.x / KB; row < s.nfull; row += blockDim.x / KB) {
+  for (int row = r0 + threadIdx.x / KB; row < r1; row += blockDim.x / KB) {
     if (!((keep >> s.cls[(row / 3) % s.npl]) & 1)) continue;
     acc += X[(size_t)row * KB + c] * Y[(size_t)row * KB + c];
   }
@@ -757,8 +766,19 @@ k_coldot_kb(const SubDev* __restrict__ subs, const int* __restrict__ flags, int 
   if (threadIdx.x < KB) {
     double t = 0.0;
     for (int w = 0; w < 8; ++w) t += sa[w][threadIdx.x];
-    pcg[((size_t)sidx * 4 + slot) * KB + threadIdx.x] = t;
+    part[((size_t)sidx * COLDOT_CH + blockIdx.x) * KB + threadIdx.x] = t;
   }
+}
+
+__global__ void k_coldot_kb_reduce(const int* __restrict__ flags, const double* __restrict__ part,
+                                   double* __restrict__ pcg, int slot, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * KB) return;
+  const int sidx = i / KB, c = i % KB;
+  if (!flags[sidx]) return;
+  double t = 0.0;
+  for (int b = 0; b < COLDOT_CH; ++b) t += part[((size_t)sidx * COLDOT_CH + b) * KB + c];
+  pcg[((size_t)sidx * 4 + slot) * KB + c] = t;
 }
 
 // CG updates per column (scalars from d_pcg slots 0: r.z, 1: p.q, 2: new r.z):
@@ -809,8 +829,13 @@ __global__ void k_pcg_shift(const int* __restrict__ flags, double* __restrict__ 
 }
 }  // namespace
 
+// (partial sums in the Gram scratch: N * COLDOT_CH * KB doubles, far below its size)
 void launch_coldot_kb(msgfem* h, int wx, int wy, int keep, int slot) {
-  k_coldot_kb<<<h->N, 256, 0, h->stream>>>(h->d_sub, h->d_flags, wx, wy, keep, h->d_pcg, slot); ++g_launch_count;
+  dim3 grid(COLDOT_CH, h->N);
+  k_coldot_kb_partial<<<grid, 256, 0, h->stream>>>(h->d_sub, h->d_flags, wx, wy, keep, h->d_gram_part);
+  ++g_launch_count;
+  k_coldot_kb_reduce<<<(h->N * KB + 255) / 256, 256, 0, h->stream>>>(h->d_flags, h->d_gram_part, h->d_pcg, slot, h->N);
+  ++g_launch_count;
 }
 
 void launch_pcg_update(msgfem* h, int mode, int wx, int wr, int wz, int wp, int wq) {
