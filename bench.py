@@ -254,7 +254,7 @@ def run_ours(args):
     ang_dev = torch.tensor(ang, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     m = MSGFEM.from_config(cfg, ang_dev, seed=1234 + rank, stream=stream.cuda_stream, profile=1,
-                           streams=args.streams)
+                           streams=args.streams, direct_launch=int(args.direct_launch))
     lam_dev = torch.empty((m.N, cfg.n_loc), dtype=torch.float64, device=dev)
     u_dev = torch.empty(m.n_dof, dtype=torch.float64, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
@@ -474,7 +474,7 @@ def run_mixed(args, cfg, ang_dev, stream, dev, rank, lam_fp64, u_fp64, flush, wo
     import torch
     from paper_2211_13893_gb300 import MSGFEM
     m = MSGFEM.from_config(cfg, ang_dev, seed=1234 + rank, stream=stream.cuda_stream, profile=1,
-                           streams=args.streams, precision=1)
+                           streams=args.streams, precision=1, direct_launch=int(args.direct_launch))
     lam = torch.empty_like(lam_fp64)
     u = torch.empty_like(u_fp64)
 
@@ -675,6 +675,9 @@ def main():
     ap.add_argument("--no-c4", action="store_true", help="skip the batched C-section (c4) run")
     ap.add_argument("--c4-steps", type=int, default=1, help="timed steps of the c4 run")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default factor schedule and solve launches")
+    ap.add_argument("--direct-launch", action="store_true",
+                    help="launch the factorisation and solve kernels one by one instead of replaying graphs "
+                         "(the same work; for kernel profilers)")
     ap.add_argument("--streams", type=int, default=0, help="stream groups of the library (0 = its default)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -141,6 +141,9 @@ typedef struct {
                            TRMM, update of the trailing matrix), 1 = left-looking (update of the
                            column by all finished columns, then POTRF, TRMM); same work, fewer
                            and longer tasks; msgfem_autotune sets it */
+  int direct_launch;    /* 0: factorisation and block-solve schedules are captured once as CUDA
+                           graphs and replayed; 1: their kernels are launched one by one (the
+                           same kernels and order; for kernel profilers) */
   double wave_mb;       /* device memory (MiB) for the layer blocks, factors and block-solve
                            buffers.  Subdomains whose storage does not fit at once are processed
                            in waves that share one pool of this size (largest first, a wave

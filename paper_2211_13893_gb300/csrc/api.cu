@@ -505,6 +505,10 @@ double solve_bytes(const msgfem* h, int mat, int p) {
 // The kernel-node count is added to the launch counter on every replay.
 template <typename Issue>
 void run_graph(msgfem* h, uint64_t key, Issue issue) {
+  if (h->opt.direct_launch) {   // the same launches, issued one by one (for kernel profilers)
+    issue(h->stream);
+    return;
+  }
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
     const long long before = g_launch_count;
