@@ -20,6 +20,7 @@
 #include <cstring>
 
 #include <type_traits>
+#include <unordered_map>
 
 #include "internal.h"
 
@@ -107,9 +108,40 @@ msgfem_status set_angles(msgfem* h, const double* ang) {
   for (size_t e = 0; e < ntot && layered; ++e)
     layered = h->h_angles[e] == h->h_angles[(e / nel) * nel + e % h->NZ];
   std::vector<double> types;
+  const bool geometric = !h->h_xyz.empty() || !h->h_frame.empty();
+  std::vector<int> etype, trep;
   if (layered) {
     for (int i = 0; i < h->S; ++i)
       types.insert(types.end(), h->h_angles.begin() + (size_t)i * nel, h->h_angles.begin() + (size_t)i * nel + h->NZ);
+  } else if (geometric) {
+    // curved mesh: elements with the same shape (corners up to a translation),
+    // ply frame and angle share one element matrix; etype maps every element
+    // (instance-major) to its type, trep gives a type's first element
+    etype.resize(ntot);
+    std::unordered_map<std::string, int> seen;
+    std::string key;
+    for (size_t g = 0; g < ntot; ++g) {
+      const size_t e = g % nel;
+      const int ie = (int)(e / ((size_t)h->NY * h->NZ)), je = (int)((e / h->NZ) % h->NY), ke = (int)(e % h->NZ);
+      double v[34];
+      double X0[3];
+      node_xyz(h, ie, je, ke, X0);
+      for (int a = 0; a < 8; ++a) {
+        double X[3];
+        node_xyz(h, ie + (a & 1), je + ((a >> 1) & 1), ke + (a >> 2), X);
+        for (int d = 0; d < 3; ++d) v[3 * a + d] = X[d] - X0[d];
+      }
+      for (int q = 0; q < 9; ++q) v[24 + q] = h->h_frame.empty() ? 0.0 : h->h_frame[e * 9 + q];
+      v[33] = h->h_angles[g];
+      key.assign(reinterpret_cast<const char*>(v), sizeof(v));
+      auto it = seen.find(key);
+      if (it == seen.end()) {
+        it = seen.emplace(key, (int)types.size()).first;
+        types.push_back(h->h_angles[g]);
+        trep.push_back((int)e);
+      }
+      etype[g] = it->second;
+    }
   } else {
     types = h->h_angles;
   }
@@ -118,7 +150,17 @@ msgfem_status set_angles(msgfem* h, const double* ang) {
     TRY(dalloc(h, &h->d_angles_type, types.size()));
     TRY(dalloc(h, &h->d_Ke, types.size() * 576));
   }
+  if (geometric && !layered) {
+    if (h->d_etype == nullptr) TRY(dalloc(h, &h->d_etype, ntot));
+    if ((int)types.size() > h->trep_cap) {
+      h->trep_cap = (int)types.size();
+      TRY(dalloc(h, &h->d_trep, types.size()));
+    }
+    CK(cudaMemcpyAsync(h->d_etype, etype.data(), ntot * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->d_trep, trep.data(), trep.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  }
   h->layered = layered ? 1 : 0;
+  h->typed = (geometric && !layered) ? 1 : 0;
   h->ntypes = (int)types.size();
   CK(cudaMemcpyAsync(h->d_angles_type, types.data(), types.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -579,11 +621,12 @@ void solve_K_kb(msgfem* h) {
   launch_zero_pins_kb(h, MV_WB);
   if (!h->mixed) return;
   flags_save(h);
-  // x = WB, b = ZB, r = TB, z = P1, p = P2, q = P3
+  // x = WB, b = ZB, r = TB, z = P1, p = P2, q = P3; ||b|| recorded once as the reference
+  launch_refine_check_tol(h, MV_ZB, -1, KEEP_K, -1, PCG_TOL);
   timed_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
   launch_x_minus_y(h, MV_ZB, MV_TB, MV_TB, KB);
   launch_zero_pins_kb(h, MV_TB);
-  launch_refine_check_tol(h, MV_TB, MV_ZB, KEEP_K, 0, PCG_TOL);
+  launch_refine_check_tol(h, MV_TB, -1, KEEP_K, 0, PCG_TOL);
   timed_solve_w(h, 0, MV_TB, MV_P1, 0, KB, 0);
   launch_zero_pins_kb(h, MV_P1);
   launch_coldot_kb(h, MV_TB, MV_P1, KEEP_K, 0);
@@ -593,7 +636,7 @@ void solve_K_kb(msgfem* h) {
     launch_zero_pins_kb(h, MV_P3);
     launch_coldot_kb(h, MV_P2, MV_P3, KEEP_K, 1);
     launch_pcg_update(h, PCG_STEP, MV_WB, MV_TB, MV_P1, MV_P2, MV_P3);
-    launch_refine_check_tol(h, MV_TB, MV_ZB, KEEP_K, 0, PCG_TOL);
+    launch_refine_check_tol(h, MV_TB, -1, KEEP_K, 0, PCG_TOL);
     if (it + 1 == h->refine) break;
     timed_solve_w(h, 0, MV_TB, MV_P1, 0, KB, 0);
     launch_zero_pins_kb(h, MV_P1);

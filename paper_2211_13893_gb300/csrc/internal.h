@@ -187,6 +187,10 @@ struct msgfem {
   int S = 1;                         // instances of the mesh batched in this handle
   int N0 = 0;                        // subdomains per instance (N = S N0)
   int layered = 0, ntypes = 0, type_cap = 0;
+  int typed = 0;                     // curved mesh: element -> type map in d_etype
+  int* d_etype = nullptr;            // [S nel] type of every element (typed)
+  int* d_trep = nullptr;             // [ntypes] first element of every type (typed)
+  int trep_cap = 0;
   std::vector<double> h_angles;
   std::vector<SubDev> sub;
   std::vector<HostSub> hsub;

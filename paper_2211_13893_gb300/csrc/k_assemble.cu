@@ -74,15 +74,17 @@ __device__ void ply_stiffness(const double* E9, double theta_deg, const double* 
 
 // One block per element type; thread (r, c) computes K_e[r][c].
 //   layered: type = instance * NZ + ply k (box beam, angle per ply);
-//   otherwise type = instance * nel + element.  With node coordinates (xyz)
-//   or ply frames the types are always per element.
+//   curved mesh (node coordinates or ply frames): one type per distinct
+//   (shape up to translation, frame, angle), trep[type] its first element;
+//   otherwise type = instance * nel + element.
 __global__ void __launch_bounds__(576)
 k_element_stiffness(const double* __restrict__ angles, const double* __restrict__ E9, int layered,
                     int NX, int NY, int NZ, double hx, double hy, double hz, const double* __restrict__ xyz,
-                    const double* __restrict__ frame, double* __restrict__ Ke) {
+                    const double* __restrict__ frame, const int* __restrict__ trep, double* __restrict__ Ke) {
   const int type = blockIdx.x;
   const int nel = NX * NY * NZ;
-  const int e = layered ? type % NZ : type % nel;   // element of the first instance
+  // element of the first instance whose corners and frame the type has
+  const int e = trep ? trep[type] : (layered ? type % NZ : type % nel);
   const int ie = layered ? 0 : e / (NY * NZ), je = layered ? 0 : (e / NZ) % NY, ke = e % NZ;
   __shared__ double C[6][6];
   __shared__ double X[8][3];        // corner coordinates
@@ -173,7 +175,8 @@ k_element_stiffness(const double* __restrict__ angles, const double* __restrict_
 // (di, dj, dk) = ((s/9)-1, ((s/3)%3)-1, (s%3)-1).  Only elements inside the
 // Omega* box contribute (Eq. restricted_bilinear_form).
 __global__ void __launch_bounds__(216)
-k_stencil(const SubDev* __restrict__ subs, const double* __restrict__ Ke, int layered, int NY, int NZ, int nel) {
+k_stencil(const SubDev* __restrict__ subs, const double* __restrict__ Ke, int layered, const int* __restrict__ etype,
+          int NY, int NZ, int nel) {
   const SubDev s = subs[blockIdx.y];
   const int tid = threadIdx.x;
   const int node = blockIdx.x * 8 + tid / 27, slot = tid % 27;
@@ -193,7 +196,8 @@ k_stencil(const SubDev* __restrict__ subs, const double* __restrict__ Ke, int la
         const int bx = ax + di, by = ay + dj, bz = az + dk;            // neighbour position
         if (bx < 0 || bx > 1 || by < 0 || by > 1 || bz < 0 || bz > 1) continue;
         const int a = ax + 2 * ay + 4 * az, b = bx + 2 * by + 4 * bz;
-        const int type = layered ? s.inst * NZ + ke : s.inst * nel + (ie * NY + je) * NZ + ke;
+        const int el = s.inst * nel + (ie * NY + je) * NZ + ke;
+        const int type = etype ? etype[el] : (layered ? s.inst * NZ + ke : el);
         const double* K = Ke + (size_t)type * 576;
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -282,14 +286,15 @@ __global__ void k_block_identity(const SubDev* __restrict__ subs, const int* __r
 void launch_element_stiffness(msgfem* h) {
   k_element_stiffness<<<h->ntypes, 576, 0, h->stream>>>(h->d_angles_type, h->d_E9, h->layered, h->NX, h->NY,
                                                         h->NZ, h->hx, h->hy, h->hz, h->d_xyz, h->d_frame,
-                                                        h->d_Ke); ++g_launch_count;
+                                                        h->typed ? h->d_trep : nullptr, h->d_Ke); ++g_launch_count;
 }
 
 void launch_stencil(msgfem* h) {
   int maxn = 0;
   for (const auto& s : h->sub) maxn = std::max(maxn, s.nnode);
   dim3 grid((maxn + 7) / 8, h->N);
-  k_stencil<<<grid, 216, 0, h->stream>>>(h->d_sub, h->d_Ke, h->layered, h->NY, h->NZ, h->NX * h->NY * h->NZ);
+  k_stencil<<<grid, 216, 0, h->stream>>>(h->d_sub, h->d_Ke, h->layered, h->typed ? h->d_etype : nullptr, h->NY, h->NZ,
+                                         h->NX * h->NY * h->NZ);
   ++g_launch_count;
 }
 

@@ -128,8 +128,8 @@ __global__ void k_prolong(const SubDev* __restrict__ subs, int N, const int* __r
 // Energy sums over elements: out[2 b] = sum d^T K_e d with d = ref - u,
 // out[2 b + 1] = sum ref^T K_e ref.
 __global__ void __launch_bounds__(256)
-k_energy(const double* __restrict__ Ke, int layered, const double* __restrict__ ref, const double* __restrict__ u,
-         int NX, int NY, int NZ, double* __restrict__ out) {
+k_energy(const double* __restrict__ Ke, int layered, const int* __restrict__ etype, const double* __restrict__ ref,
+         const double* __restrict__ u, int NX, int NY, int NZ, double* __restrict__ out) {
   __shared__ double red[2][256];
   double e0 = 0.0, e1 = 0.0;
   const int nel = NX * NY * NZ;
@@ -144,7 +144,7 @@ k_energy(const double* __restrict__ Ke, int layered, const double* __restrict__ 
         d[3 * a + c] = r[3 * a + c] - (u ? u[3 * node + c] : 0.0);
       }
     }
-    const double* K = Ke + (size_t)(layered ? ke : el) * 576;
+    const double* K = Ke + (size_t)(etype ? etype[el] : (layered ? ke : el)) * 576;
     for (int i = 0; i < 24; ++i) {
       double kd = 0.0, kr = 0.0;
       for (int j = 0; j < 24; ++j) {
@@ -215,7 +215,8 @@ int energy_blocks(msgfem* h) {
 }
 
 void launch_energy(msgfem* h, const double* d_ref, const double* d_u, double* d_out) {
-  k_energy<<<energy_blocks(h), 256, 0, h->stream>>>(h->d_Ke, h->layered, d_ref, d_u, h->NX, h->NY, h->NZ, d_out); ++g_launch_count;
+  k_energy<<<energy_blocks(h), 256, 0, h->stream>>>(h->d_Ke, h->layered, h->typed ? h->d_etype : nullptr, d_ref, d_u,
+                                                    h->NX, h->NY, h->NZ, d_out); ++g_launch_count;
 }
 
 void launch_basis_out(msgfem* h, int j, double* d_out, int ncols) {

@@ -26,8 +26,9 @@ double* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
 // Each thread sums NOALLOC_EPT consecutive elements; each block writes its own
 // two slots, so no slot has to be cleared between calls.
 __global__ void __launch_bounds__(NOALLOC_THREADS)
-k_energy_blocks(const double* __restrict__ Ke, int layered, const double* __restrict__ ref,
-                const double* __restrict__ u, int NX, int NY, int NZ, double* __restrict__ scratch) {
+k_energy_blocks(const double* __restrict__ Ke, int layered, const int* __restrict__ etype,
+                const double* __restrict__ ref, const double* __restrict__ u, int NX, int NY, int NZ,
+                double* __restrict__ scratch) {
   __shared__ double red[2][NOALLOC_THREADS];
   double e0 = 0.0, e1 = 0.0;
   const int nel = NX * NY * NZ;
@@ -42,7 +43,7 @@ k_energy_blocks(const double* __restrict__ Ke, int layered, const double* __rest
         d[3 * a + c] = r[3 * a + c] - u[3 * node + c];
       }
     }
-    const double* K = Ke + (size_t)(layered ? ke : el) * 576;
+    const double* K = Ke + (size_t)(etype ? etype[el] : (layered ? ke : el)) * 576;
     for (int i = 0; i < 24; ++i) {
       double kd = 0.0, kr = 0.0;
       for (int j = 0; j < 24; ++j) {
@@ -146,8 +147,9 @@ extern "C" msgfem_status msgfem_energy_error_noalloc(msgfem_h h, const double* u
     scratch = g_noalloc_addr[dev];
   }
   const bool dev_out = on_device(energy_err_out);
-  k_energy_blocks<<<(unsigned)nblocks, NOALLOC_THREADS, 0, h->stream>>>(h->d_Ke, h->layered, u_ref, u, h->NX, h->NY,
-                                                                       h->NZ, scratch);
+  k_energy_blocks<<<(unsigned)nblocks, NOALLOC_THREADS, 0, h->stream>>>(h->d_Ke, h->layered,
+                                                                       h->typed ? h->d_etype : nullptr, u_ref, u,
+                                                                       h->NX, h->NY, h->NZ, scratch);
   k_energy_final<<<1, 256, 0, h->stream>>>(scratch, (int)nblocks, dev_out ? energy_err_out : nullptr);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "energy kernels", __FILE__, __LINE__);
