@@ -122,7 +122,8 @@ typedef struct {
   void* stream;         /* cudaStream_t to issue work on; NULL = default stream */
   int profile;          /* 1: time the phases with CUDA events (msgfem_get_profile) */
   int solver;           /* 0: block Krylov (block width 8, basis <= 96), 1: subspace iteration */
-  int streams;          /* independent task groups run on their own streams (1..16); 0 = 16 */
+  int streams;          /* independent task groups run on their own streams (1..32); 0 = 16, and
+                           msgfem_autotune may then choose up to 32 */
   int refine;           /* MSGFEM_MIXED: most FP64 correction steps after each FP32 solve: for
                            K, preconditioned CG steps with the FP32 factor as preconditioner;
                            for A11, refinement steps.  A subdomain stops once its relative
@@ -183,11 +184,13 @@ typedef struct {
 /* Launch shapes chosen by msgfem_autotune and what it measured. */
 typedef struct {
   int factor_schedule;  /* msgfem_options.factor_schedule chosen */
-  double factor_ms[2];  /* factorisation of the measured wave: right-, left-looking */
-  int streams;          /* stream groups of the block-solve schedules (4, 8 or 16) */
+  int factor_streams;   /* stream groups of the factorisation schedules chosen (16 or 32) */
+  double factor_ms[2][2];  /* factorisation of the measured wave: [right-, left-looking][16, 32
+                              groups]; -1 = not run */
+  int streams;          /* stream groups of the block-solve schedules (4, 8, 16 or 32) */
   int solve_kernel;     /* msgfem_options.solve_kernel value chosen (1, 2 or 3) */
   double best_ms;       /* time of one 8-column K solve plus one A11 solve of the measured wave */
-  double solve_ms[3][3];   /* [streams 4, 8, 16][kernel 1, 2, 3]; -1 = not applicable or not run */
+  double solve_ms[4][3];   /* [streams 4, 8, 16, 32][kernel 1, 2, 3]; -1 = not applicable or not run */
 } msgfem_tuning;
 
 /* Per-subdomain diagnostics filled by msgfem_get_info. */
@@ -282,11 +285,12 @@ msgfem_status msgfem_energy_error_noalloc(msgfem_h h, const double* u, const dou
 /* Autotuner of the block-solve launches (not in the paper: a library
  * convenience for batches of uneven subdomains).  On the subdomains of the
  * last wave of the previous msgfem_local_spaces call it first times the
- * layer-block factorisation with the right- and the left-looking schedule
- * (re-assembling the layer blocks before each run) and keeps the faster one,
- * then times `reps` replays (0 = 3) of one 8-column K solve and
+ * layer-block factorisation with the right- and the left-looking schedule,
+ * dealt into 16 or 32 stream groups (re-assembling the layer blocks before
+ * each run), and keeps the fastest, then times `reps` replays (0 = 3) of one
+ * 8-column K solve and
  * one A11 solve, captured as a CUDA graph, for every combination of stream
- * groups {4, 8, 16} (at most msgfem_options.streams) and solve kernel (the
+ * groups {4, 8, 16, 32} (at most msgfem_options.streams) and solve kernel (the
  * cp.async ring in mixed precision only, register streaming, two-CTA
  * cluster), then regroups the solve schedules of every wave and sets the
  * kernel to the fastest combination; later calls use it.  The working blocks

@@ -958,8 +958,8 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
   if (h->opt.max_iter <= 0) h->opt.max_iter = 100;
   if (!(h->opt.tol > 0)) h->opt.tol = 1e-7;
   h->stream = static_cast<cudaStream_t>(h->opt.stream);
-  h->ngroup = h->opt.streams > 0 ? std::min(h->opt.streams, NGROUP) : NGROUP;
-  h->ngroup_created = h->ngroup;
+  h->ngroup = h->opt.streams > 0 ? std::min(h->opt.streams, NGROUP) : 16;
+  h->ngroup_created = h->opt.streams > 0 ? h->ngroup : NGROUP;
   h->ngroup_factor = h->ngroup;
   if (h->opt.solve_kernel < 0 || h->opt.solve_kernel > SOLVE_STREAM_CL2) {
     *out = h;
@@ -995,7 +995,7 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
   }
   st = set_angles(h, plies->elem_angle_deg);
   if (st != MSGFEM_OK) return st;
-  for (int g = 0; g < h->ngroup; ++g) {
+  for (int g = 0; g < h->ngroup_created; ++g) {
     CK(cudaStreamCreateWithFlags(&h->gs.s[g], cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&h->gs.join[g], cudaEventDisableTiming));
   }
@@ -1367,43 +1367,52 @@ msgfem_status msgfem_autotune(msgfem_h h, int reps, msgfem_tuning* out) {
   cudaEvent_t f0, f1;
   CK(cudaEventCreate(&f0));
   CK(cudaEventCreate(&f1));
-  // factorisation schedule of the last wave: right- vs left-looking, each
-  // timed on freshly assembled layer blocks (the second of two runs)
-  int best_f = h->factor_left;
+  // factorisation schedule of the last wave: right- vs left-looking over 16 or
+  // 32 stream groups, each timed on freshly assembled layer blocks (the second
+  // of two runs)
+  int best_f = h->factor_left, best_fg = h->ngroup_factor;
   double best_fms = 1e300;
-  for (int fv = 0; fv < 2; ++fv) {
-    h->factor_left = fv;
-    build_wave_factor_schedule(h, wl);
-    TRY(upload_wave_factor(h, wl));
-    float ms = 0.f;
-    for (int rep = 0; rep < 2; ++rep) {
-      if (h->mixed) launch_layer_blocks_f32(h);
-      else launch_layer_blocks(h);
-      CK(cudaEventRecord(f0, st));
-      if (h->mixed) run_schedule(wl.factf, st, &h->gs);
-      else run_schedule(wl.fact, st, &h->gs);
-      CK(cudaEventRecord(f1, st));
-      CK(cudaEventSynchronize(f1));
-      CK(cudaEventElapsedTime(&ms, f0, f1));
+  const int fgroups[2] = {16, 32};
+  for (int fv = 0; fv < 2; ++fv)
+    for (int gi = 0; gi < 2; ++gi) {
+      t.factor_ms[fv][gi] = -1.0;
+      if (fgroups[gi] > h->ngroup_created) continue;
+      h->factor_left = fv;
+      h->ngroup_factor = fgroups[gi];
+      build_wave_factor_schedule(h, wl);
+      TRY(upload_wave_factor(h, wl));
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        if (h->mixed) launch_layer_blocks_f32(h);
+        else launch_layer_blocks(h);
+        CK(cudaEventRecord(f0, st));
+        if (h->mixed) run_schedule(wl.factf, st, &h->gs);
+        else run_schedule(wl.fact, st, &h->gs);
+        CK(cudaEventRecord(f1, st));
+        CK(cudaEventSynchronize(f1));
+        CK(cudaEventElapsedTime(&ms, f0, f1));
+      }
+      t.factor_ms[fv][gi] = ms;
+      if (ms < best_fms) {
+        best_fms = ms;
+        best_f = fv;
+        best_fg = fgroups[gi];
+      }
     }
-    t.factor_ms[fv] = ms;
-    if (ms < best_fms) {
-      best_fms = ms;
-      best_f = fv;
-    }
-  }
   CK(cudaEventDestroy(f0));
   CK(cudaEventDestroy(f1));
   h->factor_left = best_f;
+  h->ngroup_factor = best_fg;
   t.factor_schedule = best_f;
-  const int groups[3] = {4, 8, 16};
+  t.factor_streams = best_fg;
+  const int groups[4] = {4, 8, 16, 32};
   const int variants[3] = {SOLVE_ASYNC_RING, SOLVE_STREAM, SOLVE_STREAM_CL2};
   double best = 1e300;
   int best_g = h->ngroup, best_v = h->solve_variant;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  for (int gi = 0; gi < 3; ++gi) {
+  for (int gi = 0; gi < 4; ++gi) {
     for (int vi = 0; vi < 3; ++vi) t.solve_ms[gi][vi] = -1.0;
     if (groups[gi] > h->ngroup_created) continue;
     h->ngroup = groups[gi];

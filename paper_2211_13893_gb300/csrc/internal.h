@@ -109,7 +109,7 @@ struct SubDev {
 
 // A schedule is a set of independent groups (each a sequence of steps, run on
 // its own stream); steps[g] lists the launches of group g in order.
-#define NGROUP 16   // most stream groups a schedule may use
+#define NGROUP 32   // most stream groups a schedule may use (16 by default; the autotuner may take 32)
 struct SchedStep { int first, count; };
 template <typename T>
 struct ScheduleT {

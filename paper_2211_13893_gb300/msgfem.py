@@ -51,9 +51,9 @@ class Options(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("factor_schedule", C.c_int), ("factor_ms", C.c_double * 2),
+    _fields_ = [("factor_schedule", C.c_int), ("factor_streams", C.c_int), ("factor_ms", (C.c_double * 2) * 2),
                 ("streams", C.c_int), ("solve_kernel", C.c_int), ("best_ms", C.c_double),
-                ("solve_ms", (C.c_double * 3) * 3)]
+                ("solve_ms", (C.c_double * 3) * 4)]
 
 
 class Profile(C.Structure):
@@ -230,9 +230,10 @@ class MSGFEM:
         (include/msgfem.h msgfem_autotune); returns the choice and the timings."""
         t = Tuning()
         self._check(self.lib.msgfem_autotune(self.h, reps, C.byref(t)))
-        return {"factor_schedule": t.factor_schedule, "factor_ms": [t.factor_ms[0], t.factor_ms[1]],
+        return {"factor_schedule": t.factor_schedule, "factor_streams": t.factor_streams,
+                "factor_ms": [[t.factor_ms[f][g] for g in range(2)] for f in range(2)],
                 "streams": t.streams, "solve_kernel": t.solve_kernel, "best_ms": t.best_ms,
-                "solve_ms": [[t.solve_ms[g][v] for v in range(3)] for g in range(3)]}
+                "solve_ms": [[t.solve_ms[g][v] for v in range(3)] for g in range(4)]}
 
     def info(self, j):
         inf = SubInfo()
