@@ -114,6 +114,10 @@ def dist_env():
 
 
 def workload_desc(cfg):
+    if getattr(cfg, "kind", "beam") == "section":
+        return (f"C-section spar {cfg.NX}x{cfg.NY}x{cfg.NZ} curved hex ({cfg.n_dof} DoF, {cfg.NZ} plies), "
+                f"{cfg.n_sub} subdomains ({cfg.sx} x {cfg.sy} graded boxes), overlap {cfg.overlap}, "
+                f"oversampling {cfg.oversampling}, n_loc={cfg.n_loc}")
     return (f"laminated beam {cfg.NX}x{cfg.NY}x{cfg.NZ} hex ({cfg.n_dof} DoF, {cfg.NZ} plies), "
             f"{cfg.sx}x{cfg.sy} subdomains, overlap {cfg.overlap}, oversampling {cfg.oversampling}, "
             f"n_loc={cfg.n_loc}, FP64")
