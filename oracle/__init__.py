@@ -14,7 +14,8 @@ primitives (sparse LU, dense Cholesky, symmetric eigensolvers) as steps:
 * ``element``   trilinear hexahedron stiffness by 2x2x2 Gauss quadrature
   (Eq. weak_form, Eq. element_stiffness).
 * ``mesh``      structured laminated-beam mesh, clamped x = 0 face, traction
-  load on x = L (Eq. weak_form, b(v)).
+  load on x = L (Eq. weak_form, b(v)); ``HexMesh`` for structured meshes with
+  given node coordinates and per-element ply frames (the curved C-section).
 * ``assemble``  global and subdomain-restricted stiffness (Eqs.
   element_stiffness, restricted_bilinear_form).
 * ``partition`` non-overlapping boxes, overlap and oversampling layers, the DoF
@@ -25,7 +26,8 @@ primitives (sparse LU, dense Cholesky, symmetric eigensolvers) as steps:
 * ``arpack``    the paper's own solver design: shift-invert Lanczos (ARPACK) on
   the saddle-point pencil with a sparse LU (Sec. 4.5).
 * ``coarse``    PoU-weighted basis with Gram-Schmidt (Sec. 4.3-4.4), the coarse
-  Galerkin problem (Eq. GFEM_coarse_approximation) and the energy error.
+  Galerkin problem (Eq. GFEM_coarse_approximation) and the energy error; local
+  basis sizes from n_loc or from the eigenvalue threshold (Sec. 5.5).
 * ``fine``      the fine-scale FE solution u_h (Eq. fe_matrix_system) by a
   direct sparse solve.
 
