@@ -200,3 +200,21 @@ def test_floating_curved_subdomain_has_rigid_null_modes():
     Q, _ = np.linalg.qr(phi[:, :6])
     resid = R - Q @ (Q.T @ R)
     assert np.linalg.norm(resid) < 1e-6 * np.linalg.norm(R)
+
+
+def test_general_mesh_reduces_to_the_box_beam():
+    """A HexMesh given the box beam's node coordinates and identity frames assembles
+    the same stiffness and load as the box-beam path (whose pins are the beam tests)."""
+    from oracle.assemble import assemble_global
+    from oracle.mesh import BeamMesh
+    cfg = get_config("t2")
+    box = BeamMesh.from_config(cfg)
+    i, j, k = np.meshgrid(np.arange(cfg.NX + 1), np.arange(cfg.NY + 1), np.arange(cfg.NZ + 1), indexing="ij")
+    xyz = np.stack([i * cfg.hx, j * cfg.hy, k * cfg.t], axis=-1).astype(np.float64)
+    frames = np.broadcast_to(np.eye(3), (cfg.NX, cfg.NY, cfg.NZ, 3, 3)).copy()
+    gen = HexMesh(xyz, frames)
+    ang = element_angles(cfg)
+    Ab = assemble_global(box, ang, cfg.material)
+    Ag = assemble_global(gen, ang, cfg.material, cache=make_cache(gen, cfg.material))
+    assert abs(Ab - Ag).max() <= 1e-10 * abs(Ab).max()
+    assert np.allclose(gen.compression_load(1.0), box.compression_load(1.0), rtol=0, atol=1e-12)
