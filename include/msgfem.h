@@ -219,12 +219,16 @@ msgfem_status msgfem_update_angles(msgfem_h h, const double* elem_angle_deg);
 
 /* The local stage: element stiffness and subdomain matrices (Eqs.
  * element_stiffness, restricted_bilinear_form), the n_loc smallest eigenpairs
- * of Eq. AHarmonicGeneralizeEigenProblem per subdomain (subspace iteration
- * with shift-invert at zero, Rayleigh-Ritz in FP64) and the particular
- * functions (Eq. up_r).  lambda_out (N * n_loc doubles, subdomain-major,
- * ascending; may be NULL) receives the eigenvalues.  Errors: EINVAL
- * (n_loc < 1 or larger than the A-harmonic space of a subdomain), ENOTSPD,
- * ENOCONV, ECUDA. */
+ * of Eq. AHarmonicGeneralizeEigenProblem per subdomain (block Krylov, or
+ * subspace iteration with msgfem_options.solver = 1; shift-invert at zero,
+ * Rayleigh-Ritz in FP64; the six rigid modes of a floating subdomain are
+ * exact zero eigenpairs and count in n_loc) and the particular functions
+ * (Eq. up_r), wave by wave when the factors do not fit at once
+ * (msgfem_options.wave_mb).  lambda_out (N * n_loc doubles, subdomain-major,
+ * ascending; may be NULL; host or device) receives the eigenvalues.  Errors:
+ * EINVAL (n_loc < 1 or larger than the A-harmonic space of a subdomain),
+ * ENOTSPD, ENOCONV (results are the last iterate; msgfem_subinfo gives each
+ * subdomain's residual), ECUDA. */
 msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out);
 
 /* PoU-weighted basis with Gram-Schmidt and the appended particular function
