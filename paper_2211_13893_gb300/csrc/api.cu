@@ -167,54 +167,11 @@ msgfem_status set_angles(msgfem* h, const double* ang) {
   return MSGFEM_OK;
 }
 
-// Layer blocks (D, E, Linv of K and A11), their factors and the compact solve
-// buffers of one subdomain, in the factor's precision; the parts are laid out
-// in this order, each aligned to 256 bytes.  Returns the bytes used.
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-template <typename T>
-size_t place_blocks(SubDev& s, char* base, bool assign) {
-  const size_t bK2 = (size_t)s.bK * s.bK, bA2 = (size_t)s.bA * s.bA;
-  const size_t parts[12] = {bK2 * (2 * s.nzn - 1), bK2 * s.nzn, bA2 * (2 * s.nzn - 1), bA2 * s.nzn,
-                            (size_t)s.nzn * s.bK * PST, (size_t)s.nzn * s.bA * PST, (size_t)s.bK * PST,
-                            (size_t)s.bA * PST, (size_t)s.nzn * s.bK * KB, (size_t)s.nzn * s.bA * KB,
-                            (size_t)s.bK * KB, (size_t)s.bA * KB};
-  size_t off = 0;
-  T* p[12];
-  for (int i = 0; i < 12; ++i) {
-    p[i] = reinterpret_cast<T*>(base + off);
-    off = align_up(off + parts[i] * sizeof(T), 256);
-  }
-  if (assign) {
-    if constexpr (std::is_same<T, float>::value) {
-      s.DKf = p[0]; s.EKf = p[0] + bK2 * s.nzn; s.LKf = p[1];
-      s.DAf = p[2]; s.EAf = p[2] + bA2 * s.nzn; s.LAf = p[3];
-      s.ycKf = p[4]; s.ycAf = p[5]; s.rcKf = p[6]; s.rcAf = p[7];
-      s.ycK8f = p[8]; s.ycA8f = p[9]; s.rcK8f = p[10]; s.rcA8f = p[11];
-    } else {
-      s.DK = p[0]; s.EK = p[0] + bK2 * s.nzn; s.LK = p[1];
-      s.DA = p[2]; s.EA = p[2] + bA2 * s.nzn; s.LA = p[3];
-      s.ycK = p[4]; s.ycA = p[5]; s.rcK = p[6]; s.rcA = p[7];
-      s.ycK8 = p[8]; s.ycA8 = p[9]; s.rcK8 = p[10]; s.rcA8 = p[11];
-    }
-  }
-  return off;
-}
-
-size_t block_bytes(msgfem* h, SubDev& s) {
-  return h->mixed ? place_blocks<float>(s, nullptr, false) : place_blocks<double>(s, nullptr, false);
-}
-
-// Group the subdomains into waves whose factor storage fits the budget
-// (msgfem_options.wave_mb, or by default 80 % of the free device memory less
-// room for the element matrices), allocate one pool for the largest wave and
-// point every subdomain at its slot.  Subdomains are taken largest first and a
-// wave is closed when the next one no longer fits (waves of similar sizes).
-// When everything fits: one wave of all subdomains in index order.
+// Waves of subdomains (grouping and pool placement in setup.cpp): the budget
+// is msgfem_options.wave_mb, or by default 80 % of the free device memory less
+// room for the element matrices; one pool holds the largest wave and every
+// subdomain points at its slot.
 msgfem_status alloc_waves(msgfem* h) {
-  std::vector<size_t> bytes(h->N);
-  size_t total = 0;
-  for (int j = 0; j < h->N; ++j) total += (bytes[j] = block_bytes(h, h->sub[j]));
   size_t budget;
   if (h->opt.wave_mb > 0) {
     budget = (size_t)(h->opt.wave_mb * 1048576.0);
@@ -225,49 +182,13 @@ msgfem_status alloc_waves(msgfem* h) {
     const size_t reserve = ke + ((size_t)2 << 30);
     budget = fr > reserve ? (size_t)(0.8 * (double)(fr - reserve)) : 0;
   }
-  h->waves.clear();
-  h->wave_of.assign(h->N, 0);
-  if (total <= budget) {
-    h->waves.emplace_back();
-    for (int j = 0; j < h->N; ++j) h->waves[0].members.push_back(j);
-  } else {
-    std::vector<int> order(h->N);
-    for (int j = 0; j < h->N; ++j) order[j] = j;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bytes[a] > bytes[b]; });
-    size_t used = 0;
-    for (int j : order) {
-      if (bytes[j] > budget) {
-        h->err = "a subdomain's factor storage exceeds the wave budget (msgfem_options.wave_mb)";
-        return MSGFEM_ENOMEM;
-      }
-      if (h->waves.empty() || used + bytes[j] > budget) {
-        h->waves.emplace_back();
-        used = 0;
-      }
-      h->waves.back().members.push_back(j);
-      used += bytes[j];
-    }
-    for (auto& w : h->waves) std::sort(w.members.begin(), w.members.end());
-  }
-  size_t pool = 0;
-  for (size_t w = 0; w < h->waves.size(); ++w) {
-    size_t sum = 0;
-    for (int j : h->waves[w].members) {
-      sum += bytes[j];
-      h->wave_of[j] = (int)w;
-    }
-    pool = std::max(pool, sum);
-  }
+  TRY(plan_waves(h, budget));
   char* base = nullptr;
-  TRY(dalloc(h, &base, pool));
+  TRY(dalloc(h, &base, h->pool_bytes));
   h->d_pool = base;
-  h->pool_bytes = pool;
   for (auto& w : h->waves) {
     size_t off = 0;
-    for (int j : w.members) {
-      SubDev& s = h->sub[j];
-      off += h->mixed ? place_blocks<float>(s, base + off, true) : place_blocks<double>(s, base + off, true);
-    }
+    for (int j : w.members) off += place_sub_blocks(h, j, base + off);
   }
   return MSGFEM_OK;
 }

@@ -269,6 +269,13 @@ void build_wave_factor_schedule(msgfem* h, WaveSched& w);
 void build_solve_schedules(msgfem* h);
 void build_wave_solve_schedules(msgfem* h, WaveSched& w);
 void build_coarse_schedules(msgfem* h);
+// device storage of one subdomain's layer blocks, factors and solve buffers
+// (bytes, and placement at base: pointers of sub[j] set), and the grouping of
+// the subdomains into waves that fit the byte budget (h->waves, h->wave_of,
+// h->pool_bytes = the largest wave)
+size_t sub_block_bytes(msgfem* h, int j);
+size_t place_sub_blocks(msgfem* h, int j, char* base);
+msgfem_status plan_waves(msgfem* h, size_t budget);
 
 // launchers
 void set_dense_context(int* active, int* notspd, const SubDev* subs);

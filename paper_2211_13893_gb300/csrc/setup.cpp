@@ -17,6 +17,7 @@
 #include <cstring>
 #include <map>
 #include <tuple>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -289,6 +290,100 @@ msgfem_status build_problem(msgfem* h) {
       const int y0 = std::max(S.oJ0, T.J0), y1 = std::min(S.oJ1, T.J1);
       if (x0 <= x1 && y0 <= y1) h->pairs.push_back({s, t, x0, x1, y0, y1});
     }
+  return MSGFEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device storage of the layer blocks (D, E, Linv of K and A11), their factors
+// and the compact solve buffers of one subdomain, in the factor's precision;
+// the parts are laid out in this order, each aligned to 256 bytes.
+namespace {
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+template <typename T>
+size_t place_blocks(SubDev& s, char* base, bool assign) {
+  const size_t bK2 = (size_t)s.bK * s.bK, bA2 = (size_t)s.bA * s.bA;
+  const size_t parts[12] = {bK2 * (2 * s.nzn - 1), bK2 * s.nzn, bA2 * (2 * s.nzn - 1), bA2 * s.nzn,
+                            (size_t)s.nzn * s.bK * PST, (size_t)s.nzn * s.bA * PST, (size_t)s.bK * PST,
+                            (size_t)s.bA * PST, (size_t)s.nzn * s.bK * KB, (size_t)s.nzn * s.bA * KB,
+                            (size_t)s.bK * KB, (size_t)s.bA * KB};
+  size_t off = 0;
+  T* p[12];
+  for (int i = 0; i < 12; ++i) {
+    p[i] = reinterpret_cast<T*>(base + off);
+    off = align_up(off + parts[i] * sizeof(T), 256);
+  }
+  if (assign) {
+    if constexpr (std::is_same<T, float>::value) {
+      s.DKf = p[0]; s.EKf = p[0] + bK2 * s.nzn; s.LKf = p[1];
+      s.DAf = p[2]; s.EAf = p[2] + bA2 * s.nzn; s.LAf = p[3];
+      s.ycKf = p[4]; s.ycAf = p[5]; s.rcKf = p[6]; s.rcAf = p[7];
+      s.ycK8f = p[8]; s.ycA8f = p[9]; s.rcK8f = p[10]; s.rcA8f = p[11];
+    } else {
+      s.DK = p[0]; s.EK = p[0] + bK2 * s.nzn; s.LK = p[1];
+      s.DA = p[2]; s.EA = p[2] + bA2 * s.nzn; s.LA = p[3];
+      s.ycK = p[4]; s.ycA = p[5]; s.rcK = p[6]; s.rcA = p[7];
+      s.ycK8 = p[8]; s.ycA8 = p[9]; s.rcK8 = p[10]; s.rcA8 = p[11];
+    }
+  }
+  return off;
+}
+
+}  // namespace
+
+size_t sub_block_bytes(msgfem* h, int j) {
+  SubDev& s = h->sub[j];
+  return h->mixed ? place_blocks<float>(s, nullptr, false) : place_blocks<double>(s, nullptr, false);
+}
+
+size_t place_sub_blocks(msgfem* h, int j, char* base) {
+  SubDev& s = h->sub[j];
+  return h->mixed ? place_blocks<float>(s, base, true) : place_blocks<double>(s, base, true);
+}
+
+// Subdomains are taken largest first and a wave is closed when the next one no
+// longer fits (waves of similar sizes); members are kept in index order.  When
+// everything fits: one wave of all subdomains.
+msgfem_status plan_waves(msgfem* h, size_t budget) {
+  std::vector<size_t> bytes(h->N);
+  size_t total = 0;
+  for (int j = 0; j < h->N; ++j) total += (bytes[j] = sub_block_bytes(h, j));
+  h->waves.clear();
+  h->wave_of.assign(h->N, 0);
+  if (total <= budget) {
+    h->waves.emplace_back();
+    for (int j = 0; j < h->N; ++j) h->waves[0].members.push_back(j);
+  } else {
+    std::vector<int> order(h->N);
+    for (int j = 0; j < h->N; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bytes[a] > bytes[b]; });
+    size_t used = 0;
+    for (int j : order) {
+      if (bytes[j] > budget) {
+        h->waves.clear();
+        h->err = "a subdomain's factor storage exceeds the wave budget (msgfem_options.wave_mb)";
+        return MSGFEM_ENOMEM;
+      }
+      if (h->waves.empty() || used + bytes[j] > budget) {
+        h->waves.emplace_back();
+        used = 0;
+      }
+      h->waves.back().members.push_back(j);
+      used += bytes[j];
+    }
+    for (auto& w : h->waves) std::sort(w.members.begin(), w.members.end());
+  }
+  size_t pool = 0;
+  for (size_t w = 0; w < h->waves.size(); ++w) {
+    size_t sum = 0;
+    for (int j : h->waves[w].members) {
+      sum += bytes[j];
+      h->wave_of[j] = (int)w;
+    }
+    pool = std::max(pool, sum);
+  }
+  h->pool_bytes = pool;
   return MSGFEM_OK;
 }
 

@@ -1,0 +1,188 @@
+"""The library's host-side set-up (setup.cpp, run on the CPU through the host
+harness) against the oracle: DoF classes B1/B2/B3 (Sec. 4.3), the partition of
+unity (Sec. 4.2), the consistent end-face load (Eq. up_r's right-hand side),
+and the 3-2-1 pins of floating subdomains (they must fix all six rigid
+motions, Sec. 5.1's floating local problems), on box beams and curved
+C-sections, plus the validation of explicit partition boxes and the grouping
+of subdomains into memory-bounded waves."""
+import numpy as np
+import pytest
+
+from tests.host import hostcheck as hc
+
+pytestmark = pytest.mark.skipif(hc.cuda_include() is None, reason="host harness needs the CUDA headers")
+
+CONFIGS = ("t1", "t2", "c1", "s1", "s2")
+
+
+def _cfg(name):
+    from workloads import get_config
+    return get_config(name)
+
+
+def _oracle(cfg):
+    from oracle.mesh import make_mesh
+    from oracle.partition import dof_classes, partition_of_unity, subdomains
+    mesh = make_mesh(cfg)
+    subs = subdomains(cfg)
+    mus = partition_of_unity(mesh, subs, cfg.overlap)
+    load = mesh.compression_load(cfg.traction)
+    return mesh, subs, mus, load, dof_classes
+
+
+def _local_nodes(mesh, s):
+    """Global node ids of Omega*_j in the library's local order n = k npl + q."""
+    i = np.arange(s["I0"], s["I1"] + 1)
+    j = np.arange(s["J0"], s["J1"] + 1)
+    k = np.arange(mesh.NZ + 1)
+    kk, ii, jj = np.meshgrid(k, i, j, indexing="ij")
+    return mesh.node_id(ii.ravel(), jj.ravel(), kk.ravel())
+
+
+@pytest.mark.parametrize("name", CONFIGS)
+def test_classes_pou_and_load_match_oracle(name):
+    cfg = _cfg(name)
+    hs = hc.HostSetup(cfg)
+    assert hs.status == 0, hs.error
+    mesh, subs, mus, load, dof_classes = _oracle(cfg)
+    assert hs.N == len(subs)
+    for j, sub in enumerate(subs):
+        s = hs.sub(j)
+        a = hs.arrays(j)
+        x0, x1, y0, y1 = sub.star
+        assert (s["I0"], s["I1"], s["J0"], s["J1"]) == (x0, x1, y0, y1)
+        assert (s["oI0"], s["oI1"], s["oJ0"], s["oJ1"]) == tuple(sub.omega)
+        nodes = _local_nodes(mesh, s)
+        # classes of the in-layer nodes (the same in every layer)
+        onodes, b1, b2, b3 = dof_classes(mesh, sub)
+        cls_o = np.where(b3, 3, np.where(b2, 2, 1))
+        lookup = dict(zip(onodes.tolist(), cls_o.tolist()))
+        assert [lookup[n] for n in nodes[:s["npl"]]] == a["cls"].tolist()
+        assert (s["n1"], s["n2"], s["n3"]) == (3 * b1.sum(), 3 * b2.sum(), 3 * b3.sum())
+        assert s["floating"] == int(not b3.any())
+        # partition of unity on the Omega* nodes (zero outside Omega_j)
+        np.testing.assert_allclose(a["mu"], mus[j][nodes], rtol=0, atol=1e-15)
+        # consistent nodal load of the end-face traction
+        ref = load.reshape(-1, 3)[nodes].reshape(-1)
+        np.testing.assert_allclose(a["load"], ref, rtol=1e-13, atol=1e-13 * np.abs(load).max())
+        # compact layer numberings: K keeps B1 + B2, A11 keeps B1, in layer order
+        keepK = [3 * q + c for q in range(s["npl"]) for c in range(3) if a["cls"][q] != 3]
+        keepA = [3 * q + c for q in range(s["npl"]) for c in range(3) if a["cls"][q] == 1]
+        assert a["mapK"][:s["nK"]].tolist() == keepK and (a["mapK"][s["nK"]:] == -1).all()
+        assert a["mapA"][:s["nA"]].tolist() == keepA and (a["mapA"][s["nA"]:] == -1).all()
+        assert s["bK"] % hc.TILE == 0 and s["bK"] >= s["nK"] and s["bA"] % hc.TILE == 0 and s["bA"] >= s["nA"]
+    hs.close()
+
+
+def _rigid_modes(X):
+    """The six rigid motions at points X (n x 3), as 3n x 6 (translations, rotations)."""
+    n = len(X)
+    R = np.zeros((3 * n, 6))
+    for c in range(3):
+        R[c::3, c] = 1.0
+    Xc = X - X.mean(axis=0)
+    for r, axis in enumerate(np.eye(3)):
+        R[:, 3 + r] = np.cross(axis, Xc).reshape(-1)
+    return R
+
+
+@pytest.mark.parametrize("name", CONFIGS + ("c4",))
+def test_pins_fix_all_rigid_motions(name):
+    """A floating subdomain's K is pinned at six DoFs: the pinned rows of the rigid
+    modes must be nonsingular (the pins remove every rigid motion), all pins
+    distinct DoFs of B1 or B2 on the bottom layer; a clamped one has none."""
+    cfg = _cfg(name)
+    hs = hc.HostSetup(cfg)
+    assert hs.status == 0, hs.error
+    from oracle.mesh import make_mesh
+    mesh = make_mesh(cfg)
+    nfloat = 0
+    for j in range(hs.N):
+        s = hs.sub(j)
+        pins = s["pins"]
+        if not s["floating"]:
+            assert pins == [-1] * 6
+            continue
+        nfloat += 1
+        assert len(set(pins)) == 6 and min(pins) >= 0
+        a = hs.arrays(j)
+        for p in pins:
+            q = p // 3
+            assert q < s["npl"] and a["cls"][q] != 3          # bottom layer, a kept DoF of K
+        nodes = _local_nodes(mesh, s)
+        R = _rigid_modes(mesh.coords(nodes))
+        sv = np.linalg.svd(R[pins], compute_uv=False)
+        assert sv[-1] > 1e-3 * sv[0], (j, sv)
+    assert nfloat > 0
+    hs.close()
+
+
+def test_batched_instances_repeat_the_partition():
+    cfg = _cfg("t2")
+    one = hc.HostSetup(cfg)
+    three = hc.HostSetup(cfg, instances=3)
+    assert three.N == 3 * one.N
+    for j in range(three.N):
+        assert three.sub(j) == one.sub(j % one.N)
+        a, b = three.arrays(j), one.arrays(j % one.N)
+        for k in a:
+            np.testing.assert_array_equal(a[k], b[k])
+
+
+@pytest.mark.parametrize("boxes, why", [
+    ([[0, 6, 0, 4], [5, 12, 0, 4]], "tile"),          # overlapping
+    ([[0, 6, 0, 4], [7, 12, 0, 4]], "tile"),          # a gap
+    ([[0, 6, 0, 4], [6, 13, 0, 4]], "outside"),       # beyond the mesh
+    ([[0, 12, 0, 4], [3, 3, 0, 4]], "empty"),         # empty box
+])
+def test_explicit_boxes_are_validated(boxes, why):
+    cfg = _cfg("t2")
+    hs = hc.HostSetup(cfg, boxes=np.array(boxes))
+    assert hs.status == 1 and why in hs.error, hs.error
+
+
+def test_explicit_boxes_equal_the_regular_partition():
+    cfg = _cfg("t2")
+    reg = hc.HostSetup(cfg)
+    boxes = [[a * cfg.NX // cfg.sx, (a + 1) * cfg.NX // cfg.sx, b * cfg.NY // cfg.sy, (b + 1) * cfg.NY // cfg.sy]
+             for a in range(cfg.sx) for b in range(cfg.sy)]
+    exp = hc.HostSetup(cfg, boxes=np.array(boxes))
+    assert exp.status == 0 and exp.N == reg.N
+    for j in range(reg.N):
+        assert exp.sub(j) == reg.sub(j)
+        np.testing.assert_array_equal(exp.arrays(j)["mu"], reg.arrays(j)["mu"])
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_waves_fit_the_budget(mixed):
+    """Every subdomain in exactly one wave, members ascending, every wave within
+    the budget, waves filled largest first; one wave when everything fits; a
+    subdomain larger than the budget is refused (ENOMEM)."""
+    cfg = _cfg("s2")
+    hs = hc.HostSetup(cfg, mixed=mixed)
+    sizes = np.array([hs.sub_bytes(j) for j in range(hs.N)])
+    assert (sizes % 256 == 0).all() and (sizes > 0).all()
+    assert hs.plan_waves(sizes.sum()) == 1
+    assert hs.members(0) == list(range(hs.N)) and hs.pool_bytes == sizes.sum()
+    for budget in (sizes.max(), 2 * sizes.max(), sizes.sum() // 3, sizes.sum() - 1):
+        nw = hs.plan_waves(budget)
+        assert nw >= 2
+        seen = []
+        fills = []
+        for w in range(nw):
+            m = hs.members(w)
+            assert m == sorted(m) and len(m) > 0
+            assert sizes[m].sum() <= budget
+            fills.append(sizes[m].sum())
+            seen += m
+        assert sorted(seen) == list(range(hs.N))
+        assert hs.pool_bytes == max(fills)
+        # largest first: the first wave holds the largest subdomain
+        assert int(np.argmax(sizes)) in hs.members(0)
+    assert hs.plan_waves(sizes.max() - 1) == -2          # ENOMEM
+    assert "wave budget" in hs.L.hc_error(hs.h).decode()
+    # the FP32 factors of the mixed path need about half the bytes
+    if mixed:
+        ref = hc.HostSetup(cfg, mixed=False)
+        r = np.array([ref.sub_bytes(j) for j in range(ref.N)])
+        assert (sizes < 0.6 * r).all()
