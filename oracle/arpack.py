@@ -11,6 +11,11 @@ of Eq. algebraicAharmonic,
 Here SciPy's ``eigsh`` (ARPACK) and ``splu`` (SuperLU, standing in for
 UMFPACK) are used with the shift sigma = -1e-2; eigenvectors come back
 normalised phi^T B phi = 1.  This is the timed CPU baseline of the local stage.
+
+The Lanczos start vector is a seeded Gaussian vector: a single-vector Krylov
+method sees each copy of a multiple eigenvalue (the six rigid zeros of a
+floating subdomain) only through rounding, so with ARPACK's own random start
+the number of zeros found could vary from call to call.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -25,7 +30,7 @@ def saddle_pencil(lp):
     return M, Bm
 
 
-def local_eigs_arpack(lp, n_loc, sigma=-1e-2, tol=1e-12):
+def local_eigs_arpack(lp, n_loc, sigma=-1e-2, tol=1e-12, seed=0):
     n1, n2 = len(lp.I1), len(lp.I2)
     if n2 == 0:
         return np.zeros(0), np.zeros((lp.n_star, 0))
@@ -33,7 +38,8 @@ def local_eigs_arpack(lp, n_loc, sigma=-1e-2, tol=1e-12):
     lu = spla.splu((M - sigma * Bm).tocsc())
     op = spla.LinearOperator(M.shape, matvec=lu.solve, dtype=np.float64)
     k = min(n_loc, n2)
-    lam, V = spla.eigsh(M, k=k, M=Bm, sigma=sigma, which="LM", OPinv=op, tol=tol,
+    v0 = np.random.default_rng(seed).standard_normal(M.shape[0])
+    lam, V = spla.eigsh(M, k=k, M=Bm, sigma=sigma, which="LM", OPinv=op, tol=tol, v0=v0,
                         ncv=min(M.shape[0] - 1, max(2 * k + 1, k + 20)))
     srt = np.argsort(lam)
     lam, V = lam[srt], V[:, srt]
