@@ -101,50 +101,11 @@ msgfem_status set_angles(msgfem* h, const double* ang) {
       h->err = "non-finite element angle";
       return MSGFEM_EINVAL;
     }
-  // element types: one per ply (and instance) when the angle depends on the
-  // layer only, else one per element (and instance)
-  // (node coordinates or ply frames make every element its own type)
-  bool layered = h->h_xyz.empty() && h->h_frame.empty();
-  for (size_t e = 0; e < ntot && layered; ++e)
-    layered = h->h_angles[e] == h->h_angles[(e / nel) * nel + e % h->NZ];
+  bool layered = false;
   std::vector<double> types;
-  const bool geometric = !h->h_xyz.empty() || !h->h_frame.empty();
   std::vector<int> etype, trep;
-  if (layered) {
-    for (int i = 0; i < h->S; ++i)
-      types.insert(types.end(), h->h_angles.begin() + (size_t)i * nel, h->h_angles.begin() + (size_t)i * nel + h->NZ);
-  } else if (geometric) {
-    // curved mesh: elements with the same shape (corners up to a translation),
-    // ply frame and angle share one element matrix; etype maps every element
-    // (instance-major) to its type, trep gives a type's first element
-    etype.resize(ntot);
-    std::unordered_map<std::string, int> seen;
-    std::string key;
-    for (size_t g = 0; g < ntot; ++g) {
-      const size_t e = g % nel;
-      const int ie = (int)(e / ((size_t)h->NY * h->NZ)), je = (int)((e / h->NZ) % h->NY), ke = (int)(e % h->NZ);
-      double v[34];
-      double X0[3];
-      node_xyz(h, ie, je, ke, X0);
-      for (int a = 0; a < 8; ++a) {
-        double X[3];
-        node_xyz(h, ie + (a & 1), je + ((a >> 1) & 1), ke + (a >> 2), X);
-        for (int d = 0; d < 3; ++d) v[3 * a + d] = X[d] - X0[d];
-      }
-      for (int q = 0; q < 9; ++q) v[24 + q] = h->h_frame.empty() ? 0.0 : h->h_frame[e * 9 + q];
-      v[33] = h->h_angles[g];
-      key.assign(reinterpret_cast<const char*>(v), sizeof(v));
-      auto it = seen.find(key);
-      if (it == seen.end()) {
-        it = seen.emplace(key, (int)types.size()).first;
-        types.push_back(h->h_angles[g]);
-        trep.push_back((int)e);
-      }
-      etype[g] = it->second;
-    }
-  } else {
-    types = h->h_angles;
-  }
+  element_types(h, layered, types, etype, trep);
+  const bool geometric = !h->h_xyz.empty() || !h->h_frame.empty();
   if ((int)types.size() > h->type_cap) {
     h->type_cap = (int)types.size();
     TRY(dalloc(h, &h->d_angles_type, types.size()));

@@ -276,6 +276,10 @@ void build_coarse_schedules(msgfem* h);
 size_t sub_block_bytes(msgfem* h, int j);
 size_t place_sub_blocks(msgfem* h, int j, char* base);
 msgfem_status plan_waves(msgfem* h, size_t budget);
+// element types of the angle field h->h_angles (per ply, per element shape /
+// frame / angle on curved meshes, or per element)
+void element_types(const msgfem* h, bool& layered, std::vector<double>& types, std::vector<int>& etype,
+                   std::vector<int>& trep);
 
 // launchers
 void set_dense_context(int* active, int* notspd, const SubDev* subs);

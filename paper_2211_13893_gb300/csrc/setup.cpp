@@ -18,6 +18,8 @@
 #include <map>
 #include <tuple>
 #include <type_traits>
+#include <unordered_map>
+#include <string>
 
 #include "internal.h"
 
@@ -291,6 +293,58 @@ msgfem_status build_problem(msgfem* h) {
       if (x0 <= x1 && y0 <= y1) h->pairs.push_back({s, t, x0, x1, y0, y1});
     }
   return MSGFEM_OK;
+}
+
+// Element types of the angle field in h->h_angles (one field per instance):
+// one per ply (and instance) when the angle depends on the layer only and the
+// mesh is the box with default frames (layered); on a curved mesh, elements
+// with the same shape (corners up to a translation, compared bit for bit),
+// ply frame and angle share one type, etype maps every element
+// (instance-major) to its type and trep gives a type's first element; else one
+// type per element.  types holds each type's angle.
+void element_types(const msgfem* h, bool& layered, std::vector<double>& types, std::vector<int>& etype,
+                   std::vector<int>& trep) {
+  const size_t nel = (size_t)h->NX * h->NY * h->NZ;
+  const size_t ntot = nel * h->S;
+  const bool geometric = !h->h_xyz.empty() || !h->h_frame.empty();
+  layered = !geometric;
+  for (size_t e = 0; e < ntot && layered; ++e)
+    layered = h->h_angles[e] == h->h_angles[(e / nel) * nel + e % h->NZ];
+  types.clear();
+  etype.clear();
+  trep.clear();
+  if (layered) {
+    for (int i = 0; i < h->S; ++i)
+      types.insert(types.end(), h->h_angles.begin() + (size_t)i * nel, h->h_angles.begin() + (size_t)i * nel + h->NZ);
+  } else if (geometric) {
+    etype.resize(ntot);
+    std::unordered_map<std::string, int> seen;
+    std::string key;
+    for (size_t g = 0; g < ntot; ++g) {
+      const size_t e = g % nel;
+      const int ie = (int)(e / ((size_t)h->NY * h->NZ)), je = (int)((e / h->NZ) % h->NY), ke = (int)(e % h->NZ);
+      double v[34];
+      double X0[3];
+      node_xyz(h, ie, je, ke, X0);
+      for (int a = 0; a < 8; ++a) {
+        double X[3];
+        node_xyz(h, ie + (a & 1), je + ((a >> 1) & 1), ke + (a >> 2), X);
+        for (int d = 0; d < 3; ++d) v[3 * a + d] = X[d] - X0[d];
+      }
+      for (int q = 0; q < 9; ++q) v[24 + q] = h->h_frame.empty() ? 0.0 : h->h_frame[e * 9 + q];
+      v[33] = h->h_angles[g];
+      key.assign(reinterpret_cast<const char*>(v), sizeof(v));
+      auto it = seen.find(key);
+      if (it == seen.end()) {
+        it = seen.emplace(key, (int)types.size()).first;
+        types.push_back(h->h_angles[g]);
+        trep.push_back((int)e);
+      }
+      etype[g] = it->second;
+    }
+  } else {
+    types = h->h_angles;
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -505,6 +505,27 @@ int hc_run_solve(void* p, int which, double* const* src, double* const* dst, int
   return 0;
 }
 
+// Element types of an angle field ([instances][NX NY NZ]) with optional ply
+// frames ([NX NY NZ][9]); types, etype and trep sized for one type per element.
+// Returns the number of types; *layered as the library decides it.
+int hc_element_types(void* p, const double* angles, const double* frames, int* layered, double* types, int* etype,
+                     int* trep) {
+  msgfem* h = &H(p)->h;
+  const size_t nel = (size_t)h->NX * h->NY * h->NZ, ntot = nel * h->S;
+  h->h_angles.assign(angles, angles + ntot);
+  if (frames != nullptr) h->h_frame.assign(frames, frames + 9 * nel);
+  else h->h_frame.clear();
+  bool lay = false;
+  std::vector<double> ty;
+  std::vector<int> et, tr;
+  element_types(h, lay, ty, et, tr);
+  *layered = lay ? 1 : 0;
+  memcpy(types, ty.data(), ty.size() * sizeof(double));
+  memcpy(etype, et.data(), et.size() * sizeof(int));
+  memcpy(trep, tr.data(), tr.size() * sizeof(int));
+  return (int)ty.size();
+}
+
 // A planted scheduling mistake, for checking the race check itself: step s of
 // group g merged with step s + 1 (two dependent launches made one).
 int hc_merge_steps(void* p, int which, int g, int s) {

@@ -87,6 +87,7 @@ def lib():
         L.hc_run_factor.argtypes = [vp, i, C.c_uint]
         L.hc_run_solve.argtypes = [vp, i, vp, vp, i, i, C.c_uint]
         L.hc_merge_steps.argtypes = [vp, i, i, i]
+        L.hc_element_types.argtypes = [vp, vp, vp, ip, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -205,6 +206,18 @@ class HostSetup:
         ps, _ = self._mv(src)
         pd, _ = self._mv(dst)
         assert self.L.hc_run_solve(self.h, which, ps, pd, int(gather_neg), int(scatter_add), seed) == 0
+
+    def element_types(self, angles, frames=None):
+        """(layered, types, etype, trep) of an angle field, as the library decides them."""
+        ang = np.ascontiguousarray(angles, dtype=np.float64).reshape(-1)
+        fr = None if frames is None else np.ascontiguousarray(frames, dtype=np.float64).reshape(-1)
+        n = len(ang)
+        types = np.zeros(n)
+        etype = np.full(n, -1, dtype=np.int32)
+        trep = np.full(n, -1, dtype=np.int32)
+        lay = C.c_int()
+        nt = self.L.hc_element_types(self.h, _p(ang), _p(fr), C.byref(lay), _p(types), _p(etype), _p(trep))
+        return bool(lay.value), types[:nt], etype, trep[:nt]
 
     def merge_steps(self, which, group, step):
         return self.L.hc_merge_steps(self.h, which, group, step)

@@ -3,8 +3,9 @@ harness) against the oracle: DoF classes B1/B2/B3 (Sec. 4.3), the partition of
 unity (Sec. 4.2), the consistent end-face load (Eq. up_r's right-hand side),
 and the 3-2-1 pins of floating subdomains (they must fix all six rigid
 motions, Sec. 5.1's floating local problems), on box beams and curved
-C-sections, plus the validation of explicit partition boxes and the grouping
-of subdomains into memory-bounded waves."""
+C-sections, plus the validation of explicit partition boxes, the grouping
+of subdomains into memory-bounded waves and the element types that share one
+element matrix."""
 import numpy as np
 import pytest
 
@@ -186,3 +187,67 @@ def test_waves_fit_the_budget(mixed):
         ref = hc.HostSetup(cfg, mixed=False)
         r = np.array([ref.sub_bytes(j) for j in range(ref.N)])
         assert (sizes < 0.6 * r).all()
+
+
+@pytest.mark.parametrize("name", ["s1", "s2"])
+def test_curved_element_types_share_one_stiffness(name):
+    """On a curved mesh, elements the library gives one type have the same oracle
+    element matrix (Eq. element_stiffness with their own corners, frame and
+    angle); elements of different types differ in shape, frame or angle; the
+    types are exactly the distinct (relative corners, frame, angle) keys."""
+    from oracle.element import hex_stiffness
+    from oracle.material import rotated_tensor
+    from oracle.mesh import make_mesh
+    from workloads import element_angles
+    cfg = _cfg(name)
+    mesh = make_mesh(cfg)
+    ang = element_angles(cfg)
+    hs = hc.HostSetup(cfg)
+    layered, types, etype, trep = hs.element_types(ang, mesh.frames)
+    assert not layered and etype.min() == 0 and etype.max() == len(types) - 1
+    nel = cfg.NX * cfg.NY * cfg.NZ
+    ii, jj, kk = np.unravel_index(np.arange(nel), (cfg.NX, cfg.NY, cfg.NZ))
+    keys = {}
+    for e in range(nel):
+        X = mesh.element_corners(ii[e], jj[e], kk[e])
+        key = ((X - X[0]).tobytes(), mesh.frames[ii[e], jj[e], kk[e]].tobytes(), float(ang.reshape(-1)[e]))
+        keys.setdefault(key, set()).add(int(etype[e]))
+    assert all(len(v) == 1 for v in keys.values())               # one type per key
+    assert len(keys) == len(types)                               # and one key per type
+    assert (etype[trep] == np.arange(len(types))).all()          # a type's first element carries it
+    assert np.array_equal(types, ang.reshape(-1)[trep])
+    assert len(types) < nel                                      # the curved mesh still repeats shapes
+    E = cfg.material
+    rng = np.random.default_rng(0)
+    for t in rng.choice(len(types), size=min(12, len(types)), replace=False):
+        members = np.nonzero(etype == t)[0]
+        r = trep[t]
+        Kr = hex_stiffness(mesh.element_corners(ii[r], jj[r], kk[r]),
+                           rotated_tensor(E, float(types[t]), mesh.frames[ii[r], jj[r], kk[r]]))
+        for e in members[:: max(1, len(members) // 5)]:
+            Ke = hex_stiffness(mesh.element_corners(ii[e], jj[e], kk[e]),
+                               rotated_tensor(E, float(ang.reshape(-1)[e]), mesh.frames[ii[e], jj[e], kk[e]]))
+            assert np.abs(Ke - Kr).max() <= 1e-12 * np.abs(Kr).max()
+
+
+def test_box_beam_element_types():
+    """Box beam: an angle field that depends on the ply only gives one type per
+    ply and instance (layered); one element off its ply's angle gives one type
+    per element; ply frames make the mesh curved-typed (shape, frame, angle)."""
+    from workloads import element_angles
+    cfg = _cfg("t2")
+    nel = cfg.NX * cfg.NY * cfg.NZ
+    ang = element_angles(cfg).reshape(-1)
+    hs = hc.HostSetup(cfg, instances=2)
+    two = np.concatenate([ang, ang + 15.0])
+    layered, types, etype, trep = hs.element_types(two)
+    assert layered and np.array_equal(types, np.concatenate([ang[:cfg.NZ], ang[:cfg.NZ] + 15.0]))
+    bad = two.copy()
+    bad[nel + 7] += 1.0
+    layered, types, _, _ = hs.element_types(bad)
+    assert not layered and np.array_equal(types, bad)
+    frames = np.broadcast_to(np.eye(3), (nel, 3, 3))
+    one = hc.HostSetup(cfg)
+    layered, types, etype, trep = one.element_types(ang, frames)
+    assert not layered and len(types) == len(np.unique(ang[:cfg.NZ]))   # congruent bricks: one type per angle
+    assert np.array_equal(types[etype[:nel]], ang)
