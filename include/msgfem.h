@@ -41,7 +41,10 @@
  * Errors.  Every call returns a status; msgfem_last_error gives a message.
  * Calls must come in the order setup -> local_spaces -> coarse_assemble ->
  * solve (MSGFEM_ESTATE otherwise); local_spaces may be repeated after
- * msgfem_update_angles.  A handle is not thread-safe.
+ * msgfem_update_angles.  Repeating a step discards the later ones: once a
+ * repeated local_spaces (or coarse_assemble) call has accepted its
+ * arguments, coarse_assemble (or solve) has to run again, also if the call
+ * then fails.  A handle is not thread-safe.
  */
 #ifndef MSGFEM_H
 #define MSGFEM_H

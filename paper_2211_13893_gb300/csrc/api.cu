@@ -908,6 +908,17 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
     if (n_loc > h->n2[j]) { h->err = "n_loc exceeds the B2 size of a subdomain"; return MSGFEM_EINVAL; }
     if (nw > p) { h->err = "n_loc too large for the block size (at most 31 columns)"; return MSGFEM_EINVAL; }
   }
+  if (h->opt.solver == 1 && h->mixed) {
+    h->err = "subspace iteration (solver = 1) runs in FP64 only";
+    return MSGFEM_EINVAL;
+  }
+  if (h->opt.solver == 1 && h->waves.size() > 1) {
+    h->err = "subspace iteration (solver = 1) needs every subdomain resident (one wave)";
+    return MSGFEM_EINVAL;
+  }
+  // from here on the earlier local spaces, coarse problem and solution are
+  // being replaced: a failure leaves the handle needing a new local stage
+  h->stage = 1;
   h->n_loc = n_loc;
   h->p = p;
   cudaStream_t st = h->stream;
@@ -921,14 +932,6 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   h->prof.solve_bytes = 0.0;
   h->prof.stencil_flops = 0.0;
   h->prof.solve_calls = 0;
-  if (h->opt.solver == 1 && h->mixed) {
-    h->err = "subspace iteration (solver = 1) runs in FP64 only";
-    return MSGFEM_EINVAL;
-  }
-  if (h->opt.solver == 1 && h->waves.size() > 1) {
-    h->err = "subspace iteration (solver = 1) needs every subdomain resident (one wave)";
-    return MSGFEM_EINVAL;
-  }
   // 1. assembly: element stiffness and the node stencils of every subdomain
   int sp = span_begin(h, TAG_ASSEMBLE);
   launch_element_stiffness(h);
@@ -1060,6 +1063,7 @@ msgfem_status msgfem_coarse_assemble_threshold(msgfem_h h, double t, int* coarse
     h->err = "a handle with batched instances runs the local stage only";
     return MSGFEM_EINVAL;
   }
+  h->stage = 2;   // an earlier coarse problem and solution are being replaced
   cudaStream_t st = h->stream;
   const int n_loc = h->n_loc;
   set_dense_context(h->d_flags, h->d_notspd, h->d_sub);
