@@ -30,6 +30,8 @@ primitives (sparse LU, dense Cholesky, symmetric eigensolvers) as steps:
   basis sizes from n_loc or from the eigenvalue threshold (Sec. 5.5).
 * ``fine``      the fine-scale FE solution u_h (Eq. fe_matrix_system) by a
   direct sparse solve.
+* ``errors``    the relative L2 errors e_d and e_eps of the displacement and
+  strain fields (Sec. 5.4).
 
 Parity pins live in ``tests/test_oracle_*.py``.
 """
