@@ -289,6 +289,21 @@ msgfem_status msgfem_get_basis(msgfem_h h, int j, double* phi_out, int* rows, in
  * threads) race on the array and must be serialised by the caller. */
 msgfem_status msgfem_energy_error_noalloc(msgfem_h h, const double* u, const double* u_ref, double* energy_err_out);
 
+/* Relative L2 errors (Sec. 5.4) of the coarse solution u^G of the last
+ * msgfem_solve against a reference u_ref ([3 n_nodes] doubles, node-major as
+ * u_out of msgfem_solve; host or device; copied):
+ *   errors_out[0] = e_d   = ||u_ref - u^G|| / ||u_ref||,
+ *   errors_out[1] = e_eps = ||eps(u_ref - u^G)|| / ||eps(u_ref)||,
+ * with the norms of L2(Omega) of the finite element fields, integrated over
+ * every element by 2x2x2 Gauss quadrature through its trilinear map (node
+ * coordinates or the box), and eps : eps (tensor components) as the strain's
+ * pointwise square.  The paper writes ||.||_2 without saying whether the
+ * vector or the field norm is meant; the field norm is taken.  errors_out: 2
+ * doubles, host.  A reference with zero norm gives 0.  Errors: EINVAL (NULL
+ * argument), ESTATE (no msgfem_solve since the last local stage or coarse
+ * assembly), ECUDA. */
+msgfem_status msgfem_solution_errors(msgfem_h h, const double* u_ref, double* errors_out);
+
 /* Autotuner of the block-solve launches (not in the paper: a library
  * convenience for batches of uneven subdomains).  On the subdomains of the
  * last wave of the previous msgfem_local_spaces call it first times the

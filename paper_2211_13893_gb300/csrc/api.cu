@@ -278,6 +278,7 @@ msgfem_status allocate(msgfem* h) {
   TRY(dalloc(h, &h->d_u, ndof));
   TRY(dalloc(h, &h->d_ref, ndof));
   TRY(dalloc(h, &h->d_energy, 2 * 1024));
+  TRY(dalloc(h, &h->d_l2, 4 * 1024));
   // schedules
   build_factor_schedule(h);
   build_solve_schedules(h);

@@ -242,6 +242,7 @@ struct msgfem {
   double* d_u = nullptr;
   double* d_ref = nullptr;
   double* d_energy = nullptr;
+  double* d_l2 = nullptr;            // [1024][4] block sums of the L2 errors (msgfem_solution_errors)
   Schedule cfact;
   SolveSchedule csolve;
   int n_loc = 0, p = 0;

@@ -16,7 +16,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTSPD", 5: "ENOCO
 EXPORTS = ("msgfem_setup", "msgfem_update_angles", "msgfem_local_spaces", "msgfem_coarse_assemble",
            "msgfem_solve", "msgfem_get_basis", "msgfem_get_info", "msgfem_num_subdomains",
            "msgfem_get_profile", "msgfem_reset_profile", "msgfem_energy_error_noalloc", "msgfem_last_error",
-           "msgfem_autotune", "msgfem_coarse_assemble_threshold",
+           "msgfem_autotune", "msgfem_coarse_assemble_threshold", "msgfem_solution_errors",
            "msgfem_destroy",
            # include/msgfem_warm.h
            "msgfem_net_create", "msgfem_net_param_count", "msgfem_net_get_params", "msgfem_net_set_params",
@@ -96,6 +96,7 @@ def load_library(path=LIB_PATH):
         "msgfem_get_profile": (C.c_int, [h, C.POINTER(Profile)]),
         "msgfem_autotune": (C.c_int, [h, C.c_int, C.POINTER(Tuning)]),
         "msgfem_energy_error_noalloc": (C.c_int, [h, C.c_void_p, C.c_void_p, C.c_void_p]),
+        "msgfem_solution_errors": (C.c_int, [h, C.c_void_p, C.POINTER(C.c_double)]),
         "msgfem_reset_profile": (C.c_int, [h]),
         "msgfem_num_subdomains": (C.c_int, [h]),
         "msgfem_last_error": (C.c_char_p, [h]),
@@ -217,6 +218,15 @@ class MSGFEM:
             u_ref = np.ascontiguousarray(u_ref, dtype=np.float64)
         self._check(self.lib.msgfem_solve(self.h, _ptr(u), _ptr(u_ref), C.byref(err)))
         return u, (err.value if u_ref is not None else None)
+
+    def solution_errors(self, u_ref):
+        """(e_d, e_eps): relative L2 errors of the last coarse solution against
+        u_ref (numpy array or device tensor), include/msgfem.h msgfem_solution_errors."""
+        if not hasattr(u_ref, "data_ptr"):
+            u_ref = np.ascontiguousarray(u_ref, dtype=np.float64)
+        out = (C.c_double * 2)()
+        self._check(self.lib.msgfem_solution_errors(self.h, _ptr(u_ref), out))
+        return float(out[0]), float(out[1])
 
     def basis(self, j):
         rows, cols, box = C.c_int(), C.c_int(), (C.c_int * 4)()
