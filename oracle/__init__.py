@@ -32,6 +32,8 @@ primitives (sparse LU, dense Cholesky, symmetric eigensolvers) as steps:
   direct sparse solve.
 * ``errors``    the relative L2 errors e_d and e_eps of the displacement and
   strain fields (Sec. 5.4).
+* ``geneo``     the GenEO local eigenproblem and coarse space, the paper's
+  comparison method (Sec. 2.3, Eq. bilinearGeneralizeEigenProblem).
 
 Parity pins live in ``tests/test_oracle_*.py``.
 """
