@@ -526,6 +526,19 @@ int hc_element_types(void* p, const double* angles, const double* frames, int* l
   return (int)ty.size();
 }
 
+// Coarse pairs (s, t, x0, x1, y0, y1): the node box of Omega_s cap Omega*_t over
+// which the block A^H_{st} is accumulated.  out: 6 ints per pair (NULL: count only).
+int hc_pairs(void* p, int* out) {
+  const msgfem& h = H(p)->h;
+  if (out != nullptr)
+    for (size_t i = 0; i < h.pairs.size(); ++i) {
+      const CoarsePair& c = h.pairs[i];
+      const int v[6] = {c.s, c.t, c.x0, c.x1, c.y0, c.y1};
+      memcpy(out + 6 * i, v, sizeof v);
+    }
+  return (int)h.pairs.size();
+}
+
 // A planted scheduling mistake, for checking the race check itself: step s of
 // group g merged with step s + 1 (two dependent launches made one).
 int hc_merge_steps(void* p, int which, int g, int s) {

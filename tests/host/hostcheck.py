@@ -88,6 +88,7 @@ def lib():
         L.hc_run_solve.argtypes = [vp, i, vp, vp, i, i, C.c_uint]
         L.hc_merge_steps.argtypes = [vp, i, i, i]
         L.hc_element_types.argtypes = [vp, vp, vp, ip, vp, vp, vp]
+        L.hc_pairs.argtypes = [vp, vp]
         _lib = L
     return _lib
 
@@ -218,6 +219,13 @@ class HostSetup:
         lay = C.c_int()
         nt = self.L.hc_element_types(self.h, _p(ang), _p(fr), C.byref(lay), _p(types), _p(etype), _p(trep))
         return bool(lay.value), types[:nt], etype, trep[:nt]
+
+    def pairs(self):
+        """Coarse pairs as an (n, 6) array: s, t and the node box x0, x1, y0, y1."""
+        n = self.L.hc_pairs(self.h, None)
+        out = np.zeros((n, 6), dtype=np.int32)
+        self.L.hc_pairs(self.h, _p(out))
+        return out
 
     def merge_steps(self, which, group, step):
         return self.L.hc_merge_steps(self.h, which, group, step)

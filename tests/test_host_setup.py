@@ -251,3 +251,32 @@ def test_box_beam_element_types():
     layered, types, etype, trep = one.element_types(ang, frames)
     assert not layered and len(types) == len(np.unique(ang[:cfg.NZ]))   # congruent bricks: one type per angle
     assert np.array_equal(types[etype[:nel]], ang)
+
+
+@pytest.mark.parametrize("name", ["t2", "c1", "s1", "s2"])
+def test_coarse_pairs_cover_every_coupling(name):
+    """A^H_{st} = V_s^T A V_t couples nodes p with mu_s(p) > 0 to nodes q with
+    mu_t(q) > 0 that share an element with p (oracle partition of unity).  Every
+    such (s, t) must be a coarse pair of the library, and all such nodes p must
+    lie in the pair's node box, over which the block is accumulated."""
+    cfg = _cfg(name)
+    hs = hc.HostSetup(cfg)
+    mesh, subs, mus, _, _ = _oracle(cfg)
+    pairs = {(int(r[0]), int(r[1])): r[2:] for r in hs.pairs()}
+    shape = (cfg.NX + 1, cfg.NY + 1, cfg.NZ + 1)
+    pos = [(mu > 0).reshape(shape) for mu in mus]
+    for t, pt in enumerate(pos):
+        # nodes sharing an element with the support of mu_t (index-space neighbours)
+        near = np.zeros(shape, dtype=bool)
+        padded = np.pad(pt, 1)
+        for di in (-1, 0, 1):
+            for dj in (-1, 0, 1):
+                for dk in (-1, 0, 1):
+                    near |= padded[1 + di:1 + di + shape[0], 1 + dj:1 + dj + shape[1], 1 + dk:1 + dk + shape[2]]
+        for s, ps in enumerate(pos):
+            I, J, _ = np.nonzero(ps & near)
+            if len(I) == 0:
+                continue
+            assert (s, t) in pairs, (s, t)
+            x0, x1, y0, y1 = pairs[s, t]
+            assert I.min() >= x0 and I.max() <= x1 and J.min() >= y0 and J.max() <= y1, (s, t)
