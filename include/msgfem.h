@@ -155,6 +155,17 @@ typedef struct {
                            depend on the grouping.  0 = 80 % of the device memory free at
                            set-up less room for the element matrices (one wave when everything
                            fits).  ENOMEM if one subdomain alone exceeds it */
+  /* Device memory of the handle from the caller's allocator: dev_alloc(bytes, alloc_ctx)
+     returns device memory of the current device, at least 256-byte aligned, or NULL
+     (ENOMEM); dev_free(p, bytes, alloc_ctx) takes back a block (bytes as allocated).  Both
+     are called on the thread of the API call, during msgfem_setup, msgfem_update_angles,
+     msgfem_local_spaces, msgfem_autotune, msgfem_get_basis and msgfem_destroy; the
+     library synchronises its stream before it frees a block.  Both NULL: cudaMalloc and
+     cudaFree.  One of them NULL: EINVAL.  (The network handles of msgfem_warm.h and the
+     fixed scratch array of msgfem_energy_error_noalloc do not use them.) */
+  void* (*dev_alloc)(size_t bytes, void* alloc_ctx);
+  void (*dev_free)(void* p, size_t bytes, void* alloc_ctx);
+  void* alloc_ctx;
 } msgfem_options;
 
 /* Phase timers (CUDA events on the handle's stream, milliseconds, summed over

@@ -51,31 +51,61 @@ msgfem_status cuda_fail(msgfem* h, cudaError_t e, const char* what, const char* 
 }
 
 
+// Device memory of the handle: the caller's allocator (msgfem_options.dev_alloc
+// / dev_free) or cudaMalloc / cudaFree; every block is recorded with its size in
+// h->allocs and released by msgfem_destroy.
+msgfem_status dev_alloc_bytes(msgfem* h, void** out, size_t bytes) {
+  bytes = std::max<size_t>(bytes, 1);
+  void* ptr = nullptr;
+  if (h->opt.dev_alloc != nullptr) {
+    ptr = h->opt.dev_alloc(bytes, h->opt.alloc_ctx);
+    if (ptr == nullptr) {
+      h->err = "the caller's allocator returned NULL for " + std::to_string(bytes) + " bytes";
+      return MSGFEM_ENOMEM;
+    }
+    if (reinterpret_cast<uintptr_t>(ptr) % 256 != 0) {
+      h->opt.dev_free(ptr, bytes, h->opt.alloc_ctx);
+      h->err = "the caller's allocator returned a block that is not 256-byte aligned";
+      return MSGFEM_EINVAL;
+    }
+  } else {
+    cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e != cudaSuccess) {
+      h->err = "cudaMalloc failed for " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e);
+      return MSGFEM_ENOMEM;
+    }
+  }
+  h->allocs.emplace_back(ptr, bytes);
+  *out = ptr;
+  return MSGFEM_OK;
+}
+
+void dev_free_bytes(msgfem* h, void* p) {
+  if (p == nullptr) return;
+  auto it = std::find_if(h->allocs.begin(), h->allocs.end(),
+                         [p](const std::pair<void*, size_t>& a) { return a.first == p; });
+  if (it == h->allocs.end()) return;
+  if (h->opt.dev_free != nullptr) {
+    cudaStreamSynchronize(h->stream);   // the block may still be read by queued work
+    h->opt.dev_free(p, it->second, h->opt.alloc_ctx);
+  } else {
+    cudaFree(p);
+  }
+  h->allocs.erase(it);
+}
+
 namespace {
 
 template <typename T>
 msgfem_status dalloc(msgfem* h, T** p, size_t count) {
   void* ptr = nullptr;
-  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-  cudaError_t e = cudaMalloc(&ptr, bytes);
-  if (e != cudaSuccess) {
-    h->err = "cudaMalloc failed for " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e);
-    return MSGFEM_ENOMEM;
-  }
-  h->allocs.push_back(ptr);
+  TRY(dev_alloc_bytes(h, &ptr, std::max<size_t>(count, 1) * sizeof(T)));
   *p = static_cast<T*>(ptr);
   return MSGFEM_OK;
 }
 
 // Release one allocation made by dalloc (task lists replaced by the autotuner).
-void dfree(msgfem* h, void* p) {
-  if (p == nullptr) return;
-  auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
-  if (it == h->allocs.end()) return;
-  cudaFree(p);
-  h->allocs.erase(it);
-}
-
+void dfree(msgfem* h, void* p) { dev_free_bytes(h, p); }
 
 bool is_device_ptr(const void* p) {
   if (p == nullptr) return false;
@@ -856,6 +886,13 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
     return MSGFEM_EINVAL;
   }
   h->factor_left = h->opt.factor_schedule;
+  if ((h->opt.dev_alloc == nullptr) != (h->opt.dev_free == nullptr)) {
+    h->opt.dev_alloc = nullptr;
+    h->opt.dev_free = nullptr;
+    *out = h;
+    h->err = "dev_alloc and dev_free must be given together";
+    return MSGFEM_EINVAL;
+  }
   if (h->opt.precision != MSGFEM_FP64 && h->opt.precision != MSGFEM_MIXED) {
     h->err = "unknown precision";
     return MSGFEM_EINVAL;
@@ -1197,13 +1234,14 @@ msgfem_status msgfem_get_basis(msgfem_h h, int j, double* phi_out, int* rows, in
   if (cols) *cols = h->n_loc;
   if (box_out) { box_out[0] = s.I0; box_out[1] = s.I1; box_out[2] = s.J0; box_out[3] = s.J1; }
   if (phi_out) {
-    double* tmp = nullptr;
+    void* buf = nullptr;
     const size_t n = (size_t)s.nfull * h->n_loc;
-    CK(cudaMalloc(&tmp, n * sizeof(double)));
+    TRY(dev_alloc_bytes(h, &buf, n * sizeof(double)));
+    double* tmp = static_cast<double*>(buf);
     launch_basis_out(h, j, tmp, h->n_loc);
     cudaError_t e = cudaMemcpyAsync(phi_out, tmp, n * sizeof(double), cudaMemcpyDefault, h->stream);
     cudaError_t e2 = cudaStreamSynchronize(h->stream);
-    cudaFree(tmp);
+    dev_free_bytes(h, tmp);
     CK(e);
     CK(e2);
   }
@@ -1398,7 +1436,10 @@ void msgfem_destroy(msgfem_h h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
-  for (void* p : h->allocs) cudaFree(p);
+  for (const auto& a : h->allocs) {
+    if (h->opt.dev_free != nullptr) h->opt.dev_free(a.first, a.second, h->opt.alloc_ctx);
+    else cudaFree(a.first);
+  }
   for (auto& sp : h->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
   for (int g = 0; g < NGROUP; ++g) {
     if (h->gs.s[g]) cudaStreamDestroy(h->gs.s[g]);

@@ -201,7 +201,7 @@ struct msgfem {
   std::vector<int> act_host;         // host copy of the active flags last uploaded
   std::vector<int> base_act;         // members of the wave being processed (all ones: one wave)
   std::vector<double> resid_max;
-  std::vector<void*> allocs;
+  std::vector<std::pair<void*, size_t>> allocs;   // device blocks of the handle and their sizes
   SubDev* d_sub = nullptr;
   double* d_E9 = nullptr;
   double* d_angles_type = nullptr;   // [ntypes]
@@ -262,6 +262,10 @@ struct msgfem {
 extern long long g_launch_count;   // kernel launches issued by this library
 
 msgfem_status cuda_fail(msgfem* h, cudaError_t e, const char* what, const char* file, int line);
+// device memory of the handle (msgfem_options.dev_alloc / dev_free, or cudaMalloc /
+// cudaFree), recorded in h->allocs and released by msgfem_destroy
+msgfem_status dev_alloc_bytes(msgfem* h, void** out, size_t bytes);
+void dev_free_bytes(msgfem* h, void* p);
 
 // host scheduling (setup.cpp)
 msgfem_status build_problem(msgfem* h);

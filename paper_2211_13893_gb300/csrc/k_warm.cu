@@ -158,9 +158,9 @@ msgfem_status warm_rows(msgfem* h) {
       h->err = "interface row count does not match the DoF classes";
       return MSGFEM_ESTATE;
     }
-    int* d = nullptr;
-    CK(cudaMalloc(&d, std::max<size_t>(1, rows.size()) * sizeof(int)));
-    h->allocs.push_back(d);
+    void* buf = nullptr;
+    TRY(dev_alloc_bytes(h, &buf, std::max<size_t>(1, rows.size()) * sizeof(int)));
+    int* d = static_cast<int*>(buf);
     if (!rows.empty()) CK(cudaMemcpy(d, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice));
     h->d_b2rows[j] = d;
   }
@@ -175,10 +175,7 @@ bool warm_upload(msgfem* h) {
   std::vector<WarmDev> wd(h->N);
   for (int j = 0; j < h->N; ++j)
     wd[j] = {h->warm[j].X0, h->warm[j].ld, h->warm[j].ncols, h->n2[j], h->d_b2rows[j]};
-  if (h->d_warm == nullptr) {
-    if (cudaMalloc(&h->d_warm, h->N * sizeof(WarmDev)) != cudaSuccess) return false;
-    h->allocs.push_back(h->d_warm);
-  }
+  if (h->d_warm == nullptr && dev_alloc_bytes(h, &h->d_warm, h->N * sizeof(WarmDev)) != MSGFEM_OK) return false;
   cudaMemcpyAsync(h->d_warm, wd.data(), h->N * sizeof(WarmDev), cudaMemcpyHostToDevice, h->stream);
   cudaStreamSynchronize(h->stream);
   return true;

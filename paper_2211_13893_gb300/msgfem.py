@@ -47,7 +47,13 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("block", C.c_int), ("max_iter", C.c_int), ("tol", C.c_double),
                 ("seed", C.c_ulonglong), ("stream", C.c_void_p), ("profile", C.c_int), ("solver", C.c_int),
                 ("streams", C.c_int), ("refine", C.c_int), ("instances", C.c_int), ("solve_kernel", C.c_int),
-                ("factor_schedule", C.c_int), ("direct_launch", C.c_int), ("wave_mb", C.c_double)]
+                ("factor_schedule", C.c_int), ("direct_launch", C.c_int), ("wave_mb", C.c_double),
+                ("dev_alloc", C.c_void_p), ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p)]
+
+
+# msgfem_options.dev_alloc / dev_free
+DEV_ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+DEV_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
 
 
 class Tuning(C.Structure):
@@ -142,7 +148,9 @@ class MSGFEM:
     def __init__(self, nx, ny, nz, hx, hy, hz, traction, E9, elem_angles, sx, sy, overlap, oversampling,
                  block=0, max_iter=0, tol=0.0, seed=0, stream=None, precision=0, profile=0, solver=0, streams=0, refine=0,
                  instances=0, xyz=None, frames=None, boxes=None, wave_mb=0.0, solve_kernel=0,
-                 factor_schedule=0, direct_launch=0):
+                 factor_schedule=0, direct_launch=0, allocator=None):
+        """``allocator``: optional pair (alloc(nbytes) -> device address, free(address,
+        nbytes)) through which the handle takes all its device memory."""
         self.lib = load_library()
         self.h = C.c_void_p()
         self._E9 = np.ascontiguousarray(E9, dtype=np.float64)
@@ -160,6 +168,13 @@ class MSGFEM:
         part = Partition(sx, sy, nb, _ptr(self._boxes))
         opt = Options(precision, block, max_iter, tol, seed, stream, profile, solver, streams, refine, instances,
                       solve_kernel, factor_schedule, direct_launch, wave_mb)
+        if allocator is not None:
+            alloc, free = allocator
+            # the callbacks must outlive the handle: kept on the instance
+            self._alloc_cb = DEV_ALLOC(lambda n, ctx: alloc(n) or None)
+            self._free_cb = DEV_FREE(lambda p, n, ctx: free(p, n))
+            opt.dev_alloc = C.cast(self._alloc_cb, C.c_void_p).value
+            opt.dev_free = C.cast(self._free_cb, C.c_void_p).value
         self.instances = max(1, instances)
         st = self.lib.msgfem_setup(C.byref(self.mesh), C.byref(plies), C.byref(part), overlap, oversampling,
                                    C.byref(opt), C.byref(self.h))
