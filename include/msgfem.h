@@ -81,6 +81,12 @@ typedef struct {
   double traction;      /* magnitude of the compressive traction on x = L (MPa): the load is
                            the consistent nodal force of (-traction, 0, 0) over the i = nx face */
   const double* xyz;    /* NULL (box) or [(nx+1)(ny+1)(nz+1)][3] node coordinates */
+  const double* load;   /* NULL: the traction above.  Else the right-hand side b of Eq.
+                           fe_matrix_system as nodal forces, [(nx+1)(ny+1)(nz+1)][3] in the
+                           global node order (host or device pointer, copied during
+                           msgfem_setup; traction ignored); entries on the clamped face have
+                           no effect.  A subdomain gets a particular function (Eq. up_r)
+                           when the load has a non-zero entry on its B1 DoFs. */
 } msgfem_mesh;
 
 /* Orthotropic ply material and fibre angles (Sec. 5.1).

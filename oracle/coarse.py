@@ -83,11 +83,12 @@ class MSGFEMResult:
 
 
 def run_msgfem(cfg, angles=None, n_loc=None, variant="ii", solver="dense", uh=None,
-               keep_problems=False, threshold=None):
+               keep_problems=False, threshold=None, load=None):
     """MS-GFEM with n_loc eigenvectors per subdomain, or, with ``threshold`` t,
     the eigenvectors with 1 / lambda > t among the n_loc computed (Sec. 5.5,
     Sec. 5.6: the local basis sizes m_j follow from a threshold on the
-    reciprocal eigenvalues)."""
+    reciprocal eigenvalues).  ``load``: nodal forces replacing the end-face
+    traction as the right-hand side b."""
     mesh = make_mesh(cfg)
     E = cfg.material
     if angles is None:
@@ -95,7 +96,7 @@ def run_msgfem(cfg, angles=None, n_loc=None, variant="ii", solver="dense", uh=No
     n_loc = cfg.n_loc if n_loc is None else n_loc
     cache = make_cache(mesh, E)
     A = assemble_global(mesh, angles, E, cache=cache)
-    b = mesh.compression_load(cfg.traction)
+    b = mesh.compression_load(cfg.traction) if load is None else np.asarray(load, dtype=np.float64).copy()
     subs = subdomains(cfg)
     mus = partition_of_unity(mesh, subs, cfg.overlap)
     res = MSGFEMResult(A=A, b=b)

@@ -861,6 +861,11 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
     h->err = "node coordinates: copy failed or non-finite value";
     return MSGFEM_EINVAL;
   }
+  if (mesh->load != nullptr && !copy_in(mesh->load, 3 * nnodes, h->h_load)) {
+    *out = h;
+    h->err = "nodal loads: copy failed or non-finite value";
+    return MSGFEM_EINVAL;
+  }
   if (plies->elem_frame != nullptr && !copy_in(plies->elem_frame, 9 * nel, h->h_frame)) {
     *out = h;
     h->err = "ply frames: copy failed or non-finite value";

@@ -168,6 +168,7 @@ struct msgfem {
   double hx = 0, hy = 0, hz = 0, traction = 0;
   std::vector<double> h_xyz;         // node coordinates (general mesh), empty for the box
   std::vector<double> h_frame;       // per-element ply frames, empty = x, y, z
+  std::vector<double> h_load;        // nodal loads [n_nodes][3], empty = the end-face traction
   std::vector<int> boxes;            // explicit non-overlapping element boxes, 4 per subdomain
   double* d_xyz = nullptr;           // device copies (nullptr for the box / default frames)
   double* d_frame = nullptr;

@@ -256,9 +256,24 @@ msgfem_status build_problem(msgfem* h) {
         (void)onx;
         hs.mu[(size_t)k * s.npl + q] = w / total[((size_t)gi * (NY + 1) + gj) * (NZ + 1) + k];
       }
-    // consistent nodal load of the traction (-p, 0, 0) on the x = L face
+    // the given nodal loads on the Omega* nodes (a particular function when
+    // they touch B1), or the consistent nodal load of the traction (-p, 0, 0)
+    // on the x = L face
     hs.bload.assign(s.nfull, 0.0);
-    if (s.loaded)
+    if (!h->h_load.empty()) {
+      bool b1 = false;
+      for (int k = 0; k <= NZ; ++k)
+        for (int q = 0; q < s.npl; ++q) {
+          const int gi = s.I0 + q / s.nyn, gj = s.J0 + q % s.nyn;
+          const size_t gn = ((size_t)gi * (NY + 1) + gj) * (NZ + 1) + k;
+          for (int c = 0; c < 3; ++c) {
+            const double v = h->h_load[3 * gn + c];
+            hs.bload[((size_t)k * s.npl + q) * 3 + c] = v;
+            b1 = b1 || (v != 0.0 && hs.cls[q] == 1);
+          }
+        }
+      s.loaded = b1 ? 1 : 0;
+    } else if (s.loaded)
       for (int k = 0; k <= NZ; ++k)
         for (int q = 0; q < s.npl; ++q) {
           const int gi = s.I0 + q / s.nyn, gj = s.J0 + q % s.nyn;

@@ -32,7 +32,7 @@ class MsgfemError(RuntimeError):
 
 class Mesh(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("hx", C.c_double), ("hy", C.c_double),
-                ("hz", C.c_double), ("traction", C.c_double), ("xyz", C.c_void_p)]
+                ("hz", C.c_double), ("traction", C.c_double), ("xyz", C.c_void_p), ("load", C.c_void_p)]
 
 
 class Plies(C.Structure):
@@ -148,9 +148,10 @@ class MSGFEM:
     def __init__(self, nx, ny, nz, hx, hy, hz, traction, E9, elem_angles, sx, sy, overlap, oversampling,
                  block=0, max_iter=0, tol=0.0, seed=0, stream=None, precision=0, profile=0, solver=0, streams=0, refine=0,
                  instances=0, xyz=None, frames=None, boxes=None, wave_mb=0.0, solve_kernel=0,
-                 factor_schedule=0, direct_launch=0, allocator=None):
+                 factor_schedule=0, direct_launch=0, allocator=None, load=None):
         """``allocator``: optional pair (alloc(nbytes) -> device address, free(address,
-        nbytes)) through which the handle takes all its device memory."""
+        nbytes)) through which the handle takes all its device memory.  ``load``:
+        optional nodal forces [n_nodes * 3] replacing the end-face traction."""
         self.lib = load_library()
         self.h = C.c_void_p()
         self._E9 = np.ascontiguousarray(E9, dtype=np.float64)
@@ -161,7 +162,8 @@ class MSGFEM:
         self._xyz = None if xyz is None else np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1)
         self._frames = None if frames is None else np.ascontiguousarray(frames, dtype=np.float64).reshape(-1)
         self._boxes = None if boxes is None else np.ascontiguousarray(boxes, dtype=np.int32).reshape(-1)
-        self.mesh = Mesh(nx, ny, nz, hx, hy, hz, traction, _ptr(self._xyz))
+        self._load = None if load is None else np.ascontiguousarray(load, dtype=np.float64).reshape(-1)
+        self.mesh = Mesh(nx, ny, nz, hx, hy, hz, traction, _ptr(self._xyz), _ptr(self._load))
         self.n_dof = 3 * (nx + 1) * (ny + 1) * (nz + 1)
         plies = Plies(self._E9.ctypes.data, _ptr(ang), _ptr(self._frames))
         nb = 0 if self._boxes is None else len(self._boxes) // 4

@@ -306,9 +306,11 @@ extern "C" {
 
 // A handle of the set-up code for a structured hexahedral mesh: a box of
 // bricks (xyz NULL) or node coordinates [(NX+1)(NY+1)(NZ+1)][3]; a regular
-// sx x sy partition or nboxes element boxes (x0, x1, y0, y1).
+// sx x sy partition or nboxes element boxes (x0, x1, y0, y1); nodal loads
+// [(NX+1)(NY+1)(NZ+1)][3] or NULL (the end-face traction).
 void* hc_create(int nx, int ny, int nz, double hx, double hy, double hz, double traction, int sx, int sy, int o,
-                int os, int nboxes, const int* boxes, const double* xyz, int instances, int mixed) {
+                int os, int nboxes, const int* boxes, const double* xyz, int instances, int mixed,
+                const double* load) {
   HostCheck* c = new HostCheck();
   msgfem* h = &c->h;
   h->NX = nx; h->NY = ny; h->NZ = nz;
@@ -320,6 +322,7 @@ void* hc_create(int nx, int ny, int nz, double hx, double hy, double hz, double 
     h->sy = 1;
   }
   if (xyz != nullptr) h->h_xyz.assign(xyz, xyz + 3 * (size_t)(nx + 1) * (ny + 1) * (nz + 1));
+  if (load != nullptr) h->h_load.assign(load, load + 3 * (size_t)(nx + 1) * (ny + 1) * (nz + 1));
   h->S = instances > 1 ? instances : 1;
   h->mixed = mixed;
   c->st = build_problem(h);

@@ -63,7 +63,7 @@ def lib():
         L = C.CDLL(build())
         vp, ip, dp, i, d = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int, C.c_double
         L.hc_create.restype = vp
-        L.hc_create.argtypes = [i, i, i, d, d, d, d, i, i, i, i, i, vp, vp, i, i]
+        L.hc_create.argtypes = [i, i, i, d, d, d, d, i, i, i, i, i, vp, vp, i, i, vp]
         L.hc_status.argtypes = [vp]
         L.hc_error.restype = C.c_char_p
         L.hc_error.argtypes = [vp]
@@ -100,7 +100,7 @@ def _p(a):
 class HostSetup:
     """The library's host-side set-up of one mesh and partition."""
 
-    def __init__(self, cfg, instances=1, mixed=False, xyz=None, boxes=None):
+    def __init__(self, cfg, instances=1, mixed=False, xyz=None, boxes=None, load=None):
         L = lib()
         self.L = L
         section = getattr(cfg, "kind", "beam") == "section"
@@ -111,10 +111,12 @@ class HostSetup:
             boxes = np.array(cfg.boxes)
         self._xyz = None if xyz is None else np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1)
         self._boxes = None if boxes is None else np.ascontiguousarray(boxes, dtype=np.int32).reshape(-1)
+        self._load = None if load is None else np.ascontiguousarray(load, dtype=np.float64).reshape(-1)
         nb = 0 if self._boxes is None else len(self._boxes) // 4
         hx, hy, hz = (0.0, 0.0, 0.0) if section else (cfg.hx, cfg.hy, cfg.t)
         self.h = L.hc_create(cfg.NX, cfg.NY, cfg.NZ, hx, hy, hz, cfg.traction, cfg.sx, cfg.sy, cfg.overlap,
-                             cfg.oversampling, nb, _p(self._boxes), _p(self._xyz), instances, int(mixed))
+                             cfg.oversampling, nb, _p(self._boxes), _p(self._xyz), instances, int(mixed),
+                             _p(self._load))
         self.status = L.hc_status(self.h)
         self.error = L.hc_error(self.h).decode()
         self.N = L.hc_num_subdomains(self.h)

@@ -280,3 +280,33 @@ def test_coarse_pairs_cover_every_coupling(name):
             assert (s, t) in pairs, (s, t)
             x0, x1, y0, y1 = pairs[s, t]
             assert I.min() >= x0 and I.max() <= x1 and J.min() >= y0 and J.max() <= y1, (s, t)
+
+
+@pytest.mark.parametrize("name", ["t2", "s1"])
+def test_nodal_loads_reach_every_subdomain(name):
+    """Given nodal forces replace the end-face traction: each subdomain holds
+    their restriction to its Omega* nodes, and gets a particular function
+    exactly when they are non-zero on one of its B1 DoFs."""
+    cfg = _cfg(name)
+    mesh, subs, _, _, _ = _oracle(cfg)
+    rng = np.random.default_rng(4)
+    load = np.zeros((cfg.NX + 1, cfg.NY + 1, cfg.NZ + 1, 3))
+    load[cfg.NX, :2] = rng.standard_normal((2, cfg.NZ + 1, 3))        # a corner of the free end
+    hs = hc.HostSetup(cfg, load=load)
+    assert hs.status == 0, hs.error
+    flat = load.reshape(-1, 3)
+    seen = set()
+    for j in range(hs.N):
+        s = hs.sub(j)
+        a = hs.arrays(j)
+        nodes = _local_nodes(mesh, s)
+        np.testing.assert_array_equal(a["load"], flat[nodes].reshape(-1))
+        b1 = np.repeat(np.tile(a["cls"], s["nzn"]) == 1, 3)
+        seen.add(bool(s["loaded"]))
+        assert s["loaded"] == int(np.any(a["load"][b1] != 0.0))
+    assert seen == {True, False}
+    # without the array: the traction's particular function on Omega* touching x = L
+    ref = hc.HostSetup(cfg)
+    for j in range(ref.N):
+        s = ref.sub(j)
+        assert s["loaded"] == int(s["I1"] == cfg.NX)
