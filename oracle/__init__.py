@@ -34,6 +34,8 @@ primitives (sparse LU, dense Cholesky, symmetric eigensolvers) as steps:
   strain fields (Sec. 5.4).
 * ``geneo``     the GenEO local eigenproblem and coarse space, the paper's
   comparison method (Sec. 2.3, Eq. bilinearGeneralizeEigenProblem).
+* ``schwarz``   two-level additive Schwarz preconditioned CG, the fine-scale
+  solver a coarse space preconditions (Sec. 2.3, Sec. 5.4).
 
 Parity pins live in ``tests/test_oracle_*.py``.
 """

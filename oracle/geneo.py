@@ -69,9 +69,10 @@ def geneo_eigs(gp, n_loc):
     return lam, phi
 
 
-def run_geneo(cfg, angles=None, n_loc=None, uh=None):
-    """GenEO coarse approximation with n_loc eigenvectors per subdomain:
-    (eigenvalues per subdomain, u_H, u_h, energy error ||u_h - u_H||_a / ||u_h||_a)."""
+def geneo_basis(cfg, angles=None, n_loc=None):
+    """The GenEO coarse basis V (columns on all DoFs, Gram-Schmidt in a(., .) per
+    subdomain), the eigenvalues per subdomain, and the mesh, A and b it was
+    built for."""
     mesh = make_mesh(cfg)
     E = cfg.material
     angles = element_angles(cfg) if angles is None else angles
@@ -91,7 +92,13 @@ def run_geneo(cfg, angles=None, n_loc=None, uh=None):
             col = np.zeros(mesh.n_dof)
             col[gd] = q
             cols.append(col)
-    V = sp.csc_matrix(np.stack(cols, axis=1))
+    return sp.csc_matrix(np.stack(cols, axis=1)), lams, mesh, A, b
+
+
+def run_geneo(cfg, angles=None, n_loc=None, uh=None):
+    """GenEO coarse approximation with n_loc eigenvectors per subdomain:
+    (eigenvalues per subdomain, u_H, u_h, energy error ||u_h - u_H||_a / ||u_h||_a)."""
+    V, lams, mesh, A, b = geneo_basis(cfg, angles, n_loc)
     AH = (V.T @ (A @ V)).toarray()
     c = coarse_solve(0.5 * (AH + AH.T), V.T @ b)
     uH = V @ c
