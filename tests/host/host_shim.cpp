@@ -300,6 +300,55 @@ void run_solve(HostCheck* c, int which, const MvArgs& mv, unsigned seed) {
   run(s->steps, s->tasks, seed, [&](const SolveTaskT<T>& t) { exec(t, pc, mv); });
 }
 
+// Preconditions of the tile kernels' vector loads: every operand pointer and
+// leading dimension 16-byte aligned, every inner dimension a multiple of the
+// 16-byte vector width, and the schedule's summary flags true to its tasks
+// (k32: every GEMM K % 32 == 0; k64: every solve K % 64 == 0; kmax).
+template <typename T>
+long long align_check(const ScheduleT<T>& s, std::string* first) {
+  long long n = 0;
+  bool k32 = true;
+  auto bad = [&](const char* what, size_t i) {
+    if (first->empty()) *first = std::string(what) + " of tile task " + std::to_string(i);
+    ++n;
+  };
+  for (size_t i = 0; i < s.gemm.size(); ++i) {
+    const TileTaskT<T>& t = s.gemm[i];
+    for (const void* q : {(const void*)t.A, (const void*)t.B, (const void*)t.C, (const void*)t.P})
+      if (q != nullptr && reinterpret_cast<uintptr_t>(q) % 16) bad("misaligned operand", i);
+    for (int ld : {t.lda, t.ldb, t.ldc})
+      if ((size_t)ld * sizeof(T) % 16) bad("leading dimension", i);
+    if (!(t.flags & G_POTRF)) {
+      if ((size_t)t.K * sizeof(T) % 16 || t.K <= 0) bad("inner dimension", i);
+      if (t.K % 32) k32 = false;
+    }
+  }
+  if (s.k32 && !k32) bad("k32 flag", 0);
+  return n;
+}
+
+template <typename T>
+long long align_check(const SolveScheduleT<T>& s, std::string* first) {
+  long long n = 0;
+  bool k64 = true;
+  int kmax = 0;
+  auto bad = [&](const char* what, size_t i) {
+    if (first->empty()) *first = std::string(what) + " of solve task " + std::to_string(i);
+    ++n;
+  };
+  for (size_t i = 0; i < s.tasks.size(); ++i) {
+    const SolveTaskT<T>& t = s.tasks[i];
+    for (const void* q : {(const void*)t.A, (const void*)t.B, (const void*)t.C, (const void*)t.init})
+      if (q != nullptr && reinterpret_cast<uintptr_t>(q) % 16) bad("misaligned operand", i);
+    if (t.K > 0 && ((size_t)t.lda * sizeof(T) % 16 || (size_t)t.K * sizeof(T) % 16)) bad("inner dimension", i);
+    if (t.K % 64) k64 = false;
+    kmax = std::max(kmax, t.K);
+  }
+  if (s.k64 && !k64) bad("k64 flag", 0);
+  if (s.kmax != kmax) bad("kmax", 0);
+  return n;
+}
+
 }  // namespace
 
 extern "C" {
@@ -540,6 +589,20 @@ int hc_pairs(void* p, int* out) {
       memcpy(out + 6 * i, v, sizeof v);
     }
   return (int)h.pairs.size();
+}
+
+long long hc_align_check(void* p, int which, char* msg, int len) {
+  HostCheck* c = H(p);
+  std::string first;
+  long long n = -1;
+  if (which == SC_COARSE_FACTOR) n = align_check(c->h.cfact, &first);
+  else if (which == SC_COARSE_SOLVE) n = align_check(c->h.csolve, &first);
+  else if (c->w == nullptr) n = -1;
+  else if (which == SC_FACTOR) n = c->h.mixed ? align_check(c->w->factf, &first) : align_check(c->w->fact, &first);
+  else n = c->h.mixed ? align_check(*solve_sched<float>(*c->w, which), &first)
+                      : align_check(*solve_sched<double>(*c->w, which), &first);
+  if (msg && len > 0) snprintf(msg, len, "%s", first.c_str());
+  return n;
 }
 
 // A planted scheduling mistake, for checking the race check itself: step s of

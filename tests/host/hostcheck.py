@@ -89,6 +89,8 @@ def lib():
         L.hc_merge_steps.argtypes = [vp, i, i, i]
         L.hc_element_types.argtypes = [vp, vp, vp, ip, vp, vp, vp]
         L.hc_pairs.argtypes = [vp, vp]
+        L.hc_align_check.restype = C.c_longlong
+        L.hc_align_check.argtypes = [vp, i, C.c_char_p, i]
         _lib = L
     return _lib
 
@@ -228,6 +230,13 @@ class HostSetup:
         out = np.zeros((n, 6), dtype=np.int32)
         self.L.hc_pairs(self.h, _p(out))
         return out
+
+    def align_check(self, which):
+        """Violations of the tile kernels' alignment preconditions and of the
+        schedule's summary flags (count, first one)."""
+        msg = C.create_string_buffer(200)
+        n = self.L.hc_align_check(self.h, which, msg, 200)
+        return n, msg.value.decode()
 
     def merge_steps(self, which, group, step):
         return self.L.hc_merge_steps(self.h, which, group, step)

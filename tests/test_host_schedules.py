@@ -267,3 +267,43 @@ def test_race_check_reports_planted_mistakes():
     dst[a] = dst[b] = big
     n, msg = hs.race(hc.SC_SOLVE_K, src, dst)
     assert n > 0 and "group" in msg, msg
+
+
+@pytest.mark.parametrize("name", ["t2", "s1", "c1"])
+@pytest.mark.parametrize("mixed", [False, True])
+@pytest.mark.parametrize("left", [False, True])
+def test_vector_load_preconditions(name, mixed, left):
+    """The tile kernels load operands as 16-byte vectors (float4 / double2,
+    cp.async of 16 bytes): every operand pointer and leading dimension of every
+    task is 16-byte aligned, every inner dimension a multiple of the vector
+    width, and the schedules' summary flags (all K % 32 == 0 for the FP32 GEMM
+    fast path, all K % 64 == 0 for the cp.async solve ring, the largest K for
+    shared-memory sizing) are true to their tasks; for every wave of a split
+    pool as well."""
+    cfg = _cfg(name)
+    hs = hc.HostSetup(cfg, mixed=mixed)
+    sizes = np.array([hs.sub_bytes(j) for j in range(hs.N)])
+    for budget in (1e15, max(sizes.max(), sizes.sum() // 2)):
+        nw = hs.plan_waves(budget)
+        for w in range(nw):
+            hs.build_wave(w, 16, 16, left)
+            for which in (hc.SC_FACTOR,) + hc.SOLVES:
+                n, msg = hs.align_check(which)
+                assert n == 0, (which, msg)
+    b = 3 * hc.TILE
+    bufs = [np.zeros((b, b)), np.zeros((b, b))] + [np.zeros((b, hc.PST)) for _ in range(4)]
+    hs.build_coarse(b, *bufs)
+    for which in (hc.SC_COARSE_FACTOR, hc.SC_COARSE_SOLVE):
+        assert hs.align_check(which) == (0, "")
+
+
+def test_vector_load_check_reports_misalignment():
+    cfg = _cfg("t2")
+    hs = hc.HostSetup(cfg)
+    b = 3 * hc.TILE
+    off = np.zeros(b * b + 1)[1:].reshape(b, b)          # 8 bytes past a 16-byte boundary
+    assert off.ctypes.data % 16 == 8
+    bufs = [off, np.zeros((b, b))] + [np.zeros((b, hc.PST)) for _ in range(4)]
+    hs.build_coarse(b, *bufs)
+    n, msg = hs.align_check(hc.SC_COARSE_FACTOR)
+    assert n > 0 and "misaligned" in msg
