@@ -234,6 +234,27 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies,
                            const msgfem_partition* part, int overlap, int oversampling,
                            const msgfem_options* opt, msgfem_h* out);
 
+/* Device storage that a problem needs, planned on the host without a handle
+ * and without any CUDA call (node coordinates must then be a host pointer):
+ * the same decomposition as msgfem_setup, the layer blocks, factors and
+ * block-solve buffers of every subdomain in the precision of opt (NULL:
+ * FP64), and their grouping into waves for opt->wave_mb (0: one wave, the
+ * budget msgfem_setup derives from the free device memory is unknown here). */
+typedef struct {
+  int n_subdomains;     /* N (all instances) */
+  int waves;            /* waves for the budget */
+  double pool_mb;       /* pool of the largest wave (MiB), what msgfem_setup allocates for it */
+  double blocks_mb;     /* storage of all subdomains together (MiB) */
+  double largest_mb;    /* storage of the largest subdomain (MiB); a budget below it is ENOMEM */
+  long long n_dof;      /* 3 (nx+1)(ny+1)(nz+1) */
+  int max_star_dof;     /* largest oversampling domain (DoFs) */
+} msgfem_plan_info;
+
+/* Errors: EINVAL (as msgfem_setup), ENOMEM (one subdomain exceeds wave_mb;
+ * *info still filled but waves = 0). */
+msgfem_status msgfem_plan(const msgfem_mesh* mesh, const msgfem_partition* part, int overlap, int oversampling,
+                          const msgfem_options* opt, msgfem_plan_info* info);
+
 /* Replace the element angles (same layout as msgfem_plies.elem_angle_deg). */
 msgfem_status msgfem_update_angles(msgfem_h h, const double* elem_angle_deg);
 

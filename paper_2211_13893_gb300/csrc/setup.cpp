@@ -15,6 +15,7 @@
 // element with p; mu_{j,p} = w_{j,p} / sum_i w_{i,p}.
 #include <cmath>
 #include <cstring>
+#include <limits>
 #include <map>
 #include <tuple>
 #include <type_traits>
@@ -778,4 +779,58 @@ void build_coarse_schedules(msgfem* h) {
     keys[2].push_back(b2);
   }
   flatten_solve(keys, h->csolve);
+}
+
+// Memory plan of a problem on the host (no handle, no CUDA call): the same
+// decomposition as msgfem_setup, the storage of every subdomain and the waves.
+extern "C" msgfem_status msgfem_plan(const msgfem_mesh* mesh, const msgfem_partition* part, int overlap,
+                                     int oversampling, const msgfem_options* opt, msgfem_plan_info* info) {
+  if (!mesh || !part || !info) return MSGFEM_EINVAL;
+  if (mesh->nx <= 0 || mesh->ny <= 0 || mesh->nz <= 0) return MSGFEM_EINVAL;
+  if (mesh->xyz == nullptr && (!(mesh->hx > 0) || !(mesh->hy > 0) || !(mesh->hz > 0))) return MSGFEM_EINVAL;
+  if (part->n_boxes < 0 || (part->n_boxes > 0 && part->boxes == nullptr)) return MSGFEM_EINVAL;
+  if (part->n_boxes == 0 && (part->sx <= 0 || part->sy <= 0 || part->sx > mesh->nx || part->sy > mesh->ny))
+    return MSGFEM_EINVAL;
+  if (overlap < 1 || oversampling < overlap) return MSGFEM_EINVAL;
+  if (opt && opt->precision != MSGFEM_FP64 && opt->precision != MSGFEM_MIXED) return MSGFEM_EINVAL;
+  msgfem h;
+  h.NX = mesh->nx; h.NY = mesh->ny; h.NZ = mesh->nz;
+  h.hx = mesh->hx; h.hy = mesh->hy; h.hz = mesh->hz; h.traction = mesh->traction;
+  h.sx = part->sx; h.sy = part->sy; h.o = overlap; h.os = oversampling;
+  if (part->n_boxes > 0) {
+    h.boxes.assign(part->boxes, part->boxes + 4 * (size_t)part->n_boxes);
+    h.sx = part->n_boxes;
+    h.sy = 1;
+  }
+  const size_t nnodes = (size_t)(h.NX + 1) * (h.NY + 1) * (h.NZ + 1);
+  if (mesh->xyz != nullptr) {
+    h.h_xyz.assign(mesh->xyz, mesh->xyz + 3 * nnodes);
+    for (double v : h.h_xyz)
+      if (!std::isfinite(v)) return MSGFEM_EINVAL;
+  }
+  h.S = (opt && opt->instances > 1) ? opt->instances : 1;
+  h.mixed = (opt && opt->precision == MSGFEM_MIXED) ? 1 : 0;
+  memset(info, 0, sizeof(*info));
+  msgfem_status st = build_problem(&h);
+  if (st != MSGFEM_OK) return st;
+  size_t total = 0, largest = 0;
+  int max_star = 0;
+  for (int j = 0; j < h.N; ++j) {
+    const size_t b = sub_block_bytes(&h, j);
+    total += b;
+    largest = std::max(largest, b);
+    max_star = std::max(max_star, h.sub[j].nfull);
+  }
+  const double mib = 1048576.0;
+  info->n_subdomains = h.N;
+  info->blocks_mb = (double)total / mib;
+  info->largest_mb = (double)largest / mib;
+  info->n_dof = 3 * (long long)nnodes;
+  info->max_star_dof = max_star;
+  const size_t budget = (opt && opt->wave_mb > 0) ? (size_t)(opt->wave_mb * mib) : std::numeric_limits<size_t>::max();
+  st = plan_waves(&h, budget);
+  if (st != MSGFEM_OK) return st;
+  info->waves = (int)h.waves.size();
+  info->pool_mb = (double)h.pool_bytes / mib;
+  return MSGFEM_OK;
 }

@@ -16,7 +16,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTSPD", 5: "ENOCO
 EXPORTS = ("msgfem_setup", "msgfem_update_angles", "msgfem_local_spaces", "msgfem_coarse_assemble",
            "msgfem_solve", "msgfem_get_basis", "msgfem_get_info", "msgfem_num_subdomains",
            "msgfem_get_profile", "msgfem_reset_profile", "msgfem_energy_error_noalloc", "msgfem_last_error",
-           "msgfem_autotune", "msgfem_coarse_assemble_threshold", "msgfem_solution_errors",
+           "msgfem_autotune", "msgfem_coarse_assemble_threshold", "msgfem_solution_errors", "msgfem_plan",
            "msgfem_destroy",
            # include/msgfem_warm.h
            "msgfem_net_create", "msgfem_net_param_count", "msgfem_net_get_params", "msgfem_net_set_params",
@@ -49,6 +49,11 @@ class Options(C.Structure):
                 ("streams", C.c_int), ("refine", C.c_int), ("instances", C.c_int), ("solve_kernel", C.c_int),
                 ("factor_schedule", C.c_int), ("direct_launch", C.c_int), ("wave_mb", C.c_double),
                 ("dev_alloc", C.c_void_p), ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p)]
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("n_subdomains", C.c_int), ("waves", C.c_int), ("pool_mb", C.c_double), ("blocks_mb", C.c_double),
+                ("largest_mb", C.c_double), ("n_dof", C.c_longlong), ("max_star_dof", C.c_int)]
 
 
 # msgfem_options.dev_alloc / dev_free
@@ -103,6 +108,8 @@ def load_library(path=LIB_PATH):
         "msgfem_autotune": (C.c_int, [h, C.c_int, C.POINTER(Tuning)]),
         "msgfem_energy_error_noalloc": (C.c_int, [h, C.c_void_p, C.c_void_p, C.c_void_p]),
         "msgfem_solution_errors": (C.c_int, [h, C.c_void_p, C.POINTER(C.c_double)]),
+        "msgfem_plan": (C.c_int, [C.POINTER(Mesh), C.POINTER(Partition), C.c_int, C.c_int, C.POINTER(Options),
+                                  C.POINTER(PlanInfo)]),
         "msgfem_reset_profile": (C.c_int, [h]),
         "msgfem_num_subdomains": (C.c_int, [h]),
         "msgfem_last_error": (C.c_char_p, [h]),
@@ -362,3 +369,26 @@ class Net:
             self.close()
         except Exception:
             pass
+
+
+def plan(cfg, precision=0, wave_mb=0.0, instances=0):
+    """Device storage of a workload (include/msgfem.h msgfem_plan), planned on the
+    host without a GPU: dict of the msgfem_plan_info fields and the status."""
+    lib = load_library()
+    section = getattr(cfg, "kind", "beam") == "section"
+    xyz = boxes = None
+    if section:
+        from workloads.section import section_nodes
+        xyz = np.ascontiguousarray(section_nodes(cfg), dtype=np.float64).reshape(-1)
+        boxes = np.ascontiguousarray(cfg.boxes, dtype=np.int32).reshape(-1)
+        mesh = Mesh(cfg.NX, cfg.NY, cfg.NZ, 0.0, 0.0, 0.0, cfg.traction, _ptr(xyz), None)
+    else:
+        mesh = Mesh(cfg.NX, cfg.NY, cfg.NZ, cfg.hx, cfg.hy, cfg.t, cfg.traction, None, None)
+    part = Partition(cfg.sx, cfg.sy, 0 if boxes is None else len(boxes) // 4, _ptr(boxes))
+    opt = Options()
+    opt.precision, opt.wave_mb, opt.instances = precision, wave_mb, instances
+    info = PlanInfo()
+    st = lib.msgfem_plan(C.byref(mesh), C.byref(part), cfg.overlap, cfg.oversampling, C.byref(opt), C.byref(info))
+    out = {k: getattr(info, k) for k, _ in PlanInfo._fields_}
+    out["status"] = STATUS.get(st, st)
+    return out
