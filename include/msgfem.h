@@ -236,7 +236,8 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies,
 
 /* Device storage that a problem needs, planned on the host without a handle
  * and without any CUDA call (node coordinates must then be a host pointer):
- * the same decomposition as msgfem_setup, the layer blocks, factors and
+ * the same decomposition as msgfem_setup (Secs. 3.1, 4.2, 4.3: subdomains,
+ * oversampling domains, DoF classes), the layer blocks, factors and
  * block-solve buffers of every subdomain in the precision of opt (NULL:
  * FP64), and their grouping into waves for opt->wave_mb (0: one wave, the
  * budget msgfem_setup derives from the free device memory is unknown here). */
