@@ -302,6 +302,26 @@ msgfem_status msgfem_solve(msgfem_h h, double* u_out, const double* u_ref, doubl
  * Omega*_j node box {i0, i1, j0, j1}. */
 msgfem_status msgfem_get_basis(msgfem_h h, int j, double* phi_out, int* rows, int* cols, int* box_out);
 
+/* Checkpoint of the local stage (the offline / online reuse of local bases
+ * the paper suggests, Sec. 6): subdomain j's n_loc eigenpairs and its
+ * particular function (Eq. up_r).  phi_out (may be NULL): n_star_dof *
+ * (n_loc + 1) doubles, column-major in the layout of msgfem_get_basis, the
+ * n_loc eigenvectors followed by psi_j (zero when the load does not reach
+ * B1); lambda_out (may be NULL): n_loc doubles.  Host or device pointers.
+ * Errors: EINVAL, ESTATE (before msgfem_local_spaces), ENOMEM, ECUDA. */
+msgfem_status msgfem_export_local(msgfem_h h, int j, double* phi_out, double* lambda_out);
+
+/* Resume from exported local spaces: on a handle set up like the exporting one
+ * (same mesh, angles, partition, loads), assembles the element and subdomain
+ * matrices as msgfem_local_spaces does and takes the eigenpairs and particular
+ * functions from lambda (N * n_loc doubles, subdomain-major) and phi (N
+ * pointers, each as phi_out of msgfem_export_local) instead of solving for
+ * them; the handle is then ready for msgfem_coarse_assemble.  Host or device
+ * pointers, copied.  Errors: EINVAL (NULL, n_loc outside 1 .. 31 or above a
+ * subdomain's B2 size, non-finite eigenvalue), ESTATE (before msgfem_setup),
+ * ENOMEM, ECUDA. */
+msgfem_status msgfem_import_local(msgfem_h h, int n_loc, const double* lambda, const double* const* phi);
+
 /* Energy error ||u_ref - u||_a / ||u_ref||_a of two caller-owned device
  * vectors (3 (nx+1)(ny+1)(nz+1) doubles each, the layout of msgfem_solve), the
  * same quantity msgfem_solve reports, computed without allocating any memory.

@@ -1253,6 +1253,79 @@ msgfem_status msgfem_get_basis(msgfem_h h, int j, double* phi_out, int* rows, in
   return MSGFEM_OK;
 }
 
+msgfem_status msgfem_export_local(msgfem_h h, int j, double* phi_out, double* lambda_out) {
+  if (!h || j < 0 || j >= h->N || (!phi_out && !lambda_out)) return MSGFEM_EINVAL;
+  if (h->stage < 2) return MSGFEM_ESTATE;
+  const SubDev& s = h->sub[j];
+  const int n = h->n_loc;
+  if (phi_out) {
+    void* buf = nullptr;
+    const size_t count = (size_t)s.nfull * (n + 1);
+    TRY(dev_alloc_bytes(h, &buf, count * sizeof(double)));
+    double* tmp = static_cast<double*>(buf);
+    launch_basis_out(h, j, tmp, n);
+    launch_vec_layout(h, j, s.psi, 1, tmp + (size_t)n * s.nfull, 1, 1);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(phi_out, tmp, count * sizeof(double), cudaMemcpyDefault, h->stream);
+    cudaError_t e2 = cudaStreamSynchronize(h->stream);
+    dev_free_bytes(h, tmp);
+    CK(e);
+    CK(e2);
+  }
+  if (lambda_out)
+    CK(cudaMemcpy(lambda_out, h->lam_host.data() + (size_t)j * n, n * sizeof(double), cudaMemcpyDefault));
+  return MSGFEM_OK;
+}
+
+msgfem_status msgfem_import_local(msgfem_h h, int n_loc, const double* lambda, const double* const* phi) {
+  if (!h || !lambda || !phi) return MSGFEM_EINVAL;
+  if (h->stage < 1) return MSGFEM_ESTATE;
+  if (n_loc < 1 || n_loc > PST - 1) { h->err = "n_loc must be in 1 .. 31"; return MSGFEM_EINVAL; }
+  for (int j = 0; j < h->N; ++j) {
+    if (phi[j] == nullptr) { h->err = "a subdomain without its exported local space"; return MSGFEM_EINVAL; }
+    if (n_loc > h->n2[j]) { h->err = "n_loc exceeds the B2 size of a subdomain"; return MSGFEM_EINVAL; }
+  }
+  std::vector<double> lam((size_t)h->N * n_loc);
+  CK(cudaMemcpy(lam.data(), lambda, lam.size() * sizeof(double), cudaMemcpyDefault));
+  for (double v : lam)
+    if (!std::isfinite(v)) { h->err = "non-finite eigenvalue"; return MSGFEM_EINVAL; }
+  h->stage = 1;   // the earlier local spaces, coarse problem and solution are replaced
+  cudaStream_t st = h->stream;
+  set_dense_context(h->d_flags, h->d_notspd, h->d_sub);
+  TRY(set_active(h, std::vector<int>(h->N, 1)));
+  // element and subdomain matrices, as in the local stage
+  launch_element_stiffness(h);
+  launch_stencil(h);
+  CK_LAUNCH();
+  size_t maxcount = 0;
+  for (const auto& s : h->sub) maxcount = std::max(maxcount, (size_t)s.nfull * (n_loc + 1));
+  void* buf = nullptr;
+  TRY(dev_alloc_bytes(h, &buf, maxcount * sizeof(double)));
+  double* tmp = static_cast<double*>(buf);
+  cudaError_t e = cudaSuccess;
+  for (int j = 0; j < h->N && e == cudaSuccess; ++j) {
+    const SubDev& s = h->sub[j];
+    const size_t count = (size_t)s.nfull * (n_loc + 1);
+    e = cudaMemcpyAsync(tmp, phi[j], count * sizeof(double), cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.EV, 0, (size_t)s.nfull * PST * sizeof(double), st);
+    for (int c = 0; c < n_loc && e == cudaSuccess; ++c)
+      launch_vec_layout(h, j, tmp + (size_t)c * s.nfull, 1, s.EV + c, PST, 0);
+    if (e == cudaSuccess) launch_vec_layout(h, j, tmp + (size_t)n_loc * s.nfull, 1, s.psi, 1, 0);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    // the next subdomain's copy reuses the staging buffer
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  dev_free_bytes(h, tmp);
+  CK(e);
+  h->n_loc = n_loc;
+  h->lam_host = lam;
+  h->iters.assign(h->N, 0);
+  h->m_final.assign(h->N, 0);
+  h->resid_max.assign(h->N, 0.0);
+  h->stage = 2;
+  return MSGFEM_OK;
+}
+
 msgfem_status msgfem_get_info(msgfem_h h, int j, msgfem_subinfo* info) {
   if (!h || !info || j < 0 || j >= h->N) return MSGFEM_EINVAL;
   const SubDev& s = h->sub[j];

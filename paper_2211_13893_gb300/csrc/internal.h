@@ -345,6 +345,9 @@ void launch_prolong(msgfem* h);
 int energy_blocks(msgfem* h);
 void launch_energy(msgfem* h, const double* d_ref, const double* d_u, double* d_out);
 void launch_basis_out(msgfem* h, int j, double* d_out, int ncols);
+// one vector of subdomain j between the internal layout and that of
+// msgfem_get_basis (to_output 1: internal -> output)
+void launch_vec_layout(msgfem* h, int j, const double* src, int sstride, double* dst, int dstride, int to_output);
 
 // learned warm start (k_warm.cu)
 msgfem_status warm_rows(msgfem* h);

@@ -184,7 +184,26 @@ __global__ void k_basis_out(const SubDev* __restrict__ subs, int j, double* __re
   }
 }
 
+// One vector of subdomain j between the internal full layout (row
+// (k npl + q) 3 + c, stride sstride / dstride between rows) and the layout of
+// msgfem_get_basis (row (q nzn + k) 3 + c, q = (i - I0) nyn + (j - J0)).
+__global__ void k_vec_layout(const SubDev* __restrict__ subs, int j, const double* __restrict__ src, int sstride,
+                             double* __restrict__ dst, int dstride, int to_output) {
+  const SubDev& s = subs[j];
+  for (int orow = blockIdx.x * blockDim.x + threadIdx.x; orow < s.nfull; orow += gridDim.x * blockDim.x) {
+    const int onode = orow / 3, c = orow % 3;
+    const int k = onode % s.nzn, q = onode / s.nzn;
+    const int row = (k * s.npl + q) * 3 + c;
+    if (to_output) dst[(size_t)orow * dstride] = src[(size_t)row * sstride];
+    else dst[(size_t)row * dstride] = src[(size_t)orow * sstride];
+  }
+}
+
 }  // namespace
+
+void launch_vec_layout(msgfem* h, int j, const double* src, int sstride, double* dst, int dstride, int to_output) {
+  k_vec_layout<<<64, 256, 0, h->stream>>>(h->d_sub, j, src, sstride, dst, dstride, to_output); ++g_launch_count;
+}
 
 void launch_coarse_blocks(msgfem* h) {
   int maxrows = 0;

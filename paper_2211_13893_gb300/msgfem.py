@@ -17,6 +17,7 @@ EXPORTS = ("msgfem_setup", "msgfem_update_angles", "msgfem_local_spaces", "msgfe
            "msgfem_solve", "msgfem_get_basis", "msgfem_get_info", "msgfem_num_subdomains",
            "msgfem_get_profile", "msgfem_reset_profile", "msgfem_energy_error_noalloc", "msgfem_last_error",
            "msgfem_autotune", "msgfem_coarse_assemble_threshold", "msgfem_solution_errors", "msgfem_plan",
+           "msgfem_export_local", "msgfem_import_local",
            "msgfem_destroy",
            # include/msgfem_warm.h
            "msgfem_net_create", "msgfem_net_param_count", "msgfem_net_get_params", "msgfem_net_set_params",
@@ -108,6 +109,8 @@ def load_library(path=LIB_PATH):
         "msgfem_autotune": (C.c_int, [h, C.c_int, C.POINTER(Tuning)]),
         "msgfem_energy_error_noalloc": (C.c_int, [h, C.c_void_p, C.c_void_p, C.c_void_p]),
         "msgfem_solution_errors": (C.c_int, [h, C.c_void_p, C.POINTER(C.c_double)]),
+        "msgfem_export_local": (C.c_int, [h, C.c_int, C.c_void_p, C.c_void_p]),
+        "msgfem_import_local": (C.c_int, [h, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
         "msgfem_plan": (C.c_int, [C.POINTER(Mesh), C.POINTER(Partition), C.c_int, C.c_int, C.POINTER(Options),
                                   C.POINTER(PlanInfo)]),
         "msgfem_reset_profile": (C.c_int, [h]),
@@ -251,6 +254,50 @@ class MSGFEM:
         out = (C.c_double * 2)()
         self._check(self.lib.msgfem_solution_errors(self.h, _ptr(u_ref), out))
         return float(out[0]), float(out[1])
+
+    def export_local(self, j):
+        """Subdomain j's local space (include/msgfem.h msgfem_export_local):
+        (phi [n_star_dof, n_loc + 1] = eigenvectors then psi_j, eigenvalues [n_loc])."""
+        rows = C.c_int()
+        self._check(self.lib.msgfem_get_basis(self.h, j, None, C.byref(rows), None, None))
+        n = self.n_loc
+        phi = np.zeros((n + 1) * rows.value)
+        lam = np.zeros(n)
+        self._check(self.lib.msgfem_export_local(self.h, j, phi.ctypes.data, lam.ctypes.data))
+        return phi.reshape(n + 1, rows.value).T, lam
+
+    def import_local(self, lam, phis):
+        """Resume from exported local spaces (msgfem_import_local): lam [N, n_loc],
+        phis[j] as returned by export_local."""
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        n_loc = lam.shape[1]
+        cols = [np.ascontiguousarray(np.asarray(p, dtype=np.float64).T) for p in phis]
+        ptrs = (C.c_void_p * len(cols))(*[c.ctypes.data for c in cols])
+        self._check(self.lib.msgfem_import_local(self.h, n_loc, lam.ctypes.data, ptrs))
+        self.n_loc = n_loc
+
+    def save_local(self, path):
+        """Write the local stage to path (.npz: eigenvalues and every subdomain's
+        exported space) with a JSON manifest next to it (path + '.json')."""
+        import json
+        out = [self.export_local(j) for j in range(self.N)]
+        lam = np.stack([o[1] for o in out])
+        np.savez(path, lam=lam, **{f"phi_{j}": o[0] for j, o in enumerate(out)})
+        with open(str(path) + ".json", "w") as f:
+            json.dump({"n_subdomains": self.N, "n_loc": int(self.n_loc), "n_dof": int(self.n_dof),
+                       "n_star_dof": [int(o[0].shape[0]) for o in out]}, f)
+
+    def load_local(self, path):
+        """Resume from a file written by save_local (the handle must be set up like
+        the one that wrote it)."""
+        import json
+        with open(str(path) + ".json") as f:
+            man = json.load(f)
+        if man["n_subdomains"] != self.N or man["n_dof"] != self.n_dof:
+            raise ValueError("the checkpoint was written for another problem")
+        name = str(path) if str(path).endswith(".npz") else str(path) + ".npz"
+        data = np.load(name)
+        self.import_local(data["lam"], [data[f"phi_{j}"] for j in range(self.N)])
 
     def basis(self, j):
         rows, cols, box = C.c_int(), C.c_int(), (C.c_int * 4)()
