@@ -1081,7 +1081,7 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   spans_collect(h);
   for (int j = 0; j <= h->N; ++j)
     if (notspd[j]) {
-      h->err = "non-positive pivot in a layer-block factorisation";
+      h->err = "non-positive pivot in a layer-block factorisation of subdomain " + std::to_string(j);
       return MSGFEM_ENOTSPD;
     }
   if (!all_done) {
