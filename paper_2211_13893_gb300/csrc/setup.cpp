@@ -793,7 +793,7 @@ extern "C" msgfem_status msgfem_plan(const msgfem_mesh* mesh, const msgfem_parti
     return MSGFEM_EINVAL;
   if (overlap < 1 || oversampling < overlap) return MSGFEM_EINVAL;
   if (opt && opt->precision != MSGFEM_FP64 && opt->precision != MSGFEM_MIXED) return MSGFEM_EINVAL;
-  msgfem h;
+  msgfem h{};   // value-initialised: the options and material stay zero
   h.NX = mesh->nx; h.NY = mesh->ny; h.NZ = mesh->nz;
   h.hx = mesh->hx; h.hy = mesh->hy; h.hz = mesh->hz; h.traction = mesh->traction;
   h.sx = part->sx; h.sy = part->sy; h.o = overlap; h.os = oversampling;
