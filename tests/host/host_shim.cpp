@@ -450,6 +450,46 @@ int hc_build_wave(void* p, int w, int groups_factor, int groups_solve, int left)
   return 0;
 }
 
+// Schedules of wave w built on a pool that is never touched (base address only):
+// for counting tasks and work of full-size workloads without their memory.
+int hc_build_wave_virtual(void* p, int w, int groups_factor, int groups_solve, int left) {
+  HostCheck* c = H(p);
+  msgfem* h = &c->h;
+  if (w < 0 || w >= (int)h->waves.size()) return -1;
+  char* base = reinterpret_cast<char*>((uintptr_t)1 << 40);
+  size_t off = 0;
+  for (int j : h->waves[w].members) {
+    off += place_sub_blocks(h, j, base + off);
+    h->sub[j].mapK = h->hsub[j].mapK.data();
+    h->sub[j].mapA = h->hsub[j].mapA.data();
+  }
+  h->ngroup_factor = groups_factor;
+  h->ngroup = groups_solve;
+  h->factor_left = left;
+  c->wave = w;
+  c->w = &h->waves[w];
+  c->pool = nullptr;
+  build_wave_factor_schedule(h, *c->w);
+  build_wave_solve_schedules(h, *c->w);
+  return 0;
+}
+
+// Flops the factorisation schedule of the built wave executes: 2 * 64 * 64 * K per
+// GEMM task (twice that with the 64 x 64 post-multiplication), and for a tile
+// POTRF its Cholesky (64^3 / 3 multiply-adds) and inverse (64^3 / 6 multiply-adds).
+double hc_factor_task_flops(void* p) {
+  HostCheck* c = H(p);
+  if (c->w == nullptr) return -1.0;
+  double f = 0.0;
+  auto add = [&](int flags, int K) {
+    if (flags & G_POTRF) f += 2.0 * (64.0 * 64.0 * 64.0 / 3.0 + 64.0 * 64.0 * 64.0 / 6.0);
+    else f += 2.0 * 64.0 * 64.0 * K + ((flags & G_POSTMUL) ? 2.0 * 64.0 * 64.0 * 64.0 : 0.0);
+  };
+  if (c->h.mixed) for (const auto& t : c->w->factf.gemm) add(t.flags, t.K);
+  else for (const auto& t : c->w->fact.gemm) add(t.flags, t.K);
+  return f;
+}
+
 // Pointer to part `which` of subdomain j's storage: 0 D_K (then E_K), 1 Linv_K,
 // 2 D_A (then E_A), 3 Linv_A.
 void* hc_sub_ptr(void* p, int j, int which) {

@@ -89,6 +89,9 @@ def lib():
         L.hc_merge_steps.argtypes = [vp, i, i, i]
         L.hc_element_types.argtypes = [vp, vp, vp, ip, vp, vp, vp]
         L.hc_pairs.argtypes = [vp, vp]
+        L.hc_build_wave_virtual.argtypes = [vp, i, i, i, i]
+        L.hc_factor_task_flops.restype = d
+        L.hc_factor_task_flops.argtypes = [vp]
         L.hc_align_check.restype = C.c_longlong
         L.hc_align_check.argtypes = [vp, i, C.c_char_p, i]
         _lib = L
@@ -237,6 +240,13 @@ class HostSetup:
         msg = C.create_string_buffer(200)
         n = self.L.hc_align_check(self.h, which, msg, 200)
         return n, msg.value.decode()
+
+    def build_wave_virtual(self, w, groups_factor=16, groups_solve=16, left=False):
+        """Schedules of wave w without their memory (task counts and work only)."""
+        assert self.L.hc_build_wave_virtual(self.h, w, groups_factor, groups_solve, int(left)) == 0
+
+    def factor_task_flops(self):
+        return self.L.hc_factor_task_flops(self.h)
 
     def merge_steps(self, which, group, step):
         return self.L.hc_merge_steps(self.h, which, group, step)
