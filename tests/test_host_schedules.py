@@ -332,3 +332,18 @@ def test_algorithmic_flops_do_not_exceed_the_executed_ones():
     assert len(ratios) == 1
     r = ratios.pop()
     assert 1.15 < r < 1.25, r
+
+
+@pytest.mark.parametrize("name", ["c2", "c4"])
+@pytest.mark.parametrize("mixed", [False, True])
+def test_vector_load_preconditions_at_full_size(name, mixed):
+    """The same preconditions on the full-size schedules: the c2 beam (32
+    subdomains, ~0.96M tile tasks) and the c4 spar (256 uneven subdomains,
+    ~12.7M tile tasks), built on a virtual pool."""
+    cfg = _cfg(name)
+    hs = hc.HostSetup(cfg, mixed=mixed)
+    assert hs.plan_waves(1e18) == 1
+    hs.build_wave_virtual(0, 16, 16, left=True)
+    for which in (hc.SC_FACTOR,) + hc.SOLVES:
+        n, msg = hs.align_check(which)
+        assert n == 0, (which, msg)
