@@ -45,6 +45,17 @@ def _width(which):
 @pytest.mark.parametrize("left", [False, True])
 @pytest.mark.parametrize("groups", [(16, 16), (1, 1), (32, 32), (3, 5)])
 def test_schedules_are_race_free(name, mixed, left, groups):
+    _race_free(name, mixed, left, groups)
+
+
+@pytest.mark.parametrize("name", ["t4", "s2"])
+@pytest.mark.parametrize("mixed", [False, True])
+def test_schedules_are_race_free_multi_tile(name, mixed):
+    """Larger layers (several 64-row tiles per layer block, 8 and 12 subdomains)."""
+    _race_free(name, mixed, True, (16, 16))
+
+
+def _race_free(name, mixed, left, groups):
     cfg = _cfg(name)
     hs = hc.HostSetup(cfg, mixed=mixed)
     assert hs.status == 0, hs.error
