@@ -67,14 +67,40 @@ typedef enum {
   MSGFEM_ESTATE = 6     /* call out of order */
 } msgfem_status;
 
-/* Structured hexahedral mesh of nx * ny * nz elements (Sec. 5.1: one element
- * per ply).  With xyz == NULL it is the box of bricks hx * hy * hz described
- * above.  Otherwise xyz holds the coordinates of every node, 3 doubles per
- * node in the global node order (host or device pointer, copied during
- * msgfem_setup), hx, hy, hz are ignored, and each element is the trilinear
- * map of its 8 nodes (curved laminates such as a C-section spar: index j then
- * runs along the arc of the cross-section and k through the thickness).  The
- * boundary faces stay the index faces: i = 0 clamped, i = nx loaded. */
+/* Hexahedral mesh (Sec. 5.1: one element per ply through the thickness).
+ *
+ * kind 0, structured: nx * ny * nz elements.  With xyz == NULL it is the box of
+ * bricks hx * hy * hz described above.  Otherwise xyz holds the coordinates of
+ * every node, 3 doubles per node in the global node order (host or device
+ * pointer, copied during msgfem_setup), hx, hy, hz are ignored, and each
+ * element is the trilinear map of its 8 nodes (curved laminates such as a
+ * C-section spar: index j then runs along the arc of the cross-section and k
+ * through the thickness).  The boundary faces stay the index faces: i = 0
+ * clamped, i = nx loaded.
+ *
+ * kind 1, hexahedron list (the general input of Sec. 3.1 / Sec. 4.1): n_nodes
+ * nodes with coordinates node_xyz [n_nodes][3] and n_elems elements hex8
+ * [n_elems][8] (0-based node ids, host pointers, copied) in the standard local
+ * order: nodes 0-3 counterclockwise around the face zeta = 0 seen from zeta > 0,
+ * nodes 4-7 above them, so that local directions 0->1, 0->3, 0->4 form a
+ * right-handed frame.  The list may come in any node and element order, but the
+ * layer-block factorisation of the local stage needs a structured block: the
+ * elements must form an nx x ny x nz block and share one orientation, and the
+ * 0->4 direction runs through the thickness (the plies).  msgfem_setup recovers
+ * the (i, j, k) numbering (i along 0->1, j along 0->3, k along 0->4, from the
+ * corner node that precedes no other; EINVAL with the reason otherwise) and
+ * then nx, ny, nz, hx, hy, hz and xyz are ignored.  Every per-node or
+ * per-element array of the calls (loads, angles, frames, elem_part, the
+ * solutions of msgfem_solve, msgfem_schwarz_solve, msgfem_energy_error_noalloc
+ * and msgfem_solution_errors) is in the list's own order; the local layouts
+ * of msgfem_get_basis / msgfem_export_local and the element fields of the
+ * warm start use the recovered structured numbering (msgfem_get_numbering).
+ *
+ * dirichlet_node (either kind; NULL = the face i = 0): per node 1 where all
+ * three displacement components are clamped (Gamma_D, zero displacement),
+ * 0 elsewhere.  The DoF classes and rigid-mode pins of the local stage assume
+ * that Gamma_D is the face i = 0 of the structured numbering: flags that mark
+ * anything else are refused (EINVAL). */
 typedef struct {
   int nx, ny, nz;
   double hx, hy, hz;
@@ -87,6 +113,11 @@ typedef struct {
                            msgfem_setup; traction ignored); entries on the clamped face have
                            no effect.  A subdomain gets a particular function (Eq. up_r)
                            when the load has a non-zero entry on its B1 DoFs. */
+  int kind;             /* 0 structured, 1 hexahedron list */
+  int n_nodes, n_elems; /* kind 1 */
+  const double* node_xyz;   /* kind 1: [n_nodes][3] */
+  const int* hex8;      /* kind 1: [n_elems][8] */
+  const unsigned char* dirichlet_node;   /* NULL or [nodes] 0 / 1 */
 } msgfem_mesh;
 
 /* Orthotropic ply material and fibre angles (Sec. 5.1).
@@ -108,11 +139,18 @@ typedef struct {
  * sx * sy box partition described above; otherwise n_boxes element boxes
  * boxes[4 j .. 4 j + 3] = {x0, x1, y0, y1} (elements [x0, x1) x [y0, y1) x
  * all k) that must tile the nx * ny element grid exactly (EINVAL otherwise);
- * subdomain j is box j and sx, sy are ignored.  Host pointer, copied. */
+ * subdomain j is box j and sx, sy are ignored.  Or elem_part: the part id
+ * (0 .. P - 1, every id used) of every element, as a graph partitioner such as
+ * ParMETIS gives it (Sec. 4.1); subdomain j is part j, and each part must be
+ * an (i, j) box of the structured numbering through the full thickness (the
+ * layer-block storage spans whole node layers; EINVAL naming the part
+ * otherwise); n_boxes, boxes, sx and sy are then ignored.  Host pointers,
+ * copied. */
 typedef struct {
   int sx, sy;           /* subdomains along x and y */
   int n_boxes;          /* 0 or the number of explicit boxes */
   const int* boxes;     /* NULL or [n_boxes][4] */
+  const int* elem_part; /* NULL or [elements] part ids */
 } msgfem_partition;
 
 /* MSGFEM_FP64: all arithmetic in FP64.  MSGFEM_MIXED: layer blocks, their
@@ -124,7 +162,10 @@ typedef enum { MSGFEM_FP64 = 0, MSGFEM_MIXED = 1 } msgfem_precision;
 typedef struct {
   int precision;        /* msgfem_precision */
   int block;            /* subspace iteration block size p; 0 = n_loc + max(8, n_loc / 2) */
-  int max_iter;         /* subspace iteration cap; 0 = 100 (block Krylov stops at a basis of 96) */
+  int max_iter;         /* cap on the eigensolver's steps: subspace iterations, or block Krylov
+                           block steps (restarts included; the block Krylov solver also stops
+                           after 8 thick restarts of its 96-column basis); 0 = 100.  A capped
+                           run returns ENOCONV with the last Rayleigh-Ritz pairs */
   double tol;           /* stop when ||theta E S^-1 T x - x||_T <= tol per wanted pair (or the
                            decrease stalls below 1e2 tol); 0 = 1e-7 */
   unsigned long long seed;  /* seed of the counter-based start-block generator */
@@ -172,13 +213,31 @@ typedef struct {
   void* (*dev_alloc)(size_t bytes, void* alloc_ctx);
   void (*dev_free)(void* p, size_t bytes, void* alloc_ctx);
   void* alloc_ctx;
+  int method;           /* local eigenproblem: MSGFEM_METHOD_MSGFEM (0) the A-harmonic problem on the
+                           oversampling domain (Eq. AHarmonicGeneralizeEigenProblem) with the
+                           particular functions; MSGFEM_METHOD_GENEO (1) the GenEO problem of
+                           Eq. bilinearGeneralizeEigenProblem, the paper's comparison (Sec. 2.3):
+                           a_{Omega_j}(phi, v) = lambda a_{Omega_j}(Xi_j phi, Xi_j v) on Omega_j
+                           itself (oversampling must equal overlap, EINVAL otherwise) over all its
+                           free DoFs, no A-harmonic constraint, no particular function; the coarse
+                           space is span{R_j^T Xi_j phi_{j,k}} with the Galerkin projection (Sec. 2.4).
+                           GenEO runs the block Krylov solver only (solver = 0) and takes no
+                           start blocks (msgfem_set_start_block) */
+  int factor_kernel;    /* MSGFEM_MIXED, kernel of the FP32 layer-block factorisation's tile GEMMs:
+                           0 = FP32 FMA on the CUDA cores; 1 = the tensor cores (tcgen05.mma,
+                           operands staged by TMA, each FP32 operand split into two TF32 parts:
+                           a_hi b_hi + a_hi b_lo + a_lo b_hi, FP32 accumulation in tensor memory);
+                           msgfem_autotune sets it (1 only when its factor agrees with kernel 0's) */
 } msgfem_options;
+
+enum { MSGFEM_METHOD_MSGFEM = 0, MSGFEM_METHOD_GENEO = 1 };
 
 /* Phase timers (CUDA events on the handle's stream, milliseconds, summed over
  * calls since msgfem_setup or the last msgfem_reset_profile) and algorithmic
- * work of the last local stage.  Flop counts use the unpadded layer sizes:
- * factorisation sum_l (n^3/3 + n^3/3 [inverse] + 2 n^3 [update, panel]) per
- * matrix; one block solve (4 (nL - 1) + 2 nL) n^2 p. */
+ * work of the last local stage.  Flop counts use the unpadded layer sizes n of
+ * the nL node layers: factorisation of the block-tridiagonal matrix, per
+ * matrix, sum_l n^3/3 [diagonal Cholesky] + (nL - 1) 2 n^3 [coupling block,
+ * update of the next diagonal block]; one block solve (4 (nL - 1) + 2 nL) n^2 p. */
 typedef struct {
   double assemble_ms;   /* element stiffness, stencils, layer blocks */
   double factor_ms;     /* layer-block Cholesky + inverses of K and A11 */
@@ -199,6 +258,10 @@ typedef struct {
                            fused K + sigma B pass */
   int waves;            /* waves of subdomains per local stage (msgfem_options.wave_mb) */
   double pool_mb;       /* size of the shared layer-block / factor / solve-buffer pool (MiB) */
+  double factor_flops_inverse;   /* factor_flops plus the n^3/3 per layer of the explicit
+                                    inverses of the diagonal factors that the solves use */
+  double factor_flops_executed;  /* flops the factorisation's 64 x 64 tile tasks execute
+                                    (padding, whole diagonal tiles and inverses included) */
 } msgfem_profile;
 
 /* Launch shapes chosen by msgfem_autotune and what it measured. */
@@ -211,6 +274,10 @@ typedef struct {
   int solve_kernel;     /* msgfem_options.solve_kernel value chosen (1, 2 or 3) */
   double best_ms;       /* time of one 8-column K solve plus one A11 solve of the measured wave */
   double solve_ms[4][3];   /* [streams 4, 8, 16, 32][kernel 1, 2, 3]; -1 = not applicable or not run */
+  int factor_kernel;    /* msgfem_options.factor_kernel chosen (mixed precision) */
+  double factor_ms_tc[2][2];   /* as factor_ms with the tensor-core tile kernel; -1 = not run */
+  double tc_factor_diff;       /* ||L_tc - L_fma||_F / ||L_fma||_F on the first subdomain of the measured
+                                  wave (the tensor-core kernel is adopted only when <= 1e-4); -1 = not run */
 } msgfem_tuning;
 
 /* Per-subdomain diagnostics filled by msgfem_get_info. */
@@ -223,6 +290,9 @@ typedef struct {
   double residual;      /* max relative eigen-residual over the n_loc pairs */
   int threshold_reached;   /* msgfem_coarse_assemble_threshold: 0 if every one of the n_loc
                               eigenvalues was below 1 / t (the basis may need a larger n_loc) */
+  int cold_restart;     /* 1 if the subdomain's registered start block (msgfem_set_start_block)
+                           did not lead to convergence and the block Krylov solver was run
+                           again from the cold (seeded random) start */
 } msgfem_subinfo;
 
 /* Partition, DoF classes (Sec. 4.3) and partition of unity (Sec. 4.2) on the
@@ -340,12 +410,15 @@ msgfem_status msgfem_import_local(msgfem_h h, int n_loc, const double* lambda, c
  * with a message otherwise); u and u_ref must be device pointers (EINVAL);
  * the handle must have run msgfem_local_spaces (ESTATE), whose element
  * stiffness is reused.  energy_err_out may be a host pointer (the call then
- * waits for the result) or a device pointer (written on the handle's stream).
- * The first call on a device looks up the device address of the array; make
- * that first call before any stream capture.  All calls share the one array and
- * each call overwrites every slot it reads, so consecutive calls are
- * independent, but calls whose kernels overlap on the GPU (other streams, other
- * threads) race on the array and must be serialised by the caller. */
+ * copies the result back and waits for it; ESTATE while the handle's stream is
+ * being captured) or a device pointer (written on the handle's stream).
+ * msgfem_setup looks up the device address of the array on the device current
+ * during set-up (the handle's device); this call must be made with that device
+ * current (EINVAL otherwise) and has nothing left to look up or load.  All
+ * calls share the one array and each call overwrites every slot it reads, so
+ * consecutive calls are independent, but calls whose kernels overlap on the
+ * GPU (other streams, other threads, other handles) race on the array and
+ * must be serialised by the caller. */
 msgfem_status msgfem_energy_error_noalloc(msgfem_h h, const double* u, const double* u_ref, double* energy_err_out);
 
 /* Relative L2 errors (Sec. 5.4) of the coarse solution u^G of the last
@@ -379,6 +452,61 @@ msgfem_status msgfem_solution_errors(msgfem_h h, const double* u_ref, double* er
  * previous local stage are kept.  tuning (may be NULL) receives the choice
  * and the measured times.  Errors: ESTATE before msgfem_local_spaces, ECUDA. */
 msgfem_status msgfem_autotune(msgfem_h h, int reps, msgfem_tuning* tuning);
+
+/* Two-level additive Schwarz preconditioned conjugate gradients for the fine
+ * problem A u = b (Eq. fe_matrix_system) on the free DoFs: the solver that a
+ * coarse space preconditions (Sec. 2.3, Eq. condition_bound) and the paper's
+ * reference solver for u_h (Sec. 5.3-5.4).  The preconditioner is
+ *   M^{-1} r = sum_j R_j^T A_j^{-1} R_j r + V A_0^{-1} V^T r,
+ * R_j the restriction to the DoFs of Omega_j off its cut boundary and off the
+ * clamped face, A_j = R_j A R_j^T (Dirichlet problems on the overlapping
+ * subdomains), V the coarse basis and A_0 = V^T A V.
+ *   local: a handle set up with oversampling equal to overlap (Omega*_j =
+ *          Omega_j, so its A11 factors are the A_j), one instance, one wave;
+ *          its layer blocks are assembled and factored here unless its last
+ *          msgfem_local_spaces left them in place (a GenEO handle's do).
+ *   coarse: a handle of the same mesh after msgfem_coarse_assemble (MS-GFEM or
+ *          GenEO coarse space; may be `local` itself), or NULL for the
+ *          one-level method.  Its coarse right-hand side is restored on exit.
+ *   b:     all 3 n_nodes DoFs (host or device; clamped entries ignored), or
+ *          NULL for the local handle's own load.
+ *   u0:    start vector (all DoFs, host or device), or NULL for zero; the
+ *          coarse solution u^G of msgfem_solve is a good one.
+ *   rtol:  stop when ||b - A u||_2 <= rtol ||b||_2 over the free DoFs (0 = 1e-10);
+ *   max_iter: 0 = 2000.  u_out (all DoFs, host or device) receives u.
+ *   info (may be NULL): iterations, final relative residual and the extreme
+ *          eigenvalues of M^{-1} A estimated from the CG coefficients (the
+ *          Lanczos matrix), and their ratio.
+ * Runs on the local handle's stream; uses the working blocks of both handles'
+ * eigensolvers as scratch (their local spaces and coarse problems are kept).
+ * Errors: EINVAL, ESTATE (no coarse problem on `coarse`), ENOCONV (max_iter
+ * reached; u_out holds the last iterate), ENOTSPD (CG broke down), ENOMEM,
+ * ECUDA. */
+typedef struct {
+  int iterations;
+  double residual;
+  double lambda_min, lambda_max, kappa;
+} msgfem_pcg_info;
+
+msgfem_status msgfem_schwarz_solve(msgfem_h local, msgfem_h coarse, const double* b, const double* u0, double rtol,
+                                   int max_iter, double* u_out, msgfem_pcg_info* info);
+
+/* Arithmetic throughput probe (not in the paper: the measured counterpart of
+ * the ALU peaks that bound the layer-block factorisation): dependent-chain FMA
+ * loops on every SM of the current device, FP64 (precision MSGFEM_FP64) or
+ * FP32 (MSGFEM_MIXED), timed with CUDA events on the default stream after a
+ * warm-up launch, best of three.  *tflops receives the rate in TFLOP/s (2 flops per FMA),
+ * *sm_count_out (may be NULL) the SM count.  Uses a small cudaMalloc'ed
+ * buffer of its own.  Errors: EINVAL, ENOMEM, ECUDA. */
+msgfem_status msgfem_probe_fma(int precision, double* tflops, double* sm_count_out);
+
+/* The structured numbering the handle works in (see msgfem_mesh): dims (may be
+ * NULL) receives {nx, ny, nz}; node_of_user[u] (may be NULL; n_nodes ints) the
+ * structured id (i (ny+1) + j)(nz+1) + k of node u of the caller's mesh and
+ * elem_of_user[e] (may be NULL; n_elems ints) the structured index
+ * (i ny + j) nz + k of element e; identities for a structured mesh.  Host
+ * pointers.  Errors: EINVAL. */
+msgfem_status msgfem_get_numbering(msgfem_h h, int* dims, int* node_of_user, int* elem_of_user);
 
 msgfem_status msgfem_get_info(msgfem_h h, int j, msgfem_subinfo* info);
 /* Copy the phase timers (requires msgfem_options.profile = 1 for times). */

@@ -104,6 +104,9 @@ msgfem_status dalloc(msgfem* h, T** p, size_t count) {
   return MSGFEM_OK;
 }
 
+// max that keeps a NaN (a NaN residual must never read as converged)
+inline double max_nan(double a, double b) { return (b > a || std::isnan(b)) ? b : a; }
+
 // Release one allocation made by dalloc (task lists replaced by the autotuner).
 void dfree(msgfem* h, void* p) { dev_free_bytes(h, p); }
 
@@ -118,6 +121,7 @@ bool is_device_ptr(const void* p) {
 }
 
 msgfem_status set_angles(msgfem* h, const double* ang) {
+  h->factored_wave = -1;
   const size_t nel = (size_t)h->NX * h->NY * h->NZ;
   const size_t ntot = nel * h->S;   // one field per instance
   h->h_angles.resize(ntot);
@@ -418,14 +422,33 @@ MSGFEM_TIMED_ORTHO(gram, (msgfem* h, int wx, int wy, int wg), (h, wx, wy, wg))
 MSGFEM_TIMED_ORTHO(rotate, (msgfem* h, int which, int wy, int ncols), (h, which, wy, ncols))
 #undef MSGFEM_TIMED_ORTHO
 
-// algorithmic flops of the layer-block factorisation (unpadded sizes)
-double factor_flops(const msgfem* h) {
+// flops of the layer-block factorisation (unpadded sizes n of the layers):
+// the block-tridiagonal Cholesky itself, per matrix sum over the nL layers of
+// n^3 / 3 (POTRF of the diagonal block) and, below the last layer, 2 n^3 (the
+// triangular solve for the coupling block and the update of the next diagonal
+// block); with_inverse adds the n^3 / 3 per layer of the explicit inverses of
+// the diagonal factors that this build forms for its solves
+double factor_flops(const msgfem* h, bool with_inverse = false) {
   double f = 0.0;
   for (const auto& s : h->sub)
     for (int n : {s.nK, s.nA}) {
       const double n3 = (double)n * n * n;
-      f += s.nzn * (2.0 * n3 / 3.0) + (s.nzn - 1) * 2.0 * n3;
+      f += s.nzn * ((with_inverse ? 2.0 : 1.0) * n3 / 3.0) + (s.nzn - 1) * 2.0 * n3;
     }
+  return f;
+}
+
+// flops the tile tasks of a factorisation schedule execute (64-row padding,
+// whole diagonal tiles and the inverses included): a POTRF tile task forms the
+// 64 x 64 Cholesky factor and its inverse, a GEMM tile task 2 64^2 K, plus
+// 2 64^3 for the post-multiplication by a 64 x 64 tile
+template <typename T>
+double schedule_flops(const ScheduleT<T>& sc) {
+  double f = 0.0;
+  for (const auto& t : sc.gemm) {
+    if (t.flags & G_POTRF) f += 2.0 * (64.0 * 64.0 * 64.0 / 3.0 + 64.0 * 64.0 * 64.0 / 6.0);
+    else f += 2.0 * 64.0 * 64.0 * t.K + ((t.flags & G_POSTMUL) ? 2.0 * 64.0 * 64.0 * 64.0 : 0.0);
+  }
   return f;
 }
 
@@ -598,16 +621,65 @@ void cholqr2_kb(msgfem* h, int j, bool have_nw) {
   }
 }
 
-// W <- M W for A-harmonic W: Z = B W, K solve, restrict to B2, A11 re-extension
+// W <- M W for A-harmonic W: Z = B W, K solve, restrict to B2, A11 re-extension.
+// GenEO: M = K^{-1} B on all free DoFs of Omega_j (no restriction, no extension).
 void apply_M_kb(msgfem* h) {
   timed_stencil_kb(h, MV_WB, MV_ZB, 3, 1.0);
   solve_K_kb(h);
-  launch_mask_kb(h, MV_WB, 1 << 2);
-  extend_kb(h);
+  if (!h->geneo) {
+    launch_mask_kb(h, MV_WB, 1 << 2);
+    extend_kb(h);
+  }
   project_rigid_kb(h, MV_WB);
 }
 
 }  // namespace
+
+// Layer-block factors of a one-wave handle made resident for the local
+// Dirichlet solves of the Schwarz preconditioner (msgfem_schwarz_solve): the
+// element stiffness and stencils when no local stage has run since the angles
+// were set, then the layer blocks and their factorisation, unless the last
+// local stage or an earlier call left them in place.
+msgfem_status schwarz_factors(msgfem* h) {
+  if (h->waves.size() != 1) {
+    h->err = "the Schwarz local solves need every subdomain's factors resident (one wave)";
+    return MSGFEM_EINVAL;
+  }
+  cudaStream_t st = h->stream;
+  set_dense_context(h->d_flags, h->d_notspd, h->d_sub);
+  h->cur = 0;
+  h->base_act.assign(h->N, 1);
+  TRY(set_active(h, h->base_act));
+  if (h->factored_wave == 0) return MSGFEM_OK;
+  CK(cudaMemsetAsync(h->d_notspd, 0, (h->N + 1) * sizeof(int), st));
+  if (h->stage < 2) {
+    launch_element_stiffness(h);
+    launch_stencil(h);
+  }
+  if (h->mixed) launch_layer_blocks_f32(h);
+  else launch_layer_blocks(h);
+  const WaveSched& ws = h->waves[0];
+  TRY(select_factor_kernel(h));
+  run_graph(h, (uint64_t)2 << 60, [&](cudaStream_t cs) {
+    if (h->mixed) run_schedule(ws.factf, cs, &h->gs);
+    else run_schedule(ws.fact, cs, &h->gs);
+  });
+  CK_LAUNCH();
+  std::vector<int> notspd(h->N + 1);
+  CK(cudaMemcpyAsync(notspd.data(), h->d_notspd, (h->N + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int j = 0; j < h->N; ++j)
+    if (notspd[j]) {
+      h->err = "non-positive pivot in a layer-block factorisation of subdomain " + std::to_string(j);
+      return MSGFEM_ENOTSPD;
+    }
+  h->factored_wave = 0;
+  return MSGFEM_OK;
+}
+
+// W_B1 = A11^{-1} T_B1 on the KB-wide working blocks of every subdomain (the
+// other rows of W are left as they are), in the handle's precision.
+void schwarz_local_solve(msgfem* h) { timed_solve8(h, 1, MV_TB, MV_WB, 0); }
 
 // Subspace iteration with Rayleigh-Ritz every step (solver = 1).
 msgfem_status run_subspace(msgfem* h, int n_loc, int p, bool& all_done) {
@@ -669,7 +741,7 @@ msgfem_status run_subspace(msgfem* h, int n_loc, int p, bool& all_done) {
       const int nw = n_loc - (h->sub[j].floating ? 6 : 0);
       double dmax = 0.0;
       for (int c = 0; c < nw; ++c)
-        dmax = std::max(dmax, std::sqrt(std::fabs(gdiag[(size_t)j * PST * PST + (size_t)c * PST + c])));
+        dmax = max_nan(dmax, std::sqrt(std::fabs(gdiag[(size_t)j * PST * PST + (size_t)c * PST + c])));
       // converged, or stalled at the rounding floor of the solves (less than 10 %
       // decrease over three iterations while already below 100 tol)
       bool done = dmax <= h->opt.tol;
@@ -700,35 +772,42 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
     nwmax = std::max(nwmax, nw[j]);
   }
   CK(cudaMemcpyAsync(h->d_nwk, nw.data(), h->N * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (h->geneo) {
+    // GenEO has no particular function
+    for (int j = 0; j < h->N; ++j)
+      if (act[j]) CK(cudaMemsetAsync(h->sub[j].psi, 0, (size_t)h->sub[j].nfull * sizeof(double), st));
+  }
   // particular function psi: A11 psi_1 = b_1 (one column of a KB-wide solve),
   // refined in mixed precision with the FP64 residual (K psi - b)_B1
-  launch_load_col_kb(h, MV_TB, -1.0);
-  launch_zero_kb(h, MV_WB);
-  if (h->mixed) {
-    flags_save(h);
-    launch_refine_check(h, MV_TB, -1, KEEP_A11, -1);   // reference ||b_B1||
+  if (!h->geneo) {
+    launch_load_col_kb(h, MV_TB, -1.0);
+    launch_zero_kb(h, MV_WB);
+    if (h->mixed) {
+      flags_save(h);
+      launch_refine_check(h, MV_TB, -1, KEEP_A11, -1);   // reference ||b_B1||
+    }
+    timed_solve8(h, 1, MV_TB, MV_WB, 1);
+    for (int r = 0; h->mixed && r < h->refine; ++r) {
+      timed_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
+      launch_sub_load_kb(h, MV_TB);
+      launch_refine_check(h, MV_TB, -1, KEEP_A11, r);
+      timed_solve_w(h, 1, MV_TB, MV_WB, 1, KB, 1);
+    }
+    if (h->mixed) flags_restore(h);
+    launch_take_col_kb(h, MV_WB);
   }
-  timed_solve8(h, 1, MV_TB, MV_WB, 1);
-  for (int r = 0; h->mixed && r < h->refine; ++r) {
-    timed_stencil_kb(h, MV_WB, MV_TB, 0, 1.0);
-    launch_sub_load_kb(h, MV_TB);
-    launch_refine_check(h, MV_TB, -1, KEEP_A11, r);
-    timed_solve_w(h, 1, MV_TB, MV_WB, 1, KB, 1);
-  }
-  if (h->mixed) flags_restore(h);
-  launch_take_col_kb(h, MV_WB);
   for (int j = 0; j < h->N; ++j)
     if (nw[j] <= 0) act[j] = 0;
   TRY(set_active(h, act));
   // start block on B2 (random, or a registered warm start on its first
-  // columns), A-harmonic extension, first application of M
+  // columns), A-harmonic extension, first application of M; GenEO: random on B1
   launch_random_kb(h, MV_WB, h->opt.seed);
   std::vector<int> warm(h->N, 0);
   if ((int)h->warm.size() == h->N && warm_upload(h)) {
     launch_load_start(h, MV_WB);
     for (int j = 0; j < h->N; ++j) warm[j] = h->warm[j].X0 != nullptr;
   }
-  extend_kb(h);
+  if (!h->geneo) extend_kb(h);   // A-harmonic start: extension of the B2 block (GenEO: a block on B1)
   project_rigid_kb(h, MV_WB);
   apply_M_kb(h);
   // Q_0 = W R^{-1} with W^T N W = R^T R (CholeskyQR2)
@@ -743,8 +822,13 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
   const int kkeep = std::min(PST, MQ - 2 * KB);   // Ritz vectors kept at a thick restart
   int restarts = 0;
   std::vector<int> kvec(h->N, kkeep);
+  // msgfem_options.max_iter caps the block steps (restarts included); once the
+  // cap is reached every active subdomain whose basis holds its wanted pairs
+  // takes a last Rayleigh-Ritz and the solver stops
+  int steps = 0;
   for (int j = 0; j < jmax && !all_done; ++j) {
     const int m = (j + 1) * KB;
+    const bool capped = ++steps >= h->opt.max_iter;
     apply_M_kb(h);   // W = M Q_j (W held Q_j)
     // two passes of block Gram-Schmidt against Q_0..Q_j in the N inner
     // product.  Each pass forms N W with a stencil pass (the first pass removes
@@ -765,13 +849,14 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
     }
     CK_LAUNCH();
     // Rayleigh-Ritz where the basis can hold the wanted pairs plus one block
-    bool any = false;
+    bool any = false, stop = capped;
     for (int s = 0; s < h->N; ++s) {
       // Rayleigh-Ritz once the basis can hold the wanted pairs plus one block
-      // (a warm-started subdomain: once it can hold the wanted pairs)
-      mk[s] = (act[s] && m >= nw[s] + (warm[s] ? 0 : KB)) ? m : 0;
+      // (a warm-started subdomain, or at the step cap: once it can hold the wanted pairs)
+      mk[s] = (act[s] && m >= nw[s] + ((warm[s] || capped) ? 0 : KB)) ? m : 0;
       any = any || mk[s] > 0;
       if (act[s]) h->iters[s] = j + 1;
+      if (act[s] && mk[s] == 0) stop = false;   // the cap waits for a basis that holds the wanted pairs
     }
     if (!any && m < MQ) continue;
     const bool full = m >= MQ;
@@ -791,13 +876,14 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
       if (!act[s]) continue;
       if (mk[s] > 0) {
         double rmax = 0.0;
-        for (int c = 0; c < nw[s]; ++c) rmax = std::max(rmax, res[(size_t)s * PST + c]);
+        for (int c = 0; c < nw[s]; ++c) rmax = max_nan(rmax, res[(size_t)s * PST + c]);
         h->m_final[s] = mk[s];
         if (rmax <= h->opt.tol) act[s] = 0;
       }
       if (act[s]) all_done = false;
     }
     TRY(set_active(h, act));
+    if (stop) break;
     if (full && !all_done && restarts < 8) {
       // thick restart of the unconverged subdomains: keep kkeep Ritz vectors and
       // the residual block, continue from block kkeep / KB
@@ -809,6 +895,7 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
       j = kkeep / KB - 1;
     }
   }
+  h->krylov_left = act;   // subdomains still unconverged
   // Ritz vectors of the wanted pairs (theta ascending in s.theta)
   TRY(set_active(h, h->base_act));
   CK(cudaMemcpyAsync(h->d_mk, h->m_final.data(), h->N * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -826,13 +913,22 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
   if (out == nullptr) return MSGFEM_EINVAL;
   *out = nullptr;
   if (!mesh || !plies || !part || !plies->E9 || !plies->elem_angle_deg) return MSGFEM_EINVAL;
+  // hexahedron lists, Dirichlet flags and element -> part maps: mapped onto the structured problem
+  if (mesh->kind != 0 || mesh->dirichlet_node != nullptr || part->elem_part != nullptr)
+    return setup_general(mesh, plies, part, overlap, oversampling, opt, out);
   if (mesh->nx <= 0 || mesh->ny <= 0 || mesh->nz <= 0) return MSGFEM_EINVAL;
   if (mesh->xyz == nullptr && (!(mesh->hx > 0) || !(mesh->hy > 0) || !(mesh->hz > 0))) return MSGFEM_EINVAL;
   if (part->n_boxes < 0 || (part->n_boxes > 0 && part->boxes == nullptr)) return MSGFEM_EINVAL;
   if (part->n_boxes == 0 && (part->sx <= 0 || part->sy <= 0 || part->sx > mesh->nx || part->sy > mesh->ny))
     return MSGFEM_EINVAL;
   if (overlap < 1 || oversampling < overlap) return MSGFEM_EINVAL;
+  if (!std::isfinite(mesh->traction) || !std::isfinite(mesh->hx) || !std::isfinite(mesh->hy) ||
+      !std::isfinite(mesh->hz))
+    return MSGFEM_EINVAL;
+  for (int i = 0; i < 9; ++i)
+    if (!std::isfinite(plies->E9[i])) return MSGFEM_EINVAL;
   msgfem* h = new msgfem();
+  *out = h;   // from here on a failed set-up returns the handle with its message (msgfem_destroy frees it)
   h->NX = mesh->nx; h->NY = mesh->ny; h->NZ = mesh->nz;
   h->hx = mesh->hx; h->hy = mesh->hy; h->hz = mesh->hz; h->traction = mesh->traction;
   memcpy(h->E9, plies->E9, sizeof(h->E9));
@@ -903,6 +999,20 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
     return MSGFEM_EINVAL;
   }
   h->mixed = h->opt.precision == MSGFEM_MIXED;
+  if (h->opt.method != MSGFEM_METHOD_MSGFEM && h->opt.method != MSGFEM_METHOD_GENEO) {
+    h->err = "unknown method";
+    return MSGFEM_EINVAL;
+  }
+  h->geneo = h->opt.method == MSGFEM_METHOD_GENEO;
+  if (h->opt.factor_kernel < 0 || h->opt.factor_kernel > 1 || (h->opt.factor_kernel == 1 && !h->mixed)) {
+    h->err = "factor_kernel: 0, or 1 (tensor cores) in mixed precision";
+    return MSGFEM_EINVAL;
+  }
+  h->factor_tc = h->opt.factor_kernel;
+  if (h->geneo && oversampling != overlap) {
+    h->err = "GenEO poses its local eigenproblem on Omega_j itself: oversampling must equal overlap";
+    return MSGFEM_EINVAL;
+  }
   h->S = h->opt.instances > 1 ? h->opt.instances : 1;
   h->refine = h->opt.refine > 0 ? h->opt.refine : 10;
   *out = h;
@@ -928,6 +1038,8 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
   CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
   prepare_tile_kernels();
   set_dense_context(h->d_flags, h->d_notspd, h->d_sub);
+  CK(cudaGetDevice(&h->device));
+  TRY(noalloc_prepare(h));
   h->stage = 1;
   return MSGFEM_OK;
 }
@@ -935,6 +1047,11 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
 msgfem_status msgfem_update_angles(msgfem_h h, const double* ang) {
   if (!h || !ang) return MSGFEM_EINVAL;
   if (h->stage < 1) return MSGFEM_ESTATE;
+  std::vector<double> perm;
+  if (!h->elem_of_user.empty()) {   // hexahedron list: angles in the list's element order
+    TRY(angles_in(h, ang, perm));
+    ang = perm.data();
+  }
   msgfem_status st = set_angles(h, ang);
   if (st == MSGFEM_OK) h->stage = 1;
   return st;
@@ -948,8 +1065,16 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   if (p > PST - 1) p = PST - 1;
   for (int j = 0; j < h->N; ++j) {
     const int nw = n_loc - (h->sub[j].floating ? 6 : 0);
-    if (n_loc > h->n2[j]) { h->err = "n_loc exceeds the B2 size of a subdomain"; return MSGFEM_EINVAL; }
+    // the eigenproblem lives on B2 (A-harmonic functions) or, for GenEO, on B1 where B is definite
+    if (n_loc > (h->geneo ? h->n1[j] : h->n2[j])) {
+      h->err = h->geneo ? "n_loc exceeds the B1 size of a subdomain" : "n_loc exceeds the B2 size of a subdomain";
+      return MSGFEM_EINVAL;
+    }
     if (nw > p) { h->err = "n_loc too large for the block size (at most 31 columns)"; return MSGFEM_EINVAL; }
+  }
+  if (h->geneo && h->opt.solver != 0) {
+    h->err = "the GenEO eigenproblem runs the block Krylov solver (solver = 0) only";
+    return MSGFEM_EINVAL;
   }
   if (h->opt.solver == 1 && h->mixed) {
     h->err = "subspace iteration (solver = 1) runs in FP64 only";
@@ -962,6 +1087,7 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   // from here on the earlier local spaces, coarse problem and solution are
   // being replaced: a failure leaves the handle needing a new local stage
   h->stage = 1;
+  h->factored_wave = -1;
   h->n_loc = n_loc;
   h->p = p;
   cudaStream_t st = h->stream;
@@ -971,6 +1097,9 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   CK(cudaMemsetAsync(h->d_notspd, 0, (h->N + 1) * sizeof(int), st));
   for (auto& s : h->sub) CK(cudaMemsetAsync(s.status, 0, 4 * sizeof(int), st));
   h->prof.factor_flops = factor_flops(h);
+  h->prof.factor_flops_inverse = factor_flops(h, true);
+  h->prof.factor_flops_executed = 0.0;
+  for (const auto& w : h->waves) h->prof.factor_flops_executed += h->mixed ? schedule_flops(w.factf) : schedule_flops(w.fact);
   h->prof.solve_flops = 0.0;
   h->prof.solve_bytes = 0.0;
   h->prof.stencil_flops = 0.0;
@@ -992,6 +1121,8 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   span_end(h, sp_iter);
   bool all_done = true;
   h->iters.assign(h->N, 0);
+  h->cold_restart.assign(h->N, 0);
+  h->krylov_left.assign(h->N, 0);
   h->m_final.assign(h->N, 0);
   // waves: layer blocks, factorisations, eigensolver and final residuals of
   // the subdomains that share the factor pool (one wave when all fit)
@@ -1007,6 +1138,7 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
     span_end(h, sp);
     CK_LAUNCH();
     // 2. factorisations of K and A11
+    TRY(select_factor_kernel(h));
     sp = span_begin(h, TAG_FACTOR);
     run_graph(h, ((uint64_t)2 << 60) | ((uint64_t)w << 48), [&](cudaStream_t cs) {
       if (h->mixed) run_schedule(ws.factf, cs, &h->gs);
@@ -1014,12 +1146,42 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
     });
     span_end(h, sp);
     CK_LAUNCH();
+    h->factored_wave = (int)w;
     sp_iter = span_begin(h, TAG_ITERATE);
     bool done = false;
     if (h->opt.solver == 1) {
       TRY(run_subspace(h, n_loc, p, done));
     } else {
       TRY(run_krylov(h, n_loc, done));
+      // a learned (or any registered) start that did not lead to convergence is
+      // dropped: those subdomains are solved again from the cold start
+      std::vector<int> redo(h->N, 0);
+      bool any_redo = false;
+      if (!done && (int)h->warm.size() == h->N)
+        for (int j : ws.members)
+          if (h->krylov_left[j] && h->warm[j].X0 != nullptr) {
+            redo[j] = 1;
+            any_redo = true;
+          }
+      if (any_redo) {
+        const std::vector<WarmStart> kept = h->warm;
+        for (int j = 0; j < h->N; ++j)
+          if (redo[j]) {
+            h->warm[j] = WarmStart{};
+            h->cold_restart[j] = 1;
+          }
+        const std::vector<int> wave_act = h->base_act;
+        h->base_act = redo;
+        TRY(set_active(h, redo));
+        bool redo_done = false;
+        const msgfem_status rst = run_krylov(h, n_loc, redo_done);
+        h->warm = kept;
+        h->base_act = wave_act;
+        TRY(rst);
+        done = true;
+        for (int j : ws.members)
+          if (h->krylov_left[j]) done = false;
+      }
     }
     all_done = all_done && done;
     TRY(set_active(h, h->base_act));
@@ -1028,14 +1190,19 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
       const SubDev& s = h->sub[j];
       CK(cudaMemsetAsync(s.T1, 0, (size_t)s.nfull * PST * sizeof(double), st));
     }
-    timed_solve(h, 1, MV_Z, MV_T1, 0);
-    for (int r = 0; h->mixed && r < std::min(h->refine, 5); ++r) {   // refine y~: residual Z - K y~ on B1
+    if (h->geneo) {
+      // GenEO: ||K phi - lambda B phi|| / (||K phi|| + lambda ||B phi||) over B1 and B2
+      launch_colnorms(h, MV_KPHI, MV_Z, p, KEEP_K, -1.0);
+    } else {
+      timed_solve(h, 1, MV_Z, MV_T1, 0);
+      for (int r = 0; h->mixed && r < std::min(h->refine, 5); ++r) {   // refine y~: residual Z - K y~ on B1
+        timed_stencil_apply(h, MV_T1, MV_W, 0, 1.0);
+        launch_x_minus_y(h, MV_Z, MV_W, MV_W, PST);
+        timed_solve_w(h, 1, MV_W, MV_T1, 0, PST, 1);
+      }
       timed_stencil_apply(h, MV_T1, MV_W, 0, 1.0);
-      launch_x_minus_y(h, MV_Z, MV_W, MV_W, PST);
-      timed_solve_w(h, 1, MV_W, MV_T1, 0, PST, 1);
+      launch_colnorms(h, MV_KPHI, MV_W, p);
     }
-    timed_stencil_apply(h, MV_T1, MV_W, 0, 1.0);
-    launch_colnorms(h, MV_KPHI, MV_W, p);
     span_end(h, sp_iter);
   }
   h->cur = 0;
@@ -1062,7 +1229,7 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
     CK(cudaMemcpyAsync(&theta[(size_t)j * PST], h->sub[j].theta, PST * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     const int nw = n_loc - (h->sub[j].floating ? 6 : 0);
-    for (int c = 0; c < nw; ++c) h->resid_max[j] = std::max(h->resid_max[j], res[c]);
+    for (int c = 0; c < nw; ++c) h->resid_max[j] = max_nan(h->resid_max[j], res[c]);
   }
   std::vector<double>& lam = h->lam_host;
   lam.assign((size_t)h->N * n_loc, 0.0);
@@ -1079,6 +1246,19 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   }
   h->stage = 2;
   spans_collect(h);
+  for (int j = 0; j < h->N; ++j)
+    for (int c = 0; c < n_loc; ++c)
+      if (!std::isfinite(lam[(size_t)j * n_loc + c]) || std::fabs(lam[(size_t)j * n_loc + c]) >= 1e299 ||
+          !std::isfinite(h->resid_max[j])) {
+        h->err = "non-finite eigenvalue or residual in subdomain " + std::to_string(j);
+        h->stage = 1;
+        return MSGFEM_ENOCONV;
+      }
+  for (int j = 0; j <= h->N; ++j)
+    if (notspd[j] & 2) {
+      h->err = "a tensor-core tile task of subdomain " + std::to_string(j) + " did not complete within its time limit";
+      return MSGFEM_ECUDA;
+    }
   for (int j = 0; j <= h->N; ++j)
     if (notspd[j]) {
       h->err = "non-positive pivot in a layer-block factorisation of subdomain " + std::to_string(j);
@@ -1128,12 +1308,12 @@ msgfem_status msgfem_coarse_assemble_threshold(msgfem_h h, double t, int* coarse
   std::vector<int> ncols(h->N);
   for (int j = 0; j < h->N; ++j) {
     const SubDev& s = h->sub[j];
-    ncols[j] = h->m_sel[j] + (s.loaded ? 1 : 0);
+    ncols[j] = h->m_sel[j] + ((s.loaded && !h->geneo) ? 1 : 0);
     CK(cudaMemcpyAsync(s.CB, s.EV, (size_t)s.nfull * PST * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
   CK(cudaMemcpyAsync(h->d_ncols, ncols.data(), h->N * sizeof(int), cudaMemcpyHostToDevice, st));
   for (int j = 0; j < h->N; ++j)
-    if (h->sub[j].loaded)
+    if (h->sub[j].loaded && !h->geneo)
       CK(cudaMemcpy2DAsync(h->sub[j].CB + h->m_sel[j], PST * sizeof(double), h->sub[j].psi, sizeof(double),
                            sizeof(double), h->sub[j].nfull, cudaMemcpyDeviceToDevice, st));
   // Gram-Schmidt in the B inner product (CholeskyQR, twice); psi dropped if dependent
@@ -1210,12 +1390,24 @@ msgfem_status msgfem_solve(msgfem_h h, double* u_out, const double* u_ref, doubl
   launch_prolong(h);
   span_end(h, sp_c);
   CK_LAUNCH();
-  const size_t ndof = 3 * (size_t)(h->NX + 1) * (h->NY + 1) * (h->NZ + 1);
-  if (u_out) {
-    CK(cudaMemcpyAsync(u_out, h->d_u, ndof * sizeof(double), cudaMemcpyDefault, st));
+  {
+    // the coarse coefficients decide u^G: a non-finite one means the coarse problem broke down
+    std::vector<double> c(h->Nc);   // column 0 of the [NcPad][PST] coefficient block
+    if (h->Nc > 0)
+      CK(cudaMemcpy2DAsync(c.data(), sizeof(double), h->d_cH, PST * sizeof(double), sizeof(double), h->Nc,
+                           cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (double v : c)
+      if (!std::isfinite(v)) {
+        h->err = "non-finite coarse coefficient (the coarse matrix is not positive definite)";
+        return MSGFEM_ENOTSPD;
+      }
   }
+  const size_t ndof = 3 * (size_t)(h->NX + 1) * (h->NY + 1) * (h->NZ + 1);
+  (void)ndof;
+  if (u_out) TRY(vec_out(h, h->d_u, u_out));
   if (u_ref) {
-    CK(cudaMemcpyAsync(h->d_ref, u_ref, ndof * sizeof(double), cudaMemcpyDefault, st));
+    TRY(vec_in(h, u_ref, h->d_ref));
     launch_energy(h, h->d_ref, h->d_u, h->d_energy);
     const int nb = energy_blocks(h);
     std::vector<double> e(2 * nb);
@@ -1338,6 +1530,7 @@ msgfem_status msgfem_get_info(msgfem_h h, int j, msgfem_subinfo* info) {
   info->basis_size = j < (int)h->basis_m.size() ? h->basis_m[j] : 0;
   info->residual = j < (int)h->resid_max.size() ? h->resid_max[j] : 0.0;
   info->threshold_reached = j < (int)h->thr_reached.size() ? h->thr_reached[j] : 1;
+  info->cold_restart = j < (int)h->cold_restart.size() ? h->cold_restart[j] : 0;
   return MSGFEM_OK;
 }
 
@@ -1345,6 +1538,7 @@ msgfem_status msgfem_autotune(msgfem_h h, int reps, msgfem_tuning* out) {
   if (!h) return MSGFEM_EINVAL;
   if (h->stage < 2) return MSGFEM_ESTATE;
   if (reps <= 0) reps = 3;
+  h->factored_wave = -1;   // the timed factorisations leave scratch in the pool
   cudaStream_t st = h->stream;
   CK(cudaStreamSynchronize(st));
   // the task lists are re-uploaded below: drop every captured factorisation and
@@ -1372,42 +1566,97 @@ msgfem_status msgfem_autotune(msgfem_h h, int reps, msgfem_tuning* out) {
   CK(cudaEventCreate(&f1));
   // factorisation schedule of the last wave: right- vs left-looking over 16 or
   // 32 stream groups, each timed on freshly assembled layer blocks (the second
-  // of two runs)
-  int best_f = h->factor_left, best_fg = h->ngroup_factor;
+  // of two runs); in mixed precision with the FMA tile kernel and with the
+  // tensor-core one
+  int best_f = h->factor_left, best_fg = h->ngroup_factor, best_k = h->factor_tc;
   double best_fms = 1e300;
   const int fgroups[2] = {16, 32};
+  auto factor_once = [&](float* ms) -> msgfem_status {
+    if (h->mixed) launch_layer_blocks_f32(h);
+    else launch_layer_blocks(h);
+    CK(cudaEventRecord(f0, st));
+    if (h->mixed) run_schedule(wl.factf, st, &h->gs);
+    else run_schedule(wl.fact, st, &h->gs);
+    CK(cudaEventRecord(f1, st));
+    CK(cudaEventSynchronize(f1));
+    if (ms) CK(cudaEventElapsedTime(ms, f0, f1));
+    return MSGFEM_OK;
+  };
+  t.tc_factor_diff = -1.0;
   for (int fv = 0; fv < 2; ++fv)
-    for (int gi = 0; gi < 2; ++gi) {
-      t.factor_ms[fv][gi] = -1.0;
-      if (fgroups[gi] > h->ngroup_created) continue;
-      h->factor_left = fv;
-      h->ngroup_factor = fgroups[gi];
-      build_wave_factor_schedule(h, wl);
-      TRY(upload_wave_factor(h, wl));
-      float ms = 0.f;
-      for (int rep = 0; rep < 2; ++rep) {
-        if (h->mixed) launch_layer_blocks_f32(h);
-        else launch_layer_blocks(h);
-        CK(cudaEventRecord(f0, st));
-        if (h->mixed) run_schedule(wl.factf, st, &h->gs);
-        else run_schedule(wl.fact, st, &h->gs);
-        CK(cudaEventRecord(f1, st));
-        CK(cudaEventSynchronize(f1));
-        CK(cudaEventElapsedTime(&ms, f0, f1));
+    for (int gi = 0; gi < 2; ++gi) t.factor_ms[fv][gi] = t.factor_ms_tc[fv][gi] = -1.0;
+  for (int kern = 0; kern < (h->mixed ? 2 : 1); ++kern) {
+    h->factor_tc = kern;
+    TRY(select_factor_kernel(h));
+    for (int fv = 0; fv < 2; ++fv)
+      for (int gi = 0; gi < 2; ++gi) {
+        if (fgroups[gi] > h->ngroup_created) continue;
+        h->factor_left = fv;
+        h->ngroup_factor = fgroups[gi];
+        build_wave_factor_schedule(h, wl);
+        TRY(upload_wave_factor(h, wl));
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) TRY(factor_once(&ms));
+        (kern ? t.factor_ms_tc : t.factor_ms)[fv][gi] = ms;
+        if (kern == 0 && ms < best_fms) {
+          best_fms = ms;
+          best_f = fv;
+          best_fg = fgroups[gi];
+          best_k = 0;
+        }
       }
-      t.factor_ms[fv][gi] = ms;
-      if (ms < best_fms) {
-        best_fms = ms;
-        best_f = fv;
-        best_fg = fgroups[gi];
+  }
+  if (h->mixed) {
+    // accuracy gate of the tensor-core kernel: its factor of the first subdomain
+    // of the wave against the FMA kernel's, both with the fastest FMA schedule
+    h->factor_left = best_f;
+    h->ngroup_factor = best_fg;
+    build_wave_factor_schedule(h, wl);
+    TRY(upload_wave_factor(h, wl));
+    const SubDev& s0 = h->sub[wl.members[0]];
+    const size_t nK = (size_t)s0.bK * s0.bK, nA = (size_t)s0.bA * s0.bA;
+    const float* arr[4] = {s0.DKf, s0.LKf, s0.DAf, s0.LAf};
+    const size_t len[4] = {nK * (2 * s0.nzn - 1), nK * s0.nzn, nA * (2 * s0.nzn - 1), nA * s0.nzn};
+    std::vector<std::vector<float>> ref(4), got(4);
+    h->factor_tc = 0;
+    TRY(select_factor_kernel(h));
+    TRY(factor_once(nullptr));
+    for (int a = 0; a < 4; ++a) {
+      ref[a].resize(len[a]);
+      CK(cudaMemcpy(ref[a].data(), arr[a], len[a] * sizeof(float), cudaMemcpyDeviceToHost));
+    }
+    h->factor_tc = 1;
+    TRY(select_factor_kernel(h));
+    TRY(factor_once(nullptr));
+    double num = 0.0, den = 0.0;
+    for (int a = 0; a < 4; ++a) {
+      got[a].resize(len[a]);
+      CK(cudaMemcpy(got[a].data(), arr[a], len[a] * sizeof(float), cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < len[a]; ++i) {
+        const double d = (double)got[a][i] - (double)ref[a][i];
+        num += d * d;
+        den += (double)ref[a][i] * ref[a][i];
       }
     }
+    t.tc_factor_diff = den > 0.0 ? std::sqrt(num / den) : (num > 0.0 ? 1.0 : 0.0);
+    if (t.tc_factor_diff <= 1e-4)
+      for (int fv = 0; fv < 2; ++fv)
+        for (int gi = 0; gi < 2; ++gi)
+          if (t.factor_ms_tc[fv][gi] >= 0.0 && t.factor_ms_tc[fv][gi] < best_fms) {
+            best_fms = t.factor_ms_tc[fv][gi];
+            best_f = fv;
+            best_fg = fgroups[gi];
+            best_k = 1;
+          }
+  }
   CK(cudaEventDestroy(f0));
   CK(cudaEventDestroy(f1));
   h->factor_left = best_f;
   h->ngroup_factor = best_fg;
+  h->factor_tc = best_k;
   t.factor_schedule = best_f;
   t.factor_streams = best_fg;
+  t.factor_kernel = best_k;
   const int groups[4] = {4, 8, 16, 32};
   const int variants[3] = {SOLVE_ASYNC_RING, SOLVE_STREAM, SOLVE_STREAM_CL2};
   double best = 1e300;
@@ -1495,10 +1744,13 @@ msgfem_status msgfem_reset_profile(msgfem_h h) {
   if (!h) return MSGFEM_EINVAL;
   spans_collect(h);
   const double ff = h->prof.factor_flops, sf = h->prof.solve_flops, sb = h->prof.solve_bytes;
-  const double stf = h->prof.stencil_flops;
+  const double stf = h->prof.stencil_flops, ffi = h->prof.factor_flops_inverse;
+  const double ffx = h->prof.factor_flops_executed;
   const int sc = h->prof.solve_calls;
   h->prof = msgfem_profile{};
   h->prof.factor_flops = ff;
+  h->prof.factor_flops_inverse = ffi;
+  h->prof.factor_flops_executed = ffx;
   h->prof.solve_flops = sf;
   h->prof.solve_bytes = sb;
   h->prof.stencil_flops = stf;

@@ -196,6 +196,8 @@ struct msgfem {
   std::vector<SubDev> sub;
   std::vector<HostSub> hsub;
   std::vector<int> n1, n2, n3, iters, basis_m, m_final;
+  std::vector<int> krylov_left;      // [N] 1 if the last block Krylov run left the subdomain unconverged
+  std::vector<int> cold_restart;     // [N] 1 if a registered start block was dropped for a cold start
   std::vector<double> lam_host;      // [N][n_loc] eigenvalues of the last local stage (rigid zeros first)
   std::vector<int> m_sel;            // [N] eigenvectors in the coarse basis (threshold selection)
   std::vector<int> thr_reached;      // [N] 0 if all n_loc eigenvalues were below the threshold
@@ -226,6 +228,9 @@ struct msgfem {
   void* d_pool = nullptr;            // layer-block / solve-buffer pool
   size_t pool_bytes = 0;
   int mixed = 0;                     // precision == MSGFEM_MIXED
+  int geneo = 0;                     // method == MSGFEM_METHOD_GENEO: the GenEO eigenproblem on Omega_j
+  int factor_tc = 0;                 // FP32 factorisation on the tensor cores (msgfem_options.factor_kernel)
+  void* d_tc_maps = nullptr;         // device tensor maps of every subdomain's FP32 arrays (4 per subdomain)
   int refine = 2;                    // FP64 refinement steps per FP32 solve
   std::vector<CoarsePair> pairs;
   CoarsePair* d_pairs = nullptr;
@@ -258,6 +263,22 @@ struct msgfem {
   std::vector<WarmStart> warm;       // [N] registered start blocks
   void* d_warm = nullptr;            // device descriptors of the start blocks
   std::vector<int*> d_b2rows;        // [N] ascending full-layout rows of B2
+  // device current at msgfem_setup, and the address of the fixed scratch array of
+  // msgfem_energy_error_noalloc on it
+  int device = -1;
+  double* noalloc_scratch = nullptr;
+  // wave whose layer-block factors are resident in the pool (-1: none or stale)
+  int factored_wave = -1;
+  // a hexahedron-list mesh: structured id of every node / element of the list,
+  // and on the device the same map, its inverse and a staging vector
+  std::vector<int> node_of_user, elem_of_user;
+  int* d_node_of_user = nullptr;
+  int* d_user_of_node = nullptr;
+  double* d_perm_tmp = nullptr;
+  // two-level Schwarz PCG (msgfem_schwarz_solve): global vectors x, r, z, p, q
+  // on all DoFs, partial sums of the dot products
+  double* d_pcg_vec = nullptr;
+  double* d_pcg_part = nullptr;
 };
 
 extern long long g_launch_count;   // kernel launches issued by this library
@@ -289,6 +310,14 @@ void element_types(const msgfem* h, bool& layered, std::vector<double>& types, s
 
 // launchers
 void set_dense_context(int* active, int* notspd, const SubDev* subs);
+// FP32 factorisation kernel of the next schedule runs: the tensor-core tile
+// kernel when tc_maps (device tensor maps of the subdomains' FP32 arrays) is
+// given, else the SIMT one
+void set_factor_kernel(const void* tc_maps);
+// encode and upload h->d_tc_maps (k_dense.cu)
+msgfem_status tc_maps_build(msgfem* h);
+// the kernel choice of h for its next factorisation (tensor maps built on first use)
+msgfem_status select_factor_kernel(msgfem* h);
 void prepare_tile_kernels();
 template <typename T>
 void run_schedule(const ScheduleT<T>& s, cudaStream_t st, const StreamSet* gs = nullptr);
@@ -298,6 +327,31 @@ template <typename T>
 void run_solve_mv(const SolveScheduleT<T>& s, cudaStream_t st, int src, int dst, int gather_neg, int width = PST,
                   const StreamSet* gs = nullptr, int scatter_add = 0, int variant = SOLVE_DEFAULT);
 void launch_element_stiffness(msgfem* h);
+// Structured numbering of a hexahedron list (hexmesh.cpp): the (i, j, k) block
+// dimensions and, for every node and element of the list, its structured id.
+struct HexNumbering {
+  int nx = 0, ny = 0, nz = 0;
+  std::vector<int> node_of_user, elem_of_user;
+};
+bool recover_structure(int n_nodes, int n_elems, const int* hex8, HexNumbering& out, std::string& err);
+// element boxes {x0, x1, y0, y1} of the parts of a structured element -> part map
+bool parts_to_boxes(int NX, int NY, int NZ, const int* elem_part, std::vector<int>& boxes, std::string& err);
+// per-node Dirichlet flags (structured order) equal to the clamped face i = 0
+bool dirichlet_is_clamped_face(int NX, int NY, int NZ, const unsigned char* flags, std::string& err);
+
+// general mesh input (k_numbering.cu): set-up through the structured path, and
+// node-major vectors on all DoFs between the caller's numbering (host or
+// device) and the structured one on the device; element angles into the
+// structured order on the host
+msgfem_status setup_general(const msgfem_mesh* mesh, const msgfem_plies* plies, const msgfem_partition* part,
+                            int overlap, int oversampling, const msgfem_options* opt, msgfem_h* out);
+msgfem_status vec_in(msgfem* h, const double* user, double* d_struct);
+msgfem_status vec_out(msgfem* h, const double* d_struct, double* user);
+msgfem_status angles_in(msgfem* h, const double* user, std::vector<double>& out);
+
+// load vector on all DoFs (given nodal loads or the end-face traction), zero on
+// the clamped face (setup.cpp)
+std::vector<double> global_load(const msgfem* h);
 // node coordinates of node (i, j, k): given, or those of the box (setup.cpp)
 void node_xyz(const msgfem* h, int i, int j, int k, double X[3]);
 void launch_stencil(msgfem* h);
@@ -315,7 +369,9 @@ void launch_copy_col(msgfem* h, int wsrc, int scol, int wdst, int dcol, double s
 void launch_copy_mv(msgfem* h, int wsrc, int wdst);
 void launch_rigid_modes(msgfem* h);
 void launch_chol_inv_small(msgfem* h, int wg, const int* d_ncols, int nfixed, int drop_last);
-void launch_colnorms(msgfem* h, int wa, int wb, int p);
+// relative residual per column c < p over the rows of the DoF classes in keep:
+// ||A_c + sgn theta_c B_c|| / (||A_c|| + |theta_c| ||B_c||) into resid
+void launch_colnorms(msgfem* h, int wa, int wb, int p, int keep = 1 << 2, double sgn = 1.0);
 void launch_scale_rows_mu(msgfem* h, int which);
 void launch_theta_axpy(msgfem* h, int wx, int wy, int wd, int p);
 void launch_x_minus_y(msgfem* h, int wx, int wy, int wd, int stride);
@@ -348,6 +404,15 @@ void launch_basis_out(msgfem* h, int j, double* d_out, int ncols);
 // one vector of subdomain j between the internal layout and that of
 // msgfem_get_basis (to_output 1: internal -> output)
 void launch_vec_layout(msgfem* h, int j, const double* src, int sstride, double* dst, int dstride, int to_output);
+
+// two-level Schwarz PCG (k_schwarz.cu): factors of a one-wave handle made
+// resident, and the A11 solve of the KB-wide working blocks (TB -> WB)
+msgfem_status schwarz_factors(msgfem* h);
+void schwarz_local_solve(msgfem* h);
+
+// msgfem_energy_error_noalloc (k_noalloc.cu): resolve its fixed array on the
+// current device (called by msgfem_setup)
+msgfem_status noalloc_prepare(msgfem* h);
 
 // learned warm start (k_warm.cu)
 msgfem_status warm_rows(msgfem* h);

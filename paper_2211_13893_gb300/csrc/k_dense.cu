@@ -21,6 +21,8 @@
 #include <cooperative_groups.h>
 #include <type_traits>
 
+#include "tc_gemm.cuh"
+
 namespace cg = cooperative_groups;
 
 // compile-time tunables of the streaming solve
@@ -204,16 +206,7 @@ constexpr int SKC = 32;
 constexpr int KC32 = 32;
 constexpr int LDS32 = 68;   // shared row stride (floats): 16-byte aligned rows
 
-__global__ void __launch_bounds__(256)
-k_tile_task_f32(const TileTaskT<float>* __restrict__ tasks, const int* __restrict__ active,
-                int* __restrict__ notspd) {
-  const TileTaskT<float> t = tasks[blockIdx.x];
-  if (t.sub >= 0 && active != nullptr && !active[t.sub]) return;
-  extern __shared__ double smem_d[];
-  if (t.flags & G_POTRF) {
-    tile_potrf_inv(t, reinterpret_cast<double (*)[65]>(smem_d), notspd);
-    return;
-  }
+__device__ __forceinline__ void f32_tile_gemm(const TileTaskT<float>& t, double* smem_d) {
   float* smem = reinterpret_cast<float*>(smem_d);
   float (*As)[LDS32] = reinterpret_cast<float (*)[LDS32]>(smem);                  // [KC32][LDS32]: As[k][m]
   float (*Bs)[LDS32] = reinterpret_cast<float (*)[LDS32]>(smem + KC32 * LDS32);   // [KC32][LDS32]: Bs[k][n]
@@ -310,6 +303,40 @@ k_tile_task_f32(const TileTaskT<float>* __restrict__ tasks, const int* __restric
     }
     *c = v;
   }
+}
+
+__global__ void __launch_bounds__(256)
+k_tile_task_f32(const TileTaskT<float>* __restrict__ tasks, const int* __restrict__ active,
+                int* __restrict__ notspd) {
+  const TileTaskT<float> t = tasks[blockIdx.x];
+  if (t.sub >= 0 && active != nullptr && !active[t.sub]) return;
+  extern __shared__ double smem_d[];
+  if (t.flags & G_POTRF) {
+    tile_potrf_inv(t, reinterpret_cast<double (*)[65]>(smem_d), notspd);
+    return;
+  }
+  f32_tile_gemm(t, smem_d);
+}
+
+// The same task semantics with the plain GEMM tasks (A op(B)^T, no
+// post-multiplication) on the tensor cores (tc_gemm.cuh: TMA, tcgen05.mma in
+// split TF32, TMEM accumulator); POTRF tasks and the block-inverse tasks keep
+// their FP64 / FP32 SIMT paths.
+__global__ void __launch_bounds__(256)
+k_tile_task_tc(const TileTaskT<float>* __restrict__ tasks, const int* __restrict__ active, int* __restrict__ notspd,
+               const SubDev* __restrict__ subs, const CUtensorMap* __restrict__ maps) {
+  const TileTaskT<float> t = tasks[blockIdx.x];
+  if (t.sub >= 0 && active != nullptr && !active[t.sub]) return;
+  extern __shared__ double smem_d[];
+  if (t.flags & G_POTRF) {
+    tile_potrf_inv(t, reinterpret_cast<double (*)[65]>(smem_d), notspd);
+    return;
+  }
+  if ((t.flags & G_POSTMUL) || !(t.flags & G_TRANSB) || t.K % tc::KCH != 0 || t.sub < 0) {
+    f32_tile_gemm(t, smem_d);
+    return;
+  }
+  tc::gemm_task(t, reinterpret_cast<unsigned char*>(smem_d), subs, maps, notspd);
 }
 
 template <typename T, int PC>
@@ -764,11 +791,94 @@ long long g_launch_count = 0;
 static int* g_active = nullptr;   // set by the driver before schedule runs
 static int* g_notspd = nullptr;
 static const SubDev* g_subs = nullptr;
+static const void* g_tc_maps = nullptr;   // tensor maps of the FP32 arrays: tensor-core factorisation on
 
 void set_dense_context(int* active, int* notspd, const SubDev* subs) {
   g_active = active;
   g_notspd = notspd;
   g_subs = subs;
+}
+
+void set_factor_kernel(const void* tc_maps) { g_tc_maps = tc_maps; }
+
+bool encode_tc_maps(const msgfem* h, std::vector<CUtensorMap>& maps, std::string& err);
+
+msgfem_status tc_maps_build(msgfem* h) {
+  std::vector<CUtensorMap> maps;
+  std::string err;
+  if (!encode_tc_maps(h, maps, err)) {
+    h->err = err;
+    return MSGFEM_ECUDA;
+  }
+  if (h->d_tc_maps == nullptr) TRY(dev_alloc_bytes(h, &h->d_tc_maps, maps.size() * sizeof(CUtensorMap)));
+  CK(cudaMemcpy(h->d_tc_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+  return MSGFEM_OK;
+}
+
+msgfem_status select_factor_kernel(msgfem* h) {
+  if (h->mixed && h->factor_tc) {
+    if (h->d_tc_maps == nullptr) TRY(tc_maps_build(h));
+    set_factor_kernel(h->d_tc_maps);
+  } else {
+    set_factor_kernel(nullptr);
+  }
+  return MSGFEM_OK;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  if (fn == nullptr) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// Tensor maps of every subdomain's four FP32 arrays (layer blocks D|E and
+// inverses of K, then of A11): 2-D row-major arrays of b FP32 columns, boxes of
+// 64 rows x 32 columns (128 bytes, the swizzle width) with 128-byte swizzle.
+// Every tile task of the factorisation starts on a 64-column tile boundary, so
+// each copy's inner coordinate is a multiple of 32 elements (128 bytes).
+bool encode_tc_maps(const msgfem* h, std::vector<CUtensorMap>& maps, std::string& err) {
+  EncodeTiledFn enc = encode_tiled();
+  if (enc == nullptr) {
+    err = "cuTensorMapEncodeTiled is not available from the driver";
+    return false;
+  }
+  maps.assign(4 * (size_t)h->N, CUtensorMap{});
+  for (int j = 0; j < h->N; ++j) {
+    const SubDev& s = h->sub[j];
+    const float* base[4] = {s.DKf, s.LKf, s.DAf, s.LAf};
+    const int b[4] = {s.bK, s.bK, s.bA, s.bA};
+    const int rows[4] = {(2 * s.nzn - 1) * s.bK, s.nzn * s.bK, (2 * s.nzn - 1) * s.bA, s.nzn * s.bA};
+    for (int m = 0; m < 4; ++m) {
+      if (base[m] == nullptr || b[m] < TILE) {
+        err = "tensor maps: a subdomain has no FP32 layer blocks";
+        return false;
+      }
+      const cuuint64_t dim[2] = {(cuuint64_t)b[m], (cuuint64_t)rows[m]};
+      const cuuint64_t stride[1] = {(cuuint64_t)b[m] * sizeof(float)};
+      const cuuint32_t box[2] = {(cuuint32_t)tc::KCH, 64};
+      const cuuint32_t estr[2] = {1, 1};
+      const CUresult r = enc(&maps[4 * (size_t)j + m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                             const_cast<float*>(base[m]), dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) {
+        err = "cuTensorMapEncodeTiled failed for subdomain " + std::to_string(j);
+        return false;
+      }
+    }
+  }
+  return true;
 }
 
 // Launch the steps of all groups: group g on stream gs->s[g] (forked from and
@@ -805,6 +915,7 @@ void prepare_tile_kernels() {
   cudaFuncSetAttribute(k_tile_task<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
   cudaFuncSetAttribute(k_tile_task<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
   cudaFuncSetAttribute(k_tile_task_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM);
+  cudaFuncSetAttribute(k_tile_task_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(TILE_SMEM, tc::SMEM));
   cudaFuncSetAttribute(k_solve_stream<double, SOLVE_CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
   cudaFuncSetAttribute(k_solve_stream<float, SOLVE_CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
   cudaFuncSetAttribute(k_solve_stream<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
@@ -820,6 +931,11 @@ void run_schedule(const ScheduleT<T>& s, cudaStream_t st, const StreamSet* gs) {
   prepare_tile_kernels();
   run_groups(s, st, gs, [&](const SchedStep& step, cudaStream_t stream) {
     if constexpr (std::is_same<T, float>::value) {
+      if (s.k32 && g_tc_maps != nullptr) {
+        k_tile_task_tc<<<step.count, 256, std::max(TILE_SMEM, tc::SMEM), stream>>>(
+            s.d_gemm + step.first, g_active, g_notspd, g_subs, static_cast<const CUtensorMap*>(g_tc_maps));
+        return;
+      }
       if (s.k32) {
         k_tile_task_f32<<<step.count, 256, TILE_SMEM, stream>>>(s.d_gemm + step.first, g_active, g_notspd);
         return;

@@ -147,7 +147,8 @@ extern "C" msgfem_status msgfem_solution_errors(msgfem_h h, const double* u_ref,
   }
   cudaStream_t st = h->stream;
   const size_t ndof = 3 * (size_t)(h->NX + 1) * (h->NY + 1) * (h->NZ + 1);
-  CK(cudaMemcpyAsync(h->d_ref, u_ref, ndof * sizeof(double), cudaMemcpyDefault, st));
+  (void)ndof;
+  TRY(vec_in(h, u_ref, h->d_ref));
   const int nb = l2_error_blocks(h);
   k_l2_errors<<<nb, ERR_THREADS, 0, st>>>(h->d_ref, h->d_u, h->NX, h->NY, h->NZ, h->hx, h->hy, h->hz, h->d_xyz,
                                           h->d_l2);

@@ -482,7 +482,7 @@ k_small_eig(const SubDev* __restrict__ subs, const int* __restrict__ active, int
 // alpha_c = theta[c].  Partial per chunk; reduced by k_colnorm_reduce.
 __global__ void __launch_bounds__(256)
 k_colnorm_partial(const SubDev* __restrict__ subs, const int* __restrict__ active, int wa, int wb,
-                  double* __restrict__ part, int nchunk) {
+                  double* __restrict__ part, int nchunk, int keep, double sgn) {
   const int sidx = blockIdx.y;
   if (active != nullptr && !active[sidx]) return;
   const SubDev& s = subs[sidx];
@@ -495,9 +495,9 @@ k_colnorm_partial(const SubDev* __restrict__ subs, const int* __restrict__ activ
   const double th = s.theta[lane];
   for (int r = r0 + w; r < min(r0 + GRAM_ROWS, s.nfull); r += 8) {
     const int q = (r / 3) % s.npl;
-    if (s.cls[q] != 2) continue;
+    if (!((keep >> s.cls[q]) & 1)) continue;
     const double a = A[(size_t)r * PST + lane], b = B[(size_t)r * PST + lane];
-    const double v = a + th * b;
+    const double v = a + sgn * th * b;
     a0 += v * v;
     a1 += a * a;
     a2 += b * b;
@@ -618,10 +618,11 @@ void launch_chol_inv_small(msgfem* h, int wg, const int* d_ncols, int nfixed, in
   k_chol_inv_small<<<h->N, 256, 0, h->stream>>>(h->d_sub, act(h), wg, d_ncols, nfixed, drop_last); ++g_launch_count;
 }
 
-void launch_colnorms(msgfem* h, int wa, int wb, int p) {
+void launch_colnorms(msgfem* h, int wa, int wb, int p, int keep, double sgn) {
   const int nchunk = (3 * max_nnode(h) + GRAM_ROWS - 1) / GRAM_ROWS;
   dim3 grid(nchunk, h->N);
-  k_colnorm_partial<<<grid, 256, 0, h->stream>>>(h->d_sub, act(h), wa, wb, h->d_gram_part, nchunk); ++g_launch_count;
+  k_colnorm_partial<<<grid, 256, 0, h->stream>>>(h->d_sub, act(h), wa, wb, h->d_gram_part, nchunk, keep, sgn);
+  ++g_launch_count;
   k_colnorm_reduce<<<h->N, 32, 0, h->stream>>>(h->d_sub, act(h), h->d_gram_part, nchunk, p); ++g_launch_count;
 }
 

@@ -277,7 +277,8 @@ __global__ void k_zero_kb(const SubDev* __restrict__ subs, const int* __restrict
   (void)col0_only;
 }
 
-// Start block on B2 rows (counter-based uniform(-1, 1)), zero elsewhere.
+// Start block on the rows of DoF class fill_cls (counter-based uniform(-1, 1)),
+// zero elsewhere: B2 for the A-harmonic problem, B1 for GenEO.
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
   x += 0x9E3779B97F4A7C15ull;
   x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -286,7 +287,7 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
 }
 
 __global__ void k_random_kb(const SubDev* __restrict__ subs, const int* __restrict__ active, int which,
-                            unsigned long long seed) {
+                            unsigned long long seed, int fill_cls) {
   const int sidx = blockIdx.y;
   if (active != nullptr && !active[sidx]) return;
   const SubDev& s = subs[sidx];
@@ -296,7 +297,7 @@ __global__ void k_random_kb(const SubDev* __restrict__ subs, const int* __restri
     const int row = (int)(e / KB), col = (int)(e % KB);
     const int q = (row / 3) % s.npl;
     double v = 0.0;
-    if (s.cls[q] == 2) {
+    if (s.cls[q] == fill_cls) {
       const uint64_t key = mix64(seed ^ mix64(((uint64_t)sidx << 40) ^ ((uint64_t)row << 8) ^ col));
       v = (double)(key >> 11) * (2.0 / 9007199254740992.0) - 1.0;
     }
@@ -463,7 +464,9 @@ k_rr_krylov(const SubDev* __restrict__ subs, const int* __restrict__ active, con
         r2 += v * v;
       }
     s.theta[tid] = th;
-    s.resid[tid] = th * sqrt(r2);
+    // no positive Ritz value (a basis that broke down, e.g. from a non-finite
+    // start block whose columns were all dropped): never converged
+    s.resid[tid] = mu > 0.0 ? th * sqrt(r2) : INFINITY;
   }
 }
 
@@ -584,7 +587,7 @@ void launch_store_block(msgfem* h, int src, int j, int dst) {
 
 void launch_random_kb(msgfem* h, int which, unsigned long long seed) {
   dim3 grid(256, h->N);
-  k_random_kb<<<grid, 256, 0, h->stream>>>(h->d_sub, h->d_flags, which, seed); ++g_launch_count;
+  k_random_kb<<<grid, 256, 0, h->stream>>>(h->d_sub, h->d_flags, which, seed, h->geneo ? 1 : 2); ++g_launch_count;
 }
 
 void launch_mask_kb(msgfem* h, int which, int keep) {

@@ -5,14 +5,11 @@
 // at the point of the call can still evaluate ||u_ref - u||_a / ||u_ref||_a for
 // its own device vectors.  Every GPU that loads the library holds this array
 // until the process exits.
-#include <mutex>
-
 #include "internal.h"
 
 #define NOALLOC_EPT 4                 // elements per thread
 #define NOALLOC_THREADS 256
 #define NOALLOC_MAX_BLOCKS 4096       // -> at most 4,194,304 elements per call
-#define NOALLOC_MAX_DEVICES 64
 
 // [2 b], [2 b + 1]: per-block sums of d^T K_e d and ref^T K_e ref; the last
 // slot holds the result of the most recent call.  64 KiB + 8 bytes.
@@ -20,15 +17,12 @@ static __device__ __align__(256) double g_noalloc_scratch[2 * NOALLOC_MAX_BLOCKS
 
 namespace {
 
-std::mutex g_noalloc_mu;
-double* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
-
 // Each thread sums NOALLOC_EPT consecutive elements; each block writes its own
 // two slots, so no slot has to be cleared between calls.
 __global__ void __launch_bounds__(NOALLOC_THREADS)
 k_energy_blocks(const double* __restrict__ Ke, int layered, const int* __restrict__ etype,
                 const double* __restrict__ ref, const double* __restrict__ u, int NX, int NY, int NZ,
-                double* __restrict__ scratch) {
+                const int* __restrict__ user_of_node, double* __restrict__ scratch) {
   __shared__ double red[2][NOALLOC_THREADS];
   double e0 = 0.0, e1 = 0.0;
   const int nel = NX * NY * NZ;
@@ -37,7 +31,8 @@ k_energy_blocks(const double* __restrict__ Ke, int layered, const int* __restric
     const int ke = el % NZ, ij = el / NZ, je = ij % NY, ie = ij / NY;
     double d[24], r[24];
     for (int a = 0; a < 8; ++a) {
-      const int node = ((ie + (a & 1)) * (NY + 1) + je + ((a >> 1) & 1)) * (NZ + 1) + ke + (a >> 2);
+      int node = ((ie + (a & 1)) * (NY + 1) + je + ((a >> 1) & 1)) * (NZ + 1) + ke + (a >> 2);
+      if (user_of_node) node = user_of_node[node];   // hexahedron list: vectors in the list's node order
       for (int c = 0; c < 3; ++c) {
         r[3 * a + c] = ref[3 * node + c];
         d[3 * a + c] = r[3 * a + c] - u[3 * node + c];
@@ -108,6 +103,18 @@ bool on_device(const void* p) {
 
 }  // namespace
 
+// Device address of the array on the handle's device, looked up once by
+// msgfem_setup with that device current: host code may not pass the symbol
+// itself to a kernel (in host code it names a host-side stand-in).  Taking the
+// address also loads this file's module, so a later call loads nothing.
+msgfem_status noalloc_prepare(msgfem* h) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetSymbolAddress", __FILE__, __LINE__);
+  h->noalloc_scratch = static_cast<double*>(p);
+  return MSGFEM_OK;
+}
+
 extern "C" msgfem_status msgfem_energy_error_noalloc(msgfem_h h, const double* u, const double* u_ref,
                                                      double* energy_err_out) {
   if (!h || !u || !u_ref || !energy_err_out) return MSGFEM_EINVAL;
@@ -127,29 +134,32 @@ extern "C" msgfem_status msgfem_energy_error_noalloc(msgfem_h h, const double* u
     h->err = "msgfem_energy_error_noalloc: u and u_ref must be device pointers";
     return MSGFEM_EINVAL;
   }
-  int dev = 0;
+  // kernels go to the current device: it must be the handle's, whose copy of
+  // the array msgfem_setup resolved
+  int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetDevice", __FILE__, __LINE__);
-  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
-    h->err = "msgfem_energy_error_noalloc: device index out of range";
+  if (dev != h->device || h->noalloc_scratch == nullptr) {
+    h->err = "msgfem_energy_error_noalloc: call with the handle's device (" + std::to_string(h->device) +
+             ") current, not device " + std::to_string(dev);
     return MSGFEM_EINVAL;
   }
-  double* scratch = nullptr;
-  {
-    // first call on this device: resolve the device address of the array
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (g_noalloc_addr[dev] == nullptr) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetSymbolAddress", __FILE__, __LINE__);
-      g_noalloc_addr[dev] = static_cast<double*>(p);
-    }
-    scratch = g_noalloc_addr[dev];
-  }
+  double* scratch = h->noalloc_scratch;
   const bool dev_out = on_device(energy_err_out);
+  if (!dev_out) {
+    // a host result needs a copy and a wait on the stream, which a stream capture cannot hold
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(h->stream, &cs);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamIsCapturing", __FILE__, __LINE__);
+    if (cs != cudaStreamCaptureStatusNone) {
+      h->err = "msgfem_energy_error_noalloc: the stream is being captured; pass a device pointer as energy_err_out";
+      return MSGFEM_ESTATE;
+    }
+  }
   k_energy_blocks<<<(unsigned)nblocks, NOALLOC_THREADS, 0, h->stream>>>(h->d_Ke, h->layered,
                                                                        h->typed ? h->d_etype : nullptr, u_ref, u,
-                                                                       h->NX, h->NY, h->NZ, scratch);
+                                                                       h->NX, h->NY, h->NZ, h->d_user_of_node,
+                                                                       scratch);
   k_energy_final<<<1, 256, 0, h->stream>>>(scratch, (int)nblocks, dev_out ? energy_err_out : nullptr);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "energy kernels", __FILE__, __LINE__);

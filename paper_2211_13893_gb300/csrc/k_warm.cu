@@ -233,6 +233,10 @@ msgfem_status msgfem_warm_targets(msgfem_h h, int j, const float* ref, float* ou
 msgfem_status msgfem_set_start_block(msgfem_h h, int j, const float* X0, int ld, int ncols) {
   if (!h || j < 0 || j >= h->N) return MSGFEM_EINVAL;
   if (X0 != nullptr && (ncols < 1 || ncols > KB || ld < ncols)) return MSGFEM_EINVAL;
+  if (X0 != nullptr && h->geneo) {
+    h->err = "start blocks are B2 blocks of the A-harmonic eigenproblem; a GenEO handle takes none";
+    return MSGFEM_EINVAL;
+  }
   TRY(warm_rows(h));
   if ((int)h->warm.size() != h->N) h->warm.assign(h->N, WarmStart{});
   h->warm[j] = X0 ? WarmStart{X0, ld, ncols} : WarmStart{};

@@ -102,6 +102,25 @@ std::vector<double> end_face_load(const msgfem* h) {
 
 }  // namespace
 
+// The load vector b of Eq. fe_matrix_system on all DoFs (node-major, 3 per
+// node): the given nodal loads, or the consistent nodal load of the traction
+// on the i = NX face; zero on the clamped face i = 0.
+std::vector<double> global_load(const msgfem* h) {
+  const int NX = h->NX, NY = h->NY, NZ = h->NZ;
+  const size_t nn = (size_t)(NX + 1) * (NY + 1) * (NZ + 1);
+  std::vector<double> b(3 * nn, 0.0);
+  if (!h->h_load.empty()) {
+    b = h->h_load;
+  } else {
+    const std::vector<double> face = end_face_load(h);
+    for (int j = 0; j <= NY; ++j)
+      for (int k = 0; k <= NZ; ++k) b[3 * (((size_t)NX * (NY + 1) + j) * (NZ + 1) + k)] = face[(size_t)j * (NZ + 1) + k];
+  }
+  for (size_t n = 0; n < (size_t)(NY + 1) * (NZ + 1); ++n)
+    for (int c = 0; c < 3; ++c) b[3 * n + c] = 0.0;   // i = 0: the first (NY+1)(NZ+1) nodes
+  return b;
+}
+
 void node_xyz(const msgfem* h, int i, int j, int k, double X[3]) {
   if (!h->h_xyz.empty()) {
     const size_t n = ((size_t)i * (h->NY + 1) + j) * (h->NZ + 1) + k;
@@ -786,6 +805,37 @@ void build_coarse_schedules(msgfem* h) {
 extern "C" msgfem_status msgfem_plan(const msgfem_mesh* mesh, const msgfem_partition* part, int overlap,
                                      int oversampling, const msgfem_options* opt, msgfem_plan_info* info) {
   if (!mesh || !part || !info) return MSGFEM_EINVAL;
+  if (mesh->kind == 1 || part->elem_part != nullptr) {
+    // hexahedron list (host coordinates) or element -> part map: the structured problem
+    msgfem_mesh m = *mesh;
+    msgfem_partition pt = *part;
+    HexNumbering hn;
+    std::string err;
+    std::vector<double> xyz;
+    std::vector<int> boxes;
+    if (mesh->kind == 1) {
+      if (mesh->node_xyz == nullptr || !recover_structure(mesh->n_nodes, mesh->n_elems, mesh->hex8, hn, err))
+        return MSGFEM_EINVAL;
+      xyz.assign(3 * (size_t)mesh->n_nodes, 0.0);
+      for (int u = 0; u < mesh->n_nodes; ++u)
+        for (int c = 0; c < 3; ++c) xyz[3 * (size_t)hn.node_of_user[u] + c] = mesh->node_xyz[3 * (size_t)u + c];
+      m.kind = 0;
+      m.nx = hn.nx;
+      m.ny = hn.ny;
+      m.nz = hn.nz;
+      m.xyz = xyz.data();
+    }
+    if (part->elem_part != nullptr) {
+      const size_t nel = (size_t)m.nx * m.ny * m.nz;
+      std::vector<int> ep(nel);
+      for (size_t e = 0; e < nel; ++e) ep[hn.elem_of_user.empty() ? e : hn.elem_of_user[e]] = part->elem_part[e];
+      if (!parts_to_boxes(m.nx, m.ny, m.nz, ep.data(), boxes, err)) return MSGFEM_EINVAL;
+      pt.n_boxes = (int)(boxes.size() / 4);
+      pt.boxes = boxes.data();
+      pt.elem_part = nullptr;
+    }
+    return msgfem_plan(&m, &pt, overlap, oversampling, opt, info);
+  }
   if (mesh->nx <= 0 || mesh->ny <= 0 || mesh->nz <= 0) return MSGFEM_EINVAL;
   if (mesh->xyz == nullptr && (!(mesh->hx > 0) || !(mesh->hy > 0) || !(mesh->hz > 0))) return MSGFEM_EINVAL;
   if (part->n_boxes < 0 || (part->n_boxes > 0 && part->boxes == nullptr)) return MSGFEM_EINVAL;

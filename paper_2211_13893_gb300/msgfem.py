@@ -17,7 +17,8 @@ EXPORTS = ("msgfem_setup", "msgfem_update_angles", "msgfem_local_spaces", "msgfe
            "msgfem_solve", "msgfem_get_basis", "msgfem_get_info", "msgfem_num_subdomains",
            "msgfem_get_profile", "msgfem_reset_profile", "msgfem_energy_error_noalloc", "msgfem_last_error",
            "msgfem_autotune", "msgfem_coarse_assemble_threshold", "msgfem_solution_errors", "msgfem_plan",
-           "msgfem_export_local", "msgfem_import_local",
+           "msgfem_export_local", "msgfem_import_local", "msgfem_probe_fma", "msgfem_schwarz_solve",
+           "msgfem_get_numbering",
            "msgfem_destroy",
            # include/msgfem_warm.h
            "msgfem_net_create", "msgfem_net_param_count", "msgfem_net_get_params", "msgfem_net_set_params",
@@ -33,7 +34,9 @@ class MsgfemError(RuntimeError):
 
 class Mesh(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("hx", C.c_double), ("hy", C.c_double),
-                ("hz", C.c_double), ("traction", C.c_double), ("xyz", C.c_void_p), ("load", C.c_void_p)]
+                ("hz", C.c_double), ("traction", C.c_double), ("xyz", C.c_void_p), ("load", C.c_void_p),
+                ("kind", C.c_int), ("n_nodes", C.c_int), ("n_elems", C.c_int), ("node_xyz", C.c_void_p),
+                ("hex8", C.c_void_p), ("dirichlet_node", C.c_void_p)]
 
 
 class Plies(C.Structure):
@@ -41,7 +44,8 @@ class Plies(C.Structure):
 
 
 class Partition(C.Structure):
-    _fields_ = [("sx", C.c_int), ("sy", C.c_int), ("n_boxes", C.c_int), ("boxes", C.c_void_p)]
+    _fields_ = [("sx", C.c_int), ("sy", C.c_int), ("n_boxes", C.c_int), ("boxes", C.c_void_p),
+                ("elem_part", C.c_void_p)]
 
 
 class Options(C.Structure):
@@ -49,7 +53,8 @@ class Options(C.Structure):
                 ("seed", C.c_ulonglong), ("stream", C.c_void_p), ("profile", C.c_int), ("solver", C.c_int),
                 ("streams", C.c_int), ("refine", C.c_int), ("instances", C.c_int), ("solve_kernel", C.c_int),
                 ("factor_schedule", C.c_int), ("direct_launch", C.c_int), ("wave_mb", C.c_double),
-                ("dev_alloc", C.c_void_p), ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p)]
+                ("dev_alloc", C.c_void_p), ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p), ("method", C.c_int),
+                ("factor_kernel", C.c_int)]
 
 
 class PlanInfo(C.Structure):
@@ -65,7 +70,8 @@ DEV_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
 class Tuning(C.Structure):
     _fields_ = [("factor_schedule", C.c_int), ("factor_streams", C.c_int), ("factor_ms", (C.c_double * 2) * 2),
                 ("streams", C.c_int), ("solve_kernel", C.c_int), ("best_ms", C.c_double),
-                ("solve_ms", (C.c_double * 3) * 4)]
+                ("solve_ms", (C.c_double * 3) * 4), ("factor_kernel", C.c_int),
+                ("factor_ms_tc", (C.c_double * 2) * 2), ("tc_factor_diff", C.c_double)]
 
 
 class Profile(C.Structure):
@@ -73,13 +79,19 @@ class Profile(C.Structure):
                 ("iterate_ms", C.c_double), ("coarse_ms", C.c_double), ("factor_flops", C.c_double),
                 ("solve_flops", C.c_double), ("launches", C.c_longlong), ("solve_calls", C.c_int),
                 ("solve_bytes", C.c_double), ("stencil_ms", C.c_double), ("ortho_ms", C.c_double),
-                ("stencil_flops", C.c_double), ("waves", C.c_int), ("pool_mb", C.c_double)]
+                ("stencil_flops", C.c_double), ("waves", C.c_int), ("pool_mb", C.c_double),
+                ("factor_flops_inverse", C.c_double), ("factor_flops_executed", C.c_double)]
+
+
+class PcgInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("residual", C.c_double), ("lambda_min", C.c_double),
+                ("lambda_max", C.c_double), ("kappa", C.c_double)]
 
 
 class SubInfo(C.Structure):
     _fields_ = [("n_star_dof", C.c_int), ("n1", C.c_int), ("n2", C.c_int), ("n3", C.c_int), ("floating", C.c_int),
                 ("iterations", C.c_int), ("basis_size", C.c_int), ("residual", C.c_double),
-                ("threshold_reached", C.c_int)]
+                ("threshold_reached", C.c_int), ("cold_restart", C.c_int)]
 
 
 _lib = None
@@ -105,6 +117,7 @@ def load_library(path=LIB_PATH):
         "msgfem_get_basis": (C.c_int, [h, C.c_int, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                        C.POINTER(C.c_int)]),
         "msgfem_get_info": (C.c_int, [h, C.c_int, C.POINTER(SubInfo)]),
+        "msgfem_get_numbering": (C.c_int, [h, C.c_void_p, C.c_void_p, C.c_void_p]),
         "msgfem_get_profile": (C.c_int, [h, C.POINTER(Profile)]),
         "msgfem_autotune": (C.c_int, [h, C.c_int, C.POINTER(Tuning)]),
         "msgfem_energy_error_noalloc": (C.c_int, [h, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -114,6 +127,9 @@ def load_library(path=LIB_PATH):
         "msgfem_plan": (C.c_int, [C.POINTER(Mesh), C.POINTER(Partition), C.c_int, C.c_int, C.POINTER(Options),
                                   C.POINTER(PlanInfo)]),
         "msgfem_reset_profile": (C.c_int, [h]),
+        "msgfem_probe_fma": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "msgfem_schwarz_solve": (C.c_int, [h, h, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_void_p,
+                                           C.POINTER(PcgInfo)]),
         "msgfem_num_subdomains": (C.c_int, [h]),
         "msgfem_last_error": (C.c_char_p, [h]),
         "msgfem_destroy": (None, [h]),
@@ -158,10 +174,16 @@ class MSGFEM:
     def __init__(self, nx, ny, nz, hx, hy, hz, traction, E9, elem_angles, sx, sy, overlap, oversampling,
                  block=0, max_iter=0, tol=0.0, seed=0, stream=None, precision=0, profile=0, solver=0, streams=0, refine=0,
                  instances=0, xyz=None, frames=None, boxes=None, wave_mb=0.0, solve_kernel=0,
-                 factor_schedule=0, direct_launch=0, allocator=None, load=None):
+                 factor_schedule=0, direct_launch=0, allocator=None, load=None, method=0, hex8=None,
+                 dirichlet=None, elem_part=None, factor_kernel=0):
         """``allocator``: optional pair (alloc(nbytes) -> device address, free(address,
         nbytes)) through which the handle takes all its device memory.  ``load``:
-        optional nodal forces [n_nodes * 3] replacing the end-face traction."""
+        optional nodal forces [n_nodes * 3] replacing the end-face traction.
+        ``method``: 0 MS-GFEM, 1 the GenEO comparison (oversampling = overlap).
+        ``hex8``: a hexahedron list [n_elems, 8] (standard local order) with
+        ``xyz`` [n_nodes, 3] its node coordinates; nx, ny, nz, hx, hy, hz are then
+        ignored and the structured numbering is recovered by the library.
+        ``dirichlet``: per-node clamp flags; ``elem_part``: per-element part ids."""
         self.lib = load_library()
         self.h = C.c_void_p()
         self._E9 = np.ascontiguousarray(E9, dtype=np.float64)
@@ -173,13 +195,25 @@ class MSGFEM:
         self._frames = None if frames is None else np.ascontiguousarray(frames, dtype=np.float64).reshape(-1)
         self._boxes = None if boxes is None else np.ascontiguousarray(boxes, dtype=np.int32).reshape(-1)
         self._load = None if load is None else np.ascontiguousarray(load, dtype=np.float64).reshape(-1)
-        self.mesh = Mesh(nx, ny, nz, hx, hy, hz, traction, _ptr(self._xyz), _ptr(self._load))
-        self.n_dof = 3 * (nx + 1) * (ny + 1) * (nz + 1)
+        self._dir = None if dirichlet is None else np.ascontiguousarray(dirichlet, dtype=np.uint8).reshape(-1)
+        self._epart = None if elem_part is None else np.ascontiguousarray(elem_part, dtype=np.int32).reshape(-1)
+        if hex8 is not None:
+            self._hex8 = np.ascontiguousarray(hex8, dtype=np.int32).reshape(-1)
+            n_nodes = len(self._xyz) // 3
+            self.mesh = Mesh(0, 0, 0, 0.0, 0.0, 0.0, traction, None, _ptr(self._load), 1, n_nodes,
+                             len(self._hex8) // 8, _ptr(self._xyz), _ptr(self._hex8), _ptr(self._dir))
+            self.n_dof = 3 * n_nodes
+        else:
+            self.mesh = Mesh(nx, ny, nz, hx, hy, hz, traction, _ptr(self._xyz), _ptr(self._load), 0, 0, 0, None,
+                             None, _ptr(self._dir))
+            self.n_dof = 3 * (nx + 1) * (ny + 1) * (nz + 1)
         plies = Plies(self._E9.ctypes.data, _ptr(ang), _ptr(self._frames))
         nb = 0 if self._boxes is None else len(self._boxes) // 4
-        part = Partition(sx, sy, nb, _ptr(self._boxes))
+        part = Partition(sx, sy, nb, _ptr(self._boxes), _ptr(self._epart))
         opt = Options(precision, block, max_iter, tol, seed, stream, profile, solver, streams, refine, instances,
                       solve_kernel, factor_schedule, direct_launch, wave_mb)
+        opt.method = method
+        opt.factor_kernel = factor_kernel
         if allocator is not None:
             alloc, free = allocator
             # the callbacks must outlive the handle: kept on the instance
@@ -314,7 +348,37 @@ class MSGFEM:
         return {"factor_schedule": t.factor_schedule, "factor_streams": t.factor_streams,
                 "factor_ms": [[t.factor_ms[f][g] for g in range(2)] for f in range(2)],
                 "streams": t.streams, "solve_kernel": t.solve_kernel, "best_ms": t.best_ms,
-                "solve_ms": [[t.solve_ms[g][v] for v in range(3)] for g in range(4)]}
+                "solve_ms": [[t.solve_ms[g][v] for v in range(3)] for g in range(4)],
+                "factor_kernel": t.factor_kernel,
+                "factor_ms_tc": [[t.factor_ms_tc[f][g] for g in range(2)] for f in range(2)],
+                "tc_factor_diff": t.tc_factor_diff}
+
+    def schwarz_solve(self, coarse=None, b=None, u0=None, rtol=0.0, max_iter=0, u_out=None, allow_noconv=False):
+        """Two-level additive Schwarz PCG for the fine problem (include/msgfem.h
+        msgfem_schwarz_solve) with this handle's A11 factors as the local solves
+        (oversampling = overlap) and ``coarse``'s coarse space (an MSGFEM after
+        coarse_assemble, or None for one level).  Returns (u, info dict)."""
+        u = u_out if u_out is not None else np.zeros(self.n_dof)
+        if b is not None and not hasattr(b, "data_ptr"):
+            b = np.ascontiguousarray(b, dtype=np.float64)
+        if u0 is not None and not hasattr(u0, "data_ptr"):
+            u0 = np.ascontiguousarray(u0, dtype=np.float64)
+        inf = PcgInfo()
+        self._check(self.lib.msgfem_schwarz_solve(self.h, coarse.h if coarse is not None else None, _ptr(b), _ptr(u0),
+                                                  float(rtol), int(max_iter), _ptr(u), C.byref(inf)),
+                    allow=(5,) if allow_noconv else ())
+        return u, {k: getattr(inf, k) for k, _ in PcgInfo._fields_}
+
+    def numbering(self):
+        """(dims (nx, ny, nz), node_of_user, elem_of_user) of the structured numbering
+        (include/msgfem.h msgfem_get_numbering)."""
+        dims = (C.c_int * 3)()
+        self._check(self.lib.msgfem_get_numbering(self.h, dims, None, None))
+        nx, ny, nz = dims[0], dims[1], dims[2]
+        nodes = np.zeros((nx + 1) * (ny + 1) * (nz + 1), dtype=np.int32)
+        elems = np.zeros(nx * ny * nz, dtype=np.int32)
+        self._check(self.lib.msgfem_get_numbering(self.h, None, nodes.ctypes.data, elems.ctypes.data))
+        return (nx, ny, nz), nodes, elems
 
     def info(self, j):
         inf = SubInfo()
@@ -416,6 +480,17 @@ class Net:
             self.close()
         except Exception:
             pass
+
+
+def probe_fma(precision=0):
+    """FMA throughput of the current device in TFLOP/s (include/msgfem.h
+    msgfem_probe_fma): precision 0 = FP64, 1 = FP32."""
+    lib = load_library()
+    tf, sms = C.c_double(), C.c_double()
+    st = lib.msgfem_probe_fma(precision, C.byref(tf), C.byref(sms))
+    if st != 0:
+        raise MsgfemError(st, "msgfem_probe_fma")
+    return tf.value, int(sms.value)
 
 
 def plan(cfg, precision=0, wave_mb=0.0, instances=0):
