@@ -6,6 +6,7 @@ the 32 subdomains, the Gram-Schmidt'd PoU basis with the particular functions
 appended (Sec. 4.4, variant ii), the coarse Galerkin solve (Eq.
 GFEM_coarse_approximation), the fine solution u_h (Eq. fe_matrix_system) by a
 banded Cholesky, and the relative energy error of u^G (Thm. error_bound).
+The coarse solution u^G itself goes to c2_oracle_uG.npy.
 
     python tests/golden/make_c2_golden.py [--workers 8]
 
@@ -24,10 +25,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 sys.path.insert(0, ROOT)
 
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "c2_oracle.json")
+# the oracle's coarse solution u^G on all 301,080 DoFs (float64, .npy)
+OUT_UG = os.path.join(os.path.dirname(os.path.abspath(__file__)), "c2_oracle_uG.npy")
 
 
 def _local(j):
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
     from oracle.assemble import ElementCache
     from oracle.coarse import gram_schmidt
     from oracle.local import local_eigs_dense, local_problem, particular
@@ -64,9 +66,16 @@ def main():
     from workloads import element_angles, get_config
     cfg = get_config("c2")
     t0 = time.time()
+    # one BLAS thread per worker process (set before the workers start and import numpy)
+    blas = os.environ.get("OMP_NUM_THREADS")
+    os.environ["OMP_NUM_THREADS"] = "1"
     with mp.get_context("spawn").Pool(args.workers) as pool:
         res = sorted(pool.map(_local, range(cfg.n_sub)), key=lambda r: r[0])
     t_local = time.time() - t0
+    if blas is None:
+        os.environ.pop("OMP_NUM_THREADS")
+    else:
+        os.environ["OMP_NUM_THREADS"] = blas
     mesh = BeamMesh.from_config(cfg)
     ang = element_angles(cfg)
     A = assemble_global(mesh, ang, cfg.material, cache=ElementCache(mesh, cfg.material))
@@ -98,6 +107,7 @@ def main():
     }
     with open(OUT, "w") as f:
         json.dump(out, f, indent=1)
+    np.save(OUT_UG, np.asarray(uG, dtype=np.float64))
     print(f"wrote {OUT}: energy error {err:.6e}, {t_local:.0f} s local, {time.time() - t0:.0f} s total")
 
 

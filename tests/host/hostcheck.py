@@ -17,7 +17,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 CSRC = os.path.join(ROOT, "paper_2211_13893_gb300", "csrc")
-SOURCES = [os.path.join(HERE, "host_shim.cpp"), os.path.join(CSRC, "setup.cpp")]
+SOURCES = [os.path.join(HERE, "host_shim.cpp"), os.path.join(CSRC, "setup.cpp"), os.path.join(CSRC, "hexmesh.cpp")]
 HEADERS = [os.path.join(CSRC, "internal.h"), os.path.join(ROOT, "include", "msgfem.h")]
 LIB = os.path.join(HERE, "_build", "libhostcheck.so")
 

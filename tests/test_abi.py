@@ -71,3 +71,34 @@ def test_setup_rejects_bad_descriptors(lib_path):
     p = msgfem.Partition(1, 1)
     assert lib.msgfem_setup(C.byref(m), C.byref(plies), C.byref(p), 1, 1, C.byref(opt), C.byref(h)) == 1
     assert not h.value
+
+
+def test_setup_rejects_non_finite_inputs(lib_path):
+    """A NaN traction, brick size, material constant or nodal load is refused
+    (EINVAL) before any device memory is touched."""
+    import ctypes as C
+    import numpy as np
+    from paper_2211_13893_gb300 import msgfem
+    lib = msgfem.load_library(lib_path)
+    ang = np.zeros(8)
+    h = C.c_void_p()
+    opt = msgfem.Options()
+    p = msgfem.Partition(1, 1)
+    E = np.ones(9)
+    plies = msgfem.Plies(E.ctypes.data, ang.ctypes.data)
+    for tr, hx in [(np.nan, 1.0), (1.0, np.inf)]:
+        m = msgfem.Mesh(2, 2, 2, hx, 1.0, 1.0, tr)
+        assert lib.msgfem_setup(C.byref(m), C.byref(plies), C.byref(p), 1, 1, C.byref(opt), C.byref(h)) == 1
+        assert not h.value
+    Ebad = np.ones(9)
+    Ebad[4] = np.nan
+    m = msgfem.Mesh(2, 2, 2, 1.0, 1.0, 1.0, 1.0)
+    bad = msgfem.Plies(Ebad.ctypes.data, ang.ctypes.data)
+    assert lib.msgfem_setup(C.byref(m), C.byref(bad), C.byref(p), 1, 1, C.byref(opt), C.byref(h)) == 1
+    assert not h.value
+    load = np.zeros(27 * 3)
+    load[40] = np.nan
+    m = msgfem.Mesh(2, 2, 2, 1.0, 1.0, 1.0, 1.0, None, load.ctypes.data)
+    st = lib.msgfem_setup(C.byref(m), C.byref(plies), C.byref(p), 1, 1, C.byref(opt), C.byref(h))
+    assert st == 1 and b"non-finite" in lib.msgfem_last_error(h)
+    lib.msgfem_destroy(h)

@@ -6,6 +6,8 @@ coarse problem is refused for a batched handle."""
 import numpy as np
 import pytest
 
+from parity_util import assert_eigs
+
 torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
@@ -32,10 +34,7 @@ def test_batched_instances_match_oracle(precision, tol):
     for i in range(S):
         ref = run_msgfem(cfg, angles=ang[i], solver="dense")
         for j in range(cfg.n_sub):
-            lo = np.asarray(ref.lam[j])[:cfg.n_loc]
-            scale = max(abs(lo[-1]), 1e-2)
-            got = lam[i * cfg.n_sub + j]
-            assert np.abs(got - lo).max() <= tol * scale, (i, j, got, lo)
+            assert_eigs(lam[i * cfg.n_sub + j], np.asarray(ref.lam[j])[:cfg.n_loc], tol, (i, j))
     with pytest.raises(MsgfemError):
         m.coarse_assemble()
     m.close()

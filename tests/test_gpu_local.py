@@ -1,14 +1,20 @@
 """GPU parity of the local stage and the coarse solve against the FP64 oracle.
 
-Eigenvalues must match to 1e-8 relative to the largest wanted eigenvalue of
-the subdomain (rigid-body zeros absolutely at that scale), eigenvector spans
-must agree (principal angles, compared at spectral gaps), and the global
+Every eigenvalue must match the oracle's to 1e-8 relative to itself (mixed
+precision: 1e-5; the rigid-body zeros of floating subdomains absolutely at
+that fraction of the largest eigenvalue), eigenvector spans must agree
+(principal angles, compared at spectral gaps), each particular function psi_j
+(Eq. up_r) must equal the oracle's in the energy norm of Omega*_j (1e-10,
+mixed 1e-8: the A11 solve's rounding, kappa(A11) ~ 2e4), the coarse solution
+u^G the oracle's in the global energy norm (1e-8, mixed 1e-5), and the global
 energy error must be within 1 % of the oracle's at equal n_loc.
 """
 import numpy as np
 import pytest
 
 from oracle.coarse import run_msgfem
+from oracle.local import particular
+from parity_util import assert_eigs, energy_rel
 from workloads import element_angles, get_config
 
 pytestmark = pytest.mark.gpu
@@ -41,15 +47,21 @@ def run_case(name, seed=7, tol_lam=1e-8, tol_angle=1e-5, solver=0, precision=0, 
     cfg = get_config(name)
     ang = element_angles(cfg)
     ref = run_msgfem(cfg, angles=ang, n_loc=cfg.n_loc + 1)        # one more to locate the gap at n_loc
-    ref_n = run_msgfem(cfg, angles=ang, uh=None)
+    ref_n = run_msgfem(cfg, angles=ang, uh=None, keep_problems=True)
     m = _msgfem().from_config(cfg, ang, seed=seed, solver=solver, precision=precision, **kw)
     lam = m.local_spaces(cfg.n_loc)
     nc = m.coarse_assemble()
-    _, err = m.solve(u_ref=ref_n.uh)
+    uG, err = m.solve(u_ref=ref_n.uh)
+    tol_psi = 1e-10 if precision == 0 else 1e-8
     for j in range(m.N):
         lo = ref.lam[j]
-        scale = max(abs(lo[cfg.n_loc - 1]), 1e-2)   # all-rigid subdomains: absolute at 1e-2
-        assert np.abs(lam[j] - lo[:cfg.n_loc]).max() <= tol_lam * scale, (name, j, lam[j], lo)
+        assert_eigs(lam[j], lo, tol_lam, (name, j))
+        phi_psi, _ = m.export_local(j)
+        psi_or = particular(ref_n.problems[j])
+        if np.any(psi_or != 0.0):
+            assert energy_rel(ref_n.problems[j].A, phi_psi[:, -1], psi_or) <= tol_psi, (name, j)
+        else:
+            assert np.all(phi_psi[:, -1] == 0.0), (name, j)
         phi, box = m.basis(j)
         for mm in gap_sizes(lo, cfg.n_loc):
             s = max_sin_angle(ref.phi[j][:, :mm], phi[:, :mm])
@@ -59,12 +71,13 @@ def run_case(name, seed=7, tol_lam=1e-8, tol_angle=1e-5, solver=0, precision=0, 
             assert info["iterations"] > 0
         assert info["residual"] < 1e-5, (name, j, info)
     assert nc == sum(ref_n.basis_counts)
+    assert energy_rel(ref_n.A, uG, ref_n.uG) <= (1e-8 if precision == 0 else 1e-5), (name, energy_rel(ref_n.A, uG, ref_n.uG))
     assert abs(err - ref_n.energy_error) <= 0.01 * ref_n.energy_error, (err, ref_n.energy_error)
     m.close()
     return lam, err, ref_n
 
 
-@pytest.mark.parametrize("name", ["t1", "t2", "t3", "c1"])
+@pytest.mark.parametrize("name", ["t1", "t2", "t3", "t4", "c1"])
 def test_local_stage_parity(name):
     """Block Krylov eigensolver (the default)."""
     run_case(name)
@@ -81,11 +94,6 @@ def test_local_stage_parity_mixed(name):
 def test_local_stage_parity_subspace(name):
     """Subspace iteration with Rayleigh-Ritz every step (solver = 1)."""
     run_case(name, solver=1)
-
-
-def test_t4_multi_tile_layers():
-    """t4: layer blocks span several 64-tiles with ragged padding, 8 subdomains."""
-    run_case("t4")
 
 
 def test_deterministic_across_runs():

@@ -11,6 +11,8 @@
 import numpy as np
 import pytest
 
+from parity_util import assert_eigs
+
 torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
@@ -126,8 +128,8 @@ def test_warm_start_on_wrinkled_beam():
         ws.apply(blocks)
         lam_warm = m.local_spaces(n_loc).copy()
         it_w.append(sum(m.info(j)["iterations"] for j in range(m.N)))
-        scale = np.abs(lam_cold).max(axis=1, keepdims=True)
-        assert np.max(np.abs(lam_warm - lam_cold) / scale) < 1e-8
+        for j in range(m.N):
+            assert_eigs(lam_warm[j], lam_cold[j], 1e-8, j)
         rng = np.random.default_rng(s)
         for j, (n2, nw) in enumerate(ws.sizes):
             ang_w.append(mlp.max_angle(blocks[j].cpu().numpy()[:, :nw], conv[j][:, :nw]))
@@ -153,7 +155,5 @@ def test_warm_started_eigenvalues_match_oracle():
     ws.apply(None)
     ref = run_msgfem(cfg, angles=ang.cpu().numpy().reshape(cfg.NX, cfg.NY, cfg.NZ), solver="dense")
     for j in range(m.N):
-        lo = np.asarray(ref.lam[j])[:cfg.n_loc]
-        scale = max(abs(lo[-1]), 1e-2)
-        assert np.abs(lam[j] - lo).max() <= 1e-8 * scale, (j, lam[j], lo)
+        assert_eigs(lam[j], np.asarray(ref.lam[j])[:cfg.n_loc], 1e-8, j)
     m.close()
