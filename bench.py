@@ -27,6 +27,8 @@ default); it also carries
   warm_c5      the learned warm start on the wrinkled c1 beam (512 samples,
                384 for training), 128 beams batched per local stage: cold
                start vs nominal-basis reuse vs trained network;
+  aspect       the element aspect-ratio study (in-plane edge 1, 4, 8, 15 ply
+               thicknesses): 1/lambda decay, mixed vs FP64, iterations;
   cpu_baseline the oracle on a sample of the workload's subdomains, one per
                host core.
 Under torchrun (N > 1) every rank runs an independent replica of the workload
@@ -393,6 +395,9 @@ def run_ours(args):
     warm = None
     if not args.no_warm and rank == 0:
         warm = run_warm_c5(args, dev)
+    aspect = None
+    if not args.no_aspect and rank == 0:
+        aspect = run_aspect(args, dev, stream)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
@@ -410,7 +415,7 @@ def run_ours(args):
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "solver": extra, "autotune": tuning_fp64, "mixed": mixed, "c4": c4,
-                "warm_c5": warm}
+                "warm_c5": warm, "aspect": aspect}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -429,7 +434,7 @@ def run_c4(args, dev, stream, flush, rank, world):
     t0 = time.perf_counter()
     ang = torch.tensor(element_angles(cfg).reshape(-1), dtype=torch.float64, device=dev)
     m = MSGFEM.from_config(cfg, ang, seed=11, stream=stream.cuda_stream, profile=1, precision=1,
-                           streams=args.streams)
+                           streams=args.streams, factor_kernel=max(args.factor_kernel, 0))
     setup_s = time.perf_counter() - t0
     lam = torch.empty((m.N, cfg.n_loc), dtype=torch.float64, device=dev)
     u = torch.empty(m.n_dof, dtype=torch.float64, device=dev)
@@ -507,7 +512,8 @@ def run_mixed(args, cfg, ang_dev, stream, dev, rank, lam_fp64, u_fp64, flush, wo
     import torch
     from paper_2211_13893_gb300 import MSGFEM
     m = MSGFEM.from_config(cfg, ang_dev, seed=1234 + rank, stream=stream.cuda_stream, profile=1,
-                           streams=args.streams, precision=1, direct_launch=int(args.direct_launch))
+                           streams=args.streams, precision=1, direct_launch=int(args.direct_launch),
+                           factor_kernel=max(args.factor_kernel, 0))
     lam = torch.empty_like(lam_fp64)
     u = torch.empty_like(u_fp64)
 
@@ -561,6 +567,50 @@ def run_mixed(args, cfg, ang_dev, stream, dev, rank, lam_fp64, u_fp64, flush, wo
                         "time_share": prof["solve_ms"] / total if total else None,
                         "calls_per_step": prof["solve_calls"]}}
     m.close()
+    return out
+
+
+def run_aspect(args, dev, stream):
+    """The element aspect-ratio study (Sec. 5.3) on the GPU: the c1 topology with
+    in-plane element edges of 1, 4, 8 and 15 ply thicknesses, oversampling 4,
+    n_loc = 12, FP64 and mixed: 1/lambda of the wanted pairs of subdomain 0 (the
+    decay that drives the error bound), the largest relative eigenvalue
+    difference of the mixed run to the FP64 one, block iterations, residuals
+    and the local-stage time.  Oracle parity at every aspect ratio is in
+    tests/test_gpu_aspect.py."""
+    import numpy as np
+    import torch
+    from paper_2211_13893_gb300 import MSGFEM
+    from workloads import element_angles, get_config
+    from workloads.configs import ASPECT_RATIOS
+    out = {}
+    for ar in ASPECT_RATIOS:
+        cfg = get_config(f"a{ar}")
+        ang = element_angles(cfg)
+        rec = {}
+        lam = {}
+        for prec in (0, 1):
+            m = MSGFEM.from_config(cfg, ang, seed=5, precision=prec, stream=stream.cuda_stream)
+            m.local_spaces(cfg.n_loc)                       # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lam[prec] = m.local_spaces(cfg.n_loc)
+            torch.cuda.synchronize()
+            ms = 1000.0 * (time.perf_counter() - t0)
+            infos = [m.info(j) for j in range(m.N)]
+            rec["fp64" if prec == 0 else "mixed"] = {
+                "local_stage_ms": ms, "iterations_max": max(i["iterations"] for i in infos),
+                "residual_max": max(i["residual"] for i in infos)}
+            m.close()
+        l0 = lam[0][0]
+        rec["inv_lambda_sub0"] = [float(1.0 / x) if x > 0 else None for x in l0]
+        # non-rigid eigenvalues relative to themselves, rigid zeros at the scale 1
+        scale = np.where(np.abs(lam[0]) > 1e-8 * np.maximum(np.abs(lam[0]).max(axis=1, keepdims=True), 1.0),
+                         np.abs(lam[0]), 1.0)
+        rec["mixed_eig_rel_diff_vs_fp64"] = float((np.abs(lam[1] - lam[0]) / scale).max())
+        out[f"aspect_{ar}"] = rec
+    out["workload"] = ("c1 topology 24x4x12, ply 0.25 mm, in-plane element edge = aspect ratio x ply thickness, "
+                       "2x1 subdomains, overlap 1, oversampling 4, n_loc 12")
     return out
 
 
@@ -705,12 +755,16 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison run")
     ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start (c5) run")
     ap.add_argument("--no-c4", action="store_true", help="skip the batched C-section (c4) run")
+    ap.add_argument("--no-aspect", action="store_true", help="skip the element aspect-ratio sweep")
     ap.add_argument("--c4-steps", type=int, default=1, help="timed steps of the c4 run")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default factor schedule and solve launches")
     ap.add_argument("--direct-launch", action="store_true",
                     help="launch the factorisation and solve kernels one by one instead of replaying graphs "
                          "(the same work; for kernel profilers)")
     ap.add_argument("--streams", type=int, default=0, help="stream groups of the library (0 = its default)")
+    ap.add_argument("--factor-kernel", type=int, default=-1, choices=(-1, 0, 1),
+                    help="FP32 factorisation tile kernel of the mixed legs: 0 FMA, 1 tensor cores; "
+                         "-1 = start from 0 and let the autotuner choose")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -163,9 +163,9 @@ typedef struct {
   int precision;        /* msgfem_precision */
   int block;            /* subspace iteration block size p; 0 = n_loc + max(8, n_loc / 2) */
   int max_iter;         /* cap on the eigensolver's steps: subspace iterations, or block Krylov
-                           block steps (restarts included; the block Krylov solver also stops
-                           after 8 thick restarts of its 96-column basis); 0 = 100.  A capped
-                           run returns ENOCONV with the last Rayleigh-Ritz pairs */
+                           block steps (thick restarts of the 96-column basis included: 12 steps
+                           fill it, each restart adds 8); 0 = 100.  A capped run returns ENOCONV
+                           with the last Rayleigh-Ritz pairs */
   double tol;           /* stop when ||theta E S^-1 T x - x||_T <= tol per wanted pair (or the
                            decrease stalls below 1e2 tol); 0 = 1e-7 */
   unsigned long long seed;  /* seed of the counter-based start-block generator */
@@ -368,7 +368,8 @@ msgfem_status msgfem_solve(msgfem_h h, double* u_out, const double* u_ref, doubl
  * algebraicAharmonic).  Node (i, j, k) of the Omega*_j node box
  * [i0, i1] x [j0, j1] x [0, nz] has local id ((i - i0)(j1 - j0 + 1) + (j - j0))(nz + 1) + k
  * and local DoFs 3 id + c; DoFs in B3 are zero.  *rows and *cols receive the
- * shape; phi_out may be NULL to query it.  box_out (may be NULL) receives the
+ * shape; phi_out may be NULL to query it (also before msgfem_local_spaces;
+ * *cols is then the n_loc of the last local stage, 0 before the first).  box_out (may be NULL) receives the
  * Omega*_j node box {i0, i1, j0, j1}. */
 msgfem_status msgfem_get_basis(msgfem_h h, int j, double* phi_out, int* rows, int* cols, int* box_out);
 

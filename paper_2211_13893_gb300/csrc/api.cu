@@ -804,8 +804,22 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
   launch_random_kb(h, MV_WB, h->opt.seed);
   std::vector<int> warm(h->N, 0);
   if ((int)h->warm.size() == h->N && warm_upload(h)) {
-    launch_load_start(h, MV_WB);
-    for (int j = 0; j < h->N; ++j) warm[j] = h->warm[j].X0 != nullptr;
+    // a start block with a non-finite entry is not used: that subdomain starts cold
+    std::vector<int> bad;
+    TRY(warm_check(h, bad));
+    const std::vector<WarmStart> kept = h->warm;
+    bool any_bad = false;
+    for (int j = 0; j < h->N; ++j)
+      if (bad[j] && act[j]) {
+        h->warm[j] = WarmStart{};
+        h->cold_restart[j] = 1;
+        any_bad = true;
+      }
+    if (!any_bad || warm_upload(h)) {
+      launch_load_start(h, MV_WB);
+      for (int j = 0; j < h->N; ++j) warm[j] = h->warm[j].X0 != nullptr;
+    }
+    h->warm = kept;
   }
   if (!h->geneo) extend_kb(h);   // A-harmonic start: extension of the B2 block (GenEO: a block on B1)
   project_rigid_kb(h, MV_WB);
@@ -820,7 +834,6 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
   for (int j = 0; j < h->N; ++j) all_done = all_done && !act[j];
   const int jmax = MQ / KB;
   const int kkeep = std::min(PST, MQ - 2 * KB);   // Ritz vectors kept at a thick restart
-  int restarts = 0;
   std::vector<int> kvec(h->N, kkeep);
   // msgfem_options.max_iter caps the block steps (restarts included); once the
   // cap is reached every active subdomain whose basis holds its wanted pairs
@@ -884,10 +897,9 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
     }
     TRY(set_active(h, act));
     if (stop) break;
-    if (full && !all_done && restarts < 8) {
+    if (full && !all_done) {
       // thick restart of the unconverged subdomains: keep kkeep Ritz vectors and
       // the residual block, continue from block kkeep / KB
-      ++restarts;
       launch_ritz(h, h->d_mk, h->d_ncols, 0, true, MV_QB, MV_PHI);
       launch_ritz(h, h->d_mk, h->d_ncols, 0, true, MV_NQ, MV_CW);
       launch_restart(h, m, kkeep);
@@ -1246,14 +1258,6 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   }
   h->stage = 2;
   spans_collect(h);
-  for (int j = 0; j < h->N; ++j)
-    for (int c = 0; c < n_loc; ++c)
-      if (!std::isfinite(lam[(size_t)j * n_loc + c]) || std::fabs(lam[(size_t)j * n_loc + c]) >= 1e299 ||
-          !std::isfinite(h->resid_max[j])) {
-        h->err = "non-finite eigenvalue or residual in subdomain " + std::to_string(j);
-        h->stage = 1;
-        return MSGFEM_ENOCONV;
-      }
   for (int j = 0; j <= h->N; ++j)
     if (notspd[j] & 2) {
       h->err = "a tensor-core tile task of subdomain " + std::to_string(j) + " did not complete within its time limit";
@@ -1264,6 +1268,14 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
       h->err = "non-positive pivot in a layer-block factorisation of subdomain " + std::to_string(j);
       return MSGFEM_ENOTSPD;
     }
+  for (int j = 0; j < h->N; ++j)
+    for (int c = 0; c < n_loc; ++c)
+      if (!std::isfinite(lam[(size_t)j * n_loc + c]) || std::fabs(lam[(size_t)j * n_loc + c]) >= 1e299 ||
+          !std::isfinite(h->resid_max[j])) {
+        h->err = "non-finite eigenvalue or residual in subdomain " + std::to_string(j);
+        h->stage = 1;
+        return MSGFEM_ENOCONV;
+      }
   if (!all_done) {
     h->err = "eigensolver reached max_iter";
     return MSGFEM_ENOCONV;
@@ -1425,7 +1437,7 @@ msgfem_status msgfem_solve(msgfem_h h, double* u_out, const double* u_ref, doubl
 
 msgfem_status msgfem_get_basis(msgfem_h h, int j, double* phi_out, int* rows, int* cols, int* box_out) {
   if (!h || j < 0 || j >= h->N) return MSGFEM_EINVAL;
-  if (h->stage < 2) return MSGFEM_ESTATE;
+  if (h->stage < (phi_out ? 2 : 1)) return MSGFEM_ESTATE;   // the shape and box are known from set-up
   const SubDev& s = h->sub[j];
   if (rows) *rows = s.nfull;
   if (cols) *cols = h->n_loc;

@@ -417,6 +417,7 @@ msgfem_status noalloc_prepare(msgfem* h);
 // learned warm start (k_warm.cu)
 msgfem_status warm_rows(msgfem* h);
 bool warm_upload(msgfem* h);
+msgfem_status warm_check(msgfem* h, std::vector<int>& bad);
 void launch_load_start(msgfem* h, int which);
 
 // error helpers shared by the translation units that return msgfem_status

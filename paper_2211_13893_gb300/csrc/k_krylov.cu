@@ -454,8 +454,11 @@ k_rr_krylov(const SubDev* __restrict__ subs, const int* __restrict__ active, con
     s.Yk[e] = (a < m && i < nw) ? V[a][perm[i]] : 0.0;
   }
   if (tid < nw) {
+    // Ritz values of M in the N = S + sigma T inner product lie in [0, 1 / sigma];
+    // a wanted one below 1e-14 (lambda above 1e14) comes from a basis that broke down
     const double mu = A[perm[tid]][perm[tid]];
-    const double th = mu > 0.0 ? 1.0 / mu : 1e300;
+    const bool valid = mu > 1e-14;
+    const double th = valid ? 1.0 / mu : 1e300;
     double r2 = 0.0;
     if (m + KB <= MQ + KB)
       for (int r = 0; r < KB; ++r) {
@@ -466,7 +469,7 @@ k_rr_krylov(const SubDev* __restrict__ subs, const int* __restrict__ active, con
     s.theta[tid] = th;
     // no positive Ritz value (a basis that broke down, e.g. from a non-finite
     // start block whose columns were all dropped): never converged
-    s.resid[tid] = mu > 0.0 ? th * sqrt(r2) : INFINITY;
+    s.resid[tid] = valid ? th * sqrt(r2) : INFINITY;
   }
 }
 

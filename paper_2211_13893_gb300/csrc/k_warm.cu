@@ -142,7 +142,33 @@ __global__ void k_load_start(const SubDev* __restrict__ subs, const int* __restr
   }
 }
 
+// bad[j] = 1 when the registered start block of subdomain j holds a non-finite
+// value (its first ncols columns)
+__global__ void k_check_start(const WarmDev* __restrict__ warm, int* __restrict__ bad) {
+  const WarmDev wd = warm[blockIdx.x];
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  if (wd.X0 != nullptr)
+    for (int e = threadIdx.x; e < wd.n2 * wd.ncols; e += blockDim.x)
+      if (!isfinite(wd.X0[(size_t)(e / wd.ncols) * wd.ld + e % wd.ncols])) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) bad[blockIdx.x] = any;
+}
+
 }  // namespace
+
+// Registered start blocks with a non-finite entry (a network that produced
+// NaN): bad[j] = 1 for those subdomains.  Uses d_ncols as scratch.
+msgfem_status warm_check(msgfem* h, std::vector<int>& bad) {
+  bad.assign(h->N, 0);
+  k_check_start<<<h->N, 256, 0, h->stream>>>(static_cast<const WarmDev*>(h->d_warm), h->d_ncols);
+  ++g_launch_count;
+  CK_LAUNCH();
+  CK(cudaMemcpyAsync(bad.data(), h->d_ncols, h->N * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return MSGFEM_OK;
+}
 
 // B2 row lists (ascending full-layout rows of the interface DoFs), built once
 msgfem_status warm_rows(msgfem* h) {

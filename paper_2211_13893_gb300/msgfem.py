@@ -302,9 +302,16 @@ class MSGFEM:
 
     def import_local(self, lam, phis):
         """Resume from exported local spaces (msgfem_import_local): lam [N, n_loc],
-        phis[j] as returned by export_local."""
+        phis[j] as returned by export_local ([n_star_dof_j, n_loc + 1]); the
+        shapes are checked against this handle before the library reads them."""
         lam = np.ascontiguousarray(lam, dtype=np.float64)
+        if lam.ndim != 2 or lam.shape[0] != self.N or len(phis) != self.N:
+            raise ValueError(f"lam must be [{self.N}, n_loc] with one phi per subdomain")
         n_loc = lam.shape[1]
+        for j, p in enumerate(phis):
+            if np.shape(p) != (self.basis_rows(j), n_loc + 1):
+                raise ValueError(f"phi of subdomain {j} has shape {np.shape(p)}, expected "
+                                 f"({self.basis_rows(j)}, {n_loc + 1})")
         cols = [np.ascontiguousarray(np.asarray(p, dtype=np.float64).T) for p in phis]
         ptrs = (C.c_void_p * len(cols))(*[c.ctypes.data for c in cols])
         self._check(self.lib.msgfem_import_local(self.h, n_loc, lam.ctypes.data, ptrs))
@@ -319,7 +326,8 @@ class MSGFEM:
         np.savez(path, lam=lam, **{f"phi_{j}": o[0] for j, o in enumerate(out)})
         with open(str(path) + ".json", "w") as f:
             json.dump({"n_subdomains": self.N, "n_loc": int(self.n_loc), "n_dof": int(self.n_dof),
-                       "n_star_dof": [int(o[0].shape[0]) for o in out]}, f)
+                       "n_star_dof": [int(o[0].shape[0]) for o in out],
+                       "boxes": [list(self.basis_box(j)) for j in range(self.N)]}, f)
 
     def load_local(self, path):
         """Resume from a file written by save_local (the handle must be set up like
@@ -329,9 +337,27 @@ class MSGFEM:
             man = json.load(f)
         if man["n_subdomains"] != self.N or man["n_dof"] != self.n_dof:
             raise ValueError("the checkpoint was written for another problem")
+        # the oversampling domains (their DoF counts and node boxes) must be the
+        # ones of this handle: another overlap, oversampling or partition with the
+        # same mesh would otherwise pass and be read with the wrong sizes
+        rows = [self.basis_rows(j) for j in range(self.N)]
+        if man.get("n_star_dof") != rows or man.get("boxes") != [list(self.basis_box(j)) for j in range(self.N)]:
+            raise ValueError("the checkpoint's oversampling domains differ from this handle's")
         name = str(path) if str(path).endswith(".npz") else str(path) + ".npz"
         data = np.load(name)
         self.import_local(data["lam"], [data[f"phi_{j}"] for j in range(self.N)])
+
+    def basis_rows(self, j):
+        """DoFs of Omega*_j (rows of the layouts of basis / export_local)."""
+        rows = C.c_int()
+        self._check(self.lib.msgfem_get_basis(self.h, j, None, C.byref(rows), None, None))
+        return rows.value
+
+    def basis_box(self, j):
+        """Node box (i0, i1, j0, j1) of Omega*_j."""
+        box = (C.c_int * 4)()
+        self._check(self.lib.msgfem_get_basis(self.h, j, None, None, None, box))
+        return tuple(box)
 
     def basis(self, j):
         rows, cols, box = C.c_int(), C.c_int(), (C.c_int * 4)()

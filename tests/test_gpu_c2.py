@@ -41,13 +41,14 @@ def oracle_c2():
     return cfg, json.load(open(GOLD)), np.load(GOLD_UG), A, mesh.compression_load(cfg.traction)
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 1e-5)])
-def test_c2_full_size(oracle_c2, precision, tol):
+@pytest.mark.parametrize("precision,tol,factor_kernel", [(0, 1e-8, 0), (1, 1e-5, 0), (1, 1e-5, 1)])
+def test_c2_full_size(oracle_c2, precision, tol, factor_kernel):
+    """FP64, mixed with the FMA factor kernel, mixed with the tensor-core one."""
     from paper_2211_13893_gb300 import MSGFEM
     from workloads import element_angles
     cfg, gold, uG_or, A, b = oracle_c2
     ang = torch.tensor(element_angles(cfg).reshape(-1), dtype=torch.float64, device="cuda")
-    m = MSGFEM.from_config(cfg, ang, seed=1234, precision=precision)
+    m = MSGFEM.from_config(cfg, ang, seed=1234, precision=precision, factor_kernel=factor_kernel)
     lam = m.local_spaces(cfg.n_loc)
     nc = m.coarse_assemble()
     uG, _ = m.solve()

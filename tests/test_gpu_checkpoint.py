@@ -39,3 +39,27 @@ def test_resume_from_exported_local_spaces(name, tmp_path):
     assert np.array_equal(ub2, ut)
     assert all(b.info(j)["iterations"] == 0 for j in range(b.N))
     b.close()
+
+
+def test_checkpoint_of_another_decomposition_is_refused(tmp_path):
+    """A checkpoint written with another oversampling (same mesh, same number of
+    subdomains and DoFs) is refused before the library reads it, and so are
+    arrays whose shapes do not match the handle's oversampling domains."""
+    from dataclasses import replace
+    from paper_2211_13893_gb300 import MSGFEM
+    cfg = get_config("t2")
+    ang = element_angles(cfg)
+    a = MSGFEM.from_config(cfg, ang, seed=4)
+    a.local_spaces(cfg.n_loc)
+    a.save_local(tmp_path / "local")
+    out = [a.export_local(j) for j in range(a.N)]
+    a.close()
+    b = MSGFEM.from_config(replace(cfg, oversampling=cfg.oversampling + 1), ang, seed=4)
+    with pytest.raises(ValueError):
+        b.load_local(tmp_path / "local")
+    lam = np.stack([o[1] for o in out])
+    with pytest.raises(ValueError):
+        b.import_local(lam, [o[0] for o in out])
+    with pytest.raises(ValueError):
+        b.import_local(lam[:, :3], [o[0] for o in out])
+    b.close()

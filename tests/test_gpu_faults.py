@@ -74,11 +74,15 @@ def test_step_cap_gives_enoconv(solver):
     m.close()
 
 
-def test_bad_warm_start_falls_back_to_cold_start():
-    """A registered start block that cannot converge (NaN entries) is dropped:
-    those subdomains are solved again from the cold start, which is the
-    warm start's fallback.  Eigenvalues equal those of a cold run (1e-8 per
-    eigenvalue) and msgfem_subinfo.cold_restart marks the subdomains."""
+@pytest.mark.parametrize("kind", ["nan", "zero"])
+def test_bad_warm_start_falls_back_to_cold_start(kind):
+    """Start blocks that cannot lead anywhere fall back to the cold start, the
+    warm start's fallback: a block with NaN entries (a network that produced
+    NaN) is refused before use; an all-zero block (finite, rank 0) makes the
+    block Krylov basis break down, the subdomain reaches the step cap
+    unconverged and is solved again from the cold start.  Eigenvalues equal
+    those of a cold run (1e-8 per eigenvalue) and msgfem_subinfo.cold_restart
+    marks the subdomains."""
     import numpy as np
     import torch
     from parity_util import assert_eigs
@@ -94,8 +98,9 @@ def test_bad_warm_start_falls_back_to_cold_start():
         n2, nw = m.warm_sizes(j, cfg.n_loc)
         if nw <= 0:
             continue
-        blocks[j] = torch.full((n2, 8), float("nan"), dtype=torch.float32, device="cuda")
-        m.set_start_block(j, blocks[j], 8, min(nw, 8))
+        fill = float("nan") if kind == "nan" else 0.0
+        blocks[j] = torch.full((n2, 8), fill, dtype=torch.float32, device="cuda")
+        m.set_start_block(j, blocks[j], 8, 8)
     assert blocks
     lam = m.local_spaces(cfg.n_loc)
     for j in range(m.N):

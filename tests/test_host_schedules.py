@@ -50,9 +50,12 @@ def test_schedules_are_race_free(name, mixed, left, groups):
 
 @pytest.mark.parametrize("name", ["t4", "s2"])
 @pytest.mark.parametrize("mixed", [False, True])
-def test_schedules_are_race_free_multi_tile(name, mixed):
-    """Larger layers (several 64-row tiles per layer block, 8 and 12 subdomains)."""
-    _race_free(name, mixed, True, (16, 16))
+@pytest.mark.parametrize("left", [False, True])
+@pytest.mark.parametrize("groups", [(16, 16), (3, 5)])
+def test_schedules_are_race_free_multi_tile(name, mixed, left, groups):
+    """Larger layers (several 64-row tiles per layer block, 8 and 12 subdomains),
+    right- and left-looking, even and uneven stream-group splits."""
+    _race_free(name, mixed, left, groups)
 
 
 def _race_free(name, mixed, left, groups):

@@ -17,6 +17,8 @@ Sizes are the ones of the five benchmark workloads:
   perturbation (learned warm-start workload).
 
 ``p2`` has c2-sized subdomains but only six of them (profiling).
+``a1``, ``a4``, ``a8``, ``a15``: the c1 topology with in-plane element edges of 1, 4, 8
+and 15 ply thicknesses (the element aspect-ratio study of Sec. 5.3).
 Smaller ``t*`` workloads are test cases that span several layers, ragged
 partitions and both clamped and floating subdomains.
 """
@@ -86,6 +88,12 @@ CONFIGS = {
     "t4": BeamConfig("t4", 40, 6, 12, sx=4, sy=2, overlap=2, oversampling=4, n_loc=20,
                      noise_sd_deg=1.0),
 }
+# element aspect-ratio sweep (Sec. 5.3): in-plane element edge = aspect ratio x ply
+# thickness, the c1 beam's topology, oversampling 4
+ASPECT_RATIOS = (1, 4, 8, 15)
+for _ar in ASPECT_RATIOS:
+    CONFIGS[f"a{_ar}"] = BeamConfig(f"a{_ar}", 24, 4, 12, hx=0.25 * _ar, hy=0.25 * _ar, sx=2, sy=1, overlap=1,
+                                    oversampling=4, n_loc=12)
 
 
 def get_config(name: str):
