@@ -701,7 +701,8 @@ def run_warm_c5(args, dev, n_train=384, n_test=128, batch=128):
             n2, nw = ws.size(j)
             start = blocks[j].cpu().numpy()[:, :nw] if blocks is not None else rng.standard_normal((n2, nw))
             angs.append(angle(start, conv[j][:, :nw]))
-        res[kind] = {"iterations_mean": float(np.mean(iters)), "start_angle_rad_mean": float(np.mean(angs)),
+        res[kind] = {"iterations_mean": float(np.mean(iters)), "iterations_max": int(np.max(iters)),
+                     "start_angle_rad_mean": float(np.mean(angs)),
                      "solves_per_s": m.N / (ms[-1] / 1000.0), "ms_per_batch": ms[-1]}
     ws.apply(None)
     # the same test batch in mixed precision (FP32 factors and solves, FP64
@@ -727,8 +728,8 @@ def run_warm_c5(args, dev, n_train=384, n_test=128, batch=128):
             b.synchronize()
             ms.append(a.elapsed_time(b))
         iters = [mm.info(j)["iterations"] for j in range(mm.N)]
-        mixed[kind] = {"iterations_mean": float(np.mean(iters)), "solves_per_s": mm.N / (ms[-1] / 1000.0),
-                       "ms_per_batch": ms[-1]}
+        mixed[kind] = {"iterations_mean": float(np.mean(iters)), "iterations_max": int(np.max(iters)),
+                       "solves_per_s": mm.N / (ms[-1] / 1000.0), "ms_per_batch": ms[-1]}
     mm.close()
     m.close()
     top = np.abs(lam64).max(axis=1, keepdims=True)

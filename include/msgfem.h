@@ -277,7 +277,10 @@ typedef struct {
   int factor_kernel;    /* msgfem_options.factor_kernel chosen (mixed precision) */
   double factor_ms_tc[2][2];   /* as factor_ms with the tensor-core tile kernel; -1 = not run */
   double tc_factor_diff;       /* ||L_tc - L_fma||_F / ||L_fma||_F on the first subdomain of the measured
-                                  wave (the tensor-core kernel is adopted only when <= 1e-4); -1 = not run */
+                                  wave, both with the fastest FMA schedule; -1 = not run */
+  double fma_factor_diff;      /* the same between the FMA kernel's two schedules (two summation orders:
+                                  the factor's FP32 rounding level); the tensor-core kernel is adopted
+                                  only when tc_factor_diff <= 2 fma_factor_diff and it is faster */
 } msgfem_tuning;
 
 /* Per-subdomain diagnostics filled by msgfem_get_info. */
@@ -437,15 +440,18 @@ msgfem_status msgfem_energy_error_noalloc(msgfem_h h, const double* u, const dou
  * assembly), ECUDA. */
 msgfem_status msgfem_solution_errors(msgfem_h h, const double* u_ref, double* errors_out);
 
-/* Autotuner of the block-solve launches (not in the paper: a library
- * convenience for batches of uneven subdomains).  On the subdomains of the
- * last wave of the previous msgfem_local_spaces call it first times the
+/* Autotuner of the factorisation and block-solve launches (not in the paper:
+ * a library convenience for batches of uneven subdomains).  On the subdomains
+ * of the last wave of the previous msgfem_local_spaces call it first times the
  * layer-block factorisation with the right- and the left-looking schedule,
  * dealt into 16 or 32 stream groups (re-assembling the layer blocks before
- * each run), and keeps the fastest, then times `reps` replays (0 = 3) of one
- * 8-column K solve and
- * one A11 solve, captured as a CUDA graph, for every combination of stream
- * groups {4, 8, 16, 32} (at most msgfem_options.streams) and solve kernel (the
+ * each run), in mixed precision with the FMA and with the tensor-core tile
+ * kernel (msgfem_options.factor_kernel; the latter only when its factor passes
+ * the accuracy gate of msgfem_tuning.fma_factor_diff), and keeps the fastest;
+ * then it times `reps` replays (0 = 3, each waited for on the host, as the
+ * eigensolver waits between its solves) of one 8-column K solve and one A11
+ * solve, captured as a CUDA graph, for every combination of stream groups
+ * {4, 8, 16, 32} (at most msgfem_options.streams) and solve kernel (the
  * cp.async ring in mixed precision only, register streaming, two-CTA
  * cluster), then regroups the solve schedules of every wave and sets the
  * kernel to the fastest combination; later calls use it.  The working blocks

@@ -1,20 +1,23 @@
 // Tensor-core tile GEMM of the FP32 layer-block factorisation (mixed path):
 // C(64 x 64) [+]= sign A(64 x K) B(64 x K)^T on the fifth-generation tensor
-// cores, with FP32 accuracy recovered by splitting every operand into two
-// TF32 parts (the "3xTF32" scheme: a = a_hi + a_lo with a_hi and a_lo rounded
-// to TF32, a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi; the dropped a_lo b_lo and the
-// roundings of the low parts are ~2^-21 |a| |b|, the order of an FP32 GEMM's
-// own accumulation error over a 64-deep chunk).
+// cores with FP32 accuracy.  Every FP32 operand is split exactly into three
+// TF32 parts, a = a_hi + a_mid + a_lo (11 + 11 + 2 significant bits, each part
+// rounded to TF32), and the products of weight down to 2^-22 are formed:
+//   a b ~ a_hi b_hi + a_hi b_mid + a_mid b_hi + a_mid b_mid + a_hi b_lo + a_lo b_hi,
+// so that the dropped terms are below 2^-33 |a| |b| and the accuracy is that of
+// the tensor core's FP32 accumulation (a split into two parts, the published
+// 3xTF32 scheme, leaves 2^-21 and measurably slowed the conjugate-gradient
+// solves that this factor preconditions).
 //
 // Data path per 32-deep K chunk (one CTA per tile task):
 //   TMA (cp.async.bulk.tensor.2d, 128-byte swizzle) moves the 64 x 32 FP32
 //   tiles of A and B from the layer-block arrays into shared memory, two chunks
-//   in flight on an mbarrier ring;  the CTA splits them in place into TF32
-//   high and low parts (same swizzled positions, the canonical K-major
-//   layout the MMA reads);  one elected thread issues 4 x 3 tcgen05.mma
-//   kind::tf32 (M = 128: rows 64..127 of A are zero, N = 64, K = 8) into a
-//   64-column TMEM accumulator and commits them to an mbarrier;  after the
-//   last chunk warps 0-1 read rows 0..63 back with tcgen05.ld and update C.
+//   in flight on an mbarrier ring;  the CTA splits them at the same swizzled
+//   positions into the TF32 parts (the canonical K-major layout the MMA
+//   reads);  one elected thread issues 4 x 6 tcgen05.mma kind::tf32 (M = 128:
+//   rows 64..127 of A are zero, N = 64, K = 8) into a 64-column TMEM
+//   accumulator and commits them to an mbarrier;  after the last chunk warps
+//   0-1 read rows 0..63 back with tcgen05.ld and update C.
 // Every mbarrier wait is bounded (a second of %globaltimer); a timeout sets
 // bit 1 of the subdomain's error flag, waits once more for the work in flight
 // and still frees the TMEM.
@@ -33,11 +36,11 @@ constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 1
 // shared-memory layout (bytes from a 1024-aligned base)
 constexpr int OFF_RAW_A = 0;          // [2][64 rows][128 B]  TMA destinations
 constexpr int OFF_RAW_B = 16384;      // [2][64 rows][128 B]
-constexpr int OFF_HI_A = 32768;       // [128 rows][128 B]  rows 64..127 zero
-constexpr int OFF_LO_A = 49152;
-constexpr int OFF_HI_B = 65536;       // [64 rows][128 B]
-constexpr int OFF_LO_B = 73728;
-constexpr int OFF_BAR = 81920;        // full[2], mma (8 B each), TMEM address (4 B)
+constexpr int OFF_A = 32768;          // 3 parts (hi, mid, lo) x [128 rows][128 B], rows 64..127 zero
+constexpr int A_PART = 16384;
+constexpr int OFF_B = 81920;          // 3 parts x [64 rows][128 B]
+constexpr int B_PART = 8192;
+constexpr int OFF_BAR = 106496;       // full[2], mma (8 B each), TMEM address (4 B)
 constexpr int SMEM = OFF_BAR + 64 + 1024;   // + alignment slack
 constexpr uint32_t CHUNK_BYTES = 2 * 64 * 128;   // A and B tiles of one chunk
 constexpr unsigned long long TIMEOUT_NS = 1000000000ull;
@@ -118,9 +121,13 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
-__device__ __forceinline__ void split4(const float4 v, float4& hi, float4& lo) {
-  hi = make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
-  lo = make_float4(to_tf32(v.x - hi.x), to_tf32(v.y - hi.y), to_tf32(v.z - hi.z), to_tf32(v.w - hi.w));
+// x = hi + mid + lo exactly: hi = tf32(x), mid = tf32(x - hi), lo = x - hi - mid
+// (both differences are exact in FP32; lo keeps the last two bits of x)
+__device__ __forceinline__ void split3(float x, float& hi, float& mid, float& lo) {
+  hi = to_tf32(x);
+  const float r = x - hi;
+  mid = to_tf32(r);
+  lo = to_tf32(r - mid);
 }
 
 // 16 consecutive TMEM columns of this thread's lane
@@ -183,10 +190,10 @@ __device__ void gemm_task(const Task& t, unsigned char* smem_raw, const SubDev* 
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // zero rows 64..127 of the high and low A operands (M = 128 with 64 real rows)
-  for (int e = tid; e < 2 * 512; e += THREADS) {
+  // zero rows 64..127 of the three A parts (M = 128 with 64 real rows)
+  for (int e = tid; e < 3 * 512; e += THREADS) {
     const int part = e >> 9, i = e & 511;
-    reinterpret_cast<float4*>(sm + (part ? OFF_LO_A : OFF_HI_A) + 8192)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    reinterpret_cast<float4*>(sm + OFF_A + A_PART * part + 8192)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   fence_before();
   __syncthreads();
@@ -224,12 +231,18 @@ __device__ void gemm_task(const Task& t, unsigned char* smem_raw, const SubDev* 
     }
     // split the raw tiles at the same (swizzled) positions: 16-byte chunks
     for (int e = tid; e < 1024; e += THREADS) {
-      const int part = e >> 9, i = e & 511;
-      const float4 v = reinterpret_cast<const float4*>(sm + (part ? OFF_RAW_B : OFF_RAW_A) + 8192 * s)[i];
-      float4 hi, lo;
-      split4(v, hi, lo);
-      reinterpret_cast<float4*>(sm + (part ? OFF_HI_B : OFF_HI_A))[i] = hi;
-      reinterpret_cast<float4*>(sm + (part ? OFF_LO_B : OFF_LO_A))[i] = lo;
+      const int isb = e >> 9, i = e & 511;
+      const float4 v = reinterpret_cast<const float4*>(sm + (isb ? OFF_RAW_B : OFF_RAW_A) + 8192 * s)[i];
+      float4 p0, p1, p2;
+      split3(v.x, p0.x, p1.x, p2.x);
+      split3(v.y, p0.y, p1.y, p2.y);
+      split3(v.z, p0.z, p1.z, p2.z);
+      split3(v.w, p0.w, p1.w, p2.w);
+      unsigned char* dst = sm + (isb ? OFF_B : OFF_A);
+      const int stride = isb ? B_PART : A_PART;
+      reinterpret_cast<float4*>(dst)[i] = p0;
+      reinterpret_cast<float4*>(dst + stride)[i] = p1;
+      reinterpret_cast<float4*>(dst + 2 * stride)[i] = p2;
     }
     fence_async_smem();
     fence_before();
@@ -239,10 +252,16 @@ __device__ void gemm_task(const Task& t, unsigned char* smem_raw, const SubDev* 
 #pragma unroll
       for (int ks = 0; ks < KCH / 8; ++ks) {
         const uint32_t o = 32 * ks;   // 8 TF32 along K
-        const uint64_t ah = sdesc(base + OFF_HI_A + o), al = sdesc(base + OFF_LO_A + o);
-        const uint64_t bh = sdesc(base + OFF_HI_B + o), bl = sdesc(base + OFF_LO_B + o);
+        const uint64_t ah = sdesc(base + OFF_A + o), am = sdesc(base + OFF_A + A_PART + o),
+                       al = sdesc(base + OFF_A + 2 * A_PART + o);
+        const uint64_t bh = sdesc(base + OFF_B + o), bm = sdesc(base + OFF_B + B_PART + o),
+                       bl = sdesc(base + OFF_B + 2 * B_PART + o);
+        // the smallest products first
         mma_tf32(tmem, al, bh, (c > 0 || ks > 0) ? 1u : 0u);
         mma_tf32(tmem, ah, bl, 1u);
+        mma_tf32(tmem, am, bm, 1u);
+        mma_tf32(tmem, am, bh, 1u);
+        mma_tf32(tmem, ah, bm, 1u);
         mma_tf32(tmem, ah, bh, 1u);
       }
       mma_commit(bar_mma);

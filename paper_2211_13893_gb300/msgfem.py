@@ -71,7 +71,8 @@ class Tuning(C.Structure):
     _fields_ = [("factor_schedule", C.c_int), ("factor_streams", C.c_int), ("factor_ms", (C.c_double * 2) * 2),
                 ("streams", C.c_int), ("solve_kernel", C.c_int), ("best_ms", C.c_double),
                 ("solve_ms", (C.c_double * 3) * 4), ("factor_kernel", C.c_int),
-                ("factor_ms_tc", (C.c_double * 2) * 2), ("tc_factor_diff", C.c_double)]
+                ("factor_ms_tc", (C.c_double * 2) * 2), ("tc_factor_diff", C.c_double),
+                ("fma_factor_diff", C.c_double)]
 
 
 class Profile(C.Structure):
@@ -377,7 +378,7 @@ class MSGFEM:
                 "solve_ms": [[t.solve_ms[g][v] for v in range(3)] for g in range(4)],
                 "factor_kernel": t.factor_kernel,
                 "factor_ms_tc": [[t.factor_ms_tc[f][g] for g in range(2)] for f in range(2)],
-                "tc_factor_diff": t.tc_factor_diff}
+                "tc_factor_diff": t.tc_factor_diff, "fma_factor_diff": t.fma_factor_diff}
 
     def schwarz_solve(self, coarse=None, b=None, u0=None, rtol=0.0, max_iter=0, u_out=None, allow_noconv=False):
         """Two-level additive Schwarz PCG for the fine problem (include/msgfem.h

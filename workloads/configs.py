@@ -89,11 +89,11 @@ CONFIGS = {
                      noise_sd_deg=1.0),
 }
 # element aspect-ratio sweep (Sec. 5.3): in-plane element edge = aspect ratio x ply
-# thickness, the c1 beam's topology, oversampling 4
+# thickness, the c1 beam's topology, oversampling 4, the 8 smallest eigenpairs
 ASPECT_RATIOS = (1, 4, 8, 15)
 for _ar in ASPECT_RATIOS:
     CONFIGS[f"a{_ar}"] = BeamConfig(f"a{_ar}", 24, 4, 12, hx=0.25 * _ar, hy=0.25 * _ar, sx=2, sy=1, overlap=1,
-                                    oversampling=4, n_loc=12)
+                                    oversampling=4, n_loc=8)
 
 
 def get_config(name: str):
