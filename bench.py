@@ -108,7 +108,8 @@ def _solve_kernel_name(tuning):
     k = (tuning or {}).get("solve_kernel", 1)
     return {1: "k_solve_async (FP32 block solves, 8 right-hand sides, cp.async ring)",
             2: "k_solve_stream<float, 1> (FP32 block solves, 8 right-hand sides, register streaming)",
-            3: "k_solve_stream<float, 2> (FP32 block solves, 8 right-hand sides, two-CTA cluster)"}.get(k, str(k))
+            3: "k_solve_stream<float, 2> (FP32 block solves, 8 right-hand sides, two-CTA cluster)",
+            4: "k_solve_tma (FP32 block solves, 8 right-hand sides, TMA-filled ring)"}.get(k, str(k))
 
 
 def dist_env():

@@ -187,7 +187,10 @@ typedef struct {
   int solve_kernel;     /* kernel of the 8-column block solves: 0 = build default (FP32: cp.async
                            ring, FP64: register streaming), 1 = cp.async ring (FP32 only),
                            2 = register streaming, one CTA per 64-row task, 3 = two-CTA
-                           cluster per task (inner dimension split); msgfem_autotune sets it */
+                           cluster per task (inner dimension split), 4 = the ring of 1 filled
+                           by tensor-memory-accelerator copies, one 64 x 64 tile per copy
+                           (FP32 only; a copy that does not arrive within a second makes the
+                           call return MSGFEM_ECUDA); msgfem_autotune sets it */
   int factor_schedule;  /* layer-block factorisation: 0 = right-looking (per tile column: POTRF,
                            TRMM, update of the trailing matrix), 1 = left-looking (update of the
                            column by all finished columns, then POTRF, TRMM); same work, fewer
@@ -271,13 +274,15 @@ typedef struct {
   double factor_ms[2][2];  /* factorisation of the measured wave: [right-, left-looking][16, 32
                               groups]; -1 = not run */
   int streams;          /* stream groups of the block-solve schedules (4, 8, 16 or 32) */
-  int solve_kernel;     /* msgfem_options.solve_kernel value chosen (1, 2 or 3) */
-  double best_ms;       /* time of one 8-column K solve plus one A11 solve of the measured wave */
-  double solve_ms[4][3];   /* [streams 4, 8, 16, 32][kernel 1, 2, 3]; -1 = not applicable or not run */
+  int solve_kernel;     /* msgfem_options.solve_kernel value chosen (1 to 4) */
+  double best_ms;       /* time of one application of the shift-invert operator to an 8-column
+                           block of the measured wave (solves, refinement and stencils) */
+  double solve_ms[4][4];   /* [streams 4, 8, 16, 32][kernel 1, 2, 3, 4]; -1 = not applicable or not run */
   int factor_kernel;    /* msgfem_options.factor_kernel chosen (mixed precision) */
   double factor_ms_tc[2][2];   /* as factor_ms with the tensor-core tile kernel; -1 = not run */
-  double tc_factor_diff;       /* ||L_tc - L_fma||_F / ||L_fma||_F on the first subdomain of the measured
-                                  wave, both with the fastest FMA schedule; -1 = not run */
+  double tc_factor_diff;       /* ||L_tc - L_fma||_F / ||L_fma||_F on the measured wave's subdomain
+                                  with the widest K layer, both with the fastest FMA schedule;
+                                  -1 = not run */
   double fma_factor_diff;      /* the same between the FMA kernel's two schedules (two summation orders:
                                   the factor's FP32 rounding level); the tensor-core kernel is adopted
                                   only when tc_factor_diff <= 2 fma_factor_diff and it is faster */
@@ -448,16 +453,19 @@ msgfem_status msgfem_solution_errors(msgfem_h h, const double* u_ref, double* er
  * each run), in mixed precision with the FMA and with the tensor-core tile
  * kernel (msgfem_options.factor_kernel; the latter only when its factor passes
  * the accuracy gate of msgfem_tuning.fma_factor_diff), and keeps the fastest;
- * then it times `reps` replays (0 = 3, each waited for on the host, as the
- * eigensolver waits between its solves) of one 8-column K solve and one A11
- * solve, captured as a CUDA graph, for every combination of stream groups
- * {4, 8, 16, 32} (at most msgfem_options.streams) and solve kernel (the
- * cp.async ring in mixed precision only, register streaming, two-CTA
- * cluster), then regroups the solve schedules of every wave and sets the
+ * then, for every combination of stream groups {4, 8, 16, 32} (at most
+ * msgfem_options.streams) and solve kernel (register streaming, two-CTA
+ * cluster, and in mixed precision the cp.async ring and the TMA-filled ring),
+ * it times `reps` (0 = 3) applications of the shift-invert operator as the
+ * eigensolver makes them, back to back on a fresh random block each (the
+ * N-product stencil, the 8-column K solve with, in mixed precision, its PCG
+ * refinement, and the A-harmonic extension by A11 solves), after one untimed
+ * application, then regroups the solve schedules of every wave and sets the
  * kernel to the fastest combination; later calls use it.  The working blocks
  * the timing reads and writes are scratch of the eigensolver; results of the
- * previous local stage are kept.  tuning (may be NULL) receives the choice
- * and the measured times.  Errors: ESTATE before msgfem_local_spaces, ECUDA. */
+ * previous local stage, the phase timers and the launch count are kept.
+ * tuning (may be NULL) receives the choice and the measured times.  Errors:
+ * ESTATE before msgfem_local_spaces, ECUDA. */
 msgfem_status msgfem_autotune(msgfem_h h, int reps, msgfem_tuning* tuning);
 
 /* Two-level additive Schwarz preconditioned conjugate gradients for the fine

@@ -515,6 +515,7 @@ void timed_solve_w(msgfem* h, int mat, int src, int dst, int neg, int width, int
                        ((uint64_t)width << 32) | ((uint64_t)src << 16) | ((uint64_t)dst << 4) | ((uint64_t)neg << 1) |
                        (uint64_t)add;
   const WaveSched& w = h->waves[h->cur];
+  set_solve_maps(h->d_solve_maps, h->d_kerr);
   run_graph(h, key, [&](cudaStream_t cs) {
     if (h->mixed) {
       const SolveScheduleT<float>& sc = width == KB ? (mat == 0 ? w.solveK8f : w.solveA8f)
@@ -987,7 +988,7 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
   h->ngroup = h->opt.streams > 0 ? std::min(h->opt.streams, NGROUP) : 16;
   h->ngroup_created = h->opt.streams > 0 ? h->ngroup : NGROUP;
   h->ngroup_factor = h->ngroup;
-  if (h->opt.solve_kernel < 0 || h->opt.solve_kernel > SOLVE_STREAM_CL2) {
+  if (h->opt.solve_kernel < 0 || h->opt.solve_kernel > SOLVE_TMA_RING) {
     *out = h;
     h->err = "unknown solve_kernel";
     return MSGFEM_EINVAL;
@@ -1069,7 +1070,17 @@ msgfem_status msgfem_update_angles(msgfem_h h, const double* ang) {
   return st;
 }
 
+static msgfem_status local_spaces_run(msgfem_h h, int n_loc, double* lambda_out);
+
+// every entry point that runs block solves ends by reading the TMA stages' error flag
 msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
+  if (!h) return MSGFEM_EINVAL;
+  const msgfem_status st = local_spaces_run(h, n_loc, lambda_out);
+  const msgfem_status ke = check_stage_error(h);
+  return ke != MSGFEM_OK ? ke : st;
+}
+
+static msgfem_status local_spaces_run(msgfem_h h, int n_loc, double* lambda_out) {
   if (!h) return MSGFEM_EINVAL;
   if (h->stage < 1) return MSGFEM_ESTATE;
   if (n_loc < 1) { h->err = "n_loc must be >= 1"; return MSGFEM_EINVAL; }
@@ -1546,7 +1557,16 @@ msgfem_status msgfem_get_info(msgfem_h h, int j, msgfem_subinfo* info) {
   return MSGFEM_OK;
 }
 
+static msgfem_status autotune_run(msgfem_h h, int reps, msgfem_tuning* out);
+
 msgfem_status msgfem_autotune(msgfem_h h, int reps, msgfem_tuning* out) {
+  if (!h) return MSGFEM_EINVAL;
+  const msgfem_status st = autotune_run(h, reps, out);
+  const msgfem_status ke = check_stage_error(h);
+  return ke != MSGFEM_OK ? ke : st;
+}
+
+static msgfem_status autotune_run(msgfem_h h, int reps, msgfem_tuning* out) {
   if (!h) return MSGFEM_EINVAL;
   if (h->stage < 2) return MSGFEM_ESTATE;
   if (reps <= 0) reps = 3;
@@ -1620,12 +1640,16 @@ msgfem_status msgfem_autotune(msgfem_h h, int reps, msgfem_tuning* out) {
       }
   }
   if (h->mixed) {
-    // accuracy gate of the tensor-core kernel: its factor of the first subdomain
-    // of the wave against the FMA kernel's (fastest FMA schedule), compared with
-    // the difference between the FMA kernel's two schedules (the FP32 rounding
-    // level of the factor: two summation orders); the tensor-core factor must be
-    // at most twice as far off
-    const SubDev& s0 = h->sub[wl.members[0]];
+    // accuracy gate of the tensor-core kernel: its factor of the wave's largest
+    // subdomain (widest K layer: the most tiles per layer, where the two
+    // schedules sum in different orders) against the FMA kernel's (fastest FMA
+    // schedule), compared with the difference between the FMA kernel's two
+    // schedules (the FP32 rounding level of the factor); the tensor-core factor
+    // must be at most twice as far off
+    int jg = wl.members[0];
+    for (int j : wl.members)
+      if (h->sub[j].bK > h->sub[jg].bK) jg = j;
+    const SubDev& s0 = h->sub[jg];
     const size_t nK = (size_t)s0.bK * s0.bK, nA = (size_t)s0.bA * s0.bA;
     const float* arr[4] = {s0.DKf, s0.LKf, s0.DAf, s0.LAf};
     const size_t len[4] = {nK * (2 * s0.nzn - 1), nK * s0.nzn, nA * (2 * s0.nzn - 1), nA * s0.nzn};
@@ -1679,52 +1703,55 @@ msgfem_status msgfem_autotune(msgfem_h h, int reps, msgfem_tuning* out) {
   t.factor_streams = best_fg;
   t.factor_kernel = best_k;
   const int groups[4] = {4, 8, 16, 32};
-  const int variants[3] = {SOLVE_ASYNC_RING, SOLVE_STREAM, SOLVE_STREAM_CL2};
+  const int variants[4] = {SOLVE_ASYNC_RING, SOLVE_STREAM, SOLVE_STREAM_CL2, SOLVE_TMA_RING};
+  if (h->mixed) TRY(solve_maps_build(h));
   double best = 1e300;
   int best_g = h->ngroup, best_v = h->solve_variant;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
+  auto drop_graphs = [&]() {
+    for (auto it = h->graphs.begin(); it != h->graphs.end();) {
+      if ((it->first >> 60) == 1 || (it->first >> 60) == 2) {
+        if (it->second.first) cudaGraphExecDestroy(it->second.first);
+        it = h->graphs.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  };
+  // block-solve stream groups and kernel: each choice timed on applications
+  // of the shift-invert operator as the eigensolver makes them (N-product
+  // stencil, K solve, in mixed precision with its PCG refinement, and the
+  // A-harmonic extension by A11 solves), back to back on the stream, each on
+  // a fresh random block; one untimed application first captures the graphs.
+  // The phase timers and the launch count are left as they were.
+  spans_collect(h);
+  const msgfem_profile prof_kept = h->prof;
+  const long long launches_kept = g_launch_count;
+  const int saved_variant = h->solve_variant;
   for (int gi = 0; gi < 4; ++gi) {
-    for (int vi = 0; vi < 3; ++vi) t.solve_ms[gi][vi] = -1.0;
+    for (int vi = 0; vi < 4; ++vi) t.solve_ms[gi][vi] = -1.0;
     if (groups[gi] > h->ngroup_created) continue;
+    drop_graphs();
     h->ngroup = groups[gi];
     build_wave_solve_schedules(h, wl);
     TRY(upload_wave_solves(h, wl));
-    for (int vi = 0; vi < 3; ++vi) {
+    for (int vi = 0; vi < 4; ++vi) {
       const int v = variants[vi];
-      if (v == SOLVE_ASYNC_RING && !h->mixed) continue;
-      // one KB-wide K solve and one A11 solve of the wave's working blocks (scratch), as one graph
-      cudaGraph_t g = nullptr;
-      cudaGraphExec_t ex = nullptr;
-      const long long before = g_launch_count;
-      CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-      if (h->mixed) {
-        run_solve_mv(wl.solveK8f, h->cap, MV_ZB, MV_WB, 0, KB, &h->gs, 0, v);
-        run_solve_mv(wl.solveA8f, h->cap, MV_TB, MV_WB, 1, KB, &h->gs, 0, v);
-      } else {
-        run_solve_mv(wl.solveK8, h->cap, MV_ZB, MV_WB, 0, KB, &h->gs, 0, v);
-        run_solve_mv(wl.solveA8, h->cap, MV_TB, MV_WB, 1, KB, &h->gs, 0, v);
-      }
-      CK(cudaStreamEndCapture(h->cap, &g));
-      g_launch_count = before;
-      CK(cudaGraphInstantiate(&ex, g, 0));
-      CK(cudaGraphDestroy(g));
-      CK(cudaGraphLaunch(ex, st));
-      CK(cudaStreamSynchronize(st));
-      // each replay waits for the previous one on the host, as the eigensolver's solves
-      // do (it reads convergence flags between them): the launch latency of a graph of
-      // many stream groups is part of the measured time
-      CK(cudaEventRecord(e0, st));
-      for (int r = 0; r < reps; ++r) {
-        CK(cudaGraphLaunch(ex, st));
-        CK(cudaStreamSynchronize(st));
+      if ((v == SOLVE_ASYNC_RING || v == SOLVE_TMA_RING) && !h->mixed) continue;
+      drop_graphs();
+      h->solve_variant = v;
+      for (int r = 0; r <= reps; ++r) {
+        if (r == 1) CK(cudaEventRecord(e0, st));
+        launch_random_kb(h, MV_WB, h->opt.seed + 7919ull * (r + 1));
+        apply_M_kb(h);
       }
       CK(cudaEventRecord(e1, st));
       CK(cudaEventSynchronize(e1));
+      CK_LAUNCH();
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, e0, e1));
-      CK(cudaGraphExecDestroy(ex));
       t.solve_ms[gi][vi] = ms / reps;
       if (ms / reps < best) {
         best = ms / reps;
@@ -1733,6 +1760,16 @@ msgfem_status msgfem_autotune(msgfem_h h, int reps, msgfem_tuning* out) {
       }
     }
   }
+  drop_graphs();
+  h->solve_variant = saved_variant;
+  CK(cudaStreamSynchronize(st));
+  for (auto& sp : h->spans) {   // the timing's phase spans are dropped
+    h->ev_pool.push_back(sp.a);
+    h->ev_pool.push_back(sp.b);
+  }
+  h->spans.clear();
+  h->prof = prof_kept;
+  g_launch_count = launches_kept;
   CK(cudaEventDestroy(e0));
   CK(cudaEventDestroy(e1));
   // adopt the choice: rebuild every wave's factorisation (its stream groups

@@ -231,6 +231,8 @@ struct msgfem {
   int geneo = 0;                     // method == MSGFEM_METHOD_GENEO: the GenEO eigenproblem on Omega_j
   int factor_tc = 0;                 // FP32 factorisation on the tensor cores (msgfem_options.factor_kernel)
   void* d_tc_maps = nullptr;         // device tensor maps of every subdomain's FP32 arrays (4 per subdomain)
+  void* d_solve_maps = nullptr;      // the same arrays in 64 x 64 unswizzled boxes (TMA solve stages)
+  int* d_kerr = nullptr;             // set by a TMA solve stage that did not arrive in time
   int refine = 2;                    // FP64 refinement steps per FP32 solve
   std::vector<CoarsePair> pairs;
   CoarsePair* d_pairs = nullptr;
@@ -322,7 +324,12 @@ void prepare_tile_kernels();
 template <typename T>
 void run_schedule(const ScheduleT<T>& s, cudaStream_t st, const StreamSet* gs = nullptr);
 // solve steps; scatter_add adds the result into the destination multivector
-enum { SOLVE_DEFAULT = 0, SOLVE_ASYNC_RING = 1, SOLVE_STREAM = 2, SOLVE_STREAM_CL2 = 3 };
+enum { SOLVE_DEFAULT = 0, SOLVE_ASYNC_RING = 1, SOLVE_STREAM = 2, SOLVE_STREAM_CL2 = 3, SOLVE_TMA_RING = 4 };
+// tensor maps and error flag of the TMA solve stages (k_dense.cu), set before solve runs
+void set_solve_maps(const void* maps, int* err);
+msgfem_status solve_maps_build(msgfem* h);
+// MSGFEM_ECUDA (and the flag cleared) when a TMA solve stage reported a failure
+msgfem_status check_stage_error(msgfem* h);
 template <typename T>
 void run_solve_mv(const SolveScheduleT<T>& s, cudaStream_t st, int src, int dst, int gather_neg, int width = PST,
                   const StreamSet* gs = nullptr, int scatter_add = 0, int variant = SOLVE_DEFAULT);

@@ -766,6 +766,171 @@ k_solve_async(const SolveTaskT<float>* __restrict__ tasks, const SubDev* __restr
   }
 }
 
+// The same solve step with the factor slab staged by the tensor memory
+// accelerator: one thread issues one cp.async.bulk.tensor.2d per 64 x 64 stage
+// (16 KiB, unswizzled: the ring's row-major layout) that completes on the
+// stage's mbarrier, instead of 1,024 16-byte cp.async copies from all threads.
+// The tensor maps cover the subdomain's FP32 layer-block arrays on this GPU
+// only (no multicast).  Before any copy the task's slab is checked to lie in
+// one mapped array with the array's row stride, a 16-byte-aligned column and
+// every stage inside the array; waits are bounded.  A task that fails the check
+// or a stage that does not arrive within a second sets *err and the task's
+// products are skipped.
+__global__ void __launch_bounds__(256, 2)
+k_solve_tma(const SolveTaskT<float>* __restrict__ tasks, const SubDev* __restrict__ subs,
+            const int* __restrict__ active, int src, int dst, int gather_neg, int scatter_add,
+            const CUtensorMap* __restrict__ maps, int* __restrict__ err) {
+  const SolveTaskT<float> t = tasks[blockIdx.x];
+  if (t.sub >= 0 && active != nullptr && !active[t.sub]) return;
+  extern __shared__ __align__(128) unsigned char smem_b[];
+  // the ring on a 1024-byte boundary (the launch adds 1 KiB of shared memory)
+  float* ring = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_b) + 1023) & ~uintptr_t(1023));
+  float* Bs = ring + ASYNC_DEPTH * ASYNC_STAGE;                       // [K / 4][ASYNC_CS]
+  __shared__ __align__(8) unsigned long long full[ASYNC_DEPTH];
+  __shared__ const CUtensorMap* smap;
+  __shared__ int sx, sy;
+  const int tid = threadIdx.x;
+  const bool transA = (t.flags & S_TRANSA) != 0;
+  const int nst = t.K / 64;
+  const uint32_t ring_s = tc::saddr(ring), bar0 = tc::saddr(full);
+  int issued = 0;   // stages issued (thread 0)
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  // stage i of the slab: plain A, rows 0..63 x columns 64 i ..; transposed, rows 64 i .. x columns 0..63
+  auto issue = [&](int i) {
+    const uint32_t bar = bar0 + 8 * (i % ASYNC_DEPTH);
+    tc::mbar_expect_tx(bar, (uint32_t)(ASYNC_STAGE * sizeof(float)));
+    tc::tma_load_2d(ring_s + (uint32_t)((i % ASYNC_DEPTH) * ASYNC_STAGE * sizeof(float)), smap,
+                    sx + (transA ? 0 : 64 * i), sy + (transA ? 64 * i : 0), bar);
+    issued = i + 1;
+  };
+  if (tid == 0) {
+    for (int d = 0; d < ASYNC_DEPTH; ++d) tc::mbar_init(bar0 + 8 * d, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    int x = 0, y = 0;
+    const CUtensorMap* m = t.sub >= 0 ? tc::locate(subs[t.sub], maps, t.sub, t.A, x, y) : nullptr;
+    if (m != nullptr) {
+      const SubDev& sd = subs[t.sub];
+      const int which = (int)(m - maps) - 4 * t.sub;   // DKf, LKf, DAf, LAf
+      const int b = which < 2 ? sd.bK : sd.bA;
+      const int rows = (which == 0 ? 2 * sd.nzn - 1 : which == 1 ? sd.nzn : which == 2 ? 2 * sd.nzn - 1 : sd.nzn) * b;
+      const int w = transA ? 64 : 64 * nst, hgt = transA ? 64 * nst : 64;
+      if (t.lda != b || (x & 3) != 0 || x + w > b || y + hgt > rows) m = nullptr;
+    }
+    smap = m;
+    sx = x;
+    sy = y;
+    // the factor slab does not depend on the previous step: its first stages go out first
+    if (m != nullptr)
+      for (int i = 0; i < ASYNC_DEPTH - 1 && i < nst; ++i) issue(i);
+  }
+  asm volatile("griddepcontrol.wait;" ::: "memory");   // B, the gathered vectors and C follow the previous step
+  {
+    const float4* Bv = reinterpret_cast<const float4*>(t.B);
+    for (int e = tid; e < t.K * (KB / 4); e += 256) {
+      const int k = e / (KB / 4), c = (e % (KB / 4)) * 4;
+      *reinterpret_cast<float4*>(Bs + (k / 4) * ASYNC_CS + (k % 4) * KB + c) = Bv[e];
+    }
+  }
+  __syncthreads();
+  bool ok = smap != nullptr;
+  const int h = transA ? tid / 16 : tid % 16;
+  const int g = transA ? tid % 16 : tid / 16;
+  float acc[4][KB];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < KB; ++c) acc[r][c] = 0.f;
+  int waited = 0;   // stages whose copies have been waited for
+  for (int i = 0; i < nst && ok; ++i) {
+    // keep ASYNC_DEPTH - 1 stages in flight: stage i + DEPTH - 1 goes into the
+    // slot released by the trailing barrier of iteration i - 1
+    if (tid == 0 && i + ASYNC_DEPTH - 1 < nst) {
+      tc::fence_async_smem();
+      issue(i + ASYNC_DEPTH - 1);
+    }
+    const bool w = tc::mbar_wait(bar0 + 8 * (i % ASYNC_DEPTH), (i / ASYNC_DEPTH) & 1);
+    if (!__syncthreads_and(w)) {
+      ok = false;
+      break;
+    }
+    waited = i + 1;
+    const float* stg = ring + (size_t)(i % ASYNC_DEPTH) * ASYNC_STAGE;
+    const float* bp = Bs + (size_t)(16 * i + h) * ASYNC_CS;   // B rows 64 i + 4 h .. + 3
+    float b[4][KB];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const float4 b0 = *reinterpret_cast<const float4*>(bp + v * KB);
+      const float4 b1 = *reinterpret_cast<const float4*>(bp + v * KB + 4);
+      b[v][0] = b0.x; b[v][1] = b0.y; b[v][2] = b0.z; b[v][3] = b0.w;
+      b[v][4] = b1.x; b[v][5] = b1.y; b[v][6] = b1.z; b[v][7] = b1.w;
+    }
+    if (!transA) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float4 a = *reinterpret_cast<const float4*>(stg + (4 * g + r) * 64 + 4 * h);
+        const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+#pragma unroll
+          for (int c = 0; c < KB; ++c) acc[r][c] = fmaf(av[v], b[v][c], acc[r][c]);
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const float4 a = *reinterpret_cast<const float4*>(stg + (4 * h + v) * 64 + 4 * g);
+        const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < KB; ++c) acc[r][c] = fmaf(av[r], b[v][c], acc[r][c]);
+      }
+    }
+    __syncthreads();   // every warp is done with the slot
+  }
+  if (!ok) {
+    // a stage did not arrive: wait once more (bounded) for every copy issued, then report
+    if (tid == 0) {
+      for (int i = waited; i < issued; ++i) tc::mbar_wait(bar0 + 8 * (i % ASYNC_DEPTH), (i / ASYNC_DEPTH) & 1);
+      if (err != nullptr) atomicExch(err, 1);
+    }
+    __syncthreads();
+  }
+  // sum the 16 k slices: red[h][row][c] in the (now idle) ring
+  float* red = ring;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    float* o = red + ((size_t)h * 64 + 4 * g + r) * KB;
+    *reinterpret_cast<float4*>(o) = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+    *reinterpret_cast<float4*>(o + 4) = make_float4(acc[r][4], acc[r][5], acc[r][6], acc[r][7]);
+  }
+  __syncthreads();
+  const float sgn = (t.flags & S_NEG) ? -1.f : 1.f;
+  const double* gfull = nullptr;
+  double* sfull = nullptr;
+  if (t.flags & (S_INIT_GATHER | S_SCATTER)) {
+    const SubDev& s = subs[t.sub];
+    if (t.flags & S_INIT_GATHER) gfull = mv_ptr(s, src) + (size_t)t.row_off * KB;
+    if (t.flags & S_SCATTER) sfull = mv_ptr(s, dst) + (size_t)t.row_off * KB;
+  }
+  const double gsg = gather_neg ? -1.0 : 1.0;
+  for (int e = tid; e < 64 * KB; e += 256) {
+    const int r = e / KB, c = e % KB;
+    float v = 0.f;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v += red[(size_t)q * 64 * KB + e];
+    v = sgn * v;
+    if (t.flags & S_INIT_TILE) v += t.init[r * KB + c];
+    const int gmr = (t.flags & S_INIT_GATHER) ? t.gmap[r] : -1;
+    if (gmr >= 0) v += (float)(gsg * gfull[(size_t)gmr * KB + c]);
+    t.C[r * KB + c] = v;
+    const int smr = (t.flags & S_SCATTER) ? t.smap[r] : -1;
+    if (smr >= 0) {
+      double* o = sfull + (size_t)smr * KB + c;
+      *o = scatter_add ? *o + (double)v : (double)v;
+    }
+  }
+}
+
 size_t solve_async_smem(int kmax) {
   return (size_t)ASYNC_DEPTH * ASYNC_STAGE * sizeof(float) + (size_t)((kmax + 3) / 4) * ASYNC_CS * sizeof(float);
 }
@@ -792,6 +957,8 @@ static int* g_active = nullptr;   // set by the driver before schedule runs
 static int* g_notspd = nullptr;
 static const SubDev* g_subs = nullptr;
 static const void* g_tc_maps = nullptr;   // tensor maps of the FP32 arrays: tensor-core factorisation on
+static const void* g_solve_maps = nullptr;   // tensor maps of the FP32 arrays for the TMA solve stages
+static int* g_kerr = nullptr;                // error flag of the TMA solve stages
 
 void set_dense_context(int* active, int* notspd, const SubDev* subs) {
   g_active = active;
@@ -801,17 +968,44 @@ void set_dense_context(int* active, int* notspd, const SubDev* subs) {
 
 void set_factor_kernel(const void* tc_maps) { g_tc_maps = tc_maps; }
 
-bool encode_tc_maps(const msgfem* h, std::vector<CUtensorMap>& maps, std::string& err);
+void set_solve_maps(const void* maps, int* err) {
+  g_solve_maps = maps;
+  g_kerr = err;
+}
+
+bool encode_tc_maps(const msgfem* h, std::vector<CUtensorMap>& maps, std::string& err, int box_cols,
+                    CUtensorMapSwizzle swz);
 
 msgfem_status tc_maps_build(msgfem* h) {
   std::vector<CUtensorMap> maps;
   std::string err;
-  if (!encode_tc_maps(h, maps, err)) {
+  if (!encode_tc_maps(h, maps, err, tc::KCH, CU_TENSOR_MAP_SWIZZLE_128B)) {
     h->err = err;
     return MSGFEM_ECUDA;
   }
   if (h->d_tc_maps == nullptr) TRY(dev_alloc_bytes(h, &h->d_tc_maps, maps.size() * sizeof(CUtensorMap)));
   CK(cudaMemcpy(h->d_tc_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+  return MSGFEM_OK;
+}
+
+// tensor maps of the TMA solve stages: boxes of 64 x 64 FP32, unswizzled (the
+// ring's row-major stage layout), and the stage error flag; built on first use
+msgfem_status solve_maps_build(msgfem* h) {
+  if (h->d_solve_maps == nullptr) {
+    std::vector<CUtensorMap> maps;
+    std::string err;
+    if (!encode_tc_maps(h, maps, err, 64, CU_TENSOR_MAP_SWIZZLE_NONE)) {
+      h->err = err;
+      return MSGFEM_ECUDA;
+    }
+    TRY(dev_alloc_bytes(h, &h->d_solve_maps, maps.size() * sizeof(CUtensorMap)));
+    CK(cudaMemcpy(h->d_solve_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    void* p = nullptr;
+    TRY(dev_alloc_bytes(h, &p, sizeof(int)));
+    h->d_kerr = static_cast<int*>(p);
+    CK(cudaMemset(h->d_kerr, 0, sizeof(int)));
+  }
+  set_solve_maps(h->d_solve_maps, h->d_kerr);
   return MSGFEM_OK;
 }
 
@@ -822,7 +1016,19 @@ msgfem_status select_factor_kernel(msgfem* h) {
   } else {
     set_factor_kernel(nullptr);
   }
+  if (h->mixed && h->solve_variant == SOLVE_TMA_RING) TRY(solve_maps_build(h));
+  set_solve_maps(h->d_solve_maps, h->d_kerr);
   return MSGFEM_OK;
+}
+
+msgfem_status check_stage_error(msgfem* h) {
+  if (h->d_kerr == nullptr) return MSGFEM_OK;
+  int e = 0;
+  CK(cudaMemcpy(&e, h->d_kerr, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e == 0) return MSGFEM_OK;
+  CK(cudaMemset(h->d_kerr, 0, sizeof(int)));
+  h->err = "a tensor-memory-accelerator solve stage failed its slab check or did not arrive within a second";
+  return MSGFEM_ECUDA;
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
@@ -847,7 +1053,8 @@ static EncodeTiledFn encode_tiled() {
 // 64 rows x 32 columns (128 bytes, the swizzle width) with 128-byte swizzle.
 // Every tile task of the factorisation starts on a 64-column tile boundary, so
 // each copy's inner coordinate is a multiple of 32 elements (128 bytes).
-bool encode_tc_maps(const msgfem* h, std::vector<CUtensorMap>& maps, std::string& err) {
+bool encode_tc_maps(const msgfem* h, std::vector<CUtensorMap>& maps, std::string& err, int box_cols = tc::KCH,
+                    CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
   EncodeTiledFn enc = encode_tiled();
   if (enc == nullptr) {
     err = "cuTensorMapEncodeTiled is not available from the driver";
@@ -866,11 +1073,11 @@ bool encode_tc_maps(const msgfem* h, std::vector<CUtensorMap>& maps, std::string
       }
       const cuuint64_t dim[2] = {(cuuint64_t)b[m], (cuuint64_t)rows[m]};
       const cuuint64_t stride[1] = {(cuuint64_t)b[m] * sizeof(float)};
-      const cuuint32_t box[2] = {(cuuint32_t)tc::KCH, 64};
+      const cuuint32_t box[2] = {(cuuint32_t)box_cols, 64};
       const cuuint32_t estr[2] = {1, 1};
       const CUresult r = enc(&maps[4 * (size_t)j + m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
                              const_cast<float*>(base[m]), dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (r != CUDA_SUCCESS) {
         err = "cuTensorMapEncodeTiled failed for subdomain " + std::to_string(j);
@@ -923,6 +1130,7 @@ void prepare_tile_kernels() {
   cudaFuncSetAttribute(k_solve_stream<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
   cudaFuncSetAttribute(k_solve_stream<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
   cudaFuncSetAttribute(k_solve_async, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
+  cudaFuncSetAttribute(k_solve_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX);
   done = true;
 }
 
@@ -987,7 +1195,9 @@ static void launch_stream_cluster(const SolveScheduleT<T>& s, const SchedStep& s
 // variant (KB-wide solves): SOLVE_DEFAULT = the build's choice (FP32: the
 // cp.async ring when every inner dimension is a multiple of 64; FP64: register
 // streaming), SOLVE_ASYNC_RING, SOLVE_STREAM (register streaming, one CTA per
-// 64-row task), SOLVE_STREAM_CL2 (two-CTA cluster per task).  A variant that
+// 64-row task), SOLVE_STREAM_CL2 (two-CTA cluster per task), SOLVE_TMA_RING
+// (FP32: the ring filled by tensor-memory-accelerator copies; needs the tensor
+// maps of set_solve_maps).  A variant that
 // does not apply (ring for FP64 or ragged inner dimensions, shared memory over
 // the limit) falls back to the default.
 template <typename T>
@@ -1001,6 +1211,8 @@ void run_solve_mv(const SolveScheduleT<T>& s, cudaStream_t st, int src, int dst,
   const size_t asmem = solve_async_smem(s.kmax);
   const bool async_ok = std::is_same<T, float>::value && s.k64 && asmem <= SOLVE_SMEM_MAX;
   int v = variant;
+  if (v == SOLVE_TMA_RING && (!async_ok || asmem + 1024 > SOLVE_SMEM_MAX || g_solve_maps == nullptr))
+    v = SOLVE_DEFAULT;
   if (v == SOLVE_ASYNC_RING && !async_ok) v = SOLVE_DEFAULT;
   if (v == SOLVE_STREAM && !stream_ok) v = SOLVE_DEFAULT;
   if (v == SOLVE_STREAM_CL2 && smem2 > SOLVE_SMEM_MAX) v = SOLVE_DEFAULT;
@@ -1012,6 +1224,11 @@ void run_solve_mv(const SolveScheduleT<T>& s, cudaStream_t st, int src, int dst,
       return;
     }
     if constexpr (std::is_same<T, float>::value) {
+      if (v == SOLVE_TMA_RING) {
+        launch_pdl(k_solve_tma, step.count, asmem + 1024, stream, s.d_tasks + step.first, g_subs, g_active, src, dst,
+                   gather_neg, scatter_add, static_cast<const CUtensorMap*>(g_solve_maps), g_kerr);
+        return;
+      }
       if (v == SOLVE_ASYNC_RING) {
         launch_pdl(k_solve_async, step.count, asmem, stream, s.d_tasks + step.first, g_subs, g_active, src, dst,
                    gather_neg, scatter_add);

@@ -226,10 +226,23 @@ double tridiag_extreme(const std::vector<double>& d, const std::vector<double>& 
   return 0.5 * (lo + hi);
 }
 
+msgfem_status schwarz_run(msgfem_h hl, msgfem_h hc, const double* b_in, const double* u0, double rtol,
+                          int max_iter, double* u_out, msgfem_pcg_info* info);
+
 }  // namespace
 
 extern "C" msgfem_status msgfem_schwarz_solve(msgfem_h hl, msgfem_h hc, const double* b_in, const double* u0,
                                               double rtol, int max_iter, double* u_out, msgfem_pcg_info* info) {
+  if (!hl || !u_out) return MSGFEM_EINVAL;
+  const msgfem_status st = schwarz_run(hl, hc, b_in, u0, rtol, max_iter, u_out, info);
+  const msgfem_status ke = check_stage_error(hl);   // the local solves' TMA stages
+  return ke != MSGFEM_OK ? ke : st;
+}
+
+namespace {
+
+msgfem_status schwarz_run(msgfem_h hl, msgfem_h hc, const double* b_in, const double* u0, double rtol,
+                          int max_iter, double* u_out, msgfem_pcg_info* info) {
   if (!hl || !u_out) return MSGFEM_EINVAL;
   msgfem* h = hl;
   if (h->stage < 1) return MSGFEM_ESTATE;
@@ -395,3 +408,4 @@ extern "C" msgfem_status msgfem_schwarz_solve(msgfem_h hl, msgfem_h hc, const do
   }
   return MSGFEM_OK;
 }
+}  // namespace

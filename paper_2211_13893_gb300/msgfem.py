@@ -70,7 +70,7 @@ DEV_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
 class Tuning(C.Structure):
     _fields_ = [("factor_schedule", C.c_int), ("factor_streams", C.c_int), ("factor_ms", (C.c_double * 2) * 2),
                 ("streams", C.c_int), ("solve_kernel", C.c_int), ("best_ms", C.c_double),
-                ("solve_ms", (C.c_double * 3) * 4), ("factor_kernel", C.c_int),
+                ("solve_ms", (C.c_double * 4) * 4), ("factor_kernel", C.c_int),
                 ("factor_ms_tc", (C.c_double * 2) * 2), ("tc_factor_diff", C.c_double),
                 ("fma_factor_diff", C.c_double)]
 
@@ -375,7 +375,7 @@ class MSGFEM:
         return {"factor_schedule": t.factor_schedule, "factor_streams": t.factor_streams,
                 "factor_ms": [[t.factor_ms[f][g] for g in range(2)] for f in range(2)],
                 "streams": t.streams, "solve_kernel": t.solve_kernel, "best_ms": t.best_ms,
-                "solve_ms": [[t.solve_ms[g][v] for v in range(3)] for g in range(4)],
+                "solve_ms": [[t.solve_ms[g][v] for v in range(4)] for g in range(4)],
                 "factor_kernel": t.factor_kernel,
                 "factor_ms_tc": [[t.factor_ms_tc[f][g] for g in range(2)] for f in range(2)],
                 "tc_factor_diff": t.tc_factor_diff, "fma_factor_diff": t.fma_factor_diff}

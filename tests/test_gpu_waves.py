@@ -26,13 +26,13 @@ def _run(cfg, ang, **kw):
     return lam, u, prof
 
 
-@pytest.mark.parametrize("name,precision,tol", [("t4", 0, 1e-10), ("s2", 1, 1e-8)])
-def test_waves_match_one_wave(name, precision, tol):
+@pytest.mark.parametrize("name,precision,tol,kernel", [("t4", 0, 1e-10, 0), ("s2", 1, 1e-8, 0), ("s2", 1, 1e-8, 4)])
+def test_waves_match_one_wave(name, precision, tol, kernel):
     cfg = get_config(name)
     ang = element_angles(cfg)
-    la, ua, pa = _run(cfg, ang, precision=precision)
+    la, ua, pa = _run(cfg, ang, precision=precision, solve_kernel=kernel)
     assert pa["waves"] == 1
-    lb, ub, pb = _run(cfg, ang, precision=precision, wave_mb=pa["pool_mb"] / 3.0)
+    lb, ub, pb = _run(cfg, ang, precision=precision, wave_mb=pa["pool_mb"] / 3.0, solve_kernel=kernel)
     assert pb["waves"] >= 3 and pb["pool_mb"] <= pa["pool_mb"] / 3.0 + 1e-9
     scale = np.abs(la).max(axis=1, keepdims=True)
     assert (np.abs(la - lb) / scale).max() <= tol
@@ -68,10 +68,12 @@ def test_boxes_that_do_not_tile_are_rejected():
     assert e.value.code == 1
 
 
-@pytest.mark.parametrize("name,precision,kernel", [("t4", 0, 2), ("t4", 0, 3), ("s2", 1, 1), ("s2", 1, 2),
-                                                   ("s2", 1, 3)])
+@pytest.mark.parametrize("name,precision,kernel", [("t4", 0, 2), ("t4", 0, 3), ("t4", 0, 4), ("s2", 1, 1),
+                                                   ("s2", 1, 2), ("s2", 1, 3), ("s2", 1, 4), ("t2", 1, 4),
+                                                   ("c1", 1, 4)])
 def test_solve_kernels_parity(name, precision, kernel):
-    """Every block-solve kernel the autotuner may choose gives oracle parity."""
+    """Every block-solve kernel the autotuner may choose gives oracle parity
+    (kernel 4, the TMA-filled ring, is FP32 only: with FP64 the default runs)."""
     from test_gpu_local import run_case
     tol = (1e-8, 1e-5) if precision == 0 else (1e-5, 1e-4)
     run_case(name, precision=precision, tol_lam=tol[0], tol_angle=tol[1], solve_kernel=kernel)
@@ -84,10 +86,11 @@ def test_autotune_keeps_results_and_adopts_choice():
     m = MSGFEM.from_config(cfg, ang, seed=7, precision=1)
     la = m.local_spaces(cfg.n_loc)
     t = m.autotune()
-    assert t["streams"] in (4, 8, 16, 32) and t["solve_kernel"] in (1, 2, 3) and t["best_ms"] > 0
+    assert t["streams"] in (4, 8, 16, 32) and t["solve_kernel"] in (1, 2, 3, 4) and t["best_ms"] > 0
     assert t["factor_schedule"] in (0, 1) and t["factor_streams"] in (16, 32)
     assert min(x for row in t["factor_ms"] for x in row if x > 0) > 0
     assert min(x for row in t["solve_ms"] for x in row if x > 0) == pytest.approx(t["best_ms"])
+    assert any(row[3] > 0 for row in t["solve_ms"])            # the TMA ring was timed
     lb = m.local_spaces(cfg.n_loc)
     m.close()
     scale = np.abs(la).max(axis=1, keepdims=True)
