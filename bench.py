@@ -60,10 +60,10 @@ def _hbm_peak():
 METRIC = "local eigensolves/s on 1 GB300 at fixed energy-norm error: plain FP64 vs mixed+warm"
 L2_BYTES = 129 * 2 ** 20
 
-# DRAM traffic (bytes) of one FP64 layer-block factorisation (one replay of its graph) on
-# the c2 workload: ncu dram__bytes_read.sum + dram__bytes_write.sum of the factorisation
-# graph on p2 (six c2-sized subdomains, 6.21 GB), scaled by 32 / 6 subdomains.
-NCU_TRAFFIC = {"c2": 6.214e9 * 32 / 6}
+# DRAM traffic (bytes) of one FP64 layer-block factorisation (one replay of its graph):
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one factorisation graph launch on
+# p2 (six c2-sized subdomains, 6.184 GB); c2 scaled by 32 / 6 subdomains.
+NCU_TRAFFIC = {"p2": 6.184e9, "c2": 6.184e9 * 32 / 6}
 
 
 class _Range:
@@ -435,7 +435,8 @@ def run_c4(args, dev, stream, flush, rank, world):
     t0 = time.perf_counter()
     ang = torch.tensor(element_angles(cfg).reshape(-1), dtype=torch.float64, device=dev)
     m = MSGFEM.from_config(cfg, ang, seed=11, stream=stream.cuda_stream, profile=1, precision=1,
-                           streams=args.streams, factor_kernel=max(args.factor_kernel, 0))
+                           streams=args.streams, factor_kernel=max(args.factor_kernel, 0),
+                           solve_kernel=args.solve_kernel, tile_chol=args.tile_chol)
     setup_s = time.perf_counter() - t0
     lam = torch.empty((m.N, cfg.n_loc), dtype=torch.float64, device=dev)
     u = torch.empty(m.n_dof, dtype=torch.float64, device=dev)
@@ -514,7 +515,8 @@ def run_mixed(args, cfg, ang_dev, stream, dev, rank, lam_fp64, u_fp64, flush, wo
     from paper_2211_13893_gb300 import MSGFEM
     m = MSGFEM.from_config(cfg, ang_dev, seed=1234 + rank, stream=stream.cuda_stream, profile=1,
                            streams=args.streams, precision=1, direct_launch=int(args.direct_launch),
-                           factor_kernel=max(args.factor_kernel, 0))
+                           factor_kernel=max(args.factor_kernel, 0), solve_kernel=args.solve_kernel,
+                           tile_chol=args.tile_chol)
     lam = torch.empty_like(lam_fp64)
     u = torch.empty_like(u_fp64)
 
@@ -610,8 +612,9 @@ def run_aspect(args, dev, stream):
                          np.abs(lam[0]), 1.0)
         rec["mixed_eig_rel_diff_vs_fp64"] = float((np.abs(lam[1] - lam[0]) / scale).max())
         out[f"aspect_{ar}"] = rec
+    cfg = get_config(f"a{ASPECT_RATIOS[0]}")
     out["workload"] = ("c1 topology 24x4x12, ply 0.25 mm, in-plane element edge = aspect ratio x ply thickness, "
-                       "2x1 subdomains, overlap 1, oversampling 4, n_loc 12")
+                       f"2x1 subdomains, overlap {cfg.overlap}, oversampling {cfg.oversampling}, n_loc {cfg.n_loc}")
     return out
 
 
@@ -767,6 +770,12 @@ def main():
     ap.add_argument("--factor-kernel", type=int, default=-1, choices=(-1, 0, 1),
                     help="FP32 factorisation tile kernel of the mixed legs: 0 FMA, 1 tensor cores; "
                          "-1 = start from 0 and let the autotuner choose")
+    ap.add_argument("--solve-kernel", type=int, default=0, choices=(0, 1, 2, 3, 4),
+                    help="8-column block-solve kernel of the mixed legs (msgfem_options.solve_kernel); "
+                         "0 = the library default, then the autotuner's choice")
+    ap.add_argument("--tile-chol", type=int, default=0, choices=(0, 1),
+                    help="mixed legs: tile Cholesky of the FP32 factorisation in FP32 (0, the library default) "
+                         "or FP64 (1)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -228,9 +228,17 @@ typedef struct {
                            start blocks (msgfem_set_start_block) */
   int factor_kernel;    /* MSGFEM_MIXED, kernel of the FP32 layer-block factorisation's tile GEMMs:
                            0 = FP32 FMA on the CUDA cores; 1 = the tensor cores (tcgen05.mma,
-                           operands staged by TMA, each FP32 operand split into two TF32 parts:
-                           a_hi b_hi + a_hi b_lo + a_lo b_hi, FP32 accumulation in tensor memory);
-                           msgfem_autotune sets it (1 only when its factor agrees with kernel 0's) */
+                           operands staged by TMA, each FP32 operand split exactly into three TF32
+                           parts hi + mid + lo, the six products of weight down to 2^-22 summed
+                           smallest first, FP32 accumulation in tensor memory); msgfem_autotune
+                           sets it (1 only when its factor agrees with kernel 0's) */
+  int tile_chol;        /* MSGFEM_MIXED: precision of the 64 x 64 tile Cholesky and inverse inside
+                           the FP32 factorisation: 0 = FP32 (default; a wave whose FP32 tile
+                           Cholesky meets a non-positive pivot is factorised again with FP64
+                           tiles, and so are the later waves of the call), 1 = FP64.  The factor
+                           is a preconditioner either way (every solve is refined to FP64
+                           accuracy); FP32 tiles shorten the factorisation's critical path, whose
+                           steps wait on one tile Cholesky each */
 } msgfem_options;
 
 enum { MSGFEM_METHOD_MSGFEM = 0, MSGFEM_METHOD_GENEO = 1 };
@@ -293,7 +301,9 @@ typedef struct {
   int n_star_dof;       /* DoFs of Omega*_j */
   int n1, n2, n3;       /* sizes of the DoF classes B1, B2, B3 (Sec. 4.3) */
   int floating;         /* 1 if Omega*_j does not touch the clamped face */
-  int iterations;       /* eigensolver iterations used */
+  int iterations;       /* eigensolver iterations used: block Krylov steps (thick restarts
+                           included; a warm start that fell back to a cold one counts the cold
+                           run) or subspace iterations */
   int basis_size;       /* coarse basis functions contributed (n_loc [+1]) */
   double residual;      /* max relative eigen-residual over the n_loc pairs */
   int threshold_reached;   /* msgfem_coarse_assemble_threshold: 0 if every one of the n_loc

@@ -22,6 +22,8 @@
 #include <type_traits>
 #include <unordered_map>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 void launch_stencil_kb(msgfem* h, int src, int dst, int mode, double alpha);
@@ -40,6 +42,7 @@ void launch_zero_kb(msgfem* h, int which);
 void launch_rr_krylov(msgfem* h, const int* d_m, const int* d_nw);
 void launch_ritz(msgfem* h, const int* d_m, const int* d_nw, int scale, bool masked, int src, int dst);
 void launch_restart(msgfem* h, int m, int k);
+void launch_zero_h(msgfem* h);
 constexpr double KRYLOV_SIGMA = 1e-2;   // N = S + sigma T (matches KSIGMA in k_krylov.cu)
 
 msgfem_status cuda_fail(msgfem* h, cudaError_t e, const char* what, const char* file, int line) {
@@ -636,6 +639,12 @@ void apply_M_kb(msgfem* h) {
 
 }  // namespace
 
+// Graph-cache key of the factorisation of wave w: the tile-Cholesky precision
+// is a kernel argument captured in the graph.
+static uint64_t factor_graph_key(const msgfem* h, int w) {
+  return ((uint64_t)2 << 60) | ((uint64_t)w << 48) | ((uint64_t)tile_chol_fp32(h) << 44);
+}
+
 // Layer-block factors of a one-wave handle made resident for the local
 // Dirichlet solves of the Schwarz preconditioner (msgfem_schwarz_solve): the
 // element stiffness and stencils when no local stage has run since the angles
@@ -657,18 +666,26 @@ msgfem_status schwarz_factors(msgfem* h) {
     launch_element_stiffness(h);
     launch_stencil(h);
   }
-  if (h->mixed) launch_layer_blocks_f32(h);
-  else launch_layer_blocks(h);
   const WaveSched& ws = h->waves[0];
-  TRY(select_factor_kernel(h));
-  run_graph(h, (uint64_t)2 << 60, [&](cudaStream_t cs) {
-    if (h->mixed) run_schedule(ws.factf, cs, &h->gs);
-    else run_schedule(ws.fact, cs, &h->gs);
-  });
-  CK_LAUNCH();
   std::vector<int> notspd(h->N + 1);
-  CK(cudaMemcpyAsync(notspd.data(), h->d_notspd, (h->N + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if (h->mixed) launch_layer_blocks_f32(h);
+    else launch_layer_blocks(h);
+    TRY(select_factor_kernel(h));
+    run_graph(h, factor_graph_key(h, 0), [&](cudaStream_t cs) {
+      if (h->mixed) run_schedule(ws.factf, cs, &h->gs);
+      else run_schedule(ws.fact, cs, &h->gs);
+    });
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(notspd.data(), h->d_notspd, (h->N + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    bool any = false;
+    for (int j = 0; j < h->N; ++j) any = any || notspd[j] != 0;
+    if (!any || !tile_chol_fp32(h)) break;
+    // a non-positive pivot in an FP32 tile Cholesky: again with FP64 tiles
+    h->potrf_fp64 = 1;
+    CK(cudaMemsetAsync(h->d_notspd, 0, (h->N + 1) * sizeof(int), st));
+  }
   for (int j = 0; j < h->N; ++j)
     if (notspd[j]) {
       h->err = "non-positive pivot in a layer-block factorisation of subdomain " + std::to_string(j);
@@ -773,6 +790,7 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
     nwmax = std::max(nwmax, nw[j]);
   }
   CK(cudaMemcpyAsync(h->d_nwk, nw.data(), h->N * sizeof(int), cudaMemcpyHostToDevice, st));
+  launch_zero_h(h);   // the projected operator starts empty (an earlier run's restart left rows in it)
   if (h->geneo) {
     // GenEO has no particular function
     for (int j = 0; j < h->N; ++j)
@@ -869,7 +887,7 @@ msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
       // (a warm-started subdomain, or at the step cap: once it can hold the wanted pairs)
       mk[s] = (act[s] && m >= nw[s] + ((warm[s] || capped) ? 0 : KB)) ? m : 0;
       any = any || mk[s] > 0;
-      if (act[s]) h->iters[s] = j + 1;
+      if (act[s]) h->iters[s] = steps;   // block steps, thick restarts included
       if (act[s] && mk[s] == 0) stop = false;   // the cap waits for a basis that holds the wanted pairs
     }
     if (!any && m < MQ) continue;
@@ -999,6 +1017,11 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
     h->err = "unknown factor_schedule";
     return MSGFEM_EINVAL;
   }
+  if (h->opt.tile_chol < 0 || h->opt.tile_chol > 1) {
+    *out = h;
+    h->err = "unknown tile_chol";
+    return MSGFEM_EINVAL;
+  }
   h->factor_left = h->opt.factor_schedule;
   if ((h->opt.dev_alloc == nullptr) != (h->opt.dev_free == nullptr)) {
     h->opt.dev_alloc = nullptr;
@@ -1111,6 +1134,7 @@ static msgfem_status local_spaces_run(msgfem_h h, int n_loc, double* lambda_out)
   // being replaced: a failure leaves the handle needing a new local stage
   h->stage = 1;
   h->factored_wave = -1;
+  h->potrf_fp64 = 0;   // each local stage first tries FP32 tile Cholesky (mixed precision, tile_chol 0)
   h->n_loc = n_loc;
   h->p = p;
   cudaStream_t st = h->stream;
@@ -1163,12 +1187,41 @@ static msgfem_status local_spaces_run(msgfem_h h, int n_loc, double* lambda_out)
     // 2. factorisations of K and A11
     TRY(select_factor_kernel(h));
     sp = span_begin(h, TAG_FACTOR);
-    run_graph(h, ((uint64_t)2 << 60) | ((uint64_t)w << 48), [&](cudaStream_t cs) {
+    nvtxRangePushA("msgfem_factor");   // lets a kernel profiler select the factorisation (graph or launches)
+    run_graph(h, factor_graph_key(h, (int)w), [&](cudaStream_t cs) {
       if (h->mixed) run_schedule(ws.factf, cs, &h->gs);
       else run_schedule(ws.fact, cs, &h->gs);
     });
+    nvtxRangePop();
     span_end(h, sp);
     CK_LAUNCH();
+    if (tile_chol_fp32(h)) {
+      // a non-positive pivot in an FP32 tile Cholesky: the wave (and the later
+      // ones) are factorised again with FP64 tiles before any solve reads them
+      std::vector<int> bad(h->N + 1);
+      CK(cudaMemcpyAsync(bad.data(), h->d_notspd, (h->N + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      bool any = false;
+      for (int j : ws.members)
+        if (bad[j] & 1) {
+          any = true;
+          bad[j] &= ~1;
+        }
+      if (any) {
+        h->potrf_fp64 = 1;
+        CK(cudaMemcpyAsync(h->d_notspd, bad.data(), (h->N + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+        sp = span_begin(h, TAG_ASSEMBLE);
+        launch_layer_blocks_f32(h);
+        span_end(h, sp);
+        TRY(select_factor_kernel(h));
+        sp = span_begin(h, TAG_FACTOR);
+        nvtxRangePushA("msgfem_factor");
+        run_graph(h, factor_graph_key(h, (int)w), [&](cudaStream_t cs) { run_schedule(ws.factf, cs, &h->gs); });
+        nvtxRangePop();
+        span_end(h, sp);
+        CK_LAUNCH();
+      }
+    }
     h->factored_wave = (int)w;
     sp_iter = span_begin(h, TAG_ITERATE);
     bool done = false;

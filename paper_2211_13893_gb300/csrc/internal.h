@@ -233,6 +233,7 @@ struct msgfem {
   void* d_tc_maps = nullptr;         // device tensor maps of every subdomain's FP32 arrays (4 per subdomain)
   void* d_solve_maps = nullptr;      // the same arrays in 64 x 64 unswizzled boxes (TMA solve stages)
   int* d_kerr = nullptr;             // set by a TMA solve stage that did not arrive in time
+  int potrf_fp64 = 0;                // mixed: FP64 tile Cholesky after an FP32 one met a bad pivot
   int refine = 2;                    // FP64 refinement steps per FP32 solve
   std::vector<CoarsePair> pairs;
   CoarsePair* d_pairs = nullptr;
@@ -314,8 +315,8 @@ void element_types(const msgfem* h, bool& layered, std::vector<double>& types, s
 void set_dense_context(int* active, int* notspd, const SubDev* subs);
 // FP32 factorisation kernel of the next schedule runs: the tensor-core tile
 // kernel when tc_maps (device tensor maps of the subdomains' FP32 arrays) is
-// given, else the SIMT one
-void set_factor_kernel(const void* tc_maps);
+// given, else the SIMT one; potrf32: its 64 x 64 tile Cholesky in FP32 (else FP64)
+void set_factor_kernel(const void* tc_maps, int potrf32);
 // encode and upload h->d_tc_maps (k_dense.cu)
 msgfem_status tc_maps_build(msgfem* h);
 // the kernel choice of h for its next factorisation (tensor maps built on first use)
@@ -330,6 +331,8 @@ void set_solve_maps(const void* maps, int* err);
 msgfem_status solve_maps_build(msgfem* h);
 // MSGFEM_ECUDA (and the flag cleared) when a TMA solve stage reported a failure
 msgfem_status check_stage_error(msgfem* h);
+// 1 when the FP32 factorisation's tile Cholesky runs in FP32 (k_dense.cu)
+int tile_chol_fp32(const msgfem* h);
 template <typename T>
 void run_solve_mv(const SolveScheduleT<T>& s, cudaStream_t st, int src, int dst, int gather_neg, int width = PST,
                   const StreamSet* gs = nullptr, int scatter_add = 0, int variant = SOLVE_DEFAULT);

@@ -47,28 +47,30 @@ namespace {
 constexpr int KC = 16;   // K chunk of the tile GEMM
 constexpr int TILE_SMEM = 2 * 64 * 65 * (int)sizeof(double);   // dynamic shared memory per CTA
 
-// Cholesky and inverse of one 64x64 SPD tile in shared memory (FP64).  L
-// occupies the lower triangle of A; X = L^{-1} is kept transposed in the strict
-// upper triangle shifted by one column (X[i][c] at A[c][i + 1], the pad column).
-template <typename T>
-__device__ void tile_potrf_inv(const TileTaskT<T>& t, double (*A)[65], int* notspd) {
+// Cholesky and inverse of one 64x64 SPD tile in shared memory, computed in Tc
+// (FP64; FP32 on request in the mixed path).  L occupies the lower triangle of
+// A; X = L^{-1} is kept transposed in the strict upper triangle shifted by one
+// column (X[i][c] at A[c][i + 1], the pad column).
+template <typename T, typename Tc = double>
+__device__ void tile_potrf_inv(const TileTaskT<T>& t, Tc (*A)[65], int* notspd) {
   __shared__ int bad;
   const int tid = threadIdx.x;
+  const Tc zero = (Tc)0, tiny = (Tc)(sizeof(Tc) == 4 ? 1e-30 : 1e-300);
   if (tid == 0) bad = 0;
   for (int e = tid; e < 64 * 64; e += 256) {
     const int r = e >> 6, c = e & 63;
-    A[r][c] = (c <= r) ? (double)t.C[(size_t)r * t.ldc + c] : 0.0;
+    A[r][c] = (c <= r) ? (Tc)t.C[(size_t)r * t.ldc + c] : zero;
   }
-  if (tid < 64) A[tid][64] = 0.0;
+  if (tid < 64) A[tid][64] = zero;
   __syncthreads();
   for (int j = 0; j < 64; ++j) {
     if (tid == 0) {
-      double d = A[j][j];
-      if (!(d > 0.0)) { bad = 1; d = 1e-300; }
+      Tc d = A[j][j];
+      if (!(d > zero)) { bad = 1; d = tiny; }
       A[j][j] = sqrt(d);
     }
     __syncthreads();
-    const double djj = A[j][j];
+    const Tc djj = A[j][j];
     for (int i = j + 1 + tid; i < 64; i += 256) A[i][j] /= djj;
     __syncthreads();
     const int n = 63 - j;
@@ -82,9 +84,9 @@ __device__ void tile_potrf_inv(const TileTaskT<T>& t, double (*A)[65], int* nots
   for (int i = 0; i < 64; ++i) {
     for (int c = tid; c <= i; c += 256) {
       if (c == i) {
-        A[i][i + 1] = 1.0 / A[i][i];
+        A[i][i + 1] = (Tc)1 / A[i][i];
       } else {
-        double s = 0.0;
+        Tc s = zero;
         for (int m = c; m < i; ++m) s = fma(A[i][m], A[c][m + 1], s);
         A[c][i + 1] = -s / A[i][i];
       }
@@ -94,8 +96,8 @@ __device__ void tile_potrf_inv(const TileTaskT<T>& t, double (*A)[65], int* nots
   T* Li = const_cast<T*>(t.P);
   for (int e = tid; e < 64 * 64; e += 256) {
     const int r = e >> 6, c = e & 63;
-    t.C[(size_t)r * t.ldc + c] = (T)((c <= r) ? A[r][c] : 0.0);
-    Li[(size_t)r * t.ldc + c] = (T)((c <= r) ? A[c][r + 1] : 0.0);
+    t.C[(size_t)r * t.ldc + c] = (T)((c <= r) ? A[r][c] : zero);
+    Li[(size_t)r * t.ldc + c] = (T)((c <= r) ? A[c][r + 1] : zero);
   }
   if (tid == 0 && bad && notspd != nullptr) atomicExch(&notspd[t.sub >= 0 ? t.sub : 0], 1);
 }
@@ -305,14 +307,21 @@ __device__ __forceinline__ void f32_tile_gemm(const TileTaskT<float>& t, double*
   }
 }
 
+// Tile Cholesky of the FP32 factorisation in FP64 or, with potrf32, in FP32.
+__device__ __forceinline__ void f32_tile_potrf(const TileTaskT<float>& t, double* smem_d, int* notspd,
+                                               int potrf32) {
+  if (potrf32) tile_potrf_inv<float, float>(t, reinterpret_cast<float (*)[65]>(smem_d), notspd);
+  else tile_potrf_inv<float, double>(t, reinterpret_cast<double (*)[65]>(smem_d), notspd);
+}
+
 __global__ void __launch_bounds__(256)
 k_tile_task_f32(const TileTaskT<float>* __restrict__ tasks, const int* __restrict__ active,
-                int* __restrict__ notspd) {
+                int* __restrict__ notspd, int potrf32) {
   const TileTaskT<float> t = tasks[blockIdx.x];
   if (t.sub >= 0 && active != nullptr && !active[t.sub]) return;
   extern __shared__ double smem_d[];
   if (t.flags & G_POTRF) {
-    tile_potrf_inv(t, reinterpret_cast<double (*)[65]>(smem_d), notspd);
+    f32_tile_potrf(t, smem_d, notspd, potrf32);
     return;
   }
   f32_tile_gemm(t, smem_d);
@@ -324,12 +333,12 @@ k_tile_task_f32(const TileTaskT<float>* __restrict__ tasks, const int* __restric
 // their FP64 / FP32 SIMT paths.
 __global__ void __launch_bounds__(256)
 k_tile_task_tc(const TileTaskT<float>* __restrict__ tasks, const int* __restrict__ active, int* __restrict__ notspd,
-               const SubDev* __restrict__ subs, const CUtensorMap* __restrict__ maps) {
+               const SubDev* __restrict__ subs, const CUtensorMap* __restrict__ maps, int potrf32) {
   const TileTaskT<float> t = tasks[blockIdx.x];
   if (t.sub >= 0 && active != nullptr && !active[t.sub]) return;
   extern __shared__ double smem_d[];
   if (t.flags & G_POTRF) {
-    tile_potrf_inv(t, reinterpret_cast<double (*)[65]>(smem_d), notspd);
+    f32_tile_potrf(t, smem_d, notspd, potrf32);
     return;
   }
   if ((t.flags & G_POSTMUL) || !(t.flags & G_TRANSB) || t.K % tc::KCH != 0 || t.sub < 0) {
@@ -771,11 +780,12 @@ k_solve_async(const SolveTaskT<float>* __restrict__ tasks, const SubDev* __restr
 // (16 KiB, unswizzled: the ring's row-major layout) that completes on the
 // stage's mbarrier, instead of 1,024 16-byte cp.async copies from all threads.
 // The tensor maps cover the subdomain's FP32 layer-block arrays on this GPU
-// only (no multicast).  Before any copy the task's slab is checked to lie in
-// one mapped array with the array's row stride, a 16-byte-aligned column and
-// every stage inside the array; waits are bounded.  A task that fails the check
-// or a stage that does not arrive within a second sets *err and the task's
-// products are skipped.
+// only (no multicast).  Before any copy the task's slab (when it has one:
+// tasks with inner dimension 0 only gather or add their initial tile) is
+// checked to lie in one mapped array with the array's row stride, a
+// 16-byte-aligned column and every stage inside the array; waits are bounded.
+// A task that fails the check or a stage that does not arrive within a second
+// sets *err and the task's products are skipped.
 __global__ void __launch_bounds__(256, 2)
 k_solve_tma(const SolveTaskT<float>* __restrict__ tasks, const SubDev* __restrict__ subs,
             const int* __restrict__ active, int src, int dst, int gather_neg, int scatter_add,
@@ -788,7 +798,7 @@ k_solve_tma(const SolveTaskT<float>* __restrict__ tasks, const SubDev* __restric
   float* Bs = ring + ASYNC_DEPTH * ASYNC_STAGE;                       // [K / 4][ASYNC_CS]
   __shared__ __align__(8) unsigned long long full[ASYNC_DEPTH];
   __shared__ const CUtensorMap* smap;
-  __shared__ int sx, sy;
+  __shared__ int sx, sy, sbad;
   const int tid = threadIdx.x;
   const bool transA = (t.flags & S_TRANSA) != 0;
   const int nst = t.K / 64;
@@ -807,7 +817,7 @@ k_solve_tma(const SolveTaskT<float>* __restrict__ tasks, const SubDev* __restric
     for (int d = 0; d < ASYNC_DEPTH; ++d) tc::mbar_init(bar0 + 8 * d, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     int x = 0, y = 0;
-    const CUtensorMap* m = t.sub >= 0 ? tc::locate(subs[t.sub], maps, t.sub, t.A, x, y) : nullptr;
+    const CUtensorMap* m = (nst > 0 && t.sub >= 0) ? tc::locate(subs[t.sub], maps, t.sub, t.A, x, y) : nullptr;
     if (m != nullptr) {
       const SubDev& sd = subs[t.sub];
       const int which = (int)(m - maps) - 4 * t.sub;   // DKf, LKf, DAf, LAf
@@ -819,6 +829,7 @@ k_solve_tma(const SolveTaskT<float>* __restrict__ tasks, const SubDev* __restric
     smap = m;
     sx = x;
     sy = y;
+    sbad = nst > 0 && m == nullptr;
     // the factor slab does not depend on the previous step: its first stages go out first
     if (m != nullptr)
       for (int i = 0; i < ASYNC_DEPTH - 1 && i < nst; ++i) issue(i);
@@ -832,7 +843,7 @@ k_solve_tma(const SolveTaskT<float>* __restrict__ tasks, const SubDev* __restric
     }
   }
   __syncthreads();
-  bool ok = smap != nullptr;
+  bool ok = !sbad;
   const int h = transA ? tid / 16 : tid % 16;
   const int g = transA ? tid % 16 : tid / 16;
   float acc[4][KB];
@@ -959,6 +970,7 @@ static const SubDev* g_subs = nullptr;
 static const void* g_tc_maps = nullptr;   // tensor maps of the FP32 arrays: tensor-core factorisation on
 static const void* g_solve_maps = nullptr;   // tensor maps of the FP32 arrays for the TMA solve stages
 static int* g_kerr = nullptr;                // error flag of the TMA solve stages
+static int g_potrf32 = 0;                    // tile Cholesky of the FP32 factorisation in FP32
 
 void set_dense_context(int* active, int* notspd, const SubDev* subs) {
   g_active = active;
@@ -966,7 +978,10 @@ void set_dense_context(int* active, int* notspd, const SubDev* subs) {
   g_subs = subs;
 }
 
-void set_factor_kernel(const void* tc_maps) { g_tc_maps = tc_maps; }
+void set_factor_kernel(const void* tc_maps, int potrf32) {
+  g_tc_maps = tc_maps;
+  g_potrf32 = potrf32;
+}
 
 void set_solve_maps(const void* maps, int* err) {
   g_solve_maps = maps;
@@ -1009,12 +1024,15 @@ msgfem_status solve_maps_build(msgfem* h) {
   return MSGFEM_OK;
 }
 
+int tile_chol_fp32(const msgfem* h) { return h->mixed && h->opt.tile_chol == 0 && !h->potrf_fp64 ? 1 : 0; }
+
 msgfem_status select_factor_kernel(msgfem* h) {
+  const int potrf32 = tile_chol_fp32(h);
   if (h->mixed && h->factor_tc) {
     if (h->d_tc_maps == nullptr) TRY(tc_maps_build(h));
-    set_factor_kernel(h->d_tc_maps);
+    set_factor_kernel(h->d_tc_maps, potrf32);
   } else {
-    set_factor_kernel(nullptr);
+    set_factor_kernel(nullptr, potrf32);
   }
   if (h->mixed && h->solve_variant == SOLVE_TMA_RING) TRY(solve_maps_build(h));
   set_solve_maps(h->d_solve_maps, h->d_kerr);
@@ -1141,11 +1159,13 @@ void run_schedule(const ScheduleT<T>& s, cudaStream_t st, const StreamSet* gs) {
     if constexpr (std::is_same<T, float>::value) {
       if (s.k32 && g_tc_maps != nullptr) {
         k_tile_task_tc<<<step.count, 256, std::max(TILE_SMEM, tc::SMEM), stream>>>(
-            s.d_gemm + step.first, g_active, g_notspd, g_subs, static_cast<const CUtensorMap*>(g_tc_maps));
+            s.d_gemm + step.first, g_active, g_notspd, g_subs, static_cast<const CUtensorMap*>(g_tc_maps),
+            g_potrf32);
         return;
       }
       if (s.k32) {
-        k_tile_task_f32<<<step.count, 256, TILE_SMEM, stream>>>(s.d_gemm + step.first, g_active, g_notspd);
+        k_tile_task_f32<<<step.count, 256, TILE_SMEM, stream>>>(s.d_gemm + step.first, g_active, g_notspd,
+                                                                g_potrf32);
         return;
       }
     }

@@ -517,6 +517,16 @@ __global__ void k_restart_basis(const SubDev* __restrict__ subs, const int* __re
   }
 }
 
+// H = 0 for the active subdomains before a Krylov run: the Lanczos steps write
+// only the block upper Hessenberg part, and a thick restart of an earlier run
+// leaves its arrow rows below it.
+__global__ void k_zero_h(const SubDev* __restrict__ subs, const int* __restrict__ active) {
+  const int sidx = blockIdx.x;
+  if (active != nullptr && !active[sidx]) return;
+  double* H = subs[sidx].H;
+  for (int e = threadIdx.x; e < (MQ + KB) * MQ; e += blockDim.x) H[e] = 0.0;
+}
+
 // Thick restart, projected operator: H = [diag(mu) ; R_{m+1} Y_last] in the
 // first k columns, zero elsewhere (the next block's coefficients are filled by
 // Gram-Schmidt).  One block per subdomain.
@@ -628,6 +638,11 @@ void launch_rr_krylov(msgfem* h, const int* d_m, const int* d_nw) {
 void launch_ritz(msgfem* h, const int* d_m, const int* d_nw, int scale, bool masked, int src, int dst) {
   dim3 grid(std::max(1, (3 * max_nnode_k(h) + 8 * 16 - 1) / (8 * 16)), h->N);
   k_ritz<<<grid, 256, 0, h->stream>>>(h->d_sub, masked ? h->d_flags : nullptr, d_m, d_nw, scale, src, dst);
+  ++g_launch_count;
+}
+
+void launch_zero_h(msgfem* h) {
+  k_zero_h<<<h->N, 256, 0, h->stream>>>(h->d_sub, h->d_flags);
   ++g_launch_count;
 }
 

@@ -54,7 +54,7 @@ class Options(C.Structure):
                 ("streams", C.c_int), ("refine", C.c_int), ("instances", C.c_int), ("solve_kernel", C.c_int),
                 ("factor_schedule", C.c_int), ("direct_launch", C.c_int), ("wave_mb", C.c_double),
                 ("dev_alloc", C.c_void_p), ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p), ("method", C.c_int),
-                ("factor_kernel", C.c_int)]
+                ("factor_kernel", C.c_int), ("tile_chol", C.c_int)]
 
 
 class PlanInfo(C.Structure):
@@ -176,7 +176,7 @@ class MSGFEM:
                  block=0, max_iter=0, tol=0.0, seed=0, stream=None, precision=0, profile=0, solver=0, streams=0, refine=0,
                  instances=0, xyz=None, frames=None, boxes=None, wave_mb=0.0, solve_kernel=0,
                  factor_schedule=0, direct_launch=0, allocator=None, load=None, method=0, hex8=None,
-                 dirichlet=None, elem_part=None, factor_kernel=0):
+                 dirichlet=None, elem_part=None, factor_kernel=0, tile_chol=0):
         """``allocator``: optional pair (alloc(nbytes) -> device address, free(address,
         nbytes)) through which the handle takes all its device memory.  ``load``:
         optional nodal forces [n_nodes * 3] replacing the end-face traction.
@@ -184,7 +184,9 @@ class MSGFEM:
         ``hex8``: a hexahedron list [n_elems, 8] (standard local order) with
         ``xyz`` [n_nodes, 3] its node coordinates; nx, ny, nz, hx, hy, hz are then
         ignored and the structured numbering is recovered by the library.
-        ``dirichlet``: per-node clamp flags; ``elem_part``: per-element part ids."""
+        ``dirichlet``: per-node clamp flags; ``elem_part``: per-element part ids.
+        ``tile_chol``: mixed precision, tile Cholesky of the FP32 factorisation in
+        FP32 with an FP64 retry on a non-positive pivot (0) or in FP64 (1)."""
         self.lib = load_library()
         self.h = C.c_void_p()
         self._E9 = np.ascontiguousarray(E9, dtype=np.float64)
@@ -215,6 +217,7 @@ class MSGFEM:
                       solve_kernel, factor_schedule, direct_launch, wave_mb)
         opt.method = method
         opt.factor_kernel = factor_kernel
+        opt.tile_chol = tile_chol
         if allocator is not None:
             alloc, free = allocator
             # the callbacks must outlive the handle: kept on the instance

@@ -113,6 +113,30 @@ def test_deterministic_across_runs():
     assert np.array_equal(la, lb) and np.array_equal(ua, ub)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_repeated_local_stage_on_one_handle(precision):
+    """A second local stage on the same handle repeats the first bit for bit.
+    t4's clamped subdomains need a thick restart of the Krylov basis; the
+    projected operator H of the second run must not keep the first run's
+    restart rows (it starts from zero)."""
+    cfg = get_config("t4")
+    m = _msgfem().from_config(cfg, element_angles(cfg), seed=7, precision=precision)
+    la = m.local_spaces(cfg.n_loc).copy()
+    ia = [m.info(j)["iterations"] for j in range(m.N)]
+    lb = m.local_spaces(cfg.n_loc)
+    ib = [m.info(j)["iterations"] for j in range(m.N)]
+    m.close()
+    assert np.array_equal(la, lb) and ia == ib
+    assert max(ia) > 12        # a restart happened (12 block steps fill the 96-column basis)
+
+
+@pytest.mark.parametrize("name", ["t2", "s2"])
+def test_fp64_tile_cholesky_in_mixed_factorisation(name):
+    """msgfem_options.tile_chol = 1: the FP32 factorisation's 64 x 64 tile
+    Cholesky in FP64 (the default is FP32) keeps the mixed parity bars."""
+    run_case(name, precision=1, tol_lam=1e-5, tol_angle=1e-4, tile_chol=1)
+
+
 def test_threshold_selection_matches_oracle():
     """Local basis sizes from the eigenvalue threshold t = 0.05 (keep lambda < 20):
     6, 10 and 8 eigenvectors on the three subdomain pairs of t2; the coarse
