@@ -233,12 +233,13 @@ typedef struct {
                            smallest first, FP32 accumulation in tensor memory); msgfem_autotune
                            sets it (1 only when its factor agrees with kernel 0's) */
   int tile_chol;        /* MSGFEM_MIXED: precision of the 64 x 64 tile Cholesky and inverse inside
-                           the FP32 factorisation: 0 = FP32 (default; a wave whose FP32 tile
-                           Cholesky meets a non-positive pivot is factorised again with FP64
-                           tiles, and so are the later waves of the call), 1 = FP64.  The factor
-                           is a preconditioner either way (every solve is refined to FP64
-                           accuracy); FP32 tiles shorten the factorisation's critical path, whose
-                           steps wait on one tile Cholesky each */
+                           the FP32 factorisation: 0 = FP64 (default), 1 = FP32 (a wave whose FP32
+                           tile Cholesky meets a non-positive pivot is factorised again with FP64
+                           tiles, and so are the later waves of the call).  FP32 tiles shorten
+                           the factorisation's critical path (each of its steps waits on one
+                           tile Cholesky), but their inverses are less accurate: on small
+                           clamped subdomains the A11 refinement then stalls above its target
+                           and the final eigen-residuals rise to 1e-4 */
 } msgfem_options;
 
 enum { MSGFEM_METHOD_MSGFEM = 0, MSGFEM_METHOD_GENEO = 1 };

@@ -1134,7 +1134,7 @@ static msgfem_status local_spaces_run(msgfem_h h, int n_loc, double* lambda_out)
   // being replaced: a failure leaves the handle needing a new local stage
   h->stage = 1;
   h->factored_wave = -1;
-  h->potrf_fp64 = 0;   // each local stage first tries FP32 tile Cholesky (mixed precision, tile_chol 0)
+  h->potrf_fp64 = 0;   // with tile_chol 1 each local stage first tries FP32 tile Cholesky
   h->n_loc = n_loc;
   h->p = p;
   cudaStream_t st = h->stream;

@@ -14,8 +14,10 @@
 // phases (the block inverse of layer l and the factorisation of layer l + 1)
 // can fill the same launch.  FP64 arithmetic runs at ~2 DFMA/clk/SM on this
 // part, so the FP64 kernels are bound by the FP64 pipe and only need enough
-// independent tasks in flight.  The tile Cholesky is computed in FP64 in both
-// precisions (it is 1/40 of the work).
+// independent tasks in flight.  The FP32 factorisation's tile Cholesky runs
+// in FP64 by default and in FP32 on request (msgfem_options.tile_chol): in
+// FP64 one 64 x 64 tile takes ~90k DFMA on one SM, and every tile column of
+// every layer waits for one.
 #include "internal.h"
 
 #include <cooperative_groups.h>
@@ -204,7 +206,7 @@ constexpr int SKC = 32;
 // held in registers while the current one is multiplied, and a 4 x 4 register
 // tile of contiguous rows and columns so that both operands come from shared
 // memory as 16-byte vectors (2 vector loads per 16 FMA).  POTRF tasks run the
-// FP64 tile Cholesky of k_tile_task.
+// tile Cholesky of k_tile_task in FP32 or FP64 (f32_tile_potrf).
 constexpr int KC32 = 32;
 constexpr int LDS32 = 68;   // shared row stride (floats): 16-byte aligned rows
 
@@ -1024,7 +1026,7 @@ msgfem_status solve_maps_build(msgfem* h) {
   return MSGFEM_OK;
 }
 
-int tile_chol_fp32(const msgfem* h) { return h->mixed && h->opt.tile_chol == 0 && !h->potrf_fp64 ? 1 : 0; }
+int tile_chol_fp32(const msgfem* h) { return h->mixed && h->opt.tile_chol == 1 && !h->potrf_fp64 ? 1 : 0; }
 
 msgfem_status select_factor_kernel(msgfem* h) {
   const int potrf32 = tile_chol_fp32(h);

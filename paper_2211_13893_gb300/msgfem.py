@@ -186,7 +186,7 @@ class MSGFEM:
         ignored and the structured numbering is recovered by the library.
         ``dirichlet``: per-node clamp flags; ``elem_part``: per-element part ids.
         ``tile_chol``: mixed precision, tile Cholesky of the FP32 factorisation in
-        FP32 with an FP64 retry on a non-positive pivot (0) or in FP64 (1)."""
+        FP64 (0) or in FP32 with an FP64 retry on a non-positive pivot (1)."""
         self.lib = load_library()
         self.h = C.c_void_p()
         self._E9 = np.ascontiguousarray(E9, dtype=np.float64)

@@ -141,4 +141,4 @@ class WarmStart:
             if blocks is None or blocks[j] is None:
                 self.m.set_start_block(j, None)
             else:
-                self.m.set_start_block(j, blocks[j], KB, nw)
+                self.m.set_start_block(j, blocks[j], KB, min(nw, KB))
