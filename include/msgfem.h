@@ -240,6 +240,12 @@ typedef struct {
                            tile Cholesky), but their inverses are less accurate: on small
                            clamped subdomains the A11 refinement then stalls above its target
                            and the final eigen-residuals rise to 1e-4 */
+  int factor_persistent;  /* MSGFEM_MIXED: 1 runs the FP32 factorisation of a wave as one persistent
+                           cooperative launch (FMA tile kernel; every CTA takes tasks in a
+                           topological order and waits, bounded by two seconds, on the
+                           completion counter of the previous step of the task's chain)
+                           instead of the graph-captured step schedule; the factors are the
+                           same bit for bit.  0 = the step schedule.  msgfem_autotune sets it */
 } msgfem_options;
 
 enum { MSGFEM_METHOD_MSGFEM = 0, MSGFEM_METHOD_GENEO = 1 };
@@ -295,6 +301,9 @@ typedef struct {
   double fma_factor_diff;      /* the same between the FMA kernel's two schedules (two summation orders:
                                   the factor's FP32 rounding level); the tensor-core kernel is adopted
                                   only when tc_factor_diff <= 2 fma_factor_diff and it is faster */
+  int factor_persistent;       /* msgfem_options.factor_persistent chosen (mixed precision) */
+  double factor_ms_persistent[2];   /* the persistent FMA factorisation, [right-, left-looking];
+                                       -1 = not run */
 } msgfem_tuning;
 
 /* Per-subdomain diagnostics filled by msgfem_get_info. */

@@ -197,12 +197,21 @@ msgfem_status alloc_waves(msgfem* h) {
 msgfem_status upload_wave_factor(msgfem* h, WaveSched& w) {
   dfree(h, w.factf.d_gemm);
   dfree(h, w.fact.d_gemm);
+  dfree(h, w.d_pmeta);
+  dfree(h, w.d_pcount);
   w.factf.d_gemm = nullptr;
   w.fact.d_gemm = nullptr;
+  w.d_pmeta = nullptr;
+  w.d_pcount = nullptr;
   if (h->mixed) {
     TRY(dalloc(h, &w.factf.d_gemm, std::max<size_t>(w.factf.gemm.size(), 1)));
     CK(cudaMemcpy(w.factf.d_gemm, w.factf.gemm.data(), w.factf.gemm.size() * sizeof(TileTaskT<float>),
                   cudaMemcpyHostToDevice));
+    if (!w.pmeta.empty()) {
+      TRY(dalloc(h, &w.d_pmeta, w.pmeta.size()));
+      CK(cudaMemcpy(w.d_pmeta, w.pmeta.data(), w.pmeta.size() * sizeof(int4), cudaMemcpyHostToDevice));
+      TRY(dalloc(h, &w.d_pcount, (size_t)w.pcount + 1));
+    }
   } else {
     TRY(dalloc(h, &w.fact.d_gemm, std::max<size_t>(w.fact.gemm.size(), 1)));
     CK(cudaMemcpy(w.fact.d_gemm, w.fact.gemm.data(), w.fact.gemm.size() * sizeof(GemmTask), cudaMemcpyHostToDevice));
@@ -645,6 +654,17 @@ static uint64_t factor_graph_key(const msgfem* h, int w) {
   return ((uint64_t)2 << 60) | ((uint64_t)w << 48) | ((uint64_t)tile_chol_fp32(h) << 44);
 }
 
+// The layer-block factorisation of wave w: one persistent launch (mixed
+// precision, when chosen) or the captured step schedule.
+static msgfem_status run_factorisation(msgfem* h, const WaveSched& ws, int w) {
+  if (h->mixed && h->factor_persistent) return run_factor_persistent(h, ws, h->stream);
+  run_graph(h, factor_graph_key(h, w), [&](cudaStream_t cs) {
+    if (h->mixed) run_schedule(ws.factf, cs, &h->gs);
+    else run_schedule(ws.fact, cs, &h->gs);
+  });
+  return MSGFEM_OK;
+}
+
 // Layer-block factors of a one-wave handle made resident for the local
 // Dirichlet solves of the Schwarz preconditioner (msgfem_schwarz_solve): the
 // element stiffness and stencils when no local stage has run since the angles
@@ -672,10 +692,7 @@ msgfem_status schwarz_factors(msgfem* h) {
     if (h->mixed) launch_layer_blocks_f32(h);
     else launch_layer_blocks(h);
     TRY(select_factor_kernel(h));
-    run_graph(h, factor_graph_key(h, 0), [&](cudaStream_t cs) {
-      if (h->mixed) run_schedule(ws.factf, cs, &h->gs);
-      else run_schedule(ws.fact, cs, &h->gs);
-    });
+    TRY(run_factorisation(h, ws, 0));
     CK_LAUNCH();
     CK(cudaMemcpyAsync(notspd.data(), h->d_notspd, (h->N + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -1022,6 +1039,12 @@ msgfem_status msgfem_setup(const msgfem_mesh* mesh, const msgfem_plies* plies, c
     h->err = "unknown tile_chol";
     return MSGFEM_EINVAL;
   }
+  if (h->opt.factor_persistent < 0 || h->opt.factor_persistent > 1) {
+    *out = h;
+    h->err = "unknown factor_persistent";
+    return MSGFEM_EINVAL;
+  }
+  h->factor_persistent = h->opt.factor_persistent;
   h->factor_left = h->opt.factor_schedule;
   if ((h->opt.dev_alloc == nullptr) != (h->opt.dev_free == nullptr)) {
     h->opt.dev_alloc = nullptr;
@@ -1188,11 +1211,9 @@ static msgfem_status local_spaces_run(msgfem_h h, int n_loc, double* lambda_out)
     TRY(select_factor_kernel(h));
     sp = span_begin(h, TAG_FACTOR);
     nvtxRangePushA("msgfem_factor");   // lets a kernel profiler select the factorisation (graph or launches)
-    run_graph(h, factor_graph_key(h, (int)w), [&](cudaStream_t cs) {
-      if (h->mixed) run_schedule(ws.factf, cs, &h->gs);
-      else run_schedule(ws.fact, cs, &h->gs);
-    });
+    const msgfem_status fst = run_factorisation(h, ws, (int)w);
     nvtxRangePop();
+    TRY(fst);
     span_end(h, sp);
     CK_LAUNCH();
     if (tile_chol_fp32(h)) {
@@ -1216,8 +1237,9 @@ static msgfem_status local_spaces_run(msgfem_h h, int n_loc, double* lambda_out)
         TRY(select_factor_kernel(h));
         sp = span_begin(h, TAG_FACTOR);
         nvtxRangePushA("msgfem_factor");
-        run_graph(h, factor_graph_key(h, (int)w), [&](cudaStream_t cs) { run_schedule(ws.factf, cs, &h->gs); });
+        const msgfem_status rst = run_factorisation(h, ws, (int)w);
         nvtxRangePop();
+        TRY(rst);
         span_end(h, sp);
         CK_LAUNCH();
       }
@@ -1653,14 +1675,16 @@ static msgfem_status autotune_run(msgfem_h h, int reps, msgfem_tuning* out) {
   // 32 stream groups, each timed on freshly assembled layer blocks (the second
   // of two runs); in mixed precision with the FMA tile kernel and with the
   // tensor-core one
-  int best_f = h->factor_left, best_fg = h->ngroup_factor, best_k = h->factor_tc;
+  int best_f = h->factor_left, best_fg = h->ngroup_factor, best_k = h->factor_tc, best_p = 0;
   double best_fms = 1e300;
+  h->factor_persistent = 0;
   const int fgroups[2] = {16, 32};
   auto factor_once = [&](float* ms) -> msgfem_status {
     if (h->mixed) launch_layer_blocks_f32(h);
     else launch_layer_blocks(h);
     CK(cudaEventRecord(f0, st));
-    if (h->mixed) run_schedule(wl.factf, st, &h->gs);
+    if (h->mixed && h->factor_persistent) TRY(run_factor_persistent(h, wl, st));
+    else if (h->mixed) run_schedule(wl.factf, st, &h->gs);
     else run_schedule(wl.fact, st, &h->gs);
     CK(cudaEventRecord(f1, st));
     CK(cudaEventSynchronize(f1));
@@ -1669,8 +1693,10 @@ static msgfem_status autotune_run(msgfem_h h, int reps, msgfem_tuning* out) {
   };
   t.tc_factor_diff = -1.0;
   t.fma_factor_diff = -1.0;
-  for (int fv = 0; fv < 2; ++fv)
+  for (int fv = 0; fv < 2; ++fv) {
+    t.factor_ms_persistent[fv] = -1.0;
     for (int gi = 0; gi < 2; ++gi) t.factor_ms[fv][gi] = t.factor_ms_tc[fv][gi] = -1.0;
+  }
   for (int kern = 0; kern < (h->mixed ? 2 : 1); ++kern) {
     h->factor_tc = kern;
     TRY(select_factor_kernel(h));
@@ -1746,15 +1772,37 @@ static msgfem_status autotune_run(msgfem_h h, int reps, msgfem_tuning* out) {
             best_fg = fgroups[gi];
             best_k = 1;
           }
+    // the FMA kernel as one persistent launch per factorisation (one dependency
+    // group per chain); its factors are those of the step schedule, bit for bit
+    h->factor_tc = 0;
+    TRY(select_factor_kernel(h));
+    h->factor_persistent = 1;
+    for (int fv = 0; fv < 2; ++fv) {
+      h->factor_left = fv;
+      build_wave_factor_schedule(h, wl);
+      TRY(upload_wave_factor(h, wl));
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) TRY(factor_once(&ms));
+      t.factor_ms_persistent[fv] = ms;
+      if (ms < best_fms) {
+        best_fms = ms;
+        best_f = fv;
+        best_k = 0;
+        best_p = 1;
+      }
+    }
+    h->factor_persistent = 0;
   }
   CK(cudaEventDestroy(f0));
   CK(cudaEventDestroy(f1));
   h->factor_left = best_f;
   h->ngroup_factor = best_fg;
   h->factor_tc = best_k;
+  h->factor_persistent = best_p;
   t.factor_schedule = best_f;
   t.factor_streams = best_fg;
   t.factor_kernel = best_k;
+  t.factor_persistent = best_p;
   const int groups[4] = {4, 8, 16, 32};
   const int variants[4] = {SOLVE_ASYNC_RING, SOLVE_STREAM, SOLVE_STREAM_CL2, SOLVE_TMA_RING};
   if (h->mixed) TRY(solve_maps_build(h));

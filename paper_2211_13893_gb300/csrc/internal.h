@@ -146,7 +146,16 @@ struct WaveSched {
   SolveScheduleT<double> solveK8, solveA8;   // KB columns
   ScheduleT<float> factf;                    // mixed precision: FP32 factorisation
   SolveScheduleT<float> solveKf, solveAf, solveK8f, solveA8f;
+  // persistent FP32 factorisation: per task in ticket order (counter of its
+  // step, counter of the previous step or -1, tasks in that step, index in factf)
+  std::vector<int4> pmeta;
+  int pcount = 0;                            // step counters
+  int4* d_pmeta = nullptr;
+  int* d_pcount = nullptr;                   // pcount counters, then the ticket
 };
+// Ticket order and step dependencies of a factorisation schedule for the
+// persistent kernel: steps in order of their index, across all groups (setup.cpp)
+void build_persistent_meta(const ScheduleT<float>& s, std::vector<int4>& meta, int& pcount);
 
 struct CoarsePair { int s, t, x0, x1, y0, y1; };   // (i, j) node box of Omega_s cap Omega*_t
 
@@ -234,6 +243,7 @@ struct msgfem {
   void* d_solve_maps = nullptr;      // the same arrays in 64 x 64 unswizzled boxes (TMA solve stages)
   int* d_kerr = nullptr;             // set by a TMA solve stage that did not arrive in time
   int potrf_fp64 = 0;                // mixed: FP64 tile Cholesky after an FP32 one met a bad pivot
+  int factor_persistent = 0;         // mixed: FP32 factorisation as one persistent launch
   int refine = 2;                    // FP64 refinement steps per FP32 solve
   std::vector<CoarsePair> pairs;
   CoarsePair* d_pairs = nullptr;
@@ -331,8 +341,14 @@ void set_solve_maps(const void* maps, int* err);
 msgfem_status solve_maps_build(msgfem* h);
 // MSGFEM_ECUDA (and the flag cleared) when a TMA solve stage reported a failure
 msgfem_status check_stage_error(msgfem* h);
+// allocate (once) and clear the device error flag of bounded waits (k_dense.cu)
+msgfem_status kerr_ensure(msgfem* h);
 // 1 when the FP32 factorisation's tile Cholesky runs in FP32 (k_dense.cu)
 int tile_chol_fp32(const msgfem* h);
+// the persistent FP32 factorisation of wave w on stream st (cooperative launch; k_dense.cu)
+msgfem_status run_factor_persistent(msgfem* h, const WaveSched& w, cudaStream_t st);
+// stream groups of the factorisation schedules: one per chain (persistent) or ngroup_factor
+int factor_groups(const msgfem* h, const WaveSched& w);
 template <typename T>
 void run_solve_mv(const SolveScheduleT<T>& s, cudaStream_t st, int src, int dst, int gather_neg, int width = PST,
                   const StreamSet* gs = nullptr, int scatter_add = 0, int variant = SOLVE_DEFAULT);

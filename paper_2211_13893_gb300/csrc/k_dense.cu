@@ -53,7 +53,15 @@ constexpr int TILE_SMEM = 2 * 64 * 65 * (int)sizeof(double);   // dynamic shared
 // (FP64; FP32 on request in the mixed path).  L occupies the lower triangle of
 // A; X = L^{-1} is kept transposed in the strict upper triangle shifted by one
 // column (X[i][c] at A[c][i + 1], the pad column).
-template <typename T, typename Tc = double>
+// Global loads of tile operands: plain, or (L2) at the L2 only, for operands
+// that other SMs write during the same launch (the persistent factorisation).
+template <bool L2, typename T>
+__device__ __forceinline__ T ldg_op(const T* p) {
+  if constexpr (L2) return __ldcg(p);
+  else return *p;
+}
+
+template <typename T, typename Tc = double, bool L2 = false>
 __device__ void tile_potrf_inv(const TileTaskT<T>& t, Tc (*A)[65], int* notspd) {
   __shared__ int bad;
   const int tid = threadIdx.x;
@@ -61,7 +69,7 @@ __device__ void tile_potrf_inv(const TileTaskT<T>& t, Tc (*A)[65], int* notspd) 
   if (tid == 0) bad = 0;
   for (int e = tid; e < 64 * 64; e += 256) {
     const int r = e >> 6, c = e & 63;
-    A[r][c] = (c <= r) ? (Tc)t.C[(size_t)r * t.ldc + c] : zero;
+    A[r][c] = (c <= r) ? (Tc)ldg_op<L2>(t.C + (size_t)r * t.ldc + c) : zero;
   }
   if (tid < 64) A[tid][64] = zero;
   __syncthreads();
@@ -210,6 +218,7 @@ constexpr int SKC = 32;
 constexpr int KC32 = 32;
 constexpr int LDS32 = 68;   // shared row stride (floats): 16-byte aligned rows
 
+template <bool L2 = false>
 __device__ __forceinline__ void f32_tile_gemm(const TileTaskT<float>& t, double* smem_d) {
   float* smem = reinterpret_cast<float*>(smem_d);
   float (*As)[LDS32] = reinterpret_cast<float (*)[LDS32]>(smem);                  // [KC32][LDS32]: As[k][m]
@@ -223,16 +232,16 @@ __device__ __forceinline__ void f32_tile_gemm(const TileTaskT<float>& t, double*
   float4 ra[2], rb[2];
   auto load = [&](int k0) {
     const float4* a = reinterpret_cast<const float4*>(t.A + (size_t)lm * t.lda + k0 + lk);
-    ra[0] = a[0];
-    ra[1] = a[1];
+    ra[0] = ldg_op<L2>(a);
+    ra[1] = ldg_op<L2>(a + 1);
     if (transB) {
       const float4* b = reinterpret_cast<const float4*>(t.B + (size_t)lm * t.ldb + k0 + lk);
-      rb[0] = b[0];
-      rb[1] = b[1];
+      rb[0] = ldg_op<L2>(b);
+      rb[1] = ldg_op<L2>(b + 1);
     } else {
       const float4* b = reinterpret_cast<const float4*>(t.B + (size_t)(k0 + bk) * t.ldb + bn);
-      rb[0] = b[0];
-      rb[1] = b[1];
+      rb[0] = ldg_op<L2>(b);
+      rb[1] = ldg_op<L2>(b + 1);
     }
   };
   float acc[4][4];
@@ -278,7 +287,7 @@ __device__ __forceinline__ void f32_tile_gemm(const TileTaskT<float>& t, double*
       *reinterpret_cast<float4*>(&Cs[4 * ty + i][4 * tx]) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
     for (int e = tid; e < 64 * 16; e += 256) {
       const int r = e >> 4, c = (e & 15) * 4;
-      *reinterpret_cast<float4*>(&Ps[r][c]) = *reinterpret_cast<const float4*>(t.P + (size_t)r * t.ldc + c);
+      *reinterpret_cast<float4*>(&Ps[r][c]) = ldg_op<L2>(reinterpret_cast<const float4*>(t.P + (size_t)r * t.ldc + c));
     }
     __syncthreads();
 #pragma unroll
@@ -302,7 +311,7 @@ __device__ __forceinline__ void f32_tile_gemm(const TileTaskT<float>& t, double*
     float4* c = reinterpret_cast<float4*>(t.C + (size_t)(4 * ty + i) * t.ldc + 4 * tx);
     float4 v = make_float4(sgn * acc[i][0], sgn * acc[i][1], sgn * acc[i][2], sgn * acc[i][3]);
     if (t.flags & G_ACC) {
-      const float4 o = *c;
+      const float4 o = ldg_op<L2>(c);
       v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
     }
     *c = v;
@@ -310,10 +319,11 @@ __device__ __forceinline__ void f32_tile_gemm(const TileTaskT<float>& t, double*
 }
 
 // Tile Cholesky of the FP32 factorisation in FP64 or, with potrf32, in FP32.
+template <bool L2 = false>
 __device__ __forceinline__ void f32_tile_potrf(const TileTaskT<float>& t, double* smem_d, int* notspd,
                                                int potrf32) {
-  if (potrf32) tile_potrf_inv<float, float>(t, reinterpret_cast<float (*)[65]>(smem_d), notspd);
-  else tile_potrf_inv<float, double>(t, reinterpret_cast<double (*)[65]>(smem_d), notspd);
+  if (potrf32) tile_potrf_inv<float, float, L2>(t, reinterpret_cast<float (*)[65]>(smem_d), notspd);
+  else tile_potrf_inv<float, double, L2>(t, reinterpret_cast<double (*)[65]>(smem_d), notspd);
 }
 
 __global__ void __launch_bounds__(256)
@@ -327,6 +337,67 @@ k_tile_task_f32(const TileTaskT<float>* __restrict__ tasks, const int* __restric
     return;
   }
   f32_tile_gemm(t, smem_d);
+}
+
+// Persistent form of the FP32 factorisation: one cooperative launch runs the
+// whole task list of a wave.  Every CTA takes the next task by an atomic ticket
+// (tasks are numbered step by step across all chains, a topological order),
+// waits until the previous step of the task's chain has completed (thread 0
+// spins on that step's completion counter with acquire loads, bounded by two
+// seconds, and gives up when another CTA has reported an error), runs it with
+// L2-only operand loads (operands are written by other SMs during the launch),
+// and counts it complete after a device-wide fence.  All CTAs are resident
+// (cooperative launch), so a task's predecessors, which hold smaller tickets,
+// are always running or done: the waits end.  meta[t] = (counter of the task's
+// step, counter of the previous step or -1, tasks in the previous step).
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__global__ void __launch_bounds__(256)
+k_factor_persistent(const TileTaskT<float>* __restrict__ tasks, const int4* __restrict__ meta, int ntask,
+                    int* __restrict__ counters, int* __restrict__ ticket, const int* __restrict__ active,
+                    int* __restrict__ notspd, int* __restrict__ err, int potrf32) {
+  extern __shared__ double smem_d[];
+  __shared__ int s_t, s_ok;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int t = atomicAdd(ticket, 1);
+      int ok = 1;
+      if (t < ntask) {
+        const int4 m = meta[t];
+        if (m.y >= 0) {
+          const uint64_t t0 = tc::gtimer();
+          while (ld_acquire(counters + m.y) < m.z) {
+            if (*reinterpret_cast<volatile int*>(err) != 0 || tc::gtimer() - t0 > 2000000000ull) {
+              ok = 0;
+              break;
+            }
+            __nanosleep(100);
+          }
+        }
+      }
+      s_t = t;
+      s_ok = ok;
+    }
+    __syncthreads();
+    const int t = s_t;
+    if (t >= ntask) return;
+    if (!s_ok) {
+      if (threadIdx.x == 0) atomicExch(err, 2);
+      return;
+    }
+    const TileTaskT<float> task = tasks[t];
+    if (!(task.sub >= 0 && active != nullptr && !active[task.sub])) {
+      if (task.flags & G_POTRF) f32_tile_potrf<true>(task, smem_d, notspd, potrf32);
+      else f32_tile_gemm<true>(task, smem_d);
+    }
+    __threadfence();
+    __syncthreads();   // every thread's stores are fenced; the shared tiles may be reused
+    if (threadIdx.x == 0) atomicAdd(counters + meta[t].x, 1);
+  }
 }
 
 // The same task semantics with the plain GEMM tasks (A op(B)^T, no
@@ -1017,12 +1088,54 @@ msgfem_status solve_maps_build(msgfem* h) {
     }
     TRY(dev_alloc_bytes(h, &h->d_solve_maps, maps.size() * sizeof(CUtensorMap)));
     CK(cudaMemcpy(h->d_solve_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
-    void* p = nullptr;
-    TRY(dev_alloc_bytes(h, &p, sizeof(int)));
-    h->d_kerr = static_cast<int*>(p);
-    CK(cudaMemset(h->d_kerr, 0, sizeof(int)));
   }
+  TRY(kerr_ensure(h));
   set_solve_maps(h->d_solve_maps, h->d_kerr);
+  return MSGFEM_OK;
+}
+
+// the device error flag of bounded waits (TMA solve stages, persistent factorisation)
+msgfem_status kerr_ensure(msgfem* h) {
+  if (h->d_kerr != nullptr) return MSGFEM_OK;
+  void* p = nullptr;
+  TRY(dev_alloc_bytes(h, &p, sizeof(int)));
+  h->d_kerr = static_cast<int*>(p);
+  CK(cudaMemset(h->d_kerr, 0, sizeof(int)));
+  return MSGFEM_OK;
+}
+
+msgfem_status run_factor_persistent(msgfem* h, const WaveSched& w, cudaStream_t st) {
+  static int nb = 0, nsm = 0;
+  if (nb == 0) {
+    CK(cudaFuncSetAttribute(k_factor_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_SMEM));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_factor_persistent, 256, TILE_SMEM));
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (nb < 1) {
+      nb = 0;
+      h->err = "the persistent factorisation kernel does not fit on an SM";
+      return MSGFEM_ECUDA;
+    }
+  }
+  if (w.d_pmeta == nullptr || w.d_pcount == nullptr) {
+    h->err = "the persistent factorisation has no task order (schedule built without it)";
+    return MSGFEM_ECUDA;
+  }
+  TRY(kerr_ensure(h));
+  CK(cudaMemsetAsync(w.d_pcount, 0, ((size_t)w.pcount + 1) * sizeof(int), st));
+  const TileTaskT<float>* tasks = w.factf.d_gemm;
+  const int4* meta = w.d_pmeta;
+  int ntask = (int)w.pmeta.size();
+  int* counters = w.d_pcount;
+  int* ticket = w.d_pcount + w.pcount;
+  const int* active = g_active;
+  int* notspd = g_notspd;
+  int* err = h->d_kerr;
+  int potrf32 = g_potrf32;
+  void* args[] = {&tasks, &meta, &ntask, &counters, &ticket, &active, &notspd, &err, &potrf32};
+  CK(cudaLaunchCooperativeKernel((const void*)k_factor_persistent, dim3(nb * nsm), dim3(256), args, TILE_SMEM, st));
+  ++g_launch_count;
   return MSGFEM_OK;
 }
 
@@ -1047,7 +1160,8 @@ msgfem_status check_stage_error(msgfem* h) {
   CK(cudaMemcpy(&e, h->d_kerr, sizeof(int), cudaMemcpyDeviceToHost));
   if (e == 0) return MSGFEM_OK;
   CK(cudaMemset(h->d_kerr, 0, sizeof(int)));
-  h->err = "a tensor-memory-accelerator solve stage failed its slab check or did not arrive within a second";
+  h->err = e == 2 ? "a task of the persistent factorisation waited more than two seconds for its predecessors"
+                  : "a tensor-memory-accelerator solve stage failed its slab check or did not arrive within a second";
   return MSGFEM_ECUDA;
 }
 

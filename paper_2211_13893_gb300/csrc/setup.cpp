@@ -677,10 +677,36 @@ void flatten_solve(std::map<long long, std::vector<SolveTaskT<T>>>& keys, SolveS
 // NGROUP groups, each launched on its own stream, so that a group's narrow
 // steps (POTRF, TRMM, late UPDATEs) overlap the wide steps of the others
 // instead of waiting at a common launch boundary.
+void build_persistent_meta(const ScheduleT<float>& s, std::vector<int4>& meta, int& pcount) {
+  const int ng = (int)s.steps.size();
+  std::vector<int> base(ng + 1, 0);
+  size_t smax = 0;
+  for (int g = 0; g < ng; ++g) {
+    base[g + 1] = base[g] + (int)s.steps[g].size();
+    smax = std::max(smax, s.steps[g].size());
+  }
+  pcount = base[ng];
+  meta.clear();
+  meta.reserve(s.gemm.size());
+  for (size_t k = 0; k < smax; ++k)
+    for (int g = 0; g < ng; ++g) {
+      if (k >= s.steps[g].size()) continue;
+      const SchedStep& st = s.steps[g][k];
+      const int self = base[g] + (int)k;
+      const int prev = k > 0 ? self - 1 : -1;
+      const int need = k > 0 ? s.steps[g][k - 1].count : 0;
+      for (int i = st.first; i < st.first + st.count; ++i) meta.push_back(make_int4(self, prev, need, i));
+    }
+}
+
+int factor_groups(const msgfem* h, const WaveSched& w) {
+  return (h->mixed && h->factor_persistent) ? std::max(1, 2 * (int)w.members.size()) : h->ngroup_factor;
+}
+
 void build_wave_factor_schedule(msgfem* h, WaveSched& w) {
   int Tmax = 1;
   for (const auto& s : h->sub) Tmax = std::max(Tmax, std::max(s.bK, s.bA) / TILE);
-  const int ng = h->ngroup_factor;
+  const int ng = factor_groups(h, w);
   const bool left = h->factor_left != 0;
   if (h->mixed) {
     std::vector<FactorKeysT<float>> fk(ng);
@@ -693,6 +719,8 @@ void build_wave_factor_schedule(msgfem* h, WaveSched& w) {
     w.factf.steps.clear();
     w.factf.gemm.clear();
     for (int g = 0; g < ng; ++g) flatten(fk[g], w.factf, true);
+    if (h->factor_persistent) build_persistent_meta(w.factf, w.pmeta, w.pcount);
+    else w.pmeta.clear();
     return;
   }
   std::vector<FactorKeys> fk(ng);

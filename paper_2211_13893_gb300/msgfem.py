@@ -54,7 +54,7 @@ class Options(C.Structure):
                 ("streams", C.c_int), ("refine", C.c_int), ("instances", C.c_int), ("solve_kernel", C.c_int),
                 ("factor_schedule", C.c_int), ("direct_launch", C.c_int), ("wave_mb", C.c_double),
                 ("dev_alloc", C.c_void_p), ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p), ("method", C.c_int),
-                ("factor_kernel", C.c_int), ("tile_chol", C.c_int)]
+                ("factor_kernel", C.c_int), ("tile_chol", C.c_int), ("factor_persistent", C.c_int)]
 
 
 class PlanInfo(C.Structure):
@@ -72,7 +72,8 @@ class Tuning(C.Structure):
                 ("streams", C.c_int), ("solve_kernel", C.c_int), ("best_ms", C.c_double),
                 ("solve_ms", (C.c_double * 4) * 4), ("factor_kernel", C.c_int),
                 ("factor_ms_tc", (C.c_double * 2) * 2), ("tc_factor_diff", C.c_double),
-                ("fma_factor_diff", C.c_double)]
+                ("fma_factor_diff", C.c_double), ("factor_persistent", C.c_int),
+                ("factor_ms_persistent", C.c_double * 2)]
 
 
 class Profile(C.Structure):
@@ -176,7 +177,7 @@ class MSGFEM:
                  block=0, max_iter=0, tol=0.0, seed=0, stream=None, precision=0, profile=0, solver=0, streams=0, refine=0,
                  instances=0, xyz=None, frames=None, boxes=None, wave_mb=0.0, solve_kernel=0,
                  factor_schedule=0, direct_launch=0, allocator=None, load=None, method=0, hex8=None,
-                 dirichlet=None, elem_part=None, factor_kernel=0, tile_chol=0):
+                 dirichlet=None, elem_part=None, factor_kernel=0, tile_chol=0, factor_persistent=0):
         """``allocator``: optional pair (alloc(nbytes) -> device address, free(address,
         nbytes)) through which the handle takes all its device memory.  ``load``:
         optional nodal forces [n_nodes * 3] replacing the end-face traction.
@@ -186,7 +187,9 @@ class MSGFEM:
         ignored and the structured numbering is recovered by the library.
         ``dirichlet``: per-node clamp flags; ``elem_part``: per-element part ids.
         ``tile_chol``: mixed precision, tile Cholesky of the FP32 factorisation in
-        FP64 (0) or in FP32 with an FP64 retry on a non-positive pivot (1)."""
+        FP64 (0) or in FP32 with an FP64 retry on a non-positive pivot (1).
+        ``factor_persistent``: mixed precision, the FP32 factorisation as one
+        persistent launch (1) instead of the captured step schedule (0)."""
         self.lib = load_library()
         self.h = C.c_void_p()
         self._E9 = np.ascontiguousarray(E9, dtype=np.float64)
@@ -218,6 +221,7 @@ class MSGFEM:
         opt.method = method
         opt.factor_kernel = factor_kernel
         opt.tile_chol = tile_chol
+        opt.factor_persistent = factor_persistent
         if allocator is not None:
             alloc, free = allocator
             # the callbacks must outlive the handle: kept on the instance
@@ -381,7 +385,9 @@ class MSGFEM:
                 "solve_ms": [[t.solve_ms[g][v] for v in range(4)] for g in range(4)],
                 "factor_kernel": t.factor_kernel,
                 "factor_ms_tc": [[t.factor_ms_tc[f][g] for g in range(2)] for f in range(2)],
-                "tc_factor_diff": t.tc_factor_diff, "fma_factor_diff": t.fma_factor_diff}
+                "tc_factor_diff": t.tc_factor_diff, "fma_factor_diff": t.fma_factor_diff,
+                "factor_persistent": t.factor_persistent,
+                "factor_ms_persistent": [t.factor_ms_persistent[f] for f in range(2)]}
 
     def schwarz_solve(self, coarse=None, b=None, u0=None, rtol=0.0, max_iter=0, u_out=None, allow_noconv=False):
         """Two-level additive Schwarz PCG for the fine problem (include/msgfem.h

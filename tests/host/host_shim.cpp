@@ -580,6 +580,56 @@ int hc_run_factor(void* p, int coarse, unsigned seed) {
   return bad;
 }
 
+// The persistent FP32 factorisation (on: the next hc_build_wave builds its
+// ticket order, one dependency group per chain).
+int hc_set_persistent(void* p, int on) {
+  H(p)->h.factor_persistent = on;
+  return 0;
+}
+
+long long hc_persistent_tasks(void* p) {
+  HostCheck* c = H(p);
+  return c->w ? (long long)c->w->pmeta.size() : -1;
+}
+
+// Execute the built wave's persistent task order as `window` resident CTAs
+// would: tickets are taken in order, each held ticket runs once the previous
+// step of its chain has completed (the kernel's counter condition), a random
+// ready one at a time.  Returns the number of tiles found not positive
+// definite, -2 when no held ticket can run (a deadlock of the kernel), -3 when
+// a task is missing or repeated.
+int hc_run_factor_persistent(void* p, int window, unsigned seed) {
+  HostCheck* c = H(p);
+  if (c->w == nullptr || !c->h.mixed || c->w->pmeta.empty()) return -1;
+  const std::vector<int4>& meta = c->w->pmeta;
+  if (meta.size() != c->w->factf.gemm.size()) return -3;
+  std::vector<char> seen(meta.size(), 0);
+  for (const int4& m : meta) {
+    if (m.w < 0 || (size_t)m.w >= seen.size() || seen[m.w]) return -3;
+    seen[m.w] = 1;
+  }
+  std::vector<int> cnt(c->w->pcount, 0);
+  std::mt19937 rng(seed);
+  size_t next = 0;
+  std::vector<size_t> held;
+  int bad = 0;
+  while (next < meta.size() || !held.empty()) {
+    while ((int)held.size() < window && next < meta.size()) held.push_back(next++);
+    std::vector<size_t> ready;
+    for (size_t k = 0; k < held.size(); ++k) {
+      const int4& m = meta[held[k]];
+      if (m.y < 0 || cnt[m.y] >= m.z) ready.push_back(k);
+    }
+    if (ready.empty()) return -2;
+    const size_t k = ready[rng() % ready.size()];
+    const int4 m = meta[held[k]];
+    exec(c->w->factf.gemm[m.w], &bad);
+    ++cnt[m.x];
+    held.erase(held.begin() + (long)k);
+  }
+  return bad;
+}
+
 int hc_run_solve(void* p, int which, double* const* src, double* const* dst, int gather_neg, int scatter_add,
                  unsigned seed) {
   HostCheck* c = H(p);

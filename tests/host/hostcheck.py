@@ -94,6 +94,10 @@ def lib():
         L.hc_factor_task_flops.argtypes = [vp]
         L.hc_align_check.restype = C.c_longlong
         L.hc_align_check.argtypes = [vp, i, C.c_char_p, i]
+        L.hc_set_persistent.argtypes = [vp, i]
+        L.hc_persistent_tasks.restype = C.c_longlong
+        L.hc_persistent_tasks.argtypes = [vp]
+        L.hc_run_factor_persistent.argtypes = [vp, i, C.c_uint]
         _lib = L
     return _lib
 
@@ -209,6 +213,17 @@ class HostSetup:
 
     def run_factor(self, seed=0, coarse=False):
         return self.L.hc_run_factor(self.h, int(coarse), seed)
+
+    def set_persistent(self, on=True):
+        """Build the persistent factorisation's ticket order with the next build_wave."""
+        self.L.hc_set_persistent(self.h, int(on))
+
+    def persistent_tasks(self):
+        return self.L.hc_persistent_tasks(self.h)
+
+    def run_factor_persistent(self, window, seed=0):
+        """Run the persistent ticket order as `window` resident CTAs would (see host_shim.cpp)."""
+        return self.L.hc_run_factor_persistent(self.h, window, seed)
 
     def run_solve(self, which, src, dst, gather_neg=False, scatter_add=False, seed=0):
         ps, _ = self._mv(src)

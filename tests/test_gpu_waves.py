@@ -103,3 +103,36 @@ def test_left_looking_factorisation_parity(name, precision):
     from test_gpu_local import run_case
     tol = (1e-8, 1e-5) if precision == 0 else (1e-5, 1e-4)
     run_case(name, precision=precision, tol_lam=tol[0], tol_angle=tol[1], factor_schedule=1)
+
+
+@pytest.mark.parametrize("name", ["t4", "s2", "c1"])
+def test_persistent_factorisation_is_bit_identical(name):
+    """msgfem_options.factor_persistent = 1: the FP32 factorisation as one
+    cooperative launch whose CTAs take the tasks in a topological order (one
+    dependency group per chain) gives the step schedule's factors bit for bit,
+    hence the same eigenvalues and coarse solution, also over memory-bounded
+    waves (s2)."""
+    cfg = get_config(name)
+    ang = element_angles(cfg)
+    la, ua, pa = _run(cfg, ang, precision=1)
+    lb, ub, _ = _run(cfg, ang, precision=1, factor_persistent=1)
+    assert np.array_equal(la, lb) and np.array_equal(ua, ub)
+    if name == "s2":
+        lc, uc, pc = _run(cfg, ang, precision=1, factor_persistent=1, wave_mb=pa["pool_mb"] / 3.0)
+        assert pc["waves"] >= 3
+        assert np.array_equal(la, lc) and np.array_equal(ua, uc)
+
+
+def test_autotune_times_the_persistent_factorisation():
+    from paper_2211_13893_gb300 import MSGFEM
+    cfg = get_config("c1")
+    m = MSGFEM.from_config(cfg, element_angles(cfg), seed=7, precision=1)
+    la = m.local_spaces(cfg.n_loc).copy()
+    t = m.autotune()
+    lb = m.local_spaces(cfg.n_loc)
+    m.close()
+    assert all(x > 0 for x in t["factor_ms_persistent"]), t
+    assert t["factor_persistent"] in (0, 1)
+    if t["factor_persistent"]:
+        assert t["factor_kernel"] == 0
+    assert np.array_equal(la, lb) or (np.abs(la - lb) / np.abs(la).max(axis=1, keepdims=True)).max() <= 1e-6

@@ -182,6 +182,32 @@ def test_schedules_execute_to_the_block_cholesky(name, mixed, left, groups):
                 _check_solve(hs, j, matrix, M, n, src[j], dst0[j], dst[j], gather_neg, scatter_add, tol)
 
 
+@pytest.mark.parametrize("name, left, window", [("t2", False, 1), ("t2", True, 7), ("s1", False, 64),
+                                                ("c1", True, 3)])
+def test_persistent_factorisation_order(name, left, window):
+    """The persistent FP32 factorisation's ticket order (every task once, one
+    dependency group per chain) run as `window` resident CTAs that take tickets
+    in order and start a task once the previous step of its chain is complete:
+    it never deadlocks (window 1 means the order itself is topological) and
+    reproduces the block Cholesky factor and inverses."""
+    cfg = _cfg(name)
+    hs = hc.HostSetup(cfg, mixed=True)
+    assert hs.plan_waves(1e15) == 1
+    hs.set_persistent(True)
+    hs.build_wave(0, 16, 16, left)
+    members = hs.members(0)
+    assert hs.persistent_tasks() > 0
+    rng = np.random.default_rng(2)
+    mats = {}
+    for j in members:
+        for matrix in "KA":
+            mats[j, matrix] = _fill_spd(hs, j, matrix, rng)
+    assert hs.run_factor_persistent(window, seed=5) == 0
+    for (j, matrix), (M, n, upper) in mats.items():
+        _check_factor(hs, j, matrix, M, n, upper, 2e-4)
+    hs.close()
+
+
 def test_waves_schedule_only_their_members():
     """With a budget of about a third, each wave's schedules factorise exactly
     its members (the others' blocks are left alone; they share the pool)."""
