@@ -438,7 +438,8 @@ def run_c4(args, dev, stream, flush, rank, world):
     ang = torch.tensor(element_angles(cfg).reshape(-1), dtype=torch.float64, device=dev)
     m = MSGFEM.from_config(cfg, ang, seed=11, stream=stream.cuda_stream, profile=1, precision=1,
                            streams=args.streams, factor_kernel=max(args.factor_kernel, 0),
-                           solve_kernel=args.solve_kernel, tile_chol=args.tile_chol)
+                           solve_kernel=args.solve_kernel, tile_chol=args.tile_chol,
+                           factor_persistent=args.factor_persistent)
     setup_s = time.perf_counter() - t0
     lam = torch.empty((m.N, cfg.n_loc), dtype=torch.float64, device=dev)
     u = torch.empty(m.n_dof, dtype=torch.float64, device=dev)
@@ -518,7 +519,7 @@ def run_mixed(args, cfg, ang_dev, stream, dev, rank, lam_fp64, u_fp64, flush, wo
     m = MSGFEM.from_config(cfg, ang_dev, seed=1234 + rank, stream=stream.cuda_stream, profile=1,
                            streams=args.streams, precision=1, direct_launch=int(args.direct_launch),
                            factor_kernel=max(args.factor_kernel, 0), solve_kernel=args.solve_kernel,
-                           tile_chol=args.tile_chol)
+                           tile_chol=args.tile_chol, factor_persistent=args.factor_persistent)
     lam = torch.empty_like(lam_fp64)
     u = torch.empty_like(u_fp64)
 
@@ -828,6 +829,9 @@ def main():
     ap.add_argument("--solve-kernel", type=int, default=0, choices=(0, 1, 2, 3, 4),
                     help="8-column block-solve kernel of the mixed legs (msgfem_options.solve_kernel); "
                          "0 = the library default, then the autotuner's choice")
+    ap.add_argument("--factor-persistent", type=int, default=0, choices=(0, 1),
+                    help="mixed legs: the FP32 factorisation as one persistent launch (1) instead of the "
+                         "captured step schedule (0); the autotuner may change it")
     ap.add_argument("--tile-chol", type=int, default=0, choices=(0, 1),
                     help="mixed legs: tile Cholesky of the FP32 factorisation in FP64 (0, the library default) "
                          "or FP32 (1)")

@@ -154,8 +154,8 @@ struct WaveSched {
   int* d_pcount = nullptr;                   // pcount counters, then the ticket
 };
 // Ticket order and step dependencies of a factorisation schedule for the
-// persistent kernel: steps in order of their index, across all groups (setup.cpp)
-void build_persistent_meta(const ScheduleT<float>& s, std::vector<int4>& meta, int& pcount);
+// persistent kernel: a list schedule on `workers` resident CTAs (setup.cpp)
+void build_persistent_meta(const ScheduleT<float>& s, std::vector<int4>& meta, int& pcount, int workers);
 
 struct CoarsePair { int s, t, x0, x1, y0, y1; };   // (i, j) node box of Omega_s cap Omega*_t
 

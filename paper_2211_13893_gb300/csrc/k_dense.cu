@@ -346,10 +346,12 @@ k_tile_task_f32(const TileTaskT<float>* __restrict__ tasks, const int* __restric
 // spins on that step's completion counter with acquire loads, bounded by two
 // seconds, and gives up when another CTA has reported an error), runs it with
 // L2-only operand loads (operands are written by other SMs during the launch),
-// and counts it complete after a device-wide fence.  All CTAs are resident
+// and counts it complete (a device-scope fence by thread 0 after the CTA's
+// barrier, then a release increment).  All CTAs are resident
 // (cooperative launch), so a task's predecessors, which hold smaller tickets,
 // are always running or done: the waits end.  meta[t] = (counter of the task's
-// step, counter of the previous step or -1, tasks in the previous step).
+// step, counter of the previous step or -1, tasks in the previous step, index
+// of the task in the schedule's task list).
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -389,14 +391,19 @@ k_factor_persistent(const TileTaskT<float>* __restrict__ tasks, const int4* __re
       if (threadIdx.x == 0) atomicExch(err, 2);
       return;
     }
-    const TileTaskT<float> task = tasks[t];
+    const int4 mt = meta[t];
+    const TileTaskT<float> task = tasks[mt.w];
     if (!(task.sub >= 0 && active != nullptr && !active[task.sub])) {
       if (task.flags & G_POTRF) f32_tile_potrf<true>(task, smem_d, notspd, potrf32);
       else f32_tile_gemm<true>(task, smem_d);
     }
-    __threadfence();
-    __syncthreads();   // every thread's stores are fenced; the shared tiles may be reused
-    if (threadIdx.x == 0) atomicAdd(counters + meta[t].x, 1);
+    __syncthreads();   // the task's stores are done (and the shared tiles may be reused)
+    if (threadIdx.x == 0) {
+      // a device-scope fence after the barrier covers the stores of the whole CTA;
+      // then the release increment of the step's counter
+      __threadfence();
+      asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(counters + mt.x) : "memory");
+    }
   }
 }
 

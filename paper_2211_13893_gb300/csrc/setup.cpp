@@ -15,8 +15,10 @@
 // element with p; mu_{j,p} = w_{j,p} / sum_i w_{i,p}.
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <limits>
 #include <map>
+#include <queue>
 #include <tuple>
 #include <type_traits>
 #include <unordered_map>
@@ -677,26 +679,67 @@ void flatten_solve(std::map<long long, std::vector<SolveTaskT<T>>>& keys, SolveS
 // NGROUP groups, each launched on its own stream, so that a group's narrow
 // steps (POTRF, TRMM, late UPDATEs) overlap the wide steps of the others
 // instead of waiting at a common launch boundary.
-void build_persistent_meta(const ScheduleT<float>& s, std::vector<int4>& meta, int& pcount) {
+// Ticket order of the persistent factorisation: the start order of a list
+// schedule of the tasks on `workers` resident CTAs, simulated on the host with
+// estimated task times (a tile Cholesky ~12 units, a GEMM task 2 + K / 64, one
+// more with the post-multiplication), always starting a task of the chain with
+// the longest remaining path.  A task starts in the simulation only after the
+// previous step of its chain has finished, so the order is topological.
+void build_persistent_meta(const ScheduleT<float>& s, std::vector<int4>& meta, int& pcount, int workers) {
   const int ng = (int)s.steps.size();
   std::vector<int> base(ng + 1, 0);
-  size_t smax = 0;
-  for (int g = 0; g < ng; ++g) {
-    base[g + 1] = base[g] + (int)s.steps[g].size();
-    smax = std::max(smax, s.steps[g].size());
-  }
+  for (int g = 0; g < ng; ++g) base[g + 1] = base[g] + (int)s.steps[g].size();
   pcount = base[ng];
+  auto cost = [&](const TileTaskT<float>& t) {
+    if (t.flags & G_POTRF) return 12.0;
+    return 2.0 + t.K / 64.0 + ((t.flags & G_POSTMUL) ? 1.0 : 0.0);
+  };
+  // remaining path of each chain from each step (the slowest task of every later step)
+  std::vector<std::vector<double>> rem(ng);
+  for (int g = 0; g < ng; ++g) {
+    const auto& st = s.steps[g];
+    rem[g].assign(st.size() + 1, 0.0);
+    for (int k = (int)st.size() - 1; k >= 0; --k) {
+      double mx = 0.0;
+      for (int i = st[k].first; i < st[k].first + st[k].count; ++i) mx = std::max(mx, cost(s.gemm[i]));
+      rem[g][k] = rem[g][k + 1] + mx;
+    }
+  }
+  std::vector<int> cur(ng, 0), started(ng, 0), done(ng, 0);
+  std::priority_queue<std::pair<double, int>> ready;   // (remaining path, chain)
+  for (int g = 0; g < ng; ++g)
+    if (!s.steps[g].empty()) ready.push({rem[g][0], g});
+  using Ev = std::pair<double, int>;   // (finish time, chain)
+  std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> running;
   meta.clear();
   meta.reserve(s.gemm.size());
-  for (size_t k = 0; k < smax; ++k)
-    for (int g = 0; g < ng; ++g) {
-      if (k >= s.steps[g].size()) continue;
+  double now = 0.0;
+  int free_workers = std::max(1, workers);
+  while (!ready.empty() || !running.empty()) {
+    while (free_workers > 0 && !ready.empty()) {
+      const int g = ready.top().second;
+      ready.pop();
+      const int k = cur[g];
       const SchedStep& st = s.steps[g][k];
-      const int self = base[g] + (int)k;
-      const int prev = k > 0 ? self - 1 : -1;
-      const int need = k > 0 ? s.steps[g][k - 1].count : 0;
-      for (int i = st.first; i < st.first + st.count; ++i) meta.push_back(make_int4(self, prev, need, i));
+      const int i = st.first + started[g]++;
+      const int self = base[g] + k;
+      meta.push_back(make_int4(self, k > 0 ? self - 1 : -1, k > 0 ? s.steps[g][k - 1].count : 0, i));
+      running.push({now + cost(s.gemm[i]), g});
+      --free_workers;
+      if (started[g] < st.count) ready.push({rem[g][k], g});
     }
+    if (running.empty()) break;
+    const Ev e = running.top();
+    running.pop();
+    now = e.first;
+    ++free_workers;
+    const int g = e.second;
+    if (++done[g] == s.steps[g][cur[g]].count) {   // the chain's step is complete: its next step is ready
+      ++cur[g];
+      started[g] = done[g] = 0;
+      if (cur[g] < (int)s.steps[g].size()) ready.push({rem[g][cur[g]], g});
+    }
+  }
 }
 
 int factor_groups(const msgfem* h, const WaveSched& w) {
@@ -719,7 +762,7 @@ void build_wave_factor_schedule(msgfem* h, WaveSched& w) {
     w.factf.steps.clear();
     w.factf.gemm.clear();
     for (int g = 0; g < ng; ++g) flatten(fk[g], w.factf, true);
-    if (h->factor_persistent) build_persistent_meta(w.factf, w.pmeta, w.pcount);
+    if (h->factor_persistent) build_persistent_meta(w.factf, w.pmeta, w.pcount, 3 * 152);
     else w.pmeta.clear();
     return;
   }
