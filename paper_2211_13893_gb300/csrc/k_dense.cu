@@ -49,10 +49,6 @@ namespace {
 constexpr int KC = 16;   // K chunk of the tile GEMM
 constexpr int TILE_SMEM = 2 * 64 * 65 * (int)sizeof(double);   // dynamic shared memory per CTA
 
-// Cholesky and inverse of one 64x64 SPD tile in shared memory, computed in Tc
-// (FP64; FP32 on request in the mixed path).  L occupies the lower triangle of
-// A; X = L^{-1} is kept transposed in the strict upper triangle shifted by one
-// column (X[i][c] at A[c][i + 1], the pad column).
 // Global loads of tile operands: plain, or (L2) at the L2 only, for operands
 // that other SMs write during the same launch (the persistent factorisation).
 template <bool L2, typename T>
@@ -61,6 +57,14 @@ __device__ __forceinline__ T ldg_op(const T* p) {
   else return *p;
 }
 
+// Cholesky and inverse of one 64x64 SPD tile in shared memory, computed in Tc
+// (FP64; FP32 on request in the mixed path).  L occupies the lower triangle of
+// A; X = L^{-1} is kept transposed in the strict upper triangle shifted by one
+// column (X[i][c] at A[c][i + 1], the pad column).  The tile Cholesky sits on
+// the critical path of every tile column of the factorisation, so its inner
+// loops avoid index divisions (the trailing update walks the lower triangle on
+// a 16 x 16 thread grid) and the inverse has no barriers (column c of X is
+// one thread's forward substitution, which reads only L and its own column).
 template <typename T, typename Tc = double, bool L2 = false>
 __device__ void tile_potrf_inv(const TileTaskT<T>& t, Tc (*A)[65], int* notspd) {
   __shared__ int bad;
@@ -83,26 +87,23 @@ __device__ void tile_potrf_inv(const TileTaskT<T>& t, Tc (*A)[65], int* notspd) 
     const Tc djj = A[j][j];
     for (int i = j + 1 + tid; i < 64; i += 256) A[i][j] /= djj;
     __syncthreads();
-    const int n = 63 - j;
-    for (int e = tid; e < n * n; e += 256) {
-      const int ii = j + 1 + e / n, kk = j + 1 + e % n;
-      if (kk <= ii) A[ii][kk] = fma(-A[ii][j], A[kk][j], A[ii][kk]);
+    for (int ii = j + 1 + (tid >> 4); ii < 64; ii += 16) {
+      const Tc lij = A[ii][j];
+      for (int kk = j + 1 + (tid & 15); kk <= ii; kk += 16) A[ii][kk] = fma(-lij, A[kk][j], A[ii][kk]);
     }
     __syncthreads();
   }
-  // X = L^{-1} row by row: X[i][c] = -(sum_{m=c}^{i-1} L[i][m] X[m][c]) / L[i][i]
-  for (int i = 0; i < 64; ++i) {
-    for (int c = tid; c <= i; c += 256) {
-      if (c == i) {
-        A[i][i + 1] = (Tc)1 / A[i][i];
-      } else {
-        Tc s = zero;
-        for (int m = c; m < i; ++m) s = fma(A[i][m], A[c][m + 1], s);
-        A[c][i + 1] = -s / A[i][i];
-      }
+  // X = L^{-1} by columns: X[i][c] = -(sum_{m=c}^{i-1} L[i][m] X[m][c]) / L[i][i]
+  if (tid < 64) {
+    const int c = tid;
+    A[c][c + 1] = (Tc)1 / A[c][c];
+    for (int i = c + 1; i < 64; ++i) {
+      Tc s = zero;
+      for (int m = c; m < i; ++m) s = fma(A[i][m], A[c][m + 1], s);
+      A[c][i + 1] = -s / A[i][i];
     }
-    __syncthreads();
   }
+  __syncthreads();
   T* Li = const_cast<T*>(t.P);
   for (int e = tid; e < 64 * 64; e += 256) {
     const int r = e >> 6, c = e & 63;
