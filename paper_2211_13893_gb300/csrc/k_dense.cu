@@ -61,13 +61,16 @@ __device__ __forceinline__ T ldg_op(const T* p) {
 // (FP64; FP32 on request in the mixed path).  L occupies the lower triangle of
 // A; X = L^{-1} is kept transposed in the strict upper triangle shifted by one
 // column (X[i][c] at A[c][i + 1], the pad column).  The tile Cholesky sits on
-// the critical path of every tile column of the factorisation, so its inner
-// loops avoid index divisions (the trailing update walks the lower triangle on
-// a 16 x 16 thread grid) and the inverse has no barriers (column c of X is
-// one thread's forward substitution, which reads only L and its own column).
+// the critical path of every tile column of the factorisation, and FP64 runs
+// at 2 DFMA/clk/SM here, so the dependent chains are kept short: one
+// reciprocal square root per pivot (the column is scaled by it), the trailing
+// update on a 16 x 16 thread grid over the lower triangle, and the inverse by
+// forward substitution per column with four lanes per column (partial sums
+// over m mod 4, joined by two shuffles) and the pivots' reciprocals.
 template <typename T, typename Tc = double, bool L2 = false>
 __device__ void tile_potrf_inv(const TileTaskT<T>& t, Tc (*A)[65], int* notspd) {
   __shared__ int bad;
+  __shared__ Tc rdiag[64];
   const int tid = threadIdx.x;
   const Tc zero = (Tc)0, tiny = (Tc)(sizeof(Tc) == 4 ? 1e-30 : 1e-300);
   if (tid == 0) bad = 0;
@@ -81,11 +84,13 @@ __device__ void tile_potrf_inv(const TileTaskT<T>& t, Tc (*A)[65], int* notspd) 
     if (tid == 0) {
       Tc d = A[j][j];
       if (!(d > zero)) { bad = 1; d = tiny; }
-      A[j][j] = sqrt(d);
+      const Tc r = rsqrt(d);
+      A[j][j] = d * r;
+      rdiag[j] = r;
     }
     __syncthreads();
-    const Tc djj = A[j][j];
-    for (int i = j + 1 + tid; i < 64; i += 256) A[i][j] /= djj;
+    const Tc rj = rdiag[j];
+    for (int i = j + 1 + tid; i < 64; i += 256) A[i][j] *= rj;
     __syncthreads();
     for (int ii = j + 1 + (tid >> 4); ii < 64; ii += 16) {
       const Tc lij = A[ii][j];
@@ -93,14 +98,22 @@ __device__ void tile_potrf_inv(const TileTaskT<T>& t, Tc (*A)[65], int* notspd) 
     }
     __syncthreads();
   }
-  // X = L^{-1} by columns: X[i][c] = -(sum_{m=c}^{i-1} L[i][m] X[m][c]) / L[i][i]
-  if (tid < 64) {
-    const int c = tid;
-    A[c][c + 1] = (Tc)1 / A[c][c];
-    for (int i = c + 1; i < 64; ++i) {
+  // X = L^{-1} by columns: X[i][c] = -(sum_{m=c}^{i-1} L[i][m] X[m][c]) / L[i][i];
+  // lanes 4c .. 4c + 3 own column c (a warp holds 8 columns and runs the rows
+  // from its first column on, so that every lane meets the shuffles)
+  if (tid < 64) rdiag[tid] = (Tc)1 / A[tid][tid];
+  __syncthreads();
+  {
+    const int c = tid >> 2, q = tid & 3, c0 = (tid >> 5) * 8;
+    if (q == 0) A[c][c + 1] = rdiag[c];
+    __syncwarp();
+    for (int i = c0 + 1; i < 64; ++i) {
       Tc s = zero;
-      for (int m = c; m < i; ++m) s = fma(A[i][m], A[c][m + 1], s);
-      A[c][i + 1] = -s / A[i][i];
+      for (int m = c + q; m < i; m += 4) s = fma(A[i][m], A[c][m + 1], s);
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      if (q == 0 && i > c) A[c][i + 1] = -s * rdiag[i];
+      __syncwarp();
     }
   }
   __syncthreads();
