@@ -1443,6 +1443,18 @@ msgfem_status msgfem_coarse_assemble_threshold(msgfem_h h, double t, int* coarse
     h->NcPad = NcPad;
     TRY(dalloc(h, &h->d_AH, (size_t)NcPad * NcPad));
     TRY(dalloc(h, &h->d_AHinv, (size_t)NcPad * NcPad));
+    {
+      // the coarse inverse's split rows: scratch tiles and the identity strip
+      size_t tiles = 0;
+      int maxc = 1;
+      coarse_inverse_split_sizes(NcPad / TILE, COARSE_INV_SPLIT, &tiles, &maxc);
+      TRY(dalloc(h, &h->d_cscr, std::max<size_t>(tiles, 1) * TILE * TILE));
+      std::vector<double> id((size_t)TILE * maxc * TILE, 0.0);
+      for (int r = 0; r < TILE; ++r)
+        for (int c = 0; c < maxc; ++c) id[(size_t)r * maxc * TILE + (size_t)c * TILE + r] = 1.0;
+      TRY(dalloc(h, &h->d_cid, id.size()));
+      CK(cudaMemcpy(h->d_cid, id.data(), id.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
     TRY(dalloc(h, &h->d_bH, (size_t)NcPad * PST));
     TRY(dalloc(h, &h->d_cH, (size_t)NcPad * PST));
     TRY(dalloc(h, &h->d_yH, (size_t)NcPad * PST));

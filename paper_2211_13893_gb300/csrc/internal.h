@@ -254,6 +254,8 @@ struct msgfem {
   int* d_m = nullptr;
   double* d_AH = nullptr;
   double* d_AHinv = nullptr;
+  double* d_cscr = nullptr;   // scratch tiles of the coarse inverse's split rows
+  double* d_cid = nullptr;    // identity strip [I I ... I] of the coarse inverse
   double* d_bH = nullptr;
   double* d_cH = nullptr;
   double* d_yH = nullptr;
@@ -308,7 +310,12 @@ void build_factor_schedule(msgfem* h);
 void build_wave_factor_schedule(msgfem* h, WaveSched& w);
 void build_solve_schedules(msgfem* h);
 void build_wave_solve_schedules(msgfem* h, WaveSched& w);
+// the coarse schedules; with d_cscr and d_cid set, the block inverse's rows of
+// more than COARSE_INV_SPLIT tiles are split into partial sums (setup.cpp)
 void build_coarse_schedules(msgfem* h);
+constexpr int COARSE_INV_SPLIT = 8;
+// scratch tiles and identity-strip width (in tiles) the split needs for T tiles
+void coarse_inverse_split_sizes(int T, int split, size_t* scratch_tiles, int* maxc);
 // device storage of one subdomain's layer blocks, factors and solve buffers
 // (bytes, and placement at base: pointers of sub[j] set), and the grouping of
 // the subdomains into waves that fit the byte budget (h->waves, h->wave_of,

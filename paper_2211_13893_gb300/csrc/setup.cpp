@@ -494,9 +494,23 @@ template <typename T>
 using FactorKeysT = std::map<long long, std::vector<TileTaskT<T>>>;
 using FactorKeys = FactorKeysT<double>;
 
+// Split of the block inverse's long row tasks (the coarse matrix: one dense
+// block of up to ~65 tiles): a task of block row i, column k sums i - k tile
+// products on one CTA, so the row's critical path grows with the matrix size.
+// With split > 0, a task of more than `split` tiles becomes partial sums of at
+// most `split` tiles each (one step, into scratch tiles) and a final task that
+// adds them through an identity strip [I I ... I] and post-multiplies (the next
+// step).  ident is 64 x (64 * maxc) row-major with maxc = ceil((T - 1) / split).
+struct InverseSplit {
+  int split = 0;
+  void* scratch = nullptr;   // tiles of 64 x 64, contiguous
+  const void* ident = nullptr;
+  int ident_ld = 0;
+};
+
 template <typename Sc>
 void add_matrix_tasks(FactorKeysT<Sc>& fk, Sc* D, Sc* E, Sc* L, int b, int nL, int sub, int Tmax, bool left = false,
-                      long long skew = 0) {
+                      long long skew = 0, const InverseSplit& isp = InverseSplit()) {
   const int T = b / TILE;
   const long long per_layer = 3LL * Tmax + 1;
   auto tileD = [&](int l, int i, int j) { return D + (size_t)l * b * b + (size_t)i * TILE * b + (size_t)j * TILE; };
@@ -552,11 +566,33 @@ void add_matrix_tasks(FactorKeysT<Sc>& fk, Sc* D, Sc* E, Sc* L, int b, int nL, i
     }
     // block inverse rows, deferred into the steps of the next layer
     const long long next = (l + 1) * per_layer + skew;
-    for (int i = 1; i < T; ++i) {
+    for (int i = 1; i < T && isp.split <= 0; ++i) {
       auto& tr = fk[next + (i - 1)];
       for (int k = 0; k < i; ++k)
         tr.push_back({tileD(l, i, k), tileL(l, k, k), tileL(l, i, k), tileL(l, i, i), b, b, b, (i - k) * TILE,
                       G_POSTMUL | G_NEG, sub});
+    }
+    for (int i = 1; i < T && isp.split > 0; ++i) {
+      auto& part = fk[next + 2 * (i - 1)];
+      auto& fin = fk[next + 2 * (i - 1) + 1];
+      size_t off = 0;   // scratch tiles of row i
+      for (int k = 0; k < i; ++k) {
+        if (i - k <= isp.split) {
+          fin.push_back({tileD(l, i, k), tileL(l, k, k), tileL(l, i, k), tileL(l, i, i), b, b, b, (i - k) * TILE,
+                         G_POSTMUL | G_NEG, sub});
+          continue;
+        }
+        const int nc = (i - k + isp.split - 1) / isp.split;
+        Sc* s0 = static_cast<Sc*>(isp.scratch) + off * TILE * TILE;
+        for (int c = 0; c < nc; ++c) {
+          const int m0 = k + c * isp.split, nm = std::min(isp.split, i - m0);
+          part.push_back({tileD(l, i, m0), tileL(l, m0, k), s0 + (size_t)c * TILE * TILE, nullptr, b, b, TILE,
+                          nm * TILE, 0, sub});
+        }
+        fin.push_back({static_cast<const Sc*>(isp.ident), s0, tileL(l, i, k), tileL(l, i, i), isp.ident_ld, TILE, b,
+                       nc * TILE, G_POSTMUL | G_NEG, sub});
+        off += nc;
+      }
     }
   }
 }
@@ -839,7 +875,17 @@ void build_solve_schedules(msgfem* h) {
 void build_coarse_schedules(msgfem* h) {
   FactorKeys fk;
   const int b = h->NcPad;
-  add_matrix_tasks<double>(fk, h->d_AH, nullptr, h->d_AHinv, b, 1, h->N, b / TILE);
+  InverseSplit isp;
+  if (h->d_cscr != nullptr && h->d_cid != nullptr) {
+    size_t tiles = 0;
+    int maxc = 1;
+    coarse_inverse_split_sizes(b / TILE, COARSE_INV_SPLIT, &tiles, &maxc);
+    isp.split = COARSE_INV_SPLIT;
+    isp.scratch = h->d_cscr;
+    isp.ident = h->d_cid;
+    isp.ident_ld = maxc * TILE;
+  }
+  add_matrix_tasks<double>(fk, h->d_AH, nullptr, h->d_AHinv, b, 1, h->N, b / TILE, false, 0, isp);
   flatten(fk, h->cfact);
   const int T = b / TILE;
   std::map<long long, std::vector<SolveTask>> keys;
@@ -954,4 +1000,17 @@ extern "C" msgfem_status msgfem_plan(const msgfem_mesh* mesh, const msgfem_parti
   info->waves = (int)h.waves.size();
   info->pool_mb = (double)h.pool_bytes / mib;
   return MSGFEM_OK;
+}
+
+// Scratch tiles and identity-strip width (tiles) of the split coarse inverse.
+void coarse_inverse_split_sizes(int T, int split, size_t* scratch_tiles, int* maxc) {
+  size_t most = 0;
+  for (int i = 1; i < T; ++i) {
+    size_t tiles = 0;
+    for (int k = 0; k < i; ++k)
+      if (i - k > split) tiles += (size_t)((i - k + split - 1) / split);
+    most = std::max(most, tiles);
+  }
+  *scratch_tiles = most;
+  *maxc = std::max(1, (T - 1 + split - 1) / split);
 }

@@ -34,6 +34,7 @@ struct HostCheck {
   WaveSched* w = nullptr;
   // coarse schedules
   int coarse = 0;
+  std::vector<double> cscr, cid;   // scratch and identity strip of the split coarse inverse
 };
 
 struct Iv {
@@ -511,6 +512,16 @@ int hc_build_coarse(void* p, int ncpad, double* AH, double* AHinv, double* bH, d
   if (ncpad <= 0 || ncpad % TILE) return -1;
   h->NcPad = ncpad;
   h->d_AH = AH; h->d_AHinv = AHinv; h->d_bH = bH; h->d_rH = rH; h->d_yH = yH; h->d_cH = cH;
+  // the split inverse rows, as the library allocates them
+  size_t tiles = 0;
+  int maxc = 1;
+  coarse_inverse_split_sizes(ncpad / TILE, COARSE_INV_SPLIT, &tiles, &maxc);
+  c->cscr.assign(std::max<size_t>(tiles, 1) * TILE * TILE, 0.0);
+  c->cid.assign((size_t)TILE * maxc * TILE, 0.0);
+  for (int r = 0; r < TILE; ++r)
+    for (int q = 0; q < maxc; ++q) c->cid[(size_t)r * maxc * TILE + (size_t)q * TILE + r] = 1.0;
+  h->d_cscr = c->cscr.data();
+  h->d_cid = c->cid.data();
   build_coarse_schedules(h);
   c->coarse = 1;
   return 0;

@@ -242,13 +242,17 @@ def test_waves_schedule_only_their_members():
                 _check_solve(hs, j, "K", M, n, src[j], np.zeros_like(dst2[j]), dst2[j], False, False, 1e-11)
 
 
-def test_coarse_schedules():
+@pytest.mark.parametrize("tiles", [4, 20])
+def test_coarse_schedules(tiles):
     """The coarse Galerkin matrix: one dense block of NcPad rows factorised by the
-    same tile tasks and solved by one forward and one backward sweep."""
+    same tile tasks and solved by one forward and one backward sweep; with 20
+    tiles the block inverse's long rows (more than 8 tile products) run as
+    partial sums into scratch tiles plus a final task through the identity
+    strip."""
     cfg = _cfg("t2")
     hs = hc.HostSetup(cfg)
     rng = np.random.default_rng(3)
-    b = 4 * hc.TILE
+    b = tiles * hc.TILE
     G = rng.standard_normal((b, b)) / np.sqrt(b)
     A = G @ G.T + 0.5 * np.eye(b)
     AH = A.copy()
@@ -262,6 +266,7 @@ def test_coarse_schedules():
     assert hs.run_factor(seed=5, coarse=True) == 0
     L = np.linalg.cholesky(A)
     np.testing.assert_allclose(np.tril(AH), L, atol=1e-12 * np.abs(L).max(), rtol=0)
+    np.testing.assert_allclose(np.tril(AHinv), np.linalg.inv(L), rtol=0, atol=1e-11 * np.abs(np.linalg.inv(L)).max())
     hs.run_solve(hc.SC_COARSE_SOLVE, None, None, seed=5)
     np.testing.assert_allclose(cH, np.linalg.solve(A, bH), rtol=0, atol=1e-11 * np.abs(cH).max())
 
