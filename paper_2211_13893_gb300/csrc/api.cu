@@ -638,6 +638,13 @@ void cholqr2_kb(msgfem* h, int j, bool have_nw) {
 // GenEO: M = K^{-1} B on all free DoFs of Omega_j (no restriction, no extension).
 void apply_M_kb(msgfem* h) {
   timed_stencil_kb(h, MV_WB, MV_ZB, 3, 1.0);
+  // floating subdomains: the load of the pinned K solve is made orthogonal to
+  // the rigid modes, f -= (B R)(R^T f) with R B-orthonormal (R^T f = 0 after).
+  // For an iterate B-orthogonal to R this only removes rounding, but the
+  // pinned solve amplifies any rigid content of its load, and on restarted
+  // runs that content made the Ritz residuals of converged pairs grow again
+  timed_gram_kb(h, MV_R, PST, 6, MV_ZB, 1);
+  timed_update_kb(h, MV_BR, PST, 6, MV_ZB, 1);
   solve_K_kb(h);
   if (!h->geneo) {
     launch_mask_kb(h, MV_WB, 1 << 2);
