@@ -30,7 +30,9 @@
 // Tile task: C(64x64) = [C +] sign * [P *] A(64 x K) * op(B), or with
 // G_POTRF the Cholesky factor and inverse of the SPD tile C (in place) with the
 // inverse written to P.
-enum { G_TRANSB = 1, G_ACC = 2, G_NEG = 4, G_POSTMUL = 8, G_POTRF = 16 };
+// G_TRIB: B is a lower-triangular 64 x 64 tile (a diagonal block inverse) and
+// K = 64; the FP64 tile kernel skips its all-zero 16 x 16 blocks
+enum { G_TRANSB = 1, G_ACC = 2, G_NEG = 4, G_POSTMUL = 8, G_POTRF = 16, G_TRIB = 32 };
 template <typename T>
 struct TileTaskT {
   const T* A;

@@ -126,6 +126,24 @@ __device__ void tile_potrf_inv(const TileTaskT<T>& t, Tc (*A)[65], int* notspd) 
   if (tid == 0 && bad && notspd != nullptr) atomicExch(&notspd[t.sub >= 0 ? t.sub : 0], 1);
 }
 
+// The products of one K chunk: 4 x 4 outputs per thread, output column groups
+// j >= JLO (the others meet only zeros of a triangular B in this chunk).
+template <typename T, int JLO>
+__device__ __forceinline__ void tile_chunk(T (*As)[65], T (*Bs)[65], T (&acc)[4][4], int tx, int ty) {
+#pragma unroll
+  for (int kk = 0; kk < KC; ++kk) {
+    T a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+    for (int j = JLO; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = JLO; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+  }
+}
+
 // One tile task per CTA: a 64x64 GEMM tile (4x4 outputs per thread, operands
 // staged through shared memory in K chunks of 16) or a tile POTRF.
 template <typename T>
@@ -167,18 +185,13 @@ k_tile_task(const TileTaskT<T>* __restrict__ tasks, const int* __restrict__ acti
       for (int i = 0; i < 4; ++i) Bs[k][n + i] = b[i];
     }
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < KC; ++kk) {
-      T a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-    }
+    // triangular B (G_TRIB): in the chunk at k0 the output columns below k0,
+    // tx + 16 j with j < k0 / 16, meet only zeros of B; those products are skipped
+    const int jlo = (t.flags & G_TRIB) ? (k0 >> 4) : 0;
+    if (jlo == 0) tile_chunk<T, 0>(As, Bs, acc, tx, ty);
+    else if (jlo == 1) tile_chunk<T, 1>(As, Bs, acc, tx, ty);
+    else if (jlo == 2) tile_chunk<T, 2>(As, Bs, acc, tx, ty);
+    else tile_chunk<T, 3>(As, Bs, acc, tx, ty);
     __syncthreads();
   }
   if (t.flags & G_POSTMUL) {

@@ -539,20 +539,20 @@ void add_matrix_tasks(FactorKeysT<Sc>& fk, Sc* D, Sc* E, Sc* L, int b, int nL, i
       fk[base + 2 + 3 * k].push_back({nullptr, nullptr, tileD(l, k, k), tileL(l, k, k), 0, 0, b, 0, G_POTRF, sub});
       auto& trmm = fk[base + 3 + 3 * k];
       for (int i = k + 1; i < T; ++i)
-        trmm.push_back({tileD(l, i, k), tileL(l, k, k), tileD(l, i, k), nullptr, b, b, b, TILE, G_TRANSB, sub});
+        trmm.push_back({tileD(l, i, k), tileL(l, k, k), tileD(l, i, k), nullptr, b, b, b, TILE, G_TRANSB | G_TRIB, sub});
       if (l + 1 < nL)
         for (int i = 0; i < T; ++i)
-          trmm.push_back({tileE(l, i, k), tileL(l, k, k), tileE(l, i, k), nullptr, b, b, b, TILE, G_TRANSB, sub});
+          trmm.push_back({tileE(l, i, k), tileL(l, k, k), tileE(l, i, k), nullptr, b, b, b, TILE, G_TRANSB | G_TRIB, sub});
     }
     for (int k = 0; k < T && !left; ++k) {
       // right-looking: POTRF, TRMM, then the update of the whole trailing matrix
       fk[base + 1 + 3 * k].push_back({nullptr, nullptr, tileD(l, k, k), tileL(l, k, k), 0, 0, b, 0, G_POTRF, sub});
       auto& trmm = fk[base + 2 + 3 * k];
       for (int i = k + 1; i < T; ++i)
-        trmm.push_back({tileD(l, i, k), tileL(l, k, k), tileD(l, i, k), nullptr, b, b, b, TILE, G_TRANSB, sub});
+        trmm.push_back({tileD(l, i, k), tileL(l, k, k), tileD(l, i, k), nullptr, b, b, b, TILE, G_TRANSB | G_TRIB, sub});
       if (l + 1 < nL)
         for (int i = 0; i < T; ++i)
-          trmm.push_back({tileE(l, i, k), tileL(l, k, k), tileE(l, i, k), nullptr, b, b, b, TILE, G_TRANSB, sub});
+          trmm.push_back({tileE(l, i, k), tileL(l, k, k), tileE(l, i, k), nullptr, b, b, b, TILE, G_TRANSB | G_TRIB, sub});
       auto& upd = fk[base + 3 + 3 * k];
       for (int j = k + 1; j < T; ++j) {
         for (int i = j; i < T; ++i)
