@@ -360,13 +360,15 @@ def test_algorithmic_flops_do_not_exceed_the_executed_ones():
     layers, n the unpadded layer size) by the measured time.  The tile tasks of
     the schedules execute more: the explicit inverses of the diagonal factors
     (n^3/3 per layer), 64-row padding and whole diagonal tiles.  On the full c2
-    beam they execute 1.21 times the count with the inverses and 1.38
-    times the algorithmic one, the same for both schedules and both
-    precisions, so the reported fraction of peak understates the rate of the
-    tile kernel."""
+    beam the FP32 tasks execute 1.21 times the count with the inverses and
+    1.38 times the algorithmic one, the same for both schedules; the FP64
+    kernel skips the zero blocks of the triangular operand of its TRMM tasks
+    (10 of 16 blocks computed), 1.33 times the algorithmic count.  Either way
+    the reported fraction of peak understates the rate of the tile kernel."""
     cfg = _cfg("c2")
-    ratios, ratios_inv = set(), set()
+    found = {}
     for mixed in (False, True):
+        ratios, ratios_inv = set(), set()
         hs = hc.HostSetup(cfg, mixed=mixed)
         assert hs.plan_waves(1e18) == 1
         alg = alg_inv = 0.0
@@ -379,10 +381,12 @@ def test_algorithmic_flops_do_not_exceed_the_executed_ones():
             hs.build_wave_virtual(0, 16, 16, left)
             ratios.add(round(hs.factor_task_flops() / alg, 6))
             ratios_inv.add(round(hs.factor_task_flops() / alg_inv, 6))
-    assert len(ratios) == 1 and len(ratios_inv) == 1
-    r, ri = ratios.pop(), ratios_inv.pop()
-    assert 1.15 < ri < 1.25, ri
-    assert 1.25 < r < 1.40, r
+        assert len(ratios) == 1 and len(ratios_inv) == 1
+        found[mixed] = (ratios.pop(), ratios_inv.pop())
+    r32, ri32 = found[True]
+    r64, ri64 = found[False]
+    assert 1.15 < ri32 < 1.25 and 1.25 < r32 < 1.40, found
+    assert 1.0 < r64 < r32 and 1.30 < r64 < 1.36, found
 
 
 @pytest.mark.parametrize("name", ["c2", "c4"])
