@@ -31,8 +31,10 @@
 // G_POTRF the Cholesky factor and inverse of the SPD tile C (in place) with the
 // inverse written to P.
 // G_TRIB: B is a lower-triangular 64 x 64 tile (a diagonal block inverse) and
-// K = 64; the FP64 tile kernel skips its all-zero 16 x 16 blocks
-enum { G_TRANSB = 1, G_ACC = 2, G_NEG = 4, G_POSTMUL = 8, G_POTRF = 16, G_TRIB = 32 };
+// K = 64; the FP64 tile kernel skips its all-zero 16 x 16 blocks.  G_SYMC: C is
+// a diagonal tile whose upper triangle is never read (a Cholesky update); the
+// FP64 tile kernel forms only its 16 x 16 blocks on or below the diagonal
+enum { G_TRANSB = 1, G_ACC = 2, G_NEG = 4, G_POSTMUL = 8, G_POTRF = 16, G_TRIB = 32, G_SYMC = 64 };
 template <typename T>
 struct TileTaskT {
   const T* A;

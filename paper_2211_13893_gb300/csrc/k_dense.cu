@@ -126,9 +126,10 @@ __device__ void tile_potrf_inv(const TileTaskT<T>& t, Tc (*A)[65], int* notspd) 
   if (tid == 0 && bad && notspd != nullptr) atomicExch(&notspd[t.sub >= 0 ? t.sub : 0], 1);
 }
 
-// The products of one K chunk: 4 x 4 outputs per thread, output column groups
-// j >= JLO (the others meet only zeros of a triangular B in this chunk).
-template <typename T, int JLO>
+// The products of one K chunk: 4 x 4 outputs per thread (rows ty + 16 i,
+// columns tx + 16 j), output column groups j >= JLO (the others meet only
+// zeros of a triangular B in this chunk); with SYM only the blocks j <= i.
+template <typename T, int JLO, bool SYM>
 __device__ __forceinline__ void tile_chunk(T (*As)[65], T (*Bs)[65], T (&acc)[4][4], int tx, int ty) {
 #pragma unroll
   for (int kk = 0; kk < KC; ++kk) {
@@ -140,7 +141,8 @@ __device__ __forceinline__ void tile_chunk(T (*As)[65], T (*Bs)[65], T (&acc)[4]
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = JLO; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      for (int j = JLO; j < 4; ++j)
+        if (!SYM || j <= i) acc[i][j] = fma(a[i], b[j], acc[i][j]);
   }
 }
 
@@ -187,11 +189,13 @@ k_tile_task(const TileTaskT<T>* __restrict__ tasks, const int* __restrict__ acti
     __syncthreads();
     // triangular B (G_TRIB): in the chunk at k0 the output columns below k0,
     // tx + 16 j with j < k0 / 16, meet only zeros of B; those products are skipped
+    // and a diagonal output tile (G_SYMC) forms only its blocks on or below the diagonal
     const int jlo = (t.flags & G_TRIB) ? (k0 >> 4) : 0;
-    if (jlo == 0) tile_chunk<T, 0>(As, Bs, acc, tx, ty);
-    else if (jlo == 1) tile_chunk<T, 1>(As, Bs, acc, tx, ty);
-    else if (jlo == 2) tile_chunk<T, 2>(As, Bs, acc, tx, ty);
-    else tile_chunk<T, 3>(As, Bs, acc, tx, ty);
+    if (t.flags & G_SYMC) tile_chunk<T, 0, true>(As, Bs, acc, tx, ty);
+    else if (jlo == 0) tile_chunk<T, 0, false>(As, Bs, acc, tx, ty);
+    else if (jlo == 1) tile_chunk<T, 1, false>(As, Bs, acc, tx, ty);
+    else if (jlo == 2) tile_chunk<T, 2, false>(As, Bs, acc, tx, ty);
+    else tile_chunk<T, 3, false>(As, Bs, acc, tx, ty);
     __syncthreads();
   }
   if (t.flags & G_POSTMUL) {

@@ -522,7 +522,7 @@ void add_matrix_tasks(FactorKeysT<Sc>& fk, Sc* D, Sc* E, Sc* L, int b, int nL, i
       for (int i = 0; i < T; ++i)
         for (int j = 0; j <= i; ++j)
           fk[base].push_back({tileE(l - 1, i, 0), tileE(l - 1, j, 0), tileD(l, i, j), nullptr, b, b, b, b,
-                              G_TRANSB | G_ACC | G_NEG, sub});
+                              G_TRANSB | G_ACC | G_NEG | (i == j ? G_SYMC : 0), sub});
     for (int k = 0; k < T && left; ++k) {
       // left-looking: update of tile column k with all finished columns 0..k-1
       // (one GEMM of inner dimension 64 k per tile instead of k GEMMs of 64)
@@ -530,7 +530,7 @@ void add_matrix_tasks(FactorKeysT<Sc>& fk, Sc* D, Sc* E, Sc* L, int b, int nL, i
       if (k > 0) {
         for (int i = k; i < T; ++i)
           upd.push_back({tileD(l, i, 0), tileD(l, k, 0), tileD(l, i, k), nullptr, b, b, b, k * TILE,
-                         G_TRANSB | G_ACC | G_NEG, sub});
+                         G_TRANSB | G_ACC | G_NEG | (i == k ? G_SYMC : 0), sub});
         if (l + 1 < nL)
           for (int i = 0; i < T; ++i)
             upd.push_back({tileE(l, i, 0), tileD(l, k, 0), tileE(l, i, k), nullptr, b, b, b, k * TILE,
@@ -557,7 +557,7 @@ void add_matrix_tasks(FactorKeysT<Sc>& fk, Sc* D, Sc* E, Sc* L, int b, int nL, i
       for (int j = k + 1; j < T; ++j) {
         for (int i = j; i < T; ++i)
           upd.push_back({tileD(l, i, k), tileD(l, j, k), tileD(l, i, j), nullptr, b, b, b, TILE,
-                         G_TRANSB | G_ACC | G_NEG, sub});
+                         G_TRANSB | G_ACC | G_NEG | (i == j ? G_SYMC : 0), sub});
         if (l + 1 < nL)
           for (int i = 0; i < T; ++i)
             upd.push_back({tileE(l, i, k), tileD(l, j, k), tileE(l, i, j), nullptr, b, b, b, TILE,

@@ -363,8 +363,9 @@ def test_algorithmic_flops_do_not_exceed_the_executed_ones():
     beam the FP32 tasks execute 1.21 times the count with the inverses and
     1.38 times the algorithmic one, the same for both schedules; the FP64
     kernel skips the zero blocks of the triangular operand of its TRMM tasks
-    (10 of 16 blocks computed), 1.33 times the algorithmic count.  Either way
-    the reported fraction of peak understates the rate of the tile kernel."""
+    and the blocks above the diagonal of diagonal output tiles (10 of 16
+    blocks computed), 1.29 times the algorithmic count.  Either way the
+    reported fraction of peak understates the rate of the tile kernel."""
     cfg = _cfg("c2")
     found = {}
     for mixed in (False, True):
@@ -386,7 +387,7 @@ def test_algorithmic_flops_do_not_exceed_the_executed_ones():
     r32, ri32 = found[True]
     r64, ri64 = found[False]
     assert 1.15 < ri32 < 1.25 and 1.25 < r32 < 1.40, found
-    assert 1.0 < r64 < r32 and 1.30 < r64 < 1.36, found
+    assert 1.0 < r64 < r32 and 1.26 < r64 < 1.31, found
 
 
 @pytest.mark.parametrize("name", ["c2", "c4"])
