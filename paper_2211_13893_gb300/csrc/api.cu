@@ -454,17 +454,17 @@ double factor_flops(const msgfem* h, bool with_inverse = false) {
 // whole diagonal tiles and the inverses included): a POTRF tile task forms the
 // 64 x 64 Cholesky factor and its inverse, a GEMM tile task 2 64^2 K, plus
 // 2 64^3 for the post-multiplication by a 64 x 64 tile; the FP64 kernel runs
-// 10 of the 16 16 x 16 blocks of a triangular-B task (G_TRIB) or of a diagonal
-// output tile (G_SYMC)
+// 10 of the 16 16 x 16 blocks of a triangular-B task (G_TRIB), of a diagonal
+// output tile (G_SYMC) and of the post-multiplication by a triangular tile
 template <typename T>
 double schedule_flops(const ScheduleT<T>& sc) {
+  const double part = std::is_same<T, double>::value ? 10.0 / 16.0 : 1.0;
   double f = 0.0;
   for (const auto& t : sc.gemm) {
     if (t.flags & G_POTRF) f += 2.0 * (64.0 * 64.0 * 64.0 / 3.0 + 64.0 * 64.0 * 64.0 / 6.0);
     else
-      f += 2.0 * 64.0 * 64.0 * t.K *
-               ((std::is_same<T, double>::value && (t.flags & (G_TRIB | G_SYMC))) ? 10.0 / 16.0 : 1.0) +
-           ((t.flags & G_POSTMUL) ? 2.0 * 64.0 * 64.0 * 64.0 : 0.0);
+      f += 2.0 * 64.0 * 64.0 * t.K * ((t.flags & (G_TRIB | G_SYMC)) ? part : 1.0) +
+           ((t.flags & G_POSTMUL) ? 2.0 * 64.0 * 64.0 * 64.0 * part : 0.0);
   }
   return f;
 }

@@ -199,7 +199,9 @@ k_tile_task(const TileTaskT<T>* __restrict__ tasks, const int* __restrict__ acti
     __syncthreads();
   }
   if (t.flags & G_POSTMUL) {
-    // C = P * (A op(B)): product and P both staged in shared memory
+    // C = P * (A op(B)): product and P both staged in shared memory.  P is a
+    // diagonal block inverse (lower triangular): rows 16 i .. 16 i + 15 meet
+    // only zeros of P beyond column 16 i + 15, so chunk c of m feeds row groups i >= c
     T (*Cs)[65] = reinterpret_cast<T (*)[65]>(smem);
     T (*Ps)[65] = reinterpret_cast<T (*)[65]>(smem + 64 * 65);
 #pragma unroll
@@ -212,17 +214,19 @@ k_tile_task(const TileTaskT<T>* __restrict__ tasks, const int* __restrict__ acti
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
-    for (int m = 0; m < 64; ++m) {
-      T b[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Cs[m][tx + 16 * j];
+    for (int c = 0; c < 4; ++c)
+      for (int m = 16 * c; m < 16 * c + 16; ++m) {
+        T b[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const T pv = Ps[ty + 16 * i][m];
+        for (int j = 0; j < 4; ++j) b[j] = Cs[m][tx + 16 * j];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(pv, b[j], acc[i][j]);
+        for (int i = c; i < 4; ++i) {
+          const T pv = Ps[ty + 16 * i][m];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(pv, b[j], acc[i][j]);
+        }
       }
-    }
   }
   const T sgn = (t.flags & G_NEG) ? (T)-1 : (T)1;
 #pragma unroll

@@ -487,7 +487,7 @@ double hc_factor_task_flops(void* p) {
     if (flags & G_POTRF) f += 2.0 * (64.0 * 64.0 * 64.0 / 3.0 + 64.0 * 64.0 * 64.0 / 6.0);
     else
       f += 2.0 * 64.0 * 64.0 * K * ((fp64 && (flags & (G_TRIB | G_SYMC))) ? 10.0 / 16.0 : 1.0) +
-           ((flags & G_POSTMUL) ? 2.0 * 64.0 * 64.0 * 64.0 : 0.0);
+           ((flags & G_POSTMUL) ? 2.0 * 64.0 * 64.0 * 64.0 * (fp64 ? 10.0 / 16.0 : 1.0) : 0.0);
   };
   if (c->h.mixed) for (const auto& t : c->w->factf.gemm) add(t.flags, t.K);
   else for (const auto& t : c->w->fact.gemm) add(t.flags, t.K);
