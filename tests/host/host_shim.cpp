@@ -709,6 +709,46 @@ long long hc_align_check(void* p, int which, char* msg, int len) {
   return n;
 }
 
+// Preconditions of the TMA-filled solve ring (k_solve_tma) on the FP32
+// 8-column solve schedules, the conditions the kernel checks on the device
+// before its first copy: a task with an inner dimension reads one 64-row slab
+// of one of its subdomain's four FP32 arrays (D|E and inverse of K, then of
+// A11), with that array's row stride, a column that is a multiple of 4 floats
+// (16 bytes) and every stage inside the array.  Returns the violations.
+long long hc_tma_check(void* p, int which, char* msg, int len) {
+  HostCheck* c = H(p);
+  if (c->w == nullptr || !c->h.mixed) return -1;
+  const SolveScheduleT<float>* s = solve_sched<float>(*c->w, which);
+  long long n = 0;
+  std::string first;
+  for (size_t i = 0; i < s->tasks.size(); ++i) {
+    const SolveTaskT<float>& t = s->tasks[i];
+    if (t.K <= 0) continue;
+    bool ok = false;
+    if (t.sub >= 0 && t.sub < c->h.N) {
+      const SubDev& sd = c->h.sub[t.sub];
+      const float* base[4] = {sd.DKf, sd.LKf, sd.DAf, sd.LAf};
+      const int b[4] = {sd.bK, sd.bK, sd.bA, sd.bA};
+      const int rows[4] = {(2 * sd.nzn - 1) * sd.bK, sd.nzn * sd.bK, (2 * sd.nzn - 1) * sd.bA, sd.nzn * sd.bA};
+      for (int m = 0; m < 4 && !ok; ++m) {
+        if (base[m] == nullptr || t.A < base[m]) continue;
+        const long long off = t.A - base[m];
+        if (off >= (long long)rows[m] * b[m]) continue;
+        const int y = (int)(off / b[m]), x = (int)(off % b[m]);
+        const bool tr = (t.flags & S_TRANSA) != 0;
+        const int w = tr ? 64 : t.K, hgt = tr ? t.K : 64;
+        ok = t.lda == b[m] && x % 4 == 0 && x + w <= b[m] && y + hgt <= rows[m] && t.K % 64 == 0;
+      }
+    }
+    if (!ok) {
+      if (first.empty()) first = "solve task " + std::to_string(i) + " outside the TMA preconditions";
+      ++n;
+    }
+  }
+  if (msg && len > 0) snprintf(msg, len, "%s", first.c_str());
+  return n;
+}
+
 // A planted scheduling mistake, for checking the race check itself: step s of
 // group g merged with step s + 1 (two dependent launches made one).
 int hc_merge_steps(void* p, int which, int g, int s) {

@@ -95,6 +95,8 @@ def lib():
         L.hc_align_check.restype = C.c_longlong
         L.hc_align_check.argtypes = [vp, i, C.c_char_p, i]
         L.hc_set_persistent.argtypes = [vp, i]
+        L.hc_tma_check.restype = C.c_longlong
+        L.hc_tma_check.argtypes = [vp, i, C.c_char_p, i]
         L.hc_persistent_tasks.restype = C.c_longlong
         L.hc_persistent_tasks.argtypes = [vp]
         L.hc_run_factor_persistent.argtypes = [vp, i, C.c_uint]
@@ -213,6 +215,12 @@ class HostSetup:
 
     def run_factor(self, seed=0, coarse=False):
         return self.L.hc_run_factor(self.h, int(coarse), seed)
+
+    def tma_check(self, which):
+        """Violations of the TMA solve ring's slab preconditions (count, first one)."""
+        msg = C.create_string_buffer(200)
+        n = self.L.hc_tma_check(self.h, which, msg, 200)
+        return n, msg.value.decode()
 
     def set_persistent(self, on=True):
         """Build the persistent factorisation's ticket order with the next build_wave."""

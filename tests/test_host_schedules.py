@@ -390,6 +390,22 @@ def test_algorithmic_flops_do_not_exceed_the_executed_ones():
     assert 1.0 < r64 < r32 and 1.26 < r64 < 1.31, found
 
 
+@pytest.mark.parametrize("name", ["t2", "s2", "c2", "c4"])
+def test_tma_solve_preconditions(name):
+    """Every FP32 8-column solve task with an inner dimension satisfies the
+    slab conditions the TMA-filled solve ring checks on the device (its error
+    path never fires on the library's own schedules), on full-size schedules
+    built on a virtual pool."""
+    cfg = _cfg(name)
+    hs = hc.HostSetup(cfg, mixed=True)
+    assert hs.plan_waves(1e18) == 1
+    hs.build_wave_virtual(0, 16, 4, left=False)
+    for which in (hc.SC_SOLVE_K8, hc.SC_SOLVE_A8):
+        n, msg = hs.tma_check(which)
+        assert n == 0, (which, msg)
+    hs.close()
+
+
 @pytest.mark.parametrize("name", ["c2", "c4"])
 @pytest.mark.parametrize("mixed", [False, True])
 def test_vector_load_preconditions_at_full_size(name, mixed):
