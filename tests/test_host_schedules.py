@@ -363,8 +363,8 @@ def test_algorithmic_flops_do_not_exceed_the_executed_ones():
     beam the FP32 tasks execute 1.21 times the count with the inverses and
     1.38 times the algorithmic one, the same for both schedules; the FP64
     kernel skips the zero blocks of the triangular operand of its TRMM tasks
-    and the blocks above the diagonal of diagonal output tiles (10 of 16
-    blocks computed), 1.29 times the algorithmic count.  Either way the
+    and post-multiplications and the blocks above the diagonal of diagonal
+    output tiles (10 of 16 blocks computed), 1.27 times the algorithmic count.  Either way the
     reported fraction of peak understates the rate of the tile kernel."""
     cfg = _cfg("c2")
     found = {}
