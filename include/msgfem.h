@@ -315,12 +315,14 @@ typedef struct {
                            included; a warm start that fell back to a cold one counts the cold
                            run) or subspace iterations */
   int basis_size;       /* coarse basis functions contributed (n_loc [+1]) */
-  double residual;      /* max relative eigen-residual over the n_loc pairs */
+  double residual;      /* max relative eigen-residual over the subdomain's n_loc pairs */
   int threshold_reached;   /* msgfem_coarse_assemble_threshold: 0 if every one of the n_loc
                               eigenvalues was below 1 / t (the basis may need a larger n_loc) */
   int cold_restart;     /* 1 if the subdomain's registered start block (msgfem_set_start_block)
                            did not lead to convergence and the block Krylov solver was run
                            again from the cold (seeded random) start */
+  int n_loc;            /* eigenpairs of the subdomain in the last local stage (or import),
+                           0 before the first */
 } msgfem_subinfo;
 
 /* Partition, DoF classes (Sec. 4.3) and partition of unity (Sec. 4.2) on the
@@ -366,10 +368,27 @@ msgfem_status msgfem_update_angles(msgfem_h h, const double* elem_angle_deg);
  * (Eq. up_r), wave by wave when the factors do not fit at once
  * (msgfem_options.wave_mb).  lambda_out (N * n_loc doubles, subdomain-major,
  * ascending; may be NULL; host or device) receives the eigenvalues.  Errors:
- * EINVAL (n_loc < 1 or larger than the A-harmonic space of a subdomain),
+ * EINVAL (n_loc outside 1 .. 31 (a subdomain's eigenvectors and its
+ * particular function fill at most 32 basis columns) or larger than the
+ * A-harmonic space of a subdomain),
  * ENOTSPD, ENOCONV (results are the last iterate; msgfem_subinfo gives each
  * subdomain's residual), ECUDA. */
 msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out);
+
+/* msgfem_local_spaces with its own n_loc for every subdomain: the local basis
+ * sizes m_j of Eq. AHarmonic_coarse_space, which differ between subdomains
+ * (Sec. 5.3: interior subdomains need more eigenvectors for the same local
+ * error; Sec. 5.5: m_j from 60 to 170 on the C-spar).  n_loc: N
+ * host ints, n_loc[j] eigenpairs of subdomain j, each within the limits of
+ * msgfem_local_spaces.  lambda_out (may be NULL; host or device) receives
+ * N * n_max doubles, n_max the largest n_loc[j], subdomain-major; entries
+ * c >= n_loc[j] of row j are NaN.  msgfem_get_basis and msgfem_export_local
+ * then give n_max columns per subdomain, columns c >= n_loc[j] zero (and
+ * NaN eigenvalues); msgfem_coarse_assemble keeps the n_loc[j] eigenvectors
+ * of subdomain j, msgfem_coarse_assemble_threshold at most as many.
+ * msgfem_local_spaces(h, n, out) is this call with every n_loc[j] = n.
+ * Errors as msgfem_local_spaces; EINVAL also for n_loc NULL. */
+msgfem_status msgfem_local_spaces_var(msgfem_h h, const int* n_loc, double* lambda_out);
 
 /* PoU-weighted basis with Gram-Schmidt and the appended particular function
  * (Sec. 4.3-4.4), coarse matrix A^H_{ij} = V_i^T A V_j and load b^H
@@ -415,10 +434,12 @@ msgfem_status msgfem_export_local(msgfem_h h, int j, double* phi_out, double* la
  * matrices as msgfem_local_spaces does and takes the eigenpairs and particular
  * functions from lambda (N * n_loc doubles, subdomain-major) and phi (N
  * pointers, each as phi_out of msgfem_export_local) instead of solving for
- * them; the handle is then ready for msgfem_coarse_assemble.  Host or device
- * pointers, copied.  Errors: EINVAL (NULL, n_loc outside 1 .. 31 or above a
- * subdomain's B2 size, non-finite eigenvalue), ESTATE (before msgfem_setup),
- * ENOMEM, ECUDA. */
+ * them; the handle is then ready for msgfem_coarse_assemble.  A row of lambda
+ * may end in NaN entries, as msgfem_local_spaces_var writes them: subdomain j
+ * then keeps the eigenpairs before its first NaN.  Host or device pointers,
+ * copied.  Errors: EINVAL (NULL, n_loc outside 1 .. 31 or above a
+ * subdomain's B2 size, an infinite eigenvalue, a NaN followed by a number, a
+ * row without eigenvalues), ESTATE (before msgfem_setup), ENOMEM, ECUDA. */
 msgfem_status msgfem_import_local(msgfem_h h, int n_loc, const double* lambda, const double* const* phi);
 
 /* Energy error ||u_ref - u||_a / ||u_ref||_a of two caller-owned device

@@ -76,8 +76,9 @@ msgfem_status msgfem_warm_features(msgfem_h h, const double* dtheta, float scale
 
 /* Size of the interface (B2) block of subdomain j (rows of its start block)
  * and the number of wanted non-rigid eigenpairs nw_j = n_loc - 6 for a
- * floating subdomain, n_loc otherwise (n_loc of the last msgfem_local_spaces
- * call, or of the argument when > 0). */
+ * floating subdomain, n_loc otherwise (subdomain j's n_loc in the last
+ * msgfem_local_spaces or msgfem_local_spaces_var call, or the argument when
+ * > 0). */
 msgfem_status msgfem_warm_sizes(msgfem_h h, int j, int n_loc, int* n2_out, int* nw_out);
 
 /* After msgfem_local_spaces: the wanted non-rigid eigenvectors of subdomain j

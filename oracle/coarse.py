@@ -87,8 +87,10 @@ def run_msgfem(cfg, angles=None, n_loc=None, variant="ii", solver="dense", uh=No
     """MS-GFEM with n_loc eigenvectors per subdomain, or, with ``threshold`` t,
     the eigenvectors with 1 / lambda > t among the n_loc computed (Sec. 5.5,
     Sec. 5.6: the local basis sizes m_j follow from a threshold on the
-    reciprocal eigenvalues).  ``load``: nodal forces replacing the end-face
-    traction as the right-hand side b."""
+    reciprocal eigenvalues).  n_loc may also be a sequence with one count per
+    subdomain: the m_j of Eq. AHarmonic_coarse_space chosen for each subdomain
+    (Sec. 5.3: interior subdomains need more eigenvectors).  ``load``: nodal
+    forces replacing the end-face traction as the right-hand side b."""
     mesh = make_mesh(cfg)
     E = cfg.material
     if angles is None:
@@ -104,7 +106,7 @@ def run_msgfem(cfg, angles=None, n_loc=None, variant="ii", solver="dense", uh=No
     eig = local_eigs_dense if solver == "dense" else local_eigs_arpack
     for s in subs:
         lp = local_problem(mesh, angles, E, s, mus[s.index], b, cache=cache)
-        lam, phi = eig(lp, n_loc)
+        lam, phi = eig(lp, n_loc if np.ndim(n_loc) == 0 else int(n_loc[s.index]))
         psi = particular(lp)
         res.lam.append(lam)
         res.phi.append(phi)

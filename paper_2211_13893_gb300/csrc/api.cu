@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 
 #include <type_traits>
 #include <unordered_map>
@@ -729,7 +730,7 @@ msgfem_status schwarz_factors(msgfem* h) {
 void schwarz_local_solve(msgfem* h) { timed_solve8(h, 1, MV_TB, MV_WB, 0); }
 
 // Subspace iteration with Rayleigh-Ritz every step (solver = 1).
-msgfem_status run_subspace(msgfem* h, int n_loc, int p, bool& all_done) {
+msgfem_status run_subspace(msgfem* h, const std::vector<int>& nl, int p, bool& all_done) {
   cudaStream_t st = h->stream;
   std::vector<int> act(h->base_act);
   // 3. start block X0 on B2, A-harmonic extension, and psi in the last column
@@ -785,7 +786,7 @@ msgfem_status run_subspace(msgfem* h, int n_loc, int p, bool& all_done) {
     CK(cudaStreamSynchronize(st));
     for (int j = 0; j < h->N; ++j) {
       if (!act[j]) continue;
-      const int nw = n_loc - (h->sub[j].floating ? 6 : 0);
+      const int nw = nl[j] - (h->sub[j].floating ? std::min(6, nl[j]) : 0);
       double dmax = 0.0;
       for (int c = 0; c < nw; ++c)
         dmax = max_nan(dmax, std::sqrt(std::fabs(gdiag[(size_t)j * PST * PST + (size_t)c * PST + c])));
@@ -810,12 +811,12 @@ msgfem_status run_subspace(msgfem* h, int n_loc, int p, bool& all_done) {
 // Block Krylov (block Lanczos, full re-orthogonalisation) on M = S^{-1} T in
 // the N = S + sigma T inner product, block width KB, basis up to MQ
 // (solver = 0, default).
-msgfem_status run_krylov(msgfem* h, int n_loc, bool& all_done) {
+msgfem_status run_krylov(msgfem* h, const std::vector<int>& nl, bool& all_done) {
   cudaStream_t st = h->stream;
   std::vector<int> nw(h->N), act(h->base_act), mk(h->N, 0);
   int nwmax = 0;
   for (int j = 0; j < h->N; ++j) {
-    nw[j] = n_loc - (h->sub[j].floating ? std::min(6, n_loc) : 0);
+    nw[j] = nl[j] - (h->sub[j].floating ? std::min(6, nl[j]) : 0);
     nwmax = std::max(nwmax, nw[j]);
   }
   CK(cudaMemcpyAsync(h->d_nwk, nw.data(), h->N * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -1128,30 +1129,50 @@ msgfem_status msgfem_update_angles(msgfem_h h, const double* ang) {
   return st;
 }
 
-static msgfem_status local_spaces_run(msgfem_h h, int n_loc, double* lambda_out);
+static msgfem_status local_spaces_run(msgfem_h h, const std::vector<int>& nl, double* lambda_out);
 
 // every entry point that runs block solves ends by reading the TMA stages' error flag
 msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
   if (!h) return MSGFEM_EINVAL;
-  const msgfem_status st = local_spaces_run(h, n_loc, lambda_out);
+  const msgfem_status st = local_spaces_run(h, std::vector<int>(h->N, n_loc), lambda_out);
   const msgfem_status ke = check_stage_error(h);
   return ke != MSGFEM_OK ? ke : st;
 }
 
-static msgfem_status local_spaces_run(msgfem_h h, int n_loc, double* lambda_out) {
+msgfem_status msgfem_local_spaces_var(msgfem_h h, const int* n_loc, double* lambda_out) {
+  if (!h) return MSGFEM_EINVAL;
+  if (!n_loc) { h->err = "msgfem_local_spaces_var: n_loc is NULL"; return MSGFEM_EINVAL; }
+  const msgfem_status st = local_spaces_run(h, std::vector<int>(n_loc, n_loc + h->N), lambda_out);
+  const msgfem_status ke = check_stage_error(h);
+  return ke != MSGFEM_OK ? ke : st;
+}
+
+// nl: eigenpairs per subdomain; n_loc below is the largest of them
+static msgfem_status local_spaces_run(msgfem_h h, const std::vector<int>& nl, double* lambda_out) {
   if (!h) return MSGFEM_EINVAL;
   if (h->stage < 1) return MSGFEM_ESTATE;
-  if (n_loc < 1) { h->err = "n_loc must be >= 1"; return MSGFEM_EINVAL; }
+  const int n_loc = nl.empty() ? 0 : *std::max_element(nl.begin(), nl.end());
+  // a subdomain's eigenvectors and its particular function share the PST
+  // columns of the basis blocks
+  for (int j = 0; j < h->N; ++j)
+    if (nl[j] < 1 || nl[j] > PST - 1) {
+      h->err = "n_loc must be in 1 .. 31 (subdomain " + std::to_string(j) + ")";
+      return MSGFEM_EINVAL;
+    }
   int p = h->opt.block > 0 ? h->opt.block : n_loc + std::max(8, n_loc / 2);
   if (p > PST - 1) p = PST - 1;
   for (int j = 0; j < h->N; ++j) {
-    const int nw = n_loc - (h->sub[j].floating ? 6 : 0);
+    const int nw = nl[j] - (h->sub[j].floating ? 6 : 0);
     // the eigenproblem lives on B2 (A-harmonic functions) or, for GenEO, on B1 where B is definite
-    if (n_loc > (h->geneo ? h->n1[j] : h->n2[j])) {
-      h->err = h->geneo ? "n_loc exceeds the B1 size of a subdomain" : "n_loc exceeds the B2 size of a subdomain";
+    if (nl[j] > (h->geneo ? h->n1[j] : h->n2[j])) {
+      h->err = (h->geneo ? "n_loc exceeds the B1 size of subdomain " : "n_loc exceeds the B2 size of subdomain ") +
+               std::to_string(j);
       return MSGFEM_EINVAL;
     }
-    if (nw > p) { h->err = "n_loc too large for the block size (at most 31 columns)"; return MSGFEM_EINVAL; }
+    if (nw > p) {
+      h->err = "n_loc too large for the block size (at most 31 columns; subdomain " + std::to_string(j) + ")";
+      return MSGFEM_EINVAL;
+    }
   }
   if (h->geneo && h->opt.solver != 0) {
     h->err = "the GenEO eigenproblem runs the block Krylov solver (solver = 0) only";
@@ -1171,6 +1192,7 @@ static msgfem_status local_spaces_run(msgfem_h h, int n_loc, double* lambda_out)
   h->factored_wave = -1;
   h->potrf_fp64 = 0;   // with tile_chol 1 each local stage first tries FP32 tile Cholesky
   h->n_loc = n_loc;
+  h->nloc_j = nl;
   h->p = p;
   cudaStream_t st = h->stream;
   set_dense_context(h->d_flags, h->d_notspd, h->d_sub);
@@ -1260,9 +1282,9 @@ static msgfem_status local_spaces_run(msgfem_h h, int n_loc, double* lambda_out)
     sp_iter = span_begin(h, TAG_ITERATE);
     bool done = false;
     if (h->opt.solver == 1) {
-      TRY(run_subspace(h, n_loc, p, done));
+      TRY(run_subspace(h, nl, p, done));
     } else {
-      TRY(run_krylov(h, n_loc, done));
+      TRY(run_krylov(h, nl, done));
       // a learned (or any registered) start that did not lead to convergence is
       // dropped: those subdomains are solved again from the cold start
       std::vector<int> redo(h->N, 0);
@@ -1284,7 +1306,7 @@ static msgfem_status local_spaces_run(msgfem_h h, int n_loc, double* lambda_out)
         h->base_act = redo;
         TRY(set_active(h, redo));
         bool redo_done = false;
-        const msgfem_status rst = run_krylov(h, n_loc, redo_done);
+        const msgfem_status rst = run_krylov(h, nl, redo_done);
         h->warm = kept;
         h->base_act = wave_act;
         TRY(rst);
@@ -1322,12 +1344,13 @@ static msgfem_status local_spaces_run(msgfem_h h, int n_loc, double* lambda_out)
   // eigenvectors: [rigid modes (floating), Ritz vectors]
   for (int j = 0; j < h->N; ++j) {
     const SubDev& s = h->sub[j];
-    const int nr = s.floating ? std::min(6, n_loc) : 0;
+    const int nr = s.floating ? std::min(6, nl[j]) : 0;
     CK(cudaMemsetAsync(s.EV, 0, (size_t)s.nfull * PST * sizeof(double), st));
     CK(cudaMemcpy2DAsync(s.EV, PST * sizeof(double), s.R, PST * sizeof(double), nr * sizeof(double), s.nfull,
                          cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpy2DAsync(s.EV + nr, PST * sizeof(double), s.Phi, PST * sizeof(double),
-                         (n_loc - nr) * sizeof(double), s.nfull, cudaMemcpyDeviceToDevice, st));
+    if (nl[j] > nr)
+      CK(cudaMemcpy2DAsync(s.EV + nr, PST * sizeof(double), s.Phi, PST * sizeof(double),
+                           (nl[j] - nr) * sizeof(double), s.nfull, cudaMemcpyDeviceToDevice, st));
   }
   CK_LAUNCH();
   std::vector<int> notspd(h->N + 1);
@@ -1338,14 +1361,14 @@ static msgfem_status local_spaces_run(msgfem_h h, int n_loc, double* lambda_out)
     CK(cudaMemcpyAsync(res.data(), h->sub[j].resid, PST * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&theta[(size_t)j * PST], h->sub[j].theta, PST * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    const int nw = n_loc - (h->sub[j].floating ? 6 : 0);
+    const int nw = nl[j] - (h->sub[j].floating ? 6 : 0);
     for (int c = 0; c < nw; ++c) h->resid_max[j] = max_nan(h->resid_max[j], res[c]);
   }
   std::vector<double>& lam = h->lam_host;
-  lam.assign((size_t)h->N * n_loc, 0.0);
+  lam.assign((size_t)h->N * n_loc, std::numeric_limits<double>::quiet_NaN());
   for (int j = 0; j < h->N; ++j) {
-    const int nr = h->sub[j].floating ? std::min(6, n_loc) : 0;
-    for (int c = 0; c < n_loc; ++c) lam[(size_t)j * n_loc + c] = c < nr ? 0.0 : theta[(size_t)j * PST + c - nr];
+    const int nr = h->sub[j].floating ? std::min(6, nl[j]) : 0;
+    for (int c = 0; c < nl[j]; ++c) lam[(size_t)j * n_loc + c] = c < nr ? 0.0 : theta[(size_t)j * PST + c - nr];
   }
   if (lambda_out) {
     if (is_device_ptr(lambda_out)) {
@@ -1367,7 +1390,7 @@ static msgfem_status local_spaces_run(msgfem_h h, int n_loc, double* lambda_out)
       return MSGFEM_ENOTSPD;
     }
   for (int j = 0; j < h->N; ++j)
-    for (int c = 0; c < n_loc; ++c)
+    for (int c = 0; c < nl[j]; ++c)
       if (!std::isfinite(lam[(size_t)j * n_loc + c]) || std::fabs(lam[(size_t)j * n_loc + c]) >= 1e299 ||
           !std::isfinite(h->resid_max[j])) {
         h->err = "non-finite eigenvalue or residual in subdomain " + std::to_string(j);
@@ -1403,16 +1426,16 @@ msgfem_status msgfem_coarse_assemble_threshold(msgfem_h h, double t, int* coarse
   TRY(set_active(h, std::vector<int>(h->N, 1)));
   const int sp_c = span_begin(h, TAG_COARSE);
   // local basis sizes m_j (Sec. 5.5): with a threshold t > 0 the eigenvectors
-  // with 1 / lambda > t, i.e. lambda < 1 / t, of the n_loc computed (rigid
-  // modes always); t = 0 keeps all n_loc
-  h->m_sel.assign(h->N, n_loc);
+  // with 1 / lambda > t, i.e. lambda < 1 / t, of the nloc_j computed (rigid
+  // modes always); t = 0 keeps all nloc_j
+  h->m_sel = h->nloc_j;
   h->thr_reached.assign(h->N, 1);
   if (t > 0.0)
     for (int j = 0; j < h->N; ++j) {
       int m = 0;
-      while (m < n_loc && h->lam_host[(size_t)j * n_loc + m] * t < 1.0) ++m;
+      while (m < h->nloc_j[j] && h->lam_host[(size_t)j * n_loc + m] * t < 1.0) ++m;
       h->m_sel[j] = m;
-      h->thr_reached[j] = m < n_loc ? 1 : 0;
+      h->thr_reached[j] = m < h->nloc_j[j] ? 1 : 0;
     }
   // basis [phi_1..phi_mj, psi] in CB; psi only on loaded subdomains
   std::vector<int> ncols(h->N);
@@ -1595,14 +1618,26 @@ msgfem_status msgfem_import_local(msgfem_h h, int n_loc, const double* lambda, c
   if (!h || !lambda || !phi) return MSGFEM_EINVAL;
   if (h->stage < 1) return MSGFEM_ESTATE;
   if (n_loc < 1 || n_loc > PST - 1) { h->err = "n_loc must be in 1 .. 31"; return MSGFEM_EINVAL; }
-  for (int j = 0; j < h->N; ++j) {
+  for (int j = 0; j < h->N; ++j)
     if (phi[j] == nullptr) { h->err = "a subdomain without its exported local space"; return MSGFEM_EINVAL; }
-    if (n_loc > h->n2[j]) { h->err = "n_loc exceeds the B2 size of a subdomain"; return MSGFEM_EINVAL; }
-  }
   std::vector<double> lam((size_t)h->N * n_loc);
   CK(cudaMemcpy(lam.data(), lambda, lam.size() * sizeof(double), cudaMemcpyDefault));
-  for (double v : lam)
-    if (!std::isfinite(v)) { h->err = "non-finite eigenvalue"; return MSGFEM_EINVAL; }
+  // a row may end in NaN entries (a local stage with fewer eigenpairs for
+  // that subdomain); its leading entries are the subdomain's eigenvalues
+  std::vector<int> nl(h->N);
+  for (int j = 0; j < h->N; ++j) {
+    const double* row = &lam[(size_t)j * n_loc];
+    int c = 0;
+    while (c < n_loc && !std::isnan(row[c])) ++c;
+    nl[j] = c;
+    for (int k = 0; k < n_loc; ++k)
+      if ((k < c && !std::isfinite(row[k])) || (k >= c && !std::isnan(row[k]))) {
+        h->err = "non-finite eigenvalue";
+        return MSGFEM_EINVAL;
+      }
+    if (c < 1) { h->err = "a subdomain without eigenvalues"; return MSGFEM_EINVAL; }
+    if (c > h->n2[j]) { h->err = "n_loc exceeds the B2 size of a subdomain"; return MSGFEM_EINVAL; }
+  }
   h->stage = 1;   // the earlier local spaces, coarse problem and solution are replaced
   cudaStream_t st = h->stream;
   set_dense_context(h->d_flags, h->d_notspd, h->d_sub);
@@ -1622,7 +1657,7 @@ msgfem_status msgfem_import_local(msgfem_h h, int n_loc, const double* lambda, c
     const size_t count = (size_t)s.nfull * (n_loc + 1);
     e = cudaMemcpyAsync(tmp, phi[j], count * sizeof(double), cudaMemcpyDefault, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.EV, 0, (size_t)s.nfull * PST * sizeof(double), st);
-    for (int c = 0; c < n_loc && e == cudaSuccess; ++c)
+    for (int c = 0; c < nl[j] && e == cudaSuccess; ++c)
       launch_vec_layout(h, j, tmp + (size_t)c * s.nfull, 1, s.EV + c, PST, 0);
     if (e == cudaSuccess) launch_vec_layout(h, j, tmp + (size_t)n_loc * s.nfull, 1, s.psi, 1, 0);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -1632,6 +1667,7 @@ msgfem_status msgfem_import_local(msgfem_h h, int n_loc, const double* lambda, c
   dev_free_bytes(h, tmp);
   CK(e);
   h->n_loc = n_loc;
+  h->nloc_j = nl;
   h->lam_host = lam;
   h->iters.assign(h->N, 0);
   h->m_final.assign(h->N, 0);
@@ -1653,6 +1689,7 @@ msgfem_status msgfem_get_info(msgfem_h h, int j, msgfem_subinfo* info) {
   info->residual = j < (int)h->resid_max.size() ? h->resid_max[j] : 0.0;
   info->threshold_reached = j < (int)h->thr_reached.size() ? h->thr_reached[j] : 1;
   info->cold_restart = j < (int)h->cold_restart.size() ? h->cold_restart[j] : 0;
+  info->n_loc = j < (int)h->nloc_j.size() ? h->nloc_j[j] : 0;
   return MSGFEM_OK;
 }
 

@@ -211,7 +211,9 @@ struct msgfem {
   std::vector<int> n1, n2, n3, iters, basis_m, m_final;
   std::vector<int> krylov_left;      // [N] 1 if the last block Krylov run left the subdomain unconverged
   std::vector<int> cold_restart;     // [N] 1 if a registered start block was dropped for a cold start
-  std::vector<double> lam_host;      // [N][n_loc] eigenvalues of the last local stage (rigid zeros first)
+  std::vector<double> lam_host;      // [N][n_loc] eigenvalues of the last local stage (rigid zeros first,
+                                     // NaN from a subdomain's own count nloc_j on)
+  std::vector<int> nloc_j;           // [N] eigenpairs of every subdomain in the last local stage
   std::vector<int> m_sel;            // [N] eigenvectors in the coarse basis (threshold selection)
   std::vector<int> thr_reached;      // [N] 0 if all n_loc eigenvalues were below the threshold
   std::vector<int> act_host;         // host copy of the active flags last uploaded
@@ -270,7 +272,7 @@ struct msgfem {
   double* d_l2 = nullptr;            // [1024][4] block sums of the L2 errors (msgfem_solution_errors)
   Schedule cfact;
   SolveSchedule csolve;
-  int n_loc = 0, p = 0;
+  int n_loc = 0, p = 0;              // n_loc: the largest nloc_j (columns of lam_host and of the bases)
   // profiling (CUDA events on the handle's stream)
   struct Span { int tag; cudaEvent_t a, b; };
   std::vector<Span> spans;

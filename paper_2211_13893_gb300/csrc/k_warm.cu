@@ -237,7 +237,7 @@ msgfem_status msgfem_warm_features(msgfem_h h, const double* dtheta, float scale
 
 msgfem_status msgfem_warm_sizes(msgfem_h h, int j, int n_loc, int* n2_out, int* nw_out) {
   if (!h || j < 0 || j >= h->N) return MSGFEM_EINVAL;
-  const int nl = n_loc > 0 ? n_loc : h->n_loc;
+  const int nl = n_loc > 0 ? n_loc : (j < (int)h->nloc_j.size() ? h->nloc_j[j] : h->n_loc);
   if (n2_out) *n2_out = h->n2[j];
   if (nw_out) *nw_out = nl - (h->sub[j].floating ? std::min(6, nl) : 0);
   return MSGFEM_OK;
@@ -248,8 +248,9 @@ msgfem_status msgfem_warm_targets(msgfem_h h, int j, const float* ref, float* ou
   if (h->stage < 2) return MSGFEM_ESTATE;
   TRY(warm_rows(h));
   const SubDev& s = h->sub[j];
-  const int nr = s.floating ? std::min(6, h->n_loc) : 0;
-  const int nw = std::min(KB, h->n_loc - nr);
+  const int nl = h->nloc_j[j];
+  const int nr = s.floating ? std::min(6, nl) : 0;
+  const int nw = std::min(KB, nl - nr);
   k_warm_targets<<<1, 256, 0, h->stream>>>(s.EV, h->d_b2rows[j], h->n2[j], nr, nw, ref, out, ld);
   ++g_launch_count;
   CK(cudaGetLastError());

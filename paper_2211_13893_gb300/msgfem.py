@@ -13,7 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libmsgfem.so")
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTSPD", 5: "ENOCONV", 6: "ESTATE"}
-EXPORTS = ("msgfem_setup", "msgfem_update_angles", "msgfem_local_spaces", "msgfem_coarse_assemble",
+EXPORTS = ("msgfem_setup", "msgfem_update_angles", "msgfem_local_spaces", "msgfem_local_spaces_var",
+           "msgfem_coarse_assemble",
            "msgfem_solve", "msgfem_get_basis", "msgfem_get_info", "msgfem_num_subdomains",
            "msgfem_get_profile", "msgfem_reset_profile", "msgfem_energy_error_noalloc", "msgfem_last_error",
            "msgfem_autotune", "msgfem_coarse_assemble_threshold", "msgfem_solution_errors", "msgfem_plan",
@@ -93,7 +94,7 @@ class PcgInfo(C.Structure):
 class SubInfo(C.Structure):
     _fields_ = [("n_star_dof", C.c_int), ("n1", C.c_int), ("n2", C.c_int), ("n3", C.c_int), ("floating", C.c_int),
                 ("iterations", C.c_int), ("basis_size", C.c_int), ("residual", C.c_double),
-                ("threshold_reached", C.c_int), ("cold_restart", C.c_int)]
+                ("threshold_reached", C.c_int), ("cold_restart", C.c_int), ("n_loc", C.c_int)]
 
 
 _lib = None
@@ -113,6 +114,7 @@ def load_library(path=LIB_PATH):
                                    C.POINTER(Options), C.POINTER(h)]),
         "msgfem_update_angles": (C.c_int, [h, C.c_void_p]),
         "msgfem_local_spaces": (C.c_int, [h, C.c_int, C.c_void_p]),
+        "msgfem_local_spaces_var": (C.c_int, [h, C.c_void_p, C.c_void_p]),
         "msgfem_coarse_assemble": (C.c_int, [h, C.POINTER(C.c_int)]),
         "msgfem_coarse_assemble_threshold": (C.c_int, [h, C.c_double, C.POINTER(C.c_int)]),
         "msgfem_solve": (C.c_int, [h, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
@@ -263,10 +265,22 @@ class MSGFEM:
         self._check(self.lib.msgfem_update_angles(self.h, _ptr(angles)))
 
     def local_spaces(self, n_loc, lam_out=None, allow_noconv=False):
-        """Returns eigenvalues (N, n_loc) (numpy) or fills lam_out (device tensor)."""
-        self.n_loc = n_loc
-        out = lam_out if lam_out is not None else np.zeros((self.N, n_loc))
-        self._check(self.lib.msgfem_local_spaces(self.h, n_loc, _ptr(out)), allow=(5,) if allow_noconv else ())
+        """Returns eigenvalues (N, n_loc) (numpy) or fills lam_out (device tensor).
+        n_loc may also be one count per subdomain (msgfem_local_spaces_var): the
+        rows are then max(n_loc) long, NaN from a subdomain's own count on."""
+        allow = (5,) if allow_noconv else ()
+        if np.ndim(n_loc) == 0:
+            n_loc = int(n_loc)
+            self.n_loc = n_loc
+            out = lam_out if lam_out is not None else np.zeros((self.N, n_loc))
+            self._check(self.lib.msgfem_local_spaces(self.h, n_loc, _ptr(out)), allow=allow)
+            return out
+        counts = np.ascontiguousarray(n_loc, dtype=np.int32).reshape(-1)
+        if counts.shape[0] != self.N:
+            raise ValueError(f"n_loc needs one count per subdomain ({self.N}), got {counts.shape[0]}")
+        self.n_loc = int(counts.max())
+        out = lam_out if lam_out is not None else np.zeros((self.N, self.n_loc))
+        self._check(self.lib.msgfem_local_spaces_var(self.h, counts.ctypes.data, _ptr(out)), allow=allow)
         return out
 
     def coarse_assemble(self, threshold=None):

@@ -5,7 +5,9 @@ subdomains of the full c4 C-section spar (250 x 110 x 32 curved hexahedra,
 Calls only oracle/ (and the seeded generators of workloads/): the curved mesh
 and ply frames, the partition of unity of all 256 subdomains (Sec. 4.2), and
 for each sampled subdomain the A-harmonic local eigenproblem (Eq.
-AHarmonicGeneralizeEigenProblem) in the dense-reduced form for every sample.
+AHarmonicGeneralizeEigenProblem) in the dense-reduced form for every sample,
+with the sample's own eigenpair count (16 to 31, growing with the size of
+its oversampling domain, workloads.section.n_loc_per_subdomain).
 (ARPACK shift-invert on the saddle pencil, the paper's own design, missed one
 copy of the six-fold zero eigenvalue of the floating corner domain 83: a
 single-vector Lanczos need not resolve every copy of a multiple eigenvalue,
@@ -38,7 +40,9 @@ def main():
     from oracle.mesh import make_mesh
     from oracle.partition import partition_of_unity, subdomains
     from workloads import element_angles, get_config
+    from workloads.section import n_loc_per_subdomain
     cfg = get_config("c4")
+    counts = n_loc_per_subdomain(cfg)
     t0 = time.time()
     m = make_mesh(cfg)
     ang = element_angles(cfg)
@@ -47,12 +51,13 @@ def main():
     b = m.compression_load(cfg.traction)
     cache = make_cache(m, cfg.material)
     print(f"mesh, partition of unity and load: {time.time() - t0:.1f} s", flush=True)
-    out = {"config": "c4", "n_loc": cfg.n_loc, "samples": {}}
+    out = {"config": "c4", "n_loc": [cfg.n_loc, cfg.n_loc_max], "samples": {}}
     for j, how in SAMPLES.items():
         t1 = time.time()
         lp = local_problem(m, ang, cfg.material, subs[j], mus[j], b, cache)
-        lam, _ = (local_eigs_dense if how == "dense" else local_eigs_arpack)(lp, cfg.n_loc)
-        out["samples"][str(j)] = {"solver": how, "n_star_dof": int(lp.n_star), "n1": int(len(lp.I1)),
+        lam, _ = (local_eigs_dense if how == "dense" else local_eigs_arpack)(lp, int(counts[j]))
+        out["samples"][str(j)] = {"solver": how, "n_loc": int(counts[j]), "n_star_dof": int(lp.n_star),
+                                  "n1": int(len(lp.I1)),
                                   "n2": int(len(lp.I2)), "n3": int(len(lp.I3)), "star": list(subs[j].star),
                                   "lambda": [float(x) for x in lam]}
         print(f"subdomain {j}: {lp.n_star} DoF, n2 {len(lp.I2)}, {how}, {time.time() - t1:.1f} s, "

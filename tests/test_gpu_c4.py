@@ -1,13 +1,15 @@
 """Parity at full size on the c4 C-section spar (250 x 110 x 32 curved hexahedra,
-2,758,239 DoF, 256 uneven subdomains of 4k-42k DoF) in mixed precision, all
-subdomains in one handle as the benchmark runs them.
+2,758,239 DoF, 256 uneven subdomains of 4k-42k DoF, 16 to 31 eigenpairs per
+subdomain growing with its size) in mixed precision, all subdomains in one
+handle as the benchmark runs them.
 
 The oracle cannot solve the whole spar, so parity is checked on sampled
 subdomains against tests/golden/c4_sample_eigs.json (written by
 tests/golden/make_c4_golden.py, which calls only oracle/): the DoF classes of
-each sample and each of its n_loc eigenvalues to 1e-5 relative to itself (the
+each sample and each of its own n_loc eigenvalues to 1e-5 relative to itself (the
 rigid zeros absolutely at that fraction of the largest).  For the rest, properties that hold at any size: every subdomain's
-eigen-residual below tolerance, the coarse dimension equal to the basis sizes
+eigen-residual below tolerance, its eigenpair count as asked, the other entries
+of its eigenvalue row NaN, the coarse dimension equal to the basis sizes
 reported per subdomain, zero displacement on the clamped face, and the energy
 of u^G (b^T u^G, the squared energy norm of a Galerkin projection) positive.
 """
@@ -30,20 +32,27 @@ def test_c4_sampled_subdomains_mixed():
     from oracle.mesh import make_mesh
     from paper_2211_13893_gb300 import MSGFEM
     from workloads import element_angles, get_config
+    from workloads.section import n_loc_per_subdomain
     gold = json.load(open(GOLD))
     cfg = get_config("c4")
+    counts = n_loc_per_subdomain(cfg)
+    assert counts.min() == 16 and counts.max() == 31
     ang = torch.tensor(element_angles(cfg).reshape(-1), dtype=torch.float64, device="cuda")
     m = MSGFEM.from_config(cfg, ang, seed=11, precision=1)
     assert m.N == 256
-    lam = m.local_spaces(cfg.n_loc)
+    lam = m.local_spaces(counts)
     infos = [m.info(j) for j in range(m.N)]
     for key, rec in gold["samples"].items():
         j = int(key)
         inf = infos[j]
         assert (inf["n_star_dof"], inf["n1"], inf["n2"], inf["n3"]) == (rec["n_star_dof"], rec["n1"], rec["n2"],
                                                                            rec["n3"])
-        assert_eigs(lam[j], np.array(rec["lambda"]), 1e-5, j)
+        assert rec["n_loc"] == counts[j]
+        assert_eigs(lam[j, :counts[j]], np.array(rec["lambda"]), 1e-5, j)
     assert max(i["residual"] for i in infos) < 1e-5
+    assert [i["n_loc"] for i in infos] == counts.tolist()
+    for j in range(m.N):
+        assert np.all(np.isfinite(lam[j, :counts[j]])) and np.all(np.isnan(lam[j, counts[j]:]))
     nc = m.coarse_assemble()
     assert nc == sum(m.info(j)["basis_size"] for j in range(m.N))
     u, _ = m.solve()

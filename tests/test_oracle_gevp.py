@@ -180,3 +180,26 @@ def test_threshold_selection_nested_and_exhaustive():
             assert cnt <= sub_full
         assert r.energy_error <= prev * (1 + 1e-12)
         prev = r.energy_error
+
+
+def test_per_subdomain_sizes_nested():
+    """One n_loc per subdomain (the m_j of Eq. AHarmonic_coarse_space): every
+    subdomain gets exactly its own count of eigenpairs, and raising any single
+    subdomain's count enlarges the coarse space, so the Galerkin energy error
+    cannot increase (a count read from the wrong subdomain breaks one of the
+    two); the largest counts everywhere give the uniform result."""
+    cfg = get_config("t2")
+    base = [4, 7, 5, 9, 6, 8]
+    ref = run_msgfem(cfg, n_loc=base)
+    assert [len(lam) for lam in ref.lam] == base
+    assert [phi.shape[1] for phi in ref.phi] == base
+    for j in range(len(base)):
+        up = list(base)
+        up[j] += 3
+        r = run_msgfem(cfg, n_loc=up, uh=ref.uh)
+        assert [len(lam) for lam in r.lam] == up
+        assert r.basis_counts[j] > ref.basis_counts[j]
+        assert r.energy_error <= ref.energy_error * (1 + 1e-12)
+        assert r.energy_error < ref.energy_error * (1 - 1e-6)
+    top = run_msgfem(cfg, n_loc=[cfg.n_loc] * len(base), uh=ref.uh)
+    assert top.energy_error == run_msgfem(cfg, uh=ref.uh).energy_error

@@ -49,3 +49,18 @@ def test_section_frames_orthonormal_and_tangent():
         chord = X[j + 1] - X[j]
         assert np.allclose(R[1, 1:], chord / np.linalg.norm(chord))
         assert np.allclose(R[0], [1.0, 0.0, 0.0])
+
+
+def test_per_subdomain_eigenpair_counts():
+    """c4: 16 eigenpairs on the smallest oversampling domain, 31 on the largest,
+    never fewer on a larger domain; a section without n_loc_max keeps one count."""
+    from workloads.section import n_loc_per_subdomain, omega_star_sizes
+    cfg = get_config("c4")
+    n = n_loc_per_subdomain(cfg)
+    d = omega_star_sizes(cfg)
+    assert n.shape == (256,) and n.dtype == np.int32
+    assert n[np.argmin(d)] == 16 and n[np.argmax(d)] == 31 and n.min() == 16 and n.max() == 31
+    order = np.argsort(d, kind="stable")
+    assert np.all(np.diff(n[order]) >= 0)
+    s = get_config("s2")
+    assert np.all(n_loc_per_subdomain(s) == s.n_loc)

@@ -51,6 +51,7 @@ class SectionConfig:
     overlap: int = 1
     oversampling: int = 3
     n_loc: int = 16
+    n_loc_max: int = 0           # > n_loc: per-subdomain counts from n_loc to this (n_loc_per_subdomain)
     layup_seed: int = 0
     noise_sd_deg: float = 0.0    # per-ply Gaussian angle noise (as for the beams)
     noise_seed: int = 1
@@ -191,6 +192,20 @@ def omega_star_sizes(cfg):
     return np.array(out)
 
 
+def n_loc_per_subdomain(cfg):
+    """Eigenpairs per subdomain: cfg.n_loc everywhere, or, with n_loc_max above
+    it, counts growing linearly with the oversampling domain's DoF count from
+    n_loc (the smallest domain) to n_loc_max (the largest), rounded to the
+    nearest integer.  Interior subdomains need more eigenvectors for the same
+    local error (Sec. 5.3), and the domains cut short by the clamped end, the
+    free end or a flange tip are the small ones."""
+    sizes = omega_star_sizes(cfg)
+    if cfg.n_loc_max <= cfg.n_loc or sizes.max() == sizes.min():
+        return np.full(len(sizes), cfg.n_loc, dtype=np.int32)
+    frac = (sizes - sizes.min()) / float(sizes.max() - sizes.min())
+    return (cfg.n_loc + np.floor((cfg.n_loc_max - cfg.n_loc) * frac + 0.5)).astype(np.int32)
+
+
 SECTIONS = {
     # C-section spar of 1 m: web 200 mm, flanges 60 mm, inner radius 8 mm, 32 plies
     # of 0.25 mm; 4 mm elements along x and the straight segments, ~1 mm on the
@@ -198,9 +213,10 @@ SECTIONS = {
     # 16 x 16 boxes, graded along x (1 element at the clamped end, ~21 in the
     # span) and along the arc (short boxes at the flange tips, three per corner,
     # six on the web); overlap 1, oversampling 3: oversampling domains of
-    # 4,455 to 41,580 DoF (mean 29,570).
+    # 4,455 to 41,580 DoF (mean 29,570); 16 to 31 eigenpairs per subdomain,
+    # growing with the domain's size.
     "c4": SectionConfig("c4", xparts=(1, 2, 4, 8, 12, 20, 20, 20, 20, 21, 21, 21, 21, 21, 21, 17),
-                        sparts=(5, 8, 7, 6, 6, 8, 7, 8, 8, 7, 8, 6, 6, 7, 8, 5), n_loc=16),
+                        sparts=(5, 8, 7, 6, 6, 8, 7, 8, 8, 7, 8, 6, 6, 7, 8, 5), n_loc=16, n_loc_max=31),
     # test sections: curved corners, clamped / floating / interior subdomains
     "s1": SectionConfig("s1", length=24.0, web=12.0, flange=8.0, radius=2.0, n_plies=4, t=0.5,
                         h_len=3.0, h_arc=2.0, h_corner=1.0, xparts=(3, 5), sparts=(5, 5, 5, 5),
