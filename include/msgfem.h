@@ -378,8 +378,8 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out);
 /* msgfem_local_spaces with its own n_loc for every subdomain: the local basis
  * sizes m_j of Eq. AHarmonic_coarse_space, which differ between subdomains
  * (Sec. 5.3: interior subdomains need more eigenvectors for the same local
- * error; Sec. 5.5: m_j from 60 to 170 on the C-spar).  n_loc: N
- * host ints, n_loc[j] eigenpairs of subdomain j, each within the limits of
+ * error; Sec. 5.5: m_j from 60 to 170 on the C-spar).  n_loc: N ints
+ * (host or device, copied), n_loc[j] eigenpairs of subdomain j, each within the limits of
  * msgfem_local_spaces.  lambda_out (may be NULL; host or device) receives
  * N * n_max doubles, n_max the largest n_loc[j], subdomain-major; entries
  * c >= n_loc[j] of row j are NaN.  msgfem_get_basis and msgfem_export_local

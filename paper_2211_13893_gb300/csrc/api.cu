@@ -1142,7 +1142,9 @@ msgfem_status msgfem_local_spaces(msgfem_h h, int n_loc, double* lambda_out) {
 msgfem_status msgfem_local_spaces_var(msgfem_h h, const int* n_loc, double* lambda_out) {
   if (!h) return MSGFEM_EINVAL;
   if (!n_loc) { h->err = "msgfem_local_spaces_var: n_loc is NULL"; return MSGFEM_EINVAL; }
-  const msgfem_status st = local_spaces_run(h, std::vector<int>(n_loc, n_loc + h->N), lambda_out);
+  std::vector<int> nl(h->N);
+  CK(cudaMemcpy(nl.data(), n_loc, h->N * sizeof(int), cudaMemcpyDefault));   // host or device
+  const msgfem_status st = local_spaces_run(h, nl, lambda_out);
   const msgfem_status ke = check_stage_error(h);
   return ke != MSGFEM_OK ? ke : st;
 }

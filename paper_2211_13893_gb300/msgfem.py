@@ -275,12 +275,18 @@ class MSGFEM:
             out = lam_out if lam_out is not None else np.zeros((self.N, n_loc))
             self._check(self.lib.msgfem_local_spaces(self.h, n_loc, _ptr(out)), allow=allow)
             return out
-        counts = np.ascontiguousarray(n_loc, dtype=np.int32).reshape(-1)
-        if counts.shape[0] != self.N:
-            raise ValueError(f"n_loc needs one count per subdomain ({self.N}), got {counts.shape[0]}")
+        if hasattr(n_loc, "data_ptr"):       # a device (or host) tensor of int32 counts
+            if n_loc.numel() != self.N or str(n_loc.dtype) != "torch.int32" or not n_loc.is_contiguous():
+                raise ValueError(f"n_loc needs {self.N} contiguous int32 counts")
+            counts, ptr = n_loc.cpu().numpy(), n_loc.data_ptr()
+        else:
+            counts = np.ascontiguousarray(n_loc, dtype=np.int32).reshape(-1)
+            if counts.shape[0] != self.N:
+                raise ValueError(f"n_loc needs one count per subdomain ({self.N}), got {counts.shape[0]}")
+            ptr = counts.ctypes.data
         self.n_loc = int(counts.max())
         out = lam_out if lam_out is not None else np.zeros((self.N, self.n_loc))
-        self._check(self.lib.msgfem_local_spaces_var(self.h, counts.ctypes.data, _ptr(out)), allow=allow)
+        self._check(self.lib.msgfem_local_spaces_var(self.h, ptr, _ptr(out)), allow=allow)
         return out
 
     def coarse_assemble(self, threshold=None):

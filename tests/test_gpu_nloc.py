@@ -131,3 +131,19 @@ def test_per_subdomain_counts_refused():
     lam = m.local_spaces(cfg.n_loc)
     assert np.all(np.isfinite(lam))
     m.close()
+
+
+def test_per_subdomain_counts_from_device_memory():
+    """The counts may live in device memory: the same counts and eigenvalues as
+    from a host array (a second local stage on the same handle)."""
+    import torch
+    from paper_2211_13893_gb300 import MSGFEM
+    cfg = get_config("t2")
+    counts = np.array([8, 10, 7, 9, 10, 8], dtype=np.int32)
+    m = MSGFEM.from_config(cfg, element_angles(cfg), seed=4)
+    a = m.local_spaces(counts).copy()
+    b = m.local_spaces(torch.tensor(counts, device="cuda"))
+    assert np.allclose(a, b, rtol=1e-12, atol=1e-12, equal_nan=True)
+    assert np.array_equal(np.isnan(a), np.isnan(b))
+    assert [m.info(j)["n_loc"] for j in range(m.N)] == counts.tolist()
+    m.close()
