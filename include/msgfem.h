@@ -398,9 +398,10 @@ msgfem_status msgfem_coarse_assemble(msgfem_h h, int* coarse_dim_out);
 /* msgfem_coarse_assemble with local basis sizes chosen by an eigenvalue
  * threshold (Sec. 5.5, Sec. 5.6; the error bound of Thm. error_bound is driven
  * by 1 / lambda_{j, m_j + 1}): subdomain j keeps its eigenvectors with
- * 1 / lambda > t (rigid modes always), m_j <= n_loc of the last local stage;
- * t = 0 keeps all n_loc (msgfem_coarse_assemble).  When all n_loc eigenvalues
- * of a subdomain are below 1 / t its msgfem_subinfo.threshold_reached is 0.
+ * 1 / lambda > t (rigid modes always), m_j <= the subdomain's n_loc in the
+ * last local stage; t = 0 keeps all of them (msgfem_coarse_assemble).  When all
+ * of a subdomain's eigenvalues are below 1 / t its
+ * msgfem_subinfo.threshold_reached is 0.
  * Errors: EINVAL (t < 0), ESTATE, ENOTSPD. */
 msgfem_status msgfem_coarse_assemble_threshold(msgfem_h h, double t, int* coarse_dim_out);
 
